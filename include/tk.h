@@ -1,0 +1,187 @@
+/*
+ * tk.h -- C ABI of the GB300 symmetric TensorMap contraction library (libtk).
+ *
+ * The library contracts two symmetric tensor maps whose legs are graded spaces of Z2, U(1) or
+ * SU(2) sectors with multiplicities, following the statement of the problem in the TensorKit
+ * paper (arXiv 2508.10076):
+ *   - a graded space is a list of (sector, multiplicity) pairs plus a duality flag (Sec. 5.2);
+ *   - a tensor map t : W_1 (x) ... (x) W_N2 -> V_1 (x) ... (x) V_N1 is stored as one block per
+ *     coupled sector, each block holding the reduced arrays of its fusion-tree pairs
+ *     (Sec. 3.2 eq. abeliangrouping, Sec. 4.1 canonical trees and block embedding);
+ *   - permute(t, (p, q)) follows Algorithm 2 (non-abelian: Algorithm 10);
+ *   - contract follows Algorithm 4 / Algorithm 8: permute A, permute B, one GEMM per coupled
+ *     sector (zero block when the inner dimension is empty), permute the result.
+ *
+ * Conventions
+ *   - Sector encoding: Z2 in {0,1}; U(1) integer charge; SU(2) twice the spin (2j).
+ *   - Leg numbering is 0-based: codomain legs 0..N1-1, then domain legs N1..N1+N2-1 in forward
+ *     order (the paper numbers them from 1, Algorithm 2).
+ *   - Storage layout (fixed; the paper leaves the order "arbitrary but fixed"): blocks by coupled
+ *     sector ascending, each block a column-major rows x cols matrix, blocks concatenated; inside a
+ *     block the canonical trees occupy consecutive row (splitting) / column (fusion) ranges,
+ *     trees ordered colexicographically (first leg fastest) by uncoupled labels, then by inner
+ *     labels; a reduced array is column-major with the first leg fastest.  A leg of a dual space
+ *     carries the dual sector as its tree label.
+ *   - Element types: TK_F64 (double) and TK_C128 (interleaved double real/imag).
+ *
+ * Ownership: every object returned through an out-parameter is owned by the caller and released
+ * with the matching *_destroy.  Device buffers passed to execution calls are borrowed; the
+ * library never frees them.  Plans own their device-resident task tables.
+ *
+ * Errors: every int-returning call returns TK_OK (0) or a TK_ERR_* code; no exception crosses the
+ * ABI.  tk_ctx_last_error() gives a message for the last failure on that context.  Kernel
+ * launches are asynchronous: device-side failures (a bounded wait that gave up, a launch error)
+ * are reported by the next tk_ctx_sync().
+ */
+#ifndef TK_H
+#define TK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define TK_OK 0
+#define TK_ERR_ARG 1            /* invalid argument (null pointer, bad size, bad enum)        */
+#define TK_ERR_SPACE_MISMATCH 2 /* domain(A~) != codomain(B~) including duality (Sec. 2.3)    */
+#define TK_ERR_PERM 3           /* (p, q) is not a permutation of the legs (Algorithm 2)      */
+#define TK_ERR_SECTOR 4         /* sector label not valid for the symmetry                    */
+#define TK_ERR_OOM 5            /* host or device allocation failed                           */
+#define TK_ERR_CUDA 6           /* a CUDA runtime call failed                                 */
+#define TK_ERR_UNSUPPORTED 7    /* valid request this build does not implement                */
+#define TK_ERR_TIMEOUT 8        /* a bounded device-side wait gave up                         */
+#define TK_ERR_WORKSPACE 9      /* workspace too small                                        */
+#define TK_ERR_NO_DEVICE 10     /* execution call on a host-only context                      */
+
+/* ---- enums ------------------------------------------------------------------------------ */
+#define TK_SYM_Z2 0
+#define TK_SYM_U1 1
+#define TK_SYM_SU2 2
+
+#define TK_F64 0
+#define TK_C128 1
+
+/* GEMM arithmetic of the per-sector products (step 2 of Algorithm 8). */
+#define TK_GEMM_FP64 0       /* plain FP64 on the CUDA cores                                   */
+#define TK_GEMM_OZAKI_BF16 1 /* FP64 operands split into BF16 slices, tcgen05 products, FP32
+                                exact accumulation of the leading levels, FP64 recombination */
+#define TK_GEMM_TF32X3 2     /* 3xTF32 on tcgen05 (about FP32 accuracy; reported, not gated)   */
+
+typedef struct tk_ctx tk_ctx;
+typedef struct tk_space tk_space;
+typedef struct tk_tmap tk_tmap;
+typedef struct tk_plan tk_plan;
+
+/* ---- library ---------------------------------------------------------------------------- */
+int tk_version(void);                       /* major*10000 + minor*100 + patch              */
+const char* tk_status_string(int status);   /* static string, never NULL                    */
+
+/* ---- context ------------------------------------------------------------------------------
+ * device >= 0: the CUDA device all plans and launches of this context use (it is made current
+ * inside every call).  device < 0: host-only context -- spaces, tensor structures and plans can
+ * be built and inspected, execution calls return TK_ERR_NO_DEVICE. */
+int tk_ctx_create(int device, tk_ctx** out);
+void tk_ctx_destroy(tk_ctx* ctx);
+const char* tk_ctx_last_error(const tk_ctx* ctx);
+/* Waits for `stream` (a cudaStream_t, NULL = legacy default) and reports deferred device errors
+ * (TK_ERR_TIMEOUT if a bounded wait gave up, TK_ERR_CUDA for launch/runtime failures). */
+int tk_ctx_sync(tk_ctx* ctx, void* stream);
+/* Number of the library's own kernels launched through this context so far. */
+int64_t tk_ctx_launch_count(const tk_ctx* ctx);
+
+/* ---- graded spaces (Sec. 3.1 eq. gradedbasis, Sec. 5.2) ----------------------------------
+ * sectors[i], mults[i] for i < nsec: sector labels (unique) and positive multiplicities.
+ * is_dual != 0 makes the space V*.  The object is immutable. */
+int tk_space_create(tk_ctx* ctx, int sym, int nsec, const int32_t* sectors, const int64_t* mults,
+                    int is_dual, tk_space** out);
+int tk_space_dual(tk_ctx* ctx, const tk_space* v, tk_space** out);  /* V -> V*              */
+void tk_space_destroy(tk_space* v);
+int64_t tk_space_dim(const tk_space* v);          /* sum_a n_a d_a  (-1 on NULL)              */
+int64_t tk_space_reduced_dim(const tk_space* v);  /* sum_a n_a      (-1 on NULL)              */
+
+/* ---- tensor map structures ----------------------------------------------------------------
+ * t : dom[0] (x) ... (x) dom[n_dom-1] -> cod[0] (x) ... (x) cod[n_cod-1]; n_cod + n_dom in
+ * [1, 8].  The structure owns copies of the spaces.  Data is not attached: execution calls
+ * take device pointers laid out as described at the top of this file. */
+int tk_tmap_create(tk_ctx* ctx, int n_cod, const tk_space* const* cod, int n_dom,
+                   const tk_space* const* dom, tk_tmap** out);
+void tk_tmap_destroy(tk_tmap* t);
+int64_t tk_tmap_numel(const tk_tmap* t);          /* number of stored scalars                  */
+int tk_tmap_nlegs(const tk_tmap* t, int* n_cod, int* n_dom);
+int tk_tmap_leg(tk_ctx* ctx, const tk_tmap* t, int leg, tk_space** out);  /* copy of a leg   */
+uint64_t tk_tmap_hash(const tk_tmap* t);          /* structure hash (spaces and duality)       */
+int tk_tmap_nblocks(const tk_tmap* t);
+/* i-th block (coupled sector ascending): sector label, rows, cols, element offset. */
+int tk_tmap_block(const tk_tmap* t, int i, int32_t* sector, int64_t* rows, int64_t* cols,
+                  int64_t* offset);
+int64_t tk_tmap_ntreepairs(const tk_tmap* t);
+/* i-th fusion-tree pair (block order, then splitting tree, then fusion tree).  labels receives
+ * N1 + N2 uncoupled labels, then max(N1-2,0) splitting inner labels, the coupled sector, and
+ * max(N2-2,0) fusion inner labels; dims receives the N1 + N2 extents of the reduced array.
+ * offset = element offset of its first entry, ld = rows of its block.  Any out pointer may be
+ * NULL. */
+int tk_tmap_treepair(const tk_tmap* t, int64_t i, int32_t* labels, int64_t* offset, int64_t* ld,
+                     int64_t* dims);
+
+/* ---- plans ------------------------------------------------------------------------------------
+ * A plan holds everything that depends only on structure: output spaces (Algorithm 2),
+ * recoupling coefficients of every fusion-tree transform (F-, B- and R-moves with 6j symbols
+ * from the Racah formula, Sec. 4.2), sector matching and the GEMM/zero-fill lists
+ * (Algorithm 8), and the device task tables.  Plans are cached per context by structure hash,
+ * so creating the same plan twice is cheap. */
+int tk_permute_plan(tk_ctx* ctx, const tk_tmap* a, int np, const int* p, int nq, const int* q,
+                    int dtype, tk_plan** out);
+/* Algorithm 4: A~ = permute(A, (pa, qa)), B~ = permute(B, (pb, qb)), C~ = A~ o B~,
+ * C = permute(C~, (pab, qab)).  (pab, qab) index the legs of C~ = codomain(A~) then domain(B~).
+ * gemm_mode is TK_GEMM_*; slices is the number of BF16 slices per operand for
+ * TK_GEMM_OZAKI_BF16 (0 = default), ignored otherwise. */
+int tk_contract_plan(tk_ctx* ctx, const tk_tmap* a, int npa, const int* pa, int nqa, const int* qa,
+                     const tk_tmap* b, int npb, const int* pb, int nqb, const int* qb,
+                     int npab, const int* pab, int nqab, const int* qab, int dtype, int gemm_mode,
+                     int slices, tk_plan** out);
+void tk_plan_destroy(tk_plan* plan);
+int tk_plan_output(tk_ctx* ctx, const tk_plan* plan, tk_tmap** out);  /* result structure     */
+size_t tk_plan_workspace_bytes(const tk_plan* plan);  /* device scratch needed by tk_contract  */
+/* Block flops of the plan: sum over executed sector GEMMs of 2 M K N (8 M K N complex), using
+ * reduced sizes -- each SU(2) block once (Sec. 4.4). */
+double tk_plan_flops(const tk_plan* plan);
+/* Algorithmic bytes moved by the plan's permute launches (each source element read once per
+ * use, each output element written once). */
+double tk_plan_permute_bytes(const tk_plan* plan);
+
+/* Host-side inspection of a plan's permute transforms (works on host-only contexts).
+ * which: 0 = permute of A (or the permute plan), 1 = permute of B, 2 = permute of the result.
+ * Entry k is one (source tree pair, destination tree pair, coefficient) term of Algorithm 10,
+ * tree pairs identified by the element offsets of their first entries.  Returns the count, or -1
+ * if that permute is absent (identity permutes are skipped). */
+int64_t tk_plan_ntransform(const tk_plan* plan, int which);
+int tk_plan_transform(const tk_plan* plan, int which, int64_t k, int64_t* src_offset,
+                      int64_t* dst_offset, double* coef);
+
+/* ---- execution (asynchronous on `stream`, a cudaStream_t; NULL = legacy default stream) -------
+ * All pointers are device pointers to buffers laid out as the plan's input/output structures.
+ * C is fully overwritten.  A and B are never modified. */
+int tk_permute(tk_ctx* ctx, const tk_plan* plan, const void* a, void* c, void* stream);
+int tk_contract(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, void* c,
+                void* workspace, size_t workspace_bytes, void* stream);
+
+/* Host <-> device copies on the context's device (cudaMemcpyAsync; pinned host memory makes
+ * them asynchronous). */
+int tk_copy_h2d(tk_ctx* ctx, void* dst_device, const void* src_host, size_t bytes, void* stream);
+int tk_copy_d2h(tk_ctx* ctx, void* dst_host, const void* src_device, size_t bytes, void* stream);
+
+/* ---- topological data (host, exact) ----------------------------------------------------------
+ * F^{abc}_d[e; f] (e couples (a b), f couples (b c)): for SU(2) eq. SU2FSymbol with the 6j symbol
+ * from Racah's formula evaluated in exact integer arithmetic and rounded once to the nearest
+ * double; 1 or 0 for abelian symmetries.  R^{ab}_c (eq. braiding): SU(2) (-1)^(a+b-c).
+ * Inadmissible labels give 0. */
+double tk_fsymbol(int sym, int32_t a, int32_t b, int32_t c, int32_t d, int32_t e, int32_t f);
+double tk_rsymbol(int sym, int32_t a, int32_t b, int32_t c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TK_H */

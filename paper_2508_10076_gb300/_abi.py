@@ -1,0 +1,76 @@
+"""ctypes declarations of the libtk C ABI (include/tk.h).  Argument marshalling only.
+
+Loading fails loudly if the shared library is missing: there is no fallback path.
+"""
+
+import ctypes as C
+import os
+
+from .build import LIB
+
+c_i32p = C.POINTER(C.c_int32)
+c_i64p = C.POINTER(C.c_int64)
+c_intp = C.POINTER(C.c_int)
+c_dblp = C.POINTER(C.c_double)
+c_vp = C.c_void_p
+
+# name: (restype, argtypes)
+SIGNATURES = {
+    "tk_version": (C.c_int, []),
+    "tk_status_string": (C.c_char_p, [C.c_int]),
+    "tk_ctx_create": (C.c_int, [C.c_int, C.POINTER(c_vp)]),
+    "tk_ctx_destroy": (None, [c_vp]),
+    "tk_ctx_last_error": (C.c_char_p, [c_vp]),
+    "tk_ctx_sync": (C.c_int, [c_vp, c_vp]),
+    "tk_ctx_launch_count": (C.c_int64, [c_vp]),
+    "tk_space_create": (C.c_int, [c_vp, C.c_int, C.c_int, c_i32p, c_i64p, C.c_int, C.POINTER(c_vp)]),
+    "tk_space_dual": (C.c_int, [c_vp, c_vp, C.POINTER(c_vp)]),
+    "tk_space_destroy": (None, [c_vp]),
+    "tk_space_dim": (C.c_int64, [c_vp]),
+    "tk_space_reduced_dim": (C.c_int64, [c_vp]),
+    "tk_tmap_create": (C.c_int, [c_vp, C.c_int, C.POINTER(c_vp), C.c_int, C.POINTER(c_vp), C.POINTER(c_vp)]),
+    "tk_tmap_destroy": (None, [c_vp]),
+    "tk_tmap_numel": (C.c_int64, [c_vp]),
+    "tk_tmap_nlegs": (C.c_int, [c_vp, c_intp, c_intp]),
+    "tk_tmap_leg": (C.c_int, [c_vp, c_vp, C.c_int, C.POINTER(c_vp)]),
+    "tk_tmap_hash": (C.c_uint64, [c_vp]),
+    "tk_tmap_nblocks": (C.c_int, [c_vp]),
+    "tk_tmap_block": (C.c_int, [c_vp, C.c_int, c_i32p, c_i64p, c_i64p, c_i64p]),
+    "tk_tmap_ntreepairs": (C.c_int64, [c_vp]),
+    "tk_tmap_treepair": (C.c_int, [c_vp, C.c_int64, c_i32p, c_i64p, c_i64p, c_i64p]),
+    "tk_permute_plan": (C.c_int, [c_vp, c_vp, C.c_int, c_intp, C.c_int, c_intp, C.c_int, C.POINTER(c_vp)]),
+    "tk_contract_plan": (C.c_int, [c_vp, c_vp, C.c_int, c_intp, C.c_int, c_intp, c_vp, C.c_int, c_intp,
+                                   C.c_int, c_intp, C.c_int, c_intp, C.c_int, c_intp, C.c_int, C.c_int,
+                                   C.c_int, C.POINTER(c_vp)]),
+    "tk_plan_destroy": (None, [c_vp]),
+    "tk_plan_output": (C.c_int, [c_vp, c_vp, C.POINTER(c_vp)]),
+    "tk_plan_workspace_bytes": (C.c_size_t, [c_vp]),
+    "tk_plan_flops": (C.c_double, [c_vp]),
+    "tk_plan_permute_bytes": (C.c_double, [c_vp]),
+    "tk_plan_ntransform": (C.c_int64, [c_vp, C.c_int]),
+    "tk_plan_transform": (C.c_int, [c_vp, C.c_int, C.c_int64, c_i64p, c_i64p, c_dblp]),
+    "tk_permute": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "tk_contract": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
+    "tk_copy_h2d": (C.c_int, [c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
+    "tk_copy_d2h": (C.c_int, [c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
+    "tk_fsymbol": (C.c_double, [C.c_int, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "tk_rsymbol": (C.c_double, [C.c_int, C.c_int32, C.c_int32, C.c_int32]),
+}
+
+_LIB = None
+
+
+def load(path: str = LIB):
+    """Load libtk.so (build it first with paper_2508_10076_gb300.build.build_library())."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtk.so not found at {path}; run paper_2508_10076_gb300.build.build_library()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib

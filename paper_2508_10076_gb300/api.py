@@ -1,0 +1,287 @@
+"""Thin Python objects over the libtk C ABI.  Every step of the path runs in libtk's kernels;
+this module only marshals arguments (PyTorch provides device memory and streams)."""
+
+import ctypes as C
+
+from . import _abi
+
+SYM = {"Z2": 0, "U1": 1, "SU2": 2}
+DTYPE = {"f64": 0, "c128": 1}
+GEMM = {"fp64": 0, "ozaki": 1, "tf32x3": 2}
+
+
+class TKError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libtk error {code}: {msg}")
+        self.code = code
+
+
+def _lib():
+    return _abi.load()
+
+
+def _check(rc, ctx=None):
+    if rc != 0:
+        lib = _lib()
+        msg = lib.tk_status_string(rc).decode()
+        if ctx is not None:
+            detail = lib.tk_ctx_last_error(ctx._h).decode()
+            if detail:
+                msg += ": " + detail
+        raise TKError(rc, msg)
+
+
+def _ints(xs, ctype=C.c_int):
+    xs = [int(x) for x in xs]
+    arr = (ctype * max(1, len(xs)))(*xs) if xs else (ctype * 1)()
+    return arr, len(xs)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return C.c_void_p(0)
+    if isinstance(t, int):
+        return C.c_void_p(t)
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """device >= 0: CUDA device; device < 0: host-only (planning and inspection only)."""
+
+    def __init__(self, device: int = 0):
+        self._h = C.c_void_p()
+        _check(_lib().tk_ctx_create(int(device), C.byref(self._h)))
+        self.device = device
+
+    def close(self):
+        if self._h:
+            _lib().tk_ctx_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self, stream=None):
+        _check(_lib().tk_ctx_sync(self._h, _stream_handle(stream)), self)
+
+    @property
+    def launches(self):
+        return int(_lib().tk_ctx_launch_count(self._h))
+
+    # ---- objects
+    def space(self, sym, sectors, dual=False):
+        return Space(self, sym, sectors, dual)
+
+    def tmap(self, cod, dom):
+        return TensorMap(self, cod, dom)
+
+
+class Space:
+    def __init__(self, ctx, sym, sectors, dual=False, _handle=None):
+        self.ctx = ctx
+        self._h = C.c_void_p()
+        if _handle is not None:
+            self._h = _handle
+        else:
+            items = sorted(dict(sectors).items())
+            secs, n = _ints([a for a, _ in items], C.c_int32)
+            mults, _ = _ints([m for _, m in items], C.c_int64)
+            _check(_lib().tk_space_create(ctx._h, SYM[sym] if isinstance(sym, str) else int(sym), n, secs,
+                                          mults, int(bool(dual)), C.byref(self._h)), ctx)
+
+    def __del__(self):
+        try:
+            if self._h:
+                _lib().tk_space_destroy(self._h)
+        except Exception:
+            pass
+
+    def dual(self):
+        h = C.c_void_p()
+        _check(_lib().tk_space_dual(self.ctx._h, self._h, C.byref(h)), self.ctx)
+        return Space(self.ctx, None, None, _handle=h)
+
+    @property
+    def dim(self):
+        return int(_lib().tk_space_dim(self._h))
+
+    @property
+    def reduced_dim(self):
+        return int(_lib().tk_space_reduced_dim(self._h))
+
+
+class TensorMap:
+    """Structure of a tensor map cod[0] (x) ... <- dom[0] (x) ... (no data attached)."""
+
+    def __init__(self, ctx, cod, dom, _handle=None):
+        self.ctx = ctx
+        self._h = C.c_void_p()
+        if _handle is not None:
+            self._h = _handle
+            self._legs = None
+        else:
+            self._legs = (list(cod), list(dom))  # keep the spaces alive
+            ca = (C.c_void_p * max(1, len(cod)))(*[s._h.value for s in cod])
+            da = (C.c_void_p * max(1, len(dom)))(*[s._h.value for s in dom])
+            _check(_lib().tk_tmap_create(ctx._h, len(cod), ca, len(dom), da, C.byref(self._h)), ctx)
+
+    def __del__(self):
+        try:
+            if self._h:
+                _lib().tk_tmap_destroy(self._h)
+        except Exception:
+            pass
+
+    @property
+    def numel(self):
+        return int(_lib().tk_tmap_numel(self._h))
+
+    @property
+    def nlegs(self):
+        a, b = C.c_int(), C.c_int()
+        _check(_lib().tk_tmap_nlegs(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    @property
+    def hash(self):
+        return int(_lib().tk_tmap_hash(self._h))
+
+    def leg(self, i):
+        h = C.c_void_p()
+        _check(_lib().tk_tmap_leg(self.ctx._h, self._h, int(i), C.byref(h)), self.ctx)
+        return Space(self.ctx, None, None, _handle=h)
+
+    def blocks(self):
+        out = []
+        s, r, c, o = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int64()
+        for i in range(_lib().tk_tmap_nblocks(self._h)):
+            _check(_lib().tk_tmap_block(self._h, i, C.byref(s), C.byref(r), C.byref(c), C.byref(o)))
+            out.append((s.value, r.value, c.value, o.value))
+        return out
+
+    def treepairs(self):
+        """[(uncoupled labels, split inner, coupled, fusion inner, offset, ld, dims)]"""
+        n1, n2 = self.nlegs
+        n = n1 + n2
+        ni1, ni2 = max(n1 - 2, 0), max(n2 - 2, 0)
+        lab = (C.c_int32 * (n + ni1 + 1 + ni2))()
+        dims = (C.c_int64 * n)()
+        off, ld = C.c_int64(), C.c_int64()
+        out = []
+        for i in range(_lib().tk_tmap_ntreepairs(self._h)):
+            _check(_lib().tk_tmap_treepair(self._h, i, lab, C.byref(off), C.byref(ld), dims))
+            L = list(lab)
+            out.append((tuple(L[:n]), tuple(L[n:n + ni1]), L[n + ni1], tuple(L[n + ni1 + 1:]),
+                        off.value, ld.value, tuple(dims)))
+        return out
+
+
+class Plan:
+    def __init__(self, ctx, handle, kind):
+        self.ctx, self._h, self.kind = ctx, handle, kind
+
+    def __del__(self):
+        try:
+            if self._h:
+                _lib().tk_plan_destroy(self._h)
+        except Exception:
+            pass
+
+    def output(self):
+        h = C.c_void_p()
+        _check(_lib().tk_plan_output(self.ctx._h, self._h, C.byref(h)), self.ctx)
+        return TensorMap(self.ctx, None, None, _handle=h)
+
+    @property
+    def workspace_bytes(self):
+        return int(_lib().tk_plan_workspace_bytes(self._h))
+
+    @property
+    def flops(self):
+        return float(_lib().tk_plan_flops(self._h))
+
+    @property
+    def permute_bytes(self):
+        return float(_lib().tk_plan_permute_bytes(self._h))
+
+    def transform(self, which=0):
+        """[(src_offset, dst_offset, coef)] of one permute (None when it is the identity)."""
+        lib = _lib()
+        n = lib.tk_plan_ntransform(self._h, int(which))
+        if n < 0:
+            return None
+        s, d, c = C.c_int64(), C.c_int64(), C.c_double()
+        out = []
+        for k in range(n):
+            _check(lib.tk_plan_transform(self._h, int(which), k, C.byref(s), C.byref(d), C.byref(c)))
+            out.append((s.value, d.value, c.value))
+        return out
+
+
+def permute_plan(ctx, t, p, q, dtype="f64"):
+    pa, npa = _ints(p)
+    qa, nqa = _ints(q)
+    h = C.c_void_p()
+    _check(_lib().tk_permute_plan(ctx._h, t._h, npa, pa, nqa, qa, DTYPE[dtype], C.byref(h)), ctx)
+    return Plan(ctx, h, "permute")
+
+
+def contract_plan(ctx, a, pa, qa, b, pb, qb, pab, qab, dtype="f64", gemm="fp64", slices=0):
+    args = []
+    for xs in (pa, qa):
+        arr, n = _ints(xs)
+        args += [n, arr]
+    a_args = args
+    args = []
+    for xs in (pb, qb):
+        arr, n = _ints(xs)
+        args += [n, arr]
+    b_args = args
+    c_args = []
+    for xs in (pab, qab):
+        arr, n = _ints(xs)
+        c_args += [n, arr]
+    h = C.c_void_p()
+    _check(_lib().tk_contract_plan(ctx._h, a._h, *a_args, b._h, *b_args, *c_args, DTYPE[dtype],
+                                   GEMM[gemm], int(slices), C.byref(h)), ctx)
+    return Plan(ctx, h, "contract")
+
+
+def permute(ctx, plan, a, c, stream=None):
+    _check(_lib().tk_permute(ctx._h, plan._h, _ptr(a), _ptr(c), _stream_handle(stream)), ctx)
+
+
+def contract(ctx, plan, a, b, c, workspace=None, stream=None):
+    nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(_lib().tk_contract(ctx._h, plan._h, _ptr(a), _ptr(b), _ptr(c), _ptr(workspace),
+                              C.c_size_t(nbytes), _stream_handle(stream)), ctx)
+
+
+def copy_h2d(ctx, dst, src_host_ptr, nbytes, stream=None):
+    _check(_lib().tk_copy_h2d(ctx._h, _ptr(dst), C.c_void_p(src_host_ptr), C.c_size_t(nbytes),
+                              _stream_handle(stream)), ctx)
+
+
+def copy_d2h(ctx, dst_host_ptr, src, nbytes, stream=None):
+    _check(_lib().tk_copy_d2h(ctx._h, C.c_void_p(dst_host_ptr), _ptr(src), C.c_size_t(nbytes),
+                              _stream_handle(stream)), ctx)
+
+
+def fsymbol(sym, a, b, c, d, e, f):
+    return float(_lib().tk_fsymbol(SYM[sym], a, b, c, d, e, f))
+
+
+def rsymbol(sym, a, b, c):
+    return float(_lib().tk_rsymbol(SYM[sym], a, b, c))

@@ -1,0 +1,454 @@
+// extern "C" boundary of libtk: handles, argument checking, error mapping, execution order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <exception>
+#include <new>
+
+#include "tk_internal.hpp"
+
+struct tk_ctx {
+  tk::Ctx c;
+};
+struct tk_space {
+  tk::Space s;
+};
+struct tk_tmap {
+  std::shared_ptr<tk::Structure> st;
+};
+struct tk_plan {
+  int kind = 0;  // 0 permute, 1 contract
+  std::shared_ptr<tk::PermutePlan> perm;
+  std::shared_ptr<tk::ContractPlan> con;
+};
+
+namespace {
+
+int fail(tk_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->c.last_error = msg;
+  return code;
+}
+
+template <typename F>
+int guarded(tk_ctx* ctx, F&& f) {
+  try {
+    return f();
+  } catch (const tk::Error& e) {
+    return fail(ctx, e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, TK_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(ctx, TK_ERR_ARG, e.what());
+  } catch (...) {
+    return fail(ctx, TK_ERR_ARG, "unknown error");
+  }
+}
+
+bool read_perm(int np, const int* p, int nq, const int* q, std::vector<int>& vp, std::vector<int>& vq) {
+  if (np < 0 || nq < 0 || np + nq > 8) return false;
+  if ((np > 0 && !p) || (nq > 0 && !q)) return false;
+  vp.assign(p, p + np);
+  vq.assign(q, q + nq);
+  return true;
+}
+
+int set_device(tk_ctx* ctx) {
+  if (ctx->c.device < 0) return fail(ctx, TK_ERR_NO_DEVICE, "execution call on a host-only context");
+  if (cudaSetDevice(ctx->c.device) != cudaSuccess) return fail(ctx, TK_ERR_CUDA, "cudaSetDevice failed");
+  return TK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tk_version(void) { return 100; }
+
+const char* tk_status_string(int s) {
+  switch (s) {
+    case TK_OK: return "ok";
+    case TK_ERR_ARG: return "invalid argument";
+    case TK_ERR_SPACE_MISMATCH: return "space mismatch";
+    case TK_ERR_PERM: return "invalid permutation";
+    case TK_ERR_SECTOR: return "invalid sector";
+    case TK_ERR_OOM: return "out of memory";
+    case TK_ERR_CUDA: return "CUDA error";
+    case TK_ERR_UNSUPPORTED: return "unsupported";
+    case TK_ERR_TIMEOUT: return "device wait timed out";
+    case TK_ERR_WORKSPACE: return "workspace too small";
+    case TK_ERR_NO_DEVICE: return "host-only context";
+  }
+  return "unknown status";
+}
+
+int tk_ctx_create(int device, tk_ctx** out) {
+  if (!out) return TK_ERR_ARG;
+  *out = nullptr;
+  tk_ctx* ctx = new (std::nothrow) tk_ctx();
+  if (!ctx) return TK_ERR_OOM;
+  ctx->c.device = device < 0 ? -1 : device;
+  if (device >= 0) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device >= n) {
+      delete ctx;
+      return TK_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->c.num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+      delete ctx;
+      return TK_ERR_CUDA;
+    }
+    if (cudaMalloc((void**)&ctx->c.d_status, sizeof(int) * 4) != cudaSuccess) {
+      delete ctx;
+      return TK_ERR_OOM;
+    }
+    cudaMemset(ctx->c.d_status, 0, sizeof(int) * 4);
+  }
+  *out = ctx;
+  return TK_OK;
+}
+
+void tk_ctx_destroy(tk_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->c.device >= 0) {
+    cudaSetDevice(ctx->c.device);
+    ctx->c.perm_cache.clear();
+    ctx->c.contract_cache.clear();
+    if (ctx->c.d_status) cudaFree(ctx->c.d_status);
+  }
+  delete ctx;
+}
+
+const char* tk_ctx_last_error(const tk_ctx* ctx) { return ctx ? ctx->c.last_error.c_str() : "null context"; }
+
+int tk_ctx_sync(tk_ctx* ctx, void* stream) {
+  if (!ctx) return TK_ERR_ARG;
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(ctx, TK_ERR_CUDA, std::string("stream sync: ") + cudaGetErrorString(e));
+  int status[4] = {0, 0, 0, 0};
+  if (cudaMemcpy(status, ctx->c.d_status, sizeof(status), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(ctx, TK_ERR_CUDA, "reading device status failed");
+  if (status[0] != 0) {
+    cudaMemset(ctx->c.d_status, 0, sizeof(int) * 4);
+    return fail(ctx, TK_ERR_TIMEOUT, "a bounded device-side wait gave up (kernel tag " +
+                                         std::to_string(status[1]) + ")");
+  }
+  return TK_OK;
+}
+
+int64_t tk_ctx_launch_count(const tk_ctx* ctx) { return ctx ? ctx->c.launches : -1; }
+
+int tk_space_create(tk_ctx* ctx, int sym, int nsec, const int32_t* sectors, const int64_t* mults,
+                    int is_dual, tk_space** out) {
+  if (!out) return fail(ctx, TK_ERR_ARG, "null out");
+  *out = nullptr;
+  if (sym < 0 || sym > 2) return fail(ctx, TK_ERR_ARG, "unknown symmetry");
+  if (nsec <= 0 || !sectors || !mults) return fail(ctx, TK_ERR_ARG, "a space needs at least one sector");
+  return guarded(ctx, [&]() {
+    std::vector<std::pair<int32_t, int64_t>> v;
+    for (int i = 0; i < nsec; ++i) {
+      if (!tk::sector_valid(sym, sectors[i])) return fail(ctx, TK_ERR_SECTOR, "invalid sector label");
+      if (mults[i] <= 0) return fail(ctx, TK_ERR_ARG, "multiplicities must be positive");
+      v.push_back({sectors[i], mults[i]});
+    }
+    std::sort(v.begin(), v.end());
+    for (size_t i = 1; i < v.size(); ++i)
+      if (v[i].first == v[i - 1].first) return fail(ctx, TK_ERR_ARG, "duplicate sector");
+    auto* s = new tk_space();
+    s->s.sym = sym;
+    for (auto& kv : v) {
+      s->s.sectors.push_back(kv.first);
+      s->s.mults.push_back(kv.second);
+    }
+    s->s.dual = is_dual != 0;
+    s->s.finalize();
+    *out = s;
+    return TK_OK;
+  });
+}
+
+int tk_space_dual(tk_ctx* ctx, const tk_space* v, tk_space** out) {
+  if (!v || !out) return fail(ctx, TK_ERR_ARG, "null argument");
+  return guarded(ctx, [&]() {
+    auto* s = new tk_space();
+    s->s = v->s.flipped();
+    *out = s;
+    return TK_OK;
+  });
+}
+
+void tk_space_destroy(tk_space* v) { delete v; }
+int64_t tk_space_dim(const tk_space* v) { return v ? v->s.dim() : -1; }
+int64_t tk_space_reduced_dim(const tk_space* v) { return v ? v->s.reduced_dim() : -1; }
+
+int tk_tmap_create(tk_ctx* ctx, int n_cod, const tk_space* const* cod, int n_dom,
+                   const tk_space* const* dom, tk_tmap** out) {
+  if (!out) return fail(ctx, TK_ERR_ARG, "null out");
+  *out = nullptr;
+  if (n_cod < 0 || n_dom < 0 || n_cod + n_dom < 1 || n_cod + n_dom > 8)
+    return fail(ctx, TK_ERR_ARG, "a tensor map has 1 to 8 legs");
+  if ((n_cod && !cod) || (n_dom && !dom)) return fail(ctx, TK_ERR_ARG, "null space array");
+  return guarded(ctx, [&]() {
+    std::vector<tk::Space> c, d;
+    int sym = -1;
+    for (int i = 0; i < n_cod; ++i) {
+      if (!cod[i]) return fail(ctx, TK_ERR_ARG, "null space");
+      c.push_back(cod[i]->s);
+    }
+    for (int i = 0; i < n_dom; ++i) {
+      if (!dom[i]) return fail(ctx, TK_ERR_ARG, "null space");
+      d.push_back(dom[i]->s);
+    }
+    for (auto& s : c) sym = sym < 0 ? s.sym : sym;
+    for (auto& s : d) sym = sym < 0 ? s.sym : sym;
+    for (auto& s : c)
+      if (s.sym != sym) return fail(ctx, TK_ERR_ARG, "mixed symmetries");
+    for (auto& s : d)
+      if (s.sym != sym) return fail(ctx, TK_ERR_ARG, "mixed symmetries");
+    auto* t = new tk_tmap();
+    t->st = tk::build_structure(sym, c, d);
+    *out = t;
+    return TK_OK;
+  });
+}
+
+void tk_tmap_destroy(tk_tmap* t) { delete t; }
+int64_t tk_tmap_numel(const tk_tmap* t) { return t ? t->st->numel : -1; }
+uint64_t tk_tmap_hash(const tk_tmap* t) { return t ? t->st->hash : 0; }
+
+int tk_tmap_nlegs(const tk_tmap* t, int* n_cod, int* n_dom) {
+  if (!t) return TK_ERR_ARG;
+  if (n_cod) *n_cod = (int)t->st->cod.size();
+  if (n_dom) *n_dom = (int)t->st->dom.size();
+  return TK_OK;
+}
+
+int tk_tmap_leg(tk_ctx* ctx, const tk_tmap* t, int leg, tk_space** out) {
+  if (!t || !out) return fail(ctx, TK_ERR_ARG, "null argument");
+  int n1 = (int)t->st->cod.size();
+  if (leg < 0 || leg >= t->st->nleg()) return fail(ctx, TK_ERR_ARG, "leg out of range");
+  auto* s = new (std::nothrow) tk_space();
+  if (!s) return TK_ERR_OOM;
+  s->s = leg < n1 ? t->st->cod[leg] : t->st->dom[leg - n1];
+  *out = s;
+  return TK_OK;
+}
+
+int tk_tmap_nblocks(const tk_tmap* t) { return t ? (int)t->st->blocks.size() : -1; }
+
+int tk_tmap_block(const tk_tmap* t, int i, int32_t* sector, int64_t* rows, int64_t* cols, int64_t* offset) {
+  if (!t || i < 0 || i >= (int)t->st->blocks.size()) return TK_ERR_ARG;
+  const tk::Block& b = t->st->blocks[i];
+  if (sector) *sector = b.c;
+  if (rows) *rows = b.rows;
+  if (cols) *cols = b.cols;
+  if (offset) *offset = b.offset;
+  return TK_OK;
+}
+
+int64_t tk_tmap_ntreepairs(const tk_tmap* t) { return t ? (int64_t)t->st->pairs.size() : -1; }
+
+int tk_tmap_treepair(const tk_tmap* t, int64_t i, int32_t* labels, int64_t* offset, int64_t* ld,
+                     int64_t* dims) {
+  if (!t || i < 0 || i >= (int64_t)t->st->pairs.size()) return TK_ERR_ARG;
+  const tk::Structure& st = *t->st;
+  const tk::TreePair& p = st.pairs[i];
+  const tk::Block& b = st.blocks[p.block];
+  const tk::Tree& s = st.split_trees[b.split[p.s]];
+  const tk::Tree& f = st.fuse_trees[b.fuse[p.f]];
+  if (labels) {
+    int k = 0;
+    for (auto x : s.unc) labels[k++] = x;
+    for (auto x : f.unc) labels[k++] = x;
+    for (auto x : s.inner) labels[k++] = x;
+    labels[k++] = b.c;
+    for (auto x : f.inner) labels[k++] = x;
+  }
+  if (offset) *offset = p.offset;
+  if (ld) *ld = b.rows;
+  if (dims) {
+    std::vector<int64_t> d;
+    st.pair_dims(p, d);
+    for (size_t k = 0; k < d.size(); ++k) dims[k] = d[k];
+  }
+  return TK_OK;
+}
+
+int tk_permute_plan(tk_ctx* ctx, const tk_tmap* a, int np, const int* p, int nq, const int* q,
+                    int dtype, tk_plan** out) {
+  if (!ctx || !a || !out) return fail(ctx, TK_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (dtype != TK_F64 && dtype != TK_C128) return fail(ctx, TK_ERR_ARG, "unknown dtype");
+  std::vector<int> vp, vq;
+  if (!read_perm(np, p, nq, q, vp, vq) || np + nq != a->st->nleg())
+    return fail(ctx, TK_ERR_PERM, "(p, q) must list every leg once");
+  return guarded(ctx, [&]() {
+    if (ctx->c.device >= 0 && cudaSetDevice(ctx->c.device) != cudaSuccess)
+      return fail(ctx, TK_ERR_CUDA, "cudaSetDevice failed");
+    auto pl = new tk_plan();
+    pl->kind = 0;
+    try {
+      pl->perm = tk::make_permute_plan(&ctx->c, a->st, vp, vq, dtype);
+    } catch (...) {
+      delete pl;
+      throw;
+    }
+    *out = pl;
+    return TK_OK;
+  });
+}
+
+int tk_contract_plan(tk_ctx* ctx, const tk_tmap* a, int npa, const int* pa, int nqa, const int* qa,
+                     const tk_tmap* b, int npb, const int* pb, int nqb, const int* qb, int npab,
+                     const int* pab, int nqab, const int* qab, int dtype, int gemm_mode, int slices,
+                     tk_plan** out) {
+  if (!ctx || !a || !b || !out) return fail(ctx, TK_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (dtype != TK_F64 && dtype != TK_C128) return fail(ctx, TK_ERR_ARG, "unknown dtype");
+  if (gemm_mode < TK_GEMM_FP64 || gemm_mode > TK_GEMM_TF32X3) return fail(ctx, TK_ERR_ARG, "unknown gemm mode");
+  if (gemm_mode != TK_GEMM_FP64 && dtype != TK_F64)
+    return fail(ctx, TK_ERR_UNSUPPORTED, "split-precision GEMMs take real FP64 tensors");
+  if (slices < 0 || slices > 8) return fail(ctx, TK_ERR_ARG, "slices must be in [0, 8]");
+  std::vector<int> vpa, vqa, vpb, vqb, vpab, vqab;
+  if (!read_perm(npa, pa, nqa, qa, vpa, vqa) || npa + nqa != a->st->nleg() ||
+      !read_perm(npb, pb, nqb, qb, vpb, vqb) || npb + nqb != b->st->nleg() ||
+      !read_perm(npab, pab, nqab, qab, vpab, vqab))
+    return fail(ctx, TK_ERR_PERM, "permutation tuples must list every leg once");
+  if (npab + nqab != npa + nqb) return fail(ctx, TK_ERR_PERM, "(pab, qab) must list the legs of A~ o B~");
+  return guarded(ctx, [&]() {
+    if (ctx->c.device >= 0 && cudaSetDevice(ctx->c.device) != cudaSuccess)
+      return fail(ctx, TK_ERR_CUDA, "cudaSetDevice failed");
+    auto pl = new tk_plan();
+    pl->kind = 1;
+    try {
+      pl->con = tk::make_contract_plan(&ctx->c, a->st, vpa, vqa, b->st, vpb, vqb, vpab, vqab, dtype,
+                                       gemm_mode, slices);
+    } catch (...) {
+      delete pl;
+      throw;
+    }
+    *out = pl;
+    return TK_OK;
+  });
+}
+
+void tk_plan_destroy(tk_plan* plan) { delete plan; }
+
+int tk_plan_output(tk_ctx* ctx, const tk_plan* plan, tk_tmap** out) {
+  if (!plan || !out) return fail(ctx, TK_ERR_ARG, "null argument");
+  auto* t = new (std::nothrow) tk_tmap();
+  if (!t) return TK_ERR_OOM;
+  t->st = plan->kind == 0 ? plan->perm->out : plan->con->c;
+  *out = t;
+  return TK_OK;
+}
+
+size_t tk_plan_workspace_bytes(const tk_plan* plan) {
+  if (!plan || plan->kind != 1) return 0;
+  return plan->con->ws_total;
+}
+
+double tk_plan_flops(const tk_plan* plan) {
+  if (!plan || plan->kind != 1) return 0.0;
+  return plan->con->flops;
+}
+
+double tk_plan_permute_bytes(const tk_plan* plan) {
+  if (!plan) return 0.0;
+  if (plan->kind == 0) return plan->perm->identity ? 0.0 : plan->perm->bytes;
+  double b = 0;
+  const auto& c = *plan->con;
+  if (!c.pa->identity) b += c.pa->bytes;
+  if (!c.pb->identity) b += c.pb->bytes;
+  if (c.pc) b += c.pc->bytes;
+  return b;
+}
+
+static const tk::PermutePlan* which_perm(const tk_plan* plan, int which) {
+  if (!plan) return nullptr;
+  if (plan->kind == 0) return which == 0 ? plan->perm.get() : nullptr;
+  const auto& c = *plan->con;
+  const tk::PermutePlan* p = which == 0 ? c.pa.get() : which == 1 ? c.pb.get() : which == 2 ? c.pc.get() : nullptr;
+  if (p && p->identity) return nullptr;
+  return p;
+}
+
+int64_t tk_plan_ntransform(const tk_plan* plan, int which) {
+  const tk::PermutePlan* p = which_perm(plan, which);
+  return p ? (int64_t)p->terms.size() : -1;
+}
+
+int tk_plan_transform(const tk_plan* plan, int which, int64_t k, int64_t* src_offset,
+                      int64_t* dst_offset, double* coef) {
+  const tk::PermutePlan* p = which_perm(plan, which);
+  if (!p || k < 0 || k >= (int64_t)p->terms.size()) return TK_ERR_ARG;
+  const tk::TransformTerm& t = p->terms[k];
+  if (src_offset) *src_offset = p->in->pairs[t.src_pair].offset;
+  if (dst_offset) *dst_offset = p->out->pairs[t.dst_pair].offset;
+  if (coef) *coef = t.coef;
+  return TK_OK;
+}
+
+int tk_permute(tk_ctx* ctx, const tk_plan* plan, const void* a, void* c, void* stream) {
+  if (!ctx || !plan || plan->kind != 0) return fail(ctx, TK_ERR_ARG, "not a permute plan");
+  if (!a || !c) return fail(ctx, TK_ERR_ARG, "null buffer");
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  const tk::PermutePlan& pp = *plan->perm;
+  if (pp.identity) {
+    size_t bytes = (size_t)pp.in->numel * (pp.dtype == TK_C128 ? 16 : 8);
+    if (a == c) return TK_OK;
+    if (cudaMemcpyAsync(c, a, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess)
+      return fail(ctx, TK_ERR_CUDA, "device copy failed");
+    return TK_OK;
+  }
+  return tk::launch_permute(&ctx->c, pp, a, c, stream);
+}
+
+int tk_contract(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, void* c,
+                void* workspace, size_t workspace_bytes, void* stream) {
+  if (!ctx || !plan || plan->kind != 1) return fail(ctx, TK_ERR_ARG, "not a contraction plan");
+  if (!a || !b || !c) return fail(ctx, TK_ERR_ARG, "null buffer");
+  const tk::ContractPlan& cp = *plan->con;
+  if (workspace_bytes < cp.ws_total || (cp.ws_total > 0 && !workspace))
+    return fail(ctx, TK_ERR_WORKSPACE, "workspace smaller than tk_plan_workspace_bytes()");
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  char* ws = (char*)workspace;
+  const void* at = cp.pa->identity ? a : (const void*)(ws + cp.ws_at);
+  const void* bt = cp.pb->identity ? b : (const void*)(ws + cp.ws_bt);
+  void* ct = cp.pc ? (void*)(ws + cp.ws_ct) : c;
+  if (!cp.pa->identity && (rc = tk::launch_permute(&ctx->c, *cp.pa, a, (void*)at, stream)) != TK_OK) return rc;
+  if (!cp.pb->identity && (rc = tk::launch_permute(&ctx->c, *cp.pb, b, (void*)bt, stream)) != TK_OK) return rc;
+  if ((rc = tk::launch_zero(&ctx->c, cp, ct, stream)) != TK_OK) return rc;
+  if (cp.gemm_mode == TK_GEMM_FP64)
+    rc = tk::launch_gemm_fp64(&ctx->c, cp, at, bt, ct, stream);
+  else
+    rc = tk::launch_gemm_ozaki(&ctx->c, cp, at, bt, ct, ws + cp.ws_slices, stream);
+  if (rc != TK_OK) return rc;
+  if (cp.pc && (rc = tk::launch_permute(&ctx->c, *cp.pc, ct, c, stream)) != TK_OK) return rc;
+  return TK_OK;
+}
+
+int tk_copy_h2d(tk_ctx* ctx, void* dst_device, const void* src_host, size_t bytes, void* stream) {
+  if (!ctx || (bytes && (!dst_device || !src_host))) return fail(ctx, TK_ERR_ARG, "null argument");
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  if (cudaMemcpyAsync(dst_device, src_host, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream) != cudaSuccess)
+    return fail(ctx, TK_ERR_CUDA, "host to device copy failed");
+  return TK_OK;
+}
+
+int tk_copy_d2h(tk_ctx* ctx, void* dst_host, const void* src_device, size_t bytes, void* stream) {
+  if (!ctx || (bytes && (!dst_host || !src_device))) return fail(ctx, TK_ERR_ARG, "null argument");
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  if (cudaMemcpyAsync(dst_host, src_device, bytes, cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
+    return fail(ctx, TK_ERR_CUDA, "device to host copy failed");
+  return TK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,352 @@
+// Device kernels of the contraction path (sm_103a):
+//   K1 k_permute   -- fusion-tree permute: every destination reduced array is a
+//                     coefficient-weighted sum of strided transposes of source reduced arrays
+//                     (Algorithm 10; Algorithm 6 for abelian symmetries, one source, weight 1).
+//   K2 k_gemm_f64  -- grouped FP64 GEMM over the coupled sectors (Algorithm 8, step 2).
+//   k_zero         -- zero blocks of coupled sectors whose inner dimension is empty.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "tk_internal.hpp"
+
+namespace tk {
+
+// ------------------------------------------------------------------ helpers
+int dev_upload(Ctx* ctx, void** dst, const void* src, size_t bytes) {
+  if (bytes == 0) {
+    *dst = nullptr;
+    return TK_OK;
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return TK_ERR_CUDA;
+  if (cudaMalloc(dst, bytes) != cudaSuccess) return TK_ERR_OOM;
+  if (cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return TK_ERR_CUDA;
+  return TK_OK;
+}
+
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+PermutePlan::~PermutePlan() {
+  dev_free(d_tasks);
+  dev_free(d_srcs);
+  dev_free(d_tile_starts);
+}
+
+ContractPlan::~ContractPlan() {
+  dev_free(d_gemm_items);
+  dev_free(d_gemm_tiles);
+  dev_free(d_zero);
+  for (void* p : d_oz) dev_free(p);
+}
+
+namespace {
+
+template <typename T>
+struct Elem;
+template <>
+struct Elem<double> {
+  __device__ static double zero() { return 0.0; }
+  __device__ static void fma(double& acc, double c, double v) { acc = fma_(c, v, acc); }
+  __device__ static double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+  __device__ static double scale(double c, double v) { return c * v; }
+};
+template <>
+struct Elem<double2> {
+  __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+  __device__ static void fma(double2& acc, double c, double2 v) {
+    acc.x = __fma_rn(c, v.x, acc.x);
+    acc.y = __fma_rn(c, v.y, acc.y);
+  }
+  __device__ static double2 scale(double c, double2 v) { return make_double2(c * v.x, c * v.y); }
+};
+
+// Weighted sum over the sources of one destination element.  The common abelian case (one
+// source, weight exactly 1) is a plain copy with no floating-point operation.
+template <typename T>
+__device__ __forceinline__ T gather(const PermSrc* __restrict__ srcs, int nsrc, int src_begin,
+                                    const T* __restrict__ in, int64_t ir, int64_t ic) {
+  const PermSrc s0 = srcs[src_begin];
+  T v = __ldg(in + s0.in_off + ir + ic * s0.ld);
+  if (nsrc == 1 && s0.coef == 1.0) return v;
+  T acc = Elem<T>::scale(s0.coef, v);
+  for (int s = 1; s < nsrc; ++s) {
+    const PermSrc si = srcs[src_begin + s];
+    Elem<T>::fma(acc, si.coef, __ldg(in + si.in_off + ir + ic * si.ld));
+  }
+  return acc;
+}
+
+constexpr int kTaskWords = (int)(sizeof(PermTask) / sizeof(int64_t));
+static_assert(sizeof(PermTask) % sizeof(int64_t) == 0, "PermTask must be 8-byte multiple");
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ tasks, int ntasks,
+                                                 const int64_t* __restrict__ tile_starts,
+                                                 const PermSrc* __restrict__ srcs,
+                                                 int64_t total_tiles, const T* __restrict__ in,
+                                                 T* __restrict__ out) {
+  __shared__ T tile[32][33];
+  __shared__ int64_t task_words[kTaskWords];
+  const PermTask& t = *reinterpret_cast<const PermTask*>(task_words);
+  const int tid = threadIdx.x;
+  for (int64_t tidx = blockIdx.x; tidx < total_tiles; tidx += gridDim.x) {
+    // locate the task owning this tile
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (__ldg(tile_starts + mid) <= tidx)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    __syncthreads();  // previous iteration finished with task_words / tile
+    if (tid < kTaskWords) task_words[tid] = reinterpret_cast<const int64_t*>(tasks + lo)[tid];
+    __syncthreads();
+    const int64_t local = tidx - t.tile_begin;
+    const int nd = t.ndim;
+    if (t.mode == 0) {
+      const int e0 = t.ext[0], T0 = t.t0, T1 = t.t1;
+      const int64_t nb0 = (e0 + T0 - 1) / T0;
+      const int64_t b0 = local % nb0, bo = local / nb0;
+      const int64_t i0 = b0 * T0 + (tid % T0);
+      int64_t o = bo * T1 + (tid / T0);
+      int64_t outer_total = 1;
+      for (int k = 1; k < nd; ++k) outer_total *= t.ext[k];
+      if (i0 < e0 && o < outer_total) {
+        int64_t oa = t.out_off + i0, ir = i0, ic = 0;
+        for (int k = 1; k < nd; ++k) {
+          const int64_t x = o % t.ext[k];
+          o /= t.ext[k];
+          oa += x * t.ostr[k];
+          ir += x * t.irs[k];
+          ic += x * t.ics[k];
+        }
+        out[oa] = gather<T>(srcs, t.nsrc, t.src_begin, in, ir, ic);
+      }
+    } else if (t.mode == 1) {
+      const int td = t.tdim;
+      const int e0 = t.ext[0], et = t.ext[td];
+      const int64_t nb0 = (e0 + 31) / 32, nbt = (et + 31) / 32;
+      const int64_t b0 = local % nb0;
+      int64_t rest = local / nb0;
+      const int64_t bt = rest % nbt;
+      int64_t o = rest / nbt;
+      int64_t ob = t.out_off, irb = 0, icb = 0;
+      for (int k = 1; k < nd; ++k) {
+        if (k == td) continue;
+        const int64_t x = o % t.ext[k];
+        o /= t.ext[k];
+        ob += x * t.ostr[k];
+        irb += x * t.irs[k];
+        icb += x * t.ics[k];
+      }
+      const int lx = tid & 31, ly = tid >> 5;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int j0 = ly + 8 * r;
+        const int64_t i0 = b0 * 32 + j0, it = bt * 32 + lx;
+        if (i0 < e0 && it < et) {
+          const int64_t ir = irb + i0 * t.irs[0] + it * t.irs[td];
+          const int64_t ic = icb + i0 * t.ics[0] + it * t.ics[td];
+          tile[j0][lx] = gather<T>(srcs, t.nsrc, t.src_begin, in, ir, ic);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int jt = ly + 8 * r;
+        const int64_t i0 = b0 * 32 + lx, it = bt * 32 + jt;
+        if (i0 < e0 && it < et) out[ob + i0 + it * t.ostr[td]] = tile[lx][jt];
+      }
+    } else {
+      int64_t total = 1;
+      for (int k = 0; k < nd; ++k) total *= t.ext[k];
+      int64_t e = local * 256 + tid;
+      if (e < total) {
+        int64_t oa = t.out_off, ir = 0, ic = 0;
+        for (int k = 0; k < nd; ++k) {
+          const int64_t x = e % t.ext[k];
+          e /= t.ext[k];
+          oa += x * t.ostr[k];
+          ir += x * t.irs[k];
+          ic += x * t.ics[k];
+        }
+        out[oa] = gather<T>(srcs, t.nsrc, t.src_begin, in, ir, ic);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ K2 grouped FP64 GEMM
+struct GemmTile {
+  int32_t item, m0, n0, pad;
+};
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+template <typename T>
+struct Mac;
+template <>
+struct Mac<double> {
+  __device__ static void mac(double& acc, double a, double b) { acc = __fma_rn(a, b, acc); }
+};
+template <>
+struct Mac<double2> {
+  __device__ static void mac(double2& acc, double2 a, double2 b) {
+    acc.x = __fma_rn(a.x, b.x, acc.x);
+    acc.x = __fma_rn(-a.y, b.y, acc.x);
+    acc.y = __fma_rn(a.x, b.y, acc.y);
+    acc.y = __fma_rn(a.y, b.x, acc.y);
+  }
+};
+
+// One 64x64 output tile per CTA; tiles of all sectors sorted by K descending (longest first),
+// so the hardware CTA scheduler hands the big tiles out first.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_f64(const GemmItem* __restrict__ items,
+                                                  const GemmTile* __restrict__ tiles,
+                                                  const T* __restrict__ A,
+                                                  const T* __restrict__ B, T* __restrict__ C) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmItem it = items[tl.item];
+  const int64_t M = it.M, N = it.N, K = it.K;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = Elem<T>::zero();
+  const T* Ab = A + it.a_off;
+  const T* Bb = B + it.b_off;
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int e = tid + 256 * r;
+      const int mm = e & 63, kk = e >> 6;
+      const int64_t gm = tl.m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < K) ? Ab[gm + gk * M] : Elem<T>::zero();
+      const int kb = e & 15, nn = e >> 4;
+      const int64_t gk2 = k0 + kb, gn = tl.n0 + nn;
+      Bs[kb][nn] = (gk2 < K && gn < N) ? Bb[gk2 + gn * K] : Elem<T>::zero();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Mac<T>::mac(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+  T* Cb = C + it.c_off;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int64_t gn = tl.n0 + ty + 16 * j;
+    if (gn >= N) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t gm = tl.m0 + tx + 16 * i;
+      if (gm < M) Cb[gm + gn * M] = acc[i][j];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_zero(const ZeroItem* __restrict__ items, int nitems, T* __restrict__ c) {
+  for (int i = blockIdx.y; i < nitems; i += gridDim.y) {
+    const ZeroItem z = items[i];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < z.n;
+         e += (int64_t)gridDim.x * blockDim.x)
+      c[z.off + e] = Elem<T>::zero();
+  }
+}
+
+int check_launch(Ctx* ctx, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ctx->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return TK_ERR_CUDA;
+  }
+  ctx->launches += 1;
+  return TK_OK;
+}
+
+}  // namespace
+
+int launch_permute(Ctx* ctx, const PermutePlan& pp, const void* in, void* out, void* stream) {
+  if (pp.tasks.empty()) return TK_OK;
+  const int ntasks = (int)pp.tasks.size();
+  int64_t grid = std::min<int64_t>(pp.total_tiles, (int64_t)ctx->num_sms * 8);
+  if (grid < 1) grid = 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (pp.dtype == TK_C128)
+    k_permute<double2><<<(unsigned)grid, 256, 0, s>>>(pp.d_tasks, ntasks, pp.d_tile_starts, pp.d_srcs,
+                                                      pp.total_tiles, (const double2*)in, (double2*)out);
+  else
+    k_permute<double><<<(unsigned)grid, 256, 0, s>>>(pp.d_tasks, ntasks, pp.d_tile_starts, pp.d_srcs,
+                                                     pp.total_tiles, (const double*)in, (double*)out);
+  return check_launch(ctx, "k_permute");
+}
+
+int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
+  std::vector<GemmTile> tiles;
+  std::vector<int> order(cp.gemms.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cp.gemms[a].K > cp.gemms[b].K; });
+  for (int i : order) {
+    const GemmItem& g = cp.gemms[i];
+    for (int64_t n0 = 0; n0 < g.N; n0 += BN)
+      for (int64_t m0 = 0; m0 < g.M; m0 += BM) tiles.push_back(GemmTile{i, (int32_t)m0, (int32_t)n0, 0});
+  }
+  cp.n_gemm_tiles = (int64_t)tiles.size();
+  int rc = dev_upload(ctx, &cp.d_gemm_items, cp.gemms.data(), cp.gemms.size() * sizeof(GemmItem));
+  if (rc != TK_OK) return rc;
+  rc = dev_upload(ctx, &cp.d_gemm_tiles, tiles.data(), tiles.size() * sizeof(GemmTile));
+  if (rc != TK_OK) return rc;
+  if (!cp.zeros.empty()) {
+    rc = dev_upload(ctx, &cp.d_zero, cp.zeros.data(), cp.zeros.size() * sizeof(ZeroItem));
+    if (rc != TK_OK) return rc;
+  }
+  return TK_OK;
+}
+
+int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
+                     void* stream) {
+  if (cp.n_gemm_tiles == 0) return TK_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const GemmItem* items = (const GemmItem*)cp.d_gemm_items;
+  const GemmTile* tiles = (const GemmTile*)cp.d_gemm_tiles;
+  if (cp.dtype == TK_C128)
+    k_gemm_f64<double2><<<(unsigned)cp.n_gemm_tiles, 256, 0, s>>>(items, tiles, (const double2*)a,
+                                                                  (const double2*)b, (double2*)c);
+  else
+    k_gemm_f64<double><<<(unsigned)cp.n_gemm_tiles, 256, 0, s>>>(items, tiles, (const double*)a,
+                                                                 (const double*)b, (double*)c);
+  return check_launch(ctx, "k_gemm_f64");
+}
+
+int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream) {
+  if (cp.zeros.empty()) return TK_OK;
+  int64_t maxn = 0;
+  for (auto& z : cp.zeros) maxn = std::max(maxn, z.n);
+  dim3 grid((unsigned)std::min<int64_t>((maxn + 255) / 256, 1024), (unsigned)std::min<size_t>(cp.zeros.size(), 65535));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cp.dtype == TK_C128)
+    k_zero<double2><<<grid, 256, 0, s>>>((const ZeroItem*)cp.d_zero, (int)cp.zeros.size(), (double2*)c);
+  else
+    k_zero<double><<<grid, 256, 0, s>>>((const ZeroItem*)cp.d_zero, (int)cp.zeros.size(), (double*)c);
+  return check_launch(ctx, "k_zero");
+}
+
+}  // namespace tk

@@ -1,0 +1,214 @@
+// Internal declarations of libtk (host plan layer + kernel launch wrappers).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/tk.h"
+
+namespace tk {
+
+// ------------------------------------------------------------------ symmetry (symbols.cpp)
+// Sector algebra of Z2, U(1), SU(2) (Sec. 3.1, Sec. 5.4) and the elementary moves used to
+// recouple fusion trees (Sec. 4.2).  All labels use the ABI encoding (SU(2): 2j).
+bool sector_valid(int sym, int32_t a);
+int32_t sector_dual(int sym, int32_t a);
+int32_t sector_dim(int sym, int32_t a);
+void sector_fuse(int sym, int32_t a, int32_t b, std::vector<int32_t>& out);  // ascending
+bool sector_nsym(int sym, int32_t a, int32_t b, int32_t c);
+double fsymbol(int sym, int32_t a, int32_t b, int32_t c, int32_t d, int32_t e, int32_t f);
+double rsymbol(int sym, int32_t a, int32_t b, int32_t c);
+double fs_indicator(int sym, int32_t a);  // chi_a
+// Coefficient of bending the last leg (label x, space dual flag `was_dual`) off a tree whose
+// running label before that leg is u and whose coupled sector is c, onto the last position of
+// the opposite tree (new coupled sector u).
+double bend_coef(int sym, int32_t x, bool was_dual, int32_t u, int32_t c);
+
+// ------------------------------------------------------------------ structures (structure.cpp)
+struct Space {
+  int sym = 0;
+  std::vector<int32_t> sectors;  // ascending
+  std::vector<int64_t> mults;
+  bool dual = false;
+  std::vector<int32_t> labels;   // tree labels, ascending
+  int64_t mult_of_label(int32_t lab) const;
+  int64_t dim() const;
+  int64_t reduced_dim() const;
+  bool same(const Space& o) const {
+    return sym == o.sym && dual == o.dual && sectors == o.sectors && mults == o.mults;
+  }
+  Space flipped() const;
+  void finalize();
+};
+
+struct Tree {
+  std::vector<int32_t> unc;
+  std::vector<int32_t> inner;  // running couplings u_2 .. u_{N-1}
+  int32_t coupled = 0;
+  int64_t size = 1;            // product of leg multiplicities
+};
+
+struct Block {
+  int32_t c = 0;
+  int64_t rows = 0, cols = 0, offset = 0;
+  std::vector<int> split, fuse;        // tree ids
+  std::vector<int64_t> roff, coff;     // row / column offsets of those trees
+};
+
+struct TreePair {
+  int block;
+  int s, f;                // indices into the block's split / fuse lists
+  int64_t offset;          // element offset of the first entry
+};
+
+struct Structure {
+  int sym = 0;
+  std::vector<Space> cod, dom;
+  std::vector<Tree> split_trees, fuse_trees;
+  std::vector<Block> blocks;
+  std::vector<TreePair> pairs;
+  std::map<std::vector<int32_t>, std::pair<int, int>> split_pos, fuse_pos;  // key -> (block, idx)
+  int64_t numel = 0;
+  uint64_t hash = 0;
+  int nleg() const { return (int)(cod.size() + dom.size()); }
+  int block_of(int32_t c) const;
+  // dims of the reduced array of pair p (codomain legs then domain legs)
+  void pair_dims(const TreePair& p, std::vector<int64_t>& dims) const;
+};
+
+std::vector<int32_t> tree_key(const std::vector<int32_t>& unc, const std::vector<int32_t>& inner,
+                              int32_t c);
+std::shared_ptr<Structure> build_structure(int sym, const std::vector<Space>& cod,
+                                           const std::vector<Space>& dom);
+
+// ------------------------------------------------------------------ plans (plan.cpp)
+// One term of Algorithm 10: dst += coef * permute(src).
+struct TransformTerm {
+  int64_t src_pair, dst_pair;
+  double coef;
+};
+
+// Device task of the permute kernel (K1): one destination tree pair.
+struct PermTask {
+  int64_t out_off;       // element offset of the destination reduced array
+  int64_t ostr[6];       // destination strides of the merged dims
+  int32_t ext[6];        // merged extents
+  int32_t irs[6];        // source stride = irs + ics * ld_src
+  int32_t ics[6];
+  int32_t ndim;
+  int32_t mode;          // 0: shared contiguous dim 0; 1: transpose dims (0, tdim); 2: generic
+  int32_t tdim;          // mode 1: the dim that is contiguous in the source
+  int32_t src_begin, nsrc;
+  int32_t t0, t1;        // tile extents along dim 0 and along the tiled second axis
+  int32_t pad_;
+  int64_t tile_begin;    // first global tile index of this task
+};
+struct PermSrc {
+  int64_t in_off;
+  int64_t ld;
+  double coef;
+};
+
+struct PermutePlan {
+  std::shared_ptr<Structure> in, out;
+  std::vector<int> perm;      // output leg k <- input leg perm[k]
+  bool identity = false;
+  std::vector<TransformTerm> terms;   // sorted by destination
+  std::vector<PermTask> tasks;
+  std::vector<PermSrc> srcs;
+  int64_t total_tiles = 0;
+  double bytes = 0;           // algorithmic bytes for one launch (complex counts 16 B/element)
+  int dtype = TK_F64;
+  // device copies
+  PermTask* d_tasks = nullptr;
+  PermSrc* d_srcs = nullptr;
+  int64_t* d_tile_starts = nullptr;
+  ~PermutePlan();
+};
+
+struct GemmItem {          // one sector GEMM: C~^c (M x N) = A~^c (M x K) * B~^c (K x N)
+  int32_t c;
+  int64_t M, N, K;
+  int64_t a_off, b_off, c_off;
+};
+
+struct ZeroItem {
+  int64_t off, n;
+};
+
+struct ContractPlan {
+  std::shared_ptr<PermutePlan> pa, pb, pc;  // pc permutes C~ -> C (null if identity)
+  std::shared_ptr<Structure> at, bt, ct, c;
+  std::vector<GemmItem> gemms;
+  std::vector<ZeroItem> zeros;
+  int gemm_mode = TK_GEMM_FP64;
+  int slices = 0;
+  int dtype = TK_F64;
+  double flops = 0;
+  // workspace layout (bytes)
+  size_t ws_at = 0, ws_bt = 0, ws_ct = 0, ws_slices = 0, ws_total = 0;
+  // device tables
+  void* d_gemm_items = nullptr;
+  void* d_gemm_tiles = nullptr;
+  int64_t n_gemm_tiles = 0;
+  void* d_zero = nullptr;
+  // split-precision tables (owned; freed by the destructor)
+  std::vector<void*> d_oz;
+  int64_t oz_nwork = 0;
+  size_t oz_bytes = 0;
+  ~ContractPlan();
+};
+
+struct Ctx;
+std::shared_ptr<PermutePlan> make_permute_plan(Ctx* ctx, std::shared_ptr<Structure> in,
+                                               const std::vector<int>& p,
+                                               const std::vector<int>& q, int dtype);
+std::shared_ptr<ContractPlan> make_contract_plan(Ctx* ctx, std::shared_ptr<Structure> a,
+                                                 const std::vector<int>& pa,
+                                                 const std::vector<int>& qa,
+                                                 std::shared_ptr<Structure> b,
+                                                 const std::vector<int>& pb,
+                                                 const std::vector<int>& qb,
+                                                 const std::vector<int>& pab,
+                                                 const std::vector<int>& qab, int dtype,
+                                                 int gemm_mode, int slices);
+// output spaces of permute(t, (p, q)) (Algorithm 2)
+void permute_spaces(const Structure& s, const std::vector<int>& p, const std::vector<int>& q,
+                    std::vector<Space>& cod, std::vector<Space>& dom);
+
+// ------------------------------------------------------------------ errors
+struct Error {
+  int code;
+  std::string msg;
+};
+
+struct Ctx {
+  int device = -1;
+  std::string last_error;
+  int64_t launches = 0;
+  int num_sms = 0;
+  std::mutex mu;
+  std::unordered_map<std::string, std::shared_ptr<PermutePlan>> perm_cache;
+  std::unordered_map<std::string, std::shared_ptr<ContractPlan>> contract_cache;
+  int* d_status = nullptr;  // device status word for bounded waits
+};
+
+// ------------------------------------------------------------------ device side (kernels)
+int dev_upload(Ctx* ctx, void** dst, const void* src, size_t bytes);
+void dev_free(void* p);
+int launch_permute(Ctx* ctx, const PermutePlan& pp, const void* in, void* out, void* stream);
+int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
+                     void* stream);
+int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream);
+int upload_gemm_tables(Ctx* ctx, ContractPlan& cp);
+int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
+                      void* slices_ws, void* stream);
+int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp);
+
+}  // namespace tk

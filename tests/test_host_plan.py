@@ -1,0 +1,163 @@
+"""Host logic of libtk against the oracle (no GPU): structures, exact symbols, permute transforms.
+
+The library side computes recoupling coefficients with F/B/R moves and Racah 6j symbols; the
+oracle projects permuted explicit CG trees.  The two share no code.
+"""
+
+import itertools
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import SU2, U1, Z2, GradedSpace, TensorStructure
+from oracle import ops, su2
+from paper_2508_10076_gb300 import api, build_library
+from paper_2508_10076_gb300._abi import SIGNATURES
+
+
+@pytest.fixture(scope="module")
+def hctx():
+    build_library()
+    return api.Context(-1)
+
+
+def test_library_exports_every_declared_symbol():
+    build_library()
+    import ctypes
+    from paper_2508_10076_gb300.build import LIB
+    lib = ctypes.CDLL(LIB)
+    with open(f"{ROOT}/include/tk.h") as fh:
+        header = fh.read()
+    declared = set(re.findall(r"\b(tk_[a-z0-9_]+)\s*\(", header))
+    assert declared == set(SIGNATURES), declared ^ set(SIGNATURES)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def _mk(ctx, sym, spec):
+    cod, dom = spec
+    o_cod = [GradedSpace(sym, s, d) for s, d in cod]
+    o_dom = [GradedSpace(sym, s, d) for s, d in dom]
+    l_cod = [ctx.space(sym.name, s, d) for s, d in cod]
+    l_dom = [ctx.space(sym.name, s, d) for s, d in dom]
+    return TensorStructure(o_cod, o_dom), ctx.tmap(l_cod, l_dom)
+
+
+def _same_structure(ost, lt):
+    assert lt.numel == ost.numel
+    assert lt.blocks() == [(c, r, k, off) for c, r, k, off in ost.blocks]
+    lib_pairs = lt.treepairs()
+    assert len(lib_pairs) == len(ost.pairs)
+    for (unc, si, c, fi, off, ld, dims), p in zip(lib_pairs, ost.pairs):
+        assert unc == p.split_unc + p.fuse_unc
+        assert si == p.split_inner and fi == p.fuse_inner and c == p.coupled
+        assert (off, ld, dims) == (p.offset, p.ld, p.dims)
+
+
+SPECS = [
+    (SU2, ([({0: 1, 1: 1}, False)] * 2, [({0: 1, 1: 1}, False)] * 2)),
+    (SU2, ([({0: 2, 1: 1, 2: 2}, False), ({1: 1}, False)], [({0: 1, 1: 2, 2: 1}, True), ({1: 1}, True)])),
+    (SU2, ([({1: 2, 3: 1}, True), ({0: 1, 2: 1}, False), ({1: 1}, False)], [({0: 1, 2: 2}, False)])),
+    (SU2, ([({0: 1, 2: 1}, True)], [({1: 1, 3: 1}, False), ({1: 2}, True), ({0: 1, 2: 1, 4: 1}, False)])),
+    (SU2, ([], [({1: 1, 3: 1}, False), ({1: 2, 2: 1}, True), ({0: 1, 1: 1}, False)])),
+    (U1, ([({-2: 1, -1: 2, 0: 3, 1: 2, 2: 1}, False)] * 2, [({-2: 1, -1: 2, 0: 3, 1: 2, 2: 1}, False)] * 2)),
+    (U1, ([({-1: 2, 1: 1}, True), ({0: 1, 2: 2}, False)], [({-1: 1, 1: 3, 3: 1}, False), ({1: 1, -1: 1}, True)])),
+    (Z2, ([({0: 2, 1: 1}, False), ({0: 1, 1: 2}, True), ({1: 1}, False)], [({0: 3, 1: 1}, False)])),
+]
+
+
+@pytest.mark.parametrize("k", range(len(SPECS)))
+def test_structure_bit_exact(hctx, k):
+    sym, spec = SPECS[k]
+    ost, lt = _mk(hctx, sym, spec)
+    _same_structure(ost, lt)
+
+
+def _oracle_transform_offsets(ost, p, q):
+    out, tr = ops.permute_transform(ost, p, q)
+    idx_in = ost.pair_index()
+    idx_out = out.pair_index()
+    res = {}
+    for src, lst in tr.items():
+        for dst, coef in lst:
+            res[(idx_in[src].offset, idx_out[dst].offset)] = coef
+    return out, res
+
+
+@pytest.mark.parametrize("k", range(len(SPECS)))
+def test_permute_transform_matches_oracle(hctx, k):
+    """F/B/R-move coefficients (library) == overlap-route coefficients (oracle), all (p, q) tried
+    for rank <= 3 and a random sample for rank 4."""
+    sym, spec = SPECS[k]
+    ost, lt = _mk(hctx, sym, spec)
+    n = ost.nleg
+    perms = list(itertools.permutations(range(n)))
+    rng = np.random.default_rng(k)
+    if len(perms) > 12:
+        perms = [perms[i] for i in rng.choice(len(perms), 12, replace=False)]
+    for perm in perms:
+        for split in range(n + 1):
+            p, q = tuple(perm[:split]), tuple(perm[split:])
+            out, ref = _oracle_transform_offsets(ost, p, q)
+            plan = api.permute_plan(hctx, lt, p, q)
+            _same_structure(out, plan.output())
+            got = plan.transform(0)
+            if got is None:  # identity permute
+                assert p == tuple(range(len(ost.cod))) and q == tuple(range(len(ost.cod), n))
+                continue
+            gd = {(s, d): c for s, d, c in got}
+            keys = set(gd) | set(ref)
+            for key in keys:
+                assert abs(gd.get(key, 0.0) - ref.get(key, 0.0)) < 1e-12, (p, q, key)
+
+
+def test_fsymbols_bit_exact(hctx):
+    """Library F-symbols (C++ big integers) == oracle F-symbols (Python fractions), bit for bit."""
+    n = 0
+    for ta, tb, tc, td in itertools.product(range(0, 7), repeat=4):
+        for te in range(abs(ta - tb), ta + tb + 1, 2):
+            for tf in range(abs(tb - tc), tb + tc + 1, 2):
+                ref = su2.fsymbol_exact(ta, tb, tc, td, te, tf)
+                got = api.fsymbol("SU2", ta, tb, tc, td, te, tf)
+                assert got == ref, (ta, tb, tc, td, te, tf, got, ref)
+                n += 1
+    assert n > 10000
+    for ta, tb in itertools.product(range(9), repeat=2):
+        for tc in range(abs(ta - tb), ta + tb + 1, 2):
+            assert api.rsymbol("SU2", ta, tb, tc) == su2.rsymbol_from_cg(ta, tb, tc) or \
+                abs(api.rsymbol("SU2", ta, tb, tc) - su2.rsymbol_from_cg(ta, tb, tc)) < 1e-14
+
+
+def test_contract_plan_structure_and_flops(hctx):
+    """C0: A~ has square per-charge GEMMs (1,4,10,16,19,16,10,4,1), 34,362 block flops."""
+    v = {-2: 1, -1: 2, 0: 3, 1: 2, 2: 1}
+    V, Vd = hctx.space("U1", v), hctx.space("U1", v, True)
+    A = hctx.tmap([V, V], [V, V])
+    B = hctx.tmap([V, Vd], [V, V])
+    plan = api.contract_plan(hctx, A, (0, 2), (3, 1), B, (0, 1), (2, 3), (0, 1), (2, 3))
+    assert plan.flops == 34362
+    assert plan.transform(1) is None  # B is used as is
+    out = plan.output()
+    oa = TensorStructure([GradedSpace(U1, v), GradedSpace(U1, v)], [GradedSpace(U1, v)] * 2)
+    ob = TensorStructure([GradedSpace(U1, v), GradedSpace(U1, v, True)], [GradedSpace(U1, v)] * 2)
+    xa, xb = np.zeros(oa.numel), np.zeros(ob.numel)
+    cs, _ = ops.contract(oa, xa, (0, 2), (3, 1), ob, xb, (0, 1), (2, 3), (0, 1), (2, 3), tier="block")
+    _same_structure(cs, out)
+
+
+def test_errors_are_reported(hctx):
+    V = hctx.space("SU2", {1: 1})
+    t = hctx.tmap([V], [V])
+    with pytest.raises(api.TKError) as e:
+        api.permute_plan(hctx, t, (0, 0), ())
+    assert e.value.code == 3
+    W = hctx.space("SU2", {0: 1})
+    t2 = hctx.tmap([W], [W])
+    with pytest.raises(api.TKError) as e:
+        api.contract_plan(hctx, t, (0,), (1,), t2, (0,), (1,), (0,), (1,))
+    assert e.value.code == 2
+    with pytest.raises(api.TKError) as e:
+        hctx.space("Z2", {2: 1})
+    assert e.value.code == 4
