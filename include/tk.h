@@ -91,6 +91,14 @@ const char* tk_ctx_last_error(const tk_ctx* ctx);
 int tk_ctx_sync(tk_ctx* ctx, void* stream);
 /* Number of the library's own kernels launched through this context so far. */
 int64_t tk_ctx_launch_count(const tk_ctx* ctx);
+/* Kernel profiling.  enable != 0: every later launch through ctx is bracketed by CUDA events
+ * recorded on its own stream; enable == 0 stops recording.  tk_ctx_profile_read waits for the
+ * recorded events and returns, per kernel name (at most max entries, names NUL-terminated in
+ * 32-byte slots of `names`), the number of launches and the summed event-measured time in
+ * milliseconds; *n_out receives the number of distinct kernels.  Reading clears the record. */
+int tk_ctx_profile(tk_ctx* ctx, int enable);
+int tk_ctx_profile_read(tk_ctx* ctx, int max, char* names, int64_t* counts, double* total_ms,
+                        int* n_out);
 
 /* ---- graded spaces (Sec. 3.1 eq. gradedbasis, Sec. 5.2) ----------------------------------
  * sectors[i], mults[i] for i < nsec: sector labels (unique) and positive multiplicities.

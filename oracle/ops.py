@@ -76,6 +76,11 @@ def contract_dense(a_struct, a_data, pa, qa, b_struct, b_data, pb, qb, pab, qab)
 
 
 # --------------------------------------------------------------------------- block tier
+# Magnitude below which an overlap is rounding residue of an exact zero.  Genuine recoupling
+# coefficients of the labels used here (j <= 10) are many orders of magnitude larger.
+OVERLAP_ZERO = 1e-12
+
+
 @lru_cache(maxsize=None)
 def _e_tensor(sym, su, si, c, fu, fi, cod_duals, dom_duals):
     ys = _tree_cached(sym.name, sym, su, si, c, cod_duals)
@@ -93,7 +98,9 @@ def _overlap_coeffs(sym, in_labels, in_duals, out_cands, out_duals, perm):
     for lab in out_cands:
         e_out = _e_tensor(sym, *lab, *out_duals)
         coef = float(np.sum(e_out * e_in)) / sym.dim(lab[2])
-        if coef != 0.0:
+        # Canonical tree pairs are orthonormal (eq. fusiontreeorthogonality): an overlap that is
+        # zero in exact arithmetic shows up only as rounding residue of the CG sums.
+        if abs(coef) > OVERLAP_ZERO:
             res.append((lab, coef))
     return tuple(res)
 
@@ -134,6 +141,8 @@ def permute_transform(struct: TensorStructure, p, q, out_struct=None):
 
 def permute_block(struct: TensorStructure, data, p, q):
     p, q = check_perm(struct.nleg, p, q)
+    if p + q == tuple(range(struct.nleg)) and len(p) == len(struct.cod):
+        return struct, np.array(data, copy=True)  # permute with the identity (p, q) is the identity
     out_struct, tr = permute_transform(struct, p, q)
     data = np.asarray(data)
     out = np.zeros(out_struct.numel, dtype=data.dtype)

@@ -80,6 +80,20 @@ class Context:
     def launches(self):
         return int(_lib().tk_ctx_launch_count(self._h))
 
+    def profile(self, enable=True):
+        _check(_lib().tk_ctx_profile(self._h, int(bool(enable))), self)
+
+    def profile_read(self, maxn=32):
+        """{kernel name: (launches, total ms)} of the launches recorded since profiling began."""
+        names = C.create_string_buffer(32 * maxn)
+        counts = (C.c_int64 * maxn)()
+        ms = (C.c_double * maxn)()
+        n = C.c_int()
+        _check(_lib().tk_ctx_profile_read(self._h, maxn, names, counts, ms, C.byref(n)), self)
+        raw = names.raw
+        return {raw[32 * i:32 * i + 32].split(b"\0")[0].decode(): (int(counts[i]), float(ms[i]))
+                for i in range(min(n.value, maxn))}
+
     # ---- objects
     def space(self, sym, sectors, dual=False):
         return Space(self, sym, sectors, dual)

@@ -1,0 +1,116 @@
+"""Workload drivers over libtk: the two-site effective-Hamiltonian chain x' = L.x.W.W.R
+(Algorithm 12 of the paper, repeated application), single L.x contractions and the small C0
+contraction.  Everything on the path is a libtk launch; this module allocates device memory
+with PyTorch, fills inputs from :mod:`.workloads` and sequences the ABI calls.
+"""
+
+import numpy as np
+import torch
+
+from . import api
+from . import workloads as wl
+
+
+def _tmap(ctx, sym, legs):
+    cod, dom = legs
+    return ctx.tmap([ctx.space(sym, s, d) for s, d in cod], [ctx.space(sym, s, d) for s, d in dom])
+
+
+def mpo_data(tm, entries, numel):
+    """Reduced data of the U(1) XXZ MPO in tm's layout (abelian: entries placed by label)."""
+    data = np.zeros(numel)
+    lookup = {}
+    for (wl_q, wl_k), sp, s, (wr_q, wr_k), v in entries:
+        lookup[(wl_q, sp, s, wr_q, wl_k, wr_k)] = v
+    for unc, si, c, fi, off, ld, dims in tm.treepairs():
+        wl_q, sp, s, wr_q = unc
+        for kl in range(dims[0]):
+            for kr in range(dims[3]):
+                v = lookup.get((wl_q, sp, s, wr_q, kl, kr))
+                if v is not None:
+                    data[off + kl + kr * ld] = v
+    return data
+
+
+class Contraction:
+    """One planned contraction with its device buffers (inputs, output, workspace)."""
+
+    def __init__(self, ctx, a, b, spec, dtype="f64", gemm="fp64", slices=0, device="cuda"):
+        pa, qa, pb, qb, pab, qab = spec
+        self.ctx, self.a, self.b = ctx, a, b
+        self.plan = api.contract_plan(ctx, a, pa, qa, b, pb, qb, pab, qab, dtype=dtype, gemm=gemm,
+                                      slices=slices)
+        self.out = self.plan.output()
+        tdt = torch.complex128 if dtype == "c128" else torch.float64
+        self.c = torch.empty(self.out.numel, dtype=tdt, device=device)
+        self.ws = torch.empty(max(1, self.plan.workspace_bytes), dtype=torch.uint8, device=device)
+
+    def run(self, a_buf, b_buf, stream=None):
+        api.contract(self.ctx, self.plan, a_buf, b_buf, self.c, self.ws, stream)
+        return self.c
+
+
+class HeffChain:
+    """x' = (((L x) W) W) R with all intermediates resident on the device."""
+
+    def __init__(self, ctx, sym="U1", D=1024, gemm="fp64", slices=0, seed=0, device="cuda",
+                 dtype="f64"):
+        self.ctx, self.sym, self.D = ctx, sym, D
+        V, P, W = wl.heff_spaces(sym, D)
+        self.sectors = (V, P, W)
+        legs = wl.heff_legs(V, P, W)
+        self.legs = legs
+        self.tm = {k: _tmap(ctx, sym, legs[k]) for k in ("x", "L", "W", "R")}
+        self.host = {}
+        rnd = wl.normal_complex if dtype == "c128" else wl.normal
+        for i, k in enumerate(("x", "L", "R")):
+            self.host[k] = rnd(seed * 16 + i, self.tm[k].numel)
+        if sym == "U1":
+            w = mpo_data(self.tm["W"], wl.xxz_mpo_entries(), self.tm["W"].numel)
+            self.host["W"] = w.astype(np.complex128) if dtype == "c128" else w
+        else:
+            self.host["W"] = rnd(seed * 16 + 3, self.tm["W"].numel)
+        tdt = torch.complex128 if dtype == "c128" else torch.float64
+        self.dev = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device=device, dtype=tdt)
+                    for k, v in self.host.items()}
+        specs = wl.HEFF_SPECS
+        self.steps = []
+        cur = self.tm["x"]
+        for i, (other, first) in enumerate((("L", True), ("W", False), ("W", False), ("R", False))):
+            if first:  # T1 = L x : A = L, B = x
+                st = Contraction(ctx, self.tm["L"], cur, specs[0], dtype, gemm, slices, device)
+            else:
+                st = Contraction(ctx, cur, self.tm[other], specs[i], dtype, gemm, slices, device)
+            self.steps.append(st)
+            cur = st.out
+        self.flops = sum(s.plan.flops for s in self.steps)
+        self.permute_bytes = sum(s.plan.permute_bytes for s in self.steps)
+
+    def run(self, x=None, stream=None):
+        x = self.dev["x"] if x is None else x
+        t = self.steps[0].run(self.dev["L"], x, stream)
+        t = self.steps[1].run(t, self.dev["W"], stream)
+        t = self.steps[2].run(t, self.dev["W"], stream)
+        return self.steps[3].run(t, self.dev["R"], stream)
+
+
+class LxContraction:
+    """T = L x, the environment applied to the two-site tensor (SU(2) workloads)."""
+
+    def __init__(self, ctx, sym="SU2", D=256, gemm="fp64", slices=0, seed=0, device="cuda",
+                 dtype="f64"):
+        V, P, W = wl.heff_spaces(sym, D)
+        legs = wl.heff_legs(V, P, W)
+        self.legs = legs
+        self.tm = {k: _tmap(ctx, sym, legs[k]) for k in ("x", "L")}
+        rnd = wl.normal_complex if dtype == "c128" else wl.normal
+        self.host = {"x": rnd(seed * 16 + 0, self.tm["x"].numel), "L": rnd(seed * 16 + 1, self.tm["L"].numel)}
+        tdt = torch.complex128 if dtype == "c128" else torch.float64
+        self.dev = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device=device, dtype=tdt)
+                    for k, v in self.host.items()}
+        self.step = Contraction(ctx, self.tm["L"], self.tm["x"], wl.LX_SPEC, dtype, gemm, slices, device)
+        self.flops = self.step.plan.flops
+        self.permute_bytes = self.step.plan.permute_bytes
+
+    def run(self, stream=None):
+        return self.step.run(self.dev["L"], self.dev["x"], stream)

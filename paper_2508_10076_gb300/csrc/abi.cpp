@@ -141,6 +141,50 @@ int tk_ctx_sync(tk_ctx* ctx, void* stream) {
 
 int64_t tk_ctx_launch_count(const tk_ctx* ctx) { return ctx ? ctx->c.launches : -1; }
 
+int tk_ctx_profile(tk_ctx* ctx, int enable) {
+  if (!ctx) return TK_ERR_ARG;
+  if (ctx->c.device < 0) return fail(ctx, TK_ERR_NO_DEVICE, "profiling needs a device context");
+  ctx->c.profiling = enable != 0;
+  return TK_OK;
+}
+
+int tk_ctx_profile_read(tk_ctx* ctx, int max, char* names, int64_t* counts, double* total_ms, int* n_out) {
+  if (!ctx || max < 0 || (max > 0 && (!names || !counts || !total_ms)) || !n_out) return TK_ERR_ARG;
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  std::vector<std::string> keys;
+  std::vector<int64_t> cnt;
+  std::vector<double> ms;
+  int status = TK_OK;
+  for (auto& r : ctx->c.prof) {
+    float t = 0.f;
+    cudaEvent_t s = (cudaEvent_t)r.start, e = (cudaEvent_t)r.end;
+    if (cudaEventSynchronize(e) != cudaSuccess || cudaEventElapsedTime(&t, s, e) != cudaSuccess)
+      status = TK_ERR_CUDA;
+    cudaEventDestroy(s);
+    cudaEventDestroy(e);
+    size_t i = 0;
+    while (i < keys.size() && keys[i] != r.name) ++i;
+    if (i == keys.size()) {
+      keys.push_back(r.name);
+      cnt.push_back(0);
+      ms.push_back(0.0);
+    }
+    cnt[i] += 1;
+    ms[i] += t;
+  }
+  ctx->c.prof.clear();
+  *n_out = (int)keys.size();
+  for (int i = 0; i < (int)keys.size() && i < max; ++i) {
+    std::memset(names + 32 * i, 0, 32);
+    std::strncpy(names + 32 * i, keys[i].c_str(), 31);
+    counts[i] = cnt[i];
+    total_ms[i] = ms[i];
+  }
+  if (status != TK_OK) return fail(ctx, status, "reading profile events failed");
+  return TK_OK;
+}
+
 int tk_space_create(tk_ctx* ctx, int sym, int nsec, const int32_t* sectors, const int64_t* mults,
                     int is_dual, tk_space** out) {
   if (!out) return fail(ctx, TK_ERR_ARG, "null out");

@@ -29,6 +29,19 @@ void dev_free(void* p) {
   if (p) cudaFree(p);
 }
 
+ProfScope::ProfScope(Ctx* c, const char* n, void* s) : ctx(c), name(n), stream(s) {
+  if (!ctx->profiling) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) == cudaSuccess && cudaEventRecord(e, (cudaStream_t)s) == cudaSuccess) start = e;
+}
+
+ProfScope::~ProfScope() {
+  if (!start) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) == cudaSuccess && cudaEventRecord(e, (cudaStream_t)stream) == cudaSuccess)
+    ctx->prof.push_back(Ctx::Rec{name, start, (void*)e});
+}
+
 PermutePlan::~PermutePlan() {
   dev_free(d_tasks);
   dev_free(d_srcs);
@@ -290,6 +303,7 @@ int launch_permute(Ctx* ctx, const PermutePlan& pp, const void* in, void* out, v
   int64_t grid = std::min<int64_t>(pp.total_tiles, (int64_t)ctx->num_sms * 8);
   if (grid < 1) grid = 1;
   cudaStream_t s = (cudaStream_t)stream;
+  ProfScope prof(ctx, "k_permute", stream);
   if (pp.dtype == TK_C128)
     k_permute<double2><<<(unsigned)grid, 256, 0, s>>>(pp.d_tasks, ntasks, pp.d_tile_starts, pp.d_srcs,
                                                       pp.total_tiles, (const double2*)in, (double2*)out);
@@ -325,6 +339,7 @@ int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void
                      void* stream) {
   if (cp.n_gemm_tiles == 0) return TK_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  ProfScope prof(ctx, "k_gemm_f64", stream);
   const GemmItem* items = (const GemmItem*)cp.d_gemm_items;
   const GemmTile* tiles = (const GemmTile*)cp.d_gemm_tiles;
   if (cp.dtype == TK_C128)
@@ -342,6 +357,7 @@ int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream) {
   for (auto& z : cp.zeros) maxn = std::max(maxn, z.n);
   dim3 grid((unsigned)std::min<int64_t>((maxn + 255) / 256, 1024), (unsigned)std::min<size_t>(cp.zeros.size(), 65535));
   cudaStream_t s = (cudaStream_t)stream;
+  ProfScope prof(ctx, "k_zero", stream);
   if (cp.dtype == TK_C128)
     k_zero<double2><<<grid, 256, 0, s>>>((const ZeroItem*)cp.d_zero, (int)cp.zeros.size(), (double2*)c);
   else

@@ -197,6 +197,24 @@ struct Ctx {
   std::unordered_map<std::string, std::shared_ptr<PermutePlan>> perm_cache;
   std::unordered_map<std::string, std::shared_ptr<ContractPlan>> contract_cache;
   int* d_status = nullptr;  // device status word for bounded waits
+  // opt-in kernel profiling: (kernel name, start event, end event) per launch
+  bool profiling = false;
+  struct Rec {
+    const char* name;
+    void* start;
+    void* end;
+  };
+  std::vector<Rec> prof;
+};
+
+// Brackets one launch with events on its stream when the context is profiling.
+struct ProfScope {
+  Ctx* ctx;
+  const char* name;
+  void* stream;
+  void* start = nullptr;
+  ProfScope(Ctx* c, const char* n, void* s);
+  ~ProfScope();
 };
 
 // ------------------------------------------------------------------ device side (kernels)

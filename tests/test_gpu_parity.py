@@ -1,0 +1,208 @@
+"""CUDA path (libtk through the C ABI) against the CPU oracle, element by element.
+
+Bars: integer/structure work bit-exact; abelian permutes are pure copies and must be bit-exact;
+FP64 contractions within a relative Frobenius error of 1e-12 per block.
+"""
+
+import numpy as np
+import pytest
+
+from harness import oracle_heff, oracle_heff_inputs, ostruct, rel_frobenius_per_block
+from oracle import ops
+from paper_2508_10076_gb300 import build_library
+from paper_2508_10076_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def gctx():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build_library()
+    from paper_2508_10076_gb300 import api
+    ctx = api.Context(0)
+    yield ctx
+    torch.cuda.synchronize()
+    ctx.sync()
+
+
+def _api():
+    from paper_2508_10076_gb300 import api
+    return api
+
+
+def _lib_tmap(ctx, sym, legs):
+    cod, dom = legs
+    return ctx.tmap([ctx.space(sym, s, d) for s, d in cod], [ctx.space(sym, s, d) for s, d in dom])
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+PERMUTE_CASES = [
+    # (sym, legs) -- several tiles, ragged tails, dual legs, every tile mode
+    ("U1", ([({-2: 3, -1: 37, 0: 70, 1: 41, 2: 5}, False), ({-1: 1, 1: 1}, False)],
+            [({-2: 3, -1: 37, 0: 70, 1: 41, 2: 5}, True), ({-1: 1, 1: 2}, True)])),
+    ("U1", ([({-1: 3, 0: 2, 1: 4}, False), ({0: 33, 1: 17}, True), ({-1: 5, 2: 9}, False)],
+            [({0: 40, 1: 7, 2: 3}, False)])),
+    ("SU2", ([({0: 9, 1: 7, 2: 5, 3: 2}, False), ({1: 1}, False)], [({0: 6, 1: 8, 2: 4}, True), ({1: 1}, True)])),
+    ("SU2", ([({1: 3, 2: 2}, True), ({0: 2, 2: 3}, False), ({1: 2}, False)], [({0: 5, 2: 2, 4: 1}, False)])),
+    ("Z2", ([({0: 50, 1: 45}, False), ({0: 2, 1: 3}, True)], [({0: 31, 1: 29}, False), ({1: 4}, True)])),
+]
+
+
+def _perms(n, rng, k=6):
+    out = []
+    for _ in range(k):
+        perm = list(rng.permutation(n))
+        s = int(rng.integers(0, n + 1))
+        out.append((tuple(perm[:s]), tuple(perm[s:])))
+    return out
+
+
+@pytest.mark.parametrize("case", range(len(PERMUTE_CASES)))
+@pytest.mark.parametrize("dtype", ["f64", "c128"])
+def test_permute_parity(gctx, case, dtype):
+    api = _api()
+    sym, legs = PERMUTE_CASES[case]
+    ost = ostruct(sym, legs)
+    lt = _lib_tmap(gctx, sym, legs)
+    x = wl.normal_complex(case, ost.numel) if dtype == "c128" else wl.normal(case, ost.numel)
+    xd = _dev(x)
+    rng = np.random.default_rng(100 + case)
+    perms = _perms(ost.nleg, rng)
+    perms.append(((ost.nleg - 1,) + tuple(range(ost.nleg - 1))[:1], tuple(range(1, ost.nleg - 1))))
+    for p, q in perms:
+        if sorted(p + q) != list(range(ost.nleg)):
+            continue
+        os_, ref = ops.permute_block(ost, x, p, q)
+        plan = api.permute_plan(gctx, lt, p, q, dtype=dtype)
+        out = plan.output()
+        assert out.blocks() == [(c, r, k, o) for c, r, k, o in os_.blocks]
+        yd = torch.full((out.numel,), float("nan"), dtype=xd.dtype, device="cuda")
+        api.permute(gctx, plan, xd, yd)
+        gctx.sync()
+        got = yd.cpu().numpy()
+        if sym == "SU2":
+            assert np.allclose(got, ref, rtol=1e-13, atol=1e-13), (p, q)
+        else:
+            assert np.array_equal(got, ref), (p, q)
+
+
+def test_c0_contraction_fp64(gctx):
+    api = _api()
+    v = {-2: 1, -1: 2, 0: 3, 1: 2, 2: 1}
+    la = ([(v, False), (v, False)], [(v, False), (v, False)])
+    lb = ([(v, False), (v, True)], [(v, False), (v, False)])
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    for seed in range(3):
+        xa, xb = wl.normal(2 * seed, oa.numel), wl.normal(2 * seed + 1, ob.numel)
+        cs, ref = ops.contract(oa, xa, *wl.C0_SPEC[:2], ob, xb, *wl.C0_SPEC[2:], tier="dense")
+        A, B = _lib_tmap(gctx, "U1", la), _lib_tmap(gctx, "U1", lb)
+        plan = api.contract_plan(gctx, A, *wl.C0_SPEC[:2], B, *wl.C0_SPEC[2:])
+        assert plan.flops == 34362
+        c = torch.full((plan.output().numel,), float("nan"), dtype=torch.float64, device="cuda")
+        ws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
+        api.contract(gctx, plan, _dev(xa), _dev(xb), c, ws)
+        gctx.sync()
+        got = c.cpu().numpy()
+        assert rel_frobenius_per_block(cs, got, ref) <= FP64_TOL
+
+
+def test_su2_lx_contraction_fp64(gctx):
+    """SU(2) L.x at sum n = 256 (full dimension 750): permutes with 6j recoupling + GEMMs."""
+    from paper_2508_10076_gb300.chain import LxContraction
+    lx = LxContraction(gctx, "SU2", 256)
+    got = lx.run()
+    gctx.sync()
+    st, data = oracle_heff_inputs("SU2", 256)
+    cs, ref = ops.contract(st["L"], data["L"], *wl.LX_SPEC[:2], st["x"], data["x"], *wl.LX_SPEC[2:],
+                           tier="block")
+    assert lx.step.out.blocks() == [(c, r, k, o) for c, r, k, o in cs.blocks]
+    assert rel_frobenius_per_block(cs, got.cpu().numpy(), ref) <= FP64_TOL
+
+
+def test_heff_chain_u1_d1024_fp64(gctx):
+    """The two-site heff chain at D = 1024, every intermediate against the oracle block tier."""
+    from paper_2508_10076_gb300.chain import HeffChain
+    ch = HeffChain(gctx, "U1", 1024)
+    ref = oracle_heff("U1", 1024, tier="block")
+    t = ch.dev["x"]
+    bufs = []
+    t = ch.steps[0].run(ch.dev["L"], t)
+    bufs.append(t)
+    t = ch.steps[1].run(t, ch.dev["W"])
+    bufs.append(t)
+    t = ch.steps[2].run(t, ch.dev["W"])
+    bufs.append(t)
+    t = ch.steps[3].run(t, ch.dev["R"])
+    bufs.append(t)
+    gctx.sync()
+    for i, ((cs, rd), b) in enumerate(zip(ref, bufs)):
+        assert ch.steps[i].out.blocks() == [(c, r, k, o) for c, r, k, o in cs.blocks]
+        assert rel_frobenius_per_block(cs, b.cpu().numpy(), rd) <= FP64_TOL, i
+
+
+def test_heff_chain_complex(gctx):
+    from paper_2508_10076_gb300.chain import HeffChain
+    ch = HeffChain(gctx, "U1", 96, dtype="c128", seed=3)
+    got = ch.run()
+    gctx.sync()
+    cs, rd = oracle_heff("U1", 96, seed=3, tier="block", dtype="c128")[-1]
+    assert rel_frobenius_per_block(cs, got.cpu().numpy(), rd) <= FP64_TOL
+
+
+def test_zero_blocks_when_inner_dimension_empty(gctx):
+    api = _api()
+    la = ([({0: 2, 1: 3}, False)], [({0: 3}, False)])
+    lb = ([({0: 3}, False)], [({0: 2, 1: 1}, False)])
+    A, B = _lib_tmap(gctx, "U1", la), _lib_tmap(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,))
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    xa, xb = wl.normal(1, oa.numel), wl.normal(2, ob.numel)
+    cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
+    c = torch.full((plan.output().numel,), float("nan"), dtype=torch.float64, device="cuda")
+    api.contract(gctx, plan, _dev(xa), _dev(xb), c, None)
+    gctx.sync()
+    got = c.cpu().numpy()
+    assert not np.isnan(got).any()
+    assert rel_frobenius_per_block(cs, got, ref) <= FP64_TOL
+
+
+def test_rank_one_and_trivial_extents(gctx):
+    api = _api()
+    legs = ([({0: 1}, False)], [])
+    lt = _lib_tmap(gctx, "SU2", legs)
+    plan = api.permute_plan(gctx, lt, (), (0,))
+    x = torch.tensor([2.5], dtype=torch.float64, device="cuda")
+    y = torch.empty(1, dtype=torch.float64, device="cuda")
+    api.permute(gctx, plan, x, y)
+    gctx.sync()
+    ost = ostruct("SU2", legs)
+    _, ref = ops.permute_block(ost, np.array([2.5]), (), (0,))
+    assert np.allclose(y.cpu().numpy(), ref)
+
+
+def test_workspace_too_small_is_an_error(gctx):
+    api = _api()
+    from paper_2508_10076_gb300.chain import LxContraction
+    lx = LxContraction(gctx, "SU2", 32)
+    c = lx.step.c
+    small = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(api.TKError) as e:
+        api.contract(gctx, lx.step.plan, lx.dev["L"], lx.dev["x"], c, small)
+    assert e.value.code == 9
+
+
+def test_runs_are_bitwise_deterministic(gctx):
+    from paper_2508_10076_gb300.chain import HeffChain
+    ch = HeffChain(gctx, "U1", 256)
+    a = ch.run().clone()
+    b = ch.run().clone()
+    gctx.sync()
+    assert torch.equal(a, b)
+    assert gctx.launches > 0
