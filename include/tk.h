@@ -176,6 +176,25 @@ int tk_permute(tk_ctx* ctx, const tk_plan* plan, const void* a, void* c, void* s
 int tk_contract(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, void* c,
                 void* workspace, size_t workspace_bytes, void* stream);
 
+/* Contraction without any device allocation -- no counterpart in the paper.  Same result and
+ * launch sequence as tk_contract, but the scratch memory (permuted operands and the intermediate
+ * C~) comes from a fixed array compiled into libtk instead of a caller-allocated workspace.  It
+ * is for callers that cannot allocate device memory: programs whose device memory is owned by
+ * another framework's allocator, serving loops that must not take the synchronisation a
+ * cudaMalloc can cause, plug-ins handed only their input and output buffers.  The call itself
+ * calls no cudaMalloc/cudaFree and no allocating library routine (the plan, built earlier,
+ * already holds its device tables).
+ *   - Limit: plans whose tk_plan_workspace_bytes() exceeds TK_NOALLOC_SCRATCH_BYTES are rejected
+ *     with TK_ERR_WORKSPACE.  Every GPU that loads libtk holds the array until the process exits.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls share the one array, which keeps the previous call's contents; a call writes every
+ *     scratch byte it reads, so nothing has to start at zero.  Calls whose kernels overlap on the
+ *     GPU (other streams, other host threads) race on the array: serialise them. */
+#define TK_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+int tk_contract_noalloc(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, void* c,
+                        void* stream);
+
 /* Host <-> device copies on the context's device (cudaMemcpyAsync; pinned host memory makes
  * them asynchronous). */
 int tk_copy_h2d(tk_ctx* ctx, void* dst_device, const void* src_host, size_t bytes, void* stream);

@@ -283,6 +283,16 @@ def contract(ctx, plan, a, b, c, workspace=None, stream=None):
                               C.c_size_t(nbytes), _stream_handle(stream)), ctx)
 
 
+# Mirrors TK_NOALLOC_SCRATCH_BYTES in include/tk.h.
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def contract_noalloc(ctx, plan, a, b, c, stream=None):
+    """tk_contract_noalloc: the contraction with its scratch in libtk's built-in device array,
+    for callers that cannot allocate device memory (see include/tk.h)."""
+    _check(_lib().tk_contract_noalloc(ctx._h, plan._h, _ptr(a), _ptr(b), _ptr(c), _stream_handle(stream)), ctx)
+
+
 def copy_h2d(ctx, dst, src_host_ptr, nbytes, stream=None):
     _check(_lib().tk_copy_h2d(ctx._h, _ptr(dst), C.c_void_p(src_host_ptr), C.c_size_t(nbytes),
                               _stream_handle(stream)), ctx)
