@@ -194,11 +194,17 @@ __global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ ta
 }
 
 // ------------------------------------------------------------------ K2 grouped FP64 GEMM
+// Work list of output tiles over all sector GEMMs of one contraction, each tile tagged with one
+// of three shapes chosen on the host: 64x64 (4x4 per thread), 32x32 (2x2 per thread) when the
+// 64x64 tiles are too few to fill 152 SMs, and a row kernel for N <= 8 (one output row per
+// thread; the skinny MPO products).  Tiles are sorted by cost (M_t N_t K) descending.
 struct GemmTile {
-  int32_t item, m0, n0, pad;
+  int32_t item, m0, n0, cfg;
 };
 
-constexpr int BM = 64, BN = 64, BK = 16;
+enum { CFG_64 = 0, CFG_32 = 1, CFG_ROWS = 2 };
+constexpr int BK = 16;
+constexpr int ROWS_PER_CTA = 256, ROWS_NMAX = 8, ROWS_KCHUNK = 256;
 
 template <typename T>
 struct Mac;
@@ -216,63 +222,115 @@ struct Mac<double2> {
   }
 };
 
-// One 64x64 output tile per CTA; tiles of all sectors sorted by K descending (longest first),
-// so the hardware CTA scheduler hands the big tiles out first.
-template <typename T>
-__global__ void __launch_bounds__(256) k_gemm_f64(const GemmItem* __restrict__ items,
-                                                  const GemmTile* __restrict__ tiles,
-                                                  const T* __restrict__ A,
-                                                  const T* __restrict__ B, T* __restrict__ C) {
-  __shared__ T As[BK][BM + 1];
-  __shared__ T Bs[BK][BN + 1];
-  const GemmTile tl = tiles[blockIdx.x];
-  const GemmItem it = items[tl.item];
+// One BMxBN tile with 256 threads in a 16x16 grid, TMxTN outputs per thread (BM = 16 TM).
+template <typename T, int BM, int BN, int TM, int TN>
+__device__ __forceinline__ void gemm_tile(const GemmItem& it, int64_t m0, int64_t n0,
+                                          const T* __restrict__ A, const T* __restrict__ B,
+                                          T* __restrict__ C, T* smem) {
+  T(*As)[BM + 1] = reinterpret_cast<T(*)[BM + 1]>(smem);
+  T(*Bs)[BN + 1] = reinterpret_cast<T(*)[BN + 1]>(smem + BK * (BM + 1));
   const int64_t M = it.M, N = it.N, K = it.K;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  T acc[4][4];
+  T acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = Elem<T>::zero();
+    for (int j = 0; j < TN; ++j) acc[i][j] = Elem<T>::zero();
   const T* Ab = A + it.a_off;
   const T* Bb = B + it.b_off;
   for (int64_t k0 = 0; k0 < K; k0 += BK) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int e = tid + 256 * r;
-      const int mm = e & 63, kk = e >> 6;
-      const int64_t gm = tl.m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < M && gk < K) ? Ab[gm + gk * M] : Elem<T>::zero();
-      const int kb = e & 15, nn = e >> 4;
-      const int64_t gk2 = k0 + kb, gn = tl.n0 + nn;
-      Bs[kb][nn] = (gk2 < K && gn < N) ? Bb[gk2 + gn * K] : Elem<T>::zero();
+    const int kmax = (int)((K - k0) < BK ? (K - k0) : BK);
+    for (int e = tid; e < BM * BK; e += 256) {
+      const int mm = e % BM, kk = e / BM;
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && kk < kmax) ? Ab[gm + gk * M] : Elem<T>::zero();
+    }
+    for (int e = tid; e < BN * BK; e += 256) {
+      const int kb = e % BK, nn = e / BK;
+      const int64_t gk = k0 + kb, gn = n0 + nn;
+      Bs[kb][nn] = (kb < kmax && gn < N) ? Bb[gk + gn * K] : Elem<T>::zero();
     }
     __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kmax; ++kk) {
+      T a[TM], b[TN];
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      T a[4], b[4];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][tx + 16 * i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][ty + 16 * j];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) Mac<T>::mac(acc[i][j], a[i], b[j]);
+        for (int j = 0; j < TN; ++j) Mac<T>::mac(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
   }
   T* Cb = C + it.c_off;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int64_t gn = tl.n0 + ty + 16 * j;
+  for (int j = 0; j < TN; ++j) {
+    const int64_t gn = n0 + ty + 16 * j;
     if (gn >= N) continue;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t gm = tl.m0 + tx + 16 * i;
+    for (int i = 0; i < TM; ++i) {
+      const int64_t gm = m0 + tx + 16 * i;
       if (gm < M) Cb[gm + gn * M] = acc[i][j];
     }
   }
+}
+
+// N <= 8: thread t owns row m0 + t, B streamed through shared memory in K chunks.
+template <typename T>
+__device__ __forceinline__ void gemm_rows(const GemmItem& it, int64_t m0, const T* __restrict__ A,
+                                          const T* __restrict__ B, T* __restrict__ C, T* smem) {
+  T(*Bs)[ROWS_NMAX] = reinterpret_cast<T(*)[ROWS_NMAX]>(smem);
+  const int64_t M = it.M, N = it.N, K = it.K;
+  const int tid = threadIdx.x;
+  const int64_t m = m0 + tid;
+  T acc[ROWS_NMAX];
+#pragma unroll
+  for (int j = 0; j < ROWS_NMAX; ++j) acc[j] = Elem<T>::zero();
+  const T* Ab = A + it.a_off;
+  const T* Bb = B + it.b_off;
+  for (int64_t k0 = 0; k0 < K; k0 += ROWS_KCHUNK) {
+    const int kmax = (int)((K - k0) < ROWS_KCHUNK ? (K - k0) : ROWS_KCHUNK);
+    for (int e = tid; e < ROWS_KCHUNK * ROWS_NMAX; e += 256) {
+      const int kk = e % ROWS_KCHUNK, nn = e / ROWS_KCHUNK;
+      Bs[kk][nn] = (kk < kmax && nn < N) ? Bb[(k0 + kk) + nn * K] : Elem<T>::zero();
+    }
+    __syncthreads();
+    if (m < M) {
+      for (int kk = 0; kk < kmax; ++kk) {
+        const T a = Ab[m + (k0 + kk) * M];
+#pragma unroll
+        for (int j = 0; j < ROWS_NMAX; ++j)
+          if (j < N) Mac<T>::mac(acc[j], a, Bs[kk][j]);
+      }
+    }
+    __syncthreads();
+  }
+  if (m < M) {
+    T* Cb = C + it.c_off;
+#pragma unroll
+    for (int j = 0; j < ROWS_NMAX; ++j)
+      if (j < N) Cb[m + j * M] = acc[j];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_f64(const GemmItem* __restrict__ items,
+                                                  const GemmTile* __restrict__ tiles,
+                                                  const T* __restrict__ A,
+                                                  const T* __restrict__ B, T* __restrict__ C) {
+  constexpr int kSmem = (BK * 65 * 2 > ROWS_KCHUNK * ROWS_NMAX) ? BK * 65 * 2 : ROWS_KCHUNK * ROWS_NMAX;
+  __shared__ T smem[kSmem];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmItem it = items[tl.item];
+  if (tl.cfg == CFG_64)
+    gemm_tile<T, 64, 64, 4, 4>(it, tl.m0, tl.n0, A, B, C, smem);
+  else if (tl.cfg == CFG_32)
+    gemm_tile<T, 32, 32, 2, 2>(it, tl.m0, tl.n0, A, B, C, smem);
+  else
+    gemm_rows<T>(it, tl.m0, A, B, C, smem);
 }
 
 template <typename T>
@@ -314,15 +372,34 @@ int launch_permute(Ctx* ctx, const PermutePlan& pp, const void* in, void* out, v
 }
 
 int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
-  std::vector<GemmTile> tiles;
-  std::vector<int> order(cp.gemms.size());
-  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cp.gemms[a].K > cp.gemms[b].K; });
-  for (int i : order) {
+  // shape choice: rows kernel for N <= 8; 64x64 tiles unless they give fewer than ~3 CTAs per
+  // SM over the whole launch, then 32x32
+  int64_t tiles64 = 0;
+  for (const GemmItem& g : cp.gemms)
+    if (g.N > ROWS_NMAX) tiles64 += ((g.M + 63) / 64) * ((g.N + 63) / 64);
+  const bool small_tiles = tiles64 < 3 * (int64_t)std::max(ctx->num_sms, 1);
+  struct Cand {
+    GemmTile t;
+    double cost;
+  };
+  std::vector<Cand> cands;
+  for (size_t i = 0; i < cp.gemms.size(); ++i) {
     const GemmItem& g = cp.gemms[i];
-    for (int64_t n0 = 0; n0 < g.N; n0 += BN)
-      for (int64_t m0 = 0; m0 < g.M; m0 += BM) tiles.push_back(GemmTile{i, (int32_t)m0, (int32_t)n0, 0});
+    if (g.N <= ROWS_NMAX) {
+      for (int64_t m0 = 0; m0 < g.M; m0 += ROWS_PER_CTA)
+        cands.push_back({GemmTile{(int32_t)i, (int32_t)m0, 0, CFG_ROWS},
+                         (double)std::min<int64_t>(ROWS_PER_CTA, g.M - m0) * g.N * g.K});
+      continue;
+    }
+    const int bm = small_tiles ? 32 : 64, bn = bm;
+    for (int64_t n0 = 0; n0 < g.N; n0 += bn)
+      for (int64_t m0 = 0; m0 < g.M; m0 += bm)
+        cands.push_back({GemmTile{(int32_t)i, (int32_t)m0, (int32_t)n0, small_tiles ? CFG_32 : CFG_64},
+                         (double)bm * bn * g.K});
   }
+  std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.cost > b.cost; });
+  std::vector<GemmTile> tiles;
+  for (auto& c : cands) tiles.push_back(c.t);
   cp.n_gemm_tiles = (int64_t)tiles.size();
   int rc = dev_upload(ctx, &cp.d_gemm_items, cp.gemms.data(), cp.gemms.size() * sizeof(GemmItem));
   if (rc != TK_OK) return rc;

@@ -158,10 +158,11 @@ struct ContractPlan {
   void* d_gemm_tiles = nullptr;
   int64_t n_gemm_tiles = 0;
   void* d_zero = nullptr;
-  // split-precision tables (owned; freed by the destructor)
+  // split-precision tables (owned; freed by the destructor) and the host-side layout
   std::vector<void*> d_oz;
   int64_t oz_nwork = 0;
   size_t oz_bytes = 0;
+  std::shared_ptr<void> oz;
   ~ContractPlan();
 };
 

@@ -1,0 +1,138 @@
+"""Split-precision (Ozaki BF16 on tcgen05) sector GEMMs against FP64 and the oracle."""
+
+import numpy as np
+import pytest
+
+from harness import oracle_heff, oracle_heff_inputs, ostruct, rel_frobenius_per_block
+from oracle import ops
+from paper_2508_10076_gb300 import build_library
+from paper_2508_10076_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SPLIT_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def gctx():
+    assert torch.cuda.is_available()
+    build_library()
+    from paper_2508_10076_gb300 import api
+    ctx = api.Context(0)
+    yield ctx
+    ctx.sync()
+
+
+def _api():
+    from paper_2508_10076_gb300 import api
+    return api
+
+
+def _tm(ctx, sym, legs):
+    cod, dom = legs
+    return ctx.tmap([ctx.space(sym, s, d) for s, d in cod], [ctx.space(sym, s, d) for s, d in dom])
+
+
+def _run(ctx, plan, a, b):
+    api = _api()
+    c = torch.full((plan.output().numel,), float("nan"), dtype=torch.float64, device="cuda")
+    ws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
+    api.contract(ctx, plan, a, b, c, ws)
+    ctx.sync()
+    return c
+
+
+def test_integer_inputs_are_exact(gctx):
+    """Integer entries |x| <= 255: every slice product and every exact level is an integer times a
+    power of two, so the split-precision result equals the FP64 result bit for bit (this also
+    checks that tensor-core FP32 accumulation adds these values without rounding)."""
+    api = _api()
+    legs_a = ([({-1: 40, 0: 150, 1: 60}, False), ({0: 2, 1: 1}, False)], [({-1: 30, 0: 200, 1: 45}, False)])
+    legs_b = ([({-1: 30, 0: 200, 1: 45}, False)], [({-1: 50, 0: 170, 1: 20}, False)])
+    A, B = _tm(gctx, "U1", legs_a), _tm(gctx, "U1", legs_b)
+    xa = torch.from_numpy(wl.integer_valued(1, A.numel)).cuda()
+    xb = torch.from_numpy(wl.integer_valued(2, B.numel)).cuda()
+    spec = ((0, 1), (2,), (0,), (1,), (0, 1), (2,))
+    p64 = api.contract_plan(gctx, A, *spec[:2], B, *spec[2:])
+    poz = api.contract_plan(gctx, A, *spec[:2], B, *spec[2:], gemm="ozaki")
+    c64, coz = _run(gctx, p64, xa, xb), _run(gctx, poz, xa, xb)
+    assert torch.equal(c64, coz)
+
+
+@pytest.mark.parametrize("slices,tol", [(6, SPLIT_TOL), (7, 1e-12)])
+def test_c0_split_precision(gctx, slices, tol):
+    api = _api()
+    v = {-2: 1, -1: 2, 0: 3, 1: 2, 2: 1}
+    la = ([(v, False), (v, False)], [(v, False), (v, False)])
+    lb = ([(v, False), (v, True)], [(v, False), (v, False)])
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    xa, xb = wl.normal(0, oa.numel), wl.normal(1, ob.numel)
+    cs, ref = ops.contract(oa, xa, *wl.C0_SPEC[:2], ob, xb, *wl.C0_SPEC[2:], tier="dense")
+    A, B = _tm(gctx, "U1", la), _tm(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, *wl.C0_SPEC[:2], B, *wl.C0_SPEC[2:], gemm="ozaki", slices=slices)
+    c = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda())
+    assert rel_frobenius_per_block(cs, c.cpu().numpy(), ref) <= tol
+
+
+def test_heff_chain_split_precision_d1024(gctx):
+    from paper_2508_10076_gb300.chain import HeffChain
+    ch = HeffChain(gctx, "U1", 1024, gemm="ozaki")
+    ref = oracle_heff("U1", 1024, tier="block")
+    t = ch.steps[0].run(ch.dev["L"], ch.dev["x"])
+    outs = [t]
+    for i, other in ((1, "W"), (2, "W"), (3, "R")):
+        t = ch.steps[i].run(t, ch.dev[other])
+        outs.append(t)
+    gctx.sync()
+    for i, ((cs, rd), b) in enumerate(zip(ref, outs)):
+        err = rel_frobenius_per_block(cs, b.cpu().numpy(), rd)
+        assert err <= SPLIT_TOL, (i, err)
+
+
+def test_su2_lx_split_precision(gctx):
+    from paper_2508_10076_gb300.chain import LxContraction
+    lx = LxContraction(gctx, "SU2", 256, gemm="ozaki")
+    got = lx.run()
+    gctx.sync()
+    st, data = oracle_heff_inputs("SU2", 256)
+    cs, ref = ops.contract(st["L"], data["L"], *wl.LX_SPEC[:2], st["x"], data["x"], *wl.LX_SPEC[2:], tier="block")
+    assert rel_frobenius_per_block(cs, got.cpu().numpy(), ref) <= SPLIT_TOL
+
+
+def test_long_inner_dimension_uses_segments(gctx):
+    """K = 1300 > 512: several exact segments added in FP64; ragged M, N tails."""
+    api = _api()
+    la = ([({0: 300, 1: 7}, False)], [({0: 1300, 1: 3}, False)])
+    lb = ([({0: 1300, 1: 3}, False)], [({0: 200, 1: 5}, False)])
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    xa, xb = wl.normal(5, oa.numel), wl.normal(6, ob.numel)
+    cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
+    A, B = _tm(gctx, "U1", la), _tm(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), gemm="ozaki")
+    c = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda())
+    assert rel_frobenius_per_block(cs, c.cpu().numpy(), ref) <= SPLIT_TOL
+
+
+def test_scales_span_many_binades(gctx):
+    """Rows and columns scaled by 2^(+-40): per-row/per-column power-of-two scales absorb them."""
+    api = _api()
+    la = ([({0: 130, 1: 20}, False)], [({0: 100, 1: 9}, False)])
+    lb = ([({0: 100, 1: 9}, False)], [({0: 140, 1: 33}, False)])
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    rng = np.random.default_rng(9)
+    xa = wl.normal(7, oa.numel) * np.exp2(rng.integers(-40, 41, oa.numel))
+    xb = wl.normal(8, ob.numel) * np.exp2(rng.integers(-40, 41, ob.numel))
+    cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
+    A, B = _tm(gctx, "U1", la), _tm(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), gemm="ozaki")
+    c = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda())
+    # the scheme keeps 7 s bits below each row's and each column's largest magnitude: its error
+    # is bounded by a small multiple of 2^(-7 s) K max_k|a_mk| max_k|b_kn| per entry
+    got = c.cpu().numpy()
+    for (ca, ra, ka, oa_), (cb, rb, kb, ob_), (cc, rc, kc, oc) in zip(oa.blocks, ob.blocks, cs.blocks):
+        am = xa[oa_:oa_ + ra * ka].reshape(ka, ra).T
+        bm = xb[ob_:ob_ + rb * kb].reshape(kb, rb).T
+        bound = 8 * 2.0 ** (-42) * ka * np.abs(am).max(axis=1)[:, None] * np.abs(bm).max(axis=0)[None, :]
+        err = np.abs(got[oc:oc + rc * kc] - ref[oc:oc + rc * kc]).reshape(kc, rc).T
+        assert np.all(err <= bound)
