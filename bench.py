@@ -226,6 +226,17 @@ def run_ours(args):
     for _ in range(max(3, args.warmup)):
         work.run()
     ctx.sync()
+    # one application as a CUDA graph (eager launches if capture is unavailable)
+    step_fn, per_step_launches, mode = work.run, None, "eager"
+    if not args.eager:
+        try:
+            graph, _, per_step_launches = work.capture()
+            step_fn, mode = graph.replay, "cuda_graph"
+            for _ in range(max(3, args.warmup)):
+                step_fn()
+            torch.cuda.synchronize()
+        except Exception as exc:  # keep the eager path; report why
+            step_fn, mode = work.run, f"eager (graph capture failed: {exc})"
     # ---------------- timed region: K steps, L2 flushed before each, events around each step
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -236,11 +247,11 @@ def run_ours(args):
     for i in range(args.steps):
         flush.zero_()
         starts[i].record(stream)
-        work.run()
+        step_fn()
         ends[i].record(stream)
     barrier()
     clk = clocks.stop()
-    launches = ctx.launches - launches0
+    launches = ctx.launches - launches0 if per_step_launches is None else per_step_launches * args.steps
     ctx.sync()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
@@ -283,6 +294,52 @@ def run_ours(args):
         e2e_ms = float(t.item())
     e2e_value = flops * args.steps * world / (e2e_ms * 1e-3) / 1e9
     ctx.sync()
+    # ---------------- split-precision variant of the same workload (Ozaki BF16 on tcgen05)
+    split = None
+    if not args.no_split:
+        ref_out = run().clone()
+        oz = _workload(ctx, args.config, "ozaki")
+        for _ in range(max(3, args.warmup)):
+            oz.run()
+        oz_fn = oz.run
+        if mode == "cuda_graph":
+            oz_graph, _, _ = oz.capture()
+            oz_fn = oz_graph.replay
+            for _ in range(max(3, args.warmup)):
+                oz_fn()
+        o_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        o_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        barrier()
+        for i in range(args.steps):
+            flush.zero_()
+            o_start[i].record(stream)
+            oz_fn()
+            o_end[i].record(stream)
+        barrier()
+        oz_ms = sum(s.elapsed_time(e) for s, e in zip(o_start, o_end))
+        if dist is not None:
+            t = torch.tensor([oz_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            oz_ms = float(t.item())
+        oz_out = oz.run()
+        ctx.profile(True)
+        for i in range(args.steps):
+            flush.zero_()
+            oz.run()
+        ctx.sync()
+        oz_prof = ctx.profile_read()
+        ctx.profile(False)
+        out_blocks = (oz.steps[-1].out if hasattr(oz, "steps") else oz.step.out).blocks()
+        worst = 0.0
+        refn = float(torch.linalg.norm(ref_out))
+        for _, r_, k_, o_ in out_blocks:
+            d = float(torch.linalg.norm(oz_out[o_:o_ + r_ * k_] - ref_out[o_:o_ + r_ * k_]))
+            n_ = float(torch.linalg.norm(ref_out[o_:o_ + r_ * k_]))
+            worst = max(worst, d / (n_ if n_ > 1e-13 * refn else refn))
+        split = {"value": flops * args.steps * world / (oz_ms * 1e-3) / 1e9, "unit": UNIT,
+                 "ms_per_step": oz_ms / args.steps, "slices": 6,
+                 "rel_frobenius_per_block_vs_fp64_path": worst,
+                 "kernels": {k: {"launches": c, "ms_per_step": ms / args.steps} for k, (c, ms) in oz_prof.items()}}
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -312,6 +369,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.config, "gemm": args.gemm, "block_flops_per_step": flops,
                    "permute_bytes_per_step": permute_bytes, "l2": "flushed (512 MB write) before every timed step",
+                   "launch": mode,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -319,6 +377,8 @@ def run_ours(args):
         "roofline": roof,
         "kernels": kernels,
     }
+    if split is not None:
+        line["split_precision"] = split
     if world == 1 and not args.no_cpu_baseline:
         n, dt, cores = cpu_baseline(args.config, budget_s=args.cpu_budget)
         line["cpu_baseline"] = {"value": flops * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -340,6 +400,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--budget", type=float, default=60.0, help="reference arm: total CPU seconds")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-split", action="store_true", help="skip the split-precision variant")
+    ap.add_argument("--eager", action="store_true", help="launch kernels one by one instead of a CUDA graph")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

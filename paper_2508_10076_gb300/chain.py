@@ -32,6 +32,25 @@ def mpo_data(tm, entries, numel):
     return data
 
 
+def capture_graph(ctx, fn):
+    """Record fn() (a sequence of libtk launches on the current stream) into a CUDA graph.
+
+    Two eager runs on a side stream first settle every one-time set-up (plan tables, kernel
+    attributes), so the capture contains kernel launches only."""
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    n0 = ctx.launches
+    with torch.cuda.graph(graph):
+        out = fn()
+    return graph, out, ctx.launches - n0
+
+
 class Contraction:
     """One planned contraction with its device buffers (inputs, output, workspace)."""
 
@@ -93,6 +112,10 @@ class HeffChain:
         t = self.steps[2].run(t, self.dev["W"], stream)
         return self.steps[3].run(t, self.dev["R"], stream)
 
+    def capture(self):
+        """One application recorded as a CUDA graph: (graph, output buffer, launches per replay)."""
+        return capture_graph(self.ctx, self.run)
+
 
 class LxContraction:
     """T = L x, the environment applied to the two-site tensor (SU(2) workloads)."""
@@ -114,3 +137,6 @@ class LxContraction:
 
     def run(self, stream=None):
         return self.step.run(self.dev["L"], self.dev["x"], stream)
+
+    def capture(self):
+        return capture_graph(self.step.ctx, self.run)

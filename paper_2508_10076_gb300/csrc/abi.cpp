@@ -461,20 +461,7 @@ int tk_contract(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, 
     return fail(ctx, TK_ERR_WORKSPACE, "workspace smaller than tk_plan_workspace_bytes()");
   int rc = set_device(ctx);
   if (rc != TK_OK) return rc;
-  char* ws = (char*)workspace;
-  const void* at = cp.pa->identity ? a : (const void*)(ws + cp.ws_at);
-  const void* bt = cp.pb->identity ? b : (const void*)(ws + cp.ws_bt);
-  void* ct = cp.pc ? (void*)(ws + cp.ws_ct) : c;
-  if (!cp.pa->identity && (rc = tk::launch_permute(&ctx->c, *cp.pa, a, (void*)at, stream)) != TK_OK) return rc;
-  if (!cp.pb->identity && (rc = tk::launch_permute(&ctx->c, *cp.pb, b, (void*)bt, stream)) != TK_OK) return rc;
-  if ((rc = tk::launch_zero(&ctx->c, cp, ct, stream)) != TK_OK) return rc;
-  if (cp.gemm_mode == TK_GEMM_FP64)
-    rc = tk::launch_gemm_fp64(&ctx->c, cp, at, bt, ct, stream);
-  else
-    rc = tk::launch_gemm_ozaki(&ctx->c, cp, at, bt, ct, ws + cp.ws_slices, stream);
-  if (rc != TK_OK) return rc;
-  if (cp.pc && (rc = tk::launch_permute(&ctx->c, *cp.pc, ct, c, stream)) != TK_OK) return rc;
-  return TK_OK;
+  return tk::run_contract(&ctx->c, cp, a, b, c, workspace, stream);
 }
 
 int tk_copy_h2d(tk_ctx* ctx, void* dst_device, const void* src_host, size_t bytes, void* stream) {

@@ -44,6 +44,8 @@ ProfScope::~ProfScope() {
 
 PermutePlan::~PermutePlan() {
   dev_free(d_tasks);
+  dev_free(d_rtasks);
+  dev_free(d_runs);
   dev_free(d_srcs);
   dev_free(d_tile_starts);
 }
@@ -120,26 +122,7 @@ __global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ ta
     __syncthreads();
     const int64_t local = tidx - t.tile_begin;
     const int nd = t.ndim;
-    if (t.mode == 0) {
-      const int e0 = t.ext[0], T0 = t.t0, T1 = t.t1;
-      const int64_t nb0 = (e0 + T0 - 1) / T0;
-      const int64_t b0 = local % nb0, bo = local / nb0;
-      const int64_t i0 = b0 * T0 + (tid % T0);
-      int64_t o = bo * T1 + (tid / T0);
-      int64_t outer_total = 1;
-      for (int k = 1; k < nd; ++k) outer_total *= t.ext[k];
-      if (i0 < e0 && o < outer_total) {
-        int64_t oa = t.out_off + i0, ir = i0, ic = 0;
-        for (int k = 1; k < nd; ++k) {
-          const int64_t x = o % t.ext[k];
-          o /= t.ext[k];
-          oa += x * t.ostr[k];
-          ir += x * t.irs[k];
-          ic += x * t.ics[k];
-        }
-        out[oa] = gather<T>(srcs, t.nsrc, t.src_begin, in, ir, ic);
-      }
-    } else if (t.mode == 1) {
+    if (t.mode == 1) {
       const int td = t.tdim;
       const int e0 = t.ext[0], et = t.ext[td];
       const int64_t nb0 = (e0 + 31) / 32, nbt = (et + 31) / 32;
@@ -193,6 +176,40 @@ __global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ ta
   }
 }
 
+// Contiguous runs (destination and sources share their fastest leg): one warp per run, lanes
+// along the run, four elements per lane in flight.  Abelian runs (one source, weight 1) are plain
+// copies; SU(2) runs sum their weighted sources in FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) k_permute_runs(const PermRun* __restrict__ runs, int64_t nruns,
+                                                      const PermTask* __restrict__ tasks,
+                                                      const PermSrc* __restrict__ srcs,
+                                                      const T* __restrict__ in, T* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nruns; r += nwarps) {
+    const PermRun run = runs[r];
+    const int nsrc = __ldg(&tasks[run.task].nsrc);
+    const int sb = __ldg(&tasks[run.task].src_begin);
+    const PermSrc s0 = srcs[sb];
+    T* dst = out + run.dst;
+    if (nsrc == 1 && s0.coef == 1.0) {
+      const T* src = in + s0.in_off + run.ir + run.ic * s0.ld;
+      for (int e = lane; e < run.len; e += 128) {
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (e + 32 * u < run.len) v[u] = __ldg(src + e + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (e + 32 * u < run.len) dst[e + 32 * u] = v[u];
+      }
+    } else {
+      for (int e = lane; e < run.len; e += 32)
+        dst[e] = gather<T>(srcs, nsrc, sb, in, run.ir + e, run.ic);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ K2 grouped FP64 GEMM
 // Work list of output tiles over all sector GEMMs of one contraction, each tile tagged with one
 // of three shapes chosen on the host: 64x64 (4x4 per thread), 32x32 (2x2 per thread) when the
@@ -202,7 +219,7 @@ struct GemmTile {
   int32_t item, m0, n0, cfg;
 };
 
-enum { CFG_64 = 0, CFG_32 = 1, CFG_ROWS = 2 };
+enum { CFG_64 = 0, CFG_32 = 1, CFG_ROWS = 2, CFG_ROWS_DF = 3 };
 constexpr int BK = 16;
 constexpr int ROWS_PER_CTA = 256, ROWS_NMAX = 8, ROWS_KCHUNK = 256;
 
@@ -316,6 +333,96 @@ __device__ __forceinline__ void gemm_rows(const GemmItem& it, int64_t m0, const 
   }
 }
 
+// Split-precision mode only: the N <= 8 row kernel in double-float arithmetic (pairs of FP32
+// with error-free products and sums), ~2^-44 relative per term, on the FP32 pipe.
+// a = hi + lo to ~2^-53, by integer operations on the FP64 bit pattern: hi keeps the sign, the
+// exponent and the top 23 stored mantissa bits; lo is the remaining 29 bits converted to FP32.
+// Values outside the normal FP32 range take the conversion instructions.
+__device__ __forceinline__ void df_split(double a, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) {  // zero or FP64 subnormal (far below FP32)
+    hi = 0.f;
+    lo = 0.f;
+    return;
+  }
+  const int ef = ex - 1023 + 127;
+  if (ef <= 52 || ef >= 255) {  // lo's scale 2^(ex-1075) must be a normal FP32
+    hi = __double2float_rn(a);
+    lo = __double2float_rn(a - (double)hi);
+    return;
+  }
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  hi = __uint_as_float(sign | ((unsigned int)ef << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu));
+  const unsigned int low = (unsigned int)(b & 0x1FFFFFFFu);  // value low * 2^(ex-1075)
+  // low < 2^29: its FP32 rounding loses at most 2^-24 of lo, i.e. ~2^-53 of a
+  const float lf = __uint2float_rn(low);
+  lo = __fmul_rn(lf, __uint_as_float((unsigned int)(ef - 52) << 23)) * (sign ? -1.f : 1.f);
+}
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  // __fmul_rn / __fadd_rn are never contracted into FMAs, which keeps the transformations exact
+  const float p = __fmul_rn(ah, bh);
+  const float pe = fmaf(ah, bh, -p);                 // exact error of ah*bh
+  const float cross = fmaf(ah, bl, fmaf(al, bh, pe));
+  const float s = __fadd_rn(sh, p);                  // two-sum of sh + p
+  const float bb = __fsub_rn(s, sh);
+  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sl = __fadd_rn(sl, __fadd_rn(e, cross));
+  sh = s;
+}
+__device__ __forceinline__ void gemm_rows_df(const GemmItem& it, int64_t m0, const double* __restrict__ A,
+                                             const double* __restrict__ B, double* __restrict__ C,
+                                             double* smem) {
+  float(*Bh)[ROWS_NMAX] = reinterpret_cast<float(*)[ROWS_NMAX]>(smem);
+  float(*Bl)[ROWS_NMAX] = reinterpret_cast<float(*)[ROWS_NMAX]>(reinterpret_cast<float*>(smem) + ROWS_KCHUNK * ROWS_NMAX);
+  const int64_t M = it.M, N = it.N, K = it.K;
+  const int tid = threadIdx.x;
+  const int64_t m = m0 + tid;
+  float sh[ROWS_NMAX], sl[ROWS_NMAX];
+#pragma unroll
+  for (int j = 0; j < ROWS_NMAX; ++j) sh[j] = sl[j] = 0.f;
+  const double* Ab = A + it.a_off;
+  const double* Bb = B + it.b_off;
+  for (int64_t k0 = 0; k0 < K; k0 += ROWS_KCHUNK) {
+    const int kmax = (int)((K - k0) < ROWS_KCHUNK ? (K - k0) : ROWS_KCHUNK);
+    for (int e = tid; e < ROWS_KCHUNK * ROWS_NMAX; e += 256) {
+      const int kk = e % ROWS_KCHUNK, nn = e / ROWS_KCHUNK;
+      float h = 0.f, l = 0.f;
+      if (kk < kmax && nn < N) df_split(Bb[(k0 + kk) + nn * K], h, l);
+      Bh[kk][nn] = h;
+      Bl[kk][nn] = l;
+    }
+    __syncthreads();
+    if (m < M) {
+      for (int kk = 0; kk < kmax; ++kk) {
+        float ah, al;
+        df_split(Ab[m + (k0 + kk) * M], ah, al);
+#pragma unroll
+        for (int j = 0; j < ROWS_NMAX; ++j)
+          if (j < N) df_mac(sh[j], sl[j], ah, al, Bh[kk][j], Bl[kk][j]);
+      }
+    }
+    __syncthreads();
+  }
+  if (m < M) {
+    double* Cb = C + it.c_off;
+#pragma unroll
+    for (int j = 0; j < ROWS_NMAX; ++j)
+      if (j < N) Cb[m + j * M] = (double)sh[j] + (double)sl[j];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void gemm_rows_df_dispatch(const GemmItem& it, int64_t m0, const T* A, const T* B, T* C,
+                                                      T* smem) {
+  gemm_rows<T>(it, m0, A, B, C, smem);  // complex tensors never take the split-precision path
+}
+template <>
+__device__ __forceinline__ void gemm_rows_df_dispatch<double>(const GemmItem& it, int64_t m0, const double* A,
+                                                              const double* B, double* C, double* smem) {
+  gemm_rows_df(it, m0, A, B, C, smem);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm_f64(const GemmItem* __restrict__ items,
                                                   const GemmTile* __restrict__ tiles,
@@ -329,8 +436,10 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const GemmItem* __restrict__ i
     gemm_tile<T, 64, 64, 4, 4>(it, tl.m0, tl.n0, A, B, C, smem);
   else if (tl.cfg == CFG_32)
     gemm_tile<T, 32, 32, 2, 2>(it, tl.m0, tl.n0, A, B, C, smem);
-  else
+  else if (tl.cfg == CFG_ROWS)
     gemm_rows<T>(it, tl.m0, A, B, C, smem);
+  else
+    gemm_rows_df_dispatch<T>(it, tl.m0, A, B, C, smem);
 }
 
 template <typename T>
@@ -356,26 +465,42 @@ int check_launch(Ctx* ctx, const char* what) {
 }  // namespace
 
 int launch_permute(Ctx* ctx, const PermutePlan& pp, const void* in, void* out, void* stream) {
-  if (pp.tasks.empty()) return TK_OK;
-  const int ntasks = (int)pp.tasks.size();
-  int64_t grid = std::min<int64_t>(pp.total_tiles, (int64_t)ctx->num_sms * 8);
-  if (grid < 1) grid = 1;
   cudaStream_t s = (cudaStream_t)stream;
-  ProfScope prof(ctx, "k_permute", stream);
-  if (pp.dtype == TK_C128)
-    k_permute<double2><<<(unsigned)grid, 256, 0, s>>>(pp.d_tasks, ntasks, pp.d_tile_starts, pp.d_srcs,
-                                                      pp.total_tiles, (const double2*)in, (double2*)out);
-  else
-    k_permute<double><<<(unsigned)grid, 256, 0, s>>>(pp.d_tasks, ntasks, pp.d_tile_starts, pp.d_srcs,
-                                                     pp.total_tiles, (const double*)in, (double*)out);
-  return check_launch(ctx, "k_permute");
+  if (!pp.runs.empty()) {
+    const int64_t nruns = (int64_t)pp.runs.size();
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((nruns + 7) / 8, (int64_t)ctx->num_sms * 8));
+    ProfScope prof(ctx, "k_permute", stream);
+    if (pp.dtype == TK_C128)
+      k_permute_runs<double2><<<(unsigned)grid, 256, 0, s>>>(pp.d_runs, nruns, pp.d_rtasks, pp.d_srcs,
+                                                             (const double2*)in, (double2*)out);
+    else
+      k_permute_runs<double><<<(unsigned)grid, 256, 0, s>>>(pp.d_runs, nruns, pp.d_rtasks, pp.d_srcs,
+                                                            (const double*)in, (double*)out);
+    int rc = check_launch(ctx, "k_permute_runs");
+    if (rc != TK_OK) return rc;
+  }
+  if (!pp.tasks.empty()) {
+    const int ntasks = (int)pp.tasks.size();
+    int64_t grid = std::min<int64_t>(pp.total_tiles, (int64_t)ctx->num_sms * 8);
+    if (grid < 1) grid = 1;
+    ProfScope prof(ctx, "k_permute", stream);
+    if (pp.dtype == TK_C128)
+      k_permute<double2><<<(unsigned)grid, 256, 0, s>>>(pp.d_tasks, ntasks, pp.d_tile_starts, pp.d_srcs,
+                                                        pp.total_tiles, (const double2*)in, (double2*)out);
+    else
+      k_permute<double><<<(unsigned)grid, 256, 0, s>>>(pp.d_tasks, ntasks, pp.d_tile_starts, pp.d_srcs,
+                                                       pp.total_tiles, (const double*)in, (double*)out);
+    return check_launch(ctx, "k_permute");
+  }
+  return TK_OK;
 }
 
 int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
   // shape choice: rows kernel for N <= 8; 64x64 tiles unless they give fewer than ~3 CTAs per
   // SM over the whole launch, then 32x32
+  const std::vector<GemmItem>& gl = cp.gemms_fp64;
   int64_t tiles64 = 0;
-  for (const GemmItem& g : cp.gemms)
+  for (const GemmItem& g : gl)
     if (g.N > ROWS_NMAX) tiles64 += ((g.M + 63) / 64) * ((g.N + 63) / 64);
   const bool small_tiles = tiles64 < 3 * (int64_t)std::max(ctx->num_sms, 1);
   struct Cand {
@@ -383,11 +508,12 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
     double cost;
   };
   std::vector<Cand> cands;
-  for (size_t i = 0; i < cp.gemms.size(); ++i) {
-    const GemmItem& g = cp.gemms[i];
+  for (size_t i = 0; i < gl.size(); ++i) {
+    const GemmItem& g = gl[i];
     if (g.N <= ROWS_NMAX) {
       for (int64_t m0 = 0; m0 < g.M; m0 += ROWS_PER_CTA)
-        cands.push_back({GemmTile{(int32_t)i, (int32_t)m0, 0, CFG_ROWS},
+        cands.push_back({GemmTile{(int32_t)i, (int32_t)m0, 0,
+                                  cp.gemm_mode == TK_GEMM_FP64 ? CFG_ROWS : CFG_ROWS_DF},
                          (double)std::min<int64_t>(ROWS_PER_CTA, g.M - m0) * g.N * g.K});
       continue;
     }
@@ -401,7 +527,7 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
   std::vector<GemmTile> tiles;
   for (auto& c : cands) tiles.push_back(c.t);
   cp.n_gemm_tiles = (int64_t)tiles.size();
-  int rc = dev_upload(ctx, &cp.d_gemm_items, cp.gemms.data(), cp.gemms.size() * sizeof(GemmItem));
+  int rc = dev_upload(ctx, &cp.d_gemm_items, gl.data(), gl.size() * sizeof(GemmItem));
   if (rc != TK_OK) return rc;
   rc = dev_upload(ctx, &cp.d_gemm_tiles, tiles.data(), tiles.size() * sizeof(GemmTile));
   if (rc != TK_OK) return rc;
@@ -440,6 +566,23 @@ int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream) {
   else
     k_zero<double><<<grid, 256, 0, s>>>((const ZeroItem*)cp.d_zero, (int)cp.zeros.size(), (double*)c);
   return check_launch(ctx, "k_zero");
+}
+
+int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
+                 void* stream) {
+  char* w = (char*)ws;
+  const void* at = cp.pa->identity ? a : (const void*)(w + cp.ws_at);
+  const void* bt = cp.pb->identity ? b : (const void*)(w + cp.ws_bt);
+  void* ct = cp.pc ? (void*)(w + cp.ws_ct) : c;
+  int rc;
+  if (!cp.pa->identity && (rc = launch_permute(ctx, *cp.pa, a, (void*)at, stream)) != TK_OK) return rc;
+  if (!cp.pb->identity && (rc = launch_permute(ctx, *cp.pb, b, (void*)bt, stream)) != TK_OK) return rc;
+  if ((rc = launch_zero(ctx, cp, ct, stream)) != TK_OK) return rc;
+  if (!cp.gemms_fp64.empty() && (rc = launch_gemm_fp64(ctx, cp, at, bt, ct, stream)) != TK_OK) return rc;
+  if (!cp.gemms_oz.empty() && (rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream)) != TK_OK)
+    return rc;
+  if (cp.pc && (rc = launch_permute(ctx, *cp.pc, ct, c, stream)) != TK_OK) return rc;
+  return TK_OK;
 }
 
 }  // namespace tk

@@ -34,12 +34,13 @@ namespace tk {
 namespace {
 
 constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 64;
-constexpr int OZ_STAGES = 4;
+constexpr int OZ_STAGES = 6;
 constexpr int OZ_TILE_BYTES = OZ_BM * OZ_BK * 2;  // A and B tiles are both 128 x 64 BF16
 constexpr int OZ_SEG_KC = 8;                      // k-chunks per exact segment (K <= 512)
 constexpr int OZ_NACC = 4;
 constexpr int OZ_TMEM_COLS = 512;                 // 4 accumulators x 128 FP32 columns
-constexpr int OZ_THREADS = 192;
+constexpr int OZ_EPI_WARPS = 8;                   // two per TMEM lane quadrant
+constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;  // producer warp, MMA warp, epilogue warps
 constexpr int OZ_MAX_SLICES = 8;
 constexpr int OZ_MAX_PAIRS = OZ_MAX_SLICES * (OZ_MAX_SLICES + 1) / 2;
 constexpr int OZ_DEFAULT_SLICES = 6;
@@ -168,14 +169,58 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-__device__ __forceinline__ double pow2(int e) {
-  if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(1023 + e) << 52);
-  return ldexp(1.0, e);
+// Exact FP32 -> FP64 by assembling the bit pattern with integer operations (the FP64 pipe is
+// scarce on this part); zeros and FP32 subnormals/non-finite values take the hardware path.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ex = (u >> 23) & 0xFFu;
+  if (ex == 0u) {
+    if ((u << 1) == 0u) return __longlong_as_double((long long)(u & 0x80000000u) << 32);  // +-0
+    return (double)f;
+  }
+  if (ex == 0xFFu) return (double)f;
+  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
+// v * 2^e, exact, by adding e to the exponent field when the result stays a normal number.
+__device__ __forceinline__ double scale_pow2(double v, int e) {
+  const long long b = __double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex != 0 && ex + e > 0 && ex + e < 0x7FF) return __longlong_as_double(b + ((long long)e << 52));
+  if (v == 0.0) return v;
+  return ldexp(v, e);
+}
+
+// round(v * 2^shift) to the nearest integer (ties away from zero) from the bit pattern of v; the
+// caller guarantees |v| 2^shift <= 2^62.
+__device__ __forceinline__ long long round_scaled(double v, int shift) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  int e2;
+  if (ex == 0) {
+    if (m == 0) return 0;
+    e2 = -1074;  // subnormal: v = m 2^-1074
+  } else {
+    m |= 1ull << 52;
+    e2 = ex - 1075;  // v = m 2^(ex - 1075)
+  }
+  const int sh = e2 + shift;
+  unsigned long long q;
+  if (sh >= 0)
+    q = m << sh;
+  else if (sh <= -64)
+    q = 0;
+  else
+    q = (m >> (-sh)) + ((m >> (-sh - 1)) & 1ull);
+  return (b >> 63) ? -(long long)q : (long long)q;
 }
 
 // ------------------------------------------------------------------ scale and slice kernels
@@ -185,23 +230,51 @@ __device__ __forceinline__ double oz_elem(const OzSector& s, int operand, const 
   return operand == 0 ? X[s.a_off + r + k * s.M] : X[s.b_off + k + r * s.K];
 }
 
+// Scale exponents 2^e > max_k |x_rk| for every row of A~^c and every column of B~^c.  The
+// exponent of a maximum is the maximum of the exponents, so each job covers a chunk of K and
+// folds its partial result in with atomicMax (the arrays start at kNoScale).
+constexpr int32_t kNoScale = (int32_t)0x80808080;  // memset pattern 0x80 = "no non-zero entry yet"
+constexpr int OZ_SCALE_KCHUNK = 256;
+
+// e with 2^(e-1) <= mx < 2^e for a non-negative finite mx (kNoScale for 0), from the bits.
+__device__ __forceinline__ int exponent_of(double mx) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(mx);
+  if (b == 0) return kNoScale;
+  const int ex = (int)(b >> 52);
+  if (ex != 0) return ex - 1022;
+  return -1074 + (64 - __clzll((long long)b));  // subnormal: highest set bit
+}
+
 __global__ void __launch_bounds__(256) k_oz_scale(const OzSector* __restrict__ secs, const OzJob* __restrict__ jobs,
                                                   const double* __restrict__ A, const double* __restrict__ B,
                                                   int32_t* __restrict__ scale_a, int32_t* __restrict__ scale_b) {
   const OzJob jb = jobs[blockIdx.x];
   const OzSector s = secs[jb.sector];
-  const int64_t R = jb.operand == 0 ? s.M : s.N;
-  const int64_t r = jb.r0 + threadIdx.x;
-  if (r >= R) return;
-  const double* X = jb.operand == 0 ? A : B;
+  const int64_t k0 = (int64_t)jb.kc * OZ_SCALE_KCHUNK;
+  const int64_t k1 = min(s.K, k0 + OZ_SCALE_KCHUNK);
   double mx = 0.0;
-  for (int64_t k = 0; k < s.K; ++k) mx = fmax(mx, fabs(oz_elem(s, jb.operand, X, r, k)));
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);  // mx < 2^e
-  if (jb.operand == 0)
-    scale_a[s.sa_off + r] = e;
-  else
-    scale_b[s.sb_off + r] = e;
+  if (jb.operand == 0) {  // 256 rows, one thread per row, k-chunk of 256
+    const int64_t r = jb.r0 + threadIdx.x;
+    if (r >= s.M) return;
+    const long long* x = reinterpret_cast<const long long*>(A) + s.a_off + r;
+    unsigned long long mb = 0;  // |x| ordered as unsigned integers: no FP64 instructions
+    for (int64_t k = k0; k < k1; ++k) mb = max(mb, (unsigned long long)__ldg(x + k * s.M) & 0x7FFFFFFFFFFFFFFFull);
+    mx = __longlong_as_double((long long)mb);
+    const int e = exponent_of(mx);
+    if (e != kNoScale) atomicMax(&scale_a[s.sa_off + r], e);
+  } else {  // 8 columns, one warp per column, lanes along k
+    const int64_t r = jb.r0 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= s.N) return;  // the whole warp leaves together
+    const long long* x = reinterpret_cast<const long long*>(B) + s.b_off + r * s.K;
+    unsigned long long mb = 0;
+    for (int64_t k = k0 + lane; k < k1; k += 32) mb = max(mb, (unsigned long long)__ldg(x + k) & 0x7FFFFFFFFFFFFFFFull);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mb, o));
+    mx = __longlong_as_double((long long)mb);
+    const int e = exponent_of(mx);
+    if (lane == 0 && e != kNoScale) atomicMax(&scale_b[s.sb_off + r], e);
+  }
 }
 
 // One 128 x 64 (rows x k) tile of one operand per CTA, all slices.  Thread t: row t/2, k half t%2.
@@ -219,7 +292,8 @@ __global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ s
   const int64_t rt = jb.r0;  // row-tile index
   const int64_t r = rt * OZ_BM + rl;
   const double* X = op == 0 ? A : B;
-  const int e = (r < R) ? (op == 0 ? scale_a[s.sa_off + r] : scale_b[s.sb_off + r]) : 0;
+  int e = (r < R) ? (op == 0 ? scale_a[s.sa_off + r] : scale_b[s.sb_off + r]) : 0;
+  if (e == kNoScale) e = 0;  // an all-zero row or column
   const int shift = 7 * nslices - e;
   const int64_t nrt = op == 0 ? s.nmt : s.nnt;
   const int64_t base = op == 0 ? s.ta_base : s.tb_base;
@@ -230,8 +304,8 @@ __global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ s
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
       const int64_t k = k0 + jj;
-      double v = (r < R && k < s.K) ? oz_elem(s, op, X, r, k) : 0.0;
-      long long q = llrint(ldexp(v, shift));  // |q| <= 2^(7 s)
+      const double v = (r < R && k < s.K) ? oz_elem(s, op, X, r, k) : 0.0;
+      long long q = round_scaled(v, shift);  // round(v 2^shift), |q| <= 2^(7 s)
       for (int i = nslices - 1; i >= 1; --i) {
         const long long d = ((q + 64) & 127) - 64;
         dig[jj][i] = (int32_t)d;
@@ -278,7 +352,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_init(smem_u32(&ss->empty[s]), 1);
     }
     mbar_init(smem_u32(&ss->acc_full), 1);
-    mbar_init(smem_u32(&ss->acc_empty), 4);
+    mbar_init(smem_u32(&ss->acc_empty), OZ_EPI_WARPS);
     mbar_init(smem_u32(&ss->drain), 1);
     ss->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -359,8 +433,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_wait(smem_u32(&ss->drain), 0, &never);
     }
   } else {
-    // ---------------------------------------------------------------- epilogue (warps 2..5)
-    const int quad = warp & 3;  // TMEM lanes 32*quad .. 32*quad+31
+    // ---------------------------------------------------------------- epilogue (warps 2..9)
+    const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
+    const int half = (warp - 2) >> 2;          // which 64 of the 128 columns
     const int row = quad * 32 + lane;
     // accumulators of levels without any slice pair (fewer than 4 slices) are never written
     const bool has1 = pairs.first[1] >= 0, has2 = pairs.first[2] >= 0, has3 = pairs.first[3] >= 0;
@@ -369,23 +444,32 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const OzWork wk = work[w];
       const OzSector s = secs[wk.sector];
       const int64_t m = (int64_t)wk.mt * OZ_BM + row;
-      const int em = (m < s.M) ? scale_a[s.sa_off + m] : 0;
+      int em = (m < s.M) ? scale_a[s.sa_off + m] : 0;
+      if (em == kNoScale) em = 0;
+      // this warp's 64 column exponents, two per lane, broadcast later with shuffles
+      const int64_t nb = (int64_t)wk.nt * OZ_BN + half * 64;
+      int f0 = (nb + lane < s.N) ? scale_b[s.sb_off + nb + lane] : 0;
+      int f1 = (nb + 32 + lane < s.N) ? scale_b[s.sb_off + nb + 32 + lane] : 0;
+      if (f0 == kNoScale) f0 = 0;
+      if (f1 == kNoScale) f1 = 0;
       for (int kc0 = 0; kc0 < s.nkc; kc0 += OZ_SEG_KC, ++tile) {
         if (!mbar_wait(smem_u32(&ss->acc_full), tile & 1, abort_flag)) break;
         tc_fence_after();
-        const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16);
-        for (int ch = 0; ch < OZ_BN / 16; ++ch) {
+        const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + half * 64;
+#pragma unroll 1
+        for (int ch = 0; ch < 4; ++ch) {
           uint32_t r0[16], r1[16], r2[16], r3[16];
           tc_ld16(lane_addr + 0 * OZ_BN + ch * 16, r0);
           tc_ld16(lane_addr + 1 * OZ_BN + ch * 16, r1);
           tc_ld16(lane_addr + 2 * OZ_BN + ch * 16, r2);
           tc_ld16(lane_addr + 3 * OZ_BN + ch * 16, r3);
           tc_wait_ld();
-          if (m < s.M) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int64_t n = (int64_t)wk.nt * OZ_BN + ch * 16 + j;
-              if (n >= s.N) break;
+          for (int j = 0; j < 16; ++j) {
+            const int cj = ch * 16 + j;  // column within this warp's 64
+            const int fn = __shfl_sync(0xffffffffu, (cj < 32) ? f0 : f1, cj & 31);
+            const int64_t n = nb + cj;
+            if (m < s.M && n < s.N) {
               float hi, lo, e1, e2;
               const float a1 = has1 ? __uint_as_float(r1[j]) : 0.f;
               const float a2 = has2 ? __uint_as_float(r2[j]) : 0.f;
@@ -395,7 +479,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               lo = lo + e1;
               two_sum(hi, lo, hi, e2);
               lo = e2 + a3;
-              const double v = ((double)hi + (double)lo) * pow2(em + scale_b[s.sb_off + n]);
+              const double v = scale_pow2(f32_to_f64(hi) + f32_to_f64(lo), em + fn);
               double* dst = C + s.c_off + m + n * s.M;
               *dst = (kc0 == 0) ? v : *dst + v;
             }
@@ -484,8 +568,8 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
   std::vector<OzWork> work;
   std::vector<OzJob> slice_jobs, scale_jobs;
   std::vector<std::pair<double, OzWork>> wcost;
-  for (size_t g = 0; g < cp.gemms.size(); ++g) {
-    const GemmItem& it = cp.gemms[g];
+  for (size_t g = 0; g < cp.gemms_oz.size(); ++g) {
+    const GemmItem& it = cp.gemms_oz[g];
     OzSector s;
     std::memset(&s, 0, sizeof(s));
     s.M = it.M;
@@ -513,8 +597,10 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
       for (int kc = 0; kc < s.nkc; ++kc) slice_jobs.push_back(OzJob{sid, 0, rt, kc});
     for (int rt = 0; rt < s.nnt; ++rt)
       for (int kc = 0; kc < s.nkc; ++kc) slice_jobs.push_back(OzJob{sid, 1, rt, kc});
-    for (int64_t r0 = 0; r0 < s.M; r0 += 256) scale_jobs.push_back(OzJob{sid, 0, (int32_t)r0, 0});
-    for (int64_t r0 = 0; r0 < s.N; r0 += 256) scale_jobs.push_back(OzJob{sid, 1, (int32_t)r0, 0});
+    for (int kc = 0; kc * OZ_SCALE_KCHUNK < s.K; ++kc) {
+      for (int64_t r0 = 0; r0 < s.M; r0 += 256) scale_jobs.push_back(OzJob{sid, 0, (int32_t)r0, kc});
+      for (int64_t r0 = 0; r0 < s.N; r0 += 8) scale_jobs.push_back(OzJob{sid, 1, (int32_t)r0, kc});
+    }
   }
   std::stable_sort(wcost.begin(), wcost.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
   for (auto& w : wcost) work.push_back(w.second);
@@ -573,6 +659,7 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
     return TK_ERR_CUDA;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(sa, 0x80, L->off_sb - L->off_sa + (size_t)L->ncols_b * 4, s) != cudaSuccess) return TK_ERR_CUDA;
   {
     ProfScope prof(ctx, "k_oz_scale", stream);
     k_oz_scale<<<(unsigned)L->nscale_jobs, 256, 0, s>>>(L->d_sectors, L->d_scale_jobs, (const double*)a,

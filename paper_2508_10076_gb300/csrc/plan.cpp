@@ -264,11 +264,8 @@ static void build_transform(PermutePlan& pp, const std::vector<int>& p, const st
                    [](const TransformTerm& a, const TransformTerm& b) { return a.dst_pair < b.dst_pair; });
 }
 
-static int32_t pow2ceil(int64_t x) {
-  int32_t p = 1;
-  while (p < x && p < (1 << 30)) p <<= 1;
-  return p;
-}
+// Longest run handled by one warp visit; longer contiguous runs are split.
+constexpr int64_t kRunChunk = 1024;
 
 static void build_tasks(PermutePlan& pp) {
   const Structure& in = *pp.in;
@@ -278,8 +275,9 @@ static void build_tasks(PermutePlan& pp) {
   std::vector<int> inv(n);
   for (int k = 0; k < n; ++k) inv[pp.perm[k]] = k;
   pp.tasks.clear();
+  pp.rtasks.clear();
+  pp.runs.clear();
   pp.srcs.clear();
-  int64_t tiles = 0;
   double bytes = 0;
   const double esize = pp.dtype == TK_C128 ? 16.0 : 8.0;
   std::vector<int64_t> od, idims;
@@ -344,38 +342,46 @@ static void build_tasks(PermutePlan& pp) {
     int tdim = -1;
     for (int k = 1; k < t.ndim; ++k)
       if (t.irs[k] == 1 && t.ics[k] == 0) tdim = k;
+    bytes += esize * (double)total * (1.0 + (double)t.nsrc);
     if (t.ostr[0] == 1 && t.irs[0] == 1 && t.ics[0] == 0) {
+      // mode 0: contiguous runs along dim 0 on both sides -> one run per outer position
       t.mode = 0;
-      t.t0 = std::min<int32_t>(pow2ceil(t.ext[0]), 256);
-      t.t1 = 256 / t.t0;
-      int64_t outer = total / t.ext[0];
-      tiles += ((t.ext[0] + t.t0 - 1) / t.t0) * ((outer + t.t1 - 1) / t.t1);
-      t.tile_begin = tiles;  // fixed below
-    } else if (t.ostr[0] == 1 && tdim > 0 && t.ext[0] >= 4 && t.ext[tdim] >= 4) {
+      const int32_t task_id = (int32_t)pp.rtasks.size();
+      pp.rtasks.push_back(t);
+      const int64_t outer = total / t.ext[0];
+      for (int64_t o = 0; o < outer; ++o) {
+        int64_t rem = o, dst = t.out_off, ir = 0, ic = 0;
+        for (int k = 1; k < t.ndim; ++k) {
+          const int64_t x = rem % t.ext[k];
+          rem /= t.ext[k];
+          dst += x * t.ostr[k];
+          ir += x * t.irs[k];
+          ic += x * t.ics[k];
+        }
+        for (int64_t e0 = 0; e0 < t.ext[0]; e0 += kRunChunk) {
+          const int32_t len = (int32_t)std::min<int64_t>(kRunChunk, t.ext[0] - e0);
+          pp.runs.push_back(PermRun{dst + e0, ir + e0, ic, len, task_id});
+        }
+      }
+      continue;
+    }
+    if (t.ostr[0] == 1 && tdim > 0 && t.ext[0] >= 4 && t.ext[tdim] >= 4) {
       t.mode = 1;
       t.tdim = tdim;
       t.t0 = 32;
       t.t1 = 32;
-      int64_t outer = total / ((int64_t)t.ext[0] * t.ext[tdim]);
-      tiles += ((t.ext[0] + 31) / 32) * (int64_t)((t.ext[tdim] + 31) / 32) * outer;
     } else {
       t.mode = 2;
-      tiles += (total + 255) / 256;
     }
-    t.tile_begin = 0;
     pp.tasks.push_back(t);
-    bytes += esize * (double)total * (1.0 + (double)t.nsrc);
   }
-  // tile prefix
+  // tile prefix of the tile-kernel tasks
   int64_t acc = 0;
   for (auto& t : pp.tasks) {
     t.tile_begin = acc;
     int64_t total = 1;
     for (int k = 0; k < t.ndim; ++k) total *= t.ext[k];
-    if (t.mode == 0) {
-      int64_t outer = total / t.ext[0];
-      acc += ((t.ext[0] + t.t0 - 1) / t.t0) * ((outer + t.t1 - 1) / t.t1);
-    } else if (t.mode == 1) {
+    if (t.mode == 1) {
       int64_t outer = total / ((int64_t)t.ext[0] * t.ext[t.tdim]);
       acc += ((t.ext[0] + 31) / 32) * (int64_t)((t.ext[t.tdim] + 31) / 32) * outer;
     } else {
@@ -414,14 +420,21 @@ std::shared_ptr<PermutePlan> make_permute_plan(Ctx* ctx, std::shared_ptr<Structu
   for (int i = 0; i < n && pp->identity; ++i) pp->identity = all[i] == i;
   build_transform(*pp, p, q);
   build_tasks(*pp);
-  if (ctx && ctx->device >= 0 && !pp->tasks.empty()) {
+  if (ctx && ctx->device >= 0 && (!pp->tasks.empty() || !pp->runs.empty())) {
     std::vector<int64_t> starts;
     for (auto& t : pp->tasks) starts.push_back(t.tile_begin);
-    int rc = dev_upload(ctx, (void**)&pp->d_tasks, pp->tasks.data(), pp->tasks.size() * sizeof(PermTask));
+    int rc = TK_OK;
+    if (!pp->tasks.empty()) {
+      rc = dev_upload(ctx, (void**)&pp->d_tasks, pp->tasks.data(), pp->tasks.size() * sizeof(PermTask));
+      if (rc == TK_OK)
+        rc = dev_upload(ctx, (void**)&pp->d_tile_starts, starts.data(), starts.size() * sizeof(int64_t));
+    }
+    if (rc == TK_OK && !pp->rtasks.empty())
+      rc = dev_upload(ctx, (void**)&pp->d_rtasks, pp->rtasks.data(), pp->rtasks.size() * sizeof(PermTask));
+    if (rc == TK_OK && !pp->runs.empty())
+      rc = dev_upload(ctx, (void**)&pp->d_runs, pp->runs.data(), pp->runs.size() * sizeof(PermRun));
     if (rc == TK_OK && !pp->srcs.empty())
       rc = dev_upload(ctx, (void**)&pp->d_srcs, pp->srcs.data(), pp->srcs.size() * sizeof(PermSrc));
-    if (rc == TK_OK)
-      rc = dev_upload(ctx, (void**)&pp->d_tile_starts, starts.data(), starts.size() * sizeof(int64_t));
     if (rc != TK_OK) throw Error{rc, "uploading permute tables failed"};
   }
   if (ctx) {
@@ -432,6 +445,9 @@ std::shared_ptr<PermutePlan> make_permute_plan(Ctx* ctx, std::shared_ptr<Structu
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Smallest M, N and K of a sector product that runs on the split-precision tensor-core kernel.
+constexpr int64_t kSplitMinDim = 32;
 
 std::shared_ptr<ContractPlan> make_contract_plan(Ctx* ctx, std::shared_ptr<Structure> a,
                                                  const std::vector<int>& pa,
@@ -511,6 +527,17 @@ std::shared_ptr<ContractPlan> make_contract_plan(Ctx* ctx, std::shared_ptr<Struc
   if (cp->pc) {
     cp->ws_ct = off;
     off += align256(ct.numel * es);
+  }
+  // Engine per sector product.  Split precision pays off on the tensor cores only for products
+  // that fill a 128 x 128 x 64 tile reasonably; thin products (any of M, N, K below
+  // kSplitMinDim, e.g. the matrix-product-operator steps with K = N = 4) are memory-bound and
+  // stay on the FP64 kernel.
+  for (const GemmItem& g : cp->gemms) {
+    const bool thin = g.M < kSplitMinDim || g.N < kSplitMinDim || g.K < kSplitMinDim;
+    if (gemm_mode == TK_GEMM_FP64 || thin)
+      cp->gemms_fp64.push_back(g);
+    else
+      cp->gemms_oz.push_back(g);
   }
   cp->ws_slices = off;
   cp->ws_total = off;

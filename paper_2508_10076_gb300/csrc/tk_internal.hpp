@@ -114,19 +114,28 @@ struct PermSrc {
   int64_t ld;
   double coef;
 };
+// One contiguous run of a mode-0 task: dst[e] = sum_k coef_k src_k[ir + e + ic ld_k], e < len.
+struct PermRun {
+  int64_t dst, ir, ic;
+  int32_t len, task;
+};
 
 struct PermutePlan {
   std::shared_ptr<Structure> in, out;
   std::vector<int> perm;      // output leg k <- input leg perm[k]
   bool identity = false;
   std::vector<TransformTerm> terms;   // sorted by destination
-  std::vector<PermTask> tasks;
+  std::vector<PermTask> tasks;    // tile-kernel tasks (transposing / generic)
+  std::vector<PermTask> rtasks;   // run-kernel tasks (shared contiguous dim 0)
+  std::vector<PermRun> runs;
   std::vector<PermSrc> srcs;
   int64_t total_tiles = 0;
   double bytes = 0;           // algorithmic bytes for one launch (complex counts 16 B/element)
   int dtype = TK_F64;
   // device copies
   PermTask* d_tasks = nullptr;
+  PermTask* d_rtasks = nullptr;
+  PermRun* d_runs = nullptr;
   PermSrc* d_srcs = nullptr;
   int64_t* d_tile_starts = nullptr;
   ~PermutePlan();
@@ -145,7 +154,9 @@ struct ZeroItem {
 struct ContractPlan {
   std::shared_ptr<PermutePlan> pa, pb, pc;  // pc permutes C~ -> C (null if identity)
   std::shared_ptr<Structure> at, bt, ct, c;
-  std::vector<GemmItem> gemms;
+  std::vector<GemmItem> gemms;       // every sector GEMM with K > 0
+  std::vector<GemmItem> gemms_fp64;  // run by k_gemm_f64
+  std::vector<GemmItem> gemms_oz;    // run by the split-precision tcgen05 kernel
   std::vector<ZeroItem> zeros;
   int gemm_mode = TK_GEMM_FP64;
   int slices = 0;
@@ -229,5 +240,8 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp);
 int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
                       void* slices_ws, void* stream);
 int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp);
+// The launch sequence of one planned contraction with scratch at `ws` (Algorithm 4 / 8).
+int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
+                 void* stream);
 
 }  // namespace tk

@@ -206,3 +206,17 @@ def test_runs_are_bitwise_deterministic(gctx):
     gctx.sync()
     assert torch.equal(a, b)
     assert gctx.launches > 0
+
+
+@pytest.mark.parametrize("gemm", ["fp64", "ozaki"])
+def test_cuda_graph_replay_matches_eager(gctx, gemm):
+    """One heff application recorded as a CUDA graph replays to the same bits as eager launches."""
+    from paper_2508_10076_gb300.chain import HeffChain
+    ch = HeffChain(gctx, "U1", 512, gemm=gemm, seed=2)
+    eager = ch.run().clone()
+    graph, out, launches = ch.capture()
+    assert launches > 0
+    ch.dev["x"].mul_(1.0)  # same inputs
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, eager)
