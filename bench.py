@@ -94,14 +94,36 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _workload(ctx, name, gemm, dtype="f64"):
+def max_over_ranks(dist, x):
+    """The largest of every rank's x (x itself on a single process)."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(flops_per_step, steps, world, total_ms):
+    """Whole-job block-GFLOP/s: every rank runs `steps` steps of its own replica; the job takes as
+    long as its slowest rank."""
+    return flops_per_step * steps * world / (total_ms * 1e-3) / 1e9
+
+
+def replica_seed(rank):
+    """Each rank draws its own inputs: the replicas are independent problems of the same shape."""
+    return rank
+
+
+def _workload(ctx, name, gemm, dtype="f64", seed=0):
     from paper_2508_10076_gb300 import workloads as wl
     from paper_2508_10076_gb300.chain import HeffChain, LxContraction
     cfg = wl.CONFIGS[name]
     if cfg["kind"] == "heff":
-        return HeffChain(ctx, cfg["sym"], cfg["D"], gemm=gemm, dtype=dtype)
+        return HeffChain(ctx, cfg["sym"], cfg["D"], gemm=gemm, dtype=dtype, seed=seed)
     if cfg["kind"] == "lx":
-        return LxContraction(ctx, cfg["sym"], cfg["D"], gemm=gemm, dtype=dtype)
+        return LxContraction(ctx, cfg["sym"], cfg["D"], gemm=gemm, dtype=dtype, seed=seed)
     raise SystemExit(f"config {name} is a parity case, not a bench line")
 
 
@@ -213,7 +235,7 @@ def run_ours(args):
     from paper_2508_10076_gb300 import api, build_library
     build_library()
     ctx = api.Context(local)
-    work = _workload(ctx, args.config, args.gemm)
+    work = _workload(ctx, args.config, args.gemm, seed=replica_seed(rank))
     flops = work.flops
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -255,11 +277,8 @@ def run_ours(args):
     ctx.sync()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = flops * args.steps * world / (total_ms * 1e-3) / 1e9
+    total_ms = max_over_ranks(dist, total_ms)
+    value = job_throughput(flops, args.steps, world, total_ms)
     # ---------------- per-kernel event times: the same loop with libtk's launch profiler on
     ctx.profile(True)
     for i in range(args.steps):
@@ -288,17 +307,14 @@ def run_ours(args):
         e_end[i].record(stream)
     barrier()
     e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_start, e_end))
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = flops * args.steps * world / (e2e_ms * 1e-3) / 1e9
+    e2e_ms = max_over_ranks(dist, e2e_ms)
+    e2e_value = job_throughput(flops, args.steps, world, e2e_ms)
     ctx.sync()
     # ---------------- split-precision variant of the same workload (Ozaki BF16 on tcgen05)
     split = None
     if not args.no_split:
         ref_out = run().clone()
-        oz = _workload(ctx, args.config, "ozaki")
+        oz = _workload(ctx, args.config, "ozaki", seed=replica_seed(rank))
         for _ in range(max(3, args.warmup)):
             oz.run()
         oz_fn = oz.run
@@ -317,10 +333,7 @@ def run_ours(args):
             o_end[i].record(stream)
         barrier()
         oz_ms = sum(s.elapsed_time(e) for s, e in zip(o_start, o_end))
-        if dist is not None:
-            t = torch.tensor([oz_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            oz_ms = float(t.item())
+        oz_ms = max_over_ranks(dist, oz_ms)
         oz_out = oz.run()
         ctx.profile(True)
         for i in range(args.steps):
@@ -336,7 +349,7 @@ def run_ours(args):
             d = float(torch.linalg.norm(oz_out[o_:o_ + r_ * k_] - ref_out[o_:o_ + r_ * k_]))
             n_ = float(torch.linalg.norm(ref_out[o_:o_ + r_ * k_]))
             worst = max(worst, d / (n_ if n_ > 1e-13 * refn else refn))
-        split = {"value": flops * args.steps * world / (oz_ms * 1e-3) / 1e9, "unit": UNIT,
+        split = {"value": job_throughput(flops, args.steps, world, oz_ms), "unit": UNIT,
                  "ms_per_step": oz_ms / args.steps, "slices": 6,
                  "rel_frobenius_per_block_vs_fp64_path": worst,
                  "kernels": {k: {"launches": c, "ms_per_step": ms / args.steps} for k, (c, ms) in oz_prof.items()}}

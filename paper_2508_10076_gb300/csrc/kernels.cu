@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 
 #include "tk_internal.hpp"
 
@@ -53,6 +54,8 @@ PermutePlan::~PermutePlan() {
 ContractPlan::~ContractPlan() {
   dev_free(d_gemm_items);
   dev_free(d_gemm_tiles);
+  dev_free(d_gemm_rows);
+  dev_free(d_split_counters);
   dev_free(d_zero);
   for (void* p : d_oz) dev_free(p);
 }
@@ -217,11 +220,18 @@ __global__ void __launch_bounds__(256) k_permute_runs(const PermRun* __restrict_
 // thread; the skinny MPO products).  Tiles are sorted by cost (M_t N_t K) descending.
 struct GemmTile {
   int32_t item, m0, n0, cfg;
+  int32_t k0, k1;       // inner-dimension range of this tile
+  int32_t slot, part;   // split-K: output tile slot and this tile's part (slot < 0: no split)
+  int32_t nsplit, pad0, pad1, pad2;
 };
+constexpr int SPLIT_MAX = 8;
 
 enum { CFG_64 = 0, CFG_32 = 1, CFG_ROWS = 2, CFG_ROWS_DF = 3 };
 constexpr int BK = 16;
-constexpr int ROWS_PER_CTA = 256, ROWS_NMAX = 8, ROWS_KCHUNK = 256;
+constexpr int ROWS_PER_THREAD = 1, ROWS_PER_CTA = 256 * ROWS_PER_THREAD, ROWS_NMAX = 8, ROWS_KCHUNK = 256;
+
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
 template <typename T>
 struct Mac;
@@ -241,9 +251,11 @@ struct Mac<double2> {
 
 // One BMxBN tile with 256 threads in a 16x16 grid, TMxTN outputs per thread (BM = 16 TM).
 template <typename T, int BM, int BN, int TM, int TN>
-__device__ __forceinline__ void gemm_tile(const GemmItem& it, int64_t m0, int64_t n0,
+__device__ __forceinline__ void gemm_tile(const GemmItem& it, const GemmTile& tl,
                                           const T* __restrict__ A, const T* __restrict__ B,
-                                          T* __restrict__ C, T* smem) {
+                                          T* __restrict__ C, T* smem, T* __restrict__ partials,
+                                          int* __restrict__ counters) {
+  const int64_t m0 = tl.m0, n0 = tl.n0;
   T(*As)[BM + 1] = reinterpret_cast<T(*)[BM + 1]>(smem);
   T(*Bs)[BN + 1] = reinterpret_cast<T(*)[BN + 1]>(smem + BK * (BM + 1));
   const int64_t M = it.M, N = it.N, K = it.K;
@@ -255,8 +267,9 @@ __device__ __forceinline__ void gemm_tile(const GemmItem& it, int64_t m0, int64_
     for (int j = 0; j < TN; ++j) acc[i][j] = Elem<T>::zero();
   const T* Ab = A + it.a_off;
   const T* Bb = B + it.b_off;
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
-    const int kmax = (int)((K - k0) < BK ? (K - k0) : BK);
+  const int64_t kend = tl.k1;
+  for (int64_t k0 = tl.k0; k0 < kend; k0 += BK) {
+    const int kmax = (int)((kend - k0) < BK ? (kend - k0) : BK);
     for (int e = tid; e < BM * BK; e += 256) {
       const int mm = e % BM, kk = e / BM;
       const int64_t gm = m0 + mm, gk = k0 + kk;
@@ -283,6 +296,35 @@ __device__ __forceinline__ void gemm_tile(const GemmItem& it, int64_t m0, int64_
     __syncthreads();
   }
   T* Cb = C + it.c_off;
+  if (tl.slot >= 0) {
+    // split-K: publish this part; the CTA that completes the slot sums the parts in a fixed order
+    __shared__ int s_last;
+    T* mine = partials + ((int64_t)tl.slot * SPLIT_MAX + tl.part) * (BM * BN);
+#pragma unroll
+    for (int j = 0; j < TN; ++j)
+#pragma unroll
+      for (int i = 0; i < TM; ++i) mine[(tx + 16 * i) + (ty + 16 * j) * BM] = acc[i][j];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&counters[tl.slot], 1) == tl.nsplit - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const T* base = partials + (int64_t)tl.slot * SPLIT_MAX * (BM * BN);
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t gn = n0 + ty + 16 * j;
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        const int64_t gm = m0 + tx + 16 * i;
+        T v = Elem<T>::zero();
+        for (int p = 0; p < tl.nsplit; ++p) v = add(v, __ldcg(base + p * (BM * BN) + (tx + 16 * i) + (ty + 16 * j) * BM));
+        if (gm < M && gn < N) Cb[gm + gn * M] = v;
+      }
+    }
+    if (tid == 0) counters[tl.slot] = 0;  // ready for the next launch
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < TN; ++j) {
     const int64_t gn = n0 + ty + 16 * j;
@@ -302,34 +344,47 @@ __device__ __forceinline__ void gemm_rows(const GemmItem& it, int64_t m0, const 
   T(*Bs)[ROWS_NMAX] = reinterpret_cast<T(*)[ROWS_NMAX]>(smem);
   const int64_t M = it.M, N = it.N, K = it.K;
   const int tid = threadIdx.x;
-  const int64_t m = m0 + tid;
-  T acc[ROWS_NMAX];
+  T acc[ROWS_PER_THREAD][ROWS_NMAX];
 #pragma unroll
-  for (int j = 0; j < ROWS_NMAX; ++j) acc[j] = Elem<T>::zero();
+  for (int r = 0; r < ROWS_PER_THREAD; ++r)
+#pragma unroll
+    for (int j = 0; j < ROWS_NMAX; ++j) acc[r][j] = Elem<T>::zero();
   const T* Ab = A + it.a_off;
   const T* Bb = B + it.b_off;
   for (int64_t k0 = 0; k0 < K; k0 += ROWS_KCHUNK) {
     const int kmax = (int)((K - k0) < ROWS_KCHUNK ? (K - k0) : ROWS_KCHUNK);
-    for (int e = tid; e < ROWS_KCHUNK * ROWS_NMAX; e += 256) {
-      const int kk = e % ROWS_KCHUNK, nn = e / ROWS_KCHUNK;
-      Bs[kk][nn] = (kk < kmax && nn < N) ? Bb[(k0 + kk) + nn * K] : Elem<T>::zero();
+    for (int e = tid; e < kmax * ROWS_NMAX; e += 256) {
+      const int kk = e % kmax, nn = e / kmax;
+      Bs[kk][nn] = (nn < N) ? Bb[(k0 + kk) + nn * K] : Elem<T>::zero();
     }
     __syncthreads();
-    if (m < M) {
-      for (int kk = 0; kk < kmax; ++kk) {
-        const T a = Ab[m + (k0 + kk) * M];
+    for (int kk = 0; kk < kmax; ++kk) {
+      T a[ROWS_PER_THREAD];
 #pragma unroll
-        for (int j = 0; j < ROWS_NMAX; ++j)
-          if (j < N) Mac<T>::mac(acc[j], a, Bs[kk][j]);
+      for (int r = 0; r < ROWS_PER_THREAD; ++r) {
+        const int64_t m = m0 + tid + 256 * r;
+        a[r] = (m < M) ? Ab[m + (k0 + kk) * M] : Elem<T>::zero();
+      }
+#pragma unroll
+      for (int j = 0; j < ROWS_NMAX; ++j) {
+        if (j < N) {
+          const T b = Bs[kk][j];
+#pragma unroll
+          for (int r = 0; r < ROWS_PER_THREAD; ++r) Mac<T>::mac(acc[r][j], a[r], b);
+        }
       }
     }
     __syncthreads();
   }
-  if (m < M) {
-    T* Cb = C + it.c_off;
+  T* Cb = C + it.c_off;
 #pragma unroll
-    for (int j = 0; j < ROWS_NMAX; ++j)
-      if (j < N) Cb[m + j * M] = acc[j];
+  for (int r = 0; r < ROWS_PER_THREAD; ++r) {
+    const int64_t m = m0 + tid + 256 * r;
+    if (m < M) {
+#pragma unroll
+      for (int j = 0; j < ROWS_NMAX; ++j)
+        if (j < N) Cb[m + j * M] = acc[r][j];
+    }
   }
 }
 
@@ -377,38 +432,50 @@ __device__ __forceinline__ void gemm_rows_df(const GemmItem& it, int64_t m0, con
   float(*Bl)[ROWS_NMAX] = reinterpret_cast<float(*)[ROWS_NMAX]>(reinterpret_cast<float*>(smem) + ROWS_KCHUNK * ROWS_NMAX);
   const int64_t M = it.M, N = it.N, K = it.K;
   const int tid = threadIdx.x;
-  const int64_t m = m0 + tid;
-  float sh[ROWS_NMAX], sl[ROWS_NMAX];
+  float sh[ROWS_PER_THREAD][ROWS_NMAX], sl[ROWS_PER_THREAD][ROWS_NMAX];
 #pragma unroll
-  for (int j = 0; j < ROWS_NMAX; ++j) sh[j] = sl[j] = 0.f;
+  for (int r = 0; r < ROWS_PER_THREAD; ++r)
+#pragma unroll
+    for (int j = 0; j < ROWS_NMAX; ++j) sh[r][j] = sl[r][j] = 0.f;
   const double* Ab = A + it.a_off;
   const double* Bb = B + it.b_off;
   for (int64_t k0 = 0; k0 < K; k0 += ROWS_KCHUNK) {
     const int kmax = (int)((K - k0) < ROWS_KCHUNK ? (K - k0) : ROWS_KCHUNK);
-    for (int e = tid; e < ROWS_KCHUNK * ROWS_NMAX; e += 256) {
-      const int kk = e % ROWS_KCHUNK, nn = e / ROWS_KCHUNK;
+    for (int e = tid; e < kmax * ROWS_NMAX; e += 256) {
+      const int kk = e % kmax, nn = e / kmax;
       float h = 0.f, l = 0.f;
-      if (kk < kmax && nn < N) df_split(Bb[(k0 + kk) + nn * K], h, l);
+      if (nn < N) df_split(Bb[(k0 + kk) + nn * K], h, l);
       Bh[kk][nn] = h;
       Bl[kk][nn] = l;
     }
     __syncthreads();
-    if (m < M) {
-      for (int kk = 0; kk < kmax; ++kk) {
-        float ah, al;
-        df_split(Ab[m + (k0 + kk) * M], ah, al);
+    for (int kk = 0; kk < kmax; ++kk) {
+      float ah[ROWS_PER_THREAD], al[ROWS_PER_THREAD];
 #pragma unroll
-        for (int j = 0; j < ROWS_NMAX; ++j)
-          if (j < N) df_mac(sh[j], sl[j], ah, al, Bh[kk][j], Bl[kk][j]);
+      for (int r = 0; r < ROWS_PER_THREAD; ++r) {
+        const int64_t m = m0 + tid + 256 * r;
+        df_split((m < M) ? Ab[m + (k0 + kk) * M] : 0.0, ah[r], al[r]);
+      }
+#pragma unroll
+      for (int j = 0; j < ROWS_NMAX; ++j) {
+        if (j < N) {
+          const float bh = Bh[kk][j], bl = Bl[kk][j];
+#pragma unroll
+          for (int r = 0; r < ROWS_PER_THREAD; ++r) df_mac(sh[r][j], sl[r][j], ah[r], al[r], bh, bl);
+        }
       }
     }
     __syncthreads();
   }
-  if (m < M) {
-    double* Cb = C + it.c_off;
+  double* Cb = C + it.c_off;
 #pragma unroll
-    for (int j = 0; j < ROWS_NMAX; ++j)
-      if (j < N) Cb[m + j * M] = (double)sh[j] + (double)sl[j];
+  for (int r = 0; r < ROWS_PER_THREAD; ++r) {
+    const int64_t m = m0 + tid + 256 * r;
+    if (m < M) {
+#pragma unroll
+      for (int j = 0; j < ROWS_NMAX; ++j)
+        if (j < N) Cb[m + j * M] = (double)sh[r][j] + (double)sl[r][j];
+    }
   }
 }
 
@@ -427,19 +494,30 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_gemm_f64(const GemmItem* __restrict__ items,
                                                   const GemmTile* __restrict__ tiles,
                                                   const T* __restrict__ A,
-                                                  const T* __restrict__ B, T* __restrict__ C) {
-  constexpr int kSmem = (BK * 65 * 2 > ROWS_KCHUNK * ROWS_NMAX) ? BK * 65 * 2 : ROWS_KCHUNK * ROWS_NMAX;
-  __shared__ T smem[kSmem];
+                                                  const T* __restrict__ B, T* __restrict__ C,
+                                                  T* __restrict__ partials, int* __restrict__ counters) {
+  __shared__ T smem[BK * 65 * 2];
   const GemmTile tl = tiles[blockIdx.x];
   const GemmItem it = items[tl.item];
   if (tl.cfg == CFG_64)
-    gemm_tile<T, 64, 64, 4, 4>(it, tl.m0, tl.n0, A, B, C, smem);
-  else if (tl.cfg == CFG_32)
-    gemm_tile<T, 32, 32, 2, 2>(it, tl.m0, tl.n0, A, B, C, smem);
-  else if (tl.cfg == CFG_ROWS)
-    gemm_rows<T>(it, tl.m0, A, B, C, smem);
+    gemm_tile<T, 64, 64, 4, 4>(it, tl, A, B, C, smem, partials, counters);
   else
+    gemm_tile<T, 32, 32, 2, 2>(it, tl, A, B, C, smem, partials, counters);
+}
+
+// The N <= 8 products in a launch of their own (their register needs differ from the tiles').
+template <typename T, bool DF>
+__global__ void __launch_bounds__(256) k_gemm_rows(const GemmItem* __restrict__ items,
+                                                   const GemmTile* __restrict__ tiles,
+                                                   const T* __restrict__ A, const T* __restrict__ B,
+                                                   T* __restrict__ C) {
+  __shared__ T smem[ROWS_KCHUNK * ROWS_NMAX];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmItem it = items[tl.item];
+  if (DF)
     gemm_rows_df_dispatch<T>(it, tl.m0, A, B, C, smem);
+  else
+    gemm_rows<T>(it, tl.m0, A, B, C, smem);
 }
 
 template <typename T>
@@ -503,6 +581,10 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
   for (const GemmItem& g : gl)
     if (g.N > ROWS_NMAX) tiles64 += ((g.M + 63) / 64) * ((g.N + 63) / 64);
   const bool small_tiles = tiles64 < 3 * (int64_t)std::max(ctx->num_sms, 1);
+  int64_t tiles32 = 0;
+  for (const GemmItem& g : gl)
+    if (g.N > ROWS_NMAX) tiles32 += ((g.M + 31) / 32) * ((g.N + 31) / 32);
+  int32_t nslots = 0;
   struct Cand {
     GemmTile t;
     double cost;
@@ -511,47 +593,104 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
   for (size_t i = 0; i < gl.size(); ++i) {
     const GemmItem& g = gl[i];
     if (g.N <= ROWS_NMAX) {
-      for (int64_t m0 = 0; m0 < g.M; m0 += ROWS_PER_CTA)
-        cands.push_back({GemmTile{(int32_t)i, (int32_t)m0, 0,
-                                  cp.gemm_mode == TK_GEMM_FP64 ? CFG_ROWS : CFG_ROWS_DF},
-                         (double)std::min<int64_t>(ROWS_PER_CTA, g.M - m0) * g.N * g.K});
+      for (int64_t m0 = 0; m0 < g.M; m0 += ROWS_PER_CTA) {
+        GemmTile t;
+        std::memset(&t, 0, sizeof(t));
+        t.item = (int32_t)i;
+        t.m0 = (int32_t)m0;
+        t.cfg = cp.gemm_mode == TK_GEMM_FP64 ? CFG_ROWS : CFG_ROWS_DF;
+        t.k1 = (int32_t)g.K;
+        t.slot = -1;
+        t.nsplit = 1;
+        cands.push_back({t, (double)std::min<int64_t>(ROWS_PER_CTA, g.M - m0) * g.N * g.K});
+      }
       continue;
     }
     const int bm = small_tiles ? 32 : 64, bn = bm;
+    // split-K (32x32 tiles only): enough parts to give ~6 CTAs per SM, each part >= 64 deep
+    int nsplit = 1;
+    if (small_tiles) {
+      const int64_t want = (6 * (int64_t)std::max(ctx->num_sms, 1) + tiles32 - 1) / std::max<int64_t>(tiles32, 1);
+      nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)SPLIT_MAX, g.K / 64}));
+    }
     for (int64_t n0 = 0; n0 < g.N; n0 += bn)
-      for (int64_t m0 = 0; m0 < g.M; m0 += bm)
-        cands.push_back({GemmTile{(int32_t)i, (int32_t)m0, (int32_t)n0, small_tiles ? CFG_32 : CFG_64},
-                         (double)bm * bn * g.K});
+      for (int64_t m0 = 0; m0 < g.M; m0 += bm) {
+        const int32_t slot = nsplit > 1 ? nslots++ : -1;
+        const int64_t kstep = ((g.K + nsplit - 1) / nsplit + BK - 1) / BK * BK;
+        for (int p = 0; p < nsplit; ++p) {
+          const int64_t k0 = p * kstep, k1 = std::min<int64_t>(g.K, k0 + kstep);
+          GemmTile t;
+          std::memset(&t, 0, sizeof(t));
+          t.item = (int32_t)i;
+          t.m0 = (int32_t)m0;
+          t.n0 = (int32_t)n0;
+          t.cfg = small_tiles ? CFG_32 : CFG_64;
+          t.k0 = (int32_t)k0;
+          t.k1 = (int32_t)std::max<int64_t>(k0, k1);
+          t.slot = slot;
+          t.part = p;
+          t.nsplit = nsplit;
+          cands.push_back({t, (double)bm * bn * (double)(t.k1 - t.k0)});
+        }
+      }
   }
+  cp.split_slots = nslots;
   std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.cost > b.cost; });
-  std::vector<GemmTile> tiles;
-  for (auto& c : cands) tiles.push_back(c.t);
+  std::vector<GemmTile> tiles, rows;
+  for (auto& c : cands) (c.t.cfg >= CFG_ROWS ? rows : tiles).push_back(c.t);
   cp.n_gemm_tiles = (int64_t)tiles.size();
+  cp.n_gemm_rows = (int64_t)rows.size();
   int rc = dev_upload(ctx, &cp.d_gemm_items, gl.data(), gl.size() * sizeof(GemmItem));
   if (rc != TK_OK) return rc;
   rc = dev_upload(ctx, &cp.d_gemm_tiles, tiles.data(), tiles.size() * sizeof(GemmTile));
+  if (rc != TK_OK) return rc;
+  rc = dev_upload(ctx, &cp.d_gemm_rows, rows.data(), rows.size() * sizeof(GemmTile));
   if (rc != TK_OK) return rc;
   if (!cp.zeros.empty()) {
     rc = dev_upload(ctx, &cp.d_zero, cp.zeros.data(), cp.zeros.size() * sizeof(ZeroItem));
     if (rc != TK_OK) return rc;
   }
+  if (nslots > 0) {
+    std::vector<int> zeros((size_t)nslots, 0);
+    rc = dev_upload(ctx, &cp.d_split_counters, zeros.data(), zeros.size() * sizeof(int));
+    if (rc != TK_OK) return rc;
+    cp.partials_bytes = (size_t)nslots * SPLIT_MAX * 32 * 32 * (cp.dtype == TK_C128 ? 16 : 8);
+  }
   return TK_OK;
 }
 
 int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
-                     void* stream) {
-  if (cp.n_gemm_tiles == 0) return TK_OK;
+                     void* partials, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  ProfScope prof(ctx, "k_gemm_f64", stream);
   const GemmItem* items = (const GemmItem*)cp.d_gemm_items;
-  const GemmTile* tiles = (const GemmTile*)cp.d_gemm_tiles;
-  if (cp.dtype == TK_C128)
-    k_gemm_f64<double2><<<(unsigned)cp.n_gemm_tiles, 256, 0, s>>>(items, tiles, (const double2*)a,
-                                                                  (const double2*)b, (double2*)c);
-  else
-    k_gemm_f64<double><<<(unsigned)cp.n_gemm_tiles, 256, 0, s>>>(items, tiles, (const double*)a,
-                                                                 (const double*)b, (double*)c);
-  return check_launch(ctx, "k_gemm_f64");
+  if (cp.n_gemm_tiles > 0) {
+    ProfScope prof(ctx, "k_gemm_f64", stream);
+    const GemmTile* tiles = (const GemmTile*)cp.d_gemm_tiles;
+    int* counters = (int*)cp.d_split_counters;
+    if (cp.dtype == TK_C128)
+      k_gemm_f64<double2><<<(unsigned)cp.n_gemm_tiles, 256, 0, s>>>(items, tiles, (const double2*)a, (const double2*)b,
+                                                                    (double2*)c, (double2*)partials, counters);
+    else
+      k_gemm_f64<double><<<(unsigned)cp.n_gemm_tiles, 256, 0, s>>>(items, tiles, (const double*)a, (const double*)b,
+                                                                   (double*)c, (double*)partials, counters);
+    int rc = check_launch(ctx, "k_gemm_f64");
+    if (rc != TK_OK) return rc;
+  }
+  if (cp.n_gemm_rows > 0) {
+    ProfScope prof(ctx, "k_gemm_rows", stream);
+    const GemmTile* rows = (const GemmTile*)cp.d_gemm_rows;
+    if (cp.dtype == TK_C128)
+      k_gemm_rows<double2, false><<<(unsigned)cp.n_gemm_rows, 256, 0, s>>>(items, rows, (const double2*)a,
+                                                                           (const double2*)b, (double2*)c);
+    else if (cp.gemm_mode == TK_GEMM_FP64)
+      k_gemm_rows<double, false><<<(unsigned)cp.n_gemm_rows, 256, 0, s>>>(items, rows, (const double*)a,
+                                                                          (const double*)b, (double*)c);
+    else
+      k_gemm_rows<double, true><<<(unsigned)cp.n_gemm_rows, 256, 0, s>>>(items, rows, (const double*)a,
+                                                                         (const double*)b, (double*)c);
+    return check_launch(ctx, "k_gemm_rows");
+  }
+  return TK_OK;
 }
 
 int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream) {
@@ -578,7 +717,8 @@ int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b,
   if (!cp.pa->identity && (rc = launch_permute(ctx, *cp.pa, a, (void*)at, stream)) != TK_OK) return rc;
   if (!cp.pb->identity && (rc = launch_permute(ctx, *cp.pb, b, (void*)bt, stream)) != TK_OK) return rc;
   if ((rc = launch_zero(ctx, cp, ct, stream)) != TK_OK) return rc;
-  if (!cp.gemms_fp64.empty() && (rc = launch_gemm_fp64(ctx, cp, at, bt, ct, stream)) != TK_OK) return rc;
+  if (!cp.gemms_fp64.empty() && (rc = launch_gemm_fp64(ctx, cp, at, bt, ct, w + cp.ws_partials, stream)) != TK_OK)
+    return rc;
   if (!cp.gemms_oz.empty() && (rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream)) != TK_OK)
     return rc;
   if (cp.pc && (rc = launch_permute(ctx, *cp.pc, ct, c, stream)) != TK_OK) return rc;

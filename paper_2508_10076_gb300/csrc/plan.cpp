@@ -264,8 +264,10 @@ static void build_transform(PermutePlan& pp, const std::vector<int>& p, const st
                    [](const TransformTerm& a, const TransformTerm& b) { return a.dst_pair < b.dst_pair; });
 }
 
-// Longest run handled by one warp visit; longer contiguous runs are split.
+// Longest run handled by one warp visit; longer contiguous runs are split.  Runs shorter than
+// kMinRun would leave most of a warp idle: such tasks take the element-wise tile path instead.
 constexpr int64_t kRunChunk = 1024;
+constexpr int32_t kMinRun = 8;
 
 static void build_tasks(PermutePlan& pp) {
   const Structure& in = *pp.in;
@@ -343,7 +345,7 @@ static void build_tasks(PermutePlan& pp) {
     for (int k = 1; k < t.ndim; ++k)
       if (t.irs[k] == 1 && t.ics[k] == 0) tdim = k;
     bytes += esize * (double)total * (1.0 + (double)t.nsrc);
-    if (t.ostr[0] == 1 && t.irs[0] == 1 && t.ics[0] == 0) {
+    if (t.ostr[0] == 1 && t.irs[0] == 1 && t.ics[0] == 0 && t.ext[0] >= kMinRun) {
       // mode 0: contiguous runs along dim 0 on both sides -> one run per outer position
       t.mode = 0;
       const int32_t task_id = (int32_t)pp.rtasks.size();
@@ -544,6 +546,10 @@ std::shared_ptr<ContractPlan> make_contract_plan(Ctx* ctx, std::shared_ptr<Struc
   if (ctx && ctx->device >= 0) {
     int rc = upload_gemm_tables(ctx, *cp);
     if (rc != TK_OK) throw Error{rc, "uploading GEMM tables failed"};
+    cp->ws_partials = off;
+    off += align256(cp->partials_bytes);
+    cp->ws_slices = off;
+    cp->ws_total = off;
     if (gemm_mode != TK_GEMM_FP64) {
       rc = upload_ozaki_tables(ctx, *cp);
       if (rc != TK_OK) throw Error{rc, "preparing split-precision GEMM tables failed"};

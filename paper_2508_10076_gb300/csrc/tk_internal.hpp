@@ -163,11 +163,17 @@ struct ContractPlan {
   int dtype = TK_F64;
   double flops = 0;
   // workspace layout (bytes)
-  size_t ws_at = 0, ws_bt = 0, ws_ct = 0, ws_slices = 0, ws_total = 0;
+  size_t ws_at = 0, ws_bt = 0, ws_ct = 0, ws_partials = 0, ws_slices = 0, ws_total = 0;
   // device tables
   void* d_gemm_items = nullptr;
   void* d_gemm_tiles = nullptr;
-  int64_t n_gemm_tiles = 0;
+  void* d_gemm_rows = nullptr;
+  int64_t n_gemm_tiles = 0, n_gemm_rows = 0;
+  // split-K of the FP64 tiles: per-slot arrival counters (plan-owned, self-resetting; launches of
+  // one plan must not overlap) and the partial tiles in the workspace
+  void* d_split_counters = nullptr;
+  int32_t split_slots = 0;
+  size_t partials_bytes = 0;
   void* d_zero = nullptr;
   // split-precision tables (owned; freed by the destructor) and the host-side layout
   std::vector<void*> d_oz;
@@ -234,7 +240,7 @@ int dev_upload(Ctx* ctx, void** dst, const void* src, size_t bytes);
 void dev_free(void* p);
 int launch_permute(Ctx* ctx, const PermutePlan& pp, const void* in, void* out, void* stream);
 int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
-                     void* stream);
+                     void* partials, void* stream);
 int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream);
 int upload_gemm_tables(Ctx* ctx, ContractPlan& cp);
 int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,

@@ -220,3 +220,25 @@ def test_cuda_graph_replay_matches_eager(gctx, gemm):
     graph.replay()
     torch.cuda.synchronize()
     assert torch.equal(out, eager)
+
+
+def test_split_k_few_tiles_long_inner_dimension(gctx):
+    """A handful of output tiles over K = 2000: the inner dimension is cut into parts summed in a
+    fixed order by the last CTA to finish; the result matches the oracle and repeats bit for bit."""
+    api = _api()
+    la = ([({0: 64, 1: 40}, False)], [({0: 2000, 1: 700}, False)])
+    lb = ([({0: 2000, 1: 700}, False)], [({0: 50, 1: 33}, False)])
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    xa, xb = wl.normal(11, oa.numel), wl.normal(12, ob.numel)
+    cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
+    A, B = _lib_tmap(gctx, "U1", la), _lib_tmap(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,))
+    ws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
+    outs = []
+    for _ in range(3):
+        c = torch.full((plan.output().numel,), float("nan"), dtype=torch.float64, device="cuda")
+        api.contract(gctx, plan, _dev(xa), _dev(xb), c, ws)
+        outs.append(c)
+    gctx.sync()
+    assert rel_frobenius_per_block(cs, outs[0].cpu().numpy(), ref) <= FP64_TOL
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
