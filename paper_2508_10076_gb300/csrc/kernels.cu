@@ -54,7 +54,6 @@ PermutePlan::~PermutePlan() {
 ContractPlan::~ContractPlan() {
   dev_free(d_gemm_items);
   dev_free(d_gemm_tiles);
-  dev_free(d_gemm_rows);
   dev_free(d_split_counters);
   dev_free(d_zero);
   for (void* p : d_oz) dev_free(p);
@@ -100,17 +99,36 @@ __device__ __forceinline__ T gather(const PermSrc* __restrict__ srcs, int nsrc, 
 constexpr int kTaskWords = (int)(sizeof(PermTask) / sizeof(int64_t));
 static_assert(sizeof(PermTask) % sizeof(int64_t) == 0, "PermTask must be 8-byte multiple");
 
+// One launch serves up to four segments (the run list and the tile list of up to two permutes,
+// e.g. both operands of a contraction); each segment owns a contiguous range of blocks.
+struct PermSeg {
+  int32_t kind;    // 0: contiguous runs, 1: tiles
+  int32_t ntasks;  // tiles: number of tasks (binary search range)
+  int64_t block0, nblocks, nwork;  // blocks [block0, block0 + nblocks); runs or tiles to do
+  const PermRun* runs;
+  const PermTask* tasks;  // run tasks (kind 0) or tile tasks (kind 1)
+  const int64_t* tile_starts;
+  const PermSrc* srcs;
+  const void* in;
+  void* out;
+};
+constexpr int kMaxPermSegs = 4;
+struct PermLaunch {
+  PermSeg seg[kMaxPermSegs];
+  int32_t nseg;
+};
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ tasks, int ntasks,
-                                                 const int64_t* __restrict__ tile_starts,
-                                                 const PermSrc* __restrict__ srcs,
-                                                 int64_t total_tiles, const T* __restrict__ in,
-                                                 T* __restrict__ out) {
-  __shared__ T tile[32][33];
-  __shared__ int64_t task_words[kTaskWords];
+__device__ __forceinline__ void permute_tiles(const PermSeg& g, int64_t bid, T (*tile)[33], int64_t* task_words) {
   const PermTask& t = *reinterpret_cast<const PermTask*>(task_words);
+  const PermTask* __restrict__ tasks = g.tasks;
+  const int64_t* __restrict__ tile_starts = g.tile_starts;
+  const PermSrc* __restrict__ srcs = g.srcs;
+  const T* __restrict__ in = (const T*)g.in;
+  T* __restrict__ out = (T*)g.out;
+  const int ntasks = g.ntasks;
   const int tid = threadIdx.x;
-  for (int64_t tidx = blockIdx.x; tidx < total_tiles; tidx += gridDim.x) {
+  for (int64_t tidx = bid; tidx < g.nwork; tidx += g.nblocks) {
     // locate the task owning this tile
     int lo = 0, hi = ntasks - 1;
     while (lo < hi) {
@@ -183,13 +201,15 @@ __global__ void __launch_bounds__(256) k_permute(const PermTask* __restrict__ ta
 // along the run, four elements per lane in flight.  Abelian runs (one source, weight 1) are plain
 // copies; SU(2) runs sum their weighted sources in FP64.
 template <typename T>
-__global__ void __launch_bounds__(256) k_permute_runs(const PermRun* __restrict__ runs, int64_t nruns,
-                                                      const PermTask* __restrict__ tasks,
-                                                      const PermSrc* __restrict__ srcs,
-                                                      const T* __restrict__ in, T* __restrict__ out) {
+__device__ __forceinline__ void permute_runs(const PermSeg& g, int64_t bid) {
+  const PermRun* __restrict__ runs = g.runs;
+  const PermTask* __restrict__ tasks = g.tasks;
+  const PermSrc* __restrict__ srcs = g.srcs;
+  const T* __restrict__ in = (const T*)g.in;
+  T* __restrict__ out = (T*)g.out;
   const int lane = threadIdx.x & 31;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nruns; r += nwarps) {
+  const int64_t nwarps = (g.nblocks * blockDim.x) >> 5;
+  for (int64_t r = (bid * blockDim.x + threadIdx.x) >> 5; r < g.nwork; r += nwarps) {
     const PermRun run = runs[r];
     const int nsrc = __ldg(&tasks[run.task].nsrc);
     const int sb = __ldg(&tasks[run.task].src_begin);
@@ -213,6 +233,22 @@ __global__ void __launch_bounds__(256) k_permute_runs(const PermRun* __restrict_
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermLaunch L) {
+  __shared__ T tile[32][33];
+  __shared__ int64_t task_words[kTaskWords];
+  int s = 0;
+#pragma unroll
+  for (int i = 1; i < kMaxPermSegs; ++i)
+    if (i < L.nseg && (int64_t)blockIdx.x >= L.seg[i].block0) s = i;
+  const PermSeg& g = L.seg[s];
+  const int64_t bid = (int64_t)blockIdx.x - g.block0;
+  if (g.kind == 0)
+    permute_runs<T>(g, bid);
+  else
+    permute_tiles<T>(g, bid, tile, task_words);
+}
+
 // ------------------------------------------------------------------ K2 grouped FP64 GEMM
 // Work list of output tiles over all sector GEMMs of one contraction, each tile tagged with one
 // of three shapes chosen on the host: 64x64 (4x4 per thread), 32x32 (2x2 per thread) when the
@@ -222,7 +258,8 @@ struct GemmTile {
   int32_t item, m0, n0, cfg;
   int32_t k0, k1;       // inner-dimension range of this tile
   int32_t slot, part;   // split-K: output tile slot and this tile's part (slot < 0: no split)
-  int32_t nsplit, pad0, pad1, pad2;
+  int32_t nsplit, pad0;
+  int64_t poff;         // split-K: first element of this slot's partials (nsplit parts of one tile)
 };
 constexpr int SPLIT_MAX = 8;
 
@@ -299,7 +336,7 @@ __device__ __forceinline__ void gemm_tile(const GemmItem& it, const GemmTile& tl
   if (tl.slot >= 0) {
     // split-K: publish this part; the CTA that completes the slot sums the parts in a fixed order
     __shared__ int s_last;
-    T* mine = partials + ((int64_t)tl.slot * SPLIT_MAX + tl.part) * (BM * BN);
+    T* mine = partials + tl.poff + (int64_t)tl.part * (BM * BN);
 #pragma unroll
     for (int j = 0; j < TN; ++j)
 #pragma unroll
@@ -310,7 +347,7 @@ __device__ __forceinline__ void gemm_tile(const GemmItem& it, const GemmTile& tl
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const T* base = partials + (int64_t)tl.slot * SPLIT_MAX * (BM * BN);
+    const T* base = partials + tl.poff;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int64_t gn = n0 + ty + 16 * j;
@@ -337,54 +374,113 @@ __device__ __forceinline__ void gemm_tile(const GemmItem& it, const GemmTile& tl
   }
 }
 
-// N <= 8: thread t owns row m0 + t, B streamed through shared memory in K chunks.
+// Split-K epilogue shared by the row kernels: publish this part's 256 x N partial sums; the CTA
+// that completes the slot adds the parts in part order (deterministic) and writes C.
 template <typename T>
-__device__ __forceinline__ void gemm_rows(const GemmItem& it, int64_t m0, const T* __restrict__ A,
-                                          const T* __restrict__ B, T* __restrict__ C, T* smem) {
-  T(*Bs)[ROWS_NMAX] = reinterpret_cast<T(*)[ROWS_NMAX]>(smem);
-  const int64_t M = it.M, N = it.N, K = it.K;
+__device__ __forceinline__ void rows_store(const GemmItem& it, const GemmTile& tl, const T* acc,
+                                           T* __restrict__ C, T* __restrict__ partials,
+                                           int* __restrict__ counters) {
+  const int64_t M = it.M, N = it.N;
   const int tid = threadIdx.x;
-  T acc[ROWS_PER_THREAD][ROWS_NMAX];
-#pragma unroll
-  for (int r = 0; r < ROWS_PER_THREAD; ++r)
-#pragma unroll
-    for (int j = 0; j < ROWS_NMAX; ++j) acc[r][j] = Elem<T>::zero();
-  const T* Ab = A + it.a_off;
-  const T* Bb = B + it.b_off;
-  for (int64_t k0 = 0; k0 < K; k0 += ROWS_KCHUNK) {
-    const int kmax = (int)((K - k0) < ROWS_KCHUNK ? (K - k0) : ROWS_KCHUNK);
-    for (int e = tid; e < kmax * ROWS_NMAX; e += 256) {
-      const int kk = e % kmax, nn = e / kmax;
-      Bs[kk][nn] = (nn < N) ? Bb[(k0 + kk) + nn * K] : Elem<T>::zero();
-    }
-    __syncthreads();
-    for (int kk = 0; kk < kmax; ++kk) {
-      T a[ROWS_PER_THREAD];
-#pragma unroll
-      for (int r = 0; r < ROWS_PER_THREAD; ++r) {
-        const int64_t m = m0 + tid + 256 * r;
-        a[r] = (m < M) ? Ab[m + (k0 + kk) * M] : Elem<T>::zero();
-      }
-#pragma unroll
-      for (int j = 0; j < ROWS_NMAX; ++j) {
-        if (j < N) {
-          const T b = Bs[kk][j];
-#pragma unroll
-          for (int r = 0; r < ROWS_PER_THREAD; ++r) Mac<T>::mac(acc[r][j], a[r], b);
-        }
-      }
-    }
-    __syncthreads();
-  }
+  const int64_t m = tl.m0 + tid;
   T* Cb = C + it.c_off;
-#pragma unroll
-  for (int r = 0; r < ROWS_PER_THREAD; ++r) {
-    const int64_t m = m0 + tid + 256 * r;
+  if (tl.slot < 0) {
     if (m < M) {
 #pragma unroll
       for (int j = 0; j < ROWS_NMAX; ++j)
-        if (j < N) Cb[m + j * M] = acc[r][j];
+        if (j < N) Cb[m + j * M] = acc[j];
     }
+    return;
+  }
+  __shared__ int s_last;
+  T* mine = partials + tl.poff + (int64_t)tl.part * (256 * ROWS_NMAX);
+#pragma unroll
+  for (int j = 0; j < ROWS_NMAX; ++j) mine[tid + 256 * j] = acc[j];
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(&counters[tl.slot], 1) == tl.nsplit - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const T* base = partials + tl.poff;
+  if (m < M) {
+#pragma unroll
+    for (int j = 0; j < ROWS_NMAX; ++j) {
+      if (j < N) {
+        T v = Elem<T>::zero();
+        for (int p = 0; p < tl.nsplit; ++p) v = add(v, __ldcg(base + p * (256 * ROWS_NMAX) + tid + 256 * j));
+        Cb[m + j * M] = v;
+      }
+    }
+  }
+  if (tid == 0) counters[tl.slot] = 0;  // ready for the next launch
+}
+
+// N <= 8: thread t owns row m0 + t over the inner range [k0, k1); B streamed through shared
+// memory in K chunks.  The code is instantiated for each N (NT) and walks K in groups of four
+// (four independent loads in flight) plus a guarded tail, so every FP64 FMA issued is one of the
+// product's M K N: on GB300 the FP64 pipe, not memory, bounds these skinny products.
+template <typename T, int NT>
+__device__ __forceinline__ void gemm_rows_n(const GemmItem& it, const GemmTile& tl, const T* __restrict__ A,
+                                            const T* __restrict__ B, T* __restrict__ C, T* smem,
+                                            T* __restrict__ partials, int* __restrict__ counters) {
+  T(*Bs)[NT] = reinterpret_cast<T(*)[NT]>(smem);
+  const int64_t M = it.M, K = it.K;
+  const int tid = threadIdx.x;
+  const int64_t m = tl.m0 + tid;
+  const bool live = m < M;
+  T acc[ROWS_NMAX];
+#pragma unroll
+  for (int j = 0; j < ROWS_NMAX; ++j) acc[j] = Elem<T>::zero();
+  const T* Ab = A + it.a_off + (live ? m : 0);
+  const T* Bb = B + it.b_off;
+  for (int64_t k0 = tl.k0; k0 < tl.k1; k0 += ROWS_KCHUNK) {
+    const int kmax = (int)((tl.k1 - k0) < ROWS_KCHUNK ? (tl.k1 - k0) : ROWS_KCHUNK);
+    for (int e = tid; e < kmax * NT; e += 256) {
+      const int kk = e % kmax, nn = e / kmax;
+      Bs[kk][nn] = Bb[(k0 + kk) + nn * K];
+    }
+    __syncthreads();
+    const T* Ak = Ab + k0 * M;
+    int kk = 0;
+    for (; kk + 4 <= kmax; kk += 4) {
+      T a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = live ? Ak[(int64_t)(kk + u) * M] : Elem<T>::zero();
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) Mac<T>::mac(acc[j], a[u], Bs[kk + u][j]);
+    }
+    if (kk < kmax) {  // 1..3 left; the branches are uniform over the block
+      T a[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) a[u] = (live && kk + u < kmax) ? Ak[(int64_t)(kk + u) * M] : Elem<T>::zero();
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        if (kk + u < kmax) {
+#pragma unroll
+          for (int j = 0; j < NT; ++j) Mac<T>::mac(acc[j], a[u], Bs[kk + u][j]);
+        }
+    }
+    __syncthreads();
+  }
+  rows_store<T>(it, tl, acc, C, partials, counters);
+}
+
+template <typename T>
+__device__ __forceinline__ void gemm_rows(const GemmItem& it, const GemmTile& tl, const T* __restrict__ A,
+                                          const T* __restrict__ B, T* __restrict__ C, T* smem,
+                                          T* __restrict__ partials, int* __restrict__ counters) {
+  switch (it.N) {
+    case 1: gemm_rows_n<T, 1>(it, tl, A, B, C, smem, partials, counters); break;
+    case 2: gemm_rows_n<T, 2>(it, tl, A, B, C, smem, partials, counters); break;
+    case 3: gemm_rows_n<T, 3>(it, tl, A, B, C, smem, partials, counters); break;
+    case 4: gemm_rows_n<T, 4>(it, tl, A, B, C, smem, partials, counters); break;
+    case 5: gemm_rows_n<T, 5>(it, tl, A, B, C, smem, partials, counters); break;
+    case 6: gemm_rows_n<T, 6>(it, tl, A, B, C, smem, partials, counters); break;
+    case 7: gemm_rows_n<T, 7>(it, tl, A, B, C, smem, partials, counters); break;
+    default: gemm_rows_n<T, 8>(it, tl, A, B, C, smem, partials, counters); break;
   }
 }
 
@@ -425,99 +521,107 @@ __device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al,
   sl = __fadd_rn(sl, __fadd_rn(e, cross));
   sh = s;
 }
-__device__ __forceinline__ void gemm_rows_df(const GemmItem& it, int64_t m0, const double* __restrict__ A,
-                                             const double* __restrict__ B, double* __restrict__ C,
-                                             double* smem) {
-  float(*Bh)[ROWS_NMAX] = reinterpret_cast<float(*)[ROWS_NMAX]>(smem);
-  float(*Bl)[ROWS_NMAX] = reinterpret_cast<float(*)[ROWS_NMAX]>(reinterpret_cast<float*>(smem) + ROWS_KCHUNK * ROWS_NMAX);
-  const int64_t M = it.M, N = it.N, K = it.K;
+template <int NT>
+__device__ __forceinline__ void gemm_rows_df_n(const GemmItem& it, const GemmTile& tl, const double* __restrict__ A,
+                                               const double* __restrict__ B, double* __restrict__ C,
+                                               double* smem, double* __restrict__ partials,
+                                               int* __restrict__ counters) {
+  float(*Bh)[NT] = reinterpret_cast<float(*)[NT]>(smem);
+  float(*Bl)[NT] = reinterpret_cast<float(*)[NT]>(reinterpret_cast<float*>(smem) + ROWS_KCHUNK * NT);
+  const int64_t M = it.M, K = it.K;
   const int tid = threadIdx.x;
-  float sh[ROWS_PER_THREAD][ROWS_NMAX], sl[ROWS_PER_THREAD][ROWS_NMAX];
+  const int64_t m = tl.m0 + tid;
+  const bool live = m < M;
+  float sh[NT], sl[NT];
 #pragma unroll
-  for (int r = 0; r < ROWS_PER_THREAD; ++r)
-#pragma unroll
-    for (int j = 0; j < ROWS_NMAX; ++j) sh[r][j] = sl[r][j] = 0.f;
-  const double* Ab = A + it.a_off;
+  for (int j = 0; j < NT; ++j) sh[j] = sl[j] = 0.f;
+  const double* Ab = A + it.a_off + (live ? m : 0);
   const double* Bb = B + it.b_off;
-  for (int64_t k0 = 0; k0 < K; k0 += ROWS_KCHUNK) {
-    const int kmax = (int)((K - k0) < ROWS_KCHUNK ? (K - k0) : ROWS_KCHUNK);
-    for (int e = tid; e < kmax * ROWS_NMAX; e += 256) {
+  for (int64_t k0 = tl.k0; k0 < tl.k1; k0 += ROWS_KCHUNK) {
+    const int kmax = (int)((tl.k1 - k0) < ROWS_KCHUNK ? (tl.k1 - k0) : ROWS_KCHUNK);
+    for (int e = tid; e < kmax * NT; e += 256) {
       const int kk = e % kmax, nn = e / kmax;
-      float h = 0.f, l = 0.f;
-      if (nn < N) df_split(Bb[(k0 + kk) + nn * K], h, l);
+      float h, l;
+      df_split(Bb[(k0 + kk) + nn * K], h, l);
       Bh[kk][nn] = h;
       Bl[kk][nn] = l;
     }
     __syncthreads();
-    for (int kk = 0; kk < kmax; ++kk) {
-      float ah[ROWS_PER_THREAD], al[ROWS_PER_THREAD];
+    const double* Ak = Ab + k0 * M;
+    int kk = 0;
+    for (; kk + 4 <= kmax; kk += 4) {
+      double a[4];
 #pragma unroll
-      for (int r = 0; r < ROWS_PER_THREAD; ++r) {
-        const int64_t m = m0 + tid + 256 * r;
-        df_split((m < M) ? Ab[m + (k0 + kk) * M] : 0.0, ah[r], al[r]);
+      for (int u = 0; u < 4; ++u) a[u] = live ? Ak[(int64_t)(kk + u) * M] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float ah, al;
+        df_split(a[u], ah, al);
+#pragma unroll
+        for (int j = 0; j < NT; ++j) df_mac(sh[j], sl[j], ah, al, Bh[kk + u][j], Bl[kk + u][j]);
       }
+    }
+    for (; kk < kmax; ++kk) {
+      float ah, al;
+      df_split(live ? Ak[(int64_t)kk * M] : 0.0, ah, al);
 #pragma unroll
-      for (int j = 0; j < ROWS_NMAX; ++j) {
-        if (j < N) {
-          const float bh = Bh[kk][j], bl = Bl[kk][j];
-#pragma unroll
-          for (int r = 0; r < ROWS_PER_THREAD; ++r) df_mac(sh[r][j], sl[r][j], ah[r], al[r], bh, bl);
-        }
-      }
+      for (int j = 0; j < NT; ++j) df_mac(sh[j], sl[j], ah, al, Bh[kk][j], Bl[kk][j]);
     }
     __syncthreads();
   }
-  double* Cb = C + it.c_off;
+  double acc[ROWS_NMAX];
 #pragma unroll
-  for (int r = 0; r < ROWS_PER_THREAD; ++r) {
-    const int64_t m = m0 + tid + 256 * r;
-    if (m < M) {
-#pragma unroll
-      for (int j = 0; j < ROWS_NMAX; ++j)
-        if (j < N) Cb[m + j * M] = (double)sh[r][j] + (double)sl[r][j];
-    }
+  for (int j = 0; j < ROWS_NMAX; ++j) acc[j] = j < NT ? (double)sh[j] + (double)sl[j] : 0.0;
+  rows_store<double>(it, tl, acc, C, partials, counters);
+}
+
+__device__ __forceinline__ void gemm_rows_df(const GemmItem& it, const GemmTile& tl, const double* __restrict__ A,
+                                             const double* __restrict__ B, double* __restrict__ C, double* smem,
+                                             double* __restrict__ partials, int* __restrict__ counters) {
+  switch (it.N) {
+    case 1: gemm_rows_df_n<1>(it, tl, A, B, C, smem, partials, counters); break;
+    case 2: gemm_rows_df_n<2>(it, tl, A, B, C, smem, partials, counters); break;
+    case 3: gemm_rows_df_n<3>(it, tl, A, B, C, smem, partials, counters); break;
+    case 4: gemm_rows_df_n<4>(it, tl, A, B, C, smem, partials, counters); break;
+    case 5: gemm_rows_df_n<5>(it, tl, A, B, C, smem, partials, counters); break;
+    case 6: gemm_rows_df_n<6>(it, tl, A, B, C, smem, partials, counters); break;
+    case 7: gemm_rows_df_n<7>(it, tl, A, B, C, smem, partials, counters); break;
+    default: gemm_rows_df_n<8>(it, tl, A, B, C, smem, partials, counters); break;
   }
 }
 
 template <typename T>
-__device__ __forceinline__ void gemm_rows_df_dispatch(const GemmItem& it, int64_t m0, const T* A, const T* B, T* C,
-                                                      T* smem) {
-  gemm_rows<T>(it, m0, A, B, C, smem);  // complex tensors never take the split-precision path
+__device__ __forceinline__ void gemm_rows_df_dispatch(const GemmItem& it, const GemmTile& tl, const T* A, const T* B,
+                                                      T* C, T* smem, T* partials, int* counters) {
+  gemm_rows<T>(it, tl, A, B, C, smem, partials, counters);  // complex tensors never take the split-precision path
 }
 template <>
-__device__ __forceinline__ void gemm_rows_df_dispatch<double>(const GemmItem& it, int64_t m0, const double* A,
-                                                              const double* B, double* C, double* smem) {
-  gemm_rows_df(it, m0, A, B, C, smem);
+__device__ __forceinline__ void gemm_rows_df_dispatch<double>(const GemmItem& it, const GemmTile& tl, const double* A,
+                                                              const double* B, double* C, double* smem,
+                                                              double* partials, int* counters) {
+  gemm_rows_df(it, tl, A, B, C, smem, partials, counters);
 }
 
-template <typename T>
+// One launch per contraction for every FP64-list product: 64x64 / 32x32 tiles and the N <= 8
+// row blocks share the grid (their shared-memory needs overlap in one buffer).
+template <typename T, bool DF>
 __global__ void __launch_bounds__(256) k_gemm_f64(const GemmItem* __restrict__ items,
                                                   const GemmTile* __restrict__ tiles,
                                                   const T* __restrict__ A,
                                                   const T* __restrict__ B, T* __restrict__ C,
                                                   T* __restrict__ partials, int* __restrict__ counters) {
-  __shared__ T smem[BK * 65 * 2];
+  constexpr int kTileElems = BK * 65 * 2, kRowElems = ROWS_KCHUNK * ROWS_NMAX;
+  __shared__ T smem[kTileElems > kRowElems ? kTileElems : kRowElems];
   const GemmTile tl = tiles[blockIdx.x];
   const GemmItem it = items[tl.item];
   if (tl.cfg == CFG_64)
     gemm_tile<T, 64, 64, 4, 4>(it, tl, A, B, C, smem, partials, counters);
-  else
+  else if (tl.cfg == CFG_32)
     gemm_tile<T, 32, 32, 2, 2>(it, tl, A, B, C, smem, partials, counters);
-}
-
-// The N <= 8 products in a launch of their own (their register needs differ from the tiles').
-template <typename T, bool DF>
-__global__ void __launch_bounds__(256) k_gemm_rows(const GemmItem* __restrict__ items,
-                                                   const GemmTile* __restrict__ tiles,
-                                                   const T* __restrict__ A, const T* __restrict__ B,
-                                                   T* __restrict__ C) {
-  __shared__ T smem[ROWS_KCHUNK * ROWS_NMAX];
-  const GemmTile tl = tiles[blockIdx.x];
-  const GemmItem it = items[tl.item];
-  if (DF)
-    gemm_rows_df_dispatch<T>(it, tl.m0, A, B, C, smem);
+  else if (DF)
+    gemm_rows_df_dispatch<T>(it, tl, A, B, C, smem, partials, counters);
   else
-    gemm_rows<T>(it, tl.m0, A, B, C, smem);
+    gemm_rows<T>(it, tl, A, B, C, smem, partials, counters);
 }
 
 template <typename T>
@@ -542,109 +646,178 @@ int check_launch(Ctx* ctx, const char* what) {
 
 }  // namespace
 
-int launch_permute(Ctx* ctx, const PermutePlan& pp, const void* in, void* out, void* stream) {
+int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream) {
+  // blocks per segment: runs take one warp each (8 per block), tiles one block each; when the
+  // total exceeds 8 blocks per SM the segments share that budget in proportion to their work
+  PermLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  int dtype = TK_F64;
+  int64_t natural[kMaxPermSegs] = {0};
+  for (int j = 0; j < njobs; ++j) {
+    const PermutePlan& pp = *jobs[j].plan;
+    if (pp.identity) continue;
+    dtype = pp.dtype;
+    if (!pp.runs.empty()) {
+      if (L.nseg == kMaxPermSegs) return TK_ERR_ARG;
+      PermSeg& g = L.seg[L.nseg];
+      g.kind = 0;
+      g.nwork = (int64_t)pp.runs.size();
+      g.runs = pp.d_runs;
+      g.tasks = pp.d_rtasks;
+      g.srcs = pp.d_srcs;
+      g.in = jobs[j].in;
+      g.out = jobs[j].out;
+      natural[L.nseg++] = (g.nwork + 7) / 8;
+    }
+    if (!pp.tasks.empty() && pp.total_tiles > 0) {
+      if (L.nseg == kMaxPermSegs) return TK_ERR_ARG;
+      PermSeg& g = L.seg[L.nseg];
+      g.kind = 1;
+      g.ntasks = (int32_t)pp.tasks.size();
+      g.nwork = pp.total_tiles;
+      g.tasks = pp.d_tasks;
+      g.tile_starts = pp.d_tile_starts;
+      g.srcs = pp.d_srcs;
+      g.in = jobs[j].in;
+      g.out = jobs[j].out;
+      natural[L.nseg++] = g.nwork;
+    }
+  }
+  if (L.nseg == 0) return TK_OK;
+  const int64_t cap = (int64_t)std::max(ctx->num_sms, 1) * 8;
+  int64_t total = 0;
+  for (int i = 0; i < L.nseg; ++i) total += natural[i];
+  int64_t b0 = 0;
+  for (int i = 0; i < L.nseg; ++i) {
+    int64_t nb = natural[i];
+    if (total > cap) nb = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)((double)cap * natural[i] / total)));
+    L.seg[i].block0 = b0;
+    L.seg[i].nblocks = nb;
+    b0 += nb;
+  }
   cudaStream_t s = (cudaStream_t)stream;
-  if (!pp.runs.empty()) {
-    const int64_t nruns = (int64_t)pp.runs.size();
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((nruns + 7) / 8, (int64_t)ctx->num_sms * 8));
-    ProfScope prof(ctx, "k_permute", stream);
-    if (pp.dtype == TK_C128)
-      k_permute_runs<double2><<<(unsigned)grid, 256, 0, s>>>(pp.d_runs, nruns, pp.d_rtasks, pp.d_srcs,
-                                                             (const double2*)in, (double2*)out);
-    else
-      k_permute_runs<double><<<(unsigned)grid, 256, 0, s>>>(pp.d_runs, nruns, pp.d_rtasks, pp.d_srcs,
-                                                            (const double*)in, (double*)out);
-    int rc = check_launch(ctx, "k_permute_runs");
-    if (rc != TK_OK) return rc;
-  }
-  if (!pp.tasks.empty()) {
-    const int ntasks = (int)pp.tasks.size();
-    int64_t grid = std::min<int64_t>(pp.total_tiles, (int64_t)ctx->num_sms * 8);
-    if (grid < 1) grid = 1;
-    ProfScope prof(ctx, "k_permute", stream);
-    if (pp.dtype == TK_C128)
-      k_permute<double2><<<(unsigned)grid, 256, 0, s>>>(pp.d_tasks, ntasks, pp.d_tile_starts, pp.d_srcs,
-                                                        pp.total_tiles, (const double2*)in, (double2*)out);
-    else
-      k_permute<double><<<(unsigned)grid, 256, 0, s>>>(pp.d_tasks, ntasks, pp.d_tile_starts, pp.d_srcs,
-                                                       pp.total_tiles, (const double*)in, (double*)out);
-    return check_launch(ctx, "k_permute");
-  }
-  return TK_OK;
+  ProfScope prof(ctx, "k_permute", stream);
+  if (dtype == TK_C128)
+    k_permute<double2><<<(unsigned)b0, 256, 0, s>>>(L);
+  else
+    k_permute<double><<<(unsigned)b0, 256, 0, s>>>(L);
+  return check_launch(ctx, "k_permute");
+}
+
+int launch_permute(Ctx* ctx, const PermutePlan& pp, const void* in, void* out, void* stream) {
+  const PermJob job{&pp, in, out};
+  return launch_permutes(ctx, &job, 1, stream);
 }
 
 int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
-  // shape choice: rows kernel for N <= 8; 64x64 tiles unless they give fewer than ~3 CTAs per
-  // SM over the whole launch, then 32x32
-  const std::vector<GemmItem>& gl = cp.gemms_fp64;
-  int64_t tiles64 = 0;
-  for (const GemmItem& g : gl)
-    if (g.N > ROWS_NMAX) tiles64 += ((g.M + 63) / 64) * ((g.N + 63) / 64);
-  const bool small_tiles = tiles64 < 3 * (int64_t)std::max(ctx->num_sms, 1);
-  int64_t tiles32 = 0;
-  for (const GemmItem& g : gl)
-    if (g.N > ROWS_NMAX) tiles32 += ((g.M + 31) / 32) * ((g.N + 31) / 32);
+  // Shapes: the rows kernel for N <= 8, 64x64 or 32x32 tiles otherwise.  A launch that would give
+  // the SMs too few CTAs cuts the inner dimension into up to SPLIT_MAX parts (split-K); the parts
+  // of one output tile are added in part order by the CTA that finishes last (deterministic).
+  const int64_t sms = std::max(ctx->num_sms, 1);
+  int64_t tiles64 = 0, tiles32 = 0, split64 = 0;
+  double pad64 = 0, pad32 = 0;
+  for (const GemmItem& g : cp.gemms_fp64) {
+    if (g.N <= ROWS_NMAX) continue;
+    const int64_t t64 = ((g.M + 63) / 64) * ((g.N + 63) / 64), t32 = ((g.M + 31) / 32) * ((g.N + 31) / 32);
+    tiles64 += t64;
+    tiles32 += t32;
+    split64 += t64 * std::max<int64_t>(1, std::min<int64_t>(SPLIT_MAX, g.K / 64));
+    pad64 += 4096.0 * t64 * g.K;
+    pad32 += 1024.0 * t32 * g.K;
+  }
+  // 64x64 tiles reuse registers twice as well as 32x32 ones; take them unless padding to 64 costs
+  // more than a fifth extra work, or they are too few even after splitting K
+  const bool use64 = tiles64 >= 3 * sms || (pad64 <= 1.2 * pad32 && split64 >= 3 * sms);
+  const int bm = use64 ? 64 : 32;
+  // A product whose N exceeds a multiple of the tile width by at most ROWS_NMAX columns gives those
+  // last columns to the rows kernel (B and C are column-major: their trailing columns are a
+  // contiguous sub-matrix with the same leading dimension) instead of padding a whole tile column.
+  std::vector<GemmItem> gl;
+  gl.reserve(cp.gemms_fp64.size() * 2);
+  for (const GemmItem& g : cp.gemms_fp64) {
+    const int64_t rem = g.N % bm;
+    if (g.N > bm && rem > 0 && rem <= ROWS_NMAX) {
+      GemmItem main = g, tail = g;
+      main.N = g.N - rem;
+      tail.N = rem;
+      tail.b_off = g.b_off + main.N * g.K;
+      tail.c_off = g.c_off + main.N * g.M;
+      gl.push_back(main);
+      gl.push_back(tail);
+    } else {
+      gl.push_back(g);
+    }
+  }
+  int64_t rows_ctas = 0;
+  tiles64 = tiles32 = 0;
+  for (const GemmItem& g : gl) {
+    if (g.N <= ROWS_NMAX)
+      rows_ctas += (g.M + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
+    else
+      (use64 ? tiles64 : tiles32) += ((g.M + bm - 1) / bm) * ((g.N + bm - 1) / bm);
+  }
+  const int64_t ntiles = use64 ? tiles64 : tiles32;
+  const int64_t want_tiles = ntiles >= 3 * sms ? 1 : (4 * sms + ntiles - 1) / std::max<int64_t>(ntiles, 1);
+  const int64_t want_rows = rows_ctas >= 2 * sms ? 1 : (4 * sms + rows_ctas - 1) / std::max<int64_t>(rows_ctas, 1);
   int32_t nslots = 0;
+  int64_t poff = 0;
   struct Cand {
     GemmTile t;
     double cost;
   };
   std::vector<Cand> cands;
+  // one output tile as nsplit parts over [0, K), each part's depth a multiple of kalign
+  auto emit = [&](int32_t item, int64_t m0, int64_t n0, int32_t cfg, int64_t K, int nsplit, int kalign,
+                  int64_t part_elems, double area) {
+    const int32_t slot = nsplit > 1 ? nslots++ : -1;
+    const int64_t kstep = ((K + nsplit - 1) / nsplit + kalign - 1) / kalign * kalign;
+    for (int p = 0; p < nsplit; ++p) {
+      const int64_t k0 = std::min<int64_t>(K, p * kstep), k1 = std::min<int64_t>(K, k0 + kstep);
+      GemmTile t;
+      std::memset(&t, 0, sizeof(t));
+      t.item = item;
+      t.m0 = (int32_t)m0;
+      t.n0 = (int32_t)n0;
+      t.cfg = cfg;
+      t.k0 = (int32_t)k0;
+      t.k1 = (int32_t)k1;
+      t.slot = slot;
+      t.part = p;
+      t.nsplit = nsplit;
+      t.poff = nsplit > 1 ? poff : 0;
+      cands.push_back({t, area * (double)(k1 - k0)});
+    }
+    if (nsplit > 1) poff += (int64_t)nsplit * part_elems;
+  };
   for (size_t i = 0; i < gl.size(); ++i) {
     const GemmItem& g = gl[i];
     if (g.N <= ROWS_NMAX) {
-      for (int64_t m0 = 0; m0 < g.M; m0 += ROWS_PER_CTA) {
-        GemmTile t;
-        std::memset(&t, 0, sizeof(t));
-        t.item = (int32_t)i;
-        t.m0 = (int32_t)m0;
-        t.cfg = cp.gemm_mode == TK_GEMM_FP64 ? CFG_ROWS : CFG_ROWS_DF;
-        t.k1 = (int32_t)g.K;
-        t.slot = -1;
-        t.nsplit = 1;
-        cands.push_back({t, (double)std::min<int64_t>(ROWS_PER_CTA, g.M - m0) * g.N * g.K});
-      }
+      const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want_rows, (int64_t)SPLIT_MAX, g.K / 32}));
+      const int32_t cfg = cp.gemm_mode == TK_GEMM_FP64 ? CFG_ROWS : CFG_ROWS_DF;
+      for (int64_t m0 = 0; m0 < g.M; m0 += ROWS_PER_CTA)
+        emit((int32_t)i, m0, 0, cfg, g.K, nsplit, 8, 256 * ROWS_NMAX,
+             (double)std::min<int64_t>(ROWS_PER_CTA, g.M - m0) * g.N);
       continue;
     }
-    const int bm = small_tiles ? 32 : 64, bn = bm;
-    // split-K (32x32 tiles only): enough parts to give ~6 CTAs per SM, each part >= 64 deep
-    int nsplit = 1;
-    if (small_tiles) {
-      const int64_t want = (6 * (int64_t)std::max(ctx->num_sms, 1) + tiles32 - 1) / std::max<int64_t>(tiles32, 1);
-      nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)SPLIT_MAX, g.K / 64}));
-    }
-    for (int64_t n0 = 0; n0 < g.N; n0 += bn)
-      for (int64_t m0 = 0; m0 < g.M; m0 += bm) {
-        const int32_t slot = nsplit > 1 ? nslots++ : -1;
-        const int64_t kstep = ((g.K + nsplit - 1) / nsplit + BK - 1) / BK * BK;
-        for (int p = 0; p < nsplit; ++p) {
-          const int64_t k0 = p * kstep, k1 = std::min<int64_t>(g.K, k0 + kstep);
-          GemmTile t;
-          std::memset(&t, 0, sizeof(t));
-          t.item = (int32_t)i;
-          t.m0 = (int32_t)m0;
-          t.n0 = (int32_t)n0;
-          t.cfg = small_tiles ? CFG_32 : CFG_64;
-          t.k0 = (int32_t)k0;
-          t.k1 = (int32_t)std::max<int64_t>(k0, k1);
-          t.slot = slot;
-          t.part = p;
-          t.nsplit = nsplit;
-          cands.push_back({t, (double)bm * bn * (double)(t.k1 - t.k0)});
-        }
-      }
+    const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want_tiles, (int64_t)SPLIT_MAX, g.K / 64}));
+    for (int64_t n0 = 0; n0 < g.N; n0 += bm)
+      for (int64_t m0 = 0; m0 < g.M; m0 += bm)
+        emit((int32_t)i, m0, n0, use64 ? CFG_64 : CFG_32, g.K, nsplit, BK, (int64_t)bm * bm, (double)bm * bm);
   }
   cp.split_slots = nslots;
-  std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.cost > b.cost; });
-  std::vector<GemmTile> tiles, rows;
-  for (auto& c : cands) (c.t.cfg >= CFG_ROWS ? rows : tiles).push_back(c.t);
+  // Row blocks first (they are latency-bound: a serial walk over K), then tiles by cost, largest
+  // first, so the short tiles fill the tail.
+  std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) {
+    const bool ra = a.t.cfg >= CFG_ROWS, rb = b.t.cfg >= CFG_ROWS;
+    if (ra != rb) return ra;
+    return a.cost > b.cost;
+  });
+  std::vector<GemmTile> tiles;
+  for (auto& c : cands) tiles.push_back(c.t);
   cp.n_gemm_tiles = (int64_t)tiles.size();
-  cp.n_gemm_rows = (int64_t)rows.size();
   int rc = dev_upload(ctx, &cp.d_gemm_items, gl.data(), gl.size() * sizeof(GemmItem));
   if (rc != TK_OK) return rc;
   rc = dev_upload(ctx, &cp.d_gemm_tiles, tiles.data(), tiles.size() * sizeof(GemmTile));
-  if (rc != TK_OK) return rc;
-  rc = dev_upload(ctx, &cp.d_gemm_rows, rows.data(), rows.size() * sizeof(GemmTile));
   if (rc != TK_OK) return rc;
   if (!cp.zeros.empty()) {
     rc = dev_upload(ctx, &cp.d_zero, cp.zeros.data(), cp.zeros.size() * sizeof(ZeroItem));
@@ -654,43 +827,30 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
     std::vector<int> zeros((size_t)nslots, 0);
     rc = dev_upload(ctx, &cp.d_split_counters, zeros.data(), zeros.size() * sizeof(int));
     if (rc != TK_OK) return rc;
-    cp.partials_bytes = (size_t)nslots * SPLIT_MAX * 32 * 32 * (cp.dtype == TK_C128 ? 16 : 8);
+    cp.partials_bytes = (size_t)poff * (cp.dtype == TK_C128 ? 16 : 8);
   }
   return TK_OK;
 }
 
 int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
                      void* partials, void* stream) {
+  if (cp.n_gemm_tiles == 0) return TK_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const GemmItem* items = (const GemmItem*)cp.d_gemm_items;
-  if (cp.n_gemm_tiles > 0) {
-    ProfScope prof(ctx, "k_gemm_f64", stream);
-    const GemmTile* tiles = (const GemmTile*)cp.d_gemm_tiles;
-    int* counters = (int*)cp.d_split_counters;
-    if (cp.dtype == TK_C128)
-      k_gemm_f64<double2><<<(unsigned)cp.n_gemm_tiles, 256, 0, s>>>(items, tiles, (const double2*)a, (const double2*)b,
-                                                                    (double2*)c, (double2*)partials, counters);
-    else
-      k_gemm_f64<double><<<(unsigned)cp.n_gemm_tiles, 256, 0, s>>>(items, tiles, (const double*)a, (const double*)b,
-                                                                   (double*)c, (double*)partials, counters);
-    int rc = check_launch(ctx, "k_gemm_f64");
-    if (rc != TK_OK) return rc;
-  }
-  if (cp.n_gemm_rows > 0) {
-    ProfScope prof(ctx, "k_gemm_rows", stream);
-    const GemmTile* rows = (const GemmTile*)cp.d_gemm_rows;
-    if (cp.dtype == TK_C128)
-      k_gemm_rows<double2, false><<<(unsigned)cp.n_gemm_rows, 256, 0, s>>>(items, rows, (const double2*)a,
-                                                                           (const double2*)b, (double2*)c);
-    else if (cp.gemm_mode == TK_GEMM_FP64)
-      k_gemm_rows<double, false><<<(unsigned)cp.n_gemm_rows, 256, 0, s>>>(items, rows, (const double*)a,
-                                                                          (const double*)b, (double*)c);
-    else
-      k_gemm_rows<double, true><<<(unsigned)cp.n_gemm_rows, 256, 0, s>>>(items, rows, (const double*)a,
-                                                                         (const double*)b, (double*)c);
-    return check_launch(ctx, "k_gemm_rows");
-  }
-  return TK_OK;
+  const GemmTile* tiles = (const GemmTile*)cp.d_gemm_tiles;
+  int* counters = (int*)cp.d_split_counters;
+  const unsigned grid = (unsigned)cp.n_gemm_tiles;
+  ProfScope prof(ctx, "k_gemm_f64", stream);
+  if (cp.dtype == TK_C128)
+    k_gemm_f64<double2, false><<<grid, 256, 0, s>>>(items, tiles, (const double2*)a, (const double2*)b, (double2*)c,
+                                                    (double2*)partials, counters);
+  else if (cp.gemm_mode == TK_GEMM_FP64)
+    k_gemm_f64<double, false><<<grid, 256, 0, s>>>(items, tiles, (const double*)a, (const double*)b, (double*)c,
+                                                   (double*)partials, counters);
+  else
+    k_gemm_f64<double, true><<<grid, 256, 0, s>>>(items, tiles, (const double*)a, (const double*)b, (double*)c,
+                                                  (double*)partials, counters);
+  return check_launch(ctx, "k_gemm_f64");
 }
 
 int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream) {
@@ -714,8 +874,8 @@ int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b,
   const void* bt = cp.pb->identity ? b : (const void*)(w + cp.ws_bt);
   void* ct = cp.pc ? (void*)(w + cp.ws_ct) : c;
   int rc;
-  if (!cp.pa->identity && (rc = launch_permute(ctx, *cp.pa, a, (void*)at, stream)) != TK_OK) return rc;
-  if (!cp.pb->identity && (rc = launch_permute(ctx, *cp.pb, b, (void*)bt, stream)) != TK_OK) return rc;
+  const PermJob in_jobs[2] = {{cp.pa.get(), a, (void*)at}, {cp.pb.get(), b, (void*)bt}};
+  if ((rc = launch_permutes(ctx, in_jobs, 2, stream)) != TK_OK) return rc;  // both operands, one launch
   if ((rc = launch_zero(ctx, cp, ct, stream)) != TK_OK) return rc;
   if (!cp.gemms_fp64.empty() && (rc = launch_gemm_fp64(ctx, cp, at, bt, ct, w + cp.ws_partials, stream)) != TK_OK)
     return rc;

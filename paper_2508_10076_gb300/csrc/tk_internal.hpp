@@ -167,8 +167,7 @@ struct ContractPlan {
   // device tables
   void* d_gemm_items = nullptr;
   void* d_gemm_tiles = nullptr;
-  void* d_gemm_rows = nullptr;
-  int64_t n_gemm_tiles = 0, n_gemm_rows = 0;
+  int64_t n_gemm_tiles = 0;
   // split-K of the FP64 tiles: per-slot arrival counters (plan-owned, self-resetting; launches of
   // one plan must not overlap) and the partial tiles in the workspace
   void* d_split_counters = nullptr;
@@ -239,6 +238,13 @@ struct ProfScope {
 int dev_upload(Ctx* ctx, void** dst, const void* src, size_t bytes);
 void dev_free(void* p);
 int launch_permute(Ctx* ctx, const PermutePlan& pp, const void* in, void* out, void* stream);
+struct PermJob {
+  const PermutePlan* plan;
+  const void* in;
+  void* out;
+};
+// Several permutes in one launch (identity plans are skipped; at most two plans).
+int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream);
 int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
                      void* partials, void* stream);
 int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream);
