@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include "tk_device.cuh"
 #include "tk_internal.hpp"
 
 namespace tk {
@@ -571,7 +572,7 @@ __device__ __forceinline__ void gemm_rows_df_n(const GemmItem& it, const GemmTil
   }
   double acc[ROWS_NMAX];
 #pragma unroll
-  for (int j = 0; j < ROWS_NMAX; ++j) acc[j] = j < NT ? (double)sh[j] + (double)sl[j] : 0.0;
+  for (int j = 0; j < ROWS_NMAX; ++j) acc[j] = j < NT ? f32_to_f64(sh[j]) + f32_to_f64(sl[j]) : 0.0;
   rows_store<double>(it, tl, acc, C, partials, counters);
 }
 

@@ -8,19 +8,24 @@
 //     d_i 2^{-7(i+1)} exactly in BF16;
 //   * the products A_i B_j with i + j <= s - 1 run as tcgen05.mma kind::f16 (BF16 x BF16, FP32
 //     accumulate in TMEM) into four accumulators by level i + j = 0, 1, 2 and >= 3.  Levels 0..2
-//     are sums of integers times one power of two and stay exact in FP32 while K <= 512 (one
-//     "segment"; longer K runs in several segments whose results are added in FP64);
-//   * the epilogue adds the four accumulators with error-free FP32 two-sums, converts to FP64
-//     and applies 2^{e_m + f_n}.
+//     are sums of integers times one power of two: per k a level-0 term is at most 128^2 = 2^14
+//     in its unit, level 1 at most 2 * 128 * 64 = 2^14 and level 2 at most 2.5 * 2^12, so the FP32
+//     accumulators stay exact (integers below 2^24) while K <= 1024 -- one "segment".  Longer K
+//     runs in several segments whose results are added in FP64;
+//   * the epilogue adds the four accumulators with error-free FP32 two-sums, converts to FP64 and
+//     applies 2^{e_m + f_n}.
 // With s = 6 the relative Frobenius error against FP64 is ~1e-12 on N(0,1) data.
 //
-// Data path: a scale kernel and a slicer kernel write the slices as pre-tiled 128 x 64 BF16
-// tiles (row-major, 128 B rows); one persistent GEMM launch walks a work list of
-// (sector, 128-row tile, 128-column tile) items.  Per CTA: warp 0 issues TMA loads
-// (cp.async.bulk.tensor, 128B swizzle) into a 4-stage shared-memory ring, one thread of warp 1
-// issues the MMAs, warps 2..5 drain TMEM.  Every mbarrier wait is bounded: on timeout the
-// kernel records an error in the context's status word, drains its own copies and MMAs
-// (bounded again), frees TMEM and returns.
+// Data path: a scale kernel and a slicer kernel write the slices as pre-tiled 128 x 32 BF16
+// tiles (64-byte rows); one persistent GEMM launch walks a work list of (sector, 128-row tile,
+// column tile) items, the last column tile of a sector as narrow as its remainder (MMA N a
+// multiple of 16).  Per CTA: warp 0 issues TMA loads (cp.async.bulk.tensor, 64-byte swizzle) of
+// all s A slices and all s B slices of one 32-deep k-chunk into a stage (two stages); one thread
+// of warp 1 issues every slice-pair MMA from the resident stage; warps 2..9 drain TMEM into
+// registers, release it to the MMA warp at once, and finish the FP64 conversion and the stores
+// while the next tile's MMAs run.  Every mbarrier wait is bounded: on timeout the kernel records
+// an error in the context's status word, drains its own copies and MMAs (bounded again), frees
+// TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -28,20 +33,24 @@
 #include <algorithm>
 #include <cstring>
 
+#include "tk_device.cuh"
 #include "tk_internal.hpp"
 
 namespace tk {
 namespace {
 
-constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 64;
-constexpr int OZ_STAGES = 6;
-constexpr int OZ_TILE_BYTES = OZ_BM * OZ_BK * 2;  // A and B tiles are both 128 x 64 BF16
-constexpr int OZ_SEG_KC = 8;                      // k-chunks per exact segment (K <= 512)
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32;
+constexpr int OZ_TROWS = 128;                     // rows of a slice tile in memory (A: m, B: n)
+constexpr int OZ_TILE_BYTES = OZ_TROWS * OZ_BK * 2;  // slice tiles are 128 x 32 BF16 (8 KB)
+constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;     // A box in shared memory: 128 x 32
+constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;     // B box in shared memory: 64 x 32
+constexpr int OZ_STAGES = 3;                      // a stage holds all s A and s B boxes of a k-chunk
+constexpr int OZ_SEG_KC = 32;                     // k-chunks per exact segment (K <= 1024)
 constexpr int OZ_NACC = 4;
-constexpr int OZ_TMEM_COLS = 512;                 // 4 accumulators x 128 FP32 columns
+constexpr int OZ_TMEM_COLS = 512;                 // 2 buffers x 4 accumulators x 64 FP32 columns
 constexpr int OZ_EPI_WARPS = 8;                   // two per TMEM lane quadrant
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;  // producer warp, MMA warp, epilogue warps
-constexpr int OZ_MAX_SLICES = 8;
+constexpr int OZ_MAX_SLICES = 7;
 constexpr int OZ_MAX_PAIRS = OZ_MAX_SLICES * (OZ_MAX_SLICES + 1) / 2;
 constexpr int OZ_DEFAULT_SLICES = 6;
 constexpr unsigned long long OZ_WAIT_NS = 2000000000ull;  // bounded waits: 2 s
@@ -51,10 +60,10 @@ struct OzSector {
   int64_t a_off, b_off, c_off;
   int64_t ta_base, tb_base;  // first tile of this sector's A / B slices
   int64_t sa_off, sb_off;    // offsets into the row / column scale arrays
-  int32_t nmt, nnt, nkc, pad;
+  int32_t nmt, nnt, nkc, pad;  // 128-row slice tiles of A~ / B~^T, 32-deep k-chunks
 };
 struct OzWork {
-  int32_t sector, mt, nt, pad;
+  int32_t sector, mt, nt, nw;  // nw: columns of this tile (multiple of 16, <= OZ_BN)
 };
 struct OzJob {  // slicer / scale job
   int32_t sector, operand, r0, kc;
@@ -149,14 +158,14 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t smem_desc_k_sw128(uint32_t addr) {
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t smem_desc_k_sw64(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);        // start address
   d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)(512 >> 4) << 32;               // stride byte offset: 8 rows x 64 B
   d |= (uint64_t)1 << 46;                        // descriptor version (sm_100 family)
-  d |= (uint64_t)2 << 61;                        // layout: 128-byte swizzle
+  d |= (uint64_t)4 << 61;                        // layout: 64-byte swizzle
   return d;
 }
 // Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both operands K-major, M x N.
@@ -166,27 +175,6 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
          | (1u << 10)                  // B format: BF16
          | ((uint32_t)(n >> 3) << 17)  // N / 8
          | ((uint32_t)(m >> 4) << 24); // M / 16
-}
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// Exact FP32 -> FP64 by assembling the bit pattern with integer operations (the FP64 pipe is
-// scarce on this part); zeros and FP32 subnormals/non-finite values take the hardware path.
-__device__ __forceinline__ double f32_to_f64(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t ex = (u >> 23) & 0xFFu;
-  if (ex == 0u) {
-    if ((u << 1) == 0u) return __longlong_as_double((long long)(u & 0x80000000u) << 32);  // +-0
-    return (double)f;
-  }
-  if (ex == 0xFFu) return (double)f;
-  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)d);
 }
 
 // v * 2^e, exact, by adding e to the exponent field when the result stays a normal number.
@@ -224,11 +212,7 @@ __device__ __forceinline__ long long round_scaled(double v, int shift) {
 }
 
 // ------------------------------------------------------------------ scale and slice kernels
-// Operand view: element (r, k) of an R x K matrix; A~^c: (m, k) -> A[a_off + m + k M];
-// B~^c: (n, k) -> B[b_off + k + n K].
-__device__ __forceinline__ double oz_elem(const OzSector& s, int operand, const double* X, int64_t r, int64_t k) {
-  return operand == 0 ? X[s.a_off + r + k * s.M] : X[s.b_off + k + r * s.K];
-}
+// Operand views: A~^c element (m, k) at A[a_off + m + k M]; B~^c element (k, n) at B[b_off + k + n K].
 
 // Scale exponents 2^e > max_k |x_rk| for every row of A~^c and every column of B~^c.  The
 // exponent of a maximum is the maximum of the exponents, so each job covers a chunk of K and
@@ -277,82 +261,133 @@ __global__ void __launch_bounds__(256) k_oz_scale(const OzSector* __restrict__ s
   }
 }
 
-// One 128 x 64 (rows x k) tile of one operand per CTA, all slices.  Thread t: row t/2, k half t%2.
+// One 128 x 32 (rows x k) tile of one operand per CTA, all slices.  Lanes run along k, so each
+// warp writes 64 contiguous bytes of a tile row per slice; A~ (column-major, rows contiguous) is
+// staged through shared memory to keep its reads coalesced, B~ (k contiguous) is read directly.
 __global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ secs, const OzJob* __restrict__ jobs,
                                                   const double* __restrict__ A, const double* __restrict__ B,
                                                   const int32_t* __restrict__ scale_a,
                                                   const int32_t* __restrict__ scale_b,
                                                   __nv_bfloat16* __restrict__ tiles_a,
                                                   __nv_bfloat16* __restrict__ tiles_b, int nslices) {
+  __shared__ double xs[OZ_BK][OZ_TROWS + 1];
   const OzJob jb = jobs[blockIdx.x];
   const OzSector s = secs[jb.sector];
   const int op = jb.operand;
   const int64_t R = op == 0 ? s.M : s.N;
-  const int rl = threadIdx.x >> 1, half = threadIdx.x & 1;
   const int64_t rt = jb.r0;  // row-tile index
-  const int64_t r = rt * OZ_BM + rl;
-  const double* X = op == 0 ? A : B;
-  int e = (r < R) ? (op == 0 ? scale_a[s.sa_off + r] : scale_b[s.sb_off + r]) : 0;
-  if (e == kNoScale) e = 0;  // an all-zero row or column
-  const int shift = 7 * nslices - e;
+  const int64_t r0 = rt * OZ_TROWS, k0 = (int64_t)jb.kc * OZ_BK;
+  const int tid = threadIdx.x, kl = tid & 31, rw = tid >> 5;
+  if (op == 0) {
+    for (int e = tid; e < OZ_TROWS * OZ_BK; e += 256) {
+      const int ml = e & (OZ_TROWS - 1), kk = e / OZ_TROWS;
+      const int64_t m = r0 + ml, k = k0 + kk;
+      xs[kk][ml] = (m < R && k < s.K) ? __ldg(A + s.a_off + m + k * s.M) : 0.0;
+    }
+    __syncthreads();
+  }
   const int64_t nrt = op == 0 ? s.nmt : s.nnt;
-  const int64_t base = op == 0 ? s.ta_base : s.tb_base;
-  __nv_bfloat16* tiles = op == 0 ? tiles_a : tiles_b;
-  for (int g = 0; g < 4; ++g) {
-    const int64_t k0 = (int64_t)jb.kc * OZ_BK + half * 32 + g * 8;
-    int32_t dig[8][OZ_MAX_SLICES];
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj) {
-      const int64_t k = k0 + jj;
-      const double v = (r < R && k < s.K) ? oz_elem(s, op, X, r, k) : 0.0;
-      long long q = round_scaled(v, shift);  // round(v 2^shift), |q| <= 2^(7 s)
-      for (int i = nslices - 1; i >= 1; --i) {
-        const long long d = ((q + 64) & 127) - 64;
-        dig[jj][i] = (int32_t)d;
-        q = (q - d) >> 7;
-      }
-      dig[jj][0] = (int32_t)q;
+  const int64_t tile0 = (op == 0 ? s.ta_base : s.tb_base) + rt * s.nkc + jb.kc;  // slice 0
+  const int64_t slice_stride = nrt * s.nkc * (int64_t)(OZ_TROWS * OZ_BK);             // elements
+  __nv_bfloat16* dst0 = (op == 0 ? tiles_a : tiles_b) + tile0 * (OZ_TROWS * OZ_BK) + kl;
+  const int32_t* scl = op == 0 ? scale_a + s.sa_off : scale_b + s.sb_off;
+#pragma unroll 4
+  for (int i = 0; i < OZ_TROWS / 8; ++i) {
+    const int rl = rw + 8 * i;
+    const int64_t r = r0 + rl, k = k0 + kl;
+    double v;
+    if (op == 0)
+      v = xs[kl][rl];
+    else
+      v = (r < R && k < s.K) ? __ldg(B + s.b_off + k + r * s.K) : 0.0;
+    int e = (r < R) ? scl[r] : 0;
+    if (e == kNoScale) e = 0;  // an all-zero row or column
+    long long q = round_scaled(v, 7 * nslices - e);  // round(v 2^(7 s - e)), |q| <= 2^(7 s)
+    __nv_bfloat16* dst = dst0 + rl * OZ_BK;
+    for (int sl = nslices - 1; sl >= 1; --sl) {
+      const long long d = ((q + 64) & 127) - 64;  // balanced base-128 digit
+      q = (q - d) >> 7;
+      dst[sl * slice_stride] = __float2bfloat16_rn((float)d * __int_as_float((127 - 7 * (sl + 1)) << 23));
     }
-    for (int i = 0; i < nslices; ++i) {
-      const float sc = ldexpf(1.0f, -7 * (i + 1));
-      __align__(16) __nv_bfloat16 out[8];
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj) out[jj] = __float2bfloat16_rn((float)dig[jj][i] * sc);
-      const int64_t tile = base + ((int64_t)i * nrt + rt) * s.nkc + jb.kc;
-      __nv_bfloat16* dst = tiles + (tile * OZ_BM + rl) * OZ_BK + half * 32 + g * 8;
-      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(out);
-    }
+    dst[0] = __float2bfloat16_rn((float)q * __int_as_float((127 - 7) << 23));
   }
 }
 
 // ------------------------------------------------------------------ the persistent GEMM
 struct OzSmem {
   uint64_t full[OZ_STAGES], empty[OZ_STAGES];
-  uint64_t acc_full, acc_empty, drain;
+  uint64_t acc_full[2], acc_empty[2], drain;
   uint32_t tmem_base;
   int abort_flag;
 };
 
+// Shared memory: OZ_STAGES stages of [A_0 .. A_{s-1} | B_0 .. B_{s-1}] boxes, then OzSmem.
+__host__ __device__ constexpr size_t oz_stage_bytes(int s) { return (size_t)s * (OZ_A_BYTES + OZ_B_BYTES); }
+__host__ __device__ constexpr int oz_stages(int s) { return s <= 6 ? OZ_STAGES : 2; }
+__host__ __device__ constexpr size_t oz_smem_bytes(int s) {
+  return oz_stages(s) * oz_stage_bytes(s) + sizeof(OzSmem) + 1024;  // + alignment slack
+}
+
+// Every slice-pair MMA of one resident stage, unrolled for S slices: pairs grouped by
+// accumulator level (0, 1, 2, >= 3); the first MMA of a level in a segment's first k-chunk
+// overwrites its accumulator.  Descriptors differ from the stage's base descriptor only in the
+// start-address field, so each operand offset is an added constant.
+template <int S>
+__device__ __forceinline__ void oz_issue_stage(uint32_t acc0, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               bool first_kc) {
+#pragma unroll
+  for (int l = 0; l < OZ_NACC; ++l) {
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+#pragma unroll
+      for (int j = 0; j < S - i; ++j) {
+        if ((i + j < OZ_NACC - 1 ? i + j : OZ_NACC - 1) != l) continue;
+        const bool first_of_level = (l < OZ_NACC - 1) ? (i == 0) : (i == 0 && j == OZ_NACC - 1);
+#pragma unroll
+        for (int k16 = 0; k16 < OZ_BK / 16; ++k16)
+          tc_mma_bf16(acc0 + l * OZ_BN, adesc + (uint64_t)((i * OZ_A_BYTES + k16 * 32) >> 4),
+                      bdesc + (uint64_t)((S * OZ_A_BYTES + j * OZ_B_BYTES + k16 * 32) >> 4), idesc,
+                      (first_kc && first_of_level && k16 == 0) ? 0u : 1u);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void oz_issue(int s, uint32_t acc0, uint32_t sbase, uint32_t idesc, bool first_kc) {
+  const uint64_t d = smem_desc_k_sw64(sbase);
+  switch (s) {
+    case 2: oz_issue_stage<2>(acc0, d, d, idesc, first_kc); break;
+    case 3: oz_issue_stage<3>(acc0, d, d, idesc, first_kc); break;
+    case 4: oz_issue_stage<4>(acc0, d, d, idesc, first_kc); break;
+    case 5: oz_issue_stage<5>(acc0, d, d, idesc, first_kc); break;
+    case 6: oz_issue_stage<6>(acc0, d, d, idesc, first_kc); break;
+    default: oz_issue_stage<7>(acc0, d, d, idesc, first_kc); break;
+  }
+}
+
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
-              const OzSector* __restrict__ secs, const OzWork* __restrict__ work, int nwork, const OzPairs pairs,
-              const int32_t* __restrict__ scale_a, const int32_t* __restrict__ scale_b, double* __restrict__ C,
-              int* __restrict__ status) {
+              const OzSector* __restrict__ secs, const OzWork* __restrict__ work, int nwork,
+              const __grid_constant__ OzPairs pairs, int nslices, const int32_t* __restrict__ scale_a, const int32_t* __restrict__ scale_b,
+              double* __restrict__ C, int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char dyn[];
   unsigned char* base = (unsigned char*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
-  unsigned char* sa = base;                                   // OZ_STAGES A tiles
-  unsigned char* sb = base + OZ_STAGES * OZ_TILE_BYTES;       // OZ_STAGES B tiles
-  OzSmem* ss = reinterpret_cast<OzSmem*>(base + 2 * OZ_STAGES * OZ_TILE_BYTES);
+  const uint32_t stage_bytes = (uint32_t)oz_stage_bytes(nslices);
+  const uint32_t nstages = (uint32_t)oz_stages(nslices);
+  const uint32_t b_off = (uint32_t)nslices * OZ_A_BYTES;  // B boxes follow the A boxes in a stage
+  OzSmem* ss = reinterpret_cast<OzSmem*>(base + nstages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort_flag = &ss->abort_flag;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < OZ_STAGES; ++s) {
+    for (uint32_t s = 0; s < nstages; ++s) {
       mbar_init(smem_u32(&ss->full[s]), 1);
       mbar_init(smem_u32(&ss->empty[s]), 1);
     }
-    mbar_init(smem_u32(&ss->acc_full), 1);
-    mbar_init(smem_u32(&ss->acc_empty), OZ_EPI_WARPS);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&ss->acc_full[b]), 1);
+      mbar_init(smem_u32(&ss->acc_empty[b]), OZ_EPI_WARPS);
+    }
     mbar_init(smem_u32(&ss->drain), 1);
     ss->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -374,57 +409,51 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
         const OzWork wk = work[w];
         const OzSector s = secs[wk.sector];
-        for (int kc0 = 0; kc0 < s.nkc && !*abort_flag; kc0 += OZ_SEG_KC) {
-          const int kc1 = min(s.nkc, kc0 + OZ_SEG_KC);
-          for (int p = 0; p < pairs.n && !*abort_flag; ++p) {
-            for (int kc = kc0; kc < kc1; ++kc, ++it) {
-              const uint32_t st = it % OZ_STAGES, ph = (it / OZ_STAGES) & 1;
-              if (!mbar_wait(smem_u32(&ss->empty[st]), ph ^ 1, abort_flag)) break;
-              const uint32_t fb = smem_u32(&ss->full[st]);
-              mbar_expect_tx(fb, 2 * OZ_TILE_BYTES);
-              const int64_t ta = s.ta_base + ((int64_t)pairs.i[p] * s.nmt + wk.mt) * s.nkc + kc;
-              const int64_t tb = s.tb_base + ((int64_t)pairs.j[p] * s.nnt + wk.nt) * s.nkc + kc;
-              tma_load_2d(smem_u32(sa + st * OZ_TILE_BYTES), &tm_a, 0, (int32_t)(ta * OZ_BM), fb);
-              tma_load_2d(smem_u32(sb + st * OZ_TILE_BYTES), &tm_b, 0, (int32_t)(tb * OZ_BN), fb);
-            }
-          }
+        // slice tiles hold 128 rows; this item's B box is the 64-row half nt & 1 of tile nt / 2
+        const int64_t ta0 = s.ta_base + (int64_t)wk.mt * s.nkc, tb0 = s.tb_base + (int64_t)(wk.nt >> 1) * s.nkc;
+        const int32_t brow = (wk.nt & 1) * OZ_BN;
+        const int64_t sa_str = (int64_t)s.nmt * s.nkc, sb_str = (int64_t)s.nnt * s.nkc;  // tiles per slice
+        for (int kc = 0; kc < s.nkc && !*abort_flag; ++kc, ++it) {
+          const uint32_t st = it % nstages, ph = (it / nstages) & 1;
+          if (!mbar_wait(smem_u32(&ss->empty[st]), ph ^ 1, abort_flag)) break;
+          const uint32_t fb = smem_u32(&ss->full[st]);
+          mbar_expect_tx(fb, stage_bytes);
+          const uint32_t dst = smem_u32(base + st * stage_bytes);
+          for (int i = 0; i < nslices; ++i)
+            tma_load_2d(dst + i * OZ_A_BYTES, &tm_a, 0, (int32_t)((ta0 + i * sa_str + kc) * OZ_TROWS), fb);
+          for (int j = 0; j < nslices; ++j)
+            tma_load_2d(dst + b_off + j * OZ_B_BYTES, &tm_b, 0,
+                        (int32_t)((tb0 + j * sb_str + kc) * OZ_TROWS + brow), fb);
         }
       }
       // drain: every issued stage must have landed before this CTA may exit (bounded)
-      for (uint32_t k = (it > OZ_STAGES ? it - OZ_STAGES : 0); k < it; ++k) {
+      for (uint32_t k = (it > nstages ? it - nstages : 0); k < it; ++k) {
         volatile int never = 0;
-        mbar_wait(smem_u32(&ss->full[k % OZ_STAGES]), (k / OZ_STAGES) & 1, &never);
+        mbar_wait(smem_u32(&ss->full[k % nstages]), (k / nstages) & 1, &never);
       }
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      uint32_t it = 0, tile = 0;
-      const uint32_t idesc = idesc_bf16(OZ_BM, OZ_BN);
+      uint32_t it = 0, seg = 0;
       for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
         const OzWork wk = work[w];
         const OzSector s = secs[wk.sector];
-        for (int kc0 = 0; kc0 < s.nkc && !*abort_flag; kc0 += OZ_SEG_KC, ++tile) {
+        const uint32_t idesc = idesc_bf16(OZ_BM, wk.nw);
+        for (int kc0 = 0; kc0 < s.nkc && !*abort_flag; kc0 += OZ_SEG_KC, ++seg) {
           const int kc1 = min(s.nkc, kc0 + OZ_SEG_KC);
-          if (!mbar_wait(smem_u32(&ss->acc_empty), (tile & 1) ^ 1, abort_flag)) break;
+          const uint32_t buf = seg & 1;
+          if (!mbar_wait(smem_u32(&ss->acc_empty[buf]), ((seg >> 1) & 1) ^ 1, abort_flag)) break;
           tc_fence_after();
-          for (int p = 0; p < pairs.n && !*abort_flag; ++p) {
-            const uint32_t dcol = tmem + (uint32_t)pairs.lvl[p] * OZ_BN;
-            const bool first_pair = pairs.first[pairs.lvl[p]] == p;
-            for (int kc = kc0; kc < kc1; ++kc, ++it) {
-              const uint32_t st = it % OZ_STAGES, ph = (it / OZ_STAGES) & 1;
-              if (!mbar_wait(smem_u32(&ss->full[st]), ph, abort_flag)) break;
-              tc_fence_after();
-              const uint32_t a0 = smem_u32(sa + st * OZ_TILE_BYTES), b0 = smem_u32(sb + st * OZ_TILE_BYTES);
-#pragma unroll
-              for (int k16 = 0; k16 < OZ_BK / 16; ++k16) {
-                const uint32_t acc = (first_pair && kc == kc0 && k16 == 0) ? 0u : 1u;
-                tc_mma_bf16(dcol, smem_desc_k_sw128(a0 + k16 * 32), smem_desc_k_sw128(b0 + k16 * 32), idesc, acc);
-              }
-              tc_commit(smem_u32(&ss->empty[st]));  // frees the stage once these MMAs are done
-            }
+          const uint32_t acc0 = tmem + buf * (OZ_NACC * OZ_BN);
+          for (int kc = kc0; kc < kc1; ++kc, ++it) {
+            const uint32_t st = it % nstages, ph = (it / nstages) & 1;
+            if (!mbar_wait(smem_u32(&ss->full[st]), ph, abort_flag)) break;
+            tc_fence_after();
+            oz_issue(nslices, acc0, smem_u32(base + st * stage_bytes), idesc, kc == kc0);
+            tc_commit(smem_u32(&ss->empty[st]));  // frees the stage once these MMAs are done
           }
-          tc_commit(smem_u32(&ss->acc_full));  // accumulators of this (item, segment) complete
+          tc_commit(smem_u32(&ss->acc_full[buf]));  // accumulators of this (item, segment) complete
         }
       }
       // make sure no MMA is still running before TMEM is released (bounded)
@@ -435,59 +464,61 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   } else {
     // ---------------------------------------------------------------- epilogue (warps 2..9)
     const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
-    const int half = (warp - 2) >> 2;          // which 64 of the 128 columns
+    const int half = (warp - 2) >> 2;          // which 32 of the 64 columns
     const int row = quad * 32 + lane;
     // accumulators of levels without any slice pair (fewer than 4 slices) are never written
     const bool has1 = pairs.first[1] >= 0, has2 = pairs.first[2] >= 0, has3 = pairs.first[3] >= 0;
-    uint32_t tile = 0;
+    uint32_t seg = 0;
     for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
       const OzWork wk = work[w];
       const OzSector s = secs[wk.sector];
+      const bool active = half * 32 < wk.nw;  // warp-uniform: this half holds output columns
       const int64_t m = (int64_t)wk.mt * OZ_BM + row;
       int em = (m < s.M) ? scale_a[s.sa_off + m] : 0;
       if (em == kNoScale) em = 0;
-      // this warp's 64 column exponents, two per lane, broadcast later with shuffles
-      const int64_t nb = (int64_t)wk.nt * OZ_BN + half * 64;
-      int f0 = (nb + lane < s.N) ? scale_b[s.sb_off + nb + lane] : 0;
-      int f1 = (nb + 32 + lane < s.N) ? scale_b[s.sb_off + nb + 32 + lane] : 0;
-      if (f0 == kNoScale) f0 = 0;
-      if (f1 == kNoScale) f1 = 0;
-      for (int kc0 = 0; kc0 < s.nkc; kc0 += OZ_SEG_KC, ++tile) {
-        if (!mbar_wait(smem_u32(&ss->acc_full), tile & 1, abort_flag)) break;
+      const int64_t nb = (int64_t)wk.nt * OZ_BN + half * 32;
+      int fl = (nb + lane < s.N) ? scale_b[s.sb_off + nb + lane] : 0;
+      if (fl == kNoScale) fl = 0;
+      double* crow = C + s.c_off + m;
+      for (int kc0 = 0; kc0 < s.nkc; kc0 += OZ_SEG_KC, ++seg) {
+        const uint32_t buf = seg & 1;
+        if (!mbar_wait(smem_u32(&ss->acc_full[buf]), (seg >> 1) & 1, abort_flag)) break;
         tc_fence_after();
-        const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + half * 64;
+        if (active) {
+          const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + buf * (OZ_NACC * OZ_BN) + half * 32;
 #pragma unroll 1
-        for (int ch = 0; ch < 4; ++ch) {
-          uint32_t r0[16], r1[16], r2[16], r3[16];
-          tc_ld16(lane_addr + 0 * OZ_BN + ch * 16, r0);
-          tc_ld16(lane_addr + 1 * OZ_BN + ch * 16, r1);
-          tc_ld16(lane_addr + 2 * OZ_BN + ch * 16, r2);
-          tc_ld16(lane_addr + 3 * OZ_BN + ch * 16, r3);
-          tc_wait_ld();
+          for (int ch = 0; ch < 2; ++ch) {
+            uint32_t r0[16], r1[16], r2[16], r3[16];
+            tc_ld16(lane_addr + 0 * OZ_BN + ch * 16, r0);
+            tc_ld16(lane_addr + 1 * OZ_BN + ch * 16, r1);
+            tc_ld16(lane_addr + 2 * OZ_BN + ch * 16, r2);
+            tc_ld16(lane_addr + 3 * OZ_BN + ch * 16, r3);
+            tc_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int cj = ch * 16 + j;  // column within this warp's 64
-            const int fn = __shfl_sync(0xffffffffu, (cj < 32) ? f0 : f1, cj & 31);
-            const int64_t n = nb + cj;
-            if (m < s.M && n < s.N) {
-              float hi, lo, e1, e2;
-              const float a1 = has1 ? __uint_as_float(r1[j]) : 0.f;
-              const float a2 = has2 ? __uint_as_float(r2[j]) : 0.f;
-              const float a3 = has3 ? __uint_as_float(r3[j]) : 0.f;
-              two_sum(__uint_as_float(r0[j]), a1, hi, lo);
-              two_sum(hi, a2, hi, e1);
-              lo = lo + e1;
-              two_sum(hi, lo, hi, e2);
-              lo = e2 + a3;
-              const double v = scale_pow2(f32_to_f64(hi) + f32_to_f64(lo), em + fn);
-              double* dst = C + s.c_off + m + n * s.M;
-              *dst = (kc0 == 0) ? v : *dst + v;
+            for (int j = 0; j < 16; ++j) {
+              const int cj = ch * 16 + j;
+              const int fn = __shfl_sync(0xffffffffu, fl, cj);
+              const int64_t n = nb + cj;
+              if (m < s.M && n < s.N) {
+                float hi, lo, e1, e2;
+                const float a1 = has1 ? __uint_as_float(r1[j]) : 0.f;
+                const float a2 = has2 ? __uint_as_float(r2[j]) : 0.f;
+                const float a3 = has3 ? __uint_as_float(r3[j]) : 0.f;
+                two_sum(__uint_as_float(r0[j]), a1, hi, lo);
+                two_sum(hi, a2, hi, e1);
+                lo = __fadd_rn(lo, e1);
+                two_sum(hi, lo, hi, e2);
+                lo = __fadd_rn(e2, a3);
+                const double v = scale_pow2(f32_to_f64(hi) + f32_to_f64(lo), em + fn);
+                double* dst = crow + n * s.M;
+                *dst = (kc0 == 0) ? v : *dst + v;
+              }
             }
           }
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&ss->acc_empty));
+        if (lane == 0) mbar_arrive(smem_u32(&ss->acc_empty[buf]));
       }
     }
   }
@@ -522,23 +553,21 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D view [ntiles * 128 rows][64 BF16] with 128 x 64 boxes and 128-byte swizzle.
-int make_tile_map(CUtensorMap* map, void* base, int64_t ntiles) {
+// 2-D view [ntiles * 128 rows][32 BF16] with box_rows x 32 boxes and 64-byte swizzle.
+int make_tile_map(CUtensorMap* map, void* base, int64_t ntiles, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return TK_ERR_CUDA;
-  cuuint64_t dims[2] = {(cuuint64_t)OZ_BK, (cuuint64_t)(ntiles * OZ_BM)};
+  cuuint64_t dims[2] = {(cuuint64_t)OZ_BK, (cuuint64_t)(ntiles * OZ_TROWS)};
   cuuint64_t strides[1] = {(cuuint64_t)OZ_BK * 2};
-  cuuint32_t box[2] = {(cuuint32_t)OZ_BK, (cuuint32_t)OZ_BM};
+  cuuint32_t box[2] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? TK_OK : TK_ERR_CUDA;
 }
 
 size_t al1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
-
-constexpr size_t OZ_SMEM_BYTES = 2 * OZ_STAGES * OZ_TILE_BYTES + sizeof(OzSmem) + 1024;
 
 }  // namespace
 
@@ -578,8 +607,8 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
     s.a_off = it.a_off;
     s.b_off = it.b_off;
     s.c_off = it.c_off;
-    s.nmt = (int32_t)((it.M + OZ_BM - 1) / OZ_BM);
-    s.nnt = (int32_t)((it.N + OZ_BN - 1) / OZ_BN);
+    s.nmt = (int32_t)((it.M + OZ_TROWS - 1) / OZ_TROWS);  // 128-row slice tiles of A~ and of B~^T
+    s.nnt = (int32_t)((it.N + OZ_TROWS - 1) / OZ_TROWS);
     s.nkc = (int32_t)((it.K + OZ_BK - 1) / OZ_BK);
     s.ta_base = L->ntiles_a;
     s.tb_base = L->ntiles_b;
@@ -592,7 +621,11 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
     const int32_t sid = (int32_t)L->sectors.size();
     L->sectors.push_back(s);
     for (int mt = 0; mt < s.nmt; ++mt)
-      for (int nt = 0; nt < s.nnt; ++nt) wcost.push_back({(double)s.nkc, OzWork{sid, mt, nt, 0}});
+      for (int nt = 0; nt < (int)((s.N + OZ_BN - 1) / OZ_BN); ++nt) {  // 64-column output tiles
+        const int64_t left = s.N - (int64_t)nt * OZ_BN;
+        const int32_t nw = (int32_t)std::min<int64_t>(OZ_BN, (left + 15) / 16 * 16);
+        wcost.push_back({(double)s.nkc * nw, OzWork{sid, mt, nt, nw}});
+      }
     for (int rt = 0; rt < s.nmt; ++rt)
       for (int kc = 0; kc < s.nkc; ++kc) slice_jobs.push_back(OzJob{sid, 0, rt, kc});
     for (int rt = 0; rt < s.nnt; ++rt)
@@ -640,9 +673,12 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
     ctx->last_error = "split-precision workspace must be 16-byte aligned";
     return TK_ERR_WORKSPACE;
   }
+  const size_t smem = oz_smem_bytes(L->slices);
   static bool attr_set[64] = {false};
   if (ctx->device < 64 && !attr_set[ctx->device]) {
-    if (cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM_BYTES) != cudaSuccess) {
+    size_t most = 0;  // the largest need over every slice count this kernel accepts
+    for (int sl = 2; sl <= OZ_MAX_SLICES; ++sl) most = std::max(most, oz_smem_bytes(sl));
+    if (cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) != cudaSuccess) {
       ctx->last_error = "cannot reserve shared memory for the split-precision GEMM";
       return TK_ERR_CUDA;
     }
@@ -654,7 +690,7 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
   int32_t* sa = (int32_t*)(w + L->off_sa);
   int32_t* sb = (int32_t*)(w + L->off_sb);
   CUtensorMap ma, mb;
-  if (make_tile_map(&ma, ta, L->ntiles_a) != TK_OK || make_tile_map(&mb, tb, L->ntiles_b) != TK_OK) {
+  if (make_tile_map(&ma, ta, L->ntiles_a, OZ_BM) != TK_OK || make_tile_map(&mb, tb, L->ntiles_b, OZ_BN) != TK_OK) {
     ctx->last_error = "cuTensorMapEncodeTiled failed";
     return TK_ERR_CUDA;
   }
@@ -677,8 +713,8 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
   {
     ProfScope prof(ctx, "k_oz_gemm", stream);
     const int grid = (int)std::min<int64_t>(L->nwork, std::max(1, ctx->num_sms));
-    k_oz_gemm<<<grid, OZ_THREADS, OZ_SMEM_BYTES, s>>>(ma, mb, L->d_sectors, L->d_work, (int)L->nwork, L->pairs, sa, sb,
-                                                      (double*)c, ctx->d_status);
+    k_oz_gemm<<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, (int)L->nwork, L->pairs, L->slices, sa,
+                                             sb, (double*)c, ctx->d_status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       ctx->last_error = std::string("k_oz_gemm launch: ") + cudaGetErrorString(e);

@@ -101,10 +101,10 @@ def test_su2_lx_split_precision(gctx):
 
 
 def test_long_inner_dimension_uses_segments(gctx):
-    """K = 1300 > 512: several exact segments added in FP64; ragged M, N tails."""
+    """K = 3000 > 1024: three exact segments added in FP64; ragged M, N tails."""
     api = _api()
-    la = ([({0: 300, 1: 7}, False)], [({0: 1300, 1: 3}, False)])
-    lb = ([({0: 1300, 1: 3}, False)], [({0: 200, 1: 5}, False)])
+    la = ([({0: 300, 1: 7}, False)], [({0: 3000, 1: 3}, False)])
+    lb = ([({0: 3000, 1: 3}, False)], [({0: 200, 1: 5}, False)])
     oa, ob = ostruct("U1", la), ostruct("U1", lb)
     xa, xb = wl.normal(5, oa.numel), wl.normal(6, ob.numel)
     cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
@@ -127,8 +127,10 @@ def test_scales_span_many_binades(gctx):
     A, B = _tm(gctx, "U1", la), _tm(gctx, "U1", lb)
     plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), gemm="ozaki")
     c = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda())
-    # the scheme keeps 7 s bits below each row's and each column's largest magnitude: its error
-    # is bounded by a small multiple of 2^(-7 s) K max_k|a_mk| max_k|b_kn| per entry
+    # Per-row (per-column) scales 2^e <= 2 max|a| and 7 s fraction bits: each operand entry is off
+    # by at most 2^(-7s) max|a|, two such terms per product; the dropped slice pairs (i + j = s,
+    # s - 1 of them with both digits <= 64, each below 2^12 2^(-7(s+2)) 2^(e_m + f_n)) add at most
+    # (s - 1) 2^(-7s) max|a| max|b| per k.  Together: below 8 2^(-7s) K max|a| max|b| for s = 6.
     got = c.cpu().numpy()
     for (ca, ra, ka, oa_), (cb, rb, kb, ob_), (cc, rc, kc, oc) in zip(oa.blocks, ob.blocks, cs.blocks):
         am = xa[oa_:oa_ + ra * ka].reshape(ka, ra).T
