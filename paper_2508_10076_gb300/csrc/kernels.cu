@@ -490,6 +490,10 @@ __device__ __forceinline__ void gemm_rows(const GemmItem& it, const GemmTile& tl
 // a = hi + lo to ~2^-53, by integer operations on the FP64 bit pattern: hi keeps the sign, the
 // exponent and the top 23 stored mantissa bits; lo is the remaining 29 bits converted to FP32.
 // Values outside the normal FP32 range take the conversion instructions.
+__device__ __noinline__ void df_split_slow(double a, float& hi, float& lo) {
+  hi = __double2float_rn(a);
+  lo = __double2float_rn(a - (double)hi);
+}
 __device__ __forceinline__ void df_split(double a, float& hi, float& lo) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(a);
   const int ex = (int)((b >> 52) & 0x7FF);
@@ -499,9 +503,8 @@ __device__ __forceinline__ void df_split(double a, float& hi, float& lo) {
     return;
   }
   const int ef = ex - 1023 + 127;
-  if (ef <= 52 || ef >= 255) {  // lo's scale 2^(ex-1075) must be a normal FP32
-    hi = __double2float_rn(a);
-    lo = __double2float_rn(a - (double)hi);
+  if (ef <= 52 || ef >= 255) {  // lo's scale 2^(ex-1075) must be a normal FP32: rare, out of line
+    df_split_slow(a, hi, lo);
     return;
   }
   const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;

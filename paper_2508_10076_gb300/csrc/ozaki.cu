@@ -39,16 +39,16 @@
 namespace tk {
 namespace {
 
-constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32;
+constexpr int OZ_BM = 128, OZ_BK = 32;              // k-chunk: two MMA K steps
+constexpr int OZ_BN_WIDE = 128, OZ_BN_NARROW = 64;  // output tile widths (one / two TMEM buffers)
 constexpr int OZ_TROWS = 128;                     // rows of a slice tile in memory (A: m, B: n)
-constexpr int OZ_TILE_BYTES = OZ_TROWS * OZ_BK * 2;  // slice tiles are 128 x 32 BF16 (8 KB)
+constexpr int OZ_TILE_BYTES = OZ_TROWS * OZ_BK * 2;  // slice tiles are 128 x 32 BF16 (8 KB, 64-byte rows)
 constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;     // A box in shared memory: 128 x 32
-constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;     // B box in shared memory: 64 x 32
-constexpr int OZ_STAGES = 3;                      // a stage holds all s A and s B boxes of a k-chunk
+constexpr int OZ_MAX_STAGES = 4;                  // a stage holds all s A and s B boxes of a k-chunk
 constexpr int OZ_SEG_KC = 32;                     // k-chunks per exact segment (K <= 1024)
 constexpr int OZ_NACC = 4;
-constexpr int OZ_TMEM_COLS = 512;                 // 2 buffers x 4 accumulators x 64 FP32 columns
-constexpr int OZ_EPI_WARPS = 8;                   // two per TMEM lane quadrant
+constexpr int OZ_TMEM_COLS = 512;                 // 4 accumulators x 128 columns, or 2 x 4 x 64
+constexpr int OZ_EPI_WARPS = 16;                  // four per TMEM lane quadrant
 constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;  // producer warp, MMA warp, epilogue warps
 constexpr int OZ_MAX_SLICES = 7;
 constexpr int OZ_MAX_PAIRS = OZ_MAX_SLICES * (OZ_MAX_SLICES + 1) / 2;
@@ -63,7 +63,7 @@ struct OzSector {
   int32_t nmt, nnt, nkc, pad;  // 128-row slice tiles of A~ / B~^T, 32-deep k-chunks
 };
 struct OzWork {
-  int32_t sector, mt, nt, nw;  // nw: columns of this tile (multiple of 16, <= OZ_BN)
+  int32_t sector, mt, nt, nw;  // nw: columns of this tile (multiple of 16, <= the tile width)
 };
 struct OzJob {  // slicer / scale job
   int32_t sector, operand, r0, kc;
@@ -79,6 +79,7 @@ struct OzLayout {
   int64_t ntiles_a = 0, ntiles_b = 0, nrows_a = 0, ncols_b = 0;
   size_t off_ta = 0, off_tb = 0, off_sa = 0, off_sb = 0, bytes = 0;
   int slices = OZ_DEFAULT_SLICES;
+  int bn = OZ_BN_NARROW;  // output tile width of this launch
   OzPairs pairs;
   int64_t nwork = 0, nslice_jobs = 0, nscale_jobs = 0;
   OzSector* d_sectors = nullptr;
@@ -149,12 +150,10 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uin
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -177,13 +176,22 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
          | ((uint32_t)(m >> 4) << 24); // M / 16
 }
 
-// v * 2^e, exact, by adding e to the exponent field when the result stays a normal number.
-__device__ __forceinline__ double scale_pow2(double v, int e) {
-  const long long b = __double_as_longlong(v);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex != 0 && ex + e > 0 && ex + e < 0x7FF) return __longlong_as_double(b + ((long long)e << 52));
-  if (v == 0.0) return v;
-  return ldexp(v, e);
+__device__ __noinline__ double scale_pow2_slow(double v, int e) { return ldexp(v, e); }
+
+// f * 2^sc as FP64, built from the FP32 bit pattern by adding sc to the exponent field: exact.
+// ok is cleared when f is neither zero nor normal or the result leaves the normal FP64 range.
+__device__ __forceinline__ double f32_scaled_to_f64(float f, int sc, bool& ok) {
+  const uint32_t u = __float_as_uint(f);
+  const int ex = (int)((u >> 23) & 0xFFu);
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if ((u << 1) == 0u) return __longlong_as_double((long long)sign);
+  const int e64 = ex + 896 + sc;
+  ok = ok && ex != 0 && ex != 0xFF && e64 > 0 && e64 < 0x7FF;
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)(e64 & 0x7FF) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+__device__ __noinline__ double f32_pair_scaled_slow(float hi, float lo, int sc) {
+  return scale_pow2_slow(f32_to_f64(hi) + f32_to_f64(lo), sc);
 }
 
 // round(v * 2^shift) to the nearest integer (ties away from zero) from the bit pattern of v; the
@@ -288,7 +296,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ s
   }
   const int64_t nrt = op == 0 ? s.nmt : s.nnt;
   const int64_t tile0 = (op == 0 ? s.ta_base : s.tb_base) + rt * s.nkc + jb.kc;  // slice 0
-  const int64_t slice_stride = nrt * s.nkc * (int64_t)(OZ_TROWS * OZ_BK);             // elements
+  const int64_t slice_stride = nrt * s.nkc * (int64_t)(OZ_TROWS * OZ_BK);  // elements
   __nv_bfloat16* dst0 = (op == 0 ? tiles_a : tiles_b) + tile0 * (OZ_TROWS * OZ_BK) + kl;
   const int32_t* scl = op == 0 ? scale_a + s.sa_off : scale_b + s.sb_off;
 #pragma unroll 4
@@ -315,26 +323,32 @@ __global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ s
 
 // ------------------------------------------------------------------ the persistent GEMM
 struct OzSmem {
-  uint64_t full[OZ_STAGES], empty[OZ_STAGES];
-  uint64_t acc_full[2], acc_empty[2], drain;
+  uint64_t full[OZ_MAX_STAGES], empty[OZ_MAX_STAGES];
+  uint64_t acc_full[2], acc_empty[2], drain;  // one or two TMEM buffers
   uint32_t tmem_base;
   int abort_flag;
 };
 
-// Shared memory: OZ_STAGES stages of [A_0 .. A_{s-1} | B_0 .. B_{s-1}] boxes, then OzSmem.
-__host__ __device__ constexpr size_t oz_stage_bytes(int s) { return (size_t)s * (OZ_A_BYTES + OZ_B_BYTES); }
-__host__ __device__ constexpr int oz_stages(int s) { return s <= 6 ? OZ_STAGES : 2; }
-__host__ __device__ constexpr size_t oz_smem_bytes(int s) {
-  return oz_stages(s) * oz_stage_bytes(s) + sizeof(OzSmem) + 1024;  // + alignment slack
+// Shared memory: stages of [A_0 .. A_{s-1} | B_0 .. B_{s-1}] boxes (A 128 x 32, B BN x 32), then
+// OzSmem: as many stages as fit in 227 KB (at most four).
+__host__ __device__ constexpr size_t oz_stage_bytes(int s, int bn) { return (size_t)s * (OZ_A_BYTES + bn * OZ_BK * 2); }
+__host__ __device__ constexpr int oz_stages(int s, int bn) {
+  return (int)((232448 - sizeof(OzSmem) - 1024) / oz_stage_bytes(s, bn)) < OZ_MAX_STAGES
+             ? (int)((232448 - sizeof(OzSmem) - 1024) / oz_stage_bytes(s, bn))
+             : OZ_MAX_STAGES;
+}
+__host__ __device__ constexpr size_t oz_smem_bytes(int s, int bn) {
+  return oz_stages(s, bn) * oz_stage_bytes(s, bn) + sizeof(OzSmem) + 1024;  // + alignment slack
 }
 
 // Every slice-pair MMA of one resident stage, unrolled for S slices: pairs grouped by
 // accumulator level (0, 1, 2, >= 3); the first MMA of a level in a segment's first k-chunk
 // overwrites its accumulator.  Descriptors differ from the stage's base descriptor only in the
 // start-address field, so each operand offset is an added constant.
-template <int S>
+template <int S, int BN>
 __device__ __forceinline__ void oz_issue_stage(uint32_t acc0, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                                bool first_kc) {
+  constexpr int B_BYTES = BN * OZ_BK * 2;
 #pragma unroll
   for (int l = 0; l < OZ_NACC; ++l) {
 #pragma unroll
@@ -345,26 +359,30 @@ __device__ __forceinline__ void oz_issue_stage(uint32_t acc0, uint64_t adesc, ui
         const bool first_of_level = (l < OZ_NACC - 1) ? (i == 0) : (i == 0 && j == OZ_NACC - 1);
 #pragma unroll
         for (int k16 = 0; k16 < OZ_BK / 16; ++k16)
-          tc_mma_bf16(acc0 + l * OZ_BN, adesc + (uint64_t)((i * OZ_A_BYTES + k16 * 32) >> 4),
-                      bdesc + (uint64_t)((S * OZ_A_BYTES + j * OZ_B_BYTES + k16 * 32) >> 4), idesc,
+          tc_mma_bf16(acc0 + l * BN, adesc + (uint64_t)((i * OZ_A_BYTES + k16 * 32) >> 4),
+                      bdesc + (uint64_t)((S * OZ_A_BYTES + j * B_BYTES + k16 * 32) >> 4), idesc,
                       (first_kc && first_of_level && k16 == 0) ? 0u : 1u);
       }
     }
   }
 }
 
+template <int BN>
 __device__ __forceinline__ void oz_issue(int s, uint32_t acc0, uint32_t sbase, uint32_t idesc, bool first_kc) {
   const uint64_t d = smem_desc_k_sw64(sbase);
   switch (s) {
-    case 2: oz_issue_stage<2>(acc0, d, d, idesc, first_kc); break;
-    case 3: oz_issue_stage<3>(acc0, d, d, idesc, first_kc); break;
-    case 4: oz_issue_stage<4>(acc0, d, d, idesc, first_kc); break;
-    case 5: oz_issue_stage<5>(acc0, d, d, idesc, first_kc); break;
-    case 6: oz_issue_stage<6>(acc0, d, d, idesc, first_kc); break;
-    default: oz_issue_stage<7>(acc0, d, d, idesc, first_kc); break;
+    case 2: oz_issue_stage<2, BN>(acc0, d, d, idesc, first_kc); break;
+    case 3: oz_issue_stage<3, BN>(acc0, d, d, idesc, first_kc); break;
+    case 4: oz_issue_stage<4, BN>(acc0, d, d, idesc, first_kc); break;
+    case 5: oz_issue_stage<5, BN>(acc0, d, d, idesc, first_kc); break;
+    case 6: oz_issue_stage<6, BN>(acc0, d, d, idesc, first_kc); break;
+    default: oz_issue_stage<7, BN>(acc0, d, d, idesc, first_kc); break;
   }
 }
 
+// BN = 128: one TMEM buffer (4 x 128 columns), the MMAs wait for the epilogue between tiles;
+// BN = 64: two buffers, the epilogue of one tile overlaps the MMAs of the next.
+template <int BN>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
               const OzSector* __restrict__ secs, const OzWork* __restrict__ work, int nwork,
@@ -372,8 +390,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               double* __restrict__ C, int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char dyn[];
   unsigned char* base = (unsigned char*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
-  const uint32_t stage_bytes = (uint32_t)oz_stage_bytes(nslices);
-  const uint32_t nstages = (uint32_t)oz_stages(nslices);
+  constexpr int NBUF = OZ_TMEM_COLS / (OZ_NACC * BN);
+  constexpr int B_BYTES = BN * OZ_BK * 2;
+  constexpr int SUB = OZ_TROWS / BN;  // B boxes per 128-row slice tile
+  const uint32_t stage_bytes = (uint32_t)oz_stage_bytes(nslices, BN);
+  const uint32_t nstages = (uint32_t)oz_stages(nslices, BN);
   const uint32_t b_off = (uint32_t)nslices * OZ_A_BYTES;  // B boxes follow the A boxes in a stage
   OzSmem* ss = reinterpret_cast<OzSmem*>(base + nstages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -384,7 +405,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_init(smem_u32(&ss->full[s]), 1);
       mbar_init(smem_u32(&ss->empty[s]), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NBUF; ++b) {
       mbar_init(smem_u32(&ss->acc_full[b]), 1);
       mbar_init(smem_u32(&ss->acc_empty[b]), OZ_EPI_WARPS);
     }
@@ -409,9 +430,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
         const OzWork wk = work[w];
         const OzSector s = secs[wk.sector];
-        // slice tiles hold 128 rows; this item's B box is the 64-row half nt & 1 of tile nt / 2
-        const int64_t ta0 = s.ta_base + (int64_t)wk.mt * s.nkc, tb0 = s.tb_base + (int64_t)(wk.nt >> 1) * s.nkc;
-        const int32_t brow = (wk.nt & 1) * OZ_BN;
+        // slice tiles hold 128 rows; this item's B box is part nt % SUB of tile nt / SUB
+        const int64_t ta0 = s.ta_base + (int64_t)wk.mt * s.nkc, tb0 = s.tb_base + (int64_t)(wk.nt / SUB) * s.nkc;
+        const int32_t brow = (wk.nt % SUB) * BN;
         const int64_t sa_str = (int64_t)s.nmt * s.nkc, sb_str = (int64_t)s.nnt * s.nkc;  // tiles per slice
         for (int kc = 0; kc < s.nkc && !*abort_flag; ++kc, ++it) {
           const uint32_t st = it % nstages, ph = (it / nstages) & 1;
@@ -422,7 +443,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           for (int i = 0; i < nslices; ++i)
             tma_load_2d(dst + i * OZ_A_BYTES, &tm_a, 0, (int32_t)((ta0 + i * sa_str + kc) * OZ_TROWS), fb);
           for (int j = 0; j < nslices; ++j)
-            tma_load_2d(dst + b_off + j * OZ_B_BYTES, &tm_b, 0,
+            tma_load_2d(dst + b_off + j * B_BYTES, &tm_b, 0,
                         (int32_t)((tb0 + j * sb_str + kc) * OZ_TROWS + brow), fb);
         }
       }
@@ -442,15 +463,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const uint32_t idesc = idesc_bf16(OZ_BM, wk.nw);
         for (int kc0 = 0; kc0 < s.nkc && !*abort_flag; kc0 += OZ_SEG_KC, ++seg) {
           const int kc1 = min(s.nkc, kc0 + OZ_SEG_KC);
-          const uint32_t buf = seg & 1;
-          if (!mbar_wait(smem_u32(&ss->acc_empty[buf]), ((seg >> 1) & 1) ^ 1, abort_flag)) break;
+          const uint32_t buf = seg % NBUF;
+          if (!mbar_wait(smem_u32(&ss->acc_empty[buf]), ((seg / NBUF) & 1) ^ 1, abort_flag)) break;
           tc_fence_after();
-          const uint32_t acc0 = tmem + buf * (OZ_NACC * OZ_BN);
+          const uint32_t acc0 = tmem + buf * (OZ_NACC * BN);
           for (int kc = kc0; kc < kc1; ++kc, ++it) {
             const uint32_t st = it % nstages, ph = (it / nstages) & 1;
             if (!mbar_wait(smem_u32(&ss->full[st]), ph, abort_flag)) break;
             tc_fence_after();
-            oz_issue(nslices, acc0, smem_u32(base + st * stage_bytes), idesc, kc == kc0);
+            oz_issue<BN>(nslices, acc0, smem_u32(base + st * stage_bytes), idesc, kc == kc0);
             tc_commit(smem_u32(&ss->empty[st]));  // frees the stage once these MMAs are done
           }
           tc_commit(smem_u32(&ss->acc_full[buf]));  // accumulators of this (item, segment) complete
@@ -462,9 +483,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_wait(smem_u32(&ss->drain), 0, &never);
     }
   } else {
-    // ---------------------------------------------------------------- epilogue (warps 2..9)
+    // ---------------------------------------------------------------- epilogue (warps 2..17)
+    constexpr int WCOLS = BN / 4;              // columns per warp: four warps per lane quadrant
     const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
-    const int half = (warp - 2) >> 2;          // which 32 of the 64 columns
+    const int grp = (warp - 2) >> 2;           // which quarter of the tile's columns
     const int row = quad * 32 + lane;
     // accumulators of levels without any slice pair (fewer than 4 slices) are never written
     const bool has1 = pairs.first[1] >= 0, has2 = pairs.first[2] >= 0, has3 = pairs.first[3] >= 0;
@@ -472,47 +494,52 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
       const OzWork wk = work[w];
       const OzSector s = secs[wk.sector];
-      const bool active = half * 32 < wk.nw;  // warp-uniform: this half holds output columns
+      const int c0 = grp * WCOLS;                 // first column of this warp within the tile
+      const bool active = c0 < wk.nw;             // warp-uniform
       const int64_t m = (int64_t)wk.mt * OZ_BM + row;
-      int em = (m < s.M) ? scale_a[s.sa_off + m] : 0;
+      const bool row_ok = m < s.M;
+      int em = row_ok ? scale_a[s.sa_off + m] : 0;
       if (em == kNoScale) em = 0;
-      const int64_t nb = (int64_t)wk.nt * OZ_BN + half * 32;
-      int fl = (nb + lane < s.N) ? scale_b[s.sb_off + nb + lane] : 0;
+      const int64_t nb = (int64_t)wk.nt * BN + c0;
+      const int64_t left = s.N - nb;
+      const int ncols = left < WCOLS ? (int)left : WCOLS;  // valid columns of this warp (may be <= 0)
+      int fl = (lane < ncols) ? scale_b[s.sb_off + nb + lane] : 0;  // WCOLS <= 32: one per lane
       if (fl == kNoScale) fl = 0;
-      double* crow = C + s.c_off + m;
+      double* crow = C + s.c_off + nb * s.M + m;
       for (int kc0 = 0; kc0 < s.nkc; kc0 += OZ_SEG_KC, ++seg) {
-        const uint32_t buf = seg & 1;
-        if (!mbar_wait(smem_u32(&ss->acc_full[buf]), (seg >> 1) & 1, abort_flag)) break;
+        const uint32_t buf = seg % NBUF;
+        if (!mbar_wait(smem_u32(&ss->acc_full[buf]), (seg / NBUF) & 1, abort_flag)) break;
         tc_fence_after();
         if (active) {
-          const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + buf * (OZ_NACC * OZ_BN) + half * 32;
+          const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + buf * (OZ_NACC * BN) + c0;
 #pragma unroll 1
-          for (int ch = 0; ch < 2; ++ch) {
-            uint32_t r0[16], r1[16], r2[16], r3[16];
-            tc_ld16(lane_addr + 0 * OZ_BN + ch * 16, r0);
-            tc_ld16(lane_addr + 1 * OZ_BN + ch * 16, r1);
-            tc_ld16(lane_addr + 2 * OZ_BN + ch * 16, r2);
-            tc_ld16(lane_addr + 3 * OZ_BN + ch * 16, r3);
+          for (int ch = 0; ch < WCOLS / 8; ++ch) {
+            if (ch * 8 >= ncols) break;  // warp-uniform
+            uint32_t r0[8], r1[8], r2[8], r3[8];
+            tc_ld8(lane_addr + 0 * BN + ch * 8, r0);
+            tc_ld8(lane_addr + 1 * BN + ch * 8, r1);
+            tc_ld8(lane_addr + 2 * BN + ch * 8, r2);
+            tc_ld8(lane_addr + 3 * BN + ch * 8, r3);
             tc_wait_ld();
+            double* dst = crow + (int64_t)(ch * 8) * s.M;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int cj = ch * 16 + j;
-              const int fn = __shfl_sync(0xffffffffu, fl, cj);
-              const int64_t n = nb + cj;
-              if (m < s.M && n < s.N) {
-                float hi, lo, e1, e2;
-                const float a1 = has1 ? __uint_as_float(r1[j]) : 0.f;
-                const float a2 = has2 ? __uint_as_float(r2[j]) : 0.f;
-                const float a3 = has3 ? __uint_as_float(r3[j]) : 0.f;
-                two_sum(__uint_as_float(r0[j]), a1, hi, lo);
-                two_sum(hi, a2, hi, e1);
-                lo = __fadd_rn(lo, e1);
-                two_sum(hi, lo, hi, e2);
-                lo = __fadd_rn(e2, a3);
-                const double v = scale_pow2(f32_to_f64(hi) + f32_to_f64(lo), em + fn);
-                double* dst = crow + n * s.M;
-                *dst = (kc0 == 0) ? v : *dst + v;
-              }
+            for (int j = 0; j < 8; ++j, dst += s.M) {
+              const int fn = __shfl_sync(0xffffffffu, fl, ch * 8 + j);
+              if (!row_ok || ch * 8 + j >= ncols) continue;
+              float hi, lo, e1, e2;
+              const float a1 = has1 ? __uint_as_float(r1[j]) : 0.f;
+              const float a2 = has2 ? __uint_as_float(r2[j]) : 0.f;
+              const float a3 = has3 ? __uint_as_float(r3[j]) : 0.f;
+              two_sum(__uint_as_float(r0[j]), a1, hi, lo);
+              two_sum(hi, a2, hi, e1);
+              lo = __fadd_rn(lo, e1);
+              two_sum(hi, lo, hi, e2);
+              lo = __fadd_rn(e2, a3);
+              bool ok = true;
+              const int sc = em + fn;
+              double v = f32_scaled_to_f64(hi, sc, ok) + f32_scaled_to_f64(lo, sc, ok);
+              if (!ok) v = f32_pair_scaled_slow(hi, lo, sc);
+              *dst = (kc0 == 0) ? v : *dst + v;
             }
           }
         }
@@ -597,6 +624,19 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
   std::vector<OzWork> work;
   std::vector<OzJob> slice_jobs, scale_jobs;
   std::vector<std::pair<double, OzWork>> wcost;
+  // Tile width: 128-column tiles read 25% less shared memory per MMA flop (8 KB per 128x128x16
+  // MMA instead of 6 KB per 128x64x16) but hold all of TMEM, so their epilogue stalls the MMAs;
+  // they pay off when the average inner dimension per output tile is long.
+  {
+    double kw = 0, w = 0;
+    for (const GemmItem& it : cp.gemms_oz) {
+      const double area = (double)((it.M + OZ_BM - 1) / OZ_BM) * ((it.N + 127) / 128);
+      kw += area * (double)it.K;
+      w += area;
+    }
+    L->bn = (w > 0 && kw / w >= 512.0) ? OZ_BN_WIDE : OZ_BN_NARROW;
+  }
+  const int bn = L->bn;
   for (size_t g = 0; g < cp.gemms_oz.size(); ++g) {
     const GemmItem& it = cp.gemms_oz[g];
     OzSector s;
@@ -621,10 +661,12 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
     const int32_t sid = (int32_t)L->sectors.size();
     L->sectors.push_back(s);
     for (int mt = 0; mt < s.nmt; ++mt)
-      for (int nt = 0; nt < (int)((s.N + OZ_BN - 1) / OZ_BN); ++nt) {  // 64-column output tiles
-        const int64_t left = s.N - (int64_t)nt * OZ_BN;
-        const int32_t nw = (int32_t)std::min<int64_t>(OZ_BN, (left + 15) / 16 * 16);
-        wcost.push_back({(double)s.nkc * nw, OzWork{sid, mt, nt, nw}});
+      for (int nt = 0; nt < (int)((s.N + bn - 1) / bn); ++nt) {  // bn-column output tiles
+        const int64_t left = s.N - (int64_t)nt * bn;
+        const int32_t nw = (int32_t)std::min<int64_t>(bn, (left + 15) / 16 * 16);
+        // cost key: the tile depth only, so the column tiles of one row tile (which share its A
+        // slices) stay adjacent in the list and run at the same time
+        wcost.push_back({(double)s.nkc, OzWork{sid, mt, nt, nw}});
       }
     for (int rt = 0; rt < s.nmt; ++rt)
       for (int kc = 0; kc < s.nkc; ++kc) slice_jobs.push_back(OzJob{sid, 0, rt, kc});
@@ -673,12 +715,18 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
     ctx->last_error = "split-precision workspace must be 16-byte aligned";
     return TK_ERR_WORKSPACE;
   }
-  const size_t smem = oz_smem_bytes(L->slices);
+  const size_t smem = oz_smem_bytes(L->slices, L->bn);
   static bool attr_set[64] = {false};
   if (ctx->device < 64 && !attr_set[ctx->device]) {
-    size_t most = 0;  // the largest need over every slice count this kernel accepts
-    for (int sl = 2; sl <= OZ_MAX_SLICES; ++sl) most = std::max(most, oz_smem_bytes(sl));
-    if (cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) != cudaSuccess) {
+    size_t wide = 0, narrow = 0;  // the largest need over every slice count this kernel accepts
+    for (int sl = 2; sl <= OZ_MAX_SLICES; ++sl) {
+      wide = std::max(wide, oz_smem_bytes(sl, OZ_BN_WIDE));
+      narrow = std::max(narrow, oz_smem_bytes(sl, OZ_BN_NARROW));
+    }
+    if (cudaFuncSetAttribute(k_oz_gemm<OZ_BN_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_oz_gemm<OZ_BN_NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)narrow) !=
+            cudaSuccess) {
       ctx->last_error = "cannot reserve shared memory for the split-precision GEMM";
       return TK_ERR_CUDA;
     }
@@ -690,7 +738,7 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
   int32_t* sa = (int32_t*)(w + L->off_sa);
   int32_t* sb = (int32_t*)(w + L->off_sb);
   CUtensorMap ma, mb;
-  if (make_tile_map(&ma, ta, L->ntiles_a, OZ_BM) != TK_OK || make_tile_map(&mb, tb, L->ntiles_b, OZ_BN) != TK_OK) {
+  if (make_tile_map(&ma, ta, L->ntiles_a, OZ_BM) != TK_OK || make_tile_map(&mb, tb, L->ntiles_b, L->bn) != TK_OK) {
     ctx->last_error = "cuTensorMapEncodeTiled failed";
     return TK_ERR_CUDA;
   }
@@ -713,8 +761,12 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
   {
     ProfScope prof(ctx, "k_oz_gemm", stream);
     const int grid = (int)std::min<int64_t>(L->nwork, std::max(1, ctx->num_sms));
-    k_oz_gemm<<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, (int)L->nwork, L->pairs, L->slices, sa,
-                                             sb, (double*)c, ctx->d_status);
+    if (L->bn == OZ_BN_WIDE)
+      k_oz_gemm<OZ_BN_WIDE><<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, (int)L->nwork, L->pairs,
+                                                           L->slices, sa, sb, (double*)c, ctx->d_status);
+    else
+      k_oz_gemm<OZ_BN_NARROW><<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, (int)L->nwork, L->pairs,
+                                                             L->slices, sa, sb, (double*)c, ctx->d_status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       ctx->last_error = std::string("k_oz_gemm launch: ") + cudaGetErrorString(e);
