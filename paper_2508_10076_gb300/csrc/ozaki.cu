@@ -64,7 +64,10 @@ struct OzSector {
 };
 struct OzWork {
   int32_t sector, mt, nt, nw;  // nw: columns of this tile (multiple of 16, <= the tile width)
+  int32_t kc_lo, kc_hi;        // k-chunks of this item: the whole depth, or one part of a split
+  int32_t part, nparts, slot, pad;  // split-K: part index, parts of the tile, tile slot (-1: no split)
 };
+constexpr int OZ_MAX_PARTS = 4;
 struct OzJob {  // slicer / scale job
   int32_t sector, operand, r0, kc;
 };
@@ -86,6 +89,9 @@ struct OzLayout {
   OzWork* d_work = nullptr;
   OzJob* d_slice_jobs = nullptr;
   OzJob* d_scale_jobs = nullptr;
+  int32_t nslots = 0;        // split tiles
+  size_t off_part = 0;       // their partial tiles in the workspace
+  int* d_counters = nullptr;  // per (split tile, epilogue warp) arrival counters
 };
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -118,7 +124,8 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait; returns false (and raises the CTA's abort flag) if the phase did not complete.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          bool sleepy = false) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   while (true) {
@@ -128,6 +135,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
       *abort_flag = 1;
       return false;
     }
+    if (sleepy) __nanosleep(200);  // long waits (epilogue warps) leave the issue slots to the MMA warp
   }
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y,
@@ -386,8 +394,9 @@ template <int BN>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
               const OzSector* __restrict__ secs, const OzWork* __restrict__ work, int nwork,
-              const __grid_constant__ OzPairs pairs, int nslices, const int32_t* __restrict__ scale_a, const int32_t* __restrict__ scale_b,
-              double* __restrict__ C, int* __restrict__ status) {
+              const __grid_constant__ OzPairs pairs, int nslices, const int32_t* __restrict__ scale_a,
+              const int32_t* __restrict__ scale_b, double* __restrict__ C, double* __restrict__ partials,
+              int* __restrict__ counters, int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char dyn[];
   unsigned char* base = (unsigned char*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
   constexpr int NBUF = OZ_TMEM_COLS / (OZ_NACC * BN);
@@ -434,7 +443,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int64_t ta0 = s.ta_base + (int64_t)wk.mt * s.nkc, tb0 = s.tb_base + (int64_t)(wk.nt / SUB) * s.nkc;
         const int32_t brow = (wk.nt % SUB) * BN;
         const int64_t sa_str = (int64_t)s.nmt * s.nkc, sb_str = (int64_t)s.nnt * s.nkc;  // tiles per slice
-        for (int kc = 0; kc < s.nkc && !*abort_flag; ++kc, ++it) {
+        for (int kc = wk.kc_lo; kc < wk.kc_hi && !*abort_flag; ++kc, ++it) {
           const uint32_t st = it % nstages, ph = (it / nstages) & 1;
           if (!mbar_wait(smem_u32(&ss->empty[st]), ph ^ 1, abort_flag)) break;
           const uint32_t fb = smem_u32(&ss->full[st]);
@@ -459,10 +468,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       uint32_t it = 0, seg = 0;
       for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
         const OzWork wk = work[w];
-        const OzSector s = secs[wk.sector];
         const uint32_t idesc = idesc_bf16(OZ_BM, wk.nw);
-        for (int kc0 = 0; kc0 < s.nkc && !*abort_flag; kc0 += OZ_SEG_KC, ++seg) {
-          const int kc1 = min(s.nkc, kc0 + OZ_SEG_KC);
+        for (int kc0 = wk.kc_lo; kc0 < wk.kc_hi && !*abort_flag; kc0 += OZ_SEG_KC, ++seg) {
+          const int kc1 = min(wk.kc_hi, kc0 + OZ_SEG_KC);
           const uint32_t buf = seg % NBUF;
           if (!mbar_wait(smem_u32(&ss->acc_empty[buf]), ((seg / NBUF) & 1) ^ 1, abort_flag)) break;
           tc_fence_after();
@@ -505,10 +513,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const int ncols = left < WCOLS ? (int)left : WCOLS;  // valid columns of this warp (may be <= 0)
       int fl = (lane < ncols) ? scale_b[s.sb_off + nb + lane] : 0;  // WCOLS <= 32: one per lane
       if (fl == kNoScale) fl = 0;
-      double* crow = C + s.c_off + nb * s.M + m;
-      for (int kc0 = 0; kc0 < s.nkc; kc0 += OZ_SEG_KC, ++seg) {
+      // a split tile's parts go to its partial buffers (column-major 128 x BN, one per part)
+      const bool split = wk.nparts > 1;
+      double* const pbase = split ? partials + (int64_t)wk.slot * OZ_MAX_PARTS * (OZ_BM * BN) : nullptr;
+      double* crow = split ? pbase + (int64_t)wk.part * (OZ_BM * BN) + (int64_t)c0 * OZ_BM + row
+                           : C + s.c_off + nb * s.M + m;
+      const int64_t ld = split ? OZ_BM : s.M;
+      bool done = true;
+      for (int kc0 = wk.kc_lo; kc0 < wk.kc_hi; kc0 += OZ_SEG_KC, ++seg) {
         const uint32_t buf = seg % NBUF;
-        if (!mbar_wait(smem_u32(&ss->acc_full[buf]), (seg / NBUF) & 1, abort_flag)) break;
+        if (!mbar_wait(smem_u32(&ss->acc_full[buf]), (seg / NBUF) & 1, abort_flag, true)) {
+          done = false;
+          break;
+        }
         tc_fence_after();
         if (active) {
           const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + buf * (OZ_NACC * BN) + c0;
@@ -521,9 +538,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             tc_ld8(lane_addr + 2 * BN + ch * 8, r2);
             tc_ld8(lane_addr + 3 * BN + ch * 8, r3);
             tc_wait_ld();
-            double* dst = crow + (int64_t)(ch * 8) * s.M;
+            double* dst = crow + (int64_t)(ch * 8) * ld;
 #pragma unroll
-            for (int j = 0; j < 8; ++j, dst += s.M) {
+            for (int j = 0; j < 8; ++j, dst += ld) {
               const int fn = __shfl_sync(0xffffffffu, fl, ch * 8 + j);
               if (!row_ok || ch * 8 + j >= ncols) continue;
               float hi, lo, e1, e2;
@@ -539,13 +556,35 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               const int sc = em + fn;
               double v = f32_scaled_to_f64(hi, sc, ok) + f32_scaled_to_f64(lo, sc, ok);
               if (!ok) v = f32_pair_scaled_slow(hi, lo, sc);
-              *dst = (kc0 == 0) ? v : *dst + v;
+              *dst = (kc0 == wk.kc_lo) ? v : *dst + v;
             }
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&ss->acc_empty[buf]));
+      }
+      if (split && done && active) {
+        // the warp that completes this region of the tile last adds the parts in part order
+        __threadfence();
+        __syncwarp();
+        int* cnt = counters + (int64_t)wk.slot * OZ_EPI_WARPS + (warp - 2);
+        int last = 0;
+        if (lane == 0) last = atomicAdd(cnt, 1) == wk.nparts - 1;
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+          __threadfence();
+          if (row_ok) {
+            const double* src = pbase + (int64_t)c0 * OZ_BM + row;
+            double* out = C + s.c_off + nb * s.M + m;
+            for (int j = 0; j < ncols; ++j, src += OZ_BM, out += s.M) {
+              double v = __ldcg(src);
+              for (int p = 1; p < wk.nparts; ++p) v += __ldcg(src + (int64_t)p * (OZ_BM * BN));
+              *out = v;
+            }
+          }
+          if (lane == 0) *cnt = 0;  // ready for the next launch
+        }
       }
     }
   }
@@ -666,7 +705,13 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
         const int32_t nw = (int32_t)std::min<int64_t>(bn, (left + 15) / 16 * 16);
         // cost key: the tile depth only, so the column tiles of one row tile (which share its A
         // slices) stay adjacent in the list and run at the same time
-        wcost.push_back({(double)s.nkc, OzWork{sid, mt, nt, nw}});
+        OzWork t;
+        std::memset(&t, 0, sizeof(t));
+        t.sector = sid;
+        t.mt = mt;
+        t.nt = nt;
+        t.nw = nw;
+        wcost.push_back({(double)s.nkc, t});
       }
     for (int rt = 0; rt < s.nmt; ++rt)
       for (int kc = 0; kc < s.nkc; ++kc) slice_jobs.push_back(OzJob{sid, 0, rt, kc});
@@ -678,16 +723,37 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
     }
   }
   std::stable_sort(wcost.begin(), wcost.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-  for (auto& w : wcost) work.push_back(w.second);
+  // Split-K: a launch with fewer than two tiles per SM cuts deep tiles into up to OZ_MAX_PARTS
+  // parts (at least 8 k-chunks each); their FP64 partial tiles are added in part order by the
+  // warps that finish last.
+  const int64_t sms = std::max(ctx->num_sms, 1);
+  const int64_t ntiles = (int64_t)wcost.size();
+  const int64_t want = ntiles >= 2 * sms ? 1 : (2 * sms + ntiles - 1) / std::max<int64_t>(ntiles, 1);
+  int32_t nslots = 0;
+  for (auto& w : wcost) {
+    OzWork t = w.second;
+    const int nkc = L->sectors[t.sector].nkc;
+    const int np = (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)OZ_MAX_PARTS, nkc / 8}));
+    t.nparts = np;
+    t.slot = np > 1 ? nslots++ : -1;
+    for (int p = 0; p < np; ++p) {
+      t.part = p;
+      t.kc_lo = (int32_t)((int64_t)p * nkc / np);
+      t.kc_hi = (int32_t)((int64_t)(p + 1) * nkc / np);
+      work.push_back(t);
+    }
+  }
+  L->nslots = nslots;
   L->nwork = (int64_t)work.size();
   L->nslice_jobs = (int64_t)slice_jobs.size();
   L->nscale_jobs = (int64_t)scale_jobs.size();
-  // workspace layout: A tiles | B tiles | row scales | column scales
+  // workspace layout: A tiles | B tiles | row scales | column scales | split-K partial tiles
   L->off_ta = 0;
   L->off_tb = al1k((size_t)L->ntiles_a * OZ_TILE_BYTES);
   L->off_sa = L->off_tb + al1k((size_t)L->ntiles_b * OZ_TILE_BYTES);
   L->off_sb = L->off_sa + al1k((size_t)L->nrows_a * 4);
-  L->bytes = L->off_sb + al1k((size_t)L->ncols_b * 4);
+  L->off_part = L->off_sb + al1k((size_t)L->ncols_b * 4);
+  L->bytes = L->off_part + al1k((size_t)nslots * OZ_MAX_PARTS * OZ_BM * bn * sizeof(double));
   int rc = TK_OK;
   if (!L->sectors.empty()) {
     if ((rc = dev_upload(ctx, (void**)&L->d_sectors, L->sectors.data(), L->sectors.size() * sizeof(OzSector))) != TK_OK ||
@@ -696,7 +762,11 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
         (rc = dev_upload(ctx, (void**)&L->d_scale_jobs, scale_jobs.data(), scale_jobs.size() * sizeof(OzJob))) != TK_OK)
       return rc;
   }
-  cp.d_oz = {L->d_sectors, L->d_work, L->d_slice_jobs, L->d_scale_jobs};
+  if (nslots > 0) {
+    std::vector<int> zeros((size_t)nslots * OZ_EPI_WARPS, 0);  // self-resetting arrival counters
+    if ((rc = dev_upload(ctx, (void**)&L->d_counters, zeros.data(), zeros.size() * sizeof(int))) != TK_OK) return rc;
+  }
+  cp.d_oz = {L->d_sectors, L->d_work, L->d_slice_jobs, L->d_scale_jobs, L->d_counters};
   cp.oz_nwork = L->nwork;
   cp.oz_bytes = L->bytes;
   cp.oz = L;
@@ -761,12 +831,15 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
   {
     ProfScope prof(ctx, "k_oz_gemm", stream);
     const int grid = (int)std::min<int64_t>(L->nwork, std::max(1, ctx->num_sms));
+    double* part = (double*)(w + L->off_part);
     if (L->bn == OZ_BN_WIDE)
       k_oz_gemm<OZ_BN_WIDE><<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, (int)L->nwork, L->pairs,
-                                                           L->slices, sa, sb, (double*)c, ctx->d_status);
+                                                           L->slices, sa, sb, (double*)c, part, L->d_counters,
+                                                           ctx->d_status);
     else
       k_oz_gemm<OZ_BN_NARROW><<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, (int)L->nwork, L->pairs,
-                                                             L->slices, sa, sb, (double*)c, ctx->d_status);
+                                                             L->slices, sa, sb, (double*)c, part, L->d_counters,
+                                                             ctx->d_status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       ctx->last_error = std::string("k_oz_gemm launch: ") + cudaGetErrorString(e);

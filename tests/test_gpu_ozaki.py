@@ -101,10 +101,12 @@ def test_su2_lx_split_precision(gctx):
 
 
 def test_long_inner_dimension_uses_segments(gctx):
-    """K = 3000 > 1024: three exact segments added in FP64; ragged M, N tails."""
+    """K = 5000: few output tiles, so the inner dimension is split across CTAs (parts added in
+    FP64 in part order), and each part still spans two exact 1024-deep segments; ragged M, N
+    tails.  Repeated runs agree bit for bit."""
     api = _api()
-    la = ([({0: 300, 1: 7}, False)], [({0: 3000, 1: 3}, False)])
-    lb = ([({0: 3000, 1: 3}, False)], [({0: 200, 1: 5}, False)])
+    la = ([({0: 300, 1: 7}, False)], [({0: 5000, 1: 3}, False)])
+    lb = ([({0: 5000, 1: 3}, False)], [({0: 200, 1: 5}, False)])
     oa, ob = ostruct("U1", la), ostruct("U1", lb)
     xa, xb = wl.normal(5, oa.numel), wl.normal(6, ob.numel)
     cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
@@ -112,6 +114,8 @@ def test_long_inner_dimension_uses_segments(gctx):
     plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), gemm="ozaki")
     c = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda())
     assert rel_frobenius_per_block(cs, c.cpu().numpy(), ref) <= SPLIT_TOL
+    c2 = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda())
+    assert torch.equal(c, c2)
 
 
 def test_scales_span_many_binades(gctx):
