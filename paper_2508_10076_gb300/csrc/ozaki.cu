@@ -258,7 +258,15 @@ __global__ void __launch_bounds__(256) k_oz_scale(const OzSector* __restrict__ s
     if (r >= s.M) return;
     const long long* x = reinterpret_cast<const long long*>(A) + s.a_off + r;
     unsigned long long mb = 0;  // |x| ordered as unsigned integers: no FP64 instructions
-    for (int64_t k = k0; k < k1; ++k) mb = max(mb, (unsigned long long)__ldg(x + k * s.M) & 0x7FFFFFFFFFFFFFFFull);
+    int64_t k = k0;
+    for (; k + 8 <= k1; k += 8) {  // eight independent loads in flight
+      unsigned long long v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (unsigned long long)__ldg(x + (k + u) * s.M);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) mb = max(mb, v[u] & 0x7FFFFFFFFFFFFFFFull);
+    }
+    for (; k < k1; ++k) mb = max(mb, (unsigned long long)__ldg(x + k * s.M) & 0x7FFFFFFFFFFFFFFFull);
     mx = __longlong_as_double((long long)mb);
     const int e = exponent_of(mx);
     if (e != kNoScale) atomicMax(&scale_a[s.sa_off + r], e);
@@ -323,9 +331,10 @@ __global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ s
     for (int sl = nslices - 1; sl >= 1; --sl) {
       const long long d = ((q + 64) & 127) - 64;  // balanced base-128 digit
       q = (q - d) >> 7;
-      dst[sl * slice_stride] = __float2bfloat16_rn((float)d * __int_as_float((127 - 7 * (sl + 1)) << 23));
+      // |d| <= 64: convert through a 32-bit integer (a 64-bit conversion runs on the FP64 pipe)
+      dst[sl * slice_stride] = __float2bfloat16_rn((float)(int)d * __int_as_float((127 - 7 * (sl + 1)) << 23));
     }
-    dst[0] = __float2bfloat16_rn((float)q * __int_as_float((127 - 7) << 23));
+    dst[0] = __float2bfloat16_rn((float)(int)q * __int_as_float((127 - 7) << 23));  // |q| <= 128 here
   }
 }
 
