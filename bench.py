@@ -349,8 +349,19 @@ def run_ours(args):
             d = float(torch.linalg.norm(oz_out[o_:o_ + r_ * k_] - ref_out[o_:o_ + r_ * k_]))
             n_ = float(torch.linalg.norm(ref_out[o_:o_ + r_ * k_]))
             worst = max(worst, d / (n_ if n_ > 1e-13 * refn else refn))
+        oz_kms = oz_prof.get("k_oz_gemm", (0, 0.0))[1]
+        pairs = 21  # slice pairs i + j <= s - 1 at s = 6
+        bf16_peak = _peaks().get("bf16_tflops")
+        split_roof = None
+        if oz_kms > 0 and oz.tensor_flops > 0:
+            executed = pairs * oz.tensor_flops * args.steps / (oz_kms * 1e-3) / 1e12
+            split_roof = {"kernel": "k_oz_gemm", "bound": "tensor", "achieved": executed, "peak": bf16_peak,
+                          "unit": "TFLOP/s", "frac": executed / bf16_peak if bf16_peak else None,
+                          "traffic": None, "peak_source": "measured bf16_tflops (burst)",
+                          "note": "achieved = 21 slice pairs x tensor-path block flops / k_oz_gemm time"}
         split = {"value": job_throughput(flops, args.steps, world, oz_ms), "unit": UNIT,
-                 "ms_per_step": oz_ms / args.steps, "slices": 6,
+                 "ms_per_step": oz_ms / args.steps, "slices": 6, "roofline": split_roof,
+                 "tensor_path_flops_per_step": oz.tensor_flops,
                  "rel_frobenius_per_block_vs_fp64_path": worst,
                  "kernels": {k: {"launches": c, "ms_per_step": ms / args.steps} for k, (c, ms) in oz_prof.items()}}
     if rank != 0:

@@ -156,6 +156,9 @@ size_t tk_plan_workspace_bytes(const tk_plan* plan);  /* device scratch needed b
 /* Block flops of the plan: sum over executed sector GEMMs of 2 M K N (8 M K N complex), using
  * reduced sizes -- each SU(2) block once (Sec. 4.4). */
 double tk_plan_flops(const tk_plan* plan);
+/* The part of tk_plan_flops routed to the split-precision tensor-core GEMM (0 for FP64 plans and
+ * for products too thin for tensor tiles, which stay on CUDA cores). */
+double tk_plan_tensor_flops(const tk_plan* plan);
 /* Algorithmic bytes moved by the plan's permute launches (each source element read once per
  * use, each output element written once). */
 double tk_plan_permute_bytes(const tk_plan* plan);

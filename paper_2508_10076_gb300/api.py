@@ -227,6 +227,11 @@ class Plan:
         return float(_lib().tk_plan_flops(self._h))
 
     @property
+    def tensor_flops(self):
+        """Block flops of the products that run on the split-precision tensor-core path."""
+        return float(_lib().tk_plan_tensor_flops(self._h))
+
+    @property
     def permute_bytes(self):
         return float(_lib().tk_plan_permute_bytes(self._h))
 

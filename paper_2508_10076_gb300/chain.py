@@ -103,6 +103,7 @@ class HeffChain:
             self.steps.append(st)
             cur = st.out
         self.flops = sum(s.plan.flops for s in self.steps)
+        self.tensor_flops = sum(s.plan.tensor_flops for s in self.steps)
         self.permute_bytes = sum(s.plan.permute_bytes for s in self.steps)
 
     def run(self, x=None, stream=None):
@@ -133,6 +134,7 @@ class LxContraction:
                     for k, v in self.host.items()}
         self.step = Contraction(ctx, self.tm["L"], self.tm["x"], wl.LX_SPEC, dtype, gemm, slices, device)
         self.flops = self.step.plan.flops
+        self.tensor_flops = self.step.plan.tensor_flops
         self.permute_bytes = self.step.plan.permute_bytes
 
     def run(self, stream=None):

@@ -400,6 +400,13 @@ double tk_plan_flops(const tk_plan* plan) {
   return plan->con->flops;
 }
 
+double tk_plan_tensor_flops(const tk_plan* plan) {
+  if (!plan || plan->kind != 1) return 0.0;
+  double f = 0;
+  for (const tk::GemmItem& g : plan->con->gemms_oz) f += 2.0 * (double)g.M * (double)g.N * (double)g.K;
+  return f;
+}
+
 double tk_plan_permute_bytes(const tk_plan* plan) {
   if (!plan) return 0.0;
   if (plan->kind == 0) return plan->perm->identity ? 0.0 : plan->perm->bytes;
