@@ -364,6 +364,21 @@ def run_ours(args):
                  "tensor_path_flops_per_step": oz.tensor_flops,
                  "rel_frobenius_per_block_vs_fp64_path": worst,
                  "kernels": {k: {"launches": c, "ms_per_step": ms / args.steps} for k, (c, ms) in oz_prof.items()}}
+    # ---------------- serving: Poisson stream of mixed requests through the continuous-batching loop
+    serve = None
+    if args.serve_requests > 0:
+        from paper_2508_10076_gb300.serve import Server, calibrated_rate, request_stream
+        reqs = request_stream(args.serve_requests, seed=1000 + replica_seed(rank))
+        server = Server(ctx, budget_bytes=150 << 30)
+        for r in reqs:
+            server.shape(r["sym"], r["D"], r["dtype"])
+        rate, mean_s = calibrated_rate(server, reqs, load=args.serve_load)
+        server.run(reqs[:200], rate)  # warm-up pass (allocator, first launches)
+        _, serve, _ = server.run(reqs, rate)
+        serve["p99_ms"] = max_over_ranks(dist, serve["p99_ms"])
+        serve.update({"load": args.serve_load, "mean_service_ms_alone": 1e3 * mean_s,
+                      "budget_gb": 150, "mix": "U(1) L.x at D / SU(2) L.x at D/4, D log-uniform 64-4096 "
+                      "(25-level grid), half complex128, Poisson arrivals"})
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -403,6 +418,8 @@ def run_ours(args):
     }
     if split is not None:
         line["split_precision"] = split
+    if serve is not None:
+        line["serve"] = serve
     if world == 1 and not args.no_cpu_baseline:
         n, dt, cores = cpu_baseline(args.config, budget_s=args.cpu_budget)
         line["cpu_baseline"] = {"value": flops * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -426,6 +443,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-split", action="store_true", help="skip the split-precision variant")
     ap.add_argument("--eager", action="store_true", help="launch kernels one by one instead of a CUDA graph")
+    ap.add_argument("--serve-requests", type=int, default=10000, help="serving requests (0: skip serving)")
+    ap.add_argument("--serve-load", type=float, default=0.7, help="offered load relative to alone service time")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -179,6 +179,19 @@ int tk_permute(tk_ctx* ctx, const tk_plan* plan, const void* a, void* c, void* s
 int tk_contract(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, void* c,
                 void* workspace, size_t workspace_bytes, void* stream);
 
+/* n planned contractions executed together (batching of concurrent requests; not in the paper,
+ * whose contractions run one by one).  Request i reads a[i], b[i], writes c[i] and uses
+ * workspace[i] of workspace_bytes[i] >= tk_plan_workspace_bytes(plans[i]); requests may share a
+ * plan but not a workspace or an output.  The blocks of all requests share one launch per stage:
+ * every input permute in one launch, the zero fill in one, every sector GEMM tile in one grouped
+ * GEMM, every output permute in one (a stage with more than 160 segments is split into several
+ * launches).  Each c[i] equals what tk_contract would write for that request alone.
+ * Every plan must use TK_GEMM_FP64 and all plans the same dtype (else TK_ERR_UNSUPPORTED);
+ * pointer arrays are host arrays of device pointers; n = 0 is a no-op. */
+int tk_contract_batch(tk_ctx* ctx, int n, const tk_plan* const* plans, const void* const* a,
+                      const void* const* b, void* const* c, void* const* workspace,
+                      const size_t* workspace_bytes, void* stream);
+
 /* Contraction without any device allocation -- no counterpart in the paper.  Same result and
  * launch sequence as tk_contract, but the scratch memory (permuted operands and the intermediate
  * C~) comes from a fixed array compiled into libtk instead of a caller-allocated workspace.  It

@@ -288,6 +288,21 @@ def contract(ctx, plan, a, b, c, workspace=None, stream=None):
                               C.c_size_t(nbytes), _stream_handle(stream)), ctx)
 
 
+def contract_batch(ctx, plans, a, b, c, workspaces, stream=None):
+    """tk_contract_batch: request i = (plans[i], a[i], b[i], c[i], workspaces[i]); the stages of
+    all requests share launches.  Lists of equal length; buffers are device tensors."""
+    n = len(plans)
+    if not (len(a) == len(b) == len(c) == len(workspaces) == n):
+        raise ValueError("batch lists differ in length")
+    vp = C.c_void_p * max(n, 1)
+    sz = C.c_size_t * max(n, 1)
+    hp = vp(*[p._h for p in plans])
+    ha, hb, hc = vp(*[_ptr(x) for x in a]), vp(*[_ptr(x) for x in b]), vp(*[_ptr(x) for x in c])
+    hw = vp(*[_ptr(w) for w in workspaces])
+    hn = sz(*[0 if w is None else w.numel() * w.element_size() for w in workspaces])
+    _check(_lib().tk_contract_batch(ctx._h, n, hp, ha, hb, hc, hw, hn, _stream_handle(stream)), ctx)
+
+
 # Mirrors TK_NOALLOC_SCRATCH_BYTES in include/tk.h.
 NOALLOC_SCRATCH_BYTES = 32 << 20
 

@@ -471,6 +471,28 @@ int tk_contract(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, 
   return tk::run_contract(&ctx->c, cp, a, b, c, workspace, stream);
 }
 
+int tk_contract_batch(tk_ctx* ctx, int n, const tk_plan* const* plans, const void* const* a,
+                      const void* const* b, void* const* c, void* const* workspace,
+                      const size_t* workspace_bytes, void* stream) {
+  if (!ctx || n < 0) return fail(ctx, TK_ERR_ARG, "bad batch");
+  if (n == 0) return TK_OK;
+  if (!plans || !a || !b || !c || !workspace || !workspace_bytes) return fail(ctx, TK_ERR_ARG, "null array");
+  std::vector<const tk::ContractPlan*> cps((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || plans[i]->kind != 1) return fail(ctx, TK_ERR_ARG, "not a contraction plan");
+    if (!a[i] || !b[i] || !c[i]) return fail(ctx, TK_ERR_ARG, "null buffer");
+    const tk::ContractPlan& cp = *plans[i]->con;
+    if (workspace_bytes[i] < cp.ws_total || (cp.ws_total > 0 && !workspace[i]))
+      return fail(ctx, TK_ERR_WORKSPACE, "workspace smaller than tk_plan_workspace_bytes()");
+    if (cp.gemm_mode != TK_GEMM_FP64 || cp.dtype != plans[0]->con->dtype)
+      return fail(ctx, TK_ERR_UNSUPPORTED, "a batch takes FP64-mode plans of one dtype");
+    cps[(size_t)i] = &cp;
+  }
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  return tk::run_contract_batch(&ctx->c, n, cps.data(), a, b, c, workspace, stream);
+}
+
 int tk_copy_h2d(tk_ctx* ctx, void* dst_device, const void* src_host, size_t bytes, void* stream) {
   if (!ctx || (bytes && (!dst_device || !src_host))) return fail(ctx, TK_ERR_ARG, "null argument");
   int rc = set_device(ctx);

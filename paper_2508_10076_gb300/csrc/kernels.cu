@@ -55,7 +55,6 @@ PermutePlan::~PermutePlan() {
 ContractPlan::~ContractPlan() {
   dev_free(d_gemm_items);
   dev_free(d_gemm_tiles);
-  dev_free(d_split_counters);
   dev_free(d_zero);
   for (void* p : d_oz) dev_free(p);
 }
@@ -113,11 +112,28 @@ struct PermSeg {
   const void* in;
   void* out;
 };
-constexpr int kMaxPermSegs = 4;
-struct PermLaunch {
-  PermSeg seg[kMaxPermSegs];
+constexpr int kMaxPermSegs = 4;       // one contraction: runs + tiles of two operands
+constexpr int kBatchSegs = 160;       // a packed launch over many requests (about 13 KB of parameters)
+template <int NSEG>
+struct PermLaunchT {
+  PermSeg seg[NSEG];
   int32_t nseg;
 };
+using PermLaunch = PermLaunchT<kMaxPermSegs>;
+
+// Segment owning block b: segments are sorted by their first block.
+template <typename Seg>
+__device__ __forceinline__ int find_seg(const Seg* segs, int nseg, int64_t b) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].block0 <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
 
 template <typename T>
 __device__ __forceinline__ void permute_tiles(const PermSeg& g, int64_t bid, T (*tile)[33], int64_t* task_words) {
@@ -234,15 +250,11 @@ __device__ __forceinline__ void permute_runs(const PermSeg& g, int64_t bid) {
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermLaunch L) {
+template <typename T, int NSEG>
+__global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermLaunchT<NSEG> L) {
   __shared__ T tile[32][33];
   __shared__ int64_t task_words[kTaskWords];
-  int s = 0;
-#pragma unroll
-  for (int i = 1; i < kMaxPermSegs; ++i)
-    if (i < L.nseg && (int64_t)blockIdx.x >= L.seg[i].block0) s = i;
-  const PermSeg& g = L.seg[s];
+  const PermSeg& g = L.seg[find_seg(L.seg, L.nseg, (int64_t)blockIdx.x)];
   const int64_t bid = (int64_t)blockIdx.x - g.block0;
   if (g.kind == 0)
     permute_runs<T>(g, bid);
@@ -628,6 +640,61 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const GemmItem* __restrict__ i
     gemm_rows<T>(it, tl, A, B, C, smem, partials, counters);
 }
 
+// Packed FP64 GEMM over many requests: each segment carries one request's work list and buffers.
+struct GemmSeg {
+  const GemmItem* items;
+  const GemmTile* tiles;
+  const void *A, *B;
+  void *C, *partials;
+  int* counters;
+  int64_t block0, ntiles;
+};
+struct GemmBatch {
+  GemmSeg seg[kBatchSegs];
+  int32_t nseg;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_batch(const __grid_constant__ GemmBatch L) {
+  constexpr int kTileElems = BK * 65 * 2, kRowElems = ROWS_KCHUNK * ROWS_NMAX;
+  __shared__ T smem[kTileElems > kRowElems ? kTileElems : kRowElems];
+  const GemmSeg& g = L.seg[find_seg(L.seg, L.nseg, (int64_t)blockIdx.x)];
+  const GemmTile tl = g.tiles[blockIdx.x - g.block0];
+  const GemmItem it = g.items[tl.item];
+  const T* A = (const T*)g.A;
+  const T* B = (const T*)g.B;
+  T* C = (T*)g.C;
+  T* P = (T*)g.partials;
+  if (tl.cfg == CFG_64)
+    gemm_tile<T, 64, 64, 4, 4>(it, tl, A, B, C, smem, P, g.counters);
+  else if (tl.cfg == CFG_32)
+    gemm_tile<T, 32, 32, 2, 2>(it, tl, A, B, C, smem, P, g.counters);
+  else
+    gemm_rows<T>(it, tl, A, B, C, smem, P, g.counters);
+}
+
+// Packed zero fill: block row y belongs to the segment whose first item index is the largest <= y.
+struct ZeroSeg {
+  const ZeroItem* items;
+  void* c;
+  int64_t block0;  // first global item index of this segment (named for find_seg)
+  int64_t nitems;
+};
+struct ZeroBatch {
+  ZeroSeg seg[kBatchSegs];
+  int32_t nseg;
+};
+template <typename T>
+__global__ void k_zero_batch(const __grid_constant__ ZeroBatch L, int64_t total_items) {
+  for (int64_t i = blockIdx.y; i < total_items; i += gridDim.y) {
+    const ZeroSeg& g = L.seg[find_seg(L.seg, L.nseg, i)];
+    const ZeroItem z = g.items[i - g.block0];
+    T* c = (T*)g.c;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < z.n; e += (int64_t)gridDim.x * blockDim.x)
+      c[z.off + e] = Elem<T>::zero();
+  }
+}
+
 template <typename T>
 __global__ void k_zero(const ZeroItem* __restrict__ items, int nitems, T* __restrict__ c) {
   for (int i = blockIdx.y; i < nitems; i += gridDim.y) {
@@ -650,20 +717,17 @@ int check_launch(Ctx* ctx, const char* what) {
 
 }  // namespace
 
-int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream) {
-  // blocks per segment: runs take one warp each (8 per block), tiles one block each; when the
-  // total exceeds 8 blocks per SM the segments share that budget in proportion to their work
-  PermLaunch L;
-  std::memset(&L, 0, sizeof(L));
-  int dtype = TK_F64;
-  int64_t natural[kMaxPermSegs] = {0};
+namespace {
+// Segments (runs and tiles) of the non-identity permutes among jobs, with their natural block counts.
+void perm_segments(const PermJob* jobs, int njobs, std::vector<PermSeg>& segs, std::vector<int64_t>& natural,
+                   int& dtype) {
   for (int j = 0; j < njobs; ++j) {
     const PermutePlan& pp = *jobs[j].plan;
     if (pp.identity) continue;
     dtype = pp.dtype;
     if (!pp.runs.empty()) {
-      if (L.nseg == kMaxPermSegs) return TK_ERR_ARG;
-      PermSeg& g = L.seg[L.nseg];
+      PermSeg g;
+      std::memset(&g, 0, sizeof(g));
       g.kind = 0;
       g.nwork = (int64_t)pp.runs.size();
       g.runs = pp.d_runs;
@@ -671,11 +735,12 @@ int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream) {
       g.srcs = pp.d_srcs;
       g.in = jobs[j].in;
       g.out = jobs[j].out;
-      natural[L.nseg++] = (g.nwork + 7) / 8;
+      segs.push_back(g);
+      natural.push_back((g.nwork + 7) / 8);
     }
     if (!pp.tasks.empty() && pp.total_tiles > 0) {
-      if (L.nseg == kMaxPermSegs) return TK_ERR_ARG;
-      PermSeg& g = L.seg[L.nseg];
+      PermSeg g;
+      std::memset(&g, 0, sizeof(g));
       g.kind = 1;
       g.ntasks = (int32_t)pp.tasks.size();
       g.nwork = pp.total_tiles;
@@ -684,28 +749,63 @@ int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream) {
       g.srcs = pp.d_srcs;
       g.in = jobs[j].in;
       g.out = jobs[j].out;
-      natural[L.nseg++] = g.nwork;
+      segs.push_back(g);
+      natural.push_back(g.nwork);
     }
   }
-  if (L.nseg == 0) return TK_OK;
-  const int64_t cap = (int64_t)std::max(ctx->num_sms, 1) * 8;
+}
+
+// Blocks per segment: natural counts, or a share of 8 blocks per SM in proportion to the work when
+// the total exceeds that.
+template <int NSEG>
+int64_t fill_perm_launch(PermLaunchT<NSEG>& L, const PermSeg* segs, const int64_t* natural, int n, int64_t cap) {
+  std::memset(&L, 0, sizeof(L));
   int64_t total = 0;
-  for (int i = 0; i < L.nseg; ++i) total += natural[i];
+  for (int i = 0; i < n; ++i) total += natural[i];
   int64_t b0 = 0;
-  for (int i = 0; i < L.nseg; ++i) {
+  for (int i = 0; i < n; ++i) {
     int64_t nb = natural[i];
     if (total > cap) nb = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)((double)cap * natural[i] / total)));
+    L.seg[i] = segs[i];
     L.seg[i].block0 = b0;
     L.seg[i].nblocks = nb;
     b0 += nb;
   }
+  L.nseg = n;
+  return b0;
+}
+}  // namespace
+
+int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream) {
+  std::vector<PermSeg> segs;
+  std::vector<int64_t> natural;
+  int dtype = TK_F64;
+  perm_segments(jobs, njobs, segs, natural, dtype);
+  if (segs.empty()) return TK_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  const int64_t cap = (int64_t)std::max(ctx->num_sms, 1) * 8;
   ProfScope prof(ctx, "k_permute", stream);
-  if (dtype == TK_C128)
-    k_permute<double2><<<(unsigned)b0, 256, 0, s>>>(L);
-  else
-    k_permute<double><<<(unsigned)b0, 256, 0, s>>>(L);
-  return check_launch(ctx, "k_permute");
+  if ((int)segs.size() <= kMaxPermSegs) {  // one contraction: small parameter block
+    PermLaunch L;
+    const int64_t blocks = fill_perm_launch(L, segs.data(), natural.data(), (int)segs.size(), cap);
+    if (dtype == TK_C128)
+      k_permute<double2, kMaxPermSegs><<<(unsigned)blocks, 256, 0, s>>>(L);
+    else
+      k_permute<double, kMaxPermSegs><<<(unsigned)blocks, 256, 0, s>>>(L);
+    return check_launch(ctx, "k_permute");
+  }
+  static thread_local PermLaunchT<kBatchSegs> big;  // ~13 KB: not on the stack
+  for (size_t first = 0; first < segs.size(); first += kBatchSegs) {
+    const int n = (int)std::min<size_t>(kBatchSegs, segs.size() - first);
+    const int64_t blocks = fill_perm_launch(big, segs.data() + first, natural.data() + first, n, cap);
+    if (dtype == TK_C128)
+      k_permute<double2, kBatchSegs><<<(unsigned)blocks, 256, 0, s>>>(big);
+    else
+      k_permute<double, kBatchSegs><<<(unsigned)blocks, 256, 0, s>>>(big);
+    int rc = check_launch(ctx, "k_permute");
+    if (rc != TK_OK) return rc;
+  }
+  return TK_OK;
 }
 
 int launch_permute(Ctx* ctx, const PermutePlan& pp, const void* in, void* out, void* stream) {
@@ -827,22 +927,16 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
     rc = dev_upload(ctx, &cp.d_zero, cp.zeros.data(), cp.zeros.size() * sizeof(ZeroItem));
     if (rc != TK_OK) return rc;
   }
-  if (nslots > 0) {
-    std::vector<int> zeros((size_t)nslots, 0);
-    rc = dev_upload(ctx, &cp.d_split_counters, zeros.data(), zeros.size() * sizeof(int));
-    if (rc != TK_OK) return rc;
-    cp.partials_bytes = (size_t)poff * (cp.dtype == TK_C128 ? 16 : 8);
-  }
+  if (nslots > 0) cp.partials_bytes = (size_t)poff * (cp.dtype == TK_C128 ? 16 : 8);
   return TK_OK;
 }
 
 int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
-                     void* partials, void* stream) {
+                     void* partials, int* counters, void* stream) {
   if (cp.n_gemm_tiles == 0) return TK_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const GemmItem* items = (const GemmItem*)cp.d_gemm_items;
   const GemmTile* tiles = (const GemmTile*)cp.d_gemm_tiles;
-  int* counters = (int*)cp.d_split_counters;
   const unsigned grid = (unsigned)cp.n_gemm_tiles;
   ProfScope prof(ctx, "k_gemm_f64", stream);
   if (cp.dtype == TK_C128)
@@ -881,12 +975,108 @@ int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b,
   const PermJob in_jobs[2] = {{cp.pa.get(), a, (void*)at}, {cp.pb.get(), b, (void*)bt}};
   if ((rc = launch_permutes(ctx, in_jobs, 2, stream)) != TK_OK) return rc;  // both operands, one launch
   if ((rc = launch_zero(ctx, cp, ct, stream)) != TK_OK) return rc;
-  if (!cp.gemms_fp64.empty() && (rc = launch_gemm_fp64(ctx, cp, at, bt, ct, w + cp.ws_partials, stream)) != TK_OK)
+  if (cp.split_slots > 0 &&
+      cudaMemsetAsync(w + cp.ws_counters, 0, (size_t)cp.split_slots * sizeof(int), (cudaStream_t)stream) != cudaSuccess)
+    return TK_ERR_CUDA;
+  if (!cp.gemms_fp64.empty() &&
+      (rc = launch_gemm_fp64(ctx, cp, at, bt, ct, w + cp.ws_partials, (int*)(w + cp.ws_counters), stream)) != TK_OK)
     return rc;
   if (!cp.gemms_oz.empty() && (rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream)) != TK_OK)
     return rc;
   if (cp.pc && (rc = launch_permute(ctx, *cp.pc, ct, c, stream)) != TK_OK) return rc;
   return TK_OK;
+}
+
+int run_contract_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const void* const* a,
+                       const void* const* b, void* const* c, void* const* ws, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool cplx = plans[0]->dtype == TK_C128;
+  std::vector<const void*> at((size_t)n), bt((size_t)n);
+  std::vector<void*> ct((size_t)n);
+  std::vector<PermJob> in_jobs, out_jobs;
+  for (int i = 0; i < n; ++i) {
+    const ContractPlan& cp = *plans[i];
+    char* w = (char*)ws[i];
+    at[i] = cp.pa->identity ? a[i] : (const void*)(w + cp.ws_at);
+    bt[i] = cp.pb->identity ? b[i] : (const void*)(w + cp.ws_bt);
+    ct[i] = cp.pc ? (void*)(w + cp.ws_ct) : c[i];
+    in_jobs.push_back({cp.pa.get(), a[i], (void*)at[i]});
+    in_jobs.push_back({cp.pb.get(), b[i], (void*)bt[i]});
+    if (cp.pc) out_jobs.push_back({cp.pc.get(), ct[i], c[i]});
+    if (cp.split_slots > 0 &&
+        cudaMemsetAsync(w + cp.ws_counters, 0, (size_t)cp.split_slots * sizeof(int), s) != cudaSuccess)
+      return TK_ERR_CUDA;
+  }
+  int rc = launch_permutes(ctx, in_jobs.data(), (int)in_jobs.size(), stream);
+  if (rc != TK_OK) return rc;
+  // zero fill of blocks with an empty inner dimension, all requests in one launch per 160
+  {
+    static thread_local ZeroBatch zb;
+    int64_t total = 0, maxn = 0;
+    zb.nseg = 0;
+    auto flush = [&]() -> int {
+      if (zb.nseg == 0) return TK_OK;
+      dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((maxn + 255) / 256, 1024)),
+                (unsigned)std::min<int64_t>(total, 65535));
+      ProfScope prof(ctx, "k_zero", stream);
+      if (cplx)
+        k_zero_batch<double2><<<grid, 256, 0, s>>>(zb, total);
+      else
+        k_zero_batch<double><<<grid, 256, 0, s>>>(zb, total);
+      zb.nseg = 0;
+      total = maxn = 0;
+      return check_launch(ctx, "k_zero");
+    };
+    for (int i = 0; i < n; ++i) {
+      const ContractPlan& cp = *plans[i];
+      if (cp.zeros.empty()) continue;
+      ZeroSeg& g = zb.seg[zb.nseg++];
+      g.items = (const ZeroItem*)cp.d_zero;
+      g.c = ct[i];
+      g.block0 = total;
+      g.nitems = (int64_t)cp.zeros.size();
+      total += g.nitems;
+      for (const ZeroItem& z : cp.zeros) maxn = std::max(maxn, z.n);
+      if (zb.nseg == kBatchSegs && (rc = flush()) != TK_OK) return rc;
+    }
+    if ((rc = flush()) != TK_OK) return rc;
+  }
+  // every GEMM tile of every request in one grouped launch per 160 requests
+  {
+    static thread_local GemmBatch gb;
+    int64_t blocks = 0;
+    gb.nseg = 0;
+    auto flush = [&]() -> int {
+      if (gb.nseg == 0) return TK_OK;
+      ProfScope prof(ctx, "k_gemm_f64", stream);
+      if (cplx)
+        k_gemm_batch<double2><<<(unsigned)blocks, 256, 0, s>>>(gb);
+      else
+        k_gemm_batch<double><<<(unsigned)blocks, 256, 0, s>>>(gb);
+      gb.nseg = 0;
+      blocks = 0;
+      return check_launch(ctx, "k_gemm_batch");
+    };
+    for (int i = 0; i < n; ++i) {
+      const ContractPlan& cp = *plans[i];
+      if (cp.n_gemm_tiles == 0) continue;
+      char* w = (char*)ws[i];
+      GemmSeg& g = gb.seg[gb.nseg++];
+      g.items = (const GemmItem*)cp.d_gemm_items;
+      g.tiles = (const GemmTile*)cp.d_gemm_tiles;
+      g.A = at[i];
+      g.B = bt[i];
+      g.C = ct[i];
+      g.partials = w + cp.ws_partials;
+      g.counters = (int*)(w + cp.ws_counters);
+      g.block0 = blocks;
+      g.ntiles = cp.n_gemm_tiles;
+      blocks += cp.n_gemm_tiles;
+      if (gb.nseg == kBatchSegs && (rc = flush()) != TK_OK) return rc;
+    }
+    if ((rc = flush()) != TK_OK) return rc;
+  }
+  return launch_permutes(ctx, out_jobs.data(), (int)out_jobs.size(), stream);
 }
 
 }  // namespace tk

@@ -91,7 +91,7 @@ struct OzLayout {
   OzJob* d_scale_jobs = nullptr;
   int32_t nslots = 0;        // split tiles
   size_t off_part = 0;       // their partial tiles in the workspace
-  int* d_counters = nullptr;  // per (split tile, epilogue warp) arrival counters
+  size_t off_cnt = 0;        // per (split tile, epilogue warp) arrival counters in the workspace
 };
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -762,7 +762,8 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
   L->off_sa = L->off_tb + al1k((size_t)L->ntiles_b * OZ_TILE_BYTES);
   L->off_sb = L->off_sa + al1k((size_t)L->nrows_a * 4);
   L->off_part = L->off_sb + al1k((size_t)L->ncols_b * 4);
-  L->bytes = L->off_part + al1k((size_t)nslots * OZ_MAX_PARTS * OZ_BM * bn * sizeof(double));
+  L->off_cnt = L->off_part + al1k((size_t)nslots * OZ_MAX_PARTS * OZ_BM * bn * sizeof(double));
+  L->bytes = L->off_cnt + al1k((size_t)nslots * OZ_EPI_WARPS * sizeof(int));
   int rc = TK_OK;
   if (!L->sectors.empty()) {
     if ((rc = dev_upload(ctx, (void**)&L->d_sectors, L->sectors.data(), L->sectors.size() * sizeof(OzSector))) != TK_OK ||
@@ -771,11 +772,7 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
         (rc = dev_upload(ctx, (void**)&L->d_scale_jobs, scale_jobs.data(), scale_jobs.size() * sizeof(OzJob))) != TK_OK)
       return rc;
   }
-  if (nslots > 0) {
-    std::vector<int> zeros((size_t)nslots * OZ_EPI_WARPS, 0);  // self-resetting arrival counters
-    if ((rc = dev_upload(ctx, (void**)&L->d_counters, zeros.data(), zeros.size() * sizeof(int))) != TK_OK) return rc;
-  }
-  cp.d_oz = {L->d_sectors, L->d_work, L->d_slice_jobs, L->d_scale_jobs, L->d_counters};
+  cp.d_oz = {L->d_sectors, L->d_work, L->d_slice_jobs, L->d_scale_jobs};
   cp.oz_nwork = L->nwork;
   cp.oz_bytes = L->bytes;
   cp.oz = L;
@@ -823,6 +820,9 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
   }
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(sa, 0x80, L->off_sb - L->off_sa + (size_t)L->ncols_b * 4, s) != cudaSuccess) return TK_ERR_CUDA;
+  int* counters = (int*)(w + L->off_cnt);
+  if (L->nslots > 0 && cudaMemsetAsync(counters, 0, (size_t)L->nslots * OZ_EPI_WARPS * sizeof(int), s) != cudaSuccess)
+    return TK_ERR_CUDA;
   {
     ProfScope prof(ctx, "k_oz_scale", stream);
     k_oz_scale<<<(unsigned)L->nscale_jobs, 256, 0, s>>>(L->d_sectors, L->d_scale_jobs, (const double*)a,
@@ -843,11 +843,11 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
     double* part = (double*)(w + L->off_part);
     if (L->bn == OZ_BN_WIDE)
       k_oz_gemm<OZ_BN_WIDE><<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, (int)L->nwork, L->pairs,
-                                                           L->slices, sa, sb, (double*)c, part, L->d_counters,
+                                                           L->slices, sa, sb, (double*)c, part, counters,
                                                            ctx->d_status);
     else
       k_oz_gemm<OZ_BN_NARROW><<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, (int)L->nwork, L->pairs,
-                                                             L->slices, sa, sb, (double*)c, part, L->d_counters,
+                                                             L->slices, sa, sb, (double*)c, part, counters,
                                                              ctx->d_status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

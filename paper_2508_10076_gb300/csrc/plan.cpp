@@ -548,6 +548,8 @@ std::shared_ptr<ContractPlan> make_contract_plan(Ctx* ctx, std::shared_ptr<Struc
     if (rc != TK_OK) throw Error{rc, "uploading GEMM tables failed"};
     cp->ws_partials = off;
     off += align256(cp->partials_bytes);
+    cp->ws_counters = off;
+    off += align256((size_t)cp->split_slots * sizeof(int));
     cp->ws_slices = off;
     cp->ws_total = off;
     if (gemm_mode != TK_GEMM_FP64) {

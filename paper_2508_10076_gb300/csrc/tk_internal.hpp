@@ -163,14 +163,14 @@ struct ContractPlan {
   int dtype = TK_F64;
   double flops = 0;
   // workspace layout (bytes)
-  size_t ws_at = 0, ws_bt = 0, ws_ct = 0, ws_partials = 0, ws_slices = 0, ws_total = 0;
+  size_t ws_at = 0, ws_bt = 0, ws_ct = 0, ws_partials = 0, ws_counters = 0, ws_slices = 0, ws_total = 0;
   // device tables
   void* d_gemm_items = nullptr;
   void* d_gemm_tiles = nullptr;
   int64_t n_gemm_tiles = 0;
-  // split-K of the FP64 tiles: per-slot arrival counters (plan-owned, self-resetting; launches of
-  // one plan must not overlap) and the partial tiles in the workspace
-  void* d_split_counters = nullptr;
+  // split-K of the FP64 tiles: partial tiles and per-slot arrival counters, both in the caller's
+  // workspace; the counters are cleared at the start of every call, so calls of one plan with
+  // different workspaces may overlap
   int32_t split_slots = 0;
   size_t partials_bytes = 0;
   void* d_zero = nullptr;
@@ -246,7 +246,7 @@ struct PermJob {
 // Several permutes in one launch (identity plans are skipped; at most two plans).
 int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream);
 int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
-                     void* partials, void* stream);
+                     void* partials, int* counters, void* stream);
 int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream);
 int upload_gemm_tables(Ctx* ctx, ContractPlan& cp);
 int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
@@ -255,5 +255,8 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp);
 // The launch sequence of one planned contraction with scratch at `ws` (Algorithm 4 / 8).
 int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
                  void* stream);
+// Many FP64 contractions with their stages packed into shared launches (tk_contract_batch).
+int run_contract_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const void* const* a,
+                       const void* const* b, void* const* c, void* const* ws, void* stream);
 
 }  // namespace tk

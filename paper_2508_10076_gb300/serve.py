@@ -1,0 +1,188 @@
+"""Continuous-batching request loop over libtk (C4 serving workload; the paper has no serving
+layer).  Requests are single contractions L.x of the two-site effective Hamiltonian (U(1) at bond
+dimension D, SU(2) at reduced multiplicity D/4), FP64 or complex128, arriving as a Poisson stream.
+
+Scheduling, per pass of the loop:
+  * requests whose arrival time has passed join the queue;
+  * queued requests are admitted while their device memory (output + workspace) fits the HBM
+    budget and an in-flight slot is free;
+  * the admitted requests of one dtype go to the GPU together through tk_contract_batch (their
+    permutes, zero fills and sector-GEMM tiles share launches) on the next of several CUDA streams,
+    so batches overlap on the device while new requests keep arriving;
+  * finished batches (their end event has completed) release memory and slots.
+Latency = completion time on the device clock - arrival time, both relative to one start event.
+Plans (structure, recoupling tables, GEMM work lists) are built once per shape and stay resident.
+"""
+
+import time
+
+import numpy as np
+import torch
+
+from . import api
+from . import workloads as wl
+
+
+def _tmap(ctx, sym, legs):
+    cod, dom = legs
+    return ctx.tmap([ctx.space(sym, s, d) for s, d in cod], [ctx.space(sym, s, d) for s, d in dom])
+
+
+def dimension_grid(lo=64, hi=4096, levels=25):
+    """Bond dimensions on a geometric grid: a log-uniform draw is rounded to the nearest level, so
+    that the plan cache sees a bounded set of shapes."""
+    return sorted({int(round(lo * (hi / lo) ** (i / (levels - 1)))) for i in range(levels)})
+
+
+def request_stream(n, seed=0, rate_per_s=None, grid=None):
+    """n requests (arrival_s, sym, D, dtype): symmetry 1:1 U(1)/SU(2), dtype 1:1 float64/complex128,
+    D log-uniform on [64, 4096] rounded to `grid`, Poisson arrivals at rate_per_s (filled in by the
+    caller when None)."""
+    rng = np.random.default_rng(seed)
+    grid = np.array(grid or dimension_grid())
+    logd = rng.uniform(np.log(grid[0]), np.log(grid[-1]), n)
+    D = grid[np.abs(np.log(grid)[None, :] - logd[:, None]).argmin(axis=1)]
+    sym = np.where(rng.random(n) < 0.5, "U1", "SU2")
+    dtype = np.where(rng.random(n) < 0.5, "f64", "c128")
+    gaps = rng.exponential(1.0, n)  # unit-rate Poisson gaps, scaled by 1/rate later
+    return [dict(idx=i, gap=float(gaps[i]), sym=str(sym[i]), D=int(D[i]), dtype=str(dtype[i])) for i in range(n)]
+
+
+class Shape:
+    """Plan and resident inputs of one request shape (symmetry, D, dtype)."""
+
+    def __init__(self, ctx, sym, D, dtype, seed=0):
+        V, P, W = wl.heff_spaces(sym, D if sym == "U1" else max(8, D // 4))
+        legs = wl.heff_legs(V, P, W)
+        L, x = _tmap(ctx, sym, legs["L"]), _tmap(ctx, sym, legs["x"])
+        self.plan = api.contract_plan(ctx, L, *wl.LX_SPEC[:2], x, *wl.LX_SPEC[2:], dtype=dtype)
+        self.flops = self.plan.flops
+        self.tdt = torch.complex128 if dtype == "c128" else torch.float64
+        rnd = wl.normal_complex if dtype == "c128" else wl.normal
+        self.a = torch.from_numpy(np.ascontiguousarray(rnd(seed * 16 + 1, L.numel))).to("cuda", self.tdt)
+        self.b = torch.from_numpy(np.ascontiguousarray(rnd(seed * 16 + 0, x.numel))).to("cuda", self.tdt)
+        self.out_numel = self.plan.output().numel
+        self.ws_bytes = max(1, self.plan.workspace_bytes)
+        self.bytes = self.out_numel * (16 if dtype == "c128" else 8) + self.ws_bytes
+
+
+class Server:
+    def __init__(self, ctx, budget_bytes=150 << 30, streams=3, max_batch=64, max_inflight=256):
+        self.ctx = ctx
+        self.budget = budget_bytes
+        self.streams = [torch.cuda.Stream() for _ in range(streams)]
+        self.max_batch = max_batch
+        self.max_inflight = max_inflight
+        self.shapes = {}
+
+    def shape(self, sym, D, dtype):
+        key = (sym, D, dtype)
+        if key not in self.shapes:
+            self.shapes[key] = Shape(self.ctx, sym, D, dtype)
+        return self.shapes[key]
+
+    def run(self, requests, rate_per_s, keep_outputs=False):
+        """Serve `requests` (from request_stream) arriving at rate_per_s; returns per-request
+        latencies (ms) and summary figures.  keep_outputs keeps every result for checking."""
+        for r in requests:  # plans and resident inputs first: no plan building inside the timed loop
+            self.shape(r["sym"], r["D"], r["dtype"])
+        arrivals = np.cumsum([r["gap"] for r in requests]) / rate_per_s
+        torch.cuda.synchronize()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_start.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        host0 = time.perf_counter()
+        pending = list(range(len(requests)))  # in arrival order
+        queue, inflight, done = [], [], {}
+        in_use, slots, next_stream, p = 0, 0, 0, 0
+        outputs = {}
+        batches = 0
+        while p < len(pending) or queue or inflight:
+            now = time.perf_counter() - host0
+            while p < len(pending) and arrivals[pending[p]] <= now:
+                queue.append(pending[p])
+                p += 1
+            # retire finished batches
+            still = []
+            for b in inflight:
+                if b["end"].query():
+                    t_end = t_start.elapsed_time(b["end"])  # ms since start, device clock
+                    for i in b["reqs"]:
+                        done[i] = t_end - 1e3 * arrivals[i]
+                    in_use -= b["bytes"]
+                    slots -= len(b["reqs"])
+                    if not keep_outputs:
+                        b["bufs"] = None
+                else:
+                    still.append(b)
+            inflight = still
+            # admit and launch, one batch per dtype
+            admitted = {"f64": [], "c128": []}
+            rest = []
+            for i in queue:
+                r = requests[i]
+                sh = self.shape(r["sym"], r["D"], r["dtype"])
+                group = admitted[r["dtype"]]
+                if (in_use + sh.bytes <= self.budget and slots < self.max_inflight and len(group) < self.max_batch):
+                    group.append(i)
+                    in_use += sh.bytes
+                    slots += 1
+                else:
+                    rest.append(i)
+            queue = rest
+            for dt, group in admitted.items():
+                if not group:
+                    continue
+                stream = self.streams[next_stream % len(self.streams)]
+                next_stream += 1
+                with torch.cuda.stream(stream):
+                    shapes = [self.shape(requests[i]["sym"], requests[i]["D"], dt) for i in group]
+                    outs = [torch.empty(sh.out_numel, dtype=sh.tdt, device="cuda") for sh in shapes]
+                    wss = [torch.empty(sh.ws_bytes, dtype=torch.uint8, device="cuda") for sh in shapes]
+                    api.contract_batch(self.ctx, [sh.plan for sh in shapes], [sh.a for sh in shapes],
+                                       [sh.b for sh in shapes], outs, wss, stream)
+                    end = torch.cuda.Event(enable_timing=True)
+                    end.record(stream)
+                batches += 1
+                inflight.append(dict(reqs=group, end=end, bytes=sum(sh.bytes for sh in shapes),
+                                     bufs=(outs, wss)))
+                if keep_outputs:
+                    for i, o in zip(group, outs):
+                        outputs[i] = o
+            if not admitted["f64"] and not admitted["c128"]:
+                time.sleep(20e-6)  # nothing to launch: wait for arrivals or completions
+        torch.cuda.synchronize()
+        lat = np.array([done[i] for i in range(len(requests))])
+        flops = sum(self.shape(r["sym"], r["D"], r["dtype"]).flops for r in requests)
+        # from the first arrival to the last completion, on the device clock
+        makespan = max(float(np.max(lat + 1e3 * arrivals)) - 1e3 * float(arrivals[0]), 1e-9)
+        summary = {
+            "requests": len(requests), "batches": batches, "rate_per_s": rate_per_s,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "throughput_req_per_s": len(requests) / (makespan * 1e-3),
+            "block_gflops": flops / (makespan * 1e-3) / 1e9,
+            "makespan_ms": makespan,
+        }
+        return lat, summary, outputs
+
+
+def calibrated_rate(server, requests, load=0.7):
+    """Arrival rate that keeps the GPU about `load` busy: each shape's service time is measured
+    once with tk_contract on its own, and the rate is load / mean service time."""
+    times = {}
+    for key, sh in server.shapes.items():
+        c = torch.empty(sh.out_numel, dtype=sh.tdt, device="cuda")
+        ws = torch.empty(sh.ws_bytes, dtype=torch.uint8, device="cuda")
+        api.contract(server.ctx, sh.plan, sh.a, sh.b, c, ws)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(3):
+            api.contract(server.ctx, sh.plan, sh.a, sh.b, c, ws)
+        e.record()
+        torch.cuda.synchronize()
+        times[key] = s.elapsed_time(e) / 3 * 1e-3
+    mean = float(np.mean([times[(r["sym"], r["D"], r["dtype"])] for r in requests]))
+    return load / mean, mean
+
+

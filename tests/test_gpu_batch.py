@@ -1,0 +1,91 @@
+"""tk_contract_batch: many requests whose stages share launches give, for every request, the
+bits tk_contract gives for that request alone (same tiles, same order of operations)."""
+
+import numpy as np
+import pytest
+
+from paper_2508_10076_gb300 import build_library
+from paper_2508_10076_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gctx():
+    assert torch.cuda.is_available()
+    build_library()
+    from paper_2508_10076_gb300 import api
+    ctx = api.Context(0)
+    yield ctx
+    ctx.sync()
+
+
+def _tm(ctx, sym, legs):
+    cod, dom = legs
+    return ctx.tmap([ctx.space(sym, s, d) for s, d in cod], [ctx.space(sym, s, d) for s, d in dom])
+
+
+def _requests(ctx, dtype, seed0):
+    """(plan, A data, B data) for a mix of shapes: U(1) and SU(2) L.x, C0, a zero-block case,
+    and one shape twice (two requests sharing a plan)."""
+    from paper_2508_10076_gb300 import api
+    reqs = []
+    rnd = wl.normal_complex if dtype == "c128" else wl.normal
+    tdt = torch.complex128 if dtype == "c128" else torch.float64
+    for k, (sym, D) in enumerate([("U1", 256), ("SU2", 96), ("U1", 256), ("U1", 96), ("SU2", 32)]):
+        V, P, W = wl.heff_spaces(sym, D)
+        legs = wl.heff_legs(V, P, W)
+        L, x = _tm(ctx, sym, legs["L"]), _tm(ctx, sym, legs["x"])
+        plan = api.contract_plan(ctx, L, *wl.LX_SPEC[:2], x, *wl.LX_SPEC[2:], dtype=dtype)
+        reqs.append((plan, rnd(seed0 + 2 * k, L.numel), rnd(seed0 + 2 * k + 1, x.numel)))
+    v = {-2: 1, -1: 2, 0: 3, 1: 2, 2: 1}
+    A = _tm(ctx, "U1", ([(v, False), (v, False)], [(v, False), (v, False)]))
+    B = _tm(ctx, "U1", ([(v, False), (v, True)], [(v, False), (v, False)]))
+    plan = api.contract_plan(ctx, A, *wl.C0_SPEC[:2], B, *wl.C0_SPEC[2:], dtype=dtype)
+    reqs.append((plan, rnd(seed0 + 20, A.numel), rnd(seed0 + 21, B.numel)))
+    A = _tm(ctx, "U1", ([({0: 2, 1: 3}, False)], [({0: 3}, False)]))
+    B = _tm(ctx, "U1", ([({0: 3}, False)], [({0: 2, 1: 1}, False)]))
+    plan = api.contract_plan(ctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), dtype=dtype)
+    reqs.append((plan, rnd(seed0 + 22, A.numel), rnd(seed0 + 23, B.numel)))
+    dev = [(p, torch.from_numpy(np.ascontiguousarray(a)).to("cuda", tdt),
+            torch.from_numpy(np.ascontiguousarray(b)).to("cuda", tdt)) for p, a, b in reqs]
+    return dev, tdt
+
+
+@pytest.mark.parametrize("dtype", ["f64", "c128"])
+def test_batch_equals_each_request_alone(gctx, dtype):
+    from paper_2508_10076_gb300 import api
+    reqs, tdt = _requests(gctx, dtype, 40)
+    alone, outs, wss = [], [], []
+    for plan, a, b in reqs:
+        c = torch.full((plan.output().numel,), float("nan"), dtype=tdt, device="cuda")
+        ws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
+        api.contract(gctx, plan, a, b, c, ws)
+        alone.append(c)
+        outs.append(torch.full_like(c, float("nan")))
+        wss.append(torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda"))
+    api.contract_batch(gctx, [r[0] for r in reqs], [r[1] for r in reqs], [r[2] for r in reqs], outs, wss)
+    gctx.sync()
+    for i, (x, y) in enumerate(zip(alone, outs)):
+        assert torch.equal(x, y), i
+
+
+def test_batch_rejects_mixed_modes_and_small_workspace(gctx):
+    from paper_2508_10076_gb300 import api
+    reqs, tdt = _requests(gctx, "f64", 60)
+    plan, a, b = reqs[0]
+    c = torch.empty(plan.output().numel, dtype=tdt, device="cuda")
+    small = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(api.TKError) as e:
+        api.contract_batch(gctx, [plan], [a], [b], [c], [small])
+    assert e.value.code == 9
+    V, P, W = wl.heff_spaces("U1", 256)
+    legs = wl.heff_legs(V, P, W)
+    L, x = _tm(gctx, "U1", legs["L"]), _tm(gctx, "U1", legs["x"])
+    oz = api.contract_plan(gctx, L, *wl.LX_SPEC[:2], x, *wl.LX_SPEC[2:], gemm="ozaki")
+    ws = torch.empty(max(1, oz.workspace_bytes), dtype=torch.uint8, device="cuda")
+    with pytest.raises(api.TKError) as e:
+        api.contract_batch(gctx, [oz], [a], [b], [c], [ws])
+    assert e.value.code == 7
+    api.contract_batch(gctx, [], [], [], [], [])  # empty batch: no-op

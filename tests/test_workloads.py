@@ -47,3 +47,21 @@ def test_heff_output_has_structure_of_x():
     st, _ = oracle_heff_inputs("U1", 16)
     out = oracle_heff("U1", 16, steps=4)[-1][0]
     assert out.blocks == st["x"].blocks
+
+
+def test_serving_request_stream_is_seeded_and_mixed():
+    from paper_2508_10076_gb300.serve import dimension_grid, request_stream
+    grid = dimension_grid()
+    assert grid[0] == 64 and grid[-1] == 4096 and len(grid) == 25
+    a, b = request_stream(4000, seed=3), request_stream(4000, seed=3)
+    assert a == b
+    syms = {r["sym"] for r in a}
+    dts = {r["dtype"] for r in a}
+    assert syms == {"U1", "SU2"} and dts == {"f64", "c128"}
+    frac_u1 = sum(r["sym"] == "U1" for r in a) / len(a)
+    frac_c = sum(r["dtype"] == "c128" for r in a) / len(a)
+    assert abs(frac_u1 - 0.5) < 0.05 and abs(frac_c - 0.5) < 0.05
+    assert all(r["D"] in grid for r in a)
+    # log-uniform: about as many draws below sqrt(64 * 4096) = 512 as above
+    below = sum(r["D"] < 512 for r in a) / len(a)
+    assert 0.4 < below < 0.6
