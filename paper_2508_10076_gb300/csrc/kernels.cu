@@ -102,7 +102,7 @@ static_assert(sizeof(PermTask) % sizeof(int64_t) == 0, "PermTask must be 8-byte 
 // One launch serves up to four segments (the run list and the tile list of up to two permutes,
 // e.g. both operands of a contraction); each segment owns a contiguous range of blocks.
 struct PermSeg {
-  int32_t kind;    // 0: contiguous runs, 1: tiles
+  int32_t kind;    // 0: contiguous runs, 1: tiles, 2: clear nwork ints at out (split-K counters)
   int32_t ntasks;  // tiles: number of tasks (binary search range)
   int64_t block0, nblocks, nwork;  // blocks [block0, block0 + nblocks); runs or tiles to do
   const PermRun* runs;
@@ -112,7 +112,7 @@ struct PermSeg {
   const void* in;
   void* out;
 };
-constexpr int kMaxPermSegs = 4;       // one contraction: runs + tiles of two operands
+constexpr int kMaxPermSegs = 6;       // one contraction: runs + tiles of two operands, counter clears
 constexpr int kBatchSegs = 160;       // a packed launch over many requests (about 13 KB of parameters)
 template <int NSEG>
 struct PermLaunchT {
@@ -256,10 +256,14 @@ __global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermLau
   __shared__ int64_t task_words[kTaskWords];
   const PermSeg& g = L.seg[find_seg(L.seg, L.nseg, (int64_t)blockIdx.x)];
   const int64_t bid = (int64_t)blockIdx.x - g.block0;
-  if (g.kind == 0)
+  if (g.kind == 0) {
     permute_runs<T>(g, bid);
-  else
+  } else if (g.kind == 1) {
     permute_tiles<T>(g, bid, tile, task_words);
+  } else {
+    int* p = (int*)g.out;
+    for (int64_t i = bid * blockDim.x + threadIdx.x; i < g.nwork; i += g.nblocks * blockDim.x) p[i] = 0;
+  }
 }
 
 // ------------------------------------------------------------------ K2 grouped FP64 GEMM
@@ -776,12 +780,26 @@ int64_t fill_perm_launch(PermLaunchT<NSEG>& L, const PermSeg* segs, const int64_
 }
 }  // namespace
 
-int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream) {
+int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream, const IntClear* clears, int nclears) {
   std::vector<PermSeg> segs;
   std::vector<int64_t> natural;
   int dtype = TK_F64;
   perm_segments(jobs, njobs, segs, natural, dtype);
-  if (segs.empty()) return TK_OK;
+  if (segs.empty()) {  // nothing to permute: clear with plain memsets
+    for (int i = 0; i < nclears; ++i)
+      if (cudaMemsetAsync(clears[i].p, 0, (size_t)clears[i].n * sizeof(int), (cudaStream_t)stream) != cudaSuccess)
+        return TK_ERR_CUDA;
+    return TK_OK;
+  }
+  for (int i = 0; i < nclears; ++i) {  // ride along in the permute launch that precedes the GEMM
+    PermSeg g;
+    std::memset(&g, 0, sizeof(g));
+    g.kind = 2;
+    g.nwork = clears[i].n;
+    g.out = clears[i].p;
+    segs.push_back(g);
+    natural.push_back(1);
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t cap = (int64_t)std::max(ctx->num_sms, 1) * 8;
   ProfScope prof(ctx, "k_permute", stream);
@@ -810,7 +828,7 @@ int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream) {
 
 int launch_permute(Ctx* ctx, const PermutePlan& pp, const void* in, void* out, void* stream) {
   const PermJob job{&pp, in, out};
-  return launch_permutes(ctx, &job, 1, stream);
+  return launch_permutes(ctx, &job, 1, stream, nullptr, 0);
 }
 
 int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
@@ -973,11 +991,10 @@ int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b,
   void* ct = cp.pc ? (void*)(w + cp.ws_ct) : c;
   int rc;
   const PermJob in_jobs[2] = {{cp.pa.get(), a, (void*)at}, {cp.pb.get(), b, (void*)bt}};
-  if ((rc = launch_permutes(ctx, in_jobs, 2, stream)) != TK_OK) return rc;  // both operands, one launch
+  const IntClear clear{(int*)(w + cp.ws_counters), (int64_t)cp.split_slots};
+  // both operands in one launch, which also clears the split-K counters
+  if ((rc = launch_permutes(ctx, in_jobs, 2, stream, &clear, cp.split_slots > 0 ? 1 : 0)) != TK_OK) return rc;
   if ((rc = launch_zero(ctx, cp, ct, stream)) != TK_OK) return rc;
-  if (cp.split_slots > 0 &&
-      cudaMemsetAsync(w + cp.ws_counters, 0, (size_t)cp.split_slots * sizeof(int), (cudaStream_t)stream) != cudaSuccess)
-    return TK_ERR_CUDA;
   if (!cp.gemms_fp64.empty() &&
       (rc = launch_gemm_fp64(ctx, cp, at, bt, ct, w + cp.ws_partials, (int*)(w + cp.ws_counters), stream)) != TK_OK)
     return rc;
@@ -994,6 +1011,7 @@ int run_contract_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const 
   std::vector<const void*> at((size_t)n), bt((size_t)n);
   std::vector<void*> ct((size_t)n);
   std::vector<PermJob> in_jobs, out_jobs;
+  std::vector<IntClear> clears;
   for (int i = 0; i < n; ++i) {
     const ContractPlan& cp = *plans[i];
     char* w = (char*)ws[i];
@@ -1003,11 +1021,9 @@ int run_contract_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const 
     in_jobs.push_back({cp.pa.get(), a[i], (void*)at[i]});
     in_jobs.push_back({cp.pb.get(), b[i], (void*)bt[i]});
     if (cp.pc) out_jobs.push_back({cp.pc.get(), ct[i], c[i]});
-    if (cp.split_slots > 0 &&
-        cudaMemsetAsync(w + cp.ws_counters, 0, (size_t)cp.split_slots * sizeof(int), s) != cudaSuccess)
-      return TK_ERR_CUDA;
+    if (cp.split_slots > 0) clears.push_back({(int*)(w + cp.ws_counters), (int64_t)cp.split_slots});
   }
-  int rc = launch_permutes(ctx, in_jobs.data(), (int)in_jobs.size(), stream);
+  int rc = launch_permutes(ctx, in_jobs.data(), (int)in_jobs.size(), stream, clears.data(), (int)clears.size());
   if (rc != TK_OK) return rc;
   // zero fill of blocks with an empty inner dimension, all requests in one launch per 160
   {
@@ -1076,7 +1092,7 @@ int run_contract_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const 
     }
     if ((rc = flush()) != TK_OK) return rc;
   }
-  return launch_permutes(ctx, out_jobs.data(), (int)out_jobs.size(), stream);
+  return launch_permutes(ctx, out_jobs.data(), (int)out_jobs.size(), stream, nullptr, 0);
 }
 
 }  // namespace tk

@@ -247,7 +247,10 @@ __device__ __forceinline__ int exponent_of(double mx) {
 
 __global__ void __launch_bounds__(256) k_oz_scale(const OzSector* __restrict__ secs, const OzJob* __restrict__ jobs,
                                                   const double* __restrict__ A, const double* __restrict__ B,
-                                                  int32_t* __restrict__ scale_a, int32_t* __restrict__ scale_b) {
+                                                  int32_t* __restrict__ scale_a, int32_t* __restrict__ scale_b,
+                                                  int* __restrict__ counters, int ncounters) {
+  if (blockIdx.x == 0)  // the GEMM's split-K arrival counters start at zero
+    for (int i = threadIdx.x; i < ncounters; i += blockDim.x) counters[i] = 0;
   const OzJob jb = jobs[blockIdx.x];
   const OzSector s = secs[jb.sector];
   const int64_t k0 = (int64_t)jb.kc * OZ_SCALE_KCHUNK;
@@ -820,13 +823,12 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
   }
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(sa, 0x80, L->off_sb - L->off_sa + (size_t)L->ncols_b * 4, s) != cudaSuccess) return TK_ERR_CUDA;
-  int* counters = (int*)(w + L->off_cnt);
-  if (L->nslots > 0 && cudaMemsetAsync(counters, 0, (size_t)L->nslots * OZ_EPI_WARPS * sizeof(int), s) != cudaSuccess)
-    return TK_ERR_CUDA;
+  int* counters = (int*)(w + L->off_cnt);  // cleared by the scale kernel
   {
     ProfScope prof(ctx, "k_oz_scale", stream);
     k_oz_scale<<<(unsigned)L->nscale_jobs, 256, 0, s>>>(L->d_sectors, L->d_scale_jobs, (const double*)a,
-                                                       (const double*)b, sa, sb);
+                                                       (const double*)b, sa, sb, counters,
+                                                       (int)(L->nslots * OZ_EPI_WARPS));
     if (cudaGetLastError() != cudaSuccess) return TK_ERR_CUDA;
     ctx->launches += 1;
   }

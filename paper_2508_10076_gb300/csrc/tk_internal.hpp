@@ -243,8 +243,13 @@ struct PermJob {
   const void* in;
   void* out;
 };
-// Several permutes in one launch (identity plans are skipped; at most two plans).
-int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream);
+struct IntClear {
+  int* p;
+  int64_t n;
+};
+// Several permutes in one launch (identity plans are skipped; more than 160 segments take several
+// launches), optionally also clearing int arrays (split-K counters) in the same launch.
+int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream, const IntClear* clears, int nclears);
 int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
                      void* partials, int* counters, void* stream);
 int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream);
