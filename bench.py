@@ -310,11 +310,10 @@ def run_ours(args):
     e2e_ms = max_over_ranks(dist, e2e_ms)
     e2e_value = job_throughput(flops, args.steps, world, e2e_ms)
     ctx.sync()
-    # ---------------- split-precision variant of the same workload (Ozaki BF16 on tcgen05)
-    split = None
-    if not args.no_split:
-        ref_out = run().clone()
-        oz = _workload(ctx, args.config, "ozaki", seed=replica_seed(rank))
+    # ---------------- split-precision variants of the same workload on tcgen05: Ozaki BF16 slices
+    # (s = 6, 21 slice pairs) and 3xTF32 (3 products, tensor rate half of BF16)
+    def split_variant(gemm, ref_out):
+        oz = _workload(ctx, args.config, gemm, seed=replica_seed(rank))
         for _ in range(max(3, args.warmup)):
             oz.run()
         oz_fn = oz.run
@@ -350,20 +349,30 @@ def run_ours(args):
             n_ = float(torch.linalg.norm(ref_out[o_:o_ + r_ * k_]))
             worst = max(worst, d / (n_ if n_ > 1e-13 * refn else refn))
         oz_kms = oz_prof.get("k_oz_gemm", (0, 0.0))[1]
-        pairs = 21  # slice pairs i + j <= s - 1 at s = 6
-        bf16_peak = _peaks().get("bf16_tflops")
-        split_roof = None
+        if gemm == "ozaki":
+            products, peak, peak_key = 21, _peaks().get("bf16_tflops"), "measured bf16_tflops (burst)"
+        else:  # TF32 dense rate is half of BF16 on this part (nominal 1.1 vs 2.25 PFLOP/s)
+            bf = _peaks().get("bf16_tflops")
+            products, peak, peak_key = 3, (bf / 2 if bf else None), "measured bf16_tflops (burst) x 1/2 (nominal TF32:BF16)"
+        roof = None
         if oz_kms > 0 and oz.tensor_flops > 0:
-            executed = pairs * oz.tensor_flops * args.steps / (oz_kms * 1e-3) / 1e12
-            split_roof = {"kernel": "k_oz_gemm", "bound": "tensor", "achieved": executed, "peak": bf16_peak,
-                          "unit": "TFLOP/s", "frac": executed / bf16_peak if bf16_peak else None,
-                          "traffic": None, "peak_source": "measured bf16_tflops (burst)",
-                          "note": "achieved = 21 slice pairs x tensor-path block flops / k_oz_gemm time"}
-        split = {"value": job_throughput(flops, args.steps, world, oz_ms), "unit": UNIT,
-                 "ms_per_step": oz_ms / args.steps, "slices": 6, "roofline": split_roof,
-                 "tensor_path_flops_per_step": oz.tensor_flops,
-                 "rel_frobenius_per_block_vs_fp64_path": worst,
-                 "kernels": {k: {"launches": c, "ms_per_step": ms / args.steps} for k, (c, ms) in oz_prof.items()}}
+            executed = products * oz.tensor_flops * args.steps / (oz_kms * 1e-3) / 1e12
+            roof = {"kernel": "k_oz_gemm", "bound": "tensor", "achieved": executed, "peak": peak,
+                    "unit": "TFLOP/s", "frac": executed / peak if peak else None, "traffic": None,
+                    "peak_source": peak_key,
+                    "note": f"achieved = {products} products x tensor-path block flops / k_oz_gemm time"}
+        return {"value": job_throughput(flops, args.steps, world, oz_ms), "unit": UNIT,
+                "ms_per_step": oz_ms / args.steps, "roofline": roof,
+                "tensor_path_flops_per_step": oz.tensor_flops,
+                "rel_frobenius_per_block_vs_fp64_path": worst,
+                "kernels": {k: {"launches": c, "ms_per_step": ms / args.steps} for k, (c, ms) in oz_prof.items()}}
+
+    split = tf32 = None
+    if not args.no_split:
+        ref_out = run().clone()
+        split = split_variant("ozaki", ref_out)
+        split["slices"] = 6
+        tf32 = split_variant("tf32x3", ref_out)
     # ---------------- serving: Poisson stream of mixed requests through the continuous-batching loop
     serve = None
     if args.serve_requests > 0:
@@ -418,6 +427,8 @@ def run_ours(args):
     }
     if split is not None:
         line["split_precision"] = split
+    if tf32 is not None:
+        line["split_precision_tf32x3"] = tf32
     if serve is not None:
         line["serve"] = serve
     if world == 1 and not args.no_cpu_baseline:

@@ -31,6 +31,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 
 #include "tk_device.cuh"
@@ -42,8 +43,17 @@ namespace {
 constexpr int OZ_BM = 128, OZ_BK = 32;              // k-chunk: two MMA K steps
 constexpr int OZ_BN_WIDE = 128, OZ_BN_NARROW = 64;  // output tile widths (one / two TMEM buffers)
 constexpr int OZ_TROWS = 128;                     // rows of a slice tile in memory (A: m, B: n)
-constexpr int OZ_TILE_BYTES = OZ_TROWS * OZ_BK * 2;  // slice tiles are 128 x 32 BF16 (8 KB, 64-byte rows)
-constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;     // A box in shared memory: 128 x 32
+// Two product schemes share the pipeline (template parameter MODE):
+//   MODE 0, Ozaki BF16: s BF16 slices per operand, pairs i + j <= s - 1 into four level accumulators;
+//   MODE 1, 3xTF32: a = hi + lo with hi, lo TF32 (FP32 containers, 13 low mantissa bits zero);
+//     products hi.hi + hi.lo + lo.hi into one FP32 accumulator (about FP32 accuracy).
+template <int MODE>
+struct OzMode {
+  static constexpr int ESZ = MODE == 0 ? 2 : 4;          // bytes per slice element
+  static constexpr int ROW = OZ_BK * ESZ;                // bytes of one tile row (64 or 128)
+  static constexpr int A_BYTES = OZ_BM * ROW;            // A box in shared memory
+  static constexpr int MMAS = ROW / 32;                  // MMAs per k-chunk and pair (32 B of K each)
+};
 constexpr int OZ_MAX_STAGES = 4;                  // a stage holds all s A and s B boxes of a k-chunk
 constexpr int OZ_SEG_KC = 32;                     // k-chunks per exact segment (K <= 1024)
 constexpr int OZ_NACC = 4;
@@ -82,6 +92,7 @@ struct OzLayout {
   int64_t ntiles_a = 0, ntiles_b = 0, nrows_a = 0, ncols_b = 0;
   size_t off_ta = 0, off_tb = 0, off_sa = 0, off_sb = 0, bytes = 0;
   int slices = OZ_DEFAULT_SLICES;
+  int mode = 0;           // 0: Ozaki BF16 slices, 1: 3xTF32
   int bn = OZ_BN_NARROW;  // output tile width of this launch
   OzPairs pairs;
   int64_t nwork = 0, nslice_jobs = 0, nscale_jobs = 0;
@@ -158,6 +169,22 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uin
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+template <int MODE>
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  if (MODE == 0)
+    tc_mma_bf16(d_tmem, adesc, bdesc, idesc, accumulate);
+  else
+    tc_mma_tf32(d_tmem, adesc, bdesc, idesc, accumulate);
+}
 __device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
@@ -165,23 +192,27 @@ __device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row groups 512 B apart.
-__device__ __forceinline__ uint64_t smem_desc_k_sw64(uint32_t addr) {
+// Shared-memory matrix descriptor: K-major operand, rows of ROW bytes with the matching swizzle
+// (64 B: 64-byte swizzle, 128 B: 128-byte swizzle), 8-row groups 8 ROW bytes apart.
+template <int ROW>
+__device__ __forceinline__ uint64_t smem_desc_k(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);        // start address
   d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(512 >> 4) << 32;               // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)((8 * ROW) >> 4) << 32;         // stride byte offset: 8 rows
   d |= (uint64_t)1 << 46;                        // descriptor version (sm_100 family)
-  d |= (uint64_t)4 << 61;                        // layout: 64-byte swizzle
+  d |= (uint64_t)(ROW == 128 ? 2 : 4) << 61;     // layout: 128-byte / 64-byte swizzle
   return d;
 }
-// Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both operands K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-  return (1u << 4)                     // D format: F32
-         | (1u << 7)                   // A format: BF16
-         | (1u << 10)                  // B format: BF16
-         | ((uint32_t)(n >> 3) << 17)  // N / 8
-         | ((uint32_t)(m >> 4) << 24); // M / 16
+// Instruction descriptor: FP32 accumulate, both operands K-major, M x N; A and B both BF16
+// (kind::f16, format 1) or both TF32 (kind::tf32, format 2).
+template <int MODE>
+__host__ __device__ constexpr uint32_t idesc_mma(int m, int n) {
+  return (1u << 4)                                  // D format: F32
+         | ((MODE == 0 ? 1u : 2u) << 7)             // A format
+         | ((MODE == 0 ? 1u : 2u) << 10)            // B format
+         | ((uint32_t)(n >> 3) << 17)               // N / 8
+         | ((uint32_t)(m >> 4) << 24);              // M / 16
 }
 
 __device__ __noinline__ double scale_pow2_slow(double v, int e) { return ldexp(v, e); }
@@ -288,15 +319,57 @@ __global__ void __launch_bounds__(256) k_oz_scale(const OzSector* __restrict__ s
   }
 }
 
+// v 2^-e (|v| < 2^e) as hi + lo, both TF32 values in FP32 containers (11 significant bits, the
+// 13 low mantissa bits zero), by integer operations on the FP64 bit pattern: hi is v 2^-e rounded
+// to 11 bits, lo the remainder rounded to 11 bits.  Parts below the FP32 normal range are
+// dropped (they are below 2^-126 of the row's or column's scale).
+__device__ __forceinline__ void tf32_split(double v, int e, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  hi = lo = 0.f;
+  if (ex == 0) return;  // zero, or an FP64 subnormal: far below any scale
+  const uint32_t sign = (uint32_t)(b >> 63) << 31;
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  int E = ex - 1023 - e;  // v 2^-e = m 2^(E - 52)
+  unsigned long long mh = (m + (1ull << 41)) >> 42;  // 11 bits, or 2^11 after rounding up
+  const long long r = (long long)m - (long long)(mh << 42);  // remainder, |r| <= 2^41
+  const int Er = E;
+  if (mh >> 11) {
+    mh >>= 1;
+    E += 1;
+  }
+  if (E + 127 <= 0) return;
+  hi = __uint_as_float(sign | ((uint32_t)(E + 127) << 23) | ((uint32_t)(mh - 1024) << 13));
+  if (r == 0) return;
+  unsigned long long ar = (unsigned long long)(r < 0 ? -r : r);
+  int p = 63 - __clzll((long long)ar);  // leading one of |r|
+  unsigned long long q;
+  if (p > 10) {
+    q = (ar + (1ull << (p - 11))) >> (p - 10);
+    if (q >> 11) {
+      q >>= 1;
+      p += 1;
+    }
+  } else {
+    q = ar << (10 - p);
+  }
+  const int el = Er - 52 + p + 127;  // FP32 exponent field of lo
+  if (el <= 0) return;
+  const uint32_t slo = r < 0 ? (sign ^ 0x80000000u) : sign;
+  lo = __uint_as_float(slo | ((uint32_t)el << 23) | ((uint32_t)(q - 1024) << 13));
+}
+
 // One 128 x 32 (rows x k) tile of one operand per CTA, all slices.  Lanes run along k, so each
-// warp writes 64 contiguous bytes of a tile row per slice; A~ (column-major, rows contiguous) is
-// staged through shared memory to keep its reads coalesced, B~ (k contiguous) is read directly.
+// warp writes one contiguous tile row per slice; A~ (column-major, rows contiguous) is staged
+// through shared memory to keep its reads coalesced, B~ (k contiguous) is read directly.
+// MODE 0 writes s BF16 digit slices, MODE 1 the TF32 pair (hi, lo).
+template <int MODE>
 __global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ secs, const OzJob* __restrict__ jobs,
                                                   const double* __restrict__ A, const double* __restrict__ B,
                                                   const int32_t* __restrict__ scale_a,
-                                                  const int32_t* __restrict__ scale_b,
-                                                  __nv_bfloat16* __restrict__ tiles_a,
-                                                  __nv_bfloat16* __restrict__ tiles_b, int nslices) {
+                                                  const int32_t* __restrict__ scale_b, void* __restrict__ tiles_a,
+                                                  void* __restrict__ tiles_b, int nslices) {
+  using Elt = typename std::conditional<MODE == 0, __nv_bfloat16, float>::type;
   __shared__ double xs[OZ_BK][OZ_TROWS + 1];
   const OzJob jb = jobs[blockIdx.x];
   const OzSector s = secs[jb.sector];
@@ -316,7 +389,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ s
   const int64_t nrt = op == 0 ? s.nmt : s.nnt;
   const int64_t tile0 = (op == 0 ? s.ta_base : s.tb_base) + rt * s.nkc + jb.kc;  // slice 0
   const int64_t slice_stride = nrt * s.nkc * (int64_t)(OZ_TROWS * OZ_BK);  // elements
-  __nv_bfloat16* dst0 = (op == 0 ? tiles_a : tiles_b) + tile0 * (OZ_TROWS * OZ_BK) + kl;
+  Elt* dst0 = (Elt*)(op == 0 ? tiles_a : tiles_b) + tile0 * (OZ_TROWS * OZ_BK) + kl;
   const int32_t* scl = op == 0 ? scale_a + s.sa_off : scale_b + s.sb_off;
 #pragma unroll 4
   for (int i = 0; i < OZ_TROWS / 8; ++i) {
@@ -329,15 +402,22 @@ __global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ s
       v = (r < R && k < s.K) ? __ldg(B + s.b_off + k + r * s.K) : 0.0;
     int e = (r < R) ? scl[r] : 0;
     if (e == kNoScale) e = 0;  // an all-zero row or column
-    long long q = round_scaled(v, 7 * nslices - e);  // round(v 2^(7 s - e)), |q| <= 2^(7 s)
-    __nv_bfloat16* dst = dst0 + rl * OZ_BK;
-    for (int sl = nslices - 1; sl >= 1; --sl) {
-      const long long d = ((q + 64) & 127) - 64;  // balanced base-128 digit
-      q = (q - d) >> 7;
-      // |d| <= 64: convert through a 32-bit integer (a 64-bit conversion runs on the FP64 pipe)
-      dst[sl * slice_stride] = __float2bfloat16_rn((float)(int)d * __int_as_float((127 - 7 * (sl + 1)) << 23));
+    Elt* dst = dst0 + rl * OZ_BK;
+    if constexpr (MODE == 0) {
+      long long q = round_scaled(v, 7 * nslices - e);  // round(v 2^(7 s - e)), |q| <= 2^(7 s)
+      for (int sl = nslices - 1; sl >= 1; --sl) {
+        const long long d = ((q + 64) & 127) - 64;  // balanced base-128 digit
+        q = (q - d) >> 7;
+        // |d| <= 64: convert through a 32-bit integer (a 64-bit conversion runs on the FP64 pipe)
+        dst[sl * slice_stride] = (Elt)__float2bfloat16_rn((float)(int)d * __int_as_float((127 - 7 * (sl + 1)) << 23));
+      }
+      dst[0] = (Elt)__float2bfloat16_rn((float)(int)q * __int_as_float((127 - 7) << 23));  // |q| <= 128 here
+    } else {
+      float hi, lo;
+      tf32_split(v, e, hi, lo);
+      dst[0] = (Elt)hi;
+      dst[slice_stride] = (Elt)lo;
     }
-    dst[0] = __float2bfloat16_rn((float)(int)q * __int_as_float((127 - 7) << 23));  // |q| <= 128 here
   }
 }
 
@@ -349,60 +429,70 @@ struct OzSmem {
   int abort_flag;
 };
 
-// Shared memory: stages of [A_0 .. A_{s-1} | B_0 .. B_{s-1}] boxes (A 128 x 32, B BN x 32), then
-// OzSmem: as many stages as fit in 227 KB (at most four).
-__host__ __device__ constexpr size_t oz_stage_bytes(int s, int bn) { return (size_t)s * (OZ_A_BYTES + bn * OZ_BK * 2); }
-__host__ __device__ constexpr int oz_stages(int s, int bn) {
-  return (int)((232448 - sizeof(OzSmem) - 1024) / oz_stage_bytes(s, bn)) < OZ_MAX_STAGES
-             ? (int)((232448 - sizeof(OzSmem) - 1024) / oz_stage_bytes(s, bn))
+// Shared memory: stages of [A_0 .. A_{s-1} | B_0 .. B_{s-1}] boxes (A 128 x 32, B BN x 32 elements
+// of `row` bytes per 32), then OzSmem: as many stages as fit in 227 KB (at most four).
+__host__ __device__ constexpr size_t oz_stage_bytes(int s, int bn, int row) {
+  return (size_t)s * (OZ_BM + bn) * row;
+}
+__host__ __device__ constexpr int oz_stages(int s, int bn, int row) {
+  return (int)((232448 - sizeof(OzSmem) - 1024) / oz_stage_bytes(s, bn, row)) < OZ_MAX_STAGES
+             ? (int)((232448 - sizeof(OzSmem) - 1024) / oz_stage_bytes(s, bn, row))
              : OZ_MAX_STAGES;
 }
-__host__ __device__ constexpr size_t oz_smem_bytes(int s, int bn) {
-  return oz_stages(s, bn) * oz_stage_bytes(s, bn) + sizeof(OzSmem) + 1024;  // + alignment slack
+__host__ __device__ constexpr size_t oz_smem_bytes(int s, int bn, int row) {
+  return oz_stages(s, bn, row) * oz_stage_bytes(s, bn, row) + sizeof(OzSmem) + 1024;  // + alignment slack
 }
 
 // Every slice-pair MMA of one resident stage, unrolled for S slices: pairs grouped by
 // accumulator level (0, 1, 2, >= 3); the first MMA of a level in a segment's first k-chunk
 // overwrites its accumulator.  Descriptors differ from the stage's base descriptor only in the
 // start-address field, so each operand offset is an added constant.
-template <int S, int BN>
+template <int S, int BN, int MODE>
 __device__ __forceinline__ void oz_issue_stage(uint32_t acc0, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                                bool first_kc) {
-  constexpr int B_BYTES = BN * OZ_BK * 2;
+  using M = OzMode<MODE>;
+  constexpr int B_BYTES = BN * M::ROW;
 #pragma unroll
   for (int l = 0; l < OZ_NACC; ++l) {
 #pragma unroll
     for (int i = 0; i < S; ++i) {
 #pragma unroll
       for (int j = 0; j < S - i; ++j) {
-        if ((i + j < OZ_NACC - 1 ? i + j : OZ_NACC - 1) != l) continue;
-        const bool first_of_level = (l < OZ_NACC - 1) ? (i == 0) : (i == 0 && j == OZ_NACC - 1);
+        // 3xTF32: every product into accumulator 0; Ozaki: level i + j (>= 3 together)
+        const int lvl = MODE == 1 ? 0 : (i + j < OZ_NACC - 1 ? i + j : OZ_NACC - 1);
+        if (lvl != l) continue;
+        const bool first_of_level =
+            MODE == 1 ? (i == 0 && j == 0) : ((l < OZ_NACC - 1) ? (i == 0) : (i == 0 && j == OZ_NACC - 1));
 #pragma unroll
-        for (int k16 = 0; k16 < OZ_BK / 16; ++k16)
-          tc_mma_bf16(acc0 + l * BN, adesc + (uint64_t)((i * OZ_A_BYTES + k16 * 32) >> 4),
-                      bdesc + (uint64_t)((S * OZ_A_BYTES + j * B_BYTES + k16 * 32) >> 4), idesc,
-                      (first_kc && first_of_level && k16 == 0) ? 0u : 1u);
+        for (int kk = 0; kk < M::MMAS; ++kk)
+          tc_mma<MODE>(acc0 + l * BN, adesc + (uint64_t)((i * M::A_BYTES + kk * 32) >> 4),
+                       bdesc + (uint64_t)((S * M::A_BYTES + j * B_BYTES + kk * 32) >> 4), idesc,
+                       (first_kc && first_of_level && kk == 0) ? 0u : 1u);
       }
     }
   }
 }
 
-template <int BN>
+template <int BN, int MODE>
 __device__ __forceinline__ void oz_issue(int s, uint32_t acc0, uint32_t sbase, uint32_t idesc, bool first_kc) {
-  const uint64_t d = smem_desc_k_sw64(sbase);
+  const uint64_t d = smem_desc_k<OzMode<MODE>::ROW>(sbase);
+  if (MODE == 1) {  // the TF32 pair
+    oz_issue_stage<2, BN, MODE>(acc0, d, d, idesc, first_kc);
+    return;
+  }
   switch (s) {
-    case 2: oz_issue_stage<2, BN>(acc0, d, d, idesc, first_kc); break;
-    case 3: oz_issue_stage<3, BN>(acc0, d, d, idesc, first_kc); break;
-    case 4: oz_issue_stage<4, BN>(acc0, d, d, idesc, first_kc); break;
-    case 5: oz_issue_stage<5, BN>(acc0, d, d, idesc, first_kc); break;
-    case 6: oz_issue_stage<6, BN>(acc0, d, d, idesc, first_kc); break;
-    default: oz_issue_stage<7, BN>(acc0, d, d, idesc, first_kc); break;
+    case 2: oz_issue_stage<2, BN, MODE>(acc0, d, d, idesc, first_kc); break;
+    case 3: oz_issue_stage<3, BN, MODE>(acc0, d, d, idesc, first_kc); break;
+    case 4: oz_issue_stage<4, BN, MODE>(acc0, d, d, idesc, first_kc); break;
+    case 5: oz_issue_stage<5, BN, MODE>(acc0, d, d, idesc, first_kc); break;
+    case 6: oz_issue_stage<6, BN, MODE>(acc0, d, d, idesc, first_kc); break;
+    default: oz_issue_stage<7, BN, MODE>(acc0, d, d, idesc, first_kc); break;
   }
 }
 
 // BN = 128: one TMEM buffer (4 x 128 columns), the MMAs wait for the epilogue between tiles;
 // BN = 64: two buffers, the epilogue of one tile overlaps the MMAs of the next.
-template <int BN>
+template <int BN, int MODE>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
               const OzSector* __restrict__ secs, const OzWork* __restrict__ work, int nwork,
@@ -412,11 +502,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   extern __shared__ __align__(1024) unsigned char dyn[];
   unsigned char* base = (unsigned char*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
   constexpr int NBUF = OZ_TMEM_COLS / (OZ_NACC * BN);
-  constexpr int B_BYTES = BN * OZ_BK * 2;
+  using MD = OzMode<MODE>;
+  constexpr int B_BYTES = BN * MD::ROW;
   constexpr int SUB = OZ_TROWS / BN;  // B boxes per 128-row slice tile
-  const uint32_t stage_bytes = (uint32_t)oz_stage_bytes(nslices, BN);
-  const uint32_t nstages = (uint32_t)oz_stages(nslices, BN);
-  const uint32_t b_off = (uint32_t)nslices * OZ_A_BYTES;  // B boxes follow the A boxes in a stage
+  const uint32_t stage_bytes = (uint32_t)oz_stage_bytes(nslices, BN, MD::ROW);
+  const uint32_t nstages = (uint32_t)oz_stages(nslices, BN, MD::ROW);
+  const uint32_t b_off = (uint32_t)nslices * MD::A_BYTES;  // B boxes follow the A boxes in a stage
   OzSmem* ss = reinterpret_cast<OzSmem*>(base + nstages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort_flag = &ss->abort_flag;
@@ -462,7 +553,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           mbar_expect_tx(fb, stage_bytes);
           const uint32_t dst = smem_u32(base + st * stage_bytes);
           for (int i = 0; i < nslices; ++i)
-            tma_load_2d(dst + i * OZ_A_BYTES, &tm_a, 0, (int32_t)((ta0 + i * sa_str + kc) * OZ_TROWS), fb);
+            tma_load_2d(dst + i * MD::A_BYTES, &tm_a, 0, (int32_t)((ta0 + i * sa_str + kc) * OZ_TROWS), fb);
           for (int j = 0; j < nslices; ++j)
             tma_load_2d(dst + b_off + j * B_BYTES, &tm_b, 0,
                         (int32_t)((tb0 + j * sb_str + kc) * OZ_TROWS + brow), fb);
@@ -480,7 +571,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       uint32_t it = 0, seg = 0;
       for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
         const OzWork wk = work[w];
-        const uint32_t idesc = idesc_bf16(OZ_BM, wk.nw);
+        const uint32_t idesc = idesc_mma<MODE>(OZ_BM, wk.nw);
         for (int kc0 = wk.kc_lo; kc0 < wk.kc_hi && !*abort_flag; kc0 += OZ_SEG_KC, ++seg) {
           const int kc1 = min(wk.kc_hi, kc0 + OZ_SEG_KC);
           const uint32_t buf = seg % NBUF;
@@ -491,7 +582,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const uint32_t st = it % nstages, ph = (it / nstages) & 1;
             if (!mbar_wait(smem_u32(&ss->full[st]), ph, abort_flag)) break;
             tc_fence_after();
-            oz_issue<BN>(nslices, acc0, smem_u32(base + st * stage_bytes), idesc, kc == kc0);
+            oz_issue<BN, MODE>(nslices, acc0, smem_u32(base + st * stage_bytes), idesc, kc == kc0);
             tc_commit(smem_u32(&ss->empty[st]));  // frees the stage once these MMAs are done
           }
           tc_commit(smem_u32(&ss->acc_full[buf]));  // accumulators of this (item, segment) complete
@@ -631,18 +722,31 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D view [ntiles * 128 rows][32 BF16] with box_rows x 32 boxes and 64-byte swizzle.
-int make_tile_map(CUtensorMap* map, void* base, int64_t ntiles, int box_rows) {
+// 2-D view [ntiles * 128 rows][32 elements] with box_rows x 32 boxes: BF16 with 64-byte swizzle
+// (mode 0) or FP32 with 128-byte swizzle (mode 1).
+int make_tile_map(CUtensorMap* map, void* base, int64_t ntiles, int box_rows, int mode) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return TK_ERR_CUDA;
+  const int esz = mode == 0 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)OZ_BK, (cuuint64_t)(ntiles * OZ_TROWS)};
-  cuuint64_t strides[1] = {(cuuint64_t)OZ_BK * 2};
+  cuuint64_t strides[1] = {(cuuint64_t)OZ_BK * esz};
   cuuint32_t box[2] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = fn(map, mode == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  mode == 0 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? TK_OK : TK_ERR_CUDA;
+}
+
+template <int BN, int MODE>
+int set_smem_attr() {
+  size_t most = 0;  // the largest need over every slice count this kernel accepts
+  for (int sl = 2; sl <= OZ_MAX_SLICES; ++sl) most = std::max(most, oz_smem_bytes(sl, BN, OzMode<MODE>::ROW));
+  return cudaFuncSetAttribute(k_oz_gemm<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) ==
+                 cudaSuccess
+             ? TK_OK
+             : TK_ERR_CUDA;
 }
 
 size_t al1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
@@ -650,13 +754,11 @@ size_t al1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
 }  // namespace
 
 int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
-  if (cp.gemm_mode != TK_GEMM_OZAKI_BF16) {
-    ctx->last_error = "3xTF32 GEMMs are not available in this build";
-    return TK_ERR_UNSUPPORTED;
-  }
   auto L = std::make_shared<OzLayout>();
-  L->slices = cp.slices > 0 ? cp.slices : OZ_DEFAULT_SLICES;
+  L->mode = cp.gemm_mode == TK_GEMM_TF32X3 ? 1 : 0;
+  L->slices = L->mode == 1 ? 2 : (cp.slices > 0 ? cp.slices : OZ_DEFAULT_SLICES);
   if (L->slices < 2 || L->slices > OZ_MAX_SLICES) return TK_ERR_ARG;
+  const size_t tile_bytes = (size_t)OZ_TROWS * OZ_BK * (L->mode == 0 ? 2 : 4);
   // pair list ordered by accumulator level
   OzPairs& P = L->pairs;
   std::memset(&P, 0, sizeof(P));
@@ -664,7 +766,7 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
   for (int lvl = 0; lvl < OZ_NACC; ++lvl)
     for (int i = 0; i < L->slices; ++i)
       for (int j = 0; j < L->slices - i; ++j) {
-        const int l = std::min(i + j, OZ_NACC - 1);
+        const int l = L->mode == 1 ? 0 : std::min(i + j, OZ_NACC - 1);  // 3xTF32: one accumulator
         if (l != lvl) continue;
         if (P.first[l] < 0) P.first[l] = P.n;
         P.i[P.n] = (int8_t)i;
@@ -675,9 +777,10 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
   std::vector<OzWork> work;
   std::vector<OzJob> slice_jobs, scale_jobs;
   std::vector<std::pair<double, OzWork>> wcost;
-  // Tile width: 128-column tiles read 25% less shared memory per MMA flop (8 KB per 128x128x16
-  // MMA instead of 6 KB per 128x64x16) but hold all of TMEM, so their epilogue stalls the MMAs;
-  // they pay off when the average inner dimension per output tile is long.
+  // Tile width: a 128 x N x 16 MMA costs at least ~45 cycles whatever N, so 128-column tiles run
+  // the tensor pipe at full rate where 64-column tiles reach two thirds of it; but 128-column tiles
+  // hold all of TMEM, so their epilogue stalls the MMAs: they pay off when the average inner
+  // dimension per output tile is long.
   {
     double kw = 0, w = 0;
     for (const GemmItem& it : cp.gemms_oz) {
@@ -761,8 +864,8 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
   L->nscale_jobs = (int64_t)scale_jobs.size();
   // workspace layout: A tiles | B tiles | row scales | column scales | split-K partial tiles
   L->off_ta = 0;
-  L->off_tb = al1k((size_t)L->ntiles_a * OZ_TILE_BYTES);
-  L->off_sa = L->off_tb + al1k((size_t)L->ntiles_b * OZ_TILE_BYTES);
+  L->off_tb = al1k((size_t)L->ntiles_a * tile_bytes);
+  L->off_sa = L->off_tb + al1k((size_t)L->ntiles_b * tile_bytes);
   L->off_sb = L->off_sa + al1k((size_t)L->nrows_a * 4);
   L->off_part = L->off_sb + al1k((size_t)L->ncols_b * 4);
   L->off_cnt = L->off_part + al1k((size_t)nslots * OZ_MAX_PARTS * OZ_BM * bn * sizeof(double));
@@ -794,30 +897,24 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
     ctx->last_error = "split-precision workspace must be 16-byte aligned";
     return TK_ERR_WORKSPACE;
   }
-  const size_t smem = oz_smem_bytes(L->slices, L->bn);
+  const size_t smem = oz_smem_bytes(L->slices, L->bn, L->mode == 0 ? OzMode<0>::ROW : OzMode<1>::ROW);
   static bool attr_set[64] = {false};
   if (ctx->device < 64 && !attr_set[ctx->device]) {
-    size_t wide = 0, narrow = 0;  // the largest need over every slice count this kernel accepts
-    for (int sl = 2; sl <= OZ_MAX_SLICES; ++sl) {
-      wide = std::max(wide, oz_smem_bytes(sl, OZ_BN_WIDE));
-      narrow = std::max(narrow, oz_smem_bytes(sl, OZ_BN_NARROW));
-    }
-    if (cudaFuncSetAttribute(k_oz_gemm<OZ_BN_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_oz_gemm<OZ_BN_NARROW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)narrow) !=
-            cudaSuccess) {
+    if (set_smem_attr<OZ_BN_WIDE, 0>() != TK_OK || set_smem_attr<OZ_BN_NARROW, 0>() != TK_OK ||
+        set_smem_attr<OZ_BN_WIDE, 1>() != TK_OK || set_smem_attr<OZ_BN_NARROW, 1>() != TK_OK) {
       ctx->last_error = "cannot reserve shared memory for the split-precision GEMM";
       return TK_ERR_CUDA;
     }
     attr_set[ctx->device] = true;
   }
   char* w = (char*)ws;
-  __nv_bfloat16* ta = (__nv_bfloat16*)(w + L->off_ta);
-  __nv_bfloat16* tb = (__nv_bfloat16*)(w + L->off_tb);
+  void* ta = w + L->off_ta;
+  void* tb = w + L->off_tb;
   int32_t* sa = (int32_t*)(w + L->off_sa);
   int32_t* sb = (int32_t*)(w + L->off_sb);
   CUtensorMap ma, mb;
-  if (make_tile_map(&ma, ta, L->ntiles_a, OZ_BM) != TK_OK || make_tile_map(&mb, tb, L->ntiles_b, L->bn) != TK_OK) {
+  if (make_tile_map(&ma, ta, L->ntiles_a, OZ_BM, L->mode) != TK_OK ||
+      make_tile_map(&mb, tb, L->ntiles_b, L->bn, L->mode) != TK_OK) {
     ctx->last_error = "cuTensorMapEncodeTiled failed";
     return TK_ERR_CUDA;
   }
@@ -834,8 +931,12 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
   }
   {
     ProfScope prof(ctx, "k_oz_slice", stream);
-    k_oz_slice<<<(unsigned)L->nslice_jobs, 256, 0, s>>>(L->d_sectors, L->d_slice_jobs, (const double*)a,
-                                                       (const double*)b, sa, sb, ta, tb, L->slices);
+    if (L->mode == 0)
+      k_oz_slice<0><<<(unsigned)L->nslice_jobs, 256, 0, s>>>(L->d_sectors, L->d_slice_jobs, (const double*)a,
+                                                            (const double*)b, sa, sb, ta, tb, L->slices);
+    else
+      k_oz_slice<1><<<(unsigned)L->nslice_jobs, 256, 0, s>>>(L->d_sectors, L->d_slice_jobs, (const double*)a,
+                                                            (const double*)b, sa, sb, ta, tb, L->slices);
     if (cudaGetLastError() != cudaSuccess) return TK_ERR_CUDA;
     ctx->launches += 1;
   }
@@ -843,14 +944,21 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
     ProfScope prof(ctx, "k_oz_gemm", stream);
     const int grid = (int)std::min<int64_t>(L->nwork, std::max(1, ctx->num_sms));
     double* part = (double*)(w + L->off_part);
-    if (L->bn == OZ_BN_WIDE)
-      k_oz_gemm<OZ_BN_WIDE><<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, (int)L->nwork, L->pairs,
-                                                           L->slices, sa, sb, (double*)c, part, counters,
-                                                           ctx->d_status);
-    else
-      k_oz_gemm<OZ_BN_NARROW><<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, (int)L->nwork, L->pairs,
-                                                             L->slices, sa, sb, (double*)c, part, counters,
-                                                             ctx->d_status);
+#define TK_OZ_LAUNCH(BNV, MODEV)                                                                           \
+  k_oz_gemm<BNV, MODEV><<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, (int)L->nwork, L->pairs, \
+                                                       L->slices, sa, sb, (double*)c, part, counters, ctx->d_status)
+    if (L->mode == 0) {
+      if (L->bn == OZ_BN_WIDE)
+        TK_OZ_LAUNCH(OZ_BN_WIDE, 0);
+      else
+        TK_OZ_LAUNCH(OZ_BN_NARROW, 0);
+    } else {
+      if (L->bn == OZ_BN_WIDE)
+        TK_OZ_LAUNCH(OZ_BN_WIDE, 1);
+      else
+        TK_OZ_LAUNCH(OZ_BN_NARROW, 1);
+    }
+#undef TK_OZ_LAUNCH
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       ctx->last_error = std::string("k_oz_gemm launch: ") + cudaGetErrorString(e);

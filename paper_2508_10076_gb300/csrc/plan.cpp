@@ -461,6 +461,8 @@ std::shared_ptr<ContractPlan> make_contract_plan(Ctx* ctx, std::shared_ptr<Struc
                                                  const std::vector<int>& qab, int dtype,
                                                  int gemm_mode, int slices) {
   if (a->sym != b->sym) throw Error{TK_ERR_SPACE_MISMATCH, "A and B have different symmetries"};
+  if (dtype == TK_C128 && gemm_mode != TK_GEMM_FP64)
+    throw Error{TK_ERR_UNSUPPORTED, "split-precision products of complex tensors are not available"};
   std::ostringstream os;
   os << perm_key(a->hash, pa, qa, dtype) << "#" << perm_key(b->hash, pb, qb, dtype) << "#";
   for (int x : pab) os << x << ",";

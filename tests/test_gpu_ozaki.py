@@ -142,3 +142,69 @@ def test_scales_span_many_binades(gctx):
         bound = 8 * 2.0 ** (-42) * ka * np.abs(am).max(axis=1)[:, None] * np.abs(bm).max(axis=0)[None, :]
         err = np.abs(got[oc:oc + rc * kc] - ref[oc:oc + rc * kc]).reshape(kc, rc).T
         assert np.all(err <= bound)
+
+
+TF32X3_TOL = 1e-5  # about FP32 accuracy: reported, not gated at the split-precision bar
+
+
+def test_tf32x3_c0_and_heff(gctx):
+    """3xTF32 (hi.hi + hi.lo + lo.hi on tcgen05 kind::tf32): about FP32 accuracy on C0 and on every
+    step of the D = 1024 heff chain."""
+    api = _api()
+    v = {-2: 1, -1: 2, 0: 3, 1: 2, 2: 1}
+    la = ([(v, False), (v, False)], [(v, False), (v, False)])
+    lb = ([(v, False), (v, True)], [(v, False), (v, False)])
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    xa, xb = wl.normal(0, oa.numel), wl.normal(1, ob.numel)
+    cs, ref = ops.contract(oa, xa, *wl.C0_SPEC[:2], ob, xb, *wl.C0_SPEC[2:], tier="dense")
+    A, B = _tm(gctx, "U1", la), _tm(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, *wl.C0_SPEC[:2], B, *wl.C0_SPEC[2:], gemm="tf32x3")
+    c = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda())
+    err = rel_frobenius_per_block(cs, c.cpu().numpy(), ref)
+    assert 0 < err <= TF32X3_TOL
+    from paper_2508_10076_gb300.chain import HeffChain
+    ch = HeffChain(gctx, "U1", 1024, gemm="tf32x3")
+    refs = oracle_heff("U1", 1024, tier="block")
+    t = ch.steps[0].run(ch.dev["L"], ch.dev["x"])
+    outs = [t]
+    for i, other in ((1, "W"), (2, "W"), (3, "R")):
+        t = ch.steps[i].run(t, ch.dev[other])
+        outs.append(t)
+    gctx.sync()
+    for i, ((cs, rd), b) in enumerate(zip(refs, outs)):
+        assert rel_frobenius_per_block(cs, b.cpu().numpy(), rd) <= TF32X3_TOL, i
+
+
+def test_tf32x3_wide_range_and_split_k(gctx):
+    """Rows and columns scaled by 2^(+-40) and K = 5000 (split across CTAs): per-row and
+    per-column scales keep 3xTF32 at about FP32 accuracy relative to each row's and column's
+    largest entries."""
+    api = _api()
+    la = ([({0: 130, 1: 20}, False)], [({0: 5000, 1: 9}, False)])
+    lb = ([({0: 5000, 1: 9}, False)], [({0: 140, 1: 33}, False)])
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    rng = np.random.default_rng(10)
+    xa = wl.normal(17, oa.numel) * np.exp2(rng.integers(-40, 41, oa.numel))
+    xb = wl.normal(18, ob.numel) * np.exp2(rng.integers(-40, 41, ob.numel))
+    cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
+    A, B = _tm(gctx, "U1", la), _tm(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), gemm="tf32x3")
+    c = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda())
+    got = c.cpu().numpy()
+    for (ca, ra, ka, oa_), (cb, rb, kb, ob_), (cc, rc, kc, oc) in zip(oa.blocks, ob.blocks, cs.blocks):
+        am = xa[oa_:oa_ + ra * ka].reshape(ka, ra).T
+        bm = xb[ob_:ob_ + rb * kb].reshape(kb, rb).T
+        # hi and lo keep 22 bits: each operand entry is off by at most 2^-21 of its row's (column's)
+        # scale 2^e <= 2 max; FP32 accumulation adds at most K 2^-24 of the running magnitude
+        bound = (2 * 2 * 2.0 ** (-21) + 2.0 ** (-24) * 4) * ka * np.abs(am).max(axis=1)[:, None] * np.abs(bm).max(axis=0)[None, :]
+        err = np.abs(got[oc:oc + rc * kc] - ref[oc:oc + rc * kc]).reshape(kc, rc).T
+        assert np.all(err <= bound)
+
+
+def test_complex_split_precision_is_refused(gctx):
+    api = _api()
+    v = {-1: 2, 0: 3, 1: 2}
+    A = _tm(gctx, "U1", ([(v, False)], [(v, False)]))
+    with pytest.raises(api.TKError) as e:
+        api.contract_plan(gctx, A, (0,), (1,), A, (0,), (1,), (0,), (1,), dtype="c128", gemm="ozaki")
+    assert e.value.code == 7
