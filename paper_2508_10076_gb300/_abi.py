@@ -49,6 +49,7 @@ SIGNATURES = {
     "tk_plan_workspace_bytes": (C.c_size_t, [c_vp]),
     "tk_plan_flops": (C.c_double, [c_vp]),
     "tk_plan_tensor_flops": (C.c_double, [c_vp]),
+    "tk_plan_permute_stats": (C.c_int, [c_vp, C.c_int, c_vp]),
     "tk_plan_permute_bytes": (C.c_double, [c_vp]),
     "tk_plan_ntransform": (C.c_int64, [c_vp, C.c_int]),
     "tk_plan_transform": (C.c_int, [c_vp, C.c_int, C.c_int64, c_i64p, c_i64p, c_dblp]),

@@ -235,6 +235,16 @@ class Plan:
     def permute_bytes(self):
         return float(_lib().tk_plan_permute_bytes(self._h))
 
+    def permute_stats(self, which=0):
+        """Task mix of one permute: dict of run / transpose / element-wise task and element counts
+        (None when that permute is the identity)."""
+        st = (C.c_int64 * 8)()
+        if _lib().tk_plan_permute_stats(self._h, int(which), st) != 0:
+            return None
+        keys = ("run_tasks", "run_elems", "runs", "transpose_tasks", "transpose_elems", "generic_tasks",
+                "generic_elems", "tiles")
+        return dict(zip(keys, list(st)))
+
     def transform(self, which=0):
         """[(src_offset, dst_offset, coef)] of one permute (None when it is the identity)."""
         lib = _lib()

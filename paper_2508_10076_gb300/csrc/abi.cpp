@@ -443,6 +443,29 @@ int tk_plan_transform(const tk_plan* plan, int which, int64_t k, int64_t* src_of
   return TK_OK;
 }
 
+int tk_plan_permute_stats(const tk_plan* plan, int which, int64_t* stats) {
+  const tk::PermutePlan* p = which_perm(plan, which);
+  if (!p || !stats) return TK_ERR_ARG;
+  for (int i = 0; i < 8; ++i) stats[i] = 0;
+  auto elems = [](const tk::PermTask& t) {
+    int64_t n = 1;
+    for (int k = 0; k < t.ndim; ++k) n *= t.ext[k];
+    return n;
+  };
+  for (const auto& t : p->rtasks) {
+    stats[0] += 1;
+    stats[1] += elems(t);
+  }
+  stats[2] = (int64_t)p->runs.size();
+  for (const auto& t : p->tasks) {
+    const int m = t.mode == 1 ? 3 : 5;
+    stats[m] += 1;
+    stats[m + 1] += elems(t);
+  }
+  stats[7] = p->total_tiles;
+  return TK_OK;
+}
+
 int tk_permute(tk_ctx* ctx, const tk_plan* plan, const void* a, void* c, void* stream) {
   if (!ctx || !plan || plan->kind != 0) return fail(ctx, TK_ERR_ARG, "not a permute plan");
   if (!a || !c) return fail(ctx, TK_ERR_ARG, "null buffer");

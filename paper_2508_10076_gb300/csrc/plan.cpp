@@ -299,6 +299,12 @@ static void build_tasks(PermutePlan& pp) {
       ++ti;
     }
     t.nsrc = (int32_t)pp.srcs.size() - t.src_begin;
+    // When every source block has the same leading dimension ld (always so for one source), a
+    // column step is a fixed element stride ld: fold it into the row stride, so that contiguity
+    // along a domain leg (e.g. blocks with one row) is seen by the mode choice below.
+    int64_t fold = pp.srcs[t.src_begin].ld;
+    for (int32_t q = t.src_begin + 1; q < t.src_begin + t.nsrc; ++q)
+      if (pp.srcs[q].ld != fold) fold = 0;
     // strides per output leg
     idims.assign(n, 1);
     for (int k = 0; k < n; ++k) idims[pp.perm[k]] = od[k];
@@ -310,6 +316,8 @@ static void build_tasks(PermutePlan& pp) {
       int64_t r = 0, c = 0;
       if (j < n1i)
         r = prod64(idims, 0, j);
+      else if (fold > 0)
+        r = prod64(idims, n1i, j) * fold;
       else
         c = prod64(idims, n1i, j);
       // merge with the previous kept dim when contiguous on both sides
@@ -332,6 +340,11 @@ static void build_tasks(PermutePlan& pp) {
       ics.push_back(0);
     }
     if (ext.size() > 6) throw std::runtime_error("permute task with more than 6 non-mergeable dims");
+    {
+      int64_t elems = 1;
+      for (int64_t x : ext) elems *= x;
+      if (elems >= ((int64_t)1 << 31)) throw std::runtime_error("permute task with 2^31 or more elements");
+    }
     t.ndim = (int32_t)ext.size();
     int64_t total = 1;
     for (size_t k = 0; k < ext.size(); ++k) {
