@@ -236,6 +236,7 @@ def run_ours(args):
     build_library()
     ctx = api.Context(local)
     work = _workload(ctx, args.config, args.gemm, seed=replica_seed(rank))
+    tuned = work.autotune() if not args.no_autotune else None  # before any graph capture
     flops = work.flops
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -314,6 +315,7 @@ def run_ours(args):
     # (s = 6, 21 slice pairs) and 3xTF32 (3 products, tensor rate half of BF16)
     def split_variant(gemm, ref_out):
         oz = _workload(ctx, args.config, gemm, seed=replica_seed(rank))
+        oz_tuned = oz.autotune() if not args.no_autotune else None
         for _ in range(max(3, args.warmup)):
             oz.run()
         oz_fn = oz.run
@@ -362,7 +364,7 @@ def run_ours(args):
                     "peak_source": peak_key,
                     "note": f"achieved = {products} products x tensor-path block flops / k_oz_gemm time"}
         return {"value": job_throughput(flops, args.steps, world, oz_ms), "unit": UNIT,
-                "ms_per_step": oz_ms / args.steps, "roofline": roof,
+                "ms_per_step": oz_ms / args.steps, "roofline": roof, "autotune": oz_tuned,
                 "tensor_path_flops_per_step": oz.tensor_flops,
                 "rel_frobenius_per_block_vs_fp64_path": worst,
                 "kernels": {k: {"launches": c, "ms_per_step": ms / args.steps} for k, (c, ms) in oz_prof.items()}}
@@ -417,7 +419,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.config, "gemm": args.gemm, "block_flops_per_step": flops,
                    "permute_bytes_per_step": permute_bytes, "l2": "flushed (512 MB write) before every timed step",
-                   "launch": mode,
+                   "launch": mode, "autotune": tuned,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -455,6 +457,7 @@ def main():
     ap.add_argument("--no-split", action="store_true", help="skip the split-precision variant")
     ap.add_argument("--eager", action="store_true", help="launch kernels one by one instead of a CUDA graph")
     ap.add_argument("--serve-requests", type=int, default=10000, help="serving requests (0: skip serving)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic work lists")
     ap.add_argument("--serve-load", type=float, default=0.7, help="offered load relative to alone service time")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -196,6 +196,18 @@ int tk_contract_batch(tk_ctx* ctx, int n, const tk_plan* const* plans, const voi
                       const void* const* b, void* const* c, void* const* workspace,
                       const size_t* workspace_bytes, void* stream);
 
+/* Autotuner (not in the paper): times the candidate work lists of a contraction plan on the given
+ * buffers (median of three runs each, CUDA events on `stream`, which is synchronised) and keeps the
+ * fastest: FP64 tiles 32 or 64 wide with split-K off or at its maximum, or the built-in heuristic;
+ * for split-precision plans then also the tensor-core tile width (64 / 128 columns) and its
+ * split-K.  Candidates whose workspace would exceed workspace_bytes are skipped, so the plan's
+ * tk_plan_workspace_bytes() stays <= workspace_bytes.  The plan's device tables are rebuilt: call
+ * it before capturing the plan in a CUDA graph and while no launch of the plan is in flight.
+ * c and the workspace are overwritten.  *choice (if not NULL) receives 8 * fp64 candidate + split-
+ * precision candidate (candidate 0 = heuristic). */
+int tk_plan_autotune(tk_ctx* ctx, tk_plan* plan, const void* a, const void* b, void* c, void* workspace,
+                     size_t workspace_bytes, void* stream, int* choice);
+
 /* Contraction without any device allocation -- no counterpart in the paper.  Same result and
  * launch sequence as tk_contract, but the scratch memory (permuted operands and the intermediate
  * C~) comes from a fixed array compiled into libtk instead of a caller-allocated workspace.  It

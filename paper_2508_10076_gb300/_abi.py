@@ -57,6 +57,7 @@ SIGNATURES = {
     "tk_contract": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
     "tk_contract_noalloc": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tk_contract_batch": (C.c_int, [c_vp, C.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "tk_plan_autotune": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, C.c_size_t, c_vp, c_vp]),
     "tk_copy_h2d": (C.c_int, [c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
     "tk_copy_d2h": (C.c_int, [c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
     "tk_fsymbol": (C.c_double, [C.c_int, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),

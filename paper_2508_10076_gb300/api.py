@@ -313,6 +313,16 @@ def contract_batch(ctx, plans, a, b, c, workspaces, stream=None):
     _check(_lib().tk_contract_batch(ctx._h, n, hp, ha, hb, hc, hw, hn, _stream_handle(stream)), ctx)
 
 
+def autotune(ctx, plan, a, b, c, workspace, stream=None):
+    """tk_plan_autotune: time the plan's candidate work lists on these buffers, keep the fastest.
+    Returns (fp64 candidate, split-precision candidate); 0 means the built-in heuristic."""
+    choice = C.c_int(0)
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(_lib().tk_plan_autotune(ctx._h, plan._h, _ptr(a), _ptr(b), _ptr(c), _ptr(workspace),
+                                   C.c_size_t(nbytes), _stream_handle(stream), C.byref(choice)), ctx)
+    return choice.value // 8, choice.value % 8
+
+
 # Mirrors TK_NOALLOC_SCRATCH_BYTES in include/tk.h.
 NOALLOC_SCRATCH_BYTES = 32 << 20
 

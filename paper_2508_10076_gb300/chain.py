@@ -68,6 +68,15 @@ class Contraction:
         api.contract(self.ctx, self.plan, a_buf, b_buf, self.c, self.ws, stream)
         return self.c
 
+    def autotune(self, a_buf, b_buf, headroom=2.0):
+        """Let libtk time this contraction's candidate work lists on these operands; the workspace
+        may grow up to `headroom` times its heuristic size and is re-sized to the choice."""
+        big = torch.empty(max(1, int(self.plan.workspace_bytes * headroom)), dtype=torch.uint8,
+                          device=self.ws.device)
+        choice = api.autotune(self.ctx, self.plan, a_buf, b_buf, self.c, big)
+        self.ws = torch.empty(max(1, self.plan.workspace_bytes), dtype=torch.uint8, device=self.ws.device)
+        return choice
+
 
 class HeffChain:
     """x' = (((L x) W) W) R with all intermediates resident on the device."""
@@ -113,6 +122,17 @@ class HeffChain:
         t = self.steps[2].run(t, self.dev["W"], stream)
         return self.steps[3].run(t, self.dev["R"], stream)
 
+    def autotune(self):
+        """Tune every step on the chain's own intermediates (before any graph capture)."""
+        x = self.dev["x"]
+        t = self.steps[0].run(self.dev["L"], x)
+        choices = [self.steps[0].autotune(self.dev["L"], x)]
+        for i, other in ((1, "W"), (2, "W"), (3, "R")):
+            t = self.steps[i - 1].c
+            choices.append(self.steps[i].autotune(t, self.dev[other]))
+            self.steps[i].run(t, self.dev[other])
+        return choices
+
     def capture(self):
         """One application recorded as a CUDA graph: (graph, output buffer, launches per replay)."""
         return capture_graph(self.ctx, self.run)
@@ -139,6 +159,9 @@ class LxContraction:
 
     def run(self, stream=None):
         return self.step.run(self.dev["L"], self.dev["x"], stream)
+
+    def autotune(self):
+        return [self.step.autotune(self.dev["L"], self.dev["x"])]
 
     def capture(self):
         return capture_graph(self.step.ctx, self.run)

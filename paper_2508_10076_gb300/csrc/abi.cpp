@@ -516,6 +516,79 @@ int tk_contract_batch(tk_ctx* ctx, int n, const tk_plan* const* plans, const voi
   return tk::run_contract_batch(&ctx->c, n, cps.data(), a, b, c, workspace, stream);
 }
 
+int tk_plan_autotune(tk_ctx* ctx, tk_plan* plan, const void* a, const void* b, void* c, void* workspace,
+                     size_t workspace_bytes, void* stream, int* choice) {
+  if (!ctx || !plan || plan->kind != 1) return fail(ctx, TK_ERR_ARG, "not a contraction plan");
+  if (!a || !b || !c || !workspace) return fail(ctx, TK_ERR_ARG, "null buffer");
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  tk::ContractPlan& cp = *plan->con;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(ctx, TK_ERR_CUDA, "stream synchronize failed");
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(ctx, TK_ERR_CUDA, "event creation failed");
+  // time one configuration: median of three runs after one warm-up; infinite if it does not fit
+  auto measure = [&](float* ms) -> int {
+    *ms = 1e30f;
+    int r = tk::finalize_device_tables(&ctx->c, cp);
+    if (r != TK_OK) return r;
+    if (cp.ws_total > workspace_bytes) return TK_OK;
+    float t[3];
+    if ((r = tk::run_contract(&ctx->c, cp, a, b, c, workspace, stream)) != TK_OK) return r;
+    for (float& x : t) {
+      cudaEventRecord(e0, s);
+      if ((r = tk::run_contract(&ctx->c, cp, a, b, c, workspace, stream)) != TK_OK) return r;
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return TK_ERR_CUDA;
+      cudaEventElapsedTime(&x, e0, e1);
+    }
+    std::sort(t, t + 3);
+    *ms = t[1];
+    return TK_OK;
+  };
+  struct Cand {
+    int tile, split;
+  };
+  const Cand fp64c[] = {{0, 0}, {32, 1}, {64, 1}, {32, 2}, {64, 2}};
+  const Cand ozc[] = {{0, 0}, {64, 1}, {128, 1}, {64, 2}, {128, 2}};
+  int best_i = 0, best_j = 0;
+  float best = 1e30f, ms = 0;
+  for (int i = 0; i < 5 && rc == TK_OK; ++i) {  // FP64 work list (heuristic split-precision choice)
+    cp.tune_tile = fp64c[i].tile;
+    cp.tune_split = fp64c[i].split;
+    cp.tune_oz_bn = cp.tune_oz_split = 0;
+    if ((rc = measure(&ms)) == TK_OK && ms < best) {
+      best = ms;
+      best_i = i;
+    }
+  }
+  if (rc == TK_OK && cp.gemm_mode != TK_GEMM_FP64 && !cp.gemms_oz.empty()) {
+    cp.tune_tile = fp64c[best_i].tile;
+    cp.tune_split = fp64c[best_i].split;
+    best = 1e30f;
+    for (int j = 0; j < 5 && rc == TK_OK; ++j) {  // split-precision work list
+      cp.tune_oz_bn = ozc[j].tile;
+      cp.tune_oz_split = ozc[j].split;
+      if ((rc = measure(&ms)) == TK_OK && ms < best) {
+        best = ms;
+        best_j = j;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cp.tune_tile = fp64c[best_i].tile;
+  cp.tune_split = fp64c[best_i].split;
+  cp.tune_oz_bn = ozc[best_j].tile;
+  cp.tune_oz_split = ozc[best_j].split;
+  const int rc2 = tk::finalize_device_tables(&ctx->c, cp);
+  if (rc != TK_OK) return fail(ctx, rc, "autotuning run failed");
+  if (rc2 != TK_OK) return fail(ctx, rc2, "rebuilding the chosen work lists failed");
+  if (choice) *choice = best_i * 8 + best_j;
+  return TK_OK;
+}
+
 int tk_copy_h2d(tk_ctx* ctx, void* dst_device, const void* src_host, size_t bytes, void* stream) {
   if (!ctx || (bytes && (!dst_device || !src_host))) return fail(ctx, TK_ERR_ARG, "null argument");
   int rc = set_device(ctx);

@@ -849,7 +849,9 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
   }
   // 64x64 tiles reuse registers twice as well as 32x32 ones; take them unless padding to 64 costs
   // more than a fifth extra work, or they are too few even after splitting K
-  const bool use64 = tiles64 >= 3 * sms || (pad64 <= 1.2 * pad32 && split64 >= 3 * sms);
+  const bool use64 = cp.tune_tile == 64 ? true
+                    : cp.tune_tile == 32 ? false
+                                         : (tiles64 >= 3 * sms || (pad64 <= 1.2 * pad32 && split64 >= 3 * sms));
   const int bm = use64 ? 64 : 32;
   // A product whose N exceeds a multiple of the tile width by at most ROWS_NMAX columns gives those
   // last columns to the rows kernel (B and C are column-major: their trailing columns are a
@@ -879,8 +881,10 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
       (use64 ? tiles64 : tiles32) += ((g.M + bm - 1) / bm) * ((g.N + bm - 1) / bm);
   }
   const int64_t ntiles = use64 ? tiles64 : tiles32;
-  const int64_t want_tiles = ntiles >= 3 * sms ? 1 : (4 * sms + ntiles - 1) / std::max<int64_t>(ntiles, 1);
-  const int64_t want_rows = rows_ctas >= 2 * sms ? 1 : (4 * sms + rows_ctas - 1) / std::max<int64_t>(rows_ctas, 1);
+  int64_t want_tiles = ntiles >= 3 * sms ? 1 : (4 * sms + ntiles - 1) / std::max<int64_t>(ntiles, 1);
+  int64_t want_rows = rows_ctas >= 2 * sms ? 1 : (4 * sms + rows_ctas - 1) / std::max<int64_t>(rows_ctas, 1);
+  if (cp.tune_split == 1) want_tiles = want_rows = 1;           // no split-K
+  if (cp.tune_split == 2) want_tiles = want_rows = SPLIT_MAX;   // as many parts as K allows
   int32_t nslots = 0;
   int64_t poff = 0;
   struct Cand {

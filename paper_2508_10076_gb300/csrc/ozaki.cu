@@ -789,6 +789,7 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
       w += area;
     }
     L->bn = (w > 0 && kw / w >= 512.0) ? OZ_BN_WIDE : OZ_BN_NARROW;
+    if (cp.tune_oz_bn == OZ_BN_WIDE || cp.tune_oz_bn == OZ_BN_NARROW) L->bn = cp.tune_oz_bn;
   }
   const int bn = L->bn;
   for (size_t g = 0; g < cp.gemms_oz.size(); ++g) {
@@ -843,7 +844,9 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
   // warps that finish last.
   const int64_t sms = std::max(ctx->num_sms, 1);
   const int64_t ntiles = (int64_t)wcost.size();
-  const int64_t want = ntiles >= 2 * sms ? 1 : (2 * sms + ntiles - 1) / std::max<int64_t>(ntiles, 1);
+  int64_t want = ntiles >= 2 * sms ? 1 : (2 * sms + ntiles - 1) / std::max<int64_t>(ntiles, 1);
+  if (cp.tune_oz_split == 1) want = 1;
+  if (cp.tune_oz_split == 2) want = OZ_MAX_PARTS;
   int32_t nslots = 0;
   for (auto& w : wcost) {
     OzWork t = w.second;

@@ -464,6 +464,30 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Smallest M, N and K of a sector product that runs on the split-precision tensor-core kernel.
 constexpr int64_t kSplitMinDim = 32;
 
+int finalize_device_tables(Ctx* ctx, ContractPlan& cp) {
+  for (void* p : {cp.d_gemm_items, cp.d_gemm_tiles, cp.d_zero}) dev_free(p);
+  cp.d_gemm_items = cp.d_gemm_tiles = cp.d_zero = nullptr;
+  for (void* p : cp.d_oz) dev_free(p);
+  cp.d_oz.clear();
+  cp.oz.reset();
+  cp.partials_bytes = 0;
+  cp.split_slots = 0;
+  int rc = upload_gemm_tables(ctx, cp);
+  if (rc != TK_OK) return rc;
+  size_t off = cp.ws_base;
+  cp.ws_partials = off;
+  off += align256(cp.partials_bytes);
+  cp.ws_counters = off;
+  off += align256((size_t)cp.split_slots * sizeof(int));
+  cp.ws_slices = off;
+  cp.ws_total = off;
+  if (cp.gemm_mode != TK_GEMM_FP64) {
+    if ((rc = upload_ozaki_tables(ctx, cp)) != TK_OK) return rc;
+    cp.ws_total = cp.ws_slices + align256(cp.oz_bytes);
+  }
+  return TK_OK;
+}
+
 std::shared_ptr<ContractPlan> make_contract_plan(Ctx* ctx, std::shared_ptr<Structure> a,
                                                  const std::vector<int>& pa,
                                                  const std::vector<int>& qa,
@@ -556,22 +580,12 @@ std::shared_ptr<ContractPlan> make_contract_plan(Ctx* ctx, std::shared_ptr<Struc
     else
       cp->gemms_oz.push_back(g);
   }
+  cp->ws_base = off;
   cp->ws_slices = off;
   cp->ws_total = off;
   if (ctx && ctx->device >= 0) {
-    int rc = upload_gemm_tables(ctx, *cp);
+    int rc = finalize_device_tables(ctx, *cp);
     if (rc != TK_OK) throw Error{rc, "uploading GEMM tables failed"};
-    cp->ws_partials = off;
-    off += align256(cp->partials_bytes);
-    cp->ws_counters = off;
-    off += align256((size_t)cp->split_slots * sizeof(int));
-    cp->ws_slices = off;
-    cp->ws_total = off;
-    if (gemm_mode != TK_GEMM_FP64) {
-      rc = upload_ozaki_tables(ctx, *cp);
-      if (rc != TK_OK) throw Error{rc, "preparing split-precision GEMM tables failed"};
-      cp->ws_total = cp->ws_slices + align256(cp->oz_bytes);
-    }
   } else if (gemm_mode != TK_GEMM_FP64) {
     cp->ws_total = cp->ws_slices;  // sized on device contexts only
   }

@@ -179,10 +179,20 @@ struct ContractPlan {
   int64_t oz_nwork = 0;
   size_t oz_bytes = 0;
   std::shared_ptr<void> oz;
+  // work-list choices (0: heuristic); set by the autotuner, applied by finalize_device_tables
+  int tune_tile = 0;      // FP64 tiles: 32 or 64 wide
+  int tune_split = 0;     // FP64 split-K: 1 off, 2 as many parts as allowed
+  int tune_oz_bn = 0;     // split-precision tile width: 64 or 128
+  int tune_oz_split = 0;  // split-precision split-K: 1 off, 2 as many parts as allowed
+  size_t ws_base = 0;     // workspace bytes of the permuted operands and C~ (before GEMM scratch)
   ~ContractPlan();
 };
 
+
 struct Ctx;
+// (Re)build a contraction plan's device work lists for its current tune_* choices and lay out the
+// GEMM part of its workspace.
+int finalize_device_tables(Ctx* ctx, ContractPlan& cp);
 std::shared_ptr<PermutePlan> make_permute_plan(Ctx* ctx, std::shared_ptr<Structure> in,
                                                const std::vector<int>& p,
                                                const std::vector<int>& q, int dtype);
