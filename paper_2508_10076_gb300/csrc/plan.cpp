@@ -462,7 +462,7 @@ std::shared_ptr<PermutePlan> make_permute_plan(Ctx* ctx, std::shared_ptr<Structu
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Smallest M, N and K of a sector product that runs on the split-precision tensor-core kernel.
-constexpr int64_t kSplitMinDim = 32;
+constexpr int64_t kSplitMinK = 16, kRowsMaxN = 8, kRowsMaxK = 64;
 
 int finalize_device_tables(Ctx* ctx, ContractPlan& cp) {
   for (void* p : {cp.d_gemm_items, cp.d_gemm_tiles, cp.d_zero}) dev_free(p);
@@ -569,12 +569,14 @@ std::shared_ptr<ContractPlan> make_contract_plan(Ctx* ctx, std::shared_ptr<Struc
     cp->ws_ct = off;
     off += align256(ct.numel * es);
   }
-  // Engine per sector product.  Split precision pays off on the tensor cores only for products
-  // that fill a 128 x 128 x 64 tile reasonably; thin products (any of M, N, K below
-  // kSplitMinDim, e.g. the matrix-product-operator steps with K = N = 4) are memory-bound and
-  // stay on the FP64 kernel.
+  // Engine per sector product in the split-precision modes.  The tensor path pads M to 128, N to a
+  // multiple of 16 and K to 32, but runs ~100x the FP64 rate, so it takes every product except
+  // very shallow ones (K < 16) and the skinny matrix-product-operator steps (N <= 8 with K below
+  // 64, e.g. K = N = 4), which are memory-bound and stay on the CUDA cores (double-float row
+  // kernel).  A product with N <= 8 but a deep K goes to the tensor path: the row kernel walks K
+  // serially per row.
   for (const GemmItem& g : cp->gemms) {
-    const bool thin = g.M < kSplitMinDim || g.N < kSplitMinDim || g.K < kSplitMinDim;
+    const bool thin = g.K < kSplitMinK || (g.N <= kRowsMaxN && g.K < kRowsMaxK);
     if (gemm_mode == TK_GEMM_FP64 || thin)
       cp->gemms_fp64.push_back(g);
     else
