@@ -359,8 +359,46 @@ __device__ __forceinline__ void tf32_split(double v, int e, float& hi, float& lo
   lo = __uint_as_float(slo | ((uint32_t)el << 23) | ((uint32_t)(q - 1024) << 13));
 }
 
-// One 128 x 32 (rows x k) tile of one operand per CTA, all slices.  Lanes run along k, so each
-// warp writes one contiguous tile row per slice; A~ (column-major, rows contiguous) is staged
+// The S balanced base-128 digits of q (|q| <= 2^(7 S)), lowest first as in the 64-bit recurrence
+// d = ((q + 64) mod 128) - 64, q = (q - d) / 128, but in 32-bit arithmetic: the low 7 (S - 4)
+// bits are peeled off first (their carry joins the high part), then the high part fits an int.
+template <int S>
+__device__ __forceinline__ void oz_digits(long long q, int (&d)[S]) {
+  constexpr int NP = S > 4 ? S - 4 : 0;
+  uint32_t L = (uint32_t)(q & ((1ll << (7 * NP)) - 1));
+  int H = (int)(q >> (7 * NP));
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    const int x = (int)((L + 64u) & 127u) - 64;
+    d[S - 1 - j] = x;
+    L = (uint32_t)((int)L - x) >> 7;
+  }
+  H += (int)L;
+#pragma unroll
+  for (int i = S - 1 - NP; i >= 1; --i) {
+    const int x = ((H + 64) & 127) - 64;
+    d[i] = x;
+    H = (H - x) >> 7;
+  }
+  d[0] = H;
+}
+
+// Digits of a pair of entries, written as S packed BF16 pairs (slice i holds d_i 2^(-7 (i + 1))).
+template <int S>
+__device__ __forceinline__ void oz_slice_pair(double v0, double v1, int e, __nv_bfloat162* dst, int64_t stride2) {
+  int d0[S], d1[S];
+  oz_digits<S>(round_scaled(v0, 7 * S - e), d0);  // round(v 2^(7 S - e)), |q| <= 2^(7 S)
+  oz_digits<S>(round_scaled(v1, 7 * S - e), d1);
+#pragma unroll
+  for (int sl = 0; sl < S; ++sl) {
+    const float sc = __int_as_float((127 - 7 * (sl + 1)) << 23);  // 2^(-7 (sl + 1)), exact
+    dst[sl * stride2] = __floats2bfloat162_rn((float)d0[sl] * sc, (float)d1[sl] * sc);
+  }
+}
+
+// One 128 x 32 (rows x k) tile of one operand per CTA, all slices.  Each thread takes two
+// consecutive k of a row, so a slice of the pair is one packed 32-bit (BF16 pair) or 64-bit (TF32
+// pair) store and a half-warp writes a full tile row; A~ (column-major, rows contiguous) is staged
 // through shared memory to keep its reads coalesced, B~ (k contiguous) is read directly.
 // MODE 0 writes s BF16 digit slices, MODE 1 the TF32 pair (hi, lo).
 template <int MODE>
@@ -369,7 +407,6 @@ __global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ s
                                                   const int32_t* __restrict__ scale_a,
                                                   const int32_t* __restrict__ scale_b, void* __restrict__ tiles_a,
                                                   void* __restrict__ tiles_b, int nslices) {
-  using Elt = typename std::conditional<MODE == 0, __nv_bfloat16, float>::type;
   __shared__ double xs[OZ_BK][OZ_TROWS + 1];
   const OzJob jb = jobs[blockIdx.x];
   const OzSector s = secs[jb.sector];
@@ -377,7 +414,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ s
   const int64_t R = op == 0 ? s.M : s.N;
   const int64_t rt = jb.r0;  // row-tile index
   const int64_t r0 = rt * OZ_TROWS, k0 = (int64_t)jb.kc * OZ_BK;
-  const int tid = threadIdx.x, kl = tid & 31, rw = tid >> 5;
+  const int tid = threadIdx.x;
   if (op == 0) {
     for (int e = tid; e < OZ_TROWS * OZ_BK; e += 256) {
       const int ml = e & (OZ_TROWS - 1), kk = e / OZ_TROWS;
@@ -386,37 +423,47 @@ __global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ s
     }
     __syncthreads();
   }
+  const int kp = (tid & 15) * 2, rw = tid >> 4;  // k pair and row of this thread
   const int64_t nrt = op == 0 ? s.nmt : s.nnt;
   const int64_t tile0 = (op == 0 ? s.ta_base : s.tb_base) + rt * s.nkc + jb.kc;  // slice 0
   const int64_t slice_stride = nrt * s.nkc * (int64_t)(OZ_TROWS * OZ_BK);  // elements
-  Elt* dst0 = (Elt*)(op == 0 ? tiles_a : tiles_b) + tile0 * (OZ_TROWS * OZ_BK) + kl;
   const int32_t* scl = op == 0 ? scale_a + s.sa_off : scale_b + s.sb_off;
-#pragma unroll 4
-  for (int i = 0; i < OZ_TROWS / 8; ++i) {
-    const int rl = rw + 8 * i;
-    const int64_t r = r0 + rl, k = k0 + kl;
-    double v;
-    if (op == 0)
-      v = xs[kl][rl];
-    else
-      v = (r < R && k < s.K) ? __ldg(B + s.b_off + k + r * s.K) : 0.0;
+#pragma unroll 2
+  for (int i = 0; i < OZ_TROWS / 16; ++i) {
+    const int rl = rw + 16 * i;
+    const int64_t r = r0 + rl, k = k0 + kp;
+    double v0, v1;
+    if (op == 0) {
+      v0 = xs[kp][rl];
+      v1 = xs[kp + 1][rl];
+    } else {
+      const double* src = B + s.b_off + k + r * s.K;
+      v0 = (r < R && k < s.K) ? __ldg(src) : 0.0;
+      v1 = (r < R && k + 1 < s.K) ? __ldg(src + 1) : 0.0;
+    }
     int e = (r < R) ? scl[r] : 0;
     if (e == kNoScale) e = 0;  // an all-zero row or column
-    Elt* dst = dst0 + rl * OZ_BK;
+    const int64_t at = tile0 * (OZ_TROWS * OZ_BK) + rl * OZ_BK + kp;  // element index of slice 0
     if constexpr (MODE == 0) {
-      long long q = round_scaled(v, 7 * nslices - e);  // round(v 2^(7 s - e)), |q| <= 2^(7 s)
-      for (int sl = nslices - 1; sl >= 1; --sl) {
-        const long long d = ((q + 64) & 127) - 64;  // balanced base-128 digit
-        q = (q - d) >> 7;
-        // |d| <= 64: convert through a 32-bit integer (a 64-bit conversion runs on the FP64 pipe)
-        dst[sl * slice_stride] = (Elt)__float2bfloat16_rn((float)(int)d * __int_as_float((127 - 7 * (sl + 1)) << 23));
+      // at is even and tiles are 1 KB aligned: the pair is a 4-byte aligned store
+      __nv_bfloat162* dst =
+          reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(op == 0 ? tiles_a : tiles_b) + at);
+      const int64_t st2 = slice_stride / 2;
+      switch (nslices) {
+        case 2: oz_slice_pair<2>(v0, v1, e, dst, st2); break;
+        case 3: oz_slice_pair<3>(v0, v1, e, dst, st2); break;
+        case 4: oz_slice_pair<4>(v0, v1, e, dst, st2); break;
+        case 5: oz_slice_pair<5>(v0, v1, e, dst, st2); break;
+        case 6: oz_slice_pair<6>(v0, v1, e, dst, st2); break;
+        default: oz_slice_pair<7>(v0, v1, e, dst, st2); break;
       }
-      dst[0] = (Elt)__float2bfloat16_rn((float)(int)q * __int_as_float((127 - 7) << 23));  // |q| <= 128 here
     } else {
-      float hi, lo;
-      tf32_split(v, e, hi, lo);
-      dst[0] = (Elt)hi;
-      dst[slice_stride] = (Elt)lo;
+      float h0, l0, h1, l1;
+      tf32_split(v0, e, h0, l0);
+      tf32_split(v1, e, h1, l1);
+      float2* dst = reinterpret_cast<float2*>(reinterpret_cast<float*>(op == 0 ? tiles_a : tiles_b) + at);
+      dst[0] = make_float2(h0, h1);
+      dst[slice_stride / 2] = make_float2(l0, l1);
     }
   }
 }
