@@ -120,8 +120,9 @@ def _workload(ctx, name, gemm, dtype="f64", seed=0):
     from paper_2508_10076_gb300 import workloads as wl
     from paper_2508_10076_gb300.chain import HeffChain, LxContraction
     cfg = wl.CONFIGS[name]
-    if cfg["kind"] == "heff":
-        return HeffChain(ctx, cfg["sym"], cfg["D"], gemm=gemm, dtype=dtype, seed=seed)
+    if cfg["kind"] in ("heff", "heff1"):
+        return HeffChain(ctx, cfg["sym"], cfg["D"], gemm=gemm, dtype=dtype, seed=seed,
+                         sites=2 if cfg["kind"] == "heff" else 1)
     if cfg["kind"] == "lx":
         return LxContraction(ctx, cfg["sym"], cfg["D"], gemm=gemm, dtype=dtype, seed=seed)
     raise SystemExit(f"config {name} is a parity case, not a bench line")
@@ -141,8 +142,9 @@ def cpu_baseline(name, budget_s=15.0):
     from oracle import ops  # noqa: E402
     from paper_2508_10076_gb300 import workloads as wl
     cfg = wl.CONFIGS[name]
-    if cfg["kind"] == "heff":
-        run = lambda: oracle_heff(cfg["sym"], cfg["D"], tier="block")  # noqa: E731
+    if cfg["kind"] in ("heff", "heff1"):
+        sites = 2 if cfg["kind"] == "heff" else 1
+        run = lambda: oracle_heff(cfg["sym"], cfg["D"], tier="block", sites=sites)  # noqa: E731
         flops = None
     else:
         st, data = oracle_heff_inputs(cfg["sym"], cfg["D"])
@@ -203,7 +205,7 @@ def _host_flops(hctx, name):
     from paper_2508_10076_gb300 import api
     cfg = wl.CONFIGS[name]
     V, P, W = wl.heff_spaces(cfg["sym"], cfg["D"])
-    legs = wl.heff_legs(V, P, W)
+    legs = wl.heff_legs(V, P, W) if cfg["kind"] != "heff1" else wl.heff1_legs(V, P, W)
 
     def tm(k):
         cod, dom = legs[k]
@@ -212,11 +214,13 @@ def _host_flops(hctx, name):
     if cfg["kind"] == "lx":
         return api.contract_plan(hctx, tm("L"), *wl.LX_SPEC[:2], tm("x"), *wl.LX_SPEC[2:]).flops
     total, cur = 0.0, tm("x")
-    for i, spec in enumerate(wl.HEFF_SPECS):
+    specs = wl.HEFF_SPECS if cfg["kind"] != "heff1" else wl.HEFF1_SPECS
+    others = ("L", "W", "W", "R") if cfg["kind"] != "heff1" else ("L", "W", "R")
+    for i, spec in enumerate(specs):
         if i == 0:
             pl = api.contract_plan(hctx, tm("L"), *spec[:2], cur, *spec[2:])
         else:
-            pl = api.contract_plan(hctx, cur, *spec[:2], tm("W" if i < 3 else "R"), *spec[2:])
+            pl = api.contract_plan(hctx, cur, *spec[:2], tm(others[i]), *spec[2:])
         total += pl.flops
         cur = pl.output()
     return total

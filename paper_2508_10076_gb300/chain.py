@@ -79,14 +79,15 @@ class Contraction:
 
 
 class HeffChain:
-    """x' = (((L x) W) W) R with all intermediates resident on the device."""
+    """Two-site x' = (((L x) W) W) R (Algorithm 12), or with sites=1 the single-site
+    x' = ((L x) W) R (Algorithm 11), with all intermediates resident on the device."""
 
     def __init__(self, ctx, sym="U1", D=1024, gemm="fp64", slices=0, seed=0, device="cuda",
-                 dtype="f64"):
-        self.ctx, self.sym, self.D = ctx, sym, D
+                 dtype="f64", sites=2):
+        self.ctx, self.sym, self.D, self.sites = ctx, sym, D, sites
         V, P, W = wl.heff_spaces(sym, D)
         self.sectors = (V, P, W)
-        legs = wl.heff_legs(V, P, W)
+        legs = wl.heff_legs(V, P, W) if sites == 2 else wl.heff1_legs(V, P, W)
         self.legs = legs
         self.tm = {k: _tmap(ctx, sym, legs[k]) for k in ("x", "L", "W", "R")}
         self.host = {}
@@ -101,10 +102,12 @@ class HeffChain:
         tdt = torch.complex128 if dtype == "c128" else torch.float64
         self.dev = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device=device, dtype=tdt)
                     for k, v in self.host.items()}
-        specs = wl.HEFF_SPECS
+        specs = wl.HEFF_SPECS if sites == 2 else wl.HEFF1_SPECS
+        self.others = ("L", "W", "W", "R") if sites == 2 else ("L", "W", "R")
         self.steps = []
         cur = self.tm["x"]
-        for i, (other, first) in enumerate((("L", True), ("W", False), ("W", False), ("R", False))):
+        for i, other in enumerate(self.others):
+            first = i == 0
             if first:  # T1 = L x : A = L, B = x
                 st = Contraction(ctx, self.tm["L"], cur, specs[0], dtype, gemm, slices, device)
             else:
@@ -118,19 +121,19 @@ class HeffChain:
     def run(self, x=None, stream=None):
         x = self.dev["x"] if x is None else x
         t = self.steps[0].run(self.dev["L"], x, stream)
-        t = self.steps[1].run(t, self.dev["W"], stream)
-        t = self.steps[2].run(t, self.dev["W"], stream)
-        return self.steps[3].run(t, self.dev["R"], stream)
+        for st, other in zip(self.steps[1:], self.others[1:]):
+            t = st.run(t, self.dev[other], stream)
+        return t
 
     def autotune(self):
         """Tune every step on the chain's own intermediates (before any graph capture)."""
         x = self.dev["x"]
-        t = self.steps[0].run(self.dev["L"], x)
+        self.steps[0].run(self.dev["L"], x)
         choices = [self.steps[0].autotune(self.dev["L"], x)]
-        for i, other in ((1, "W"), (2, "W"), (3, "R")):
-            t = self.steps[i - 1].c
-            choices.append(self.steps[i].autotune(t, self.dev[other]))
-            self.steps[i].run(t, self.dev[other])
+        for i in range(1, len(self.steps)):
+            t, other = self.steps[i - 1].c, self.dev[self.others[i]]
+            choices.append(self.steps[i].autotune(t, other))
+            self.steps[i].run(t, other)
         return choices
 
     def capture(self):

@@ -127,6 +127,15 @@ HEFF_SPECS = [
 # Environment applied to the two-site tensor: T = L x (the first step of the chain).
 LX_SPEC = HEFF_SPECS[0]
 
+# Single-site effective Hamiltonian (Algorithm 11): x' = ((L x) W) R with x : V (x) P <- V.
+# Steps: T1 = L x over the left virtual leg; T2 = T1 W over (MPO bond, physical leg);
+# x' = T2 R over (MPO bond, right virtual leg); x' has the structure of x.
+HEFF1_SPECS = [
+    ((0, 2), (1,), (0,), (1, 2), (0, 1), (2, 3)),
+    ((0, 3), (1, 2), (0, 2), (1, 3), (0, 1), (2, 3)),
+    ((0, 2), (3, 1), (0, 2), (1,), (0, 1), (2,)),
+]
+
 
 def heff_spaces(sym: str, D: int):
     """(V, P, W) sector dicts of the two-site heff workload."""
@@ -144,11 +153,20 @@ def heff_legs(V, P, W):
     return {"x": x, "L": L, "W": Wt, "R": R}
 
 
+def heff1_legs(V, P, W):
+    """Leg lists of the single-site workload: x : V (x) P <- V; L, W, R as in heff_legs."""
+    legs = heff_legs(V, P, W)
+    legs["x"] = ([(V, False), (P, False)], [(V, False)])
+    return legs
+
+
 CONFIGS = {
     "c0_u1_small": dict(sym="U1", D=9, kind="c0"),
     "c1_u1_heff_d1024": dict(sym="U1", D=1024, kind="heff"),
     "c2a_su2_lx_n256": dict(sym="SU2", D=256, kind="lx"),
     "c2b_su2_lx_n512": dict(sym="SU2", D=512, kind="lx"),
     "c3_u1_heff_d4096": dict(sym="U1", D=4096, kind="heff"),
+    "c5_u1_heff1_d4096": dict(sym="U1", D=4096, kind="heff1"),
+    "c5_su2_heff1_n1024": dict(sym="SU2", D=1024, kind="heff1"),
     "c3_su2_lx_n1024": dict(sym="SU2", D=1024, kind="lx"),
 }

@@ -29,9 +29,9 @@ def oracle_mpo(struct, entries):
     return data
 
 
-def oracle_heff_inputs(sym, D, seed=0, dtype="f64"):
+def oracle_heff_inputs(sym, D, seed=0, dtype="f64", sites=2):
     V, P, W = wl.heff_spaces(sym, D)
-    legs = wl.heff_legs(V, P, W)
+    legs = wl.heff_legs(V, P, W) if sites == 2 else wl.heff1_legs(V, P, W)
     st = {k: ostruct(sym, legs[k]) for k in ("x", "L", "W", "R")}
     rnd = wl.normal_complex if dtype == "c128" else wl.normal
     data = {k: rnd(seed * 16 + i, st[k].numel) for i, k in enumerate(("x", "L", "R"))}
@@ -44,17 +44,20 @@ def oracle_heff_inputs(sym, D, seed=0, dtype="f64"):
     return st, data
 
 
-def oracle_heff(sym, D, seed=0, tier="block", dtype="f64", steps=4):
-    """[(structure, data)] of T1, T2, T3, x' computed by the oracle."""
-    st, data = oracle_heff_inputs(sym, D, seed, dtype)
+def oracle_heff(sym, D, seed=0, tier="block", dtype="f64", steps=None, sites=2):
+    """[(structure, data)] of every intermediate and x' computed by the oracle: the two-site chain
+    (T1, T2, T3, x'; Algorithm 12) or with sites=1 the single-site chain (T1, T2, x'; Algorithm 11)."""
+    st, data = oracle_heff_inputs(sym, D, seed, dtype, sites)
+    specs = wl.HEFF_SPECS if sites == 2 else wl.HEFF1_SPECS
+    others = ("L", "W", "W", "R") if sites == 2 else ("L", "W", "R")
     out = []
     cur_s, cur_d = st["x"], data["x"]
-    for i in range(steps):
-        spec = wl.HEFF_SPECS[i]
+    for i in range(len(specs) if steps is None else steps):
+        spec = specs[i]
         if i == 0:
             a, ad, b, bd = st["L"], data["L"], cur_s, cur_d
         else:
-            other = "W" if i < 3 else "R"
+            other = others[i]
             a, ad, b, bd = cur_s, cur_d, st[other], data[other]
         cur_s, cur_d = ops.contract(a, ad, spec[0], spec[1], b, bd, spec[2], spec[3], spec[4], spec[5], tier=tier)
         out.append((cur_s, cur_d))

@@ -208,3 +208,12 @@ def test_complex_split_precision_is_refused(gctx):
     with pytest.raises(api.TKError) as e:
         api.contract_plan(gctx, A, (0,), (1,), A, (0,), (1,), (0,), (1,), dtype="c128", gemm="ozaki")
     assert e.value.code == 7
+
+
+def test_single_site_heff_split_precision(gctx):
+    from paper_2508_10076_gb300.chain import HeffChain
+    ch = HeffChain(gctx, "SU2", 256, sites=1, gemm="ozaki", seed=8)
+    got = ch.run()
+    gctx.sync()
+    cs, rd = oracle_heff("SU2", 256, seed=8, tier="block", sites=1)[-1]
+    assert rel_frobenius_per_block(cs, got.cpu().numpy(), rd) <= SPLIT_TOL

@@ -242,3 +242,21 @@ def test_split_k_few_tiles_long_inner_dimension(gctx):
     gctx.sync()
     assert rel_frobenius_per_block(cs, outs[0].cpu().numpy(), ref) <= FP64_TOL
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("sym,D", [("U1", 1024), ("SU2", 256)])
+def test_single_site_heff_chain_fp64(gctx, sym, D):
+    """Algorithm 11 (x' = L.x.W.R, three contractions): every intermediate against the oracle."""
+    from paper_2508_10076_gb300.chain import HeffChain
+    ch = HeffChain(gctx, sym, D, sites=1, seed=7)
+    ref = oracle_heff(sym, D, seed=7, tier="block", sites=1)
+    t = ch.steps[0].run(ch.dev["L"], ch.dev["x"])
+    outs = [t.clone()]
+    for i in (1, 2):
+        t = ch.steps[i].run(t, ch.dev[ch.others[i]])
+        outs.append(t.clone())
+    gctx.sync()
+    assert len(ch.steps) == 3
+    for i, ((cs, rd), b) in enumerate(zip(ref, outs)):
+        assert ch.steps[i].out.blocks() == [(c, r, k, o) for c, r, k, o in cs.blocks]
+        assert rel_frobenius_per_block(cs, b.cpu().numpy(), rd) <= FP64_TOL, i

@@ -65,3 +65,18 @@ def test_serving_request_stream_is_seeded_and_mixed():
     # log-uniform: about as many draws below sqrt(64 * 4096) = 512 as above
     below = sum(r["D"] < 512 for r in a) / len(a)
     assert 0.4 < below < 0.6
+
+
+def test_single_site_heff_dense_equals_block_and_keeps_structure():
+    """Algorithm 11 chain on small spaces: the oracle's dense tier (explicit CG embedding) and
+    block tier agree, and x' has the block structure of x, for U(1) and SU(2)."""
+    from harness import oracle_heff, oracle_heff_inputs
+    for sym, D in (("U1", 24), ("SU2", 10)):
+        st, _ = oracle_heff_inputs(sym, D, sites=1)
+        blk = oracle_heff(sym, D, sites=1, tier="block")
+        den = oracle_heff(sym, D, sites=1, tier="dense")
+        assert len(blk) == 3
+        for (sb, db), (sd, dd) in zip(blk, den):
+            assert sb.blocks == sd.blocks
+            assert np.allclose(db, dd, rtol=1e-12, atol=1e-12 * max(1.0, float(np.abs(dd).max())))
+        assert blk[-1][0].blocks == st["x"].blocks
