@@ -146,6 +146,10 @@ int tk_permute_plan(tk_ctx* ctx, const tk_tmap* a, int np, const int* p, int nq,
  * C = permute(C~, (pab, qab)).  (pab, qab) index the legs of C~ = codomain(A~) then domain(B~).
  * gemm_mode is TK_GEMM_*; slices is the number of BF16 slices per operand for
  * TK_GEMM_OZAKI_BF16 (0 = default), ignored otherwise. */
+/* Adjoint t^dagger : dom <- cod of t : cod <- dom (Sec. 2; conjugate for complex data).  With
+ * the orthonormal canonical trees, block c of the result is the conjugate transpose of block c of
+ * t.  The result is a permute-kind plan: run it with tk_permute, inspect it with tk_plan_output. */
+int tk_adjoint_plan(tk_ctx* ctx, const tk_tmap* a, int dtype, tk_plan** out);
 int tk_contract_plan(tk_ctx* ctx, const tk_tmap* a, int npa, const int* pa, int nqa, const int* qa,
                      const tk_tmap* b, int npb, const int* pb, int nqb, const int* qb,
                      int npab, const int* pab, int nqab, const int* qab, int dtype, int gemm_mode,

@@ -200,3 +200,34 @@ def contract_block(a_struct, a_data, pa, qa, b_struct, b_data, pb, qb, pab, qab)
 def contract(a_struct, a_data, pa, qa, b_struct, b_data, pb, qb, pab, qab, tier="dense"):
     f = contract_dense if tier == "dense" else contract_block
     return f(a_struct, a_data, pa, qa, b_struct, b_data, pb, qb, pab, qab)
+
+
+def adjoint_dense(struct: TensorStructure, data):
+    """t^dagger : dom <- cod of t : cod <- dom (the adjoint of the paper's Sec. 2): the dense array
+    conjugated with codomain and domain axes exchanged, projected onto the canonical trees of the
+    exchanged spaces."""
+    dense = embed(struct, data)
+    n1 = len(struct.cod)
+    perm = list(range(n1, struct.nleg)) + list(range(n1))
+    adj = TensorStructure(struct.dom, struct.cod)
+    return adj, project(adj, np.conj(dense).transpose(perm))
+
+
+def adjoint_block(struct: TensorStructure, data):
+    """Block tier of the adjoint: with orthonormal canonical trees the splitting and fusion trees
+    exchange roles, so block c of t^dagger is the conjugate transpose of block c of t."""
+    adj = TensorStructure(struct.dom, struct.cod)
+    data = np.asarray(data)
+    out = np.zeros(adj.numel, dtype=data.dtype)
+    src = struct.block_dict()
+    for c, rows, cols, off in adj.blocks:
+        r0, c0, o0 = src[c]
+        assert r0 == cols and c0 == rows
+        blk = data[o0:o0 + r0 * c0].reshape(c0, r0).T          # rows x cols of t, column-major storage
+        out[off:off + rows * cols] = np.conj(blk).reshape(-1)   # its transpose, column-major
+    return adj, out
+
+
+def adjoint(struct, data, tier="block"):
+    return adjoint_dense(struct, data) if tier == "dense" else adjoint_block(struct, data)
+

@@ -41,6 +41,7 @@ SIGNATURES = {
     "tk_tmap_ntreepairs": (C.c_int64, [c_vp]),
     "tk_tmap_treepair": (C.c_int, [c_vp, C.c_int64, c_i32p, c_i64p, c_i64p, c_i64p]),
     "tk_permute_plan": (C.c_int, [c_vp, c_vp, C.c_int, c_intp, C.c_int, c_intp, C.c_int, C.POINTER(c_vp)]),
+    "tk_adjoint_plan": (C.c_int, [c_vp, c_vp, C.c_int, C.POINTER(c_vp)]),
     "tk_contract_plan": (C.c_int, [c_vp, c_vp, C.c_int, c_intp, C.c_int, c_intp, c_vp, C.c_int, c_intp,
                                    C.c_int, c_intp, C.c_int, c_intp, C.c_int, c_intp, C.c_int, C.c_int,
                                    C.c_int, C.POINTER(c_vp)]),

@@ -267,6 +267,14 @@ def permute_plan(ctx, t, p, q, dtype="f64"):
     return Plan(ctx, h, "permute")
 
 
+def adjoint_plan(ctx, t, dtype="f64"):
+    """tk_adjoint_plan: t^dagger (domain and codomain exchanged, complex data conjugated); run it
+    with permute()."""
+    h = C.c_void_p()
+    _check(_lib().tk_adjoint_plan(ctx._h, t._h, DTYPE[dtype], C.byref(h)), ctx)
+    return Plan(ctx, h, "permute")
+
+
 def contract_plan(ctx, a, pa, qa, b, pb, qb, pab, qab, dtype="f64", gemm="fp64", slices=0):
     args = []
     for xs in (pa, qa):

@@ -345,6 +345,26 @@ int tk_permute_plan(tk_ctx* ctx, const tk_tmap* a, int np, const int* p, int nq,
   });
 }
 
+int tk_adjoint_plan(tk_ctx* ctx, const tk_tmap* a, int dtype, tk_plan** out) {
+  if (!ctx || !a || !out) return fail(ctx, TK_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (dtype != TK_F64 && dtype != TK_C128) return fail(ctx, TK_ERR_ARG, "unknown dtype");
+  return guarded(ctx, [&]() {
+    if (ctx->c.device >= 0 && cudaSetDevice(ctx->c.device) != cudaSuccess)
+      return fail(ctx, TK_ERR_CUDA, "cudaSetDevice failed");
+    auto pl = new tk_plan();
+    pl->kind = 0;
+    try {
+      pl->perm = tk::make_adjoint_plan(&ctx->c, a->st, dtype);
+    } catch (...) {
+      delete pl;
+      throw;
+    }
+    *out = pl;
+    return TK_OK;
+  });
+}
+
 int tk_contract_plan(tk_ctx* ctx, const tk_tmap* a, int npa, const int* pa, int nqa, const int* qa,
                      const tk_tmap* b, int npb, const int* pb, int nqb, const int* qb, int npab,
                      const int* pab, int nqab, const int* qab, int dtype, int gemm_mode, int slices,

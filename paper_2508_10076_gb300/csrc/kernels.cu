@@ -66,6 +66,7 @@ struct Elem;
 template <>
 struct Elem<double> {
   __device__ static double zero() { return 0.0; }
+  __device__ static double conj(double v) { return v; }
   __device__ static void fma(double& acc, double c, double v) { acc = fma_(c, v, acc); }
   __device__ static double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
   __device__ static double scale(double c, double v) { return c * v; }
@@ -73,6 +74,7 @@ struct Elem<double> {
 template <>
 struct Elem<double2> {
   __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+  __device__ static double2 conj(double2 v) { return make_double2(v.x, -v.y); }
   __device__ static void fma(double2& acc, double c, double2 v) {
     acc.x = __fma_rn(c, v.x, acc.x);
     acc.y = __fma_rn(c, v.y, acc.y);
@@ -84,9 +86,10 @@ struct Elem<double2> {
 // source, weight exactly 1) is a plain copy with no floating-point operation.
 template <typename T>
 __device__ __forceinline__ T gather(const PermSrc* __restrict__ srcs, int nsrc, int src_begin,
-                                    const T* __restrict__ in, int64_t ir, int64_t ic) {
+                                    const T* __restrict__ in, int64_t ir, int64_t ic, int conj = 0) {
   const PermSrc s0 = srcs[src_begin];
   T v = __ldg(in + s0.in_off + ir + ic * s0.ld);
+  if (conj) v = Elem<T>::conj(v);  // adjoint tasks: one source, weight 1
   if (nsrc == 1 && s0.coef == 1.0) return v;
   T acc = Elem<T>::scale(s0.coef, v);
   for (int s = 1; s < nsrc; ++s) {
@@ -185,7 +188,7 @@ __device__ __forceinline__ void permute_tiles(const PermSeg& g, int64_t bid, T (
         if (i0 < e0 && it < et) {
           const int64_t ir = irb + i0 * t.irs[0] + it * t.irs[td];
           const int64_t ic = icb + i0 * t.ics[0] + it * t.ics[td];
-          tile[j0][lx] = gather<T>(srcs, t.nsrc, t.src_begin, in, ir, ic);
+          tile[j0][lx] = gather<T>(srcs, t.nsrc, t.src_begin, in, ir, ic, t.conj);
         }
       }
       __syncthreads();
@@ -208,7 +211,7 @@ __device__ __forceinline__ void permute_tiles(const PermSeg& g, int64_t bid, T (
           ir += x * t.irs[k];
           ic += x * t.ics[k];
         }
-        out[oa] = gather<T>(srcs, t.nsrc, t.src_begin, in, ir, ic);
+        out[oa] = gather<T>(srcs, t.nsrc, t.src_begin, in, ir, ic, t.conj);
       }
     }
   }
@@ -230,8 +233,14 @@ __device__ __forceinline__ void permute_runs(const PermSeg& g, int64_t bid) {
     const PermRun run = runs[r];
     const int nsrc = __ldg(&tasks[run.task].nsrc);
     const int sb = __ldg(&tasks[run.task].src_begin);
+    const int conj = __ldg(&tasks[run.task].conj);
     const PermSrc s0 = srcs[sb];
     T* dst = out + run.dst;
+    if (conj) {  // adjoint: conjugating copy
+      const T* src = in + s0.in_off + run.ir + run.ic * s0.ld;
+      for (int e = lane; e < run.len; e += 32) dst[e] = Elem<T>::conj(__ldg(src + e));
+      continue;
+    }
     if (nsrc == 1 && s0.coef == 1.0) {
       const T* src = in + s0.in_off + run.ir + run.ic * s0.ld;
       for (int e = lane; e < run.len; e += 128) {

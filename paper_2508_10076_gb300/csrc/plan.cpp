@@ -269,6 +269,86 @@ static void build_transform(PermutePlan& pp, const std::vector<int>& p, const st
 constexpr int64_t kRunChunk = 1024;
 constexpr int32_t kMinRun = 8;
 
+// One destination task from its merged dims: run tasks (mode 0, contiguous on both sides) become
+// runs; the rest go to the tile kernel as transposes (mode 1) or element-wise (mode 2).
+static void emit_task(PermutePlan& pp, PermTask t, std::vector<int64_t>& ext, std::vector<int64_t>& ostr,
+                      std::vector<int64_t>& irs, std::vector<int64_t>& ics, double& bytes) {
+  const double esize = pp.dtype == TK_C128 ? 16.0 : 8.0;
+  if (ext.empty()) {
+    ext.push_back(1);
+    ostr.push_back(1);
+    irs.push_back(1);
+    ics.push_back(0);
+  }
+  if (ext.size() > 6) throw std::runtime_error("permute task with more than 6 non-mergeable dims");
+  {
+    int64_t elems = 1;
+    for (int64_t x : ext) elems *= x;
+    if (elems >= ((int64_t)1 << 31)) throw std::runtime_error("permute task with 2^31 or more elements");
+  }
+  t.ndim = (int32_t)ext.size();
+  int64_t total = 1;
+  for (size_t k = 0; k < ext.size(); ++k) {
+    t.ext[k] = (int32_t)ext[k];
+    t.ostr[k] = ostr[k];
+    t.irs[k] = (int32_t)irs[k];
+    t.ics[k] = (int32_t)ics[k];
+    total *= ext[k];
+  }
+  int tdim = -1;
+  for (int k = 1; k < t.ndim; ++k)
+    if (t.irs[k] == 1 && t.ics[k] == 0) tdim = k;
+  bytes += esize * (double)total * (1.0 + (double)t.nsrc);
+  if (t.ostr[0] == 1 && t.irs[0] == 1 && t.ics[0] == 0 && t.ext[0] >= kMinRun) {
+    // mode 0: contiguous runs along dim 0 on both sides -> one run per outer position
+    t.mode = 0;
+    const int32_t task_id = (int32_t)pp.rtasks.size();
+    pp.rtasks.push_back(t);
+    const int64_t outer = total / t.ext[0];
+    for (int64_t o = 0; o < outer; ++o) {
+      int64_t rem = o, dst = t.out_off, ir = 0, ic = 0;
+      for (int k = 1; k < t.ndim; ++k) {
+        const int64_t x = rem % t.ext[k];
+        rem /= t.ext[k];
+        dst += x * t.ostr[k];
+        ir += x * t.irs[k];
+        ic += x * t.ics[k];
+      }
+      for (int64_t e0 = 0; e0 < t.ext[0]; e0 += kRunChunk) {
+        const int32_t len = (int32_t)std::min<int64_t>(kRunChunk, t.ext[0] - e0);
+        pp.runs.push_back(PermRun{dst + e0, ir + e0, ic, len, task_id});
+      }
+    }
+    return;
+  }
+  if (t.ostr[0] == 1 && tdim > 0 && t.ext[0] >= 4 && t.ext[tdim] >= 4) {
+    t.mode = 1;
+    t.tdim = tdim;
+    t.t0 = 32;
+    t.t1 = 32;
+  } else {
+    t.mode = 2;
+  }
+  pp.tasks.push_back(t);
+}
+
+// Tile prefix of the tile-kernel tasks.
+static void finish_tiles(PermutePlan& pp) {
+  int64_t acc = 0;
+  for (auto& t : pp.tasks) {
+    t.tile_begin = acc;
+    int64_t total = 1;
+    for (int k = 0; k < t.ndim; ++k) total *= t.ext[k];
+    if (t.mode == 1) {
+      int64_t outer = total / ((int64_t)t.ext[0] * t.ext[t.tdim]);
+      acc += ((t.ext[0] + 31) / 32) * (int64_t)((t.ext[t.tdim] + 31) / 32) * outer;
+    } else {
+      acc += (total + 255) / 256;
+    }
+  }
+  pp.total_tiles = acc;
+}
+
 static void build_tasks(PermutePlan& pp) {
   const Structure& in = *pp.in;
   const Structure& out = *pp.out;
@@ -339,72 +419,84 @@ static void build_tasks(PermutePlan& pp) {
       irs.push_back(1);
       ics.push_back(0);
     }
-    if (ext.size() > 6) throw std::runtime_error("permute task with more than 6 non-mergeable dims");
-    {
-      int64_t elems = 1;
-      for (int64_t x : ext) elems *= x;
-      if (elems >= ((int64_t)1 << 31)) throw std::runtime_error("permute task with 2^31 or more elements");
-    }
-    t.ndim = (int32_t)ext.size();
-    int64_t total = 1;
-    for (size_t k = 0; k < ext.size(); ++k) {
-      t.ext[k] = (int32_t)ext[k];
-      t.ostr[k] = ostr[k];
-      t.irs[k] = (int32_t)irs[k];
-      t.ics[k] = (int32_t)ics[k];
-      total *= ext[k];
-    }
-    int tdim = -1;
-    for (int k = 1; k < t.ndim; ++k)
-      if (t.irs[k] == 1 && t.ics[k] == 0) tdim = k;
-    bytes += esize * (double)total * (1.0 + (double)t.nsrc);
-    if (t.ostr[0] == 1 && t.irs[0] == 1 && t.ics[0] == 0 && t.ext[0] >= kMinRun) {
-      // mode 0: contiguous runs along dim 0 on both sides -> one run per outer position
-      t.mode = 0;
-      const int32_t task_id = (int32_t)pp.rtasks.size();
-      pp.rtasks.push_back(t);
-      const int64_t outer = total / t.ext[0];
-      for (int64_t o = 0; o < outer; ++o) {
-        int64_t rem = o, dst = t.out_off, ir = 0, ic = 0;
-        for (int k = 1; k < t.ndim; ++k) {
-          const int64_t x = rem % t.ext[k];
-          rem /= t.ext[k];
-          dst += x * t.ostr[k];
-          ir += x * t.irs[k];
-          ic += x * t.ics[k];
-        }
-        for (int64_t e0 = 0; e0 < t.ext[0]; e0 += kRunChunk) {
-          const int32_t len = (int32_t)std::min<int64_t>(kRunChunk, t.ext[0] - e0);
-          pp.runs.push_back(PermRun{dst + e0, ir + e0, ic, len, task_id});
-        }
-      }
-      continue;
-    }
-    if (t.ostr[0] == 1 && tdim > 0 && t.ext[0] >= 4 && t.ext[tdim] >= 4) {
-      t.mode = 1;
-      t.tdim = tdim;
-      t.t0 = 32;
-      t.t1 = 32;
-    } else {
-      t.mode = 2;
-    }
-    pp.tasks.push_back(t);
+    emit_task(pp, t, ext, ostr, irs, ics, bytes);
   }
-  // tile prefix of the tile-kernel tasks
-  int64_t acc = 0;
-  for (auto& t : pp.tasks) {
-    t.tile_begin = acc;
-    int64_t total = 1;
-    for (int k = 0; k < t.ndim; ++k) total *= t.ext[k];
-    if (t.mode == 1) {
-      int64_t outer = total / ((int64_t)t.ext[0] * t.ext[t.tdim]);
-      acc += ((t.ext[0] + 31) / 32) * (int64_t)((t.ext[t.tdim] + 31) / 32) * outer;
-    } else {
-      acc += (total + 255) / 256;
-    }
-  }
-  pp.total_tiles = acc;
+
+  finish_tiles(pp);
   pp.bytes = bytes;
+}
+
+static void upload_permute_tables(Ctx* ctx, PermutePlan& pp) {
+  if (!ctx || ctx->device < 0 || (pp.tasks.empty() && pp.runs.empty())) return;
+  std::vector<int64_t> starts;
+  for (auto& t : pp.tasks) starts.push_back(t.tile_begin);
+  int rc = TK_OK;
+  if (!pp.tasks.empty()) {
+    rc = dev_upload(ctx, (void**)&pp.d_tasks, pp.tasks.data(), pp.tasks.size() * sizeof(PermTask));
+    if (rc == TK_OK) rc = dev_upload(ctx, (void**)&pp.d_tile_starts, starts.data(), starts.size() * sizeof(int64_t));
+  }
+  if (rc == TK_OK && !pp.rtasks.empty())
+    rc = dev_upload(ctx, (void**)&pp.d_rtasks, pp.rtasks.data(), pp.rtasks.size() * sizeof(PermTask));
+  if (rc == TK_OK && !pp.runs.empty())
+    rc = dev_upload(ctx, (void**)&pp.d_runs, pp.runs.data(), pp.runs.size() * sizeof(PermRun));
+  if (rc == TK_OK && !pp.srcs.empty())
+    rc = dev_upload(ctx, (void**)&pp.d_srcs, pp.srcs.data(), pp.srcs.size() * sizeof(PermSrc));
+  if (rc != TK_OK) throw Error{rc, "uploading permute tables failed"};
+}
+
+// Adjoint t^dagger : dom <- cod of t : cod <- dom.  With orthonormal canonical trees the splitting
+// and fusion trees exchange roles, so block c of the result is the conjugate transpose of block c
+// of t: one transpose task per block on the permute kernels (conjugation for complex data).
+std::shared_ptr<PermutePlan> make_adjoint_plan(Ctx* ctx, std::shared_ptr<Structure> in, int dtype) {
+  std::string key = "adj#" + perm_key(in->hash, {}, {}, dtype);
+  if (ctx) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->perm_cache.find(key);
+    if (it != ctx->perm_cache.end()) return it->second;
+  }
+  auto pp = std::make_shared<PermutePlan>();
+  pp->in = in;
+  pp->dtype = dtype;
+  pp->out = build_structure(in->sym, in->dom, in->cod);
+  pp->identity = false;
+  const Structure& out = *pp->out;
+  double bytes = 0;
+  for (const Block& ob : out.blocks) {
+    const int ib = in->block_of(ob.c);
+    if (ib < 0) throw Error{TK_ERR_ARG, "adjoint: coupled sector missing from the input"};
+    const Block& bl = in->blocks[ib];  // rows x cols; the result block is cols x rows
+    PermTask t;
+    std::memset(&t, 0, sizeof(t));
+    t.out_off = ob.offset;
+    t.src_begin = (int32_t)pp->srcs.size();
+    t.nsrc = 1;
+    t.conj = dtype == TK_C128 ? 1 : 0;
+    pp->srcs.push_back(PermSrc{bl.offset, bl.rows, 1.0});
+    // result (k, r) <- input (r, k): dim 0 runs over the input's columns (source stride rows),
+    // dim 1 over its rows (source stride 1); extents of 1 are dropped
+    std::vector<int64_t> ext, ostr, irs, ics;
+    if (bl.cols > 1) {
+      ext.push_back(bl.cols);
+      ostr.push_back(1);
+      irs.push_back(bl.rows);
+      ics.push_back(0);
+    }
+    if (bl.rows > 1) {
+      ext.push_back(bl.rows);
+      ostr.push_back(bl.cols);
+      irs.push_back(1);
+      ics.push_back(0);
+    }
+    emit_task(*pp, t, ext, ostr, irs, ics, bytes);
+  }
+  finish_tiles(*pp);
+  pp->bytes = bytes;
+  upload_permute_tables(ctx, *pp);
+  if (ctx) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->perm_cache[key] = pp;
+  }
+  return pp;
 }
 
 std::shared_ptr<PermutePlan> make_permute_plan(Ctx* ctx, std::shared_ptr<Structure> in,
@@ -435,23 +527,7 @@ std::shared_ptr<PermutePlan> make_permute_plan(Ctx* ctx, std::shared_ptr<Structu
   for (int i = 0; i < n && pp->identity; ++i) pp->identity = all[i] == i;
   build_transform(*pp, p, q);
   build_tasks(*pp);
-  if (ctx && ctx->device >= 0 && (!pp->tasks.empty() || !pp->runs.empty())) {
-    std::vector<int64_t> starts;
-    for (auto& t : pp->tasks) starts.push_back(t.tile_begin);
-    int rc = TK_OK;
-    if (!pp->tasks.empty()) {
-      rc = dev_upload(ctx, (void**)&pp->d_tasks, pp->tasks.data(), pp->tasks.size() * sizeof(PermTask));
-      if (rc == TK_OK)
-        rc = dev_upload(ctx, (void**)&pp->d_tile_starts, starts.data(), starts.size() * sizeof(int64_t));
-    }
-    if (rc == TK_OK && !pp->rtasks.empty())
-      rc = dev_upload(ctx, (void**)&pp->d_rtasks, pp->rtasks.data(), pp->rtasks.size() * sizeof(PermTask));
-    if (rc == TK_OK && !pp->runs.empty())
-      rc = dev_upload(ctx, (void**)&pp->d_runs, pp->runs.data(), pp->runs.size() * sizeof(PermRun));
-    if (rc == TK_OK && !pp->srcs.empty())
-      rc = dev_upload(ctx, (void**)&pp->d_srcs, pp->srcs.data(), pp->srcs.size() * sizeof(PermSrc));
-    if (rc != TK_OK) throw Error{rc, "uploading permute tables failed"};
-  }
+  upload_permute_tables(ctx, *pp);
   if (ctx) {
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->perm_cache[key] = pp;

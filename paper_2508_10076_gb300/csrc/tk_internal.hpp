@@ -106,7 +106,7 @@ struct PermTask {
   int32_t tdim;          // mode 1: the dim that is contiguous in the source
   int32_t src_begin, nsrc;
   int32_t t0, t1;        // tile extents along dim 0 and along the tiled second axis
-  int32_t pad_;
+  int32_t conj;          // 1: conjugate complex values (adjoint)
   int64_t tile_begin;    // first global tile index of this task
 };
 struct PermSrc {
@@ -196,6 +196,7 @@ int finalize_device_tables(Ctx* ctx, ContractPlan& cp);
 std::shared_ptr<PermutePlan> make_permute_plan(Ctx* ctx, std::shared_ptr<Structure> in,
                                                const std::vector<int>& p,
                                                const std::vector<int>& q, int dtype);
+std::shared_ptr<PermutePlan> make_adjoint_plan(Ctx* ctx, std::shared_ptr<Structure> in, int dtype);
 std::shared_ptr<ContractPlan> make_contract_plan(Ctx* ctx, std::shared_ptr<Structure> a,
                                                  const std::vector<int>& pa,
                                                  const std::vector<int>& qa,

@@ -260,3 +260,24 @@ def test_single_site_heff_chain_fp64(gctx, sym, D):
     for i, ((cs, rd), b) in enumerate(zip(ref, outs)):
         assert ch.steps[i].out.blocks() == [(c, r, k, o) for c, r, k, o in cs.blocks]
         assert rel_frobenius_per_block(cs, b.cpu().numpy(), rd) <= FP64_TOL, i
+
+
+@pytest.mark.parametrize("dtype", ["f64", "c128"])
+def test_adjoint_parity(gctx, dtype):
+    """t^dagger on the GPU (block transposes on the permute kernels, conjugated for complex)
+    against the oracle's dense definition, bit for bit (pure data movement)."""
+    api = _api()
+    for case, (sym, legs) in enumerate(PERMUTE_CASES):
+        ost = ostruct(sym, legs)
+        x = wl.normal_complex(30 + case, ost.numel) if dtype == "c128" else wl.normal(30 + case, ost.numel)
+        os2, ref = ops.adjoint(ost, x, tier="dense")
+        lt = _lib_tmap(gctx, sym, legs)
+        plan = api.adjoint_plan(gctx, lt, dtype=dtype)
+        assert plan.output().blocks() == [(c, r, k, o) for c, r, k, o in os2.blocks]
+        xd = _dev(x)
+        y = torch.full((plan.output().numel,), float("nan"), dtype=xd.dtype, device="cuda")
+        api.permute(gctx, plan, xd, y)
+        gctx.sync()
+        _, blk = ops.adjoint(ost, x, tier="block")
+        assert np.array_equal(y.cpu().numpy(), blk)
+        assert np.allclose(y.cpu().numpy(), ref, atol=1e-12)

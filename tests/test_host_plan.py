@@ -161,3 +161,17 @@ def test_errors_are_reported(hctx):
     with pytest.raises(api.TKError) as e:
         hctx.space("Z2", {2: 1})
     assert e.value.code == 4
+
+
+def test_adjoint_plan_structure_matches_oracle(hctx):
+    """The adjoint plan's output structure is the oracle's (domain and codomain exchanged), bit
+    for bit, on a host-only context."""
+    from harness import ostruct
+    for sym, legs in (("SU2", ([({0: 2, 1: 1}, False), ({1: 2}, True)], [({0: 1, 1: 2, 2: 1}, False)])),
+                      ("U1", ([({-1: 2, 0: 3}, False)], [({0: 2, 1: 1}, True), ({-1: 1, 1: 2}, False)]))):
+        ost = ostruct(sym, legs)
+        cod, dom = legs
+        t = hctx.tmap([hctx.space(sym, s, d) for s, d in cod], [hctx.space(sym, s, d) for s, d in dom])
+        plan = api.adjoint_plan(hctx, t)
+        os2, _ = ops.adjoint_block(ost, np.zeros(ost.numel))
+        assert plan.output().blocks() == [(c, r, k, o) for c, r, k, o in os2.blocks]

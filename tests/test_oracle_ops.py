@@ -168,3 +168,41 @@ def test_embed_project_roundtrip_complex():
     rng = np.random.default_rng(11)
     x = rng.standard_normal(st.numel) + 1j * rng.standard_normal(st.numel)
     assert np.allclose(project(st, embed(st, x)), x, atol=1e-14)
+
+
+def _su2_tensor(seed, cod, dom, cplx=False):
+    st = TensorStructure([GradedSpace(SU2, *x) for x in cod], [GradedSpace(SU2, *x) for x in dom])
+    rng = np.random.default_rng(seed)
+    d = rng.normal(size=st.numel)
+    if cplx:
+        d = d + 1j * rng.normal(size=st.numel)
+    return st, d
+
+
+def test_adjoint_dense_equals_block_and_is_an_involution():
+    """The dense definition (conjugate, exchange codomain and domain, project) and the block
+    form agree; applying the adjoint twice gives back t; the Frobenius norm is kept."""
+    st, d = _su2_tensor(3, [({0: 2, 1: 1}, False), ({1: 2}, True)], [({0: 1, 1: 2, 2: 1}, False)], cplx=True)
+    s1, a1 = ops.adjoint(st, d, tier="dense")
+    s2, a2 = ops.adjoint(st, d, tier="block")
+    assert s1.blocks == s2.blocks
+    assert np.allclose(a1, a2, atol=1e-13)
+    s3, a3 = ops.adjoint(s2, a2, tier="dense")
+    assert s3.blocks == st.blocks and np.allclose(a3, d, atol=1e-13)
+    assert np.isclose(np.linalg.norm(a2), np.linalg.norm(d))
+
+
+def test_adjoint_reverses_composition():
+    """(A o B)^dagger = B^dagger o A^dagger, on SU(2) maps with dual legs (dense tier throughout)."""
+    V = ({0: 1, 1: 2}, False)
+    W = ({1: 1, 2: 1}, True)
+    U = ({0: 2, 2: 1}, False)
+    sa, da = _su2_tensor(4, [V, W], [U, V], cplx=True)       # A : V W <- U V
+    sb, db = _su2_tensor(5, [U, V], [W], cplx=True)          # B : U V <- W
+    sab, dab = ops.contract(sa, da, (0, 1), (2, 3), sb, db, (0, 1), (2,), (0, 1), (2,), tier="dense")
+    s_l, d_l = ops.adjoint(sab, dab, tier="dense")           # (A o B)^dagger : W <- V W
+    sbd, dbd = ops.adjoint(sb, db, tier="dense")             # B^dagger : W <- U V
+    sad, dad = ops.adjoint(sa, da, tier="dense")             # A^dagger : U V <- V W
+    s_r, d_r = ops.contract(sbd, dbd, (0,), (1, 2), sad, dad, (0, 1), (2, 3), (0,), (1, 2), tier="dense")
+    assert s_l.blocks == s_r.blocks
+    assert np.allclose(d_l, d_r, atol=1e-12)
