@@ -200,6 +200,30 @@ int tk_contract_batch(tk_ctx* ctx, int n, const tk_plan* const* plans, const voi
                       const void* const* b, void* const* c, void* const* workspace,
                       const size_t* workspace_bytes, void* stream);
 
+/* ---- block SVD and truncation (Algorithm 9, the decomposition after the two-site step of
+ * Algorithm 12).  For t : cod <- dom the SVD is block-wise: t = U S V^dagger with the bond space
+ * W = sum_c (c, r_c), r_c = min(rows_c, cols_c) over the coupled sectors c of t, U : cod <- W,
+ * V^dagger : W <- dom, and the singular values concatenated by sector (descending within a
+ * sector; SU(2) values stand for d_c states each).  Blocks are factorised with cuSOLVER's Jacobi
+ * SVD (gesvdj) on a copy in the workspace.
+ *   tk_svd_plan     plan for t's structure (dtype TK_F64 or TK_C128);
+ *   tk_svd_outputs  structures of U and V^dagger (caller frees with tk_tmap_destroy) and the number
+ *                   of singular values;
+ *   tk_svd_block    block i: coupled sector, rows, columns and the offset of its singular values;
+ *   tk_svd          t -> U, S, V^dagger (device buffers; workspace of tk_plan_workspace_bytes);
+ *   tk_svd_truncate keep[i] (0..min(rows, cols)) leading triplets of block i into the truncated
+ *                   U : cod <- W', S, V^dagger : W' <- dom with W' = sum_c (c, keep_c) (sectors with
+ *                   keep 0 dropped), all concatenated in sector order. */
+int tk_svd_plan(tk_ctx* ctx, const tk_tmap* a, int dtype, tk_plan** out);
+int tk_svd_outputs(tk_ctx* ctx, const tk_plan* plan, tk_tmap** u, tk_tmap** vh, int64_t* nvalues);
+int64_t tk_svd_nblocks(const tk_plan* plan);
+int tk_svd_block(const tk_plan* plan, int64_t i, int32_t* sector, int64_t* rows, int64_t* cols,
+                 int64_t* values_offset);
+int tk_svd(tk_ctx* ctx, const tk_plan* plan, const void* a, void* u, double* s, void* vh, void* workspace,
+           size_t workspace_bytes, void* stream);
+int tk_svd_truncate(tk_ctx* ctx, const tk_plan* plan, const int64_t* keep, const void* u, const double* s,
+                    const void* vh, void* ut, double* st, void* vht, void* stream);
+
 /* Autotuner (not in the paper): times the candidate work lists of a contraction plan on the given
  * buffers (median of three runs each, CUDA events on `stream`, which is synchronised) and keeps the
  * fastest: FP64 tiles 32 or 64 wide with split-K off or at its maximum, or the built-in heuristic;

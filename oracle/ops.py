@@ -231,3 +231,41 @@ def adjoint_block(struct: TensorStructure, data):
 def adjoint(struct, data, tier="block"):
     return adjoint_dense(struct, data) if tier == "dense" else adjoint_block(struct, data)
 
+
+def svd_block(struct: TensorStructure, data):
+    """Block SVD (Algorithm 9): per coupled sector c, t_c = U_c diag(s_c) V_c^dagger with
+    r_c = min(rows_c, cols_c) values, descending.  Returns [(c, U_c, s_c, Vh_c)] in sector order
+    (dense numpy matrices; sectors with an empty block are skipped)."""
+    data = np.asarray(data)
+    out = []
+    for c, rows, cols, off in struct.blocks:
+        if min(rows, cols) == 0:
+            continue
+        blk = data[off:off + rows * cols].reshape(cols, rows).T
+        u, s, vh = np.linalg.svd(blk, full_matrices=False)
+        out.append((c, u, s, vh))
+    return out
+
+
+def truncation_keep(struct: TensorStructure, svals, dmax):
+    """Keep counts per block for a truncation to at most dmax states: the largest singular values
+    over all sectors, each value of sector c standing for d_c states (an SU(2) multiplet); ties
+    broken by ascending sector.  Returns (keep per block, relative discarded weight
+    sqrt(sum_discarded d_c s^2 / sum_all d_c s^2))."""
+    entries = []
+    for b, (c, s) in enumerate(svals):
+        for v in s:
+            entries.append((-float(v), c, b))
+    entries.sort()
+    keep = [0] * len(svals)
+    used, kept_w, total_w = 0, 0.0, 0.0
+    for negv, c, b in entries:
+        d = struct.sym.dim(c)
+        total_w += d * negv * negv
+        if used + d <= dmax:
+            keep[b] += 1
+            used += d
+            kept_w += d * negv * negv
+    err = np.sqrt(max(total_w - kept_w, 0.0) / total_w) if total_w > 0 else 0.0
+    return keep, err
+

@@ -58,6 +58,13 @@ SIGNATURES = {
     "tk_contract": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
     "tk_contract_noalloc": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tk_contract_batch": (C.c_int, [c_vp, C.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "tk_svd_plan": (C.c_int, [c_vp, c_vp, C.c_int, C.POINTER(c_vp)]),
+    "tk_svd_outputs": (C.c_int, [c_vp, c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(C.c_int64)]),
+    "tk_svd_nblocks": (C.c_int64, [c_vp]),
+    "tk_svd_block": (C.c_int, [c_vp, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                               C.POINTER(C.c_int64)]),
+    "tk_svd": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
+    "tk_svd_truncate": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tk_plan_autotune": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, C.c_size_t, c_vp, c_vp]),
     "tk_copy_h2d": (C.c_int, [c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
     "tk_copy_d2h": (C.c_int, [c_vp, c_vp, c_vp, C.c_size_t, c_vp]),

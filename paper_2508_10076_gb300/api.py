@@ -275,6 +275,45 @@ def adjoint_plan(ctx, t, dtype="f64"):
     return Plan(ctx, h, "permute")
 
 
+class SvdPlan(Plan):
+    """Block SVD of a tensor map's structure (tk_svd_plan)."""
+
+    def outputs(self):
+        """(U structure, V^dagger structure, number of singular values)."""
+        hu, hv, n = C.c_void_p(), C.c_void_p(), C.c_int64(0)
+        _check(_lib().tk_svd_outputs(self.ctx._h, self._h, C.byref(hu), C.byref(hv), C.byref(n)), self.ctx)
+        return TensorMap(self.ctx, None, None, _handle=hu), TensorMap(self.ctx, None, None, _handle=hv), n.value
+
+    def blocks(self):
+        """[(sector, rows, cols, offset of its singular values)] in sector order."""
+        out = []
+        for i in range(int(_lib().tk_svd_nblocks(self._h))):
+            c, r, k, o = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int64()
+            _lib().tk_svd_block(self._h, i, C.byref(c), C.byref(r), C.byref(k), C.byref(o))
+            out.append((c.value, r.value, k.value, o.value))
+        return out
+
+
+def svd_plan(ctx, t, dtype="f64"):
+    h = C.c_void_p()
+    _check(_lib().tk_svd_plan(ctx._h, t._h, DTYPE[dtype], C.byref(h)), ctx)
+    return SvdPlan(ctx, h, "svd")
+
+
+def svd(ctx, plan, a, u, s, vh, workspace, stream=None):
+    """tk_svd: a -> (u, s, vh) device tensors laid out as plan.outputs()."""
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(_lib().tk_svd(ctx._h, plan._h, _ptr(a), _ptr(u), _ptr(s), _ptr(vh), _ptr(workspace),
+                         C.c_size_t(nbytes), _stream_handle(stream)), ctx)
+
+
+def svd_truncate(ctx, plan, keep, u, s, vh, ut, st, vht, stream=None):
+    """tk_svd_truncate: keep[i] leading triplets of block i (plan.blocks() order)."""
+    arr = (C.c_int64 * max(1, len(keep)))(*[int(k) for k in keep])
+    _check(_lib().tk_svd_truncate(ctx._h, plan._h, arr, _ptr(u), _ptr(s), _ptr(vh), _ptr(ut), _ptr(st), _ptr(vht),
+                                  _stream_handle(stream)), ctx)
+
+
 def contract_plan(ctx, a, pa, qa, b, pb, qb, pab, qab, dtype="f64", gemm="fp64", slices=0):
     args = []
     for xs in (pa, qa):

@@ -18,9 +18,10 @@ struct tk_tmap {
   std::shared_ptr<tk::Structure> st;
 };
 struct tk_plan {
-  int kind = 0;  // 0 permute, 1 contract
+  int kind = 0;  // 0 permute, 1 contract, 2 block SVD
   std::shared_ptr<tk::PermutePlan> perm;
   std::shared_ptr<tk::ContractPlan> con;
+  std::shared_ptr<tk::SvdPlan> svd;
 };
 
 namespace {
@@ -115,6 +116,7 @@ void tk_ctx_destroy(tk_ctx* ctx) {
     cudaSetDevice(ctx->c.device);
     ctx->c.perm_cache.clear();
     ctx->c.contract_cache.clear();
+    tk::destroy_solver_handle(&ctx->c);
     if (ctx->c.d_status) cudaFree(ctx->c.d_status);
   }
   delete ctx;
@@ -405,13 +407,15 @@ int tk_plan_output(tk_ctx* ctx, const tk_plan* plan, tk_tmap** out) {
   if (!plan || !out) return fail(ctx, TK_ERR_ARG, "null argument");
   auto* t = new (std::nothrow) tk_tmap();
   if (!t) return TK_ERR_OOM;
-  t->st = plan->kind == 0 ? plan->perm->out : plan->con->c;
+  t->st = plan->kind == 0 ? plan->perm->out : plan->kind == 1 ? plan->con->c : plan->svd->u;
   *out = t;
   return TK_OK;
 }
 
 size_t tk_plan_workspace_bytes(const tk_plan* plan) {
-  if (!plan || plan->kind != 1) return 0;
+  if (!plan) return 0;
+  if (plan->kind == 2) return plan->svd->ws_total;
+  if (plan->kind != 1) return 0;
   return plan->con->ws_total;
 }
 
@@ -607,6 +611,76 @@ int tk_plan_autotune(tk_ctx* ctx, tk_plan* plan, const void* a, const void* b, v
   if (rc2 != TK_OK) return fail(ctx, rc2, "rebuilding the chosen work lists failed");
   if (choice) *choice = best_i * 8 + best_j;
   return TK_OK;
+}
+
+int tk_svd_plan(tk_ctx* ctx, const tk_tmap* a, int dtype, tk_plan** out) {
+  if (!ctx || !a || !out) return fail(ctx, TK_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (dtype != TK_F64 && dtype != TK_C128) return fail(ctx, TK_ERR_ARG, "unknown dtype");
+  return guarded(ctx, [&]() {
+    if (ctx->c.device >= 0 && cudaSetDevice(ctx->c.device) != cudaSuccess)
+      return fail(ctx, TK_ERR_CUDA, "cudaSetDevice failed");
+    auto pl = new tk_plan();
+    pl->kind = 2;
+    try {
+      pl->svd = tk::make_svd_plan(&ctx->c, a->st, dtype);
+    } catch (...) {
+      delete pl;
+      throw;
+    }
+    *out = pl;
+    return TK_OK;
+  });
+}
+
+int tk_svd_outputs(tk_ctx* ctx, const tk_plan* plan, tk_tmap** u, tk_tmap** vh, int64_t* nvalues) {
+  if (!plan || plan->kind != 2) return fail(ctx, TK_ERR_ARG, "not an SVD plan");
+  if (u) {
+    *u = new (std::nothrow) tk_tmap();
+    if (!*u) return TK_ERR_OOM;
+    (*u)->st = plan->svd->u;
+  }
+  if (vh) {
+    *vh = new (std::nothrow) tk_tmap();
+    if (!*vh) return TK_ERR_OOM;
+    (*vh)->st = plan->svd->vh;
+  }
+  if (nvalues) *nvalues = plan->svd->nvalues;
+  return TK_OK;
+}
+
+int64_t tk_svd_nblocks(const tk_plan* plan) { return plan && plan->kind == 2 ? (int64_t)plan->svd->blocks.size() : -1; }
+
+int tk_svd_block(const tk_plan* plan, int64_t i, int32_t* sector, int64_t* rows, int64_t* cols, int64_t* values_offset) {
+  if (!plan || plan->kind != 2 || i < 0 || i >= (int64_t)plan->svd->blocks.size()) return TK_ERR_ARG;
+  const tk::SvdBlock& k = plan->svd->blocks[(size_t)i];
+  if (sector) *sector = k.c;
+  if (rows) *rows = k.m;
+  if (cols) *cols = k.n;
+  if (values_offset) *values_offset = k.s_off;
+  return TK_OK;
+}
+
+int tk_svd(tk_ctx* ctx, const tk_plan* plan, const void* a, void* u, double* s, void* vh, void* workspace,
+           size_t workspace_bytes, void* stream) {
+  if (!ctx || !plan || plan->kind != 2) return fail(ctx, TK_ERR_ARG, "not an SVD plan");
+  if (!a || !u || !s || !vh) return fail(ctx, TK_ERR_ARG, "null buffer");
+  const tk::SvdPlan& sp = *plan->svd;
+  if (workspace_bytes < sp.ws_total || !workspace)
+    return fail(ctx, TK_ERR_WORKSPACE, "workspace smaller than tk_plan_workspace_bytes()");
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  rc = tk::run_svd(&ctx->c, sp, a, u, s, vh, workspace, stream);
+  return rc == TK_OK ? TK_OK : fail(ctx, rc, ctx->c.last_error.empty() ? "block SVD failed" : ctx->c.last_error);
+}
+
+int tk_svd_truncate(tk_ctx* ctx, const tk_plan* plan, const int64_t* keep, const void* u, const double* s,
+                    const void* vh, void* ut, double* st, void* vht, void* stream) {
+  if (!ctx || !plan || plan->kind != 2 || !keep) return fail(ctx, TK_ERR_ARG, "not an SVD plan");
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  rc = tk::run_svd_truncate(&ctx->c, *plan->svd, keep, u, s, vh, ut, st, vht, stream);
+  return rc == TK_OK ? TK_OK : fail(ctx, rc, "truncation copy failed");
 }
 
 int tk_copy_h2d(tk_ctx* ctx, void* dst_device, const void* src_host, size_t bytes, void* stream) {

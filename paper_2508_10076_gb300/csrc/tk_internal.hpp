@@ -233,7 +233,31 @@ struct Ctx {
     void* end;
   };
   std::vector<Rec> prof;
+  void* solver = nullptr;  // cuSOLVER dense handle, created on first use (block SVD)
 };
+
+// ---- block SVD (Algorithm 9 after the two-site step of Algorithm 12)
+struct SvdBlock {
+  int32_t c;
+  int64_t m, n, r;                       // block rows, columns, min(m, n)
+  int64_t a_off, u_off, vh_off, s_off;   // element offsets in t, U, V^dagger and the values
+};
+struct SvdPlan {
+  std::shared_ptr<Structure> in, u, vh;  // t : cod <- dom, U : cod <- W, V^dagger : W <- dom
+  Space bond;                            // W = sum_c (c, min(rows_c, cols_c))
+  std::vector<SvdBlock> blocks;
+  int64_t nvalues = 0;                   // singular values, concatenated by sector
+  int64_t lwork = 0;
+  size_t ws_solver = 0, ws_total = 0;
+  int dtype = TK_F64;
+  ~SvdPlan();
+};
+void* solver_handle(Ctx* ctx);  // the context's cuSOLVER handle (created on first use), or null
+void destroy_solver_handle(Ctx* ctx);
+std::shared_ptr<SvdPlan> make_svd_plan(Ctx* ctx, std::shared_ptr<Structure> in, int dtype);
+int run_svd(Ctx* ctx, const SvdPlan& sp, const void* a, void* u, double* s, void* vh, void* ws, void* stream);
+int run_svd_truncate(Ctx* ctx, const SvdPlan& sp, const int64_t* keep, const void* u, const double* s, const void* vh,
+                     void* ut, double* st, void* vht, void* stream);
 
 // Brackets one launch with events on its stream when the context is profiling.
 struct ProfScope {

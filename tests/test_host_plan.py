@@ -175,3 +175,20 @@ def test_adjoint_plan_structure_matches_oracle(hctx):
         plan = api.adjoint_plan(hctx, t)
         os2, _ = ops.adjoint_block(ost, np.zeros(ost.numel))
         assert plan.output().blocks() == [(c, r, k, o) for c, r, k, o in os2.blocks]
+
+
+def test_svd_plan_structures_match_oracle(hctx):
+    """U : cod <- W and V^dagger : W <- dom with W = sum_c (c, min(rows_c, cols_c)), bit for bit."""
+    from harness import ostruct
+    for sym, legs in (("SU2", ([({0: 2, 1: 2}, False), ({1: 1}, False)], [({0: 1, 1: 2, 2: 1}, False), ({1: 1}, True)])),
+                      ("U1", ([({-1: 2, 0: 3}, False), ({1: 1, -1: 1}, False)], [({0: 2, 1: 1}, False)]))):
+        ost = ostruct(sym, legs)
+        cod, dom = legs
+        t = hctx.tmap([hctx.space(sym, s, d) for s, d in cod], [hctx.space(sym, s, d) for s, d in dom])
+        plan = api.svd_plan(hctx, t)
+        u, vh, n = plan.outputs()
+        w = GradedSpace(ost.sym, {c: min(r, k) for c, r, k, _ in ost.blocks if min(r, k) > 0})
+        ou, ov = TensorStructure(ost.cod, [w]), TensorStructure([w], ost.dom)
+        assert u.blocks() == [(c, r, k, o) for c, r, k, o in ou.blocks]
+        assert vh.blocks() == [(c, r, k, o) for c, r, k, o in ov.blocks]
+        assert n == sum(min(r, k) for _, r, k, _ in ost.blocks)

@@ -206,3 +206,29 @@ def test_adjoint_reverses_composition():
     s_r, d_r = ops.contract(sbd, dbd, (0,), (1, 2), sad, dad, (0, 1), (2, 3), (0,), (1, 2), tier="dense")
     assert s_l.blocks == s_r.blocks
     assert np.allclose(d_l, d_r, atol=1e-12)
+
+
+def test_block_svd_matches_dense_spectrum_and_reconstructs():
+    """The block SVD of an SU(2) tensor map: every block singular value appears d_c times among
+    the singular values of the dense embedded matrix (codomain x domain), the blocks reconstruct
+    t, and the truncation rule keeps whole multiplets."""
+    st, d = _su2_tensor(9, [({0: 2, 1: 2}, False), ({1: 1}, False)], [({0: 1, 1: 2, 2: 1}, False), ({1: 1}, True)])
+    blocks = ops.svd_block(st, d)
+    n1 = len(st.cod)
+    dense = embed(st, d)
+    rows = int(np.prod(dense.shape[:n1]))
+    sv_dense = np.sort(np.linalg.svd(dense.reshape(rows, -1), compute_uv=False))[::-1]
+    sv_blocks = np.sort(np.concatenate([np.repeat(s, st.sym.dim(c)) for c, _, s, _ in blocks]))[::-1]
+    nz = sv_dense[sv_dense > 1e-10]
+    assert np.allclose(nz, sv_blocks[:len(nz)], rtol=1e-12)
+    assert np.all(sv_blocks[len(nz):] < 1e-10)
+    bd = st.block_dict()
+    for c, u, s, vh in blocks:
+        r, k, off = bd[c]
+        assert np.allclose((u * s) @ vh, d[off:off + r * k].reshape(k, r).T, atol=1e-12)
+    keep, err = ops.truncation_keep(st, [(c, s) for c, _, s, _ in blocks], dmax=7)
+    assert sum(st.sym.dim(c) * k for (c, _, _, _), k in zip(blocks, keep)) <= 7
+    assert 0 < err < 1
+    # the kept values are the largest: any discarded value of a sector is below every kept one of it
+    for (c, _, s, _), k in zip(blocks, keep):
+        assert np.all(s[:k][:, None] >= s[k:][None, :])
