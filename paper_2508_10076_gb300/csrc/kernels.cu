@@ -331,19 +331,47 @@ __device__ __forceinline__ void gemm_tile(const GemmItem& it, const GemmTile& tl
   const T* Ab = A + it.a_off;
   const T* Bb = B + it.b_off;
   const int64_t kend = tl.k1;
-  for (int64_t k0 = tl.k0; k0 < kend; k0 += BK) {
-    const int kmax = (int)((kend - k0) < BK ? (kend - k0) : BK);
-    for (int e = tid; e < BM * BK; e += 256) {
-      const int mm = e % BM, kk = e / BM;
+  // The next k-chunk's operands are loaded into registers while the current chunk is multiplied
+  // out of shared memory, so each chunk's global-load latency overlaps the previous chunk's FMAs.
+  constexpr int LA = BM * BK / 256, LB = BN * BK / 256;
+  T ra[LA], rb[LB];
+  auto load = [&](int64_t k0, int kmax) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + 256 * q, mm = e % BM, kk = e / BM;
       const int64_t gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < M && kk < kmax) ? Ab[gm + gk * M] : Elem<T>::zero();
+      ra[q] = (gm < M && kk < kmax) ? Ab[gm + gk * M] : Elem<T>::zero();
     }
-    for (int e = tid; e < BN * BK; e += 256) {
-      const int kb = e % BK, nn = e / BK;
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + 256 * q, kb = e % BK, nn = e / BK;
       const int64_t gk = k0 + kb, gn = n0 + nn;
-      Bs[kb][nn] = (kb < kmax && gn < N) ? Bb[gk + gn * K] : Elem<T>::zero();
+      rb[q] = (kb < kmax && gn < N) ? Bb[gk + gn * K] : Elem<T>::zero();
     }
-    __syncthreads();
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      const int e = tid + 256 * q;
+      As[e / BM][e % BM] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int e = tid + 256 * q;
+      Bs[e % BK][e / BK] = rb[q];
+    }
+  };
+  int64_t k0 = tl.k0;
+  int kmax = (int)((kend - k0) < BK ? (kend - k0) : BK);
+  if (k0 < kend) {
+    load(k0, kmax);
+    store();
+  }
+  __syncthreads();
+  while (k0 < kend) {
+    const int64_t kn = k0 + BK;
+    const int kmaxn = kn < kend ? (int)((kend - kn) < BK ? (kend - kn) : BK) : 0;
+    if (kn < kend) load(kn, kmaxn);
 #pragma unroll 4
     for (int kk = 0; kk < kmax; ++kk) {
       T a[TM], b[TN];
@@ -357,6 +385,10 @@ __device__ __forceinline__ void gemm_tile(const GemmItem& it, const GemmTile& tl
         for (int j = 0; j < TN; ++j) Mac<T>::mac(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
+    if (kn < kend) store();
+    __syncthreads();
+    k0 = kn;
+    kmax = kmaxn;
   }
   T* Cb = C + it.c_off;
   if (tl.slot >= 0) {
@@ -634,7 +666,7 @@ __device__ __forceinline__ void gemm_rows_df_dispatch<double>(const GemmItem& it
 // One launch per contraction for every FP64-list product: 64x64 / 32x32 tiles and the N <= 8
 // row blocks share the grid (their shared-memory needs overlap in one buffer).
 template <typename T, bool DF>
-__global__ void __launch_bounds__(256) k_gemm_f64(const GemmItem* __restrict__ items,
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 1) k_gemm_f64(const GemmItem* __restrict__ items,
                                                   const GemmTile* __restrict__ tiles,
                                                   const T* __restrict__ A,
                                                   const T* __restrict__ B, T* __restrict__ C,
@@ -668,7 +700,7 @@ struct GemmBatch {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_gemm_batch(const __grid_constant__ GemmBatch L) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 1) k_gemm_batch(const __grid_constant__ GemmBatch L) {
   constexpr int kTileElems = BK * 65 * 2, kRowElems = ROWS_KCHUNK * ROWS_NMAX;
   __shared__ T smem[kTileElems > kRowElems ? kTileElems : kRowElems];
   const GemmSeg& g = L.seg[find_seg(L.seg, L.nseg, (int64_t)blockIdx.x)];
