@@ -174,8 +174,8 @@ double tk_plan_permute_bytes(const tk_plan* plan);
  * if that permute is absent (identity permutes are skipped). */
 int64_t tk_plan_ntransform(const tk_plan* plan, int which);
 /* How the device executes one of the plan's permutes (which as above), for tuning and tests:
- * stats[0..2] = contiguous-run tasks, their elements, runs; stats[3..4] = transpose-tile tasks,
- * their elements; stats[5..6] = element-wise tasks, their elements; stats[7] = tiles. */
+ * stats[0..2] = contiguous-run tasks, their elements, runs; stats[3..4] = transpose-tile tasks
+ * (scalar tiles, or tiles of short vectors contiguous on both sides), their elements; stats[5..6] = element-wise tasks, their elements; stats[7] = tiles. */
 int tk_plan_permute_stats(const tk_plan* plan, int which, int64_t* stats);
 int tk_plan_transform(const tk_plan* plan, int which, int64_t k, int64_t* src_offset,
                       int64_t* dst_offset, double* coef);

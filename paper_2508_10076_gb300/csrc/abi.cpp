@@ -482,7 +482,7 @@ int tk_plan_permute_stats(const tk_plan* plan, int which, int64_t* stats) {
   }
   stats[2] = (int64_t)p->runs.size();
   for (const auto& t : p->tasks) {
-    const int m = t.mode == 1 ? 3 : 5;
+    const int m = (t.mode == 1 || t.mode == 3) ? 3 : 5;
     stats[m] += 1;
     stats[m + 1] += elems(t);
   }

@@ -49,7 +49,7 @@ PermutePlan::~PermutePlan() {
   dev_free(d_rtasks);
   dev_free(d_runs);
   dev_free(d_srcs);
-  dev_free(d_tile_starts);
+  dev_free(d_tile_task);
 }
 
 ContractPlan::~ContractPlan() {
@@ -106,11 +106,11 @@ static_assert(sizeof(PermTask) % sizeof(int64_t) == 0, "PermTask must be 8-byte 
 // e.g. both operands of a contraction); each segment owns a contiguous range of blocks.
 struct PermSeg {
   int32_t kind;    // 0: contiguous runs, 1: tiles, 2: clear nwork ints at out (split-K counters)
-  int32_t ntasks;  // tiles: number of tasks (binary search range)
+  int32_t pad_;
   int64_t block0, nblocks, nwork;  // blocks [block0, block0 + nblocks); runs or tiles to do
   const PermRun* runs;
   const PermTask* tasks;  // run tasks (kind 0) or tile tasks (kind 1)
-  const int64_t* tile_starts;
+  const int32_t* tile_task;  // tiles: owning task of every tile
   const PermSrc* srcs;
   const void* in;
   void* out;
@@ -138,56 +138,89 @@ __device__ __forceinline__ int find_seg(const Seg* segs, int nseg, int64_t b) {
   return lo;
 }
 
+// Outer offsets of one tile: the dims other than the tiled ones, decoded from o (32-bit: a task
+// has fewer than 2^31 elements).
+__device__ __forceinline__ void tile_outer(const PermTask& t, int kfirst, int skip1, int skip2, int o, int64_t& ob,
+                                           int64_t& irb, int64_t& icb) {
+  ob = t.out_off;
+  irb = 0;
+  icb = 0;
+  for (int k = kfirst; k < t.ndim; ++k) {
+    if (k == skip1 || k == skip2) continue;
+    const int x = o % t.ext[k];
+    o /= t.ext[k];
+    ob += (int64_t)x * t.ostr[k];
+    irb += (int64_t)x * t.irs[k];
+    icb += (int64_t)x * t.ics[k];
+  }
+}
+
+// Short-vector transpose tile (mode 3): dim 0 (E elements) is contiguous on both sides and moves
+// as a unit; dim 1 follows it in the destination, dim td in the source.  A tile is 16 (dim 1) x
+// 16 (dim td) vectors: loads run along (dim 0, dim td), stores along (dim 0, dim 1).
+template <typename T, int E>
+__device__ __forceinline__ void permute_vec_tile(const PermTask& t, int local, const PermSrc* __restrict__ srcs,
+                                                 const T* __restrict__ in, T* __restrict__ out, T* s) {
+  constexpr int SPAN = 16 * E, ROW = SPAN + 1;  // s: [16 b][16 E + 1]
+  const int tid = threadIdx.x;
+  const int td = t.tdim, ea = t.ext[1], eb = t.ext[td];
+  const int nba = (ea + 15) / 16, nbb = (eb + 15) / 16;
+  const int ba = local % nba, rest = local / nba;
+  const int bb = rest % nbb;
+  int64_t ob, irb, icb;
+  tile_outer(t, 2, td, td, rest / nbb, ob, irb, icb);
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const int idx = tid + 256 * q;
+    const int wb = idx % SPAN, al = idx / SPAN;  // along the source: (w, b) contiguous
+    const int w = wb % E, bl = wb / E;
+    const int a = ba * 16 + al, b = bb * 16 + bl;
+    if (a < ea && b < eb)
+      s[bl * ROW + al * E + w] =
+          gather<T>(srcs, t.nsrc, t.src_begin, in, irb + (int64_t)a * t.irs[1] + (int64_t)b * E + w,
+                    icb + (int64_t)a * t.ics[1], t.conj);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const int idx = tid + 256 * q;
+    const int wa = idx % SPAN, bl = idx / SPAN;  // along the destination: (w, a) contiguous
+    const int a = ba * 16 + wa / E, b = bb * 16 + bl;
+    if (a < ea && b < eb) out[ob + (int64_t)b * t.ostr[td] + (int64_t)ba * 16 * E + wa] = s[bl * ROW + wa];
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void permute_tiles(const PermSeg& g, int64_t bid, T (*tile)[33], int64_t* task_words) {
   const PermTask& t = *reinterpret_cast<const PermTask*>(task_words);
   const PermTask* __restrict__ tasks = g.tasks;
-  const int64_t* __restrict__ tile_starts = g.tile_starts;
+  const int32_t* __restrict__ tile_task = g.tile_task;
   const PermSrc* __restrict__ srcs = g.srcs;
   const T* __restrict__ in = (const T*)g.in;
   T* __restrict__ out = (T*)g.out;
-  const int ntasks = g.ntasks;
   const int tid = threadIdx.x;
   for (int64_t tidx = bid; tidx < g.nwork; tidx += g.nblocks) {
-    // locate the task owning this tile
-    int lo = 0, hi = ntasks - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (__ldg(tile_starts + mid) <= tidx)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
+    const int task = __ldg(tile_task + tidx);  // the task owning this tile
     __syncthreads();  // previous iteration finished with task_words / tile
-    if (tid < kTaskWords) task_words[tid] = reinterpret_cast<const int64_t*>(tasks + lo)[tid];
+    if (tid < kTaskWords) task_words[tid] = __ldg(reinterpret_cast<const int64_t*>(tasks + task) + tid);
     __syncthreads();
-    const int64_t local = tidx - t.tile_begin;
-    const int nd = t.ndim;
+    const int local = (int)(tidx - t.tile_begin);
     if (t.mode == 1) {
       const int td = t.tdim;
       const int e0 = t.ext[0], et = t.ext[td];
-      const int64_t nb0 = (e0 + 31) / 32, nbt = (et + 31) / 32;
-      const int64_t b0 = local % nb0;
-      int64_t rest = local / nb0;
-      const int64_t bt = rest % nbt;
-      int64_t o = rest / nbt;
-      int64_t ob = t.out_off, irb = 0, icb = 0;
-      for (int k = 1; k < nd; ++k) {
-        if (k == td) continue;
-        const int64_t x = o % t.ext[k];
-        o /= t.ext[k];
-        ob += x * t.ostr[k];
-        irb += x * t.irs[k];
-        icb += x * t.ics[k];
-      }
+      const int nb0 = (e0 + 31) / 32, nbt = (et + 31) / 32;
+      const int b0 = local % nb0, rest = local / nb0;
+      const int bt = rest % nbt;
+      int64_t ob, irb, icb;
+      tile_outer(t, 1, td, td, rest / nbt, ob, irb, icb);
       const int lx = tid & 31, ly = tid >> 5;
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int j0 = ly + 8 * r;
-        const int64_t i0 = b0 * 32 + j0, it = bt * 32 + lx;
+        const int i0 = b0 * 32 + j0, it = bt * 32 + lx;
         if (i0 < e0 && it < et) {
-          const int64_t ir = irb + i0 * t.irs[0] + it * t.irs[td];
-          const int64_t ic = icb + i0 * t.ics[0] + it * t.ics[td];
+          const int64_t ir = irb + (int64_t)i0 * t.irs[0] + it;  // irs[td] = 1
+          const int64_t ic = icb + (int64_t)i0 * t.ics[0];       // ics[td] = 0
           tile[j0][lx] = gather<T>(srcs, t.nsrc, t.src_begin, in, ir, ic, t.conj);
         }
       }
@@ -195,21 +228,29 @@ __device__ __forceinline__ void permute_tiles(const PermSeg& g, int64_t bid, T (
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int jt = ly + 8 * r;
-        const int64_t i0 = b0 * 32 + lx, it = bt * 32 + jt;
-        if (i0 < e0 && it < et) out[ob + i0 + it * t.ostr[td]] = tile[lx][jt];
+        const int i0 = b0 * 32 + lx, it = bt * 32 + jt;
+        if (i0 < e0 && it < et) out[ob + i0 + (int64_t)it * t.ostr[td]] = tile[lx][jt];
       }
+    } else if (t.mode == 3) {
+      T* s = &tile[0][0];
+      if (t.ext[0] == 2)
+        permute_vec_tile<T, 2>(t, local, srcs, in, out, s);
+      else if (t.ext[0] == 3)
+        permute_vec_tile<T, 3>(t, local, srcs, in, out, s);
+      else
+        permute_vec_tile<T, 4>(t, local, srcs, in, out, s);
     } else {
-      int64_t total = 1;
-      for (int k = 0; k < nd; ++k) total *= t.ext[k];
-      int64_t e = local * 256 + tid;
+      int total = 1;
+      for (int k = 0; k < t.ndim; ++k) total *= t.ext[k];
+      int e = local * 256 + tid;
       if (e < total) {
         int64_t oa = t.out_off, ir = 0, ic = 0;
-        for (int k = 0; k < nd; ++k) {
-          const int64_t x = e % t.ext[k];
+        for (int k = 0; k < t.ndim; ++k) {
+          const int x = e % t.ext[k];
           e /= t.ext[k];
-          oa += x * t.ostr[k];
-          ir += x * t.irs[k];
-          ic += x * t.ics[k];
+          oa += (int64_t)x * t.ostr[k];
+          ir += (int64_t)x * t.irs[k];
+          ic += (int64_t)x * t.ics[k];
         }
         out[oa] = gather<T>(srcs, t.nsrc, t.src_begin, in, ir, ic, t.conj);
       }
@@ -260,7 +301,7 @@ __device__ __forceinline__ void permute_runs(const PermSeg& g, int64_t bid) {
 }
 
 template <typename T, int NSEG>
-__global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PermLaunchT<NSEG> L) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 5 : 4) k_permute(const __grid_constant__ PermLaunchT<NSEG> L) {
   __shared__ T tile[32][33];
   __shared__ int64_t task_words[kTaskWords];
   const PermSeg& g = L.seg[find_seg(L.seg, L.nseg, (int64_t)blockIdx.x)];
@@ -284,14 +325,19 @@ struct GemmTile {
   int32_t item, m0, n0, cfg;
   int32_t k0, k1;       // inner-dimension range of this tile
   int32_t slot, part;   // split-K: output tile slot and this tile's part (slot < 0: no split)
-  int32_t nsplit, pad0;
+  int32_t nsplit, rpt;  // rpt: rows per thread of a row block (N <= 8 products)
   int64_t poff;         // split-K: first element of this slot's partials (nsplit parts of one tile)
 };
 constexpr int SPLIT_MAX = 8;
 
 enum { CFG_64 = 0, CFG_32 = 1, CFG_ROWS = 2, CFG_ROWS_DF = 3 };
 constexpr int BK = 16;
-constexpr int ROWS_PER_THREAD = 1, ROWS_PER_CTA = 256 * ROWS_PER_THREAD, ROWS_NMAX = 8, ROWS_KCHUNK = 256;
+constexpr int ROWS_NMAX = 8, ROWS_KCHUNK = 256;
+// Rows per thread of an N <= 8 row block over a long product (real data): four groups of four
+// loads and the accumulators stay within the three-CTAs-per-SM register budget.  Row blocks of
+// shorter products, and all complex ones, take one row per thread (more CTAs).  A row block
+// covers 256 x rpt rows.
+__host__ __device__ constexpr int rows_rpt(int nt) { return nt <= 2 ? 4 : nt <= 4 ? 2 : 1; }
 
 __device__ __forceinline__ double add(double a, double b) { return a + b; }
 __device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -432,28 +478,34 @@ __device__ __forceinline__ void gemm_tile(const GemmItem& it, const GemmTile& tl
   }
 }
 
-// Split-K epilogue shared by the row kernels: publish this part's 256 x N partial sums; the CTA
-// that completes the slot adds the parts in part order (deterministic) and writes C.
-template <typename T>
-__device__ __forceinline__ void rows_store(const GemmItem& it, const GemmTile& tl, const T* acc,
+// Split-K epilogue shared by the row kernels: publish this part's (256 RPT) x NT partial sums; the
+// CTA that completes the slot adds the parts in part order (deterministic) and writes C.  Thread
+// tid owns rows m0 + tid + 256 r, r < RPT.
+template <typename T, int NT, int RPT>
+__device__ __forceinline__ void rows_store(const GemmItem& it, const GemmTile& tl, const T (&acc)[RPT][NT],
                                            T* __restrict__ C, T* __restrict__ partials,
                                            int* __restrict__ counters) {
-  const int64_t M = it.M, N = it.N;
+  const int64_t M = it.M;
   const int tid = threadIdx.x;
-  const int64_t m = tl.m0 + tid;
   T* Cb = C + it.c_off;
   if (tl.slot < 0) {
-    if (m < M) {
 #pragma unroll
-      for (int j = 0; j < ROWS_NMAX; ++j)
-        if (j < N) Cb[m + j * M] = acc[j];
+    for (int r = 0; r < RPT; ++r) {
+      const int64_t m = (int64_t)tl.m0 + r * 256 + tid;
+      if (m < M) {
+#pragma unroll
+        for (int j = 0; j < NT; ++j) Cb[m + j * M] = acc[r][j];
+      }
     }
     return;
   }
+  constexpr int PS = 256 * RPT * NT;  // elements of one part
   __shared__ int s_last;
-  T* mine = partials + tl.poff + (int64_t)tl.part * (256 * ROWS_NMAX);
+  T* mine = partials + tl.poff + (int64_t)tl.part * PS;
 #pragma unroll
-  for (int j = 0; j < ROWS_NMAX; ++j) mine[tid + 256 * j] = acc[j];
+  for (int r = 0; r < RPT; ++r)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) mine[r * 256 + tid + 256 * RPT * j] = acc[r][j];
   __threadfence();
   __syncthreads();
   if (tid == 0) s_last = (atomicAdd(&counters[tl.slot], 1) == tl.nsplit - 1);
@@ -461,12 +513,14 @@ __device__ __forceinline__ void rows_store(const GemmItem& it, const GemmTile& t
   if (!s_last) return;
   __threadfence();
   const T* base = partials + tl.poff;
-  if (m < M) {
 #pragma unroll
-    for (int j = 0; j < ROWS_NMAX; ++j) {
-      if (j < N) {
+  for (int r = 0; r < RPT; ++r) {
+    const int64_t m = (int64_t)tl.m0 + r * 256 + tid;
+    if (m < M) {
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
         T v = Elem<T>::zero();
-        for (int p = 0; p < tl.nsplit; ++p) v = add(v, __ldcg(base + p * (256 * ROWS_NMAX) + tid + 256 * j));
+        for (int p = 0; p < tl.nsplit; ++p) v = add(v, __ldcg(base + p * PS + r * 256 + tid + 256 * RPT * j));
         Cb[m + j * M] = v;
       }
     }
@@ -474,23 +528,25 @@ __device__ __forceinline__ void rows_store(const GemmItem& it, const GemmTile& t
   if (tid == 0) counters[tl.slot] = 0;  // ready for the next launch
 }
 
-// N <= 8: thread t owns row m0 + t over the inner range [k0, k1); B streamed through shared
-// memory in K chunks.  The code is instantiated for each N (NT) and walks K in groups of four
-// (four independent loads in flight) plus a guarded tail, so every FP64 FMA issued is one of the
-// product's M K N: on GB300 the FP64 pipe, not memory, bounds these skinny products.
-template <typename T, int NT>
+// N <= 8 products (the skinny MPO steps): streams over A's rows.  Thread tid owns RPT rows
+// (m0 + tid + 256 r) and walks K in groups of four (4 RPT independent loads in flight) plus a
+// guarded tail; B is broadcast from shared memory in K chunks.  The code is instantiated for each
+// N (NT), so every FMA issued is one of the product's M K N.
+template <typename T, int NT, int RPT>
 __device__ __forceinline__ void gemm_rows_n(const GemmItem& it, const GemmTile& tl, const T* __restrict__ A,
                                             const T* __restrict__ B, T* __restrict__ C, T* smem,
                                             T* __restrict__ partials, int* __restrict__ counters) {
   T(*Bs)[NT] = reinterpret_cast<T(*)[NT]>(smem);
   const int64_t M = it.M, K = it.K;
   const int tid = threadIdx.x;
-  const int64_t m = tl.m0 + tid;
-  const bool live = m < M;
-  T acc[ROWS_NMAX];
+  bool live[RPT];
 #pragma unroll
-  for (int j = 0; j < ROWS_NMAX; ++j) acc[j] = Elem<T>::zero();
-  const T* Ab = A + it.a_off + (live ? m : 0);
+  for (int r = 0; r < RPT; ++r) live[r] = (int64_t)tl.m0 + r * 256 + tid < M;
+  T acc[RPT][NT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[r][j] = Elem<T>::zero();
   const T* Bb = B + it.b_off;
   for (int64_t k0 = tl.k0; k0 < tl.k1; k0 += ROWS_KCHUNK) {
     const int kmax = (int)((tl.k1 - k0) < ROWS_KCHUNK ? (tl.k1 - k0) : ROWS_KCHUNK);
@@ -499,54 +555,76 @@ __device__ __forceinline__ void gemm_rows_n(const GemmItem& it, const GemmTile& 
       Bs[kk][nn] = Bb[(k0 + kk) + nn * K];
     }
     __syncthreads();
-    const T* Ak = Ab + k0 * M;
+    const T* Ak = A + it.a_off + tl.m0 + tid + k0 * M;  // column k0 of this thread's first row
     int kk = 0;
-    for (; kk + 4 <= kmax; kk += 4) {
-      T a[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = live ? Ak[(int64_t)(kk + u) * M] : Elem<T>::zero();
+    for (; kk + 4 <= kmax; kk += 4, Ak += 4 * M) {
+      T a[4][RPT];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int j = 0; j < NT; ++j) Mac<T>::mac(acc[j], a[u], Bs[kk + u][j]);
+        for (int r = 0; r < RPT; ++r) a[u][r] = live[r] ? Ak[u * M + r * 256] : Elem<T>::zero();
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          const T b = Bs[kk + u][j];
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) Mac<T>::mac(acc[r][j], a[u][r], b);
+        }
     }
     if (kk < kmax) {  // 1..3 left; the branches are uniform over the block
-      T a[3];
-#pragma unroll
-      for (int u = 0; u < 3; ++u) a[u] = (live && kk + u < kmax) ? Ak[(int64_t)(kk + u) * M] : Elem<T>::zero();
+      const int left = kmax - kk;
+      T a[3][RPT];
 #pragma unroll
       for (int u = 0; u < 3; ++u)
-        if (kk + u < kmax) {
 #pragma unroll
-          for (int j = 0; j < NT; ++j) Mac<T>::mac(acc[j], a[u], Bs[kk + u][j]);
+        for (int r = 0; r < RPT; ++r) a[u][r] = (live[r] && u < left) ? Ak[u * M + r * 256] : Elem<T>::zero();
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        if (u < left) {
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            const T b = Bs[kk + u][j];
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) Mac<T>::mac(acc[r][j], a[u][r], b);
+          }
         }
     }
     __syncthreads();
   }
-  rows_store<T>(it, tl, acc, C, partials, counters);
+  rows_store<T, NT, RPT>(it, tl, acc, C, partials, counters);
 }
 
 template <typename T>
 __device__ __forceinline__ void gemm_rows(const GemmItem& it, const GemmTile& tl, const T* __restrict__ A,
                                           const T* __restrict__ B, T* __restrict__ C, T* smem,
                                           T* __restrict__ partials, int* __restrict__ counters) {
+  constexpr bool CX = sizeof(T) == 16;
+#define TK_ROWS_CASE(NT)                                                                                  \
+  if (CX || tl.rpt == 1)                                                                                  \
+    gemm_rows_n<T, NT, 1>(it, tl, A, B, C, smem, partials, counters);                                     \
+  else                                                                                                    \
+    gemm_rows_n<T, NT, CX ? 1 : rows_rpt(NT)>(it, tl, A, B, C, smem, partials, counters);
   switch (it.N) {
-    case 1: gemm_rows_n<T, 1>(it, tl, A, B, C, smem, partials, counters); break;
-    case 2: gemm_rows_n<T, 2>(it, tl, A, B, C, smem, partials, counters); break;
-    case 3: gemm_rows_n<T, 3>(it, tl, A, B, C, smem, partials, counters); break;
-    case 4: gemm_rows_n<T, 4>(it, tl, A, B, C, smem, partials, counters); break;
-    case 5: gemm_rows_n<T, 5>(it, tl, A, B, C, smem, partials, counters); break;
-    case 6: gemm_rows_n<T, 6>(it, tl, A, B, C, smem, partials, counters); break;
-    case 7: gemm_rows_n<T, 7>(it, tl, A, B, C, smem, partials, counters); break;
-    default: gemm_rows_n<T, 8>(it, tl, A, B, C, smem, partials, counters); break;
+    case 1: TK_ROWS_CASE(1) break;
+    case 2: TK_ROWS_CASE(2) break;
+    case 3: TK_ROWS_CASE(3) break;
+    case 4: TK_ROWS_CASE(4) break;
+    case 5: TK_ROWS_CASE(5) break;
+    case 6: TK_ROWS_CASE(6) break;
+    case 7: TK_ROWS_CASE(7) break;
+    default: TK_ROWS_CASE(8) break;
   }
+#undef TK_ROWS_CASE
 }
 
 // Split-precision mode only: the N <= 8 row kernel in double-float arithmetic (pairs of FP32
 // with error-free products and sums), ~2^-44 relative per term, on the FP32 pipe.
-// a = hi + lo to ~2^-53, by integer operations on the FP64 bit pattern: hi keeps the sign, the
-// exponent and the top 23 stored mantissa bits; lo is the remaining 29 bits converted to FP32.
-// Values outside the normal FP32 range take the conversion instructions.
+// a = hi + lo to within 2^-46 |a|, by integer operations on the FP64 bit pattern: hi keeps the
+// sign, the exponent and the top 23 stored mantissa bits; lo is the next 23 bits, formed as a
+// normal FP32 with those bits as its fraction minus the same number with a zero fraction (an
+// exact subtraction), so no conversion instruction runs.  Values outside the normal FP32 range
+// take the conversion instructions.
 __device__ __noinline__ void df_split_slow(double a, float& hi, float& lo) {
   hi = __double2float_rn(a);
   lo = __double2float_rn(a - (double)hi);
@@ -554,22 +632,22 @@ __device__ __noinline__ void df_split_slow(double a, float& hi, float& lo) {
 __device__ __forceinline__ void df_split(double a, float& hi, float& lo) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(a);
   const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex == 0) {  // zero or FP64 subnormal (far below FP32)
-    hi = 0.f;
-    lo = 0.f;
-    return;
-  }
   const int ef = ex - 1023 + 127;
-  if (ef <= 52 || ef >= 255) {  // lo's scale 2^(ex-1075) must be a normal FP32: rare, out of line
-    df_split_slow(a, hi, lo);
+  if ((unsigned int)(ef - 53) >= 202u) {  // lo's scale 2^(ex-1069) must be a normal FP32
+    if (ex == 0) {                        // zero or FP64 subnormal (far below FP32)
+      hi = 0.f;
+      lo = 0.f;
+    } else {
+      df_split_slow(a, hi, lo);           // rare, out of line
+    }
     return;
   }
   const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
   hi = __uint_as_float(sign | ((unsigned int)ef << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu));
-  const unsigned int low = (unsigned int)(b & 0x1FFFFFFFu);  // value low * 2^(ex-1075)
-  // low < 2^29: its FP32 rounding loses at most 2^-24 of lo, i.e. ~2^-53 of a
-  const float lf = __uint2float_rn(low);
-  lo = __fmul_rn(lf, __uint_as_float((unsigned int)(ef - 52) << 23)) * (sign ? -1.f : 1.f);
+  // mantissa bits 28..6 as t: lo = t 2^(ex-1069) = (1 + t 2^-23) 2^(ef-150) - 2^(ef-150)
+  const unsigned int e2 = (unsigned int)(ef - 23) << 23;
+  const float l = __fsub_rn(__uint_as_float(e2 | ((unsigned int)(b >> 6) & 0x7FFFFFu)), __uint_as_float(e2));
+  lo = __uint_as_float(__float_as_uint(l) ^ sign);
 }
 __device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
   // __fmul_rn / __fadd_rn are never contracted into FMAs, which keeps the transformations exact
@@ -582,7 +660,18 @@ __device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al,
   sl = __fadd_rn(sl, __fadd_rn(e, cross));
   sh = s;
 }
-template <int NT>
+template <int NT, int RPT>
+__device__ __forceinline__ void df_rows_group(float (&sh)[RPT][NT], float (&sl)[RPT][NT], const double (&a)[RPT],
+                                              const float* bh, const float* bl) {
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    float ah, al;
+    df_split(a[r], ah, al);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) df_mac(sh[r][j], sl[r][j], ah, al, bh[j], bl[j]);
+  }
+}
+template <int NT, int RPT>
 __device__ __forceinline__ void gemm_rows_df_n(const GemmItem& it, const GemmTile& tl, const double* __restrict__ A,
                                                const double* __restrict__ B, double* __restrict__ C,
                                                double* smem, double* __restrict__ partials,
@@ -591,12 +680,14 @@ __device__ __forceinline__ void gemm_rows_df_n(const GemmItem& it, const GemmTil
   float(*Bl)[NT] = reinterpret_cast<float(*)[NT]>(reinterpret_cast<float*>(smem) + ROWS_KCHUNK * NT);
   const int64_t M = it.M, K = it.K;
   const int tid = threadIdx.x;
-  const int64_t m = tl.m0 + tid;
-  const bool live = m < M;
-  float sh[NT], sl[NT];
+  bool live[RPT];
 #pragma unroll
-  for (int j = 0; j < NT; ++j) sh[j] = sl[j] = 0.f;
-  const double* Ab = A + it.a_off + (live ? m : 0);
+  for (int r = 0; r < RPT; ++r) live[r] = (int64_t)tl.m0 + r * 256 + tid < M;
+  float sh[RPT][NT], sl[RPT][NT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) sh[r][j] = sl[r][j] = 0.f;
   const double* Bb = B + it.b_off;
   for (int64_t k0 = tl.k0; k0 < tl.k1; k0 += ROWS_KCHUNK) {
     const int kmax = (int)((tl.k1 - k0) < ROWS_KCHUNK ? (tl.k1 - k0) : ROWS_KCHUNK);
@@ -608,47 +699,57 @@ __device__ __forceinline__ void gemm_rows_df_n(const GemmItem& it, const GemmTil
       Bl[kk][nn] = l;
     }
     __syncthreads();
-    const double* Ak = Ab + k0 * M;
+    const double* Ak = A + it.a_off + tl.m0 + tid + k0 * M;
     int kk = 0;
-    for (; kk + 4 <= kmax; kk += 4) {
-      double a[4];
+    for (; kk + 4 <= kmax; kk += 4, Ak += 4 * M) {
+      double a[4][RPT];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = live ? Ak[(int64_t)(kk + u) * M] : 0.0;
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        float ah, al;
-        df_split(a[u], ah, al);
+        for (int r = 0; r < RPT; ++r) a[u][r] = live[r] ? Ak[u * M + r * 256] : 0.0;
 #pragma unroll
-        for (int j = 0; j < NT; ++j) df_mac(sh[j], sl[j], ah, al, Bh[kk + u][j], Bl[kk + u][j]);
-      }
+      for (int u = 0; u < 4; ++u) df_rows_group<NT, RPT>(sh, sl, a[u], Bh[kk + u], Bl[kk + u]);
     }
-    for (; kk < kmax; ++kk) {
-      float ah, al;
-      df_split(live ? Ak[(int64_t)kk * M] : 0.0, ah, al);
+    if (kk < kmax) {  // 1..3 left; the branches are uniform over the block
+      const int left = kmax - kk;
+      double a[3][RPT];
 #pragma unroll
-      for (int j = 0; j < NT; ++j) df_mac(sh[j], sl[j], ah, al, Bh[kk][j], Bl[kk][j]);
+      for (int u = 0; u < 3; ++u)
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) a[u][r] = (live[r] && u < left) ? Ak[u * M + r * 256] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        if (u < left) df_rows_group<NT, RPT>(sh, sl, a[u], Bh[kk + u], Bl[kk + u]);
     }
     __syncthreads();
   }
-  double acc[ROWS_NMAX];
+  double acc[RPT][NT];
 #pragma unroll
-  for (int j = 0; j < ROWS_NMAX; ++j) acc[j] = j < NT ? f32_to_f64(sh[j]) + f32_to_f64(sl[j]) : 0.0;
-  rows_store<double>(it, tl, acc, C, partials, counters);
+  for (int r = 0; r < RPT; ++r)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[r][j] = f32_to_f64(sh[r][j]) + f32_to_f64(sl[r][j]);
+  rows_store<double, NT, RPT>(it, tl, acc, C, partials, counters);
 }
 
 __device__ __forceinline__ void gemm_rows_df(const GemmItem& it, const GemmTile& tl, const double* __restrict__ A,
                                              const double* __restrict__ B, double* __restrict__ C, double* smem,
                                              double* __restrict__ partials, int* __restrict__ counters) {
+#define TK_ROWS_DF_CASE(NT)                                                   \
+  if (tl.rpt == 1)                                                            \
+    gemm_rows_df_n<NT, 1>(it, tl, A, B, C, smem, partials, counters);         \
+  else                                                                        \
+    gemm_rows_df_n<NT, rows_rpt(NT)>(it, tl, A, B, C, smem, partials, counters);
   switch (it.N) {
-    case 1: gemm_rows_df_n<1>(it, tl, A, B, C, smem, partials, counters); break;
-    case 2: gemm_rows_df_n<2>(it, tl, A, B, C, smem, partials, counters); break;
-    case 3: gemm_rows_df_n<3>(it, tl, A, B, C, smem, partials, counters); break;
-    case 4: gemm_rows_df_n<4>(it, tl, A, B, C, smem, partials, counters); break;
-    case 5: gemm_rows_df_n<5>(it, tl, A, B, C, smem, partials, counters); break;
-    case 6: gemm_rows_df_n<6>(it, tl, A, B, C, smem, partials, counters); break;
-    case 7: gemm_rows_df_n<7>(it, tl, A, B, C, smem, partials, counters); break;
-    default: gemm_rows_df_n<8>(it, tl, A, B, C, smem, partials, counters); break;
+    case 1: TK_ROWS_DF_CASE(1) break;
+    case 2: TK_ROWS_DF_CASE(2) break;
+    case 3: TK_ROWS_DF_CASE(3) break;
+    case 4: TK_ROWS_DF_CASE(4) break;
+    case 5: TK_ROWS_DF_CASE(5) break;
+    case 6: TK_ROWS_DF_CASE(6) break;
+    case 7: TK_ROWS_DF_CASE(7) break;
+    default: TK_ROWS_DF_CASE(8) break;
   }
+#undef TK_ROWS_DF_CASE
 }
 
 template <typename T>
@@ -787,10 +888,9 @@ void perm_segments(const PermJob* jobs, int njobs, std::vector<PermSeg>& segs, s
       PermSeg g;
       std::memset(&g, 0, sizeof(g));
       g.kind = 1;
-      g.ntasks = (int32_t)pp.tasks.size();
       g.nwork = pp.total_tiles;
       g.tasks = pp.d_tasks;
-      g.tile_starts = pp.d_tile_starts;
+      g.tile_task = pp.d_tile_task;
       g.srcs = pp.d_srcs;
       g.in = jobs[j].in;
       g.out = jobs[j].out;
@@ -913,11 +1013,18 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
       gl.push_back(g);
     }
   }
+  // several rows per thread only where the product is long enough to give eight waves of
+  // one-row blocks at three CTAs per SM (fewer, longer-lived threads then lose nothing)
+  const bool cplx = cp.dtype == TK_C128;
+  auto rows_per_thread = [&](const GemmItem& g) {
+    return (!cplx && (g.M + 255) / 256 >= 8 * 3 * sms) ? rows_rpt((int)g.N) : 1;
+  };
+  auto rows_block = [&](const GemmItem& g) { return (int64_t)256 * rows_per_thread(g); };
   int64_t rows_ctas = 0;
   tiles64 = tiles32 = 0;
   for (const GemmItem& g : gl) {
     if (g.N <= ROWS_NMAX)
-      rows_ctas += (g.M + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
+      rows_ctas += (g.M + rows_block(g) - 1) / rows_block(g);
     else
       (use64 ? tiles64 : tiles32) += ((g.M + bm - 1) / bm) * ((g.N + bm - 1) / bm);
   }
@@ -935,7 +1042,7 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
   std::vector<Cand> cands;
   // one output tile as nsplit parts over [0, K), each part's depth a multiple of kalign
   auto emit = [&](int32_t item, int64_t m0, int64_t n0, int32_t cfg, int64_t K, int nsplit, int kalign,
-                  int64_t part_elems, double area) {
+                  int64_t part_elems, double area, int rpt) {
     const int32_t slot = nsplit > 1 ? nslots++ : -1;
     const int64_t kstep = ((K + nsplit - 1) / nsplit + kalign - 1) / kalign * kalign;
     for (int p = 0; p < nsplit; ++p) {
@@ -951,6 +1058,7 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
       t.slot = slot;
       t.part = p;
       t.nsplit = nsplit;
+      t.rpt = rpt;
       t.poff = nsplit > 1 ? poff : 0;
       cands.push_back({t, area * (double)(k1 - k0)});
     }
@@ -961,15 +1069,16 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
     if (g.N <= ROWS_NMAX) {
       const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want_rows, (int64_t)SPLIT_MAX, g.K / 32}));
       const int32_t cfg = cp.gemm_mode == TK_GEMM_FP64 ? CFG_ROWS : CFG_ROWS_DF;
-      for (int64_t m0 = 0; m0 < g.M; m0 += ROWS_PER_CTA)
-        emit((int32_t)i, m0, 0, cfg, g.K, nsplit, 8, 256 * ROWS_NMAX,
-             (double)std::min<int64_t>(ROWS_PER_CTA, g.M - m0) * g.N);
+      const int rpt = rows_per_thread(g);
+      const int64_t rb = 256 * rpt;
+      for (int64_t m0 = 0; m0 < g.M; m0 += rb)
+        emit((int32_t)i, m0, 0, cfg, g.K, nsplit, 8, rb * g.N, (double)std::min<int64_t>(rb, g.M - m0) * g.N, rpt);
       continue;
     }
     const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want_tiles, (int64_t)SPLIT_MAX, g.K / 64}));
     for (int64_t n0 = 0; n0 < g.N; n0 += bm)
       for (int64_t m0 = 0; m0 < g.M; m0 += bm)
-        emit((int32_t)i, m0, n0, use64 ? CFG_64 : CFG_32, g.K, nsplit, BK, (int64_t)bm * bm, (double)bm * bm);
+        emit((int32_t)i, m0, n0, use64 ? CFG_64 : CFG_32, g.K, nsplit, BK, (int64_t)bm * bm, (double)bm * bm, 1);
   }
   cp.split_slots = nslots;
   // Row blocks first (they are latency-bound: a serial walk over K), then tiles by cost, largest

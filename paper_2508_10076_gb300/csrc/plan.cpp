@@ -321,11 +321,23 @@ static void emit_task(PermutePlan& pp, PermTask t, std::vector<int64_t>& ext, st
     }
     return;
   }
+  // a short leading dim (2..4 elements, e.g. an MPO leg) contiguous on both sides, followed by
+  // dim 1 in the destination and by some dim vd in the source: transpose vectors of that length
+  int vd = -1;
+  if (t.ndim >= 3 && t.ostr[0] == 1 && t.irs[0] == 1 && t.ics[0] == 0 && t.ext[0] >= 2 && t.ext[0] <= 4 &&
+      t.ostr[1] == t.ext[0])
+    for (int k = 2; k < t.ndim; ++k)
+      if (t.irs[k] == t.ext[0] && t.ics[k] == 0) vd = k;
   if (t.ostr[0] == 1 && tdim > 0 && t.ext[0] >= 4 && t.ext[tdim] >= 4) {
     t.mode = 1;
     t.tdim = tdim;
     t.t0 = 32;
     t.t1 = 32;
+  } else if (vd > 0) {
+    t.mode = 3;
+    t.tdim = vd;
+    t.t0 = 16;
+    t.t1 = 16;
   } else {
     t.mode = 2;
   }
@@ -342,6 +354,9 @@ static void finish_tiles(PermutePlan& pp) {
     if (t.mode == 1) {
       int64_t outer = total / ((int64_t)t.ext[0] * t.ext[t.tdim]);
       acc += ((t.ext[0] + 31) / 32) * (int64_t)((t.ext[t.tdim] + 31) / 32) * outer;
+    } else if (t.mode == 3) {
+      int64_t outer = total / ((int64_t)t.ext[0] * t.ext[1] * t.ext[t.tdim]);
+      acc += ((t.ext[1] + 15) / 16) * (int64_t)((t.ext[t.tdim] + 15) / 16) * outer;
     } else {
       acc += (total + 255) / 256;
     }
@@ -361,7 +376,6 @@ static void build_tasks(PermutePlan& pp) {
   pp.runs.clear();
   pp.srcs.clear();
   double bytes = 0;
-  const double esize = pp.dtype == TK_C128 ? 16.0 : 8.0;
   std::vector<int64_t> od, idims;
   size_t ti = 0;
   for (int64_t y = 0; y < (int64_t)out.pairs.size(); ++y) {
@@ -428,12 +442,16 @@ static void build_tasks(PermutePlan& pp) {
 
 static void upload_permute_tables(Ctx* ctx, PermutePlan& pp) {
   if (!ctx || ctx->device < 0 || (pp.tasks.empty() && pp.runs.empty())) return;
-  std::vector<int64_t> starts;
-  for (auto& t : pp.tasks) starts.push_back(t.tile_begin);
+  std::vector<int32_t> owner((size_t)pp.total_tiles);
+  for (size_t i = 0; i < pp.tasks.size(); ++i) {
+    const int64_t end = i + 1 < pp.tasks.size() ? pp.tasks[i + 1].tile_begin : pp.total_tiles;
+    for (int64_t k = pp.tasks[i].tile_begin; k < end; ++k) owner[(size_t)k] = (int32_t)i;
+  }
   int rc = TK_OK;
   if (!pp.tasks.empty()) {
     rc = dev_upload(ctx, (void**)&pp.d_tasks, pp.tasks.data(), pp.tasks.size() * sizeof(PermTask));
-    if (rc == TK_OK) rc = dev_upload(ctx, (void**)&pp.d_tile_starts, starts.data(), starts.size() * sizeof(int64_t));
+    if (rc == TK_OK && !owner.empty())
+      rc = dev_upload(ctx, (void**)&pp.d_tile_task, owner.data(), owner.size() * sizeof(int32_t));
   }
   if (rc == TK_OK && !pp.rtasks.empty())
     rc = dev_upload(ctx, (void**)&pp.d_rtasks, pp.rtasks.data(), pp.rtasks.size() * sizeof(PermTask));

@@ -23,18 +23,19 @@ static __device__ __noinline__ double f32_to_f64_rare(float f) {
       (long long)(sign | ((unsigned long long)(p + 874) << 52) | (((unsigned long long)man << (52 - p)) & 0xFFFFFFFFFFFFFull)));
 }
 
-// Exact FP32 -> FP64 by assembling the bit pattern with integer operations (the FP64 pipe is
-// scarce on this part); zeros and normal numbers inline, everything else out of line.
+// Exact FP32 -> FP64 by assembling the bit pattern with 32-bit integer operations (the FP64 pipe
+// is scarce on this part); zeros and normal numbers inline, everything else out of line.  For a
+// normal value the high word is the sign, then exponent and fraction shifted right by 3 with the
+// exponent bias raised by 1023 - 127 = 896; the low word holds the fraction's last 3 bits.
 static __device__ __forceinline__ double f32_to_f64(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t ex = (u >> 23) & 0xFFu;
   if (ex - 1u >= 0xFEu) {  // exponent field 0 or 255
-    if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)(u >> 31) << 63));  // +-0
+    if ((u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);  // +-0
     return f32_to_f64_rare(f);
   }
-  return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
-                                          ((unsigned long long)(ex + 896u) << 52) |
-                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+  const uint32_t hi = (u & 0x80000000u) | (((u & 0x7FFFFFFFu) >> 3) + (896u << 20));
+  return __hiloint2double((int)hi, (int)(u << 29));
 }
 
 }  // namespace tk

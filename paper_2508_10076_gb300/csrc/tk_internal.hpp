@@ -102,8 +102,10 @@ struct PermTask {
   int32_t irs[6];        // source stride = irs + ics * ld_src
   int32_t ics[6];
   int32_t ndim;
-  int32_t mode;          // 0: shared contiguous dim 0; 1: transpose dims (0, tdim); 2: generic
-  int32_t tdim;          // mode 1: the dim that is contiguous in the source
+  int32_t mode;          // 0: shared contiguous dim 0; 1: transpose dims (0, tdim); 2: generic;
+                         // 3: transpose dims (1, tdim) of vectors along a short dim 0
+  int32_t tdim;          // mode 1: the dim that is contiguous in the source; mode 3: the dim
+                         // that follows dim 0 in the source
   int32_t src_begin, nsrc;
   int32_t t0, t1;        // tile extents along dim 0 and along the tiled second axis
   int32_t conj;          // 1: conjugate complex values (adjoint)
@@ -137,7 +139,7 @@ struct PermutePlan {
   PermTask* d_rtasks = nullptr;
   PermRun* d_runs = nullptr;
   PermSrc* d_srcs = nullptr;
-  int64_t* d_tile_starts = nullptr;
+  int32_t* d_tile_task = nullptr;  // owning task of every tile
   ~PermutePlan();
 };
 

@@ -93,6 +93,40 @@ def test_permute_parity(gctx, case, dtype):
             assert np.array_equal(got, ref), (p, q)
 
 
+VECTOR_TRANSPOSE_CASES = [
+    # R-like environments (MPO leg of extent 2-4 leading on both sides, then two virtual legs
+    # swapped): short-vector transpose tiles with ragged edges
+    ("U1", ([({-2: 2, 0: 3, 2: 4}, False), ({-1: 37, 0: 50, 1: 41}, True)], [({-1: 19, 0: 50, 1: 33}, True)])),
+    ("SU2", ([({0: 2, 2: 3}, False), ({1: 17, 3: 20, 5: 9}, True)], [({1: 17, 3: 20, 5: 9}, True)])),
+]
+
+
+@pytest.mark.parametrize("case", range(len(VECTOR_TRANSPOSE_CASES)))
+@pytest.mark.parametrize("dtype", ["f64", "c128"])
+def test_short_vector_transpose(gctx, case, dtype):
+    """Permute (0, 2) <- (1,) of an R-like tensor: the short MPO leg moves as a vector while the
+    virtual legs are transposed; every element against the oracle."""
+    api = _api()
+    sym, legs = VECTOR_TRANSPOSE_CASES[case]
+    ost = ostruct(sym, legs)
+    lt = _lib_tmap(gctx, sym, legs)
+    x = wl.normal_complex(40 + case, ost.numel) if dtype == "c128" else wl.normal(40 + case, ost.numel)
+    os_, ref = ops.permute_block(ost, x, (0, 2), (1,))
+    plan = api.permute_plan(gctx, lt, (0, 2), (1,), dtype=dtype)
+    st = plan.permute_stats(0)
+    assert st["transpose_tasks"] > 0 and st["generic_elems"] < st["transpose_elems"]
+    assert plan.output().blocks() == [(c, r, k, o) for c, r, k, o in os_.blocks]
+    yd = torch.full((plan.output().numel,), float("nan"), dtype=torch.complex128 if dtype == "c128" else torch.float64,
+                    device="cuda")
+    api.permute(gctx, plan, _dev(x), yd)
+    gctx.sync()
+    got = yd.cpu().numpy()
+    if sym == "SU2":
+        assert np.allclose(got, ref, rtol=1e-13, atol=1e-13)
+    else:
+        assert np.array_equal(got, ref)
+
+
 def test_c0_contraction_fp64(gctx):
     api = _api()
     v = {-2: 1, -1: 2, 0: 3, 1: 2, 2: 1}
@@ -281,3 +315,24 @@ def test_adjoint_parity(gctx, dtype):
         _, blk = ops.adjoint(ost, x, tier="block")
         assert np.array_equal(y.cpu().numpy(), blk)
         assert np.allclose(y.cpu().numpy(), ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("gemm,tol", [("fp64", FP64_TOL), ("ozaki", 1e-10), ("tf32x3", 1e-10)])
+def test_long_skinny_products(gctx, gemm, tol):
+    """MPO-like products with N <= 8 over about a million rows (the shape of the heff chain's
+    T.W steps at D = 4096): row blocks with several rows per thread, ragged last blocks, and inner
+    dimensions 4 (full groups) and 7 (a group plus a tail).  The skinny products run in FP64 or in
+    double-float in every mode, so all modes meet the FP64-class bound."""
+    api = _api()
+    la = ([({0: 1_000_003, 1: 950_001}, False)], [({0: 4, 1: 7}, False)])
+    lb = ([({0: 4, 1: 7}, False)], [({0: 2, 1: 3}, False)])
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    xa, xb = wl.normal(21, oa.numel), wl.normal(22, ob.numel)
+    cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
+    A, B = _lib_tmap(gctx, "U1", la), _lib_tmap(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), gemm=gemm)
+    ws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
+    c = torch.full((plan.output().numel,), float("nan"), dtype=torch.float64, device="cuda")
+    api.contract(gctx, plan, _dev(xa), _dev(xb), c, ws)
+    gctx.sync()
+    assert rel_frobenius_per_block(cs, c.cpu().numpy(), ref) <= tol

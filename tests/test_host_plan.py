@@ -192,3 +192,19 @@ def test_svd_plan_structures_match_oracle(hctx):
         assert u.blocks() == [(c, r, k, o) for c, r, k, o in ou.blocks]
         assert vh.blocks() == [(c, r, k, o) for c, r, k, o in ov.blocks]
         assert n == sum(min(r, k) for _, r, k, _ in ost.blocks)
+
+
+def test_mpo_leg_permute_uses_vector_tiles(hctx):
+    """An environment R : W (x) V' <- V' permuted to (W, V'_dom) <- V'_cod (the T3.R step of the
+    heff chain): the MPO leg (extent 1-4 per sector) is contiguous on both sides, so every task is
+    a transpose of short vectors, none element-wise."""
+    legs = ([({-2: 2, 0: 3, 2: 4}, False), ({-1: 37, 0: 50, 1: 41}, True)], [({-1: 19, 0: 50, 1: 33}, True)])
+    cod, dom = legs
+    t = hctx.tmap([hctx.space("U1", s, d) for s, d in cod], [hctx.space("U1", s, d) for s, d in dom])
+    p = api.permute_plan(hctx, t, (0, 2), (1,))
+    st = p.permute_stats(0)
+    assert st["generic_tasks"] == 0 and st["run_tasks"] == 0
+    assert st["transpose_elems"] == t.numel
+    ost = TensorStructure([GradedSpace(U1, s, d) for s, d in cod], [GradedSpace(U1, s, d) for s, d in dom])
+    out, _ = _oracle_transform_offsets(ost, (0, 2), (1,))
+    _same_structure(out, p.output())
