@@ -649,54 +649,60 @@ __device__ __forceinline__ void df_split(double a, float& hi, float& lo) {
   const float l = __fsub_rn(__uint_as_float(e2 | ((unsigned int)(b >> 6) & 0x7FFFFFu)), __uint_as_float(e2));
   lo = __uint_as_float(__float_as_uint(l) ^ sign);
 }
-__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
-  // __fmul_rn / __fadd_rn are never contracted into FMAs, which keeps the transformations exact
-  const float p = __fmul_rn(ah, bh);
-  const float pe = fmaf(ah, bh, -p);                 // exact error of ah*bh
-  const float cross = fmaf(ah, bl, fmaf(al, bh, pe));
-  const float s = __fadd_rn(sh, p);                  // two-sum of sh + p
-  const float bb = __fsub_rn(s, sh);
-  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  sl = __fadd_rn(sl, __fadd_rn(e, cross));
+// Double-float multiply-add on two output columns at once with the packed FP32 pair instructions
+// (one instruction per pair): (sh, sl) += a * b, a = ah + al, b = bh + bl; no operation is
+// contracted.
+__device__ __forceinline__ void df_mac2(float2& sh, float2& sl, float ah, float al, float2 bh, float2 bl) {
+  const float2 a2 = make_float2(ah, ah), l2 = make_float2(al, al);
+  const float2 p = __fmul2_rn(a2, bh);
+  const float2 pe = __ffma2_rn(a2, bh, make_float2(-p.x, -p.y));  // exact error of ah*bh
+  const float2 cross = __ffma2_rn(a2, bl, __ffma2_rn(l2, bh, pe));
+  float2 s, e;
+  two_sum2(sh, p, s, e);
+  sl = __fadd2_rn(sl, __fadd2_rn(e, cross));
   sh = s;
 }
-template <int NT, int RPT>
-__device__ __forceinline__ void df_rows_group(float (&sh)[RPT][NT], float (&sl)[RPT][NT], const double (&a)[RPT],
-                                              const float* bh, const float* bl) {
+template <int NP, int RPT>
+__device__ __forceinline__ void df_rows_group(float2 (&sh)[RPT][NP], float2 (&sl)[RPT][NP], const double (&a)[RPT],
+                                              const float2* bh, const float2* bl) {
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     float ah, al;
     df_split(a[r], ah, al);
 #pragma unroll
-    for (int j = 0; j < NT; ++j) df_mac(sh[r][j], sl[r][j], ah, al, bh[j], bl[j]);
+    for (int q = 0; q < NP; ++q) df_mac2(sh[r][q], sl[r][q], ah, al, bh[q], bl[q]);
   }
 }
+// Columns are processed in pairs (NP = ceil(NT / 2)); for odd NT the last pair's second column
+// multiplies a zero B column and is not stored.
 template <int NT, int RPT>
 __device__ __forceinline__ void gemm_rows_df_n(const GemmItem& it, const GemmTile& tl, const double* __restrict__ A,
                                                const double* __restrict__ B, double* __restrict__ C,
                                                double* smem, double* __restrict__ partials,
                                                int* __restrict__ counters) {
-  float(*Bh)[NT] = reinterpret_cast<float(*)[NT]>(smem);
-  float(*Bl)[NT] = reinterpret_cast<float(*)[NT]>(reinterpret_cast<float*>(smem) + ROWS_KCHUNK * NT);
+  constexpr int NP = (NT + 1) / 2;
+  float2(*Bh)[NP] = reinterpret_cast<float2(*)[NP]>(smem);
+  float2(*Bl)[NP] = reinterpret_cast<float2(*)[NP]>(reinterpret_cast<float2*>(smem) + ROWS_KCHUNK * NP);
   const int64_t M = it.M, K = it.K;
   const int tid = threadIdx.x;
   bool live[RPT];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) live[r] = (int64_t)tl.m0 + r * 256 + tid < M;
-  float sh[RPT][NT], sl[RPT][NT];
+  float2 sh[RPT][NP], sl[RPT][NP];
 #pragma unroll
   for (int r = 0; r < RPT; ++r)
 #pragma unroll
-    for (int j = 0; j < NT; ++j) sh[r][j] = sl[r][j] = 0.f;
+    for (int q = 0; q < NP; ++q) sh[r][q] = sl[r][q] = make_float2(0.f, 0.f);
   const double* Bb = B + it.b_off;
   for (int64_t k0 = tl.k0; k0 < tl.k1; k0 += ROWS_KCHUNK) {
     const int kmax = (int)((tl.k1 - k0) < ROWS_KCHUNK ? (tl.k1 - k0) : ROWS_KCHUNK);
-    for (int e = tid; e < kmax * NT; e += 256) {
-      const int kk = e % kmax, nn = e / kmax;
-      float h, l;
-      df_split(Bb[(k0 + kk) + nn * K], h, l);
-      Bh[kk][nn] = h;
-      Bl[kk][nn] = l;
+    for (int e = tid; e < kmax * NP; e += 256) {
+      const int kk = e % kmax, q = e / kmax;
+      float h0, l0, h1 = 0.f, l1 = 0.f;
+      df_split(Bb[(k0 + kk) + (2 * q) * K], h0, l0);
+      if (2 * q + 1 < NT) df_split(Bb[(k0 + kk) + (2 * q + 1) * K], h1, l1);
+      Bh[kk][q] = make_float2(h0, h1);
+      Bl[kk][q] = make_float2(l0, l1);
     }
     __syncthreads();
     const double* Ak = A + it.a_off + tl.m0 + tid + k0 * M;
@@ -708,7 +714,7 @@ __device__ __forceinline__ void gemm_rows_df_n(const GemmItem& it, const GemmTil
 #pragma unroll
         for (int r = 0; r < RPT; ++r) a[u][r] = live[r] ? Ak[u * M + r * 256] : 0.0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) df_rows_group<NT, RPT>(sh, sl, a[u], Bh[kk + u], Bl[kk + u]);
+      for (int u = 0; u < 4; ++u) df_rows_group<NP, RPT>(sh, sl, a[u], Bh[kk + u], Bl[kk + u]);
     }
     if (kk < kmax) {  // 1..3 left; the branches are uniform over the block
       const int left = kmax - kk;
@@ -719,7 +725,7 @@ __device__ __forceinline__ void gemm_rows_df_n(const GemmItem& it, const GemmTil
         for (int r = 0; r < RPT; ++r) a[u][r] = (live[r] && u < left) ? Ak[u * M + r * 256] : 0.0;
 #pragma unroll
       for (int u = 0; u < 3; ++u)
-        if (u < left) df_rows_group<NT, RPT>(sh, sl, a[u], Bh[kk + u], Bl[kk + u]);
+        if (u < left) df_rows_group<NP, RPT>(sh, sl, a[u], Bh[kk + u], Bl[kk + u]);
     }
     __syncthreads();
   }
@@ -727,7 +733,10 @@ __device__ __forceinline__ void gemm_rows_df_n(const GemmItem& it, const GemmTil
 #pragma unroll
   for (int r = 0; r < RPT; ++r)
 #pragma unroll
-    for (int j = 0; j < NT; ++j) acc[r][j] = f32_to_f64(sh[r][j]) + f32_to_f64(sl[r][j]);
+    for (int j = 0; j < NT; ++j) {
+      const float2 h = sh[r][j / 2], l = sl[r][j / 2];
+      acc[r][j] = (j & 1) ? f32_to_f64(h.y) + f32_to_f64(l.y) : f32_to_f64(h.x) + f32_to_f64(l.x);
+    }
   rows_store<double, NT, RPT>(it, tl, acc, C, partials, counters);
 }
 
@@ -1000,6 +1009,19 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
   std::vector<GemmItem> gl;
   gl.reserve(cp.gemms_fp64.size() * 2);
   for (const GemmItem& g : cp.gemms_fp64) {
+    if (cp.gemm_mode != TK_GEMM_FP64 && g.N > ROWS_NMAX) {
+      // split-precision modes: the thin products left to this kernel run in double-float as
+      // row blocks of at most ROWS_NMAX columns (B and C are column-major: a column range is a
+      // contiguous sub-matrix with the same leading dimension)
+      for (int64_t n0 = 0; n0 < g.N; n0 += ROWS_NMAX) {
+        GemmItem part = g;
+        part.N = std::min<int64_t>(ROWS_NMAX, g.N - n0);
+        part.b_off = g.b_off + n0 * g.K;
+        part.c_off = g.c_off + n0 * g.M;
+        gl.push_back(part);
+      }
+      continue;
+    }
     const int64_t rem = g.N % bm;
     if (g.N > bm && rem > 0 && rem <= ROWS_NMAX) {
       GemmItem main = g, tail = g;
@@ -1043,8 +1065,9 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
   // one output tile as nsplit parts over [0, K), each part's depth a multiple of kalign
   auto emit = [&](int32_t item, int64_t m0, int64_t n0, int32_t cfg, int64_t K, int nsplit, int kalign,
                   int64_t part_elems, double area, int rpt) {
-    const int32_t slot = nsplit > 1 ? nslots++ : -1;
     const int64_t kstep = ((K + nsplit - 1) / nsplit + kalign - 1) / kalign * kalign;
+    nsplit = (int)std::max<int64_t>(1, (K + kstep - 1) / kstep);  // no empty parts after rounding
+    const int32_t slot = nsplit > 1 ? nslots++ : -1;
     for (int p = 0; p < nsplit; ++p) {
       const int64_t k0 = std::min<int64_t>(K, p * kstep), k1 = std::min<int64_t>(K, k0 + kstep);
       GemmTile t;
@@ -1067,7 +1090,7 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
   for (size_t i = 0; i < gl.size(); ++i) {
     const GemmItem& g = gl[i];
     if (g.N <= ROWS_NMAX) {
-      const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want_rows, (int64_t)SPLIT_MAX, g.K / 32}));
+      const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want_rows, (int64_t)SPLIT_MAX, g.K / 8}));
       const int32_t cfg = cp.gemm_mode == TK_GEMM_FP64 ? CFG_ROWS : CFG_ROWS_DF;
       const int rpt = rows_per_thread(g);
       const int64_t rb = 256 * rpt;

@@ -100,6 +100,9 @@ struct OzLayout {
   OzWork* d_work = nullptr;
   OzJob* d_slice_jobs = nullptr;
   OzJob* d_scale_jobs = nullptr;
+  std::vector<int32_t> cta_work;   // work of CTA b: work[cta_work[b] .. cta_work[b + 1])
+  int32_t* d_cta_work = nullptr;
+  int ncta = 0;
   int32_t nslots = 0;        // split tiles
   size_t off_part = 0;       // their partial tiles in the workspace
   size_t off_cnt = 0;        // per (split tile, epilogue warp) arrival counters in the workspace
@@ -542,8 +545,8 @@ __device__ __forceinline__ void oz_issue(int s, uint32_t acc0, uint32_t sbase, u
 template <int BN, int MODE>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
-              const OzSector* __restrict__ secs, const OzWork* __restrict__ work, int nwork,
-              const __grid_constant__ OzPairs pairs, int nslices, const int32_t* __restrict__ scale_a,
+              const OzSector* __restrict__ secs, const OzWork* __restrict__ work,
+              const int32_t* __restrict__ cta_work, const __grid_constant__ OzPairs pairs, int nslices, const int32_t* __restrict__ scale_a,
               const int32_t* __restrict__ scale_b, double* __restrict__ C, double* __restrict__ partials,
               int* __restrict__ counters, int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char dyn[];
@@ -558,6 +561,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   OzSmem* ss = reinterpret_cast<OzSmem*>(base + nstages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort_flag = &ss->abort_flag;
+  const int w_begin = cta_work[blockIdx.x], w_end = cta_work[blockIdx.x + 1];  // this CTA's work items
 
   if (threadIdx.x == 0) {
     for (uint32_t s = 0; s < nstages; ++s) {
@@ -586,7 +590,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
       uint32_t it = 0;
-      for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
+      for (int w = w_begin; w < w_end && !*abort_flag; ++w) {
         const OzWork wk = work[w];
         const OzSector s = secs[wk.sector];
         // slice tiles hold 128 rows; this item's B box is part nt % SUB of tile nt / SUB
@@ -616,7 +620,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       uint32_t it = 0, seg = 0;
-      for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
+      for (int w = w_begin; w < w_end && !*abort_flag; ++w) {
         const OzWork wk = work[w];
         const uint32_t idesc = idesc_mma<MODE>(OZ_BM, wk.nw);
         for (int kc0 = wk.kc_lo; kc0 < wk.kc_hi && !*abort_flag; kc0 += OZ_SEG_KC, ++seg) {
@@ -649,7 +653,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // accumulators of levels without any slice pair (fewer than 4 slices) are never written
     const bool has1 = pairs.first[1] >= 0, has2 = pairs.first[2] >= 0, has3 = pairs.first[3] >= 0;
     uint32_t seg = 0;
-    for (int w = blockIdx.x; w < nwork && !*abort_flag; w += gridDim.x) {
+    for (int w = w_begin; w < w_end && !*abort_flag; ++w) {
       const OzWork wk = work[w];
       const OzSector s = secs[wk.sector];
       const int c0 = grp * WCOLS;                 // first column of this warp within the tile
@@ -688,20 +692,33 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             tc_ld8(lane_addr + 2 * BN + ch * 8, r2);
             tc_ld8(lane_addr + 3 * BN + ch * 8, r3);
             tc_wait_ld();
+            // level sums, two columns per instruction: hi + lo = r0 + r1 + r2 (exact levels, the
+            // FP32 rounding of the last two-sum kept in lo) with the inexact level r3 added to lo
+            float hv[8], lv[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float2 z = make_float2(0.f, 0.f);
+              const float2 x0 = make_float2(__uint_as_float(r0[2 * q]), __uint_as_float(r0[2 * q + 1]));
+              const float2 x1 = has1 ? make_float2(__uint_as_float(r1[2 * q]), __uint_as_float(r1[2 * q + 1])) : z;
+              const float2 x2 = has2 ? make_float2(__uint_as_float(r2[2 * q]), __uint_as_float(r2[2 * q + 1])) : z;
+              const float2 x3 = has3 ? make_float2(__uint_as_float(r3[2 * q]), __uint_as_float(r3[2 * q + 1])) : z;
+              float2 hi, lo, e1, e2;
+              two_sum2(x0, x1, hi, lo);
+              two_sum2(hi, x2, hi, e1);
+              lo = __fadd2_rn(lo, e1);
+              two_sum2(hi, lo, hi, e2);
+              lo = __fadd2_rn(e2, x3);
+              hv[2 * q] = hi.x;
+              hv[2 * q + 1] = hi.y;
+              lv[2 * q] = lo.x;
+              lv[2 * q + 1] = lo.y;
+            }
             double* dst = crow + (int64_t)(ch * 8) * ld;
 #pragma unroll
             for (int j = 0; j < 8; ++j, dst += ld) {
               const int fn = __shfl_sync(0xffffffffu, fl, ch * 8 + j);
               if (!row_ok || ch * 8 + j >= ncols) continue;
-              float hi, lo, e1, e2;
-              const float a1 = has1 ? __uint_as_float(r1[j]) : 0.f;
-              const float a2 = has2 ? __uint_as_float(r2[j]) : 0.f;
-              const float a3 = has3 ? __uint_as_float(r3[j]) : 0.f;
-              two_sum(__uint_as_float(r0[j]), a1, hi, lo);
-              two_sum(hi, a2, hi, e1);
-              lo = __fadd_rn(lo, e1);
-              two_sum(hi, lo, hi, e2);
-              lo = __fadd_rn(e2, a3);
+              const float hi = hv[j], lo = lv[j];
               bool ok = true;
               const int sc = em + fn;
               double v = f32_scaled_to_f64(hi, sc, ok) + f32_scaled_to_f64(lo, sc, ok);
@@ -909,6 +926,45 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
     }
   }
   L->nslots = nslots;
+  // Static schedule: items go, longest first, to the CTA with the least work so far (LPT), the
+  // cost being the item's MMAs at max(48, N/2) cycles each (a 128 x N x K-step MMA is bound by
+  // shared-memory operand reads below N = 96) plus its epilogues.  Each CTA then runs its items
+  // in that order, so at any time the CTAs work on items of similar rank (L2 reuse of slices).
+  {
+    const int mmas = L->pairs.n * (L->mode == 0 ? OzMode<0>::MMAS : OzMode<1>::MMAS);
+    const int ncta = (int)std::min<int64_t>((int64_t)work.size(), sms);
+    std::vector<std::pair<double, int>> cost;
+    cost.reserve(work.size());
+    for (size_t k = 0; k < work.size(); ++k) {
+      const OzWork& x = work[k];
+      const int nkc = x.kc_hi - x.kc_lo, nseg = (nkc + OZ_SEG_KC - 1) / OZ_SEG_KC;
+      cost.push_back({(double)nkc * mmas * std::max(48.0, x.nw / 2.0) + 50.0 * x.nw * nseg, (int)k});
+    }
+    std::stable_sort(cost.begin(), cost.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<std::vector<int>> lists((size_t)ncta);
+    std::vector<std::pair<double, int>> heap;  // (load, cta), a min-heap
+    for (int b = 0; b < ncta; ++b) heap.push_back({0.0, b});
+    auto later = [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+      return a.first != b.first ? a.first > b.first : a.second > b.second;
+    };
+    std::make_heap(heap.begin(), heap.end(), later);
+    for (const auto& c : cost) {
+      std::pop_heap(heap.begin(), heap.end(), later);
+      heap.back().first += c.first;
+      lists[(size_t)heap.back().second].push_back(c.second);
+      std::push_heap(heap.begin(), heap.end(), later);
+    }
+    std::vector<OzWork> ordered;
+    ordered.reserve(work.size());
+    L->cta_work.assign((size_t)ncta + 1, 0);
+    for (int b = 0; b < ncta; ++b) {
+      L->cta_work[(size_t)b] = (int32_t)ordered.size();
+      for (int k : lists[(size_t)b]) ordered.push_back(work[(size_t)k]);
+    }
+    L->cta_work[(size_t)ncta] = (int32_t)ordered.size();
+    L->ncta = ncta;
+    work.swap(ordered);
+  }
   L->nwork = (int64_t)work.size();
   L->nslice_jobs = (int64_t)slice_jobs.size();
   L->nscale_jobs = (int64_t)scale_jobs.size();
@@ -925,10 +981,11 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
     if ((rc = dev_upload(ctx, (void**)&L->d_sectors, L->sectors.data(), L->sectors.size() * sizeof(OzSector))) != TK_OK ||
         (rc = dev_upload(ctx, (void**)&L->d_work, work.data(), work.size() * sizeof(OzWork))) != TK_OK ||
         (rc = dev_upload(ctx, (void**)&L->d_slice_jobs, slice_jobs.data(), slice_jobs.size() * sizeof(OzJob))) != TK_OK ||
-        (rc = dev_upload(ctx, (void**)&L->d_scale_jobs, scale_jobs.data(), scale_jobs.size() * sizeof(OzJob))) != TK_OK)
+        (rc = dev_upload(ctx, (void**)&L->d_scale_jobs, scale_jobs.data(), scale_jobs.size() * sizeof(OzJob))) != TK_OK ||
+        (rc = dev_upload(ctx, (void**)&L->d_cta_work, L->cta_work.data(), L->cta_work.size() * sizeof(int32_t))) != TK_OK)
       return rc;
   }
-  cp.d_oz = {L->d_sectors, L->d_work, L->d_slice_jobs, L->d_scale_jobs};
+  cp.d_oz = {L->d_sectors, L->d_work, L->d_slice_jobs, L->d_scale_jobs, L->d_cta_work};
   cp.oz_nwork = L->nwork;
   cp.oz_bytes = L->bytes;
   cp.oz = L;
@@ -992,10 +1049,10 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
   }
   {
     ProfScope prof(ctx, "k_oz_gemm", stream);
-    const int grid = (int)std::min<int64_t>(L->nwork, std::max(1, ctx->num_sms));
+    const int grid = L->ncta;
     double* part = (double*)(w + L->off_part);
 #define TK_OZ_LAUNCH(BNV, MODEV)                                                                           \
-  k_oz_gemm<BNV, MODEV><<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, (int)L->nwork, L->pairs, \
+  k_oz_gemm<BNV, MODEV><<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, L->d_cta_work, L->pairs,  \
                                                        L->slices, sa, sb, (double*)c, part, counters, ctx->d_status)
     if (L->mode == 0) {
       if (L->bn == OZ_BN_WIDE)

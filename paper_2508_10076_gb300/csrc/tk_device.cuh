@@ -12,6 +12,18 @@ static __device__ __forceinline__ void two_sum(float a, float b, float& s, float
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Packed FP32 pairs (one instruction per pair on this part).  y - x as fma(x, -1, y): the product
+// is exact, so this rounds exactly like a subtraction.
+static __device__ __forceinline__ float2 sub2(float2 y, float2 x) {
+  return __ffma2_rn(x, make_float2(-1.f, -1.f), y);
+}
+// two_sum on both lanes of a pair.
+static __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = __fadd2_rn(a, b);
+  const float2 bb = sub2(s, a);
+  e = __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
 // Exact FP32 -> FP64 of a subnormal, infinite or NaN FP32 value, out of line (rare).
 static __device__ __noinline__ double f32_to_f64_rare(float f) {
   const uint32_t u = __float_as_uint(f);
