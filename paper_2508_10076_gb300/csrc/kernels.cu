@@ -338,6 +338,8 @@ constexpr int ROWS_NMAX = 8, ROWS_KCHUNK = 256;
 // shorter products, and all complex ones, take one row per thread (more CTAs).  A row block
 // covers 256 x rpt rows.
 __host__ __device__ constexpr int rows_rpt(int nt) { return nt <= 2 ? 4 : nt <= 4 ? 2 : 1; }
+// The double-float rows run with four CTAs per SM (64 registers): at most two rows per thread.
+__host__ __device__ constexpr int rows_rpt_df(int nt) { return nt <= 4 ? 2 : 1; }
 
 __device__ __forceinline__ double add(double a, double b) { return a + b; }
 __device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -747,7 +749,7 @@ __device__ __forceinline__ void gemm_rows_df(const GemmItem& it, const GemmTile&
   if (tl.rpt == 1)                                                            \
     gemm_rows_df_n<NT, 1>(it, tl, A, B, C, smem, partials, counters);         \
   else                                                                        \
-    gemm_rows_df_n<NT, rows_rpt(NT)>(it, tl, A, B, C, smem, partials, counters);
+    gemm_rows_df_n<NT, rows_rpt_df(NT)>(it, tl, A, B, C, smem, partials, counters);
   switch (it.N) {
     case 1: TK_ROWS_DF_CASE(1) break;
     case 2: TK_ROWS_DF_CASE(2) break;
@@ -761,26 +763,15 @@ __device__ __forceinline__ void gemm_rows_df(const GemmItem& it, const GemmTile&
 #undef TK_ROWS_DF_CASE
 }
 
-template <typename T>
-__device__ __forceinline__ void gemm_rows_df_dispatch(const GemmItem& it, const GemmTile& tl, const T* A, const T* B,
-                                                      T* C, T* smem, T* partials, int* counters) {
-  gemm_rows<T>(it, tl, A, B, C, smem, partials, counters);  // complex tensors never take the split-precision path
-}
-template <>
-__device__ __forceinline__ void gemm_rows_df_dispatch<double>(const GemmItem& it, const GemmTile& tl, const double* A,
-                                                              const double* B, double* C, double* smem,
-                                                              double* partials, int* counters) {
-  gemm_rows_df(it, tl, A, B, C, smem, partials, counters);
-}
-
 // One launch per contraction for every FP64-list product: 64x64 / 32x32 tiles and the N <= 8
 // row blocks share the grid (their shared-memory needs overlap in one buffer).
-template <typename T, bool DF>
+template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 1) k_gemm_f64(const GemmItem* __restrict__ items,
-                                                  const GemmTile* __restrict__ tiles,
-                                                  const T* __restrict__ A,
-                                                  const T* __restrict__ B, T* __restrict__ C,
-                                                  T* __restrict__ partials, int* __restrict__ counters) {
+                                                                        const GemmTile* __restrict__ tiles,
+                                                                        const T* __restrict__ A,
+                                                                        const T* __restrict__ B, T* __restrict__ C,
+                                                                        T* __restrict__ partials,
+                                                                        int* __restrict__ counters) {
   constexpr int kTileElems = BK * 65 * 2, kRowElems = ROWS_KCHUNK * ROWS_NMAX;
   __shared__ T smem[kTileElems > kRowElems ? kTileElems : kRowElems];
   const GemmTile tl = tiles[blockIdx.x];
@@ -789,10 +780,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 1) k_gemm_f64(const 
     gemm_tile<T, 64, 64, 4, 4>(it, tl, A, B, C, smem, partials, counters);
   else if (tl.cfg == CFG_32)
     gemm_tile<T, 32, 32, 2, 2>(it, tl, A, B, C, smem, partials, counters);
-  else if (DF)
-    gemm_rows_df_dispatch<T>(it, tl, A, B, C, smem, partials, counters);
   else
     gemm_rows<T>(it, tl, A, B, C, smem, partials, counters);
+}
+
+// Split-precision modes: every product left to the CUDA cores is an N <= 8 row block in
+// double-float (the planner cuts wider thin products into such blocks), so this launch runs the
+// row code alone, with the registers of four CTAs per SM.
+__global__ void __launch_bounds__(256, 4) k_gemm_rows_df(const GemmItem* __restrict__ items,
+                                                         const GemmTile* __restrict__ tiles,
+                                                         const double* __restrict__ A, const double* __restrict__ B,
+                                                         double* __restrict__ C, double* __restrict__ partials,
+                                                         int* __restrict__ counters) {
+  __shared__ double smem[ROWS_KCHUNK * ROWS_NMAX];  // B of one K chunk as double-float pairs
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmItem it = items[tl.item];
+  gemm_rows_df(it, tl, A, B, C, smem, partials, counters);
 }
 
 // Packed FP64 GEMM over many requests: each segment carries one request's work list and buffers.
@@ -1038,8 +1041,10 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
   // several rows per thread only where the product is long enough to give eight waves of
   // one-row blocks at three CTAs per SM (fewer, longer-lived threads then lose nothing)
   const bool cplx = cp.dtype == TK_C128;
+  const bool df = cp.gemm_mode != TK_GEMM_FP64;
   auto rows_per_thread = [&](const GemmItem& g) {
-    return (!cplx && (g.M + 255) / 256 >= 8 * 3 * sms) ? rows_rpt((int)g.N) : 1;
+    if (cplx || (g.M + 255) / 256 < 8 * 3 * sms) return 1;
+    return df ? rows_rpt_df((int)g.N) : rows_rpt((int)g.N);
   };
   auto rows_block = [&](const GemmItem& g) { return (int64_t)256 * rows_per_thread(g); };
   int64_t rows_ctas = 0;
@@ -1104,6 +1109,12 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
         emit((int32_t)i, m0, n0, use64 ? CFG_64 : CFG_32, g.K, nsplit, BK, (int64_t)bm * bm, (double)bm * bm, 1);
   }
   cp.split_slots = nslots;
+  if (cp.gemm_mode != TK_GEMM_FP64)  // the split-precision launch runs row blocks only
+    for (const Cand& c : cands)
+      if (c.t.cfg != CFG_ROWS_DF) {
+        ctx->last_error = "split-precision plan with a non-row CUDA-core tile";
+        return TK_ERR_UNSUPPORTED;
+      }
   // Row blocks first (they are latency-bound: a serial walk over K), then tiles by cost, largest
   // first, so the short tiles fill the tail.
   std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) {
@@ -1133,16 +1144,19 @@ int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void
   const GemmItem* items = (const GemmItem*)cp.d_gemm_items;
   const GemmTile* tiles = (const GemmTile*)cp.d_gemm_tiles;
   const unsigned grid = (unsigned)cp.n_gemm_tiles;
+  if (cp.dtype != TK_C128 && cp.gemm_mode != TK_GEMM_FP64) {
+    ProfScope prof(ctx, "k_gemm_rows_df", stream);
+    k_gemm_rows_df<<<grid, 256, 0, s>>>(items, tiles, (const double*)a, (const double*)b, (double*)c,
+                                        (double*)partials, counters);
+    return check_launch(ctx, "k_gemm_rows_df");
+  }
   ProfScope prof(ctx, "k_gemm_f64", stream);
   if (cp.dtype == TK_C128)
-    k_gemm_f64<double2, false><<<grid, 256, 0, s>>>(items, tiles, (const double2*)a, (const double2*)b, (double2*)c,
-                                                    (double2*)partials, counters);
-  else if (cp.gemm_mode == TK_GEMM_FP64)
-    k_gemm_f64<double, false><<<grid, 256, 0, s>>>(items, tiles, (const double*)a, (const double*)b, (double*)c,
-                                                   (double*)partials, counters);
+    k_gemm_f64<double2><<<grid, 256, 0, s>>>(items, tiles, (const double2*)a, (const double2*)b, (double2*)c,
+                                             (double2*)partials, counters);
   else
-    k_gemm_f64<double, true><<<grid, 256, 0, s>>>(items, tiles, (const double*)a, (const double*)b, (double*)c,
-                                                  (double*)partials, counters);
+    k_gemm_f64<double><<<grid, 256, 0, s>>>(items, tiles, (const double*)a, (const double*)b, (double*)c,
+                                            (double*)partials, counters);
   return check_launch(ctx, "k_gemm_f64");
 }
 

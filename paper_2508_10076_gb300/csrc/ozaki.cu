@@ -841,10 +841,10 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
   std::vector<OzWork> work;
   std::vector<OzJob> slice_jobs, scale_jobs;
   std::vector<std::pair<double, OzWork>> wcost;
-  // Tile width: a 128 x N x 16 MMA costs at least ~45 cycles whatever N, so 128-column tiles run
-  // the tensor pipe at full rate where 64-column tiles reach two thirds of it; but 128-column tiles
-  // hold all of TMEM, so their epilogue stalls the MMAs: they pay off when the average inner
-  // dimension per output tile is long.
+  // Tile width: measured in this kernel, a 128 x 64 x 16 MMA takes ~72 cycles and a 128 x 128 x 16
+  // one ~65 (the full rate), so 128-column tiles do nearly twice the work per cycle; but they hold
+  // all of TMEM, so their epilogue (~12k cycles a tile) stalls the MMAs.  They pay off once a tile
+  // has a few k-chunks (average inner dimension of 128 or more).
   {
     double kw = 0, w = 0;
     for (const GemmItem& it : cp.gemms_oz) {
@@ -852,7 +852,7 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
       kw += area * (double)it.K;
       w += area;
     }
-    L->bn = (w > 0 && kw / w >= 512.0) ? OZ_BN_WIDE : OZ_BN_NARROW;
+    L->bn = (w > 0 && kw / w >= 128.0) ? OZ_BN_WIDE : OZ_BN_NARROW;
     if (cp.tune_oz_bn == OZ_BN_WIDE || cp.tune_oz_bn == OZ_BN_NARROW) L->bn = cp.tune_oz_bn;
   }
   const int bn = L->bn;
