@@ -259,10 +259,12 @@ __device__ __forceinline__ void permute_tiles(const PermSeg& g, int64_t bid, T (
 }
 
 // Contiguous runs (destination and sources share their fastest leg): one warp per run, lanes
-// along the run, four elements per lane in flight.  Abelian runs (one source, weight 1) are plain
-// copies; SU(2) runs sum their weighted sources in FP64.
+// along the run, U elements per lane in flight.  Copy runs (one source, weight 1) carry their
+// source offset, so the next run's record is the only load before the data; it is fetched while
+// the current run is copied.  SU(2) runs sum their weighted sources in FP64.
 template <typename T>
 __device__ __forceinline__ void permute_runs(const PermSeg& g, int64_t bid) {
+  constexpr int U = 4;
   const PermRun* __restrict__ runs = g.runs;
   const PermTask* __restrict__ tasks = g.tasks;
   const PermSrc* __restrict__ srcs = g.srcs;
@@ -270,38 +272,39 @@ __device__ __forceinline__ void permute_runs(const PermSeg& g, int64_t bid) {
   T* __restrict__ out = (T*)g.out;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (g.nblocks * blockDim.x) >> 5;
-  for (int64_t r = (bid * blockDim.x + threadIdx.x) >> 5; r < g.nwork; r += nwarps) {
-    const PermRun run = runs[r];
-    const int nsrc = __ldg(&tasks[run.task].nsrc);
-    const int sb = __ldg(&tasks[run.task].src_begin);
-    const int conj = __ldg(&tasks[run.task].conj);
-    const PermSrc s0 = srcs[sb];
+  int64_t r = (bid * blockDim.x + threadIdx.x) >> 5;
+  PermRun next;
+  if (r < g.nwork) next = runs[r];
+  for (; r < g.nwork; r += nwarps) {
+    const PermRun run = next;
+    if (r + nwarps < g.nwork) next = runs[r + nwarps];
     T* dst = out + run.dst;
-    if (conj) {  // adjoint: conjugating copy
-      const T* src = in + s0.in_off + run.ir + run.ic * s0.ld;
-      for (int e = lane; e < run.len; e += 32) dst[e] = Elem<T>::conj(__ldg(src + e));
-      continue;
-    }
-    if (nsrc == 1 && s0.coef == 1.0) {
-      const T* src = in + s0.in_off + run.ir + run.ic * s0.ld;
-      for (int e = lane; e < run.len; e += 128) {
-        T v[4];
+    if (run.task < 0) {
+      const T* src = in + run.ir;
+      if (run.task == -2) {  // adjoint: conjugating copy
+        for (int e = lane; e < run.len; e += 32) dst[e] = Elem<T>::conj(__ldg(src + e));
+        continue;
+      }
+      for (int e = lane; e < run.len; e += 32 * U) {
+        T v[U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < U; ++u)
           if (e + 32 * u < run.len) v[u] = __ldg(src + e + 32 * u);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < U; ++u)
           if (e + 32 * u < run.len) dst[e + 32 * u] = v[u];
       }
-    } else {
-      for (int e = lane; e < run.len; e += 32)
-        dst[e] = gather<T>(srcs, nsrc, sb, in, run.ir + e, run.ic);
+      continue;
     }
+    const int nsrc = __ldg(&tasks[run.task].nsrc);
+    const int sb = __ldg(&tasks[run.task].src_begin);
+    for (int e = lane; e < run.len; e += 32)
+      dst[e] = gather<T>(srcs, nsrc, sb, in, run.ir + e, run.ic);
   }
 }
 
 template <typename T, int NSEG>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 5 : 4) k_permute(const __grid_constant__ PermLaunchT<NSEG> L) {
+__global__ void __launch_bounds__(256, 4) k_permute(const __grid_constant__ PermLaunchT<NSEG> L) {
   __shared__ T tile[32][33];
   __shared__ int64_t task_words[kTaskWords];
   const PermSeg& g = L.seg[find_seg(L.seg, L.nseg, (int64_t)blockIdx.x)];

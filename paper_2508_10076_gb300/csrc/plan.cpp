@@ -304,6 +304,8 @@ static void emit_task(PermutePlan& pp, PermTask t, std::vector<int64_t>& ext, st
     t.mode = 0;
     const int32_t task_id = (int32_t)pp.rtasks.size();
     pp.rtasks.push_back(t);
+    const PermSrc s0 = pp.srcs[(size_t)t.src_begin];
+    const bool plain = t.nsrc == 1 && s0.coef == 1.0;  // a copy (conjugating for adjoint tasks)
     const int64_t outer = total / t.ext[0];
     for (int64_t o = 0; o < outer; ++o) {
       int64_t rem = o, dst = t.out_off, ir = 0, ic = 0;
@@ -316,7 +318,10 @@ static void emit_task(PermutePlan& pp, PermTask t, std::vector<int64_t>& ext, st
       }
       for (int64_t e0 = 0; e0 < t.ext[0]; e0 += kRunChunk) {
         const int32_t len = (int32_t)std::min<int64_t>(kRunChunk, t.ext[0] - e0);
-        pp.runs.push_back(PermRun{dst + e0, ir + e0, ic, len, task_id});
+        if (plain)  // the source offset resolved here: the kernel makes no table lookups
+          pp.runs.push_back(PermRun{dst + e0, s0.in_off + ir + e0 + ic * s0.ld, 0, len, t.conj ? -2 : -1});
+        else
+          pp.runs.push_back(PermRun{dst + e0, ir + e0, ic, len, task_id});
       }
     }
     return;

@@ -117,6 +117,8 @@ struct PermSrc {
   double coef;
 };
 // One contiguous run of a mode-0 task: dst[e] = sum_k coef_k src_k[ir + e + ic ld_k], e < len.
+// Runs of one source with weight 1 carry task = -1 (copy) or -2 (conjugating copy) and the
+// absolute source offset in ir: dst[e] = src[ir + e].
 struct PermRun {
   int64_t dst, ir, ic;
   int32_t len, task;
