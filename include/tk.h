@@ -60,6 +60,13 @@ extern "C" {
 #define TK_SYM_Z2 0
 #define TK_SYM_U1 1
 #define TK_SYM_SU2 2
+/* Deligne products (Sec. 5.2, product sectors): a sector is a pair (a1, a2) of the factors'
+ * labels, passed as the int32 a1 * 4096 + f(a2) with f(a2) = a2 + 2048 for a U(1) second factor
+ * (|a2| < 2048) and f(a2) = a2 otherwise (SU(2): 2j <= 4095).  The integer order is then the
+ * lexicographic order of the pairs.  Fusion, duals and dimensions act factor by factor; F and R
+ * symbols are products of the factors' symbols. */
+#define TK_SYM_U1_SU2 3 /* U(1) x SU(2), e.g. charge x spin */
+#define TK_SYM_Z2_U1 4  /* Z2 x U(1), e.g. fermion parity x charge (bosonic braiding) */
 
 #define TK_F64 0
 #define TK_C128 1

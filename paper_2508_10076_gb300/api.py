@@ -5,7 +5,20 @@ import ctypes as C
 
 from . import _abi
 
-SYM = {"Z2": 0, "U1": 1, "SU2": 2}
+SYM = {"Z2": 0, "U1": 1, "SU2": 2, "U1xSU2": 3, "Z2xU1": 4}
+
+
+def product_sector(sym, a1, a2):
+    """int32 label of the pair (a1, a2) of a Deligne-product symmetry (layout in include/tk.h)."""
+    s = SYM[sym] if isinstance(sym, str) else int(sym)
+    if s not in (3, 4):
+        raise ValueError("not a product symmetry")
+    return int(a1) * 4096 + (int(a2) + 2048 if s == 4 else int(a2))
+
+
+def _sector_label(sym, a):
+    """Sector labels may be given as ints or, for product symmetries, as (a1, a2) pairs."""
+    return product_sector(sym, *a) if isinstance(a, tuple) else int(a)
 DTYPE = {"f64": 0, "c128": 1}
 GEMM = {"fp64": 0, "ozaki": 1, "tf32x3": 2}
 
@@ -109,7 +122,7 @@ class Space:
         if _handle is not None:
             self._h = _handle
         else:
-            items = sorted(dict(sectors).items())
+            items = sorted((_sector_label(sym, a), m) for a, m in dict(sectors).items())
             secs, n = _ints([a for a, _ in items], C.c_int32)
             mults, _ = _ints([m for _, m in items], C.c_int64)
             _check(_lib().tk_space_create(ctx._h, SYM[sym] if isinstance(sym, str) else int(sym), n, secs,

@@ -191,7 +191,7 @@ int tk_space_create(tk_ctx* ctx, int sym, int nsec, const int32_t* sectors, cons
                     int is_dual, tk_space** out) {
   if (!out) return fail(ctx, TK_ERR_ARG, "null out");
   *out = nullptr;
-  if (sym < 0 || sym > 2) return fail(ctx, TK_ERR_ARG, "unknown symmetry");
+  if (sym < 0 || sym > TK_SYM_Z2_U1) return fail(ctx, TK_ERR_ARG, "unknown symmetry");
   if (nsec <= 0 || !sectors || !mults) return fail(ctx, TK_ERR_ARG, "a space needs at least one sector");
   return guarded(ctx, [&]() {
     std::vector<std::pair<int32_t, int64_t>> v;

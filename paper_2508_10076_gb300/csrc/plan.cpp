@@ -63,9 +63,9 @@ TP decode(const std::vector<int32_t>& k) {
 using Vec = std::map<std::vector<int32_t>, double>;
 
 // running label before the last leg of a tree with uncoupled `u` and inner `in`
-int32_t before_last(const std::vector<int32_t>& u, const std::vector<int32_t>& in) {
+int32_t before_last(int sym, const std::vector<int32_t>& u, const std::vector<int32_t>& in) {
   size_t n = u.size();
-  if (n == 1) return 0;  // the unit
+  if (n == 1) return sector_unit(sym);
   if (n == 2) return u[0];
   return in[n - 3];
 }
@@ -76,7 +76,7 @@ Vec bend_f2s(int sym, const Vec& v, bool was_dual) {
   for (const auto& kv : v) {
     TP t = decode(kv.first);
     int32_t b = t.fu.back();
-    int32_t u = before_last(t.fu, t.fi);
+    int32_t u = before_last(sym, t.fu, t.fi);
     double coef = bend_coef(sym, b, was_dual, u, t.c);
     TP n;
     n.su = t.su;
@@ -97,7 +97,7 @@ Vec bend_s2f(int sym, const Vec& v, bool was_dual) {
   for (const auto& kv : v) {
     TP t = decode(kv.first);
     int32_t a = t.su.back();
-    int32_t u = before_last(t.su, t.si);
+    int32_t u = before_last(sym, t.su, t.si);
     double coef = bend_coef(sym, a, was_dual, u, t.c);
     TP n;
     n.fu = t.fu;

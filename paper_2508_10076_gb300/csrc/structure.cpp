@@ -62,7 +62,7 @@ void enumerate_trees(int sym, const std::vector<Space>& legs, std::vector<Tree>&
   const int n = (int)legs.size();
   if (n == 0) {
     Tree t;
-    t.coupled = 0;
+    t.coupled = sector_unit(sym);
     t.size = 1;
     out.push_back(t);
     return;

@@ -270,21 +270,82 @@ std::unordered_map<uint64_t, double> g_fcache;
 
 }  // namespace
 
+// Deligne products S1 x S2 (Sec. 5.2 product sectors): a sector is the pair (a1, a2), encoded as
+// a1 * 4096 + field(a2) with field(a2) = a2 + 2048 for a U(1) second factor (|a2| < 2048) and
+// a2 otherwise, so that the integer order is the lexicographic order of the pairs.  Fusion,
+// duals and dimensions act factor by factor; F, R, the Frobenius-Schur indicator and the bend
+// coefficient of a product are the products of the factors' values.
+namespace {
+constexpr int32_t kPairShift = 4096, kU1Offset = 2048;
+bool product_sym(int sym, int& s1, int& s2) {
+  switch (sym) {
+    case TK_SYM_U1_SU2: s1 = TK_SYM_U1; s2 = TK_SYM_SU2; return true;
+    case TK_SYM_Z2_U1: s1 = TK_SYM_Z2; s2 = TK_SYM_U1; return true;
+  }
+  return false;
+}
+void split_pair(int s2, int32_t a, int32_t& a1, int32_t& a2) {
+  a1 = (a >= 0 ? a : a - (kPairShift - 1)) / kPairShift;  // floor division
+  const int32_t f = a - a1 * kPairShift;
+  a2 = s2 == TK_SYM_U1 ? f - kU1Offset : f;
+}
+int32_t join_pair(int s2, int32_t a1, int32_t a2) { return a1 * kPairShift + (s2 == TK_SYM_U1 ? a2 + kU1Offset : a2); }
+}  // namespace
+
+int32_t sector_unit(int sym) {
+  int s1, s2;
+  return product_sym(sym, s1, s2) ? join_pair(s2, 0, 0) : 0;
+}
+
 bool sector_valid(int sym, int32_t a) {
+  int s1, s2;
+  if (product_sym(sym, s1, s2)) {
+    int32_t a1, a2;
+    split_pair(s2, a, a1, a2);
+    return sector_valid(s1, a1) && sector_valid(s2, a2) && a1 > -(1 << 18) && a1 < (1 << 18);
+  }
   switch (sym) {
     case TK_SYM_Z2: return a == 0 || a == 1;
     case TK_SYM_U1: return true;
-    case TK_SYM_SU2: return a >= 0 && a <= 4096;
+    case TK_SYM_SU2: return a >= 0 && a <= 4095;
   }
   return false;
 }
 
-int32_t sector_dual(int sym, int32_t a) { return sym == TK_SYM_U1 ? -a : a; }
+int32_t sector_dual(int sym, int32_t a) {
+  int s1, s2;
+  if (product_sym(sym, s1, s2)) {
+    int32_t a1, a2;
+    split_pair(s2, a, a1, a2);
+    return join_pair(s2, sector_dual(s1, a1), sector_dual(s2, a2));
+  }
+  return sym == TK_SYM_U1 ? -a : a;
+}
 
-int32_t sector_dim(int sym, int32_t a) { return sym == TK_SYM_SU2 ? a + 1 : 1; }
+int32_t sector_dim(int sym, int32_t a) {
+  int s1, s2;
+  if (product_sym(sym, s1, s2)) {
+    int32_t a1, a2;
+    split_pair(s2, a, a1, a2);
+    return sector_dim(s1, a1) * sector_dim(s2, a2);
+  }
+  return sym == TK_SYM_SU2 ? a + 1 : 1;
+}
 
 void sector_fuse(int sym, int32_t a, int32_t b, std::vector<int32_t>& out) {
   out.clear();
+  int s1, s2;
+  if (product_sym(sym, s1, s2)) {
+    int32_t a1, a2, b1, b2;
+    split_pair(s2, a, a1, a2);
+    split_pair(s2, b, b1, b2);
+    std::vector<int32_t> c1, c2;
+    sector_fuse(s1, a1, b1, c1);
+    sector_fuse(s2, a2, b2, c2);
+    for (int32_t x : c1)
+      for (int32_t y : c2) out.push_back(join_pair(s2, x, y));  // ascending: x major, y minor
+    return;
+  }
   switch (sym) {
     case TK_SYM_Z2: out.push_back(a ^ b); break;
     case TK_SYM_U1: out.push_back(a + b); break;
@@ -295,6 +356,14 @@ void sector_fuse(int sym, int32_t a, int32_t b, std::vector<int32_t>& out) {
 }
 
 bool sector_nsym(int sym, int32_t a, int32_t b, int32_t c) {
+  int s1, s2;
+  if (product_sym(sym, s1, s2)) {
+    int32_t a1, a2, b1, b2, c1, c2;
+    split_pair(s2, a, a1, a2);
+    split_pair(s2, b, b1, b2);
+    split_pair(s2, c, c1, c2);
+    return sector_nsym(s1, a1, b1, c1) && sector_nsym(s2, a2, b2, c2);
+  }
   switch (sym) {
     case TK_SYM_Z2: return c == (a ^ b);
     case TK_SYM_U1: return c == a + b;
@@ -307,6 +376,14 @@ double fsymbol(int sym, int32_t a, int32_t b, int32_t c, int32_t d, int32_t e, i
   if (!sector_nsym(sym, a, b, e) || !sector_nsym(sym, e, c, d) || !sector_nsym(sym, b, c, f) ||
       !sector_nsym(sym, a, f, d))
     return 0.0;
+  int s1, s2;
+  if (product_sym(sym, s1, s2)) {
+    int32_t x1[6], x2[6];
+    const int32_t x[6] = {a, b, c, d, e, f};
+    for (int i = 0; i < 6; ++i) split_pair(s2, x[i], x1[i], x2[i]);
+    return fsymbol(s1, x1[0], x1[1], x1[2], x1[3], x1[4], x1[5]) *
+           fsymbol(s2, x2[0], x2[1], x2[2], x2[3], x2[4], x2[5]);
+  }
   if (sym != TK_SYM_SU2) return 1.0;
   if (a < 0 || b < 0 || c < 0 || d < 0 || e < 0 || f < 0 || a > 1023 || b > 1023 || c > 1023 ||
       d > 1023 || e > 1023 || f > 1023)
@@ -326,11 +403,25 @@ double fsymbol(int sym, int32_t a, int32_t b, int32_t c, int32_t d, int32_t e, i
 
 double rsymbol(int sym, int32_t a, int32_t b, int32_t c) {
   if (!sector_nsym(sym, a, b, c)) return 0.0;
+  int s1, s2;
+  if (product_sym(sym, s1, s2)) {
+    int32_t a1, a2, b1, b2, c1, c2;
+    split_pair(s2, a, a1, a2);
+    split_pair(s2, b, b1, b2);
+    split_pair(s2, c, c1, c2);
+    return rsymbol(s1, a1, b1, c1) * rsymbol(s2, a2, b2, c2);
+  }
   if (sym != TK_SYM_SU2) return 1.0;
   return (((a + b - c) / 2) & 1) ? -1.0 : 1.0;
 }
 
 double fs_indicator(int sym, int32_t a) {
+  int s1, s2;
+  if (product_sym(sym, s1, s2)) {
+    int32_t a1, a2;
+    split_pair(s2, a, a1, a2);
+    return fs_indicator(s1, a1) * fs_indicator(s2, a2);
+  }
   if (sym != TK_SYM_SU2) return 1.0;
   return (a & 1) ? -1.0 : 1.0;
 }
@@ -338,7 +429,15 @@ double fs_indicator(int sym, int32_t a) {
 double bend_coef(int sym, int32_t x, bool was_dual, int32_t u, int32_t c) {
   // Overlap of the bent tree pair with the canonical one, divided by its norm d_u:
   //   (was_dual ? 1 : chi_x) * (-1)^(x + c - u) * sqrt(d_c / d_u)
-  // (for SU(2); abelian symmetries give 1).
+  // (for SU(2); abelian symmetries give 1; a product multiplies its factors' values).
+  int s1, s2;
+  if (product_sym(sym, s1, s2)) {
+    int32_t x1, x2, u1, u2, c1, c2;
+    split_pair(s2, x, x1, x2);
+    split_pair(s2, u, u1, u2);
+    split_pair(s2, c, c1, c2);
+    return bend_coef(s1, x1, was_dual, u1, c1) * bend_coef(s2, x2, was_dual, u2, c2);
+  }
   if (sym != TK_SYM_SU2) return 1.0;
   double s = was_dual ? 1.0 : fs_indicator(sym, x);
   if (((x + c - u) / 2) & 1) s = -s;
@@ -350,14 +449,14 @@ double bend_coef(int sym, int32_t x, bool was_dual, int32_t u, int32_t c) {
 
 extern "C" double tk_fsymbol(int sym, int32_t a, int32_t b, int32_t c, int32_t d, int32_t e,
                              int32_t f) {
-  if (sym < 0 || sym > 2) return 0.0;
+  if (sym < 0 || sym > TK_SYM_Z2_U1) return 0.0;
   for (int32_t x : {a, b, c, d, e, f})
     if (!tk::sector_valid(sym, x)) return 0.0;
   return tk::fsymbol(sym, a, b, c, d, e, f);
 }
 
 extern "C" double tk_rsymbol(int sym, int32_t a, int32_t b, int32_t c) {
-  if (sym < 0 || sym > 2) return 0.0;
+  if (sym < 0 || sym > TK_SYM_Z2_U1) return 0.0;
   for (int32_t x : {a, b, c})
     if (!tk::sector_valid(sym, x)) return 0.0;
   return tk::rsymbol(sym, a, b, c);

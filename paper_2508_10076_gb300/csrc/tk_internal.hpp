@@ -18,6 +18,7 @@ namespace tk {
 // Sector algebra of Z2, U(1), SU(2) (Sec. 3.1, Sec. 5.4) and the elementary moves used to
 // recouple fusion trees (Sec. 4.2).  All labels use the ABI encoding (SU(2): 2j).
 bool sector_valid(int sym, int32_t a);
+int32_t sector_unit(int sym);  // label of the trivial sector
 int32_t sector_dual(int sym, int32_t a);
 int32_t sector_dim(int sym, int32_t a);
 void sector_fuse(int sym, int32_t a, int32_t b, std::vector<int32_t>& out);  // ascending

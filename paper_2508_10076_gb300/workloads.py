@@ -9,7 +9,8 @@ Spaces follow the paper's benchmark shapes (Sec. 6): x : V (x) P <- V (x) P*,
 W : W (x) P <- P (x) W, L : V <- V (x) W, R : W (x) V* <- V*.  Multiplicity laws stand in for the
 MPSKit-derived spaces of the paper's benchmark repository (not available): U(1) charges
 q = -16..16 with n_q proportional to exp(-q^2/72); SU(2) spins j = 0..4 with n_j proportional to
-exp(-j^2/4); rounded to the stated total by largest remainder (ties: smaller |label| first).
+exp(-j^2/4); U(1) x SU(2) charge x spin pairs (Hubbard-like, see u1su2_virtual); rounded to the
+stated total by largest remainder (ties: smaller |label| first).
 """
 
 import math
@@ -52,6 +53,27 @@ def su2_virtual(total: int = 256):
     tjs = list(range(0, 9))  # 2j = 0..8, j = 0..4
     return apportion(total, tjs, [math.exp(-(tj / 2.0) ** 2 / 4.0) for tj in tjs])
 
+
+def pair_label(a1: int, a2: int, u1_second: bool = False) -> int:
+    """Integer label of the sector pair (a1, a2) of a Deligne-product symmetry: a1 * 4096 + a2,
+    with a2 offset by 2048 when the second factor is U(1) (the label layout of the C ABI)."""
+    return int(a1) * 4096 + int(a2) + (2048 if u1_second else 0)
+
+
+def u1su2_virtual(total: int = 1024):
+    """Charge x spin virtual space (Hubbard-like): q = -4..4 (particle number relative to half
+    filling), 2j = 0..6 with q + 2j even, n proportional to exp(-q^2/8 - j^2/4)."""
+    pairs = [(q, tj) for q in range(-4, 5) for tj in range(0, 7) if (q + tj) % 2 == 0]
+    labels = [pair_label(q, tj) for q, tj in pairs]
+    return apportion(total, labels, [math.exp(-q * q / 8.0 - (tj / 2.0) ** 2 / 4.0) for q, tj in pairs])
+
+
+# Hubbard site: empty (q = -1, j = 0), singly occupied (q = 0, j = 1/2), doubly occupied (q = 1,
+# j = 0); MPO bond: two identity channels and the hopping operators c^dagger (q = 1, j = 1/2) and
+# c (q = -1, j = 1/2).  The MPO's reduced blocks are random (the fermionic signs of a true
+# Hubbard MPO need fermionic braiding, which this path leaves out).
+U1SU2_PHYS = {pair_label(-1, 0): 1, pair_label(0, 1): 1, pair_label(1, 0): 1}
+U1SU2_MPO = {pair_label(0, 0): 2, pair_label(1, 1): 1, pair_label(-1, 1): 1}
 
 U1_PHYS = {-1: 1, 1: 1}          # spin-1/2, charge 2 S_z
 U1_MPO = {-2: 1, 0: 3, 2: 1}     # XXZ bond space
@@ -141,6 +163,8 @@ def heff_spaces(sym: str, D: int):
     """(V, P, W) sector dicts of the two-site heff workload."""
     if sym == "U1":
         return u1_virtual(D), U1_PHYS, U1_MPO
+    if sym == "U1xSU2":
+        return u1su2_virtual(D), U1SU2_PHYS, U1SU2_MPO
     return su2_virtual(D), SU2_PHYS, SU2_MPO
 
 
@@ -169,4 +193,5 @@ CONFIGS = {
     "c5_u1_heff1_d4096": dict(sym="U1", D=4096, kind="heff1"),
     "c5_su2_heff1_n1024": dict(sym="SU2", D=1024, kind="heff1"),
     "c3_su2_lx_n1024": dict(sym="SU2", D=1024, kind="lx"),
+    "c6_u1su2_heff_n2048": dict(sym="U1xSU2", D=2048, kind="heff"),
 }

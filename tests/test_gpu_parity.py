@@ -52,6 +52,11 @@ PERMUTE_CASES = [
     ("SU2", ([({0: 9, 1: 7, 2: 5, 3: 2}, False), ({1: 1}, False)], [({0: 6, 1: 8, 2: 4}, True), ({1: 1}, True)])),
     ("SU2", ([({1: 3, 2: 2}, True), ({0: 2, 2: 3}, False), ({1: 2}, False)], [({0: 5, 2: 2, 4: 1}, False)])),
     ("Z2", ([({0: 50, 1: 45}, False), ({0: 2, 1: 3}, True)], [({0: 31, 1: 29}, False), ({1: 4}, True)])),
+    # Deligne products (labels a1 * 4096 + f(a2), layout in include/tk.h)
+    ("U1xSU2", ([({4096 * -1 + 1: 9, 0: 20, 2: 7, 4096 + 1: 11}, False), ({4096 + 1: 1, -4096 + 1: 1}, False)],
+                [({0: 12, 2: 5, 4096 + 1: 6, -4096 + 1: 6, 2 * 4096: 3}, True), ({4096 + 1: 1}, True)])),
+    ("Z2xU1", ([({2047: 30, 2048 + 4096: 41, 2049: 17}, False), ({2049 + 4096: 2, 2047: 1}, True)],
+               [({2048 + 4096: 25, 2048: 33, 2050 + 4096: 4}, False), ({2049: 2}, True)])),
 ]
 
 
@@ -87,7 +92,7 @@ def test_permute_parity(gctx, case, dtype):
         api.permute(gctx, plan, xd, yd)
         gctx.sync()
         got = yd.cpu().numpy()
-        if sym == "SU2":
+        if sym in ("SU2", "U1xSU2"):  # non-abelian: weighted sums of sources
             assert np.allclose(got, ref, rtol=1e-13, atol=1e-13), (p, q)
         else:
             assert np.array_equal(got, ref), (p, q)
@@ -336,3 +341,48 @@ def test_long_skinny_products(gctx, gemm, tol):
     api.contract(gctx, plan, _dev(xa), _dev(xb), c, ws)
     gctx.sync()
     assert rel_frobenius_per_block(cs, c.cpu().numpy(), ref) <= tol
+
+
+@pytest.mark.parametrize("gemm,tol", [("fp64", FP64_TOL), ("ozaki", 1e-10)])
+def test_product_symmetry_contraction(gctx, gemm, tol):
+    """U(1) x SU(2) environment times two-site-like tensor (the L.x step with charge x spin
+    sectors): block structure bit-exact and values within the FP64 / split-precision bounds."""
+    from oracle.symmetry import U1xSU2
+    api = _api()
+    P = U1xSU2.pair
+    vs = {P(q, t): n for (q, t), n in {(-2, 0): 20, (-1, 1): 31, (0, 0): 40, (0, 2): 23, (1, 1): 29,
+                                         (2, 0): 17, (1, 3): 9, (-1, 3): 8}.items()}
+    ps = {P(1, 1): 1, P(-1, 1): 1}
+    ws = {P(0, 0): 2, P(0, 2): 1}
+    la = ([(vs, False)], [(vs, False), (ws, False)])
+    lx = ([(vs, False), (ps, False)], [(vs, False), (ps, True)])
+    oa, ox = ostruct("U1xSU2", la), ostruct("U1xSU2", lx)
+    xa, xx = wl.normal(31, oa.numel), wl.normal(32, ox.numel)
+    spec = ((0, 2), (1,), (0,), (1, 2, 3), (0, 1, 2, 3, 4), ())
+    cs, ref = ops.contract(oa, xa, *spec[:2], ox, xx, *spec[2:], tier="block")
+    A, X = _lib_tmap(gctx, "U1xSU2", la), _lib_tmap(gctx, "U1xSU2", lx)
+    plan = api.contract_plan(gctx, A, *spec[:2], X, *spec[2:], gemm=gemm)
+    assert plan.output().blocks() == [(c, r, k, o) for c, r, k, o in cs.blocks]
+    ws_ = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
+    c = torch.full((plan.output().numel,), float("nan"), dtype=torch.float64, device="cuda")
+    api.contract(gctx, plan, _dev(xa), _dev(xx), c, ws_)
+    gctx.sync()
+    assert rel_frobenius_per_block(cs, c.cpu().numpy(), ref) <= tol
+
+
+@pytest.mark.parametrize("gemm,tol", [("fp64", FP64_TOL), ("ozaki", 1e-10)])
+def test_heff_chain_product_symmetry(gctx, gemm, tol):
+    """The two-site heff chain with U(1) x SU(2) (charge x spin) sectors, reduced virtual
+    dimension 256: every intermediate against the oracle block tier."""
+    from paper_2508_10076_gb300.chain import HeffChain
+    ch = HeffChain(gctx, "U1xSU2", 256, gemm=gemm, seed=3)
+    ref = oracle_heff("U1xSU2", 256, seed=3, tier="block")
+    t = ch.steps[0].run(ch.dev["L"], ch.dev["x"])
+    outs = [t]
+    for i, other in ((1, "W"), (2, "W"), (3, "R")):
+        t = ch.steps[i].run(t, ch.dev[other])
+        outs.append(t)
+    gctx.sync()
+    for i, ((cs, rd), b) in enumerate(zip(ref, outs)):
+        assert ch.steps[i].out.blocks() == [(c, r, k, o) for c, r, k, o in cs.blocks]
+        assert rel_frobenius_per_block(cs, b.cpu().numpy(), rd) <= tol, i

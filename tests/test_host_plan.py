@@ -12,6 +12,7 @@ import pytest
 
 from conftest import ROOT
 from oracle import SU2, U1, Z2, GradedSpace, TensorStructure
+from oracle.symmetry import U1xSU2, Z2xU1
 from oracle import ops, su2
 from paper_2508_10076_gb300 import api, build_library
 from paper_2508_10076_gb300._abi import SIGNATURES
@@ -56,6 +57,8 @@ def _same_structure(ost, lt):
         assert (off, ld, dims) == (p.offset, p.ld, p.dims)
 
 
+_P, _Q = U1xSU2.pair, Z2xU1.pair
+
 SPECS = [
     (SU2, ([({0: 1, 1: 1}, False)] * 2, [({0: 1, 1: 1}, False)] * 2)),
     (SU2, ([({0: 2, 1: 1, 2: 2}, False), ({1: 1}, False)], [({0: 1, 1: 2, 2: 1}, True), ({1: 1}, True)])),
@@ -65,6 +68,13 @@ SPECS = [
     (U1, ([({-2: 1, -1: 2, 0: 3, 1: 2, 2: 1}, False)] * 2, [({-2: 1, -1: 2, 0: 3, 1: 2, 2: 1}, False)] * 2)),
     (U1, ([({-1: 2, 1: 1}, True), ({0: 1, 2: 2}, False)], [({-1: 1, 1: 3, 3: 1}, False), ({1: 1, -1: 1}, True)])),
     (Z2, ([({0: 2, 1: 1}, False), ({0: 1, 1: 2}, True), ({1: 1}, False)], [({0: 3, 1: 1}, False)])),
+    # Deligne products: charge x spin (non-abelian) and parity x charge (abelian)
+    (U1xSU2, ([({_P(-1, 1): 1, _P(0, 0): 2, _P(1, 1): 1}, False), ({_P(1, 1): 1, _P(-1, 1): 1}, False)],
+              [({_P(0, 0): 1, _P(0, 2): 1, _P(1, 1): 1, _P(-1, 1): 1}, True), ({_P(1, 1): 1}, True)])),
+    (U1xSU2, ([({_P(0, 1): 2, _P(1, 0): 1}, True), ({_P(0, 1): 1, _P(1, 2): 1}, False), ({_P(-1, 1): 1}, False)],
+              [({_P(0, 0): 1, _P(0, 2): 1, _P(1, 1): 1}, False)])),
+    (Z2xU1, ([({_Q(0, -1): 1, _Q(1, 0): 2, _Q(0, 1): 1}, False), ({_Q(1, 1): 1, _Q(0, -1): 1}, True)],
+             [({_Q(1, 0): 1, _Q(0, 0): 2, _Q(1, 2): 1}, False), ({_Q(0, 1): 1}, True)])),
 ]
 
 

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from golden_io import matrix
+from oracle.symmetry import U1xSU2, Z2xU1
 from oracle import SU2, U1, Z2, GradedSpace, TensorStructure
 from oracle import ops
 from oracle.dense import embed, project
@@ -53,6 +54,11 @@ SMALL = [
     (U1, [({-2: 1, -1: 2, 0: 3, 1: 2, 2: 1}, False), ({-1: 1, 1: 1}, False)],
      [({-2: 1, -1: 2, 0: 3, 1: 2, 2: 1}, True), ({-1: 1, 1: 1}, True)]),
     (Z2, [({0: 2, 1: 3}, False), ({0: 1, 1: 2}, True)], [({0: 2, 1: 1}, False)]),
+    (U1xSU2, [({U1xSU2.pair(0, 0): 1, U1xSU2.pair(1, 1): 2}, False), ({U1xSU2.pair(-1, 1): 1}, True)],
+     [({U1xSU2.pair(0, 0): 1, U1xSU2.pair(0, 2): 1, U1xSU2.pair(2, 0): 1, U1xSU2.pair(1, 1): 1}, True),
+      ({U1xSU2.pair(0, 1): 1}, False)]),
+    (Z2xU1, [({Z2xU1.pair(0, 0): 2, Z2xU1.pair(1, 1): 1}, False), ({Z2xU1.pair(1, -1): 1}, True)],
+     [({Z2xU1.pair(0, 0): 1, Z2xU1.pair(1, 0): 2, Z2xU1.pair(0, 2): 1}, False)]),
 ]
 
 
@@ -232,3 +238,38 @@ def test_block_svd_matches_dense_spectrum_and_reconstructs():
     # the kept values are the largest: any discarded value of a sector is below every kept one of it
     for (c, _, s, _), k in zip(blocks, keep):
         assert np.all(s[:k][:, None] >= s[k:][None, :])
+
+
+def test_product_symmetry_contraction_dense_vs_block_and_bruteforce():
+    """U(1) x SU(2) (charge x spin, Sec. 5.2 product sectors): the block contraction (overlap-route
+    recoupling of Kronecker-product splitting tensors) equals the dense contraction, and the dense
+    result is a plain einsum of the dense operands."""
+    P = U1xSU2.pair
+    v = GradedSpace(U1xSU2, {P(-1, 1): 1, P(0, 0): 2, P(0, 2): 1, P(1, 1): 1})
+    p = GradedSpace(U1xSU2, {P(1, 1): 1})
+    w = GradedSpace(U1xSU2, {P(0, 0): 1, P(0, 2): 1})
+    L = TensorStructure([v], [v, w])
+    X = TensorStructure([v, p], [v, p.flip()])
+    rng = np.random.default_rng(5)
+    xl, xx = rng.standard_normal(L.numel), rng.standard_normal(X.numel)
+    args = (L, xl, (0, 2), (1,), X, xx, (0,), (1, 2, 3), (0, 1, 2, 3, 4), ())
+    cs1, y1 = ops.contract(*args, tier="dense")
+    cs2, y2 = ops.contract(*args, tier="block")
+    assert cs1.blocks == cs2.blocks
+    assert np.allclose(y1, y2, atol=1e-12)
+    dl, dx = embed(L, xl), embed(X, xx)
+    ref = np.einsum("abw,bpcq->awpcq", dl, dx)  # contract L's domain V with x's codomain V
+    assert np.allclose(embed(cs1, y1), ref, atol=1e-12)
+
+
+def test_product_splitting_tensors_orthonormal_complete():
+    """Kronecker-product splitting tensors of U(1) x SU(2) and Z2 x U(1) form an orthonormal basis
+    of a (x) b (d_a d_b = sum_c N_ab^c d_c), channel by channel."""
+    for sym, labels in ((U1xSU2, [U1xSU2.pair(q, t) for q in (-1, 0, 2) for t in (0, 1, 2, 3)]),
+                        (Z2xU1, [Z2xU1.pair(z, q) for z in (0, 1) for q in (-2, 0, 1)])):
+        for a, b in itertools.product(labels, labels):
+            cs = sym.fuse(a, b)
+            assert sym.dim(a) * sym.dim(b) == sum(sym.dim(c) for c in cs)
+            u = np.concatenate([sym.cg_tensor(a, b, c).reshape(sym.dim(a) * sym.dim(b), sym.dim(c)) for c in cs],
+                               axis=1)
+            assert np.allclose(u.T @ u, np.eye(u.shape[0]), atol=1e-14)

@@ -8,6 +8,7 @@ import pytest
 
 from golden_io import lines
 from oracle import SU2, U1, Z2, GradedSpace, TensorStructure
+from oracle.symmetry import ProductSymmetry, U1xSU2, Z2xU1
 from oracle.dense import embed
 from oracle.ops import permute_spaces
 
@@ -73,30 +74,37 @@ def test_block_rows_count_fusion_multiplicities():
 
 
 # ------------------------------------------------------------------ brute force invariants
-def _leg_generators(sym, sp):
-    """Lie-algebra (or group) generators acting on the dense basis of one leg."""
-    mats = []
+def _multiplet_generators(sym, a):
+    """[(matrix on the d_a-dim multiplet of sector a, kind)]: Lie generators ('lie') or group
+    elements ('group').  SU(2): J_z, J_+, J_- in the |j, m> basis (m ascending); U(1): the charge;
+    Z2: the parity; a Deligne product: each factor's generators on its tensor factor."""
+    if isinstance(sym, ProductSymmetry):
+        a1, a2 = sym.split(a)
+        d1, d2 = sym.s1.dim(a1), sym.s2.dim(a2)
+        return ([(np.kron(g, np.eye(d2)), k) for g, k in _multiplet_generators(sym.s1, a1)] +
+                [(np.kron(np.eye(d1), g), k) for g, k in _multiplet_generators(sym.s2, a2)])
     if sym is SU2:
-        blocks = {"z": [], "p": [], "m": []}
-        for a, n in sp.sectors.items():
-            d = a + 1
-            j = a / 2
-            ms = [(2 * i - a) / 2 for i in range(d)]
-            jz = np.diag(ms)
-            jp = np.zeros((d, d))
-            for i in range(d - 1):
-                jp[i + 1, i] = math.sqrt(j * (j + 1) - ms[i] * (ms[i] + 1))
-            for key, x in (("z", jz), ("p", jp), ("m", jp.T)):
-                blocks[key].append(np.kron(np.eye(n), x))
-        mats = [_blockdiag(blocks[k]) for k in ("z", "p", "m")]
-        kind = "lie"
-    elif sym is U1:
-        mats = [np.diag([float(a) for a, n in sp.sectors.items() for _ in range(n)])]
-        kind = "lie"
-    else:
-        mats = [np.diag([(-1.0) ** a for a, n in sp.sectors.items() for _ in range(n)])]
-        kind = "group"
-    return mats, kind
+        d = a + 1
+        j = a / 2
+        ms = [(2 * i - a) / 2 for i in range(d)]
+        jp = np.zeros((d, d))
+        for i in range(d - 1):
+            jp[i + 1, i] = math.sqrt(j * (j + 1) - ms[i] * (ms[i] + 1))
+        return [(np.diag(ms), "lie"), (jp, "lie"), (jp.T, "lie")]
+    if sym is U1:
+        return [(np.array([[float(a)]]), "lie")]
+    return [(np.array([[(-1.0) ** a]]), "group")]
+
+
+def _leg_generators(sym, sp):
+    """[(generator on the dense basis of one leg, kind)], block diagonal over its sectors."""
+    per = {a: _multiplet_generators(sym, a) for a in sp.sectors}
+    ngen = len(next(iter(per.values())))
+    out = []
+    for g in range(ngen):
+        blocks = [np.kron(np.eye(n), per[a][g][0]) for a, n in sp.sectors.items()]
+        out.append((_blockdiag(blocks), per[next(iter(per))][g][1]))
+    return out
 
 
 def _blockdiag(ms):
@@ -114,30 +122,32 @@ def _total_generators(struct):
     """Generators of the symmetry on the tensor space V_1 (x) .. (x) W_1* (x) .. ."""
     legs = []
     for i, sp in enumerate(struct.spaces()):
-        mats, kind = _leg_generators(struct.sym, sp)
+        gens = _leg_generators(struct.sym, sp)
         in_domain = i >= len(struct.cod)
         dualized = sp.dual != in_domain          # acts through the contragredient
         if dualized:
-            mats = [(-m.T if kind == "lie" else np.linalg.inv(m).T) for m in mats]
-        legs.append(mats)
+            gens = [((-m.T if kind == "lie" else np.linalg.inv(m).T), kind) for m, kind in gens]
+        legs.append(gens)
     dims = [sp.dim for sp in struct.spaces()]
     total = []
     for g in range(len(legs[0])):
-        if _leg_generators(struct.sym, struct.spaces()[0])[1] == "lie":
+        if legs[0][g][1] == "lie":
             acc = np.zeros((math.prod(dims),) * 2)
             for i in range(len(dims)):
                 op = np.array([[1.0]])
                 for k in range(len(dims)):
-                    op = np.kron(op, legs[k][g] if k == i else np.eye(dims[k]))
+                    op = np.kron(op, legs[k][g][0] if k == i else np.eye(dims[k]))
                 acc += op
             total.append(acc)
         else:
             op = np.array([[1.0]])
             for k in range(len(dims)):
-                op = np.kron(op, legs[k][g])
+                op = np.kron(op, legs[k][g][0])
             total.append(op - np.eye(op.shape[0]))
     return total
 
+
+_P, _Q = U1xSU2.pair, Z2xU1.pair
 
 CASES = [
     (SU2, [({0: 1, 1: 1}, False), ({0: 1, 1: 1}, False)], [({0: 1, 1: 1}, False), ({0: 1, 1: 1}, False)]),
@@ -145,6 +155,10 @@ CASES = [
     (SU2, [({0: 1, 1: 1, 2: 1}, True)], [({1: 1}, False), ({0: 2, 2: 1}, False), ({1: 1}, True)]),
     (U1, [({-1: 1, 0: 2, 1: 1}, False), ({-1: 1, 1: 2}, True)], [({0: 1, 2: 1, -2: 1}, False)]),
     (Z2, [({0: 2, 1: 1}, False), ({0: 1, 1: 1}, True)], [({0: 1, 1: 2}, True), ({1: 1}, False)]),
+    (U1xSU2, [({_P(0, 0): 1, _P(1, 1): 1}, False), ({_P(-1, 1): 1, _P(1, 1): 1}, True)],
+     [({_P(0, 0): 1, _P(0, 2): 1, _P(2, 0): 1}, False)]),
+    (Z2xU1, [({_Q(0, 0): 1, _Q(1, 1): 2}, False), ({_Q(1, -1): 1, _Q(0, 1): 1}, True)],
+     [({_Q(1, 0): 1, _Q(0, 2): 1, _Q(1, 2): 1}, True)]),
 ]
 
 
