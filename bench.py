@@ -122,7 +122,7 @@ def _workload(ctx, name, gemm, dtype="f64", seed=0):
     cfg = wl.CONFIGS[name]
     if cfg["kind"] in ("heff", "heff1"):
         return HeffChain(ctx, cfg["sym"], cfg["D"], gemm=gemm, dtype=dtype, seed=seed,
-                         sites=2 if cfg["kind"] == "heff" else 1)
+                         sites=2 if cfg["kind"] == "heff" else 1, mpo=cfg.get("mpo"))
     if cfg["kind"] == "lx":
         return LxContraction(ctx, cfg["sym"], cfg["D"], gemm=gemm, dtype=dtype, seed=seed)
     raise SystemExit(f"config {name} is a parity case, not a bench line")
@@ -144,7 +144,7 @@ def cpu_baseline(name, budget_s=15.0):
     cfg = wl.CONFIGS[name]
     if cfg["kind"] in ("heff", "heff1"):
         sites = 2 if cfg["kind"] == "heff" else 1
-        run = lambda: oracle_heff(cfg["sym"], cfg["D"], tier="block", sites=sites)  # noqa: E731
+        run = lambda: oracle_heff(cfg["sym"], cfg["D"], tier="block", sites=sites, mpo=cfg.get("mpo"))  # noqa: E731
         flops = None
     else:
         st, data = oracle_heff_inputs(cfg["sym"], cfg["D"])

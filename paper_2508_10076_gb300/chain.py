@@ -83,7 +83,7 @@ class HeffChain:
     x' = ((L x) W) R (Algorithm 11), with all intermediates resident on the device."""
 
     def __init__(self, ctx, sym="U1", D=1024, gemm="fp64", slices=0, seed=0, device="cuda",
-                 dtype="f64", sites=2):
+                 dtype="f64", sites=2, mpo=None):
         self.ctx, self.sym, self.D, self.sites = ctx, sym, D, sites
         V, P, W = wl.heff_spaces(sym, D)
         self.sectors = (V, P, W)
@@ -96,6 +96,11 @@ class HeffChain:
             self.host[k] = rnd(seed * 16 + i, self.tm[k].numel)
         if sym == "U1":
             w = mpo_data(self.tm["W"], wl.xxz_mpo_entries(), self.tm["W"].numel)
+            self.host["W"] = w.astype(np.complex128) if dtype == "c128" else w
+        elif mpo == "heisenberg":  # SU(2) Heisenberg MPO (stored reduced entries)
+            if sym != "SU2" or self.tm["W"].numel != len(wl.HEISENBERG_SU2_MPO):
+                raise ValueError("the Heisenberg MPO is defined for the SU(2) workload spaces")
+            w = np.array(wl.HEISENBERG_SU2_MPO, dtype=np.float64)
             self.host["W"] = w.astype(np.complex128) if dtype == "c128" else w
         else:
             self.host["W"] = rnd(seed * 16 + 3, self.tm["W"].numel)

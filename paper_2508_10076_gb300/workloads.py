@@ -80,6 +80,12 @@ U1_MPO = {-2: 1, 0: 3, 2: 1}     # XXZ bond space
 SU2_PHYS = {1: 1}                # j = 1/2
 SU2_MPO = {0: 2, 2: 1}           # 2 (0) (+) (1), the Heisenberg bond of Sec. 6.1
 
+# SU(2) Heisenberg MPO (J = 1) on W : W (x) P <- P (x) W with W = 2 (0) (+) (1), P = (1/2): its
+# ten reduced entries in storage order, as written to tests/golden/heisenberg_su2_mpo.txt by
+# tests/golden/make_heisenberg_su2_mpo.py (the oracle's projection of the dense lower-triangular
+# MPO with identity, spin-vector and J S.S channels).
+HEISENBERG_SU2_MPO = (1.0, 0.0, -0.8660254037844386, 0.0, 1.0, 0.0, 0.0, 0.8660254037844386, 0.0, 0.0)
+
 # bond state b of the XXZ MPO -> (charge, outer index); states 0 (identity before), 3 (S_z),
 # 4 (identity after) share charge 0; 1 carries S+, 2 carries S-.
 _BOND = {0: (0, 0), 1: (-2, 0), 2: (2, 0), 3: (0, 1), 4: (0, 2)}
@@ -194,4 +200,5 @@ CONFIGS = {
     "c5_su2_heff1_n1024": dict(sym="SU2", D=1024, kind="heff1"),
     "c3_su2_lx_n1024": dict(sym="SU2", D=1024, kind="lx"),
     "c6_u1su2_heff_n2048": dict(sym="U1xSU2", D=2048, kind="heff"),
+    "c7_su2_heisenberg_heff_n1024": dict(sym="SU2", D=1024, kind="heff", mpo="heisenberg"),
 }

@@ -1,8 +1,11 @@
-"""Oracle-side construction of the seeded workloads (tests only)."""
+"""Oracle-side construction of the seeded workloads and symmetry generators (tests only)."""
+
+import math
 
 import numpy as np
 
-from oracle import GradedSpace, TensorStructure, sym_from_name
+from oracle import SU2, U1, GradedSpace, TensorStructure, sym_from_name
+from oracle.symmetry import ProductSymmetry
 from oracle import ops
 from paper_2508_10076_gb300 import workloads as wl
 
@@ -29,7 +32,7 @@ def oracle_mpo(struct, entries):
     return data
 
 
-def oracle_heff_inputs(sym, D, seed=0, dtype="f64", sites=2):
+def oracle_heff_inputs(sym, D, seed=0, dtype="f64", sites=2, mpo=None):
     V, P, W = wl.heff_spaces(sym, D)
     legs = wl.heff_legs(V, P, W) if sites == 2 else wl.heff1_legs(V, P, W)
     st = {k: ostruct(sym, legs[k]) for k in ("x", "L", "W", "R")}
@@ -39,15 +42,17 @@ def oracle_heff_inputs(sym, D, seed=0, dtype="f64", sites=2):
         data["W"] = oracle_mpo(st["W"], wl.xxz_mpo_entries())
         if dtype == "c128":
             data["W"] = data["W"].astype(np.complex128)
+    elif mpo == "heisenberg":
+        data["W"] = np.array(wl.HEISENBERG_SU2_MPO, dtype=np.complex128 if dtype == "c128" else np.float64)
     else:
         data["W"] = rnd(seed * 16 + 3, st["W"].numel)
     return st, data
 
 
-def oracle_heff(sym, D, seed=0, tier="block", dtype="f64", steps=None, sites=2):
+def oracle_heff(sym, D, seed=0, tier="block", dtype="f64", steps=None, sites=2, mpo=None):
     """[(structure, data)] of every intermediate and x' computed by the oracle: the two-site chain
     (T1, T2, T3, x'; Algorithm 12) or with sites=1 the single-site chain (T1, T2, x'; Algorithm 11)."""
-    st, data = oracle_heff_inputs(sym, D, seed, dtype, sites)
+    st, data = oracle_heff_inputs(sym, D, seed, dtype, sites, mpo)
     specs = wl.HEFF_SPECS if sites == 2 else wl.HEFF1_SPECS
     others = ("L", "W", "W", "R") if sites == 2 else ("L", "W", "R")
     out = []
@@ -79,3 +84,77 @@ def rel_frobenius_per_block(struct, got, ref):
         den = nf if nf > 1e-13 * total else total
         worst = max(worst, float(np.linalg.norm(g - f) / den))
     return worst
+
+
+# ---------------------------------------------------------------- symmetry generators (pins)
+def _multiplet_generators(sym, a):
+    """[(matrix on the d_a-dim multiplet of sector a, kind)]: Lie generators ('lie') or group
+    elements ('group').  SU(2): J_z, J_+, J_- in the |j, m> basis (m ascending); U(1): the charge;
+    Z2: the parity; a Deligne product: each factor's generators on its tensor factor."""
+    if isinstance(sym, ProductSymmetry):
+        a1, a2 = sym.split(a)
+        d1, d2 = sym.s1.dim(a1), sym.s2.dim(a2)
+        return ([(np.kron(g, np.eye(d2)), k) for g, k in _multiplet_generators(sym.s1, a1)] +
+                [(np.kron(np.eye(d1), g), k) for g, k in _multiplet_generators(sym.s2, a2)])
+    if sym is SU2:
+        d = a + 1
+        j = a / 2
+        ms = [(2 * i - a) / 2 for i in range(d)]
+        jp = np.zeros((d, d))
+        for i in range(d - 1):
+            jp[i + 1, i] = math.sqrt(j * (j + 1) - ms[i] * (ms[i] + 1))
+        return [(np.diag(ms), "lie"), (jp, "lie"), (jp.T, "lie")]
+    if sym is U1:
+        return [(np.array([[float(a)]]), "lie")]
+    return [(np.array([[(-1.0) ** a]]), "group")]
+
+
+def _leg_generators(sym, sp):
+    """[(generator on the dense basis of one leg, kind)], block diagonal over its sectors."""
+    per = {a: _multiplet_generators(sym, a) for a in sp.sectors}
+    ngen = len(next(iter(per.values())))
+    out = []
+    for g in range(ngen):
+        blocks = [np.kron(np.eye(n), per[a][g][0]) for a, n in sp.sectors.items()]
+        out.append((_blockdiag(blocks), per[next(iter(per))][g][1]))
+    return out
+
+
+def _blockdiag(ms):
+    n = sum(m.shape[0] for m in ms)
+    out = np.zeros((n, n))
+    o = 0
+    for m in ms:
+        k = m.shape[0]
+        out[o:o + k, o:o + k] = m
+        o += k
+    return out
+
+
+def total_generators(struct):
+    """Generators of the symmetry on the tensor space V_1 (x) .. (x) W_1* (x) .. ."""
+    legs = []
+    for i, sp in enumerate(struct.spaces()):
+        gens = _leg_generators(struct.sym, sp)
+        in_domain = i >= len(struct.cod)
+        dualized = sp.dual != in_domain          # acts through the contragredient
+        if dualized:
+            gens = [((-m.T if kind == "lie" else np.linalg.inv(m).T), kind) for m, kind in gens]
+        legs.append(gens)
+    dims = [sp.dim for sp in struct.spaces()]
+    total = []
+    for g in range(len(legs[0])):
+        if legs[0][g][1] == "lie":
+            acc = np.zeros((math.prod(dims),) * 2)
+            for i in range(len(dims)):
+                op = np.array([[1.0]])
+                for k in range(len(dims)):
+                    op = np.kron(op, legs[k][g][0] if k == i else np.eye(dims[k]))
+                acc += op
+            total.append(acc)
+        else:
+            op = np.array([[1.0]])
+            for k in range(len(dims)):
+                op = np.kron(op, legs[k][g][0])
+            total.append(op - np.eye(op.shape[0]))
+    return total

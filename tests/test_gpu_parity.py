@@ -386,3 +386,21 @@ def test_heff_chain_product_symmetry(gctx, gemm, tol):
     for i, ((cs, rd), b) in enumerate(zip(ref, outs)):
         assert ch.steps[i].out.blocks() == [(c, r, k, o) for c, r, k, o in cs.blocks]
         assert rel_frobenius_per_block(cs, b.cpu().numpy(), rd) <= tol, i
+
+
+@pytest.mark.parametrize("gemm,tol", [("fp64", FP64_TOL), ("ozaki", 1e-10)])
+def test_heff_chain_su2_heisenberg(gctx, gemm, tol):
+    """The SU(2) two-site heff chain with the Heisenberg MPO (stored reduced entries, pinned
+    against the oracle's projection of the dense MPO): every intermediate against the oracle."""
+    from paper_2508_10076_gb300.chain import HeffChain
+    ch = HeffChain(gctx, "SU2", 256, gemm=gemm, seed=4, mpo="heisenberg")
+    ref = oracle_heff("SU2", 256, seed=4, tier="block", mpo="heisenberg")
+    t = ch.steps[0].run(ch.dev["L"], ch.dev["x"])
+    outs = [t]
+    for i, other in ((1, "W"), (2, "W"), (3, "R")):
+        t = ch.steps[i].run(t, ch.dev[other])
+        outs.append(t)
+    gctx.sync()
+    for i, ((cs, rd), b) in enumerate(zip(ref, outs)):
+        assert ch.steps[i].out.blocks() == [(c, r, k, o) for c, r, k, o in cs.blocks]
+        assert rel_frobenius_per_block(cs, b.cpu().numpy(), rd) <= tol, i

@@ -8,7 +8,8 @@ import pytest
 
 from golden_io import lines
 from oracle import SU2, U1, Z2, GradedSpace, TensorStructure
-from oracle.symmetry import ProductSymmetry, U1xSU2, Z2xU1
+from oracle.symmetry import U1xSU2, Z2xU1
+from harness import total_generators
 from oracle.dense import embed
 from oracle.ops import permute_spaces
 
@@ -74,79 +75,6 @@ def test_block_rows_count_fusion_multiplicities():
 
 
 # ------------------------------------------------------------------ brute force invariants
-def _multiplet_generators(sym, a):
-    """[(matrix on the d_a-dim multiplet of sector a, kind)]: Lie generators ('lie') or group
-    elements ('group').  SU(2): J_z, J_+, J_- in the |j, m> basis (m ascending); U(1): the charge;
-    Z2: the parity; a Deligne product: each factor's generators on its tensor factor."""
-    if isinstance(sym, ProductSymmetry):
-        a1, a2 = sym.split(a)
-        d1, d2 = sym.s1.dim(a1), sym.s2.dim(a2)
-        return ([(np.kron(g, np.eye(d2)), k) for g, k in _multiplet_generators(sym.s1, a1)] +
-                [(np.kron(np.eye(d1), g), k) for g, k in _multiplet_generators(sym.s2, a2)])
-    if sym is SU2:
-        d = a + 1
-        j = a / 2
-        ms = [(2 * i - a) / 2 for i in range(d)]
-        jp = np.zeros((d, d))
-        for i in range(d - 1):
-            jp[i + 1, i] = math.sqrt(j * (j + 1) - ms[i] * (ms[i] + 1))
-        return [(np.diag(ms), "lie"), (jp, "lie"), (jp.T, "lie")]
-    if sym is U1:
-        return [(np.array([[float(a)]]), "lie")]
-    return [(np.array([[(-1.0) ** a]]), "group")]
-
-
-def _leg_generators(sym, sp):
-    """[(generator on the dense basis of one leg, kind)], block diagonal over its sectors."""
-    per = {a: _multiplet_generators(sym, a) for a in sp.sectors}
-    ngen = len(next(iter(per.values())))
-    out = []
-    for g in range(ngen):
-        blocks = [np.kron(np.eye(n), per[a][g][0]) for a, n in sp.sectors.items()]
-        out.append((_blockdiag(blocks), per[next(iter(per))][g][1]))
-    return out
-
-
-def _blockdiag(ms):
-    n = sum(m.shape[0] for m in ms)
-    out = np.zeros((n, n))
-    o = 0
-    for m in ms:
-        k = m.shape[0]
-        out[o:o + k, o:o + k] = m
-        o += k
-    return out
-
-
-def _total_generators(struct):
-    """Generators of the symmetry on the tensor space V_1 (x) .. (x) W_1* (x) .. ."""
-    legs = []
-    for i, sp in enumerate(struct.spaces()):
-        gens = _leg_generators(struct.sym, sp)
-        in_domain = i >= len(struct.cod)
-        dualized = sp.dual != in_domain          # acts through the contragredient
-        if dualized:
-            gens = [((-m.T if kind == "lie" else np.linalg.inv(m).T), kind) for m, kind in gens]
-        legs.append(gens)
-    dims = [sp.dim for sp in struct.spaces()]
-    total = []
-    for g in range(len(legs[0])):
-        if legs[0][g][1] == "lie":
-            acc = np.zeros((math.prod(dims),) * 2)
-            for i in range(len(dims)):
-                op = np.array([[1.0]])
-                for k in range(len(dims)):
-                    op = np.kron(op, legs[k][g][0] if k == i else np.eye(dims[k]))
-                acc += op
-            total.append(acc)
-        else:
-            op = np.array([[1.0]])
-            for k in range(len(dims)):
-                op = np.kron(op, legs[k][g][0])
-            total.append(op - np.eye(op.shape[0]))
-    return total
-
-
 _P, _Q = U1xSU2.pair, Z2xU1.pair
 
 CASES = [
@@ -168,7 +96,7 @@ def test_numel_equals_invariant_subspace_dimension(case):
     the dense embedding maps onto it (Schur's lemma / Wigner-Eckart, Sec. 3.1 and 4.1)."""
     sym, cod, dom = CASES[case]
     st = TensorStructure([GradedSpace(sym, s, d) for s, d in cod], [GradedSpace(sym, s, d) for s, d in dom])
-    gens = np.concatenate(_total_generators(st), axis=0)
+    gens = np.concatenate(total_generators(st), axis=0)
     sv = np.linalg.svd(gens, compute_uv=False)
     n = math.prod(sp.dim for sp in st.spaces())
     null_dim = n - int(np.sum(sv > 1e-9))
