@@ -384,13 +384,18 @@ def run_ours(args):
     if args.serve_requests > 0:
         from paper_2508_10076_gb300.serve import Server, calibrated_rate, request_stream
         reqs = request_stream(args.serve_requests, seed=1000 + replica_seed(rank))
-        server = Server(ctx, budget_bytes=150 << 30)
+        server = Server(ctx, budget_bytes=150 << 30, split_gemm=None if args.serve_fp64 else "ozaki")
         for r in reqs:
             server.shape(r["sym"], r["D"], r["dtype"])
         rate, mean_s = calibrated_rate(server, reqs, load=args.serve_load)
         server.run(reqs[:200], rate)  # warm-up pass (allocator, first launches)
         _, serve, _ = server.run(reqs, rate)
         serve["p99_ms"] = max_over_ranks(dist, serve["p99_ms"])
+        solo = sorted(k for k, sh in server.shapes.items() if sh.solo)
+        serve.update({"precision": "FP64 (complex128) in packed batches; shapes whose FP64 service alone is >= 1 ms and "
+                      "faster in Ozaki BF16 (s = 6, <= 1e-10) are served one by one in that mode"
+                      if not args.serve_fp64 else "FP64 (complex128) in packed batches",
+                      "split_precision_shapes": len(solo), "shapes": len(server.shapes)})
         serve.update({"load": args.serve_load, "mean_service_ms_alone": 1e3 * mean_s,
                       "budget_gb": 150, "mix": "U(1) L.x at D / SU(2) L.x at D/4, D log-uniform 64-4096 "
                       "(25-level grid), half complex128, Poisson arrivals"})
@@ -463,6 +468,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=10000, help="serving requests (0: skip serving)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic work lists")
     ap.add_argument("--serve-load", type=float, default=0.7, help="offered load relative to alone service time")
+    ap.add_argument("--serve-fp64", action="store_true", help="serve every request in FP64 (no split-precision solo path)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -149,14 +149,17 @@ int tk_tmap_treepair(const tk_tmap* t, int64_t i, int32_t* labels, int64_t* offs
  * so creating the same plan twice is cheap. */
 int tk_permute_plan(tk_ctx* ctx, const tk_tmap* a, int np, const int* p, int nq, const int* q,
                     int dtype, tk_plan** out);
-/* Algorithm 4: A~ = permute(A, (pa, qa)), B~ = permute(B, (pb, qb)), C~ = A~ o B~,
- * C = permute(C~, (pab, qab)).  (pab, qab) index the legs of C~ = codomain(A~) then domain(B~).
- * gemm_mode is TK_GEMM_*; slices is the number of BF16 slices per operand for
- * TK_GEMM_OZAKI_BF16 (0 = default), ignored otherwise. */
 /* Adjoint t^dagger : dom <- cod of t : cod <- dom (Sec. 2; conjugate for complex data).  With
  * the orthonormal canonical trees, block c of the result is the conjugate transpose of block c of
  * t.  The result is a permute-kind plan: run it with tk_permute, inspect it with tk_plan_output. */
 int tk_adjoint_plan(tk_ctx* ctx, const tk_tmap* a, int dtype, tk_plan** out);
+/* Algorithm 4: A~ = permute(A, (pa, qa)), B~ = permute(B, (pb, qb)), C~ = A~ o B~,
+ * C = permute(C~, (pab, qab)).  (pab, qab) index the legs of C~ = codomain(A~) then domain(B~).
+ * gemm_mode is TK_GEMM_*; slices is the number of BF16 slices per operand for
+ * TK_GEMM_OZAKI_BF16 (0 = default), ignored otherwise.  Complex data (TK_C128) in a
+ * split-precision mode runs as the four real products Re A Re B, Im A Im B, Re A Im B, Im A Re B
+ * (the recoupling coefficients are real) on de-interleaved copies in the workspace, combined as
+ * (RR - II) + i (RI + IR). */
 int tk_contract_plan(tk_ctx* ctx, const tk_tmap* a, int npa, const int* pa, int nqa, const int* qa,
                      const tk_tmap* b, int npb, const int* pb, int nqb, const int* qb,
                      int npab, const int* pab, int nqab, const int* qab, int dtype, int gemm_mode,

@@ -375,8 +375,6 @@ int tk_contract_plan(tk_ctx* ctx, const tk_tmap* a, int npa, const int* pa, int 
   *out = nullptr;
   if (dtype != TK_F64 && dtype != TK_C128) return fail(ctx, TK_ERR_ARG, "unknown dtype");
   if (gemm_mode < TK_GEMM_FP64 || gemm_mode > TK_GEMM_TF32X3) return fail(ctx, TK_ERR_ARG, "unknown gemm mode");
-  if (gemm_mode != TK_GEMM_FP64 && dtype != TK_F64)
-    return fail(ctx, TK_ERR_UNSUPPORTED, "split-precision GEMMs take real FP64 tensors");
   if (slices < 0 || slices > 8) return fail(ctx, TK_ERR_ARG, "slices must be in [0, 8]");
   std::vector<int> vpa, vqa, vpb, vqb, vpab, vqab;
   if (!read_perm(npa, pa, nqa, qa, vpa, vqa) || npa + nqa != a->st->nleg() ||
@@ -416,7 +414,7 @@ size_t tk_plan_workspace_bytes(const tk_plan* plan) {
   if (!plan) return 0;
   if (plan->kind == 2) return plan->svd->ws_total;
   if (plan->kind != 1) return 0;
-  return plan->con->ws_total;
+  return tk::contract_ws_bytes(*plan->con);
 }
 
 double tk_plan_flops(const tk_plan* plan) {
@@ -426,20 +424,21 @@ double tk_plan_flops(const tk_plan* plan) {
 
 double tk_plan_tensor_flops(const tk_plan* plan) {
   if (!plan || plan->kind != 1) return 0.0;
+  const tk::ContractPlan& cp = plan->con->re ? *plan->con->re : *plan->con;
   double f = 0;
-  for (const tk::GemmItem& g : plan->con->gemms_oz) f += 2.0 * (double)g.M * (double)g.N * (double)g.K;
-  return f;
+  for (const tk::GemmItem& g : cp.gemms_oz) f += 2.0 * (double)g.M * (double)g.N * (double)g.K;
+  return plan->con->re ? 4.0 * f : f;  // a complex plan runs four real products
 }
 
 double tk_plan_permute_bytes(const tk_plan* plan) {
   if (!plan) return 0.0;
   if (plan->kind == 0) return plan->perm->identity ? 0.0 : plan->perm->bytes;
   double b = 0;
-  const auto& c = *plan->con;
+  const auto& c = plan->con->re ? *plan->con->re : *plan->con;
   if (!c.pa->identity) b += c.pa->bytes;
   if (!c.pb->identity) b += c.pb->bytes;
   if (c.pc) b += c.pc->bytes;
-  return b;
+  return plan->con->re ? 4.0 * b : b;  // a complex plan runs four real products
 }
 
 static const tk::PermutePlan* which_perm(const tk_plan* plan, int which) {
@@ -511,7 +510,8 @@ int tk_contract(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, 
   if (!ctx || !plan || plan->kind != 1) return fail(ctx, TK_ERR_ARG, "not a contraction plan");
   if (!a || !b || !c) return fail(ctx, TK_ERR_ARG, "null buffer");
   const tk::ContractPlan& cp = *plan->con;
-  if (workspace_bytes < cp.ws_total || (cp.ws_total > 0 && !workspace))
+  const size_t need = tk::contract_ws_bytes(cp);
+  if (workspace_bytes < need || (need > 0 && !workspace))
     return fail(ctx, TK_ERR_WORKSPACE, "workspace smaller than tk_plan_workspace_bytes()");
   int rc = set_device(ctx);
   if (rc != TK_OK) return rc;
@@ -540,13 +540,9 @@ int tk_contract_batch(tk_ctx* ctx, int n, const tk_plan* const* plans, const voi
   return tk::run_contract_batch(&ctx->c, n, cps.data(), a, b, c, workspace, stream);
 }
 
-int tk_plan_autotune(tk_ctx* ctx, tk_plan* plan, const void* a, const void* b, void* c, void* workspace,
-                     size_t workspace_bytes, void* stream, int* choice) {
-  if (!ctx || !plan || plan->kind != 1) return fail(ctx, TK_ERR_ARG, "not a contraction plan");
-  if (!a || !b || !c || !workspace) return fail(ctx, TK_ERR_ARG, "null buffer");
-  int rc = set_device(ctx);
-  if (rc != TK_OK) return rc;
-  tk::ContractPlan& cp = *plan->con;
+static int autotune_contract(tk_ctx* ctx, tk::ContractPlan& cp, const void* a, const void* b, void* c,
+                             void* workspace, size_t workspace_bytes, void* stream, int* choice) {
+  int rc = TK_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(ctx, TK_ERR_CUDA, "stream synchronize failed");
   cudaEvent_t e0, e1;
@@ -611,6 +607,28 @@ int tk_plan_autotune(tk_ctx* ctx, tk_plan* plan, const void* a, const void* b, v
   if (rc2 != TK_OK) return fail(ctx, rc2, "rebuilding the chosen work lists failed");
   if (choice) *choice = best_i * 8 + best_j;
   return TK_OK;
+}
+
+int tk_plan_autotune(tk_ctx* ctx, tk_plan* plan, const void* a, const void* b, void* c, void* workspace,
+                     size_t workspace_bytes, void* stream, int* choice) {
+  if (!ctx || !plan || plan->kind != 1) return fail(ctx, TK_ERR_ARG, "not a contraction plan");
+  if (!a || !b || !c || !workspace) return fail(ctx, TK_ERR_ARG, "null buffer");
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  tk::ContractPlan& cp = *plan->con;
+  if (!cp.re) return autotune_contract(ctx, cp, a, b, c, workspace, workspace_bytes, stream, choice);
+  // complex split precision: one full run leaves Re A and Re B in the workspace; the real plan
+  // is tuned on them (its result buffer is the first real product's), then the total is resized
+  if (workspace_bytes < tk::contract_ws_bytes(cp))
+    return fail(ctx, TK_ERR_WORKSPACE, "workspace smaller than tk_plan_workspace_bytes()");
+  if ((rc = tk::run_contract(&ctx->c, cp, a, b, c, workspace, stream)) != TK_OK) return fail(ctx, rc, "autotuning run failed");
+  char* w = (char*)workspace;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const void* ar = w;
+  const void* br = w + 2 * al((size_t)cp.cx_na * 8);
+  void* t0 = w + 2 * al((size_t)cp.cx_na * 8) + 2 * al((size_t)cp.cx_nb * 8);
+  rc = autotune_contract(ctx, *cp.re, ar, br, t0, w + cp.ws_cx, workspace_bytes - cp.ws_cx, stream, choice);
+  return rc;
 }
 
 int tk_svd_plan(tk_ctx* ctx, const tk_tmap* a, int dtype, tk_plan** out) {

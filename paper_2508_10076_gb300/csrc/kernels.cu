@@ -1177,8 +1177,85 @@ int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream) {
   return check_launch(ctx, "k_zero");
 }
 
+namespace {
+// Complex operands of a split-precision plan: real and imaginary parts into separate arrays, and
+// the four real products back into one complex result.
+__global__ void k_cx_split(const double2* __restrict__ a, double* __restrict__ ar, double* __restrict__ ai,
+                           int64_t na, const double2* __restrict__ b, double* __restrict__ br,
+                           double* __restrict__ bi, int64_t nb) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < na + nb; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < na) {
+      const double2 v = a[i];
+      ar[i] = v.x;
+      ai[i] = v.y;
+    } else {
+      const double2 v = b[i - na];
+      br[i - na] = v.x;
+      bi[i - na] = v.y;
+    }
+  }
+}
+// c = (rr - ii) + i (ri + ir)
+__global__ void k_cx_join(const double* __restrict__ rr, const double* __restrict__ ii,
+                          const double* __restrict__ ri, const double* __restrict__ ir, double2* __restrict__ c,
+                          int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    c[k] = make_double2(rr[k] - ii[k], ri[k] + ir[k]);
+}
+}  // namespace
+
+// Workspace of a complex split-precision plan: Re A | Im A | Re B | Im B | four real results |
+// the real plan's workspace.
+struct CxLayout {
+  double *ar, *ai, *br, *bi, *t[4];
+  char* ws_re;
+};
+static CxLayout cx_layout(const ContractPlan& cp, void* ws) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  char* w = (char*)ws;
+  CxLayout L;
+  L.ar = (double*)w;
+  w += al((size_t)cp.cx_na * 8);
+  L.ai = (double*)w;
+  w += al((size_t)cp.cx_na * 8);
+  L.br = (double*)w;
+  w += al((size_t)cp.cx_nb * 8);
+  L.bi = (double*)w;
+  w += al((size_t)cp.cx_nb * 8);
+  for (int k = 0; k < 4; ++k) {
+    L.t[k] = (double*)w;
+    w += al((size_t)cp.cx_nc * 8);
+  }
+  L.ws_re = w;
+  return L;
+}
+
+int run_contract_cx_split(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
+                          void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const CxLayout L = cx_layout(cp, ws);
+  const int64_t nab = cp.cx_na + cp.cx_nb;
+  const unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nab + 255) / 256, (int64_t)ctx->num_sms * 16));
+  {
+    ProfScope prof(ctx, "k_cx_split", stream);
+    k_cx_split<<<g1, 256, 0, s>>>((const double2*)a, L.ar, L.ai, cp.cx_na, (const double2*)b, L.br, L.bi, cp.cx_nb);
+    int rc = check_launch(ctx, "k_cx_split");
+    if (rc != TK_OK) return rc;
+  }
+  const double* ops[4][2] = {{L.ar, L.br}, {L.ai, L.bi}, {L.ar, L.bi}, {L.ai, L.br}};
+  for (int k = 0; k < 4; ++k) {
+    int rc = run_contract(ctx, *cp.re, ops[k][0], ops[k][1], L.t[k], L.ws_re, stream);
+    if (rc != TK_OK) return rc;
+  }
+  const unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cp.cx_nc + 255) / 256, (int64_t)ctx->num_sms * 16));
+  ProfScope prof(ctx, "k_cx_join", stream);
+  k_cx_join<<<g2, 256, 0, s>>>(L.t[0], L.t[1], L.t[2], L.t[3], (double2*)c, cp.cx_nc);
+  return check_launch(ctx, "k_cx_join");
+}
+
 int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
                  void* stream) {
+  if (cp.re) return run_contract_cx_split(ctx, cp, a, b, c, ws, stream);
   char* w = (char*)ws;
   const void* at = cp.pa->identity ? a : (const void*)(w + cp.ws_at);
   const void* bt = cp.pb->identity ? b : (const void*)(w + cp.ws_bt);

@@ -81,8 +81,8 @@ extern "C" int tk_contract_noalloc(tk_ctx* ctx, const tk_plan* plan, const void*
     return TK_ERR_NO_DEVICE;
   }
   const tk::ContractPlan& cp = *plan->con;
-  if (cp.ws_total > kNoallocScratchBytes) {
-    ctx->c.last_error = "plan needs " + std::to_string(cp.ws_total) +
+  if (tk::contract_ws_bytes(cp) > kNoallocScratchBytes) {
+    ctx->c.last_error = "plan needs " + std::to_string(tk::contract_ws_bytes(cp)) +
                         " bytes of scratch; tk_contract_noalloc has " + std::to_string(kNoallocScratchBytes) +
                         " (use tk_contract with a caller-allocated workspace)";
     return TK_ERR_WORKSPACE;

@@ -597,8 +597,32 @@ std::shared_ptr<ContractPlan> make_contract_plan(Ctx* ctx, std::shared_ptr<Struc
                                                  const std::vector<int>& qab, int dtype,
                                                  int gemm_mode, int slices) {
   if (a->sym != b->sym) throw Error{TK_ERR_SPACE_MISMATCH, "A and B have different symmetries"};
-  if (dtype == TK_C128 && gemm_mode != TK_GEMM_FP64)
-    throw Error{TK_ERR_UNSUPPORTED, "split-precision products of complex tensors are not available"};
+  if (dtype == TK_C128 && gemm_mode != TK_GEMM_FP64) {
+    // complex operands, split-precision products: four real products of the real plan (the
+    // recoupling coefficients are real, so permutes act on real and imaginary parts alike)
+    auto re = make_contract_plan(ctx, a, pa, qa, b, pb, qb, pab, qab, TK_F64, gemm_mode, slices);
+    auto cp = std::make_shared<ContractPlan>();
+    cp->dtype = TK_C128;
+    cp->gemm_mode = gemm_mode;
+    cp->slices = slices;
+    cp->re = re;
+    cp->pa = re->pa;
+    cp->pb = re->pb;
+    cp->pc = re->pc;
+    cp->at = re->at;
+    cp->bt = re->bt;
+    cp->ct = re->ct;
+    cp->c = re->c;
+    cp->gemms = re->gemms;
+    cp->flops = 4.0 * re->flops;  // 8 MKN
+    cp->cx_na = a->numel;
+    cp->cx_nb = b->numel;
+    cp->cx_nc = re->c->numel;
+    cp->ws_cx = 2 * align256((size_t)cp->cx_na * 8) + 2 * align256((size_t)cp->cx_nb * 8) +
+                4 * align256((size_t)cp->cx_nc * 8);
+    cp->ws_total = cp->ws_cx + re->ws_total;
+    return cp;
+  }
   std::ostringstream os;
   os << perm_key(a->hash, pa, qa, dtype) << "#" << perm_key(b->hash, pb, qb, dtype) << "#";
   for (int x : pab) os << x << ",";

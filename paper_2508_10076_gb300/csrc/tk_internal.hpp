@@ -190,9 +190,19 @@ struct ContractPlan {
   int tune_oz_bn = 0;     // split-precision tile width: 64 or 128
   int tune_oz_split = 0;  // split-precision split-K: 1 off, 2 as many parts as allowed
   size_t ws_base = 0;     // workspace bytes of the permuted operands and C~ (before GEMM scratch)
+  // Complex tensors in a split-precision mode: C = A B runs as the four real products
+  // Re A Re B, Im A Im B, Re A Im B, Im A Re B of the real plan `re`, on de-interleaved copies of
+  // A and B in the workspace; ws_total = ws_cx + re->ws_total.
+  std::shared_ptr<ContractPlan> re;
+  size_t ws_cx = 0;
+  int64_t cx_na = 0, cx_nb = 0, cx_nc = 0;  // element counts of A, B and C
   ~ContractPlan();
 };
 
+
+// Workspace bytes a call of this contraction plan needs (a complex split-precision plan adds its
+// real plan's current size, which the autotuner may change).
+inline size_t contract_ws_bytes(const ContractPlan& cp) { return cp.re ? cp.ws_cx + cp.re->ws_total : cp.ws_total; }
 
 struct Ctx;
 // (Re)build a contraction plan's device work lists for its current tune_* choices and lay out the

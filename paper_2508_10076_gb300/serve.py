@@ -9,6 +9,9 @@ Scheduling, per pass of the loop:
   * the admitted requests of one dtype go to the GPU together through tk_contract_batch (their
     permutes, zero fills and sector-GEMM tiles share launches) on the next of several CUDA streams,
     so batches overlap on the device while new requests keep arriving;
+  * optionally (split_gemm), shapes whose FP64 service time alone is at least solo_ms and whose
+    split-precision time is shorter run one by one in that mode (Ozaki BF16: within 1e-10 of FP64)
+    instead of in the FP64 batches;
   * finished batches (their end event has completed) release memory and slots.
 Latency = completion time on the device clock - arrival time, both relative to one start event.
 Plans (structure, recoupling tables, GEMM work lists) are built once per shape and stay resident.
@@ -49,9 +52,9 @@ def request_stream(n, seed=0, rate_per_s=None, grid=None):
 
 
 class Shape:
-    """Plan and resident inputs of one request shape (symmetry, D, dtype)."""
+    """Plans and resident inputs of one request shape (symmetry, D, dtype)."""
 
-    def __init__(self, ctx, sym, D, dtype, seed=0):
+    def __init__(self, ctx, sym, D, dtype, seed=0, split_gemm=None):
         V, P, W = wl.heff_spaces(sym, D if sym == "U1" else max(8, D // 4))
         legs = wl.heff_legs(V, P, W)
         L, x = _tmap(ctx, sym, legs["L"]), _tmap(ctx, sym, legs["x"])
@@ -61,14 +64,31 @@ class Shape:
         rnd = wl.normal_complex if dtype == "c128" else wl.normal
         self.a = torch.from_numpy(np.ascontiguousarray(rnd(seed * 16 + 1, L.numel))).to("cuda", self.tdt)
         self.b = torch.from_numpy(np.ascontiguousarray(rnd(seed * 16 + 0, x.numel))).to("cuda", self.tdt)
+        self.split_plan = (api.contract_plan(ctx, L, *wl.LX_SPEC[:2], x, *wl.LX_SPEC[2:], dtype=dtype, gemm=split_gemm)
+                           if split_gemm else None)
+        self.solo = False  # served alone in split precision (set by calibrated_rate)
         self.out_numel = self.plan.output().numel
-        self.ws_bytes = max(1, self.plan.workspace_bytes)
-        self.bytes = self.out_numel * (16 if dtype == "c128" else 8) + self.ws_bytes
+        self.esize = 16 if dtype == "c128" else 8
+
+    @property
+    def serve_plan(self):
+        return self.split_plan if self.solo else self.plan
+
+    @property
+    def ws_bytes(self):
+        return max(1, self.serve_plan.workspace_bytes)
+
+    @property
+    def bytes(self):
+        return self.out_numel * self.esize + self.ws_bytes
 
 
 class Server:
-    def __init__(self, ctx, budget_bytes=150 << 30, streams=3, max_batch=64, max_inflight=256):
+    def __init__(self, ctx, budget_bytes=150 << 30, streams=3, max_batch=64, max_inflight=256,
+                 split_gemm=None, solo_ms=1.0):
         self.ctx = ctx
+        self.split_gemm = split_gemm
+        self.solo_ms = solo_ms
         self.budget = budget_bytes
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
         self.max_batch = max_batch
@@ -78,7 +98,7 @@ class Server:
     def shape(self, sym, D, dtype):
         key = (sym, D, dtype)
         if key not in self.shapes:
-            self.shapes[key] = Shape(self.ctx, sym, D, dtype)
+            self.shapes[key] = Shape(self.ctx, sym, D, dtype, split_gemm=self.split_gemm)
         return self.shapes[key]
 
     def run(self, requests, rate_per_s, keep_outputs=False):
@@ -116,14 +136,16 @@ class Server:
                 else:
                     still.append(b)
             inflight = still
-            # admit and launch, one batch per dtype
+            # admit and launch: one FP64 batch per dtype, split-precision requests one by one
             admitted = {"f64": [], "c128": []}
+            solo = []
             rest = []
             for i in queue:
                 r = requests[i]
                 sh = self.shape(r["sym"], r["D"], r["dtype"])
-                group = admitted[r["dtype"]]
-                if (in_use + sh.bytes <= self.budget and slots < self.max_inflight and len(group) < self.max_batch):
+                group = solo if sh.solo else admitted[r["dtype"]]
+                if (in_use + sh.bytes <= self.budget and slots < self.max_inflight and
+                        (sh.solo or len(group) < self.max_batch)):
                     group.append(i)
                     in_use += sh.bytes
                     slots += 1
@@ -149,7 +171,22 @@ class Server:
                 if keep_outputs:
                     for i, o in zip(group, outs):
                         outputs[i] = o
-            if not admitted["f64"] and not admitted["c128"]:
+            for i in solo:
+                r = requests[i]
+                sh = self.shape(r["sym"], r["D"], r["dtype"])
+                stream = self.streams[next_stream % len(self.streams)]
+                next_stream += 1
+                with torch.cuda.stream(stream):
+                    out = torch.empty(sh.out_numel, dtype=sh.tdt, device="cuda")
+                    ws = torch.empty(sh.ws_bytes, dtype=torch.uint8, device="cuda")
+                    api.contract(self.ctx, sh.split_plan, sh.a, sh.b, out, ws, stream)
+                    end = torch.cuda.Event(enable_timing=True)
+                    end.record(stream)
+                batches += 1
+                inflight.append(dict(reqs=[i], end=end, bytes=sh.bytes, bufs=(out, ws)))
+                if keep_outputs:
+                    outputs[i] = out
+            if not admitted["f64"] and not admitted["c128"] and not solo:
                 time.sleep(20e-6)  # nothing to launch: wait for arrivals or completions
         torch.cuda.synchronize()
         lat = np.array([done[i] for i in range(len(requests))])
@@ -167,21 +204,33 @@ class Server:
         return lat, summary, outputs
 
 
+def _alone_time(server, sh, plan):
+    c = torch.empty(sh.out_numel, dtype=sh.tdt, device="cuda")
+    ws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
+    api.contract(server.ctx, plan, sh.a, sh.b, c, ws)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(3):
+        api.contract(server.ctx, plan, sh.a, sh.b, c, ws)
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / 3 * 1e-3
+
+
 def calibrated_rate(server, requests, load=0.7):
     """Arrival rate that keeps the GPU about `load` busy: each shape's service time is measured
-    once with tk_contract on its own, and the rate is load / mean service time."""
+    once with tk_contract on its own, and the rate is load / mean service time.  With a split mode
+    on the server, a shape is served alone in that mode when its FP64 time is at least solo_ms and
+    the split-precision time is shorter."""
     times = {}
     for key, sh in server.shapes.items():
-        c = torch.empty(sh.out_numel, dtype=sh.tdt, device="cuda")
-        ws = torch.empty(sh.ws_bytes, dtype=torch.uint8, device="cuda")
-        api.contract(server.ctx, sh.plan, sh.a, sh.b, c, ws)
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record()
-        for _ in range(3):
-            api.contract(server.ctx, sh.plan, sh.a, sh.b, c, ws)
-        e.record()
-        torch.cuda.synchronize()
-        times[key] = s.elapsed_time(e) / 3 * 1e-3
+        t64 = _alone_time(server, sh, sh.plan)
+        times[key] = t64
+        if sh.split_plan is not None and t64 * 1e3 >= server.solo_ms:
+            ts = _alone_time(server, sh, sh.split_plan)
+            if ts < t64:
+                sh.solo = True
+                times[key] = ts
     mean = float(np.mean([times[(r["sym"], r["D"], r["dtype"])] for r in requests]))
     return load / mean, mean
 

@@ -201,13 +201,35 @@ def test_tf32x3_wide_range_and_split_k(gctx):
         assert np.all(err <= bound)
 
 
-def test_complex_split_precision_is_refused(gctx):
-    api = _api()
-    v = {-1: 2, 0: 3, 1: 2}
-    A = _tm(gctx, "U1", ([(v, False)], [(v, False)]))
-    with pytest.raises(api.TKError) as e:
-        api.contract_plan(gctx, A, (0,), (1,), A, (0,), (1,), (0,), (1,), dtype="c128", gemm="ozaki")
-    assert e.value.code == 7
+@pytest.mark.parametrize("gemm,tol", [("ozaki", SPLIT_TOL), ("tf32x3", 2e-5)])
+def test_complex_split_precision(gctx, gemm, tol):
+    """Complex tensors in the split-precision modes: four real products on the tensor cores,
+    combined into the complex result; the complex heff chain against the oracle."""
+    from paper_2508_10076_gb300.chain import HeffChain
+    ch = HeffChain(gctx, "U1", 256, dtype="c128", gemm=gemm, seed=5)
+    refs = oracle_heff("U1", 256, seed=5, tier="block", dtype="c128")
+    t = ch.steps[0].run(ch.dev["L"], ch.dev["x"])
+    outs = [t]
+    for i, other in ((1, "W"), (2, "W"), (3, "R")):
+        t = ch.steps[i].run(t, ch.dev[other])
+        outs.append(t)
+    gctx.sync()
+    for i, ((cs, rd), b) in enumerate(zip(refs, outs)):
+        assert ch.steps[i].out.blocks() == [(c, r, k, o) for c, r, k, o in cs.blocks]
+        assert rel_frobenius_per_block(cs, b.cpu().numpy(), rd) <= tol, i
+
+
+def test_complex_split_precision_su2_autotuned(gctx):
+    """SU(2) complex L.x in Ozaki mode after autotuning (the real plan is tuned on the real parts)
+    and replayed from a CUDA graph."""
+    from paper_2508_10076_gb300.chain import LxContraction
+    ch = LxContraction(gctx, "SU2", 256, dtype="c128", gemm="ozaki", seed=6)
+    ch.autotune()
+    graph, out, _ = ch.capture()
+    graph.replay()
+    torch.cuda.synchronize()
+    cs, rd = oracle_heff("SU2", 256, seed=6, tier="block", dtype="c128", steps=1)[0]
+    assert rel_frobenius_per_block(cs, out.cpu().numpy(), rd) <= SPLIT_TOL
 
 
 def test_single_site_heff_split_precision(gctx):
