@@ -330,6 +330,7 @@ struct GemmTile {
   int32_t slot, part;   // split-K: output tile slot and this tile's part (slot < 0: no split)
   int32_t nsplit, rpt;  // rpt: rows per thread of a row block (N <= 8 products)
   int64_t poff;         // split-K: first element of this slot's partials (nsplit parts of one tile)
+  int32_t nblk, pad1;   // row blocks: consecutive 256 x rpt row groups walked by one CTA (>= 1)
 };
 constexpr int SPLIT_MAX = 8;
 
@@ -487,16 +488,16 @@ __device__ __forceinline__ void gemm_tile(const GemmItem& it, const GemmTile& tl
 // CTA that completes the slot adds the parts in part order (deterministic) and writes C.  Thread
 // tid owns rows m0 + tid + 256 r, r < RPT.
 template <typename T, int NT, int RPT>
-__device__ __forceinline__ void rows_store(const GemmItem& it, const GemmTile& tl, const T (&acc)[RPT][NT],
-                                           T* __restrict__ C, T* __restrict__ partials,
-                                           int* __restrict__ counters) {
+__device__ __forceinline__ void rows_store(const GemmItem& it, const GemmTile& tl, int64_t m0,
+                                           const T (&acc)[RPT][NT], T* __restrict__ C,
+                                           T* __restrict__ partials, int* __restrict__ counters) {
   const int64_t M = it.M;
   const int tid = threadIdx.x;
   T* Cb = C + it.c_off;
   if (tl.slot < 0) {
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-      const int64_t m = (int64_t)tl.m0 + r * 256 + tid;
+      const int64_t m = m0 + r * 256 + tid;
       if (m < M) {
 #pragma unroll
         for (int j = 0; j < NT; ++j) Cb[m + j * M] = acc[r][j];
@@ -520,7 +521,7 @@ __device__ __forceinline__ void rows_store(const GemmItem& it, const GemmTile& t
   const T* base = partials + tl.poff;
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
-    const int64_t m = (int64_t)tl.m0 + r * 256 + tid;
+    const int64_t m = m0 + r * 256 + tid;
     if (m < M) {
 #pragma unroll
       for (int j = 0; j < NT; ++j) {
@@ -544,60 +545,68 @@ __device__ __forceinline__ void gemm_rows_n(const GemmItem& it, const GemmTile& 
   T(*Bs)[NT] = reinterpret_cast<T(*)[NT]>(smem);
   const int64_t M = it.M, K = it.K;
   const int tid = threadIdx.x;
-  bool live[RPT];
-#pragma unroll
-  for (int r = 0; r < RPT; ++r) live[r] = (int64_t)tl.m0 + r * 256 + tid < M;
-  T acc[RPT][NT];
-#pragma unroll
-  for (int r = 0; r < RPT; ++r)
-#pragma unroll
-    for (int j = 0; j < NT; ++j) acc[r][j] = Elem<T>::zero();
+  // one K chunk: B is staged once for all of this CTA's row groups
+  const bool one_chunk = tl.k1 - tl.k0 <= ROWS_KCHUNK;
   const T* Bb = B + it.b_off;
-  for (int64_t k0 = tl.k0; k0 < tl.k1; k0 += ROWS_KCHUNK) {
-    const int kmax = (int)((tl.k1 - k0) < ROWS_KCHUNK ? (tl.k1 - k0) : ROWS_KCHUNK);
-    for (int e = tid; e < kmax * NT; e += 256) {
-      const int kk = e % kmax, nn = e / kmax;
-      Bs[kk][nn] = Bb[(k0 + kk) + nn * K];
-    }
-    __syncthreads();
-    const T* Ak = A + it.a_off + tl.m0 + tid + k0 * M;  // column k0 of this thread's first row
-    int kk = 0;
-    for (; kk + 4 <= kmax; kk += 4, Ak += 4 * M) {
-      T a[4][RPT];
+  for (int sb = 0; sb < tl.nblk; ++sb) {
+    const int64_t m0 = (int64_t)tl.m0 + (int64_t)sb * 256 * RPT;
+    if (m0 >= M) break;
+    bool live[RPT];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+    for (int r = 0; r < RPT; ++r) live[r] = m0 + r * 256 + tid < M;
+    T acc[RPT][NT];
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) a[u][r] = live[r] ? Ak[u * M + r * 256] : Elem<T>::zero();
+    for (int r = 0; r < RPT; ++r)
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int j = 0; j < NT; ++j) {
-          const T b = Bs[kk + u][j];
-#pragma unroll
-          for (int r = 0; r < RPT; ++r) Mac<T>::mac(acc[r][j], a[u][r], b);
+      for (int j = 0; j < NT; ++j) acc[r][j] = Elem<T>::zero();
+    for (int64_t k0 = tl.k0; k0 < tl.k1; k0 += ROWS_KCHUNK) {
+      const int kmax = (int)((tl.k1 - k0) < ROWS_KCHUNK ? (tl.k1 - k0) : ROWS_KCHUNK);
+      if (sb == 0 || !one_chunk) {
+        for (int e = tid; e < kmax * NT; e += 256) {
+          const int kk = e % kmax, nn = e / kmax;
+          Bs[kk][nn] = Bb[(k0 + kk) + nn * K];
         }
-    }
-    if (kk < kmax) {  // 1..3 left; the branches are uniform over the block
-      const int left = kmax - kk;
-      T a[3][RPT];
+        __syncthreads();
+      }
+      const T* Ak = A + it.a_off + m0 + tid + k0 * M;  // column k0 of this thread's first row
+      int kk = 0;
+      for (; kk + 4 <= kmax; kk += 4, Ak += 4 * M) {
+        T a[4][RPT];
 #pragma unroll
-      for (int u = 0; u < 3; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) a[u][r] = (live[r] && u < left) ? Ak[u * M + r * 256] : Elem<T>::zero();
+          for (int r = 0; r < RPT; ++r) a[u][r] = live[r] ? Ak[u * M + r * 256] : Elem<T>::zero();
 #pragma unroll
-      for (int u = 0; u < 3; ++u)
-        if (u < left) {
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int j = 0; j < NT; ++j) {
             const T b = Bs[kk + u][j];
 #pragma unroll
             for (int r = 0; r < RPT; ++r) Mac<T>::mac(acc[r][j], a[u][r], b);
           }
-        }
+      }
+      if (kk < kmax) {  // 1..3 left; the branches are uniform over the block
+        const int left = kmax - kk;
+        T a[3][RPT];
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) a[u][r] = (live[r] && u < left) ? Ak[u * M + r * 256] : Elem<T>::zero();
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (u < left) {
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+              const T b = Bs[kk + u][j];
+#pragma unroll
+              for (int r = 0; r < RPT; ++r) Mac<T>::mac(acc[r][j], a[u][r], b);
+            }
+          }
+      }
+      if (!one_chunk) __syncthreads();
     }
-    __syncthreads();
+    rows_store<T, NT, RPT>(it, tl, m0, acc, C, partials, counters);
   }
-  rows_store<T, NT, RPT>(it, tl, acc, C, partials, counters);
 }
 
 template <typename T>
@@ -690,59 +699,66 @@ __device__ __forceinline__ void gemm_rows_df_n(const GemmItem& it, const GemmTil
   float2(*Bl)[NP] = reinterpret_cast<float2(*)[NP]>(reinterpret_cast<float2*>(smem) + ROWS_KCHUNK * NP);
   const int64_t M = it.M, K = it.K;
   const int tid = threadIdx.x;
-  bool live[RPT];
-#pragma unroll
-  for (int r = 0; r < RPT; ++r) live[r] = (int64_t)tl.m0 + r * 256 + tid < M;
-  float2 sh[RPT][NP], sl[RPT][NP];
-#pragma unroll
-  for (int r = 0; r < RPT; ++r)
-#pragma unroll
-    for (int q = 0; q < NP; ++q) sh[r][q] = sl[r][q] = make_float2(0.f, 0.f);
+  const bool one_chunk = tl.k1 - tl.k0 <= ROWS_KCHUNK;  // then B is staged once for all row groups
   const double* Bb = B + it.b_off;
-  for (int64_t k0 = tl.k0; k0 < tl.k1; k0 += ROWS_KCHUNK) {
-    const int kmax = (int)((tl.k1 - k0) < ROWS_KCHUNK ? (tl.k1 - k0) : ROWS_KCHUNK);
-    for (int e = tid; e < kmax * NP; e += 256) {
-      const int kk = e % kmax, q = e / kmax;
-      float h0, l0, h1 = 0.f, l1 = 0.f;
-      df_split(Bb[(k0 + kk) + (2 * q) * K], h0, l0);
-      if (2 * q + 1 < NT) df_split(Bb[(k0 + kk) + (2 * q + 1) * K], h1, l1);
-      Bh[kk][q] = make_float2(h0, h1);
-      Bl[kk][q] = make_float2(l0, l1);
+  for (int sb = 0; sb < tl.nblk; ++sb) {
+    const int64_t m0 = (int64_t)tl.m0 + (int64_t)sb * 256 * RPT;
+    if (m0 >= M) break;
+    bool live[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) live[r] = m0 + r * 256 + tid < M;
+    float2 sh[RPT][NP], sl[RPT][NP];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+      for (int q = 0; q < NP; ++q) sh[r][q] = sl[r][q] = make_float2(0.f, 0.f);
+    for (int64_t k0 = tl.k0; k0 < tl.k1; k0 += ROWS_KCHUNK) {
+      const int kmax = (int)((tl.k1 - k0) < ROWS_KCHUNK ? (tl.k1 - k0) : ROWS_KCHUNK);
+      if (sb == 0 || !one_chunk) {
+        for (int e = tid; e < kmax * NP; e += 256) {
+          const int kk = e % kmax, q = e / kmax;
+          float h0, l0, h1 = 0.f, l1 = 0.f;
+          df_split(Bb[(k0 + kk) + (2 * q) * K], h0, l0);
+          if (2 * q + 1 < NT) df_split(Bb[(k0 + kk) + (2 * q + 1) * K], h1, l1);
+          Bh[kk][q] = make_float2(h0, h1);
+          Bl[kk][q] = make_float2(l0, l1);
+        }
+        __syncthreads();
+      }
+      const double* Ak = A + it.a_off + m0 + tid + k0 * M;
+      int kk = 0;
+      for (; kk + 4 <= kmax; kk += 4, Ak += 4 * M) {
+        double a[4][RPT];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) a[u][r] = live[r] ? Ak[u * M + r * 256] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) df_rows_group<NP, RPT>(sh, sl, a[u], Bh[kk + u], Bl[kk + u]);
+      }
+      if (kk < kmax) {  // 1..3 left; the branches are uniform over the block
+        const int left = kmax - kk;
+        double a[3][RPT];
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) a[u][r] = (live[r] && u < left) ? Ak[u * M + r * 256] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (u < left) df_rows_group<NP, RPT>(sh, sl, a[u], Bh[kk + u], Bl[kk + u]);
+      }
+      if (!one_chunk) __syncthreads();
     }
-    __syncthreads();
-    const double* Ak = A + it.a_off + tl.m0 + tid + k0 * M;
-    int kk = 0;
-    for (; kk + 4 <= kmax; kk += 4, Ak += 4 * M) {
-      double a[4][RPT];
+    double acc[RPT][NT];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+    for (int r = 0; r < RPT; ++r)
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) a[u][r] = live[r] ? Ak[u * M + r * 256] : 0.0;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) df_rows_group<NP, RPT>(sh, sl, a[u], Bh[kk + u], Bl[kk + u]);
-    }
-    if (kk < kmax) {  // 1..3 left; the branches are uniform over the block
-      const int left = kmax - kk;
-      double a[3][RPT];
-#pragma unroll
-      for (int u = 0; u < 3; ++u)
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) a[u][r] = (live[r] && u < left) ? Ak[u * M + r * 256] : 0.0;
-#pragma unroll
-      for (int u = 0; u < 3; ++u)
-        if (u < left) df_rows_group<NP, RPT>(sh, sl, a[u], Bh[kk + u], Bl[kk + u]);
-    }
-    __syncthreads();
+      for (int j = 0; j < NT; ++j) {
+        const float2 h = sh[r][j / 2], l = sl[r][j / 2];
+        acc[r][j] = (j & 1) ? f32_to_f64(h.y) + f32_to_f64(l.y) : f32_to_f64(h.x) + f32_to_f64(l.x);
+      }
+    rows_store<double, NT, RPT>(it, tl, m0, acc, C, partials, counters);
   }
-  double acc[RPT][NT];
-#pragma unroll
-  for (int r = 0; r < RPT; ++r)
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      const float2 h = sh[r][j / 2], l = sl[r][j / 2];
-      acc[r][j] = (j & 1) ? f32_to_f64(h.y) + f32_to_f64(l.y) : f32_to_f64(h.x) + f32_to_f64(l.x);
-    }
-  rows_store<double, NT, RPT>(it, tl, acc, C, partials, counters);
 }
 
 __device__ __forceinline__ void gemm_rows_df(const GemmItem& it, const GemmTile& tl, const double* __restrict__ A,
@@ -1072,7 +1088,7 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
   std::vector<Cand> cands;
   // one output tile as nsplit parts over [0, K), each part's depth a multiple of kalign
   auto emit = [&](int32_t item, int64_t m0, int64_t n0, int32_t cfg, int64_t K, int nsplit, int kalign,
-                  int64_t part_elems, double area, int rpt) {
+                  int64_t part_elems, double area, int rpt, int nblk) {
     const int64_t kstep = ((K + nsplit - 1) / nsplit + kalign - 1) / kalign * kalign;
     nsplit = (int)std::max<int64_t>(1, (K + kstep - 1) / kstep);  // no empty parts after rounding
     const int32_t slot = nsplit > 1 ? nslots++ : -1;
@@ -1090,6 +1106,7 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
       t.part = p;
       t.nsplit = nsplit;
       t.rpt = rpt;
+      t.nblk = nblk;
       t.poff = nsplit > 1 ? poff : 0;
       cands.push_back({t, area * (double)(k1 - k0)});
     }
@@ -1101,15 +1118,18 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
       const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want_rows, (int64_t)SPLIT_MAX, g.K / 8}));
       const int32_t cfg = cp.gemm_mode == TK_GEMM_FP64 ? CFG_ROWS : CFG_ROWS_DF;
       const int rpt = rows_per_thread(g);
-      const int64_t rb = 256 * rpt;
+      // a CTA walks several row groups of a long product that needs one K chunk and no split
+      const int nblk = (nsplit == 1 && g.K <= ROWS_KCHUNK && rpt > 1) ? 4 : 1;
+      const int64_t rb = 256 * rpt * nblk;
       for (int64_t m0 = 0; m0 < g.M; m0 += rb)
-        emit((int32_t)i, m0, 0, cfg, g.K, nsplit, 8, rb * g.N, (double)std::min<int64_t>(rb, g.M - m0) * g.N, rpt);
+        emit((int32_t)i, m0, 0, cfg, g.K, nsplit, 8, (int64_t)256 * rpt * g.N,
+             (double)std::min<int64_t>(rb, g.M - m0) * g.N, rpt, nblk);
       continue;
     }
     const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want_tiles, (int64_t)SPLIT_MAX, g.K / 64}));
     for (int64_t n0 = 0; n0 < g.N; n0 += bm)
       for (int64_t m0 = 0; m0 < g.M; m0 += bm)
-        emit((int32_t)i, m0, n0, use64 ? CFG_64 : CFG_32, g.K, nsplit, BK, (int64_t)bm * bm, (double)bm * bm, 1);
+        emit((int32_t)i, m0, n0, use64 ? CFG_64 : CFG_32, g.K, nsplit, BK, (int64_t)bm * bm, (double)bm * bm, 1, 1);
   }
   cp.split_slots = nslots;
   if (cp.gemm_mode != TK_GEMM_FP64)  // the split-precision launch runs row blocks only
