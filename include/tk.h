@@ -203,9 +203,12 @@ int tk_contract(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, 
  * plan but not a workspace or an output.  The blocks of all requests share one launch per stage:
  * every input permute in one launch, the zero fill in one, every sector GEMM tile in one grouped
  * GEMM, every output permute in one (a stage with more than 160 segments is split into several
- * launches).  Each c[i] equals what tk_contract would write for that request alone.
- * Every plan must use TK_GEMM_FP64 and all plans the same dtype (else TK_ERR_UNSUPPORTED);
- * pointer arrays are host arrays of device pointers; n = 0 is a no-op. */
+ * launches).  In the split-precision modes the double-float row blocks of all requests share one
+ * launch and the tensor-core products one launch per group of up to 32 requests with the same
+ * tile width and slice count (each request's operands are scaled and sliced by its own launches).
+ * Each c[i] equals what tk_contract would write for that request alone.  All plans must share
+ * the dtype and the gemm mode, and complex split-precision plans are not batched (else
+ * TK_ERR_UNSUPPORTED); pointer arrays are host arrays of device pointers; n = 0 is a no-op. */
 int tk_contract_batch(tk_ctx* ctx, int n, const tk_plan* const* plans, const void* const* a,
                       const void* const* b, void* const* c, void* const* workspace,
                       const size_t* workspace_bytes, void* stream);

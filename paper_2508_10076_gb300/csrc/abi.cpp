@@ -531,8 +531,9 @@ int tk_contract_batch(tk_ctx* ctx, int n, const tk_plan* const* plans, const voi
     const tk::ContractPlan& cp = *plans[i]->con;
     if (workspace_bytes[i] < cp.ws_total || (cp.ws_total > 0 && !workspace[i]))
       return fail(ctx, TK_ERR_WORKSPACE, "workspace smaller than tk_plan_workspace_bytes()");
-    if (cp.gemm_mode != TK_GEMM_FP64 || cp.dtype != plans[0]->con->dtype)
-      return fail(ctx, TK_ERR_UNSUPPORTED, "a batch takes FP64-mode plans of one dtype");
+    if (cp.gemm_mode != plans[0]->con->gemm_mode || cp.dtype != plans[0]->con->dtype)
+      return fail(ctx, TK_ERR_UNSUPPORTED, "a batch takes plans of one dtype and one gemm mode");
+    if (cp.re) return fail(ctx, TK_ERR_UNSUPPORTED, "complex split-precision plans run one by one");
     cps[(size_t)i] = &cp;
   }
   int rc = set_device(ctx);

@@ -850,6 +850,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 1) k_gemm_batch(cons
     gemm_rows<T>(it, tl, A, B, C, smem, P, g.counters);
 }
 
+// Packed double-float row blocks (split-precision batches): as k_gemm_batch, row code only.
+__global__ void __launch_bounds__(256, 4) k_gemm_rows_df_batch(const __grid_constant__ GemmBatch L) {
+  __shared__ double smem[ROWS_KCHUNK * ROWS_NMAX];
+  const GemmSeg& g = L.seg[find_seg(L.seg, L.nseg, (int64_t)blockIdx.x)];
+  const GemmTile tl = g.tiles[blockIdx.x - g.block0];
+  const GemmItem it = g.items[tl.item];
+  gemm_rows_df(it, tl, (const double*)g.A, (const double*)g.B, (double*)g.C, smem, (double*)g.partials,
+               g.counters);
+}
+
 // Packed zero fill: block row y belongs to the segment whose first item index is the largest <= y.
 struct ZeroSeg {
   const ZeroItem* items;
@@ -1299,6 +1309,7 @@ int run_contract_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const 
                        const void* const* b, void* const* c, void* const* ws, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const bool cplx = plans[0]->dtype == TK_C128;
+  const bool split = plans[0]->gemm_mode != TK_GEMM_FP64;  // a batch has one gemm mode (checked by the ABI)
   std::vector<const void*> at((size_t)n), bt((size_t)n);
   std::vector<void*> ct((size_t)n);
   std::vector<PermJob> in_jobs, out_jobs;
@@ -1355,6 +1366,13 @@ int run_contract_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const 
     gb.nseg = 0;
     auto flush = [&]() -> int {
       if (gb.nseg == 0) return TK_OK;
+      if (split) {
+        ProfScope prof(ctx, "k_gemm_rows_df", stream);
+        k_gemm_rows_df_batch<<<(unsigned)blocks, 256, 0, s>>>(gb);
+        gb.nseg = 0;
+        blocks = 0;
+        return check_launch(ctx, "k_gemm_rows_df_batch");
+      }
       ProfScope prof(ctx, "k_gemm_f64", stream);
       if (cplx)
         k_gemm_batch<double2><<<(unsigned)blocks, 256, 0, s>>>(gb);
@@ -1382,6 +1400,12 @@ int run_contract_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const 
       if (gb.nseg == kBatchSegs && (rc = flush()) != TK_OK) return rc;
     }
     if ((rc = flush()) != TK_OK) return rc;
+  }
+  if (split) {  // the tensor-core products of every request, packed
+    std::vector<void*> wsl((size_t)n);
+    for (int i = 0; i < n; ++i) wsl[(size_t)i] = (char*)ws[i] + plans[i]->ws_slices;
+    if ((rc = launch_gemm_ozaki_batch(ctx, n, plans, at.data(), bt.data(), ct.data(), wsl.data(), stream)) != TK_OK)
+      return rc;
   }
   return launch_permutes(ctx, out_jobs.data(), (int)out_jobs.size(), stream, nullptr, 0);
 }

@@ -472,6 +472,28 @@ __global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ s
 }
 
 // ------------------------------------------------------------------ the persistent GEMM
+// One request of a launch: its slice tiles (tensor maps over its workspace), tables and outputs.
+// A launch serves NREQ requests of one (mode, tile width, slice count); each request's items are
+// already spread over the CTAs (cta_work), and every CTA walks its share of each request in turn.
+struct OzReq {
+  CUtensorMap ma, mb;  // A and B slice tiles
+  const OzSector* secs;
+  const OzWork* work;
+  const int32_t* cta_work;  // items of CTA b: work[cta_work[b] .. cta_work[b + 1]), b < ncta
+  const int32_t* sa;
+  const int32_t* sb;
+  double* C;
+  double* partials;
+  int* counters;
+  int32_t ncta, pad;
+};
+template <int NREQ>
+struct OzBatchT {
+  OzReq req[NREQ];
+  int32_t nreq;
+};
+constexpr int OZ_BATCH = 32;  // requests per packed launch
+
 struct OzSmem {
   uint64_t full[OZ_MAX_STAGES], empty[OZ_MAX_STAGES];
   uint64_t acc_full[2], acc_empty[2], drain;  // one or two TMEM buffers
@@ -542,13 +564,10 @@ __device__ __forceinline__ void oz_issue(int s, uint32_t acc0, uint32_t sbase, u
 
 // BN = 128: one TMEM buffer (4 x 128 columns), the MMAs wait for the epilogue between tiles;
 // BN = 64: two buffers, the epilogue of one tile overlaps the MMAs of the next.
-template <int BN, int MODE>
+template <int BN, int MODE, int NREQ>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    k_oz_gemm(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
-              const OzSector* __restrict__ secs, const OzWork* __restrict__ work,
-              const int32_t* __restrict__ cta_work, const __grid_constant__ OzPairs pairs, int nslices, const int32_t* __restrict__ scale_a,
-              const int32_t* __restrict__ scale_b, double* __restrict__ C, double* __restrict__ partials,
-              int* __restrict__ counters, int* __restrict__ status) {
+    k_oz_gemm(const __grid_constant__ OzBatchT<NREQ> L, const __grid_constant__ OzPairs pairs, int nslices,
+              int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char dyn[];
   unsigned char* base = (unsigned char*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
   constexpr int NBUF = OZ_TMEM_COLS / (OZ_NACC * BN);
@@ -561,7 +580,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   OzSmem* ss = reinterpret_cast<OzSmem*>(base + nstages * stage_bytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort_flag = &ss->abort_flag;
-  const int w_begin = cta_work[blockIdx.x], w_end = cta_work[blockIdx.x + 1];  // this CTA's work items
 
   if (threadIdx.x == 0) {
     for (uint32_t s = 0; s < nstages; ++s) {
@@ -590,24 +608,31 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
       uint32_t it = 0;
-      for (int w = w_begin; w < w_end && !*abort_flag; ++w) {
-        const OzWork wk = work[w];
-        const OzSector s = secs[wk.sector];
-        // slice tiles hold 128 rows; this item's B box is part nt % SUB of tile nt / SUB
-        const int64_t ta0 = s.ta_base + (int64_t)wk.mt * s.nkc, tb0 = s.tb_base + (int64_t)(wk.nt / SUB) * s.nkc;
-        const int32_t brow = (wk.nt % SUB) * BN;
-        const int64_t sa_str = (int64_t)s.nmt * s.nkc, sb_str = (int64_t)s.nnt * s.nkc;  // tiles per slice
-        for (int kc = wk.kc_lo; kc < wk.kc_hi && !*abort_flag; ++kc, ++it) {
-          const uint32_t st = it % nstages, ph = (it / nstages) & 1;
-          if (!mbar_wait(smem_u32(&ss->empty[st]), ph ^ 1, abort_flag)) break;
-          const uint32_t fb = smem_u32(&ss->full[st]);
-          mbar_expect_tx(fb, stage_bytes);
-          const uint32_t dst = smem_u32(base + st * stage_bytes);
-          for (int i = 0; i < nslices; ++i)
-            tma_load_2d(dst + i * MD::A_BYTES, &tm_a, 0, (int32_t)((ta0 + i * sa_str + kc) * OZ_TROWS), fb);
-          for (int j = 0; j < nslices; ++j)
-            tma_load_2d(dst + b_off + j * B_BYTES, &tm_b, 0,
-                        (int32_t)((tb0 + j * sb_str + kc) * OZ_TROWS + brow), fb);
+      for (int r = 0; r < L.nreq && !*abort_flag; ++r) {
+        const OzReq& R = L.req[r];
+        if ((int)blockIdx.x >= R.ncta) continue;  // this request has fewer work lists than CTAs
+        const int w_begin = R.cta_work[blockIdx.x], w_end = R.cta_work[blockIdx.x + 1];  // this CTA's items
+        const OzSector* __restrict__ secs = R.secs;
+        const OzWork* __restrict__ work = R.work;
+        for (int w = w_begin; w < w_end && !*abort_flag; ++w) {
+          const OzWork wk = work[w];
+          const OzSector s = secs[wk.sector];
+          // slice tiles hold 128 rows; this item's B box is part nt % SUB of tile nt / SUB
+          const int64_t ta0 = s.ta_base + (int64_t)wk.mt * s.nkc, tb0 = s.tb_base + (int64_t)(wk.nt / SUB) * s.nkc;
+          const int32_t brow = (wk.nt % SUB) * BN;
+          const int64_t sa_str = (int64_t)s.nmt * s.nkc, sb_str = (int64_t)s.nnt * s.nkc;  // tiles per slice
+          for (int kc = wk.kc_lo; kc < wk.kc_hi && !*abort_flag; ++kc, ++it) {
+            const uint32_t st = it % nstages, ph = (it / nstages) & 1;
+            if (!mbar_wait(smem_u32(&ss->empty[st]), ph ^ 1, abort_flag)) break;
+            const uint32_t fb = smem_u32(&ss->full[st]);
+            mbar_expect_tx(fb, stage_bytes);
+            const uint32_t dst = smem_u32(base + st * stage_bytes);
+            for (int i = 0; i < nslices; ++i)
+              tma_load_2d(dst + i * MD::A_BYTES, &R.ma, 0, (int32_t)((ta0 + i * sa_str + kc) * OZ_TROWS), fb);
+            for (int j = 0; j < nslices; ++j)
+              tma_load_2d(dst + b_off + j * B_BYTES, &R.mb, 0,
+                          (int32_t)((tb0 + j * sb_str + kc) * OZ_TROWS + brow), fb);
+          }
         }
       }
       // drain: every issued stage must have landed before this CTA may exit (bounded)
@@ -620,23 +645,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       uint32_t it = 0, seg = 0;
-      for (int w = w_begin; w < w_end && !*abort_flag; ++w) {
-        const OzWork wk = work[w];
-        const uint32_t idesc = idesc_mma<MODE>(OZ_BM, wk.nw);
-        for (int kc0 = wk.kc_lo; kc0 < wk.kc_hi && !*abort_flag; kc0 += OZ_SEG_KC, ++seg) {
-          const int kc1 = min(wk.kc_hi, kc0 + OZ_SEG_KC);
-          const uint32_t buf = seg % NBUF;
-          if (!mbar_wait(smem_u32(&ss->acc_empty[buf]), ((seg / NBUF) & 1) ^ 1, abort_flag)) break;
-          tc_fence_after();
-          const uint32_t acc0 = tmem + buf * (OZ_NACC * BN);
-          for (int kc = kc0; kc < kc1; ++kc, ++it) {
-            const uint32_t st = it % nstages, ph = (it / nstages) & 1;
-            if (!mbar_wait(smem_u32(&ss->full[st]), ph, abort_flag)) break;
+      for (int r = 0; r < L.nreq && !*abort_flag; ++r) {
+        const OzReq& R = L.req[r];
+        if ((int)blockIdx.x >= R.ncta) continue;  // this request has fewer work lists than CTAs
+        const int w_begin = R.cta_work[blockIdx.x], w_end = R.cta_work[blockIdx.x + 1];  // this CTA's items
+        const OzWork* __restrict__ work = R.work;
+        for (int w = w_begin; w < w_end && !*abort_flag; ++w) {
+          const OzWork wk = work[w];
+          const uint32_t idesc = idesc_mma<MODE>(OZ_BM, wk.nw);
+          for (int kc0 = wk.kc_lo; kc0 < wk.kc_hi && !*abort_flag; kc0 += OZ_SEG_KC, ++seg) {
+            const int kc1 = min(wk.kc_hi, kc0 + OZ_SEG_KC);
+            const uint32_t buf = seg % NBUF;
+            if (!mbar_wait(smem_u32(&ss->acc_empty[buf]), ((seg / NBUF) & 1) ^ 1, abort_flag)) break;
             tc_fence_after();
-            oz_issue<BN, MODE>(nslices, acc0, smem_u32(base + st * stage_bytes), idesc, kc == kc0);
-            tc_commit(smem_u32(&ss->empty[st]));  // frees the stage once these MMAs are done
+            const uint32_t acc0 = tmem + buf * (OZ_NACC * BN);
+            for (int kc = kc0; kc < kc1; ++kc, ++it) {
+              const uint32_t st = it % nstages, ph = (it / nstages) & 1;
+              if (!mbar_wait(smem_u32(&ss->full[st]), ph, abort_flag)) break;
+              tc_fence_after();
+              oz_issue<BN, MODE>(nslices, acc0, smem_u32(base + st * stage_bytes), idesc, kc == kc0);
+              tc_commit(smem_u32(&ss->empty[st]));  // frees the stage once these MMAs are done
+            }
+            tc_commit(smem_u32(&ss->acc_full[buf]));  // accumulators of this (item, segment) complete
           }
-          tc_commit(smem_u32(&ss->acc_full[buf]));  // accumulators of this (item, segment) complete
         }
       }
       // make sure no MMA is still running before TMEM is released (bounded)
@@ -653,104 +684,116 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     // accumulators of levels without any slice pair (fewer than 4 slices) are never written
     const bool has1 = pairs.first[1] >= 0, has2 = pairs.first[2] >= 0, has3 = pairs.first[3] >= 0;
     uint32_t seg = 0;
-    for (int w = w_begin; w < w_end && !*abort_flag; ++w) {
-      const OzWork wk = work[w];
-      const OzSector s = secs[wk.sector];
-      const int c0 = grp * WCOLS;                 // first column of this warp within the tile
-      const bool active = c0 < wk.nw;             // warp-uniform
-      const int64_t m = (int64_t)wk.mt * OZ_BM + row;
-      const bool row_ok = m < s.M;
-      int em = row_ok ? scale_a[s.sa_off + m] : 0;
-      if (em == kNoScale) em = 0;
-      const int64_t nb = (int64_t)wk.nt * BN + c0;
-      const int64_t left = s.N - nb;
-      const int ncols = left < WCOLS ? (int)left : WCOLS;  // valid columns of this warp (may be <= 0)
-      int fl = (lane < ncols) ? scale_b[s.sb_off + nb + lane] : 0;  // WCOLS <= 32: one per lane
-      if (fl == kNoScale) fl = 0;
-      // a split tile's parts go to its partial buffers (column-major 128 x BN, one per part)
-      const bool split = wk.nparts > 1;
-      double* const pbase = split ? partials + (int64_t)wk.slot * OZ_MAX_PARTS * (OZ_BM * BN) : nullptr;
-      double* crow = split ? pbase + (int64_t)wk.part * (OZ_BM * BN) + (int64_t)c0 * OZ_BM + row
-                           : C + s.c_off + nb * s.M + m;
-      const int64_t ld = split ? OZ_BM : s.M;
-      bool done = true;
-      for (int kc0 = wk.kc_lo; kc0 < wk.kc_hi; kc0 += OZ_SEG_KC, ++seg) {
-        const uint32_t buf = seg % NBUF;
-        if (!mbar_wait(smem_u32(&ss->acc_full[buf]), (seg / NBUF) & 1, abort_flag, true)) {
-          done = false;
-          break;
-        }
-        tc_fence_after();
-        if (active) {
-          const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + buf * (OZ_NACC * BN) + c0;
+    for (int r = 0; r < L.nreq && !*abort_flag; ++r) {
+      const OzReq& R = L.req[r];
+      if ((int)blockIdx.x >= R.ncta) continue;  // this request has fewer work lists than CTAs
+      const int w_begin = R.cta_work[blockIdx.x], w_end = R.cta_work[blockIdx.x + 1];  // this CTA's items
+      const OzSector* __restrict__ secs = R.secs;
+      const OzWork* __restrict__ work = R.work;
+      const int32_t* __restrict__ scale_a = R.sa;
+      const int32_t* __restrict__ scale_b = R.sb;
+      double* __restrict__ C = R.C;
+      double* __restrict__ partials = R.partials;
+      int* __restrict__ counters = R.counters;
+      for (int w = w_begin; w < w_end && !*abort_flag; ++w) {
+        const OzWork wk = work[w];
+        const OzSector s = secs[wk.sector];
+        const int c0 = grp * WCOLS;                 // first column of this warp within the tile
+        const bool active = c0 < wk.nw;             // warp-uniform
+        const int64_t m = (int64_t)wk.mt * OZ_BM + row;
+        const bool row_ok = m < s.M;
+        int em = row_ok ? scale_a[s.sa_off + m] : 0;
+        if (em == kNoScale) em = 0;
+        const int64_t nb = (int64_t)wk.nt * BN + c0;
+        const int64_t left = s.N - nb;
+        const int ncols = left < WCOLS ? (int)left : WCOLS;  // valid columns of this warp (may be <= 0)
+        int fl = (lane < ncols) ? scale_b[s.sb_off + nb + lane] : 0;  // WCOLS <= 32: one per lane
+        if (fl == kNoScale) fl = 0;
+        // a split tile's parts go to its partial buffers (column-major 128 x BN, one per part)
+        const bool split = wk.nparts > 1;
+        double* const pbase = split ? partials + (int64_t)wk.slot * OZ_MAX_PARTS * (OZ_BM * BN) : nullptr;
+        double* crow = split ? pbase + (int64_t)wk.part * (OZ_BM * BN) + (int64_t)c0 * OZ_BM + row
+                             : C + s.c_off + nb * s.M + m;
+        const int64_t ld = split ? OZ_BM : s.M;
+        bool done = true;
+        for (int kc0 = wk.kc_lo; kc0 < wk.kc_hi; kc0 += OZ_SEG_KC, ++seg) {
+          const uint32_t buf = seg % NBUF;
+          if (!mbar_wait(smem_u32(&ss->acc_full[buf]), (seg / NBUF) & 1, abort_flag, true)) {
+            done = false;
+            break;
+          }
+          tc_fence_after();
+          if (active) {
+            const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + buf * (OZ_NACC * BN) + c0;
 #pragma unroll 1
-          for (int ch = 0; ch < WCOLS / 8; ++ch) {
-            if (ch * 8 >= ncols) break;  // warp-uniform
-            uint32_t r0[8], r1[8], r2[8], r3[8];
-            tc_ld8(lane_addr + 0 * BN + ch * 8, r0);
-            tc_ld8(lane_addr + 1 * BN + ch * 8, r1);
-            tc_ld8(lane_addr + 2 * BN + ch * 8, r2);
-            tc_ld8(lane_addr + 3 * BN + ch * 8, r3);
-            tc_wait_ld();
-            // level sums, two columns per instruction: hi + lo = r0 + r1 + r2 (exact levels, the
-            // FP32 rounding of the last two-sum kept in lo) with the inexact level r3 added to lo
-            float hv[8], lv[8];
+            for (int ch = 0; ch < WCOLS / 8; ++ch) {
+              if (ch * 8 >= ncols) break;  // warp-uniform
+              uint32_t r0[8], r1[8], r2[8], r3[8];
+              tc_ld8(lane_addr + 0 * BN + ch * 8, r0);
+              tc_ld8(lane_addr + 1 * BN + ch * 8, r1);
+              tc_ld8(lane_addr + 2 * BN + ch * 8, r2);
+              tc_ld8(lane_addr + 3 * BN + ch * 8, r3);
+              tc_wait_ld();
+              // level sums, two columns per instruction: hi + lo = r0 + r1 + r2 (exact levels, the
+              // FP32 rounding of the last two-sum kept in lo) with the inexact level r3 added to lo
+              float hv[8], lv[8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float2 z = make_float2(0.f, 0.f);
-              const float2 x0 = make_float2(__uint_as_float(r0[2 * q]), __uint_as_float(r0[2 * q + 1]));
-              const float2 x1 = has1 ? make_float2(__uint_as_float(r1[2 * q]), __uint_as_float(r1[2 * q + 1])) : z;
-              const float2 x2 = has2 ? make_float2(__uint_as_float(r2[2 * q]), __uint_as_float(r2[2 * q + 1])) : z;
-              const float2 x3 = has3 ? make_float2(__uint_as_float(r3[2 * q]), __uint_as_float(r3[2 * q + 1])) : z;
-              float2 hi, lo, e1, e2;
-              two_sum2(x0, x1, hi, lo);
-              two_sum2(hi, x2, hi, e1);
-              lo = __fadd2_rn(lo, e1);
-              two_sum2(hi, lo, hi, e2);
-              lo = __fadd2_rn(e2, x3);
-              hv[2 * q] = hi.x;
-              hv[2 * q + 1] = hi.y;
-              lv[2 * q] = lo.x;
-              lv[2 * q + 1] = lo.y;
-            }
-            double* dst = crow + (int64_t)(ch * 8) * ld;
+              for (int q = 0; q < 4; ++q) {
+                const float2 z = make_float2(0.f, 0.f);
+                const float2 x0 = make_float2(__uint_as_float(r0[2 * q]), __uint_as_float(r0[2 * q + 1]));
+                const float2 x1 = has1 ? make_float2(__uint_as_float(r1[2 * q]), __uint_as_float(r1[2 * q + 1])) : z;
+                const float2 x2 = has2 ? make_float2(__uint_as_float(r2[2 * q]), __uint_as_float(r2[2 * q + 1])) : z;
+                const float2 x3 = has3 ? make_float2(__uint_as_float(r3[2 * q]), __uint_as_float(r3[2 * q + 1])) : z;
+                float2 hi, lo, e1, e2;
+                two_sum2(x0, x1, hi, lo);
+                two_sum2(hi, x2, hi, e1);
+                lo = __fadd2_rn(lo, e1);
+                two_sum2(hi, lo, hi, e2);
+                lo = __fadd2_rn(e2, x3);
+                hv[2 * q] = hi.x;
+                hv[2 * q + 1] = hi.y;
+                lv[2 * q] = lo.x;
+                lv[2 * q + 1] = lo.y;
+              }
+              double* dst = crow + (int64_t)(ch * 8) * ld;
 #pragma unroll
-            for (int j = 0; j < 8; ++j, dst += ld) {
-              const int fn = __shfl_sync(0xffffffffu, fl, ch * 8 + j);
-              if (!row_ok || ch * 8 + j >= ncols) continue;
-              const float hi = hv[j], lo = lv[j];
-              bool ok = true;
-              const int sc = em + fn;
-              double v = f32_scaled_to_f64(hi, sc, ok) + f32_scaled_to_f64(lo, sc, ok);
-              if (!ok) v = f32_pair_scaled_slow(hi, lo, sc);
-              *dst = (kc0 == wk.kc_lo) ? v : *dst + v;
+              for (int j = 0; j < 8; ++j, dst += ld) {
+                const int fn = __shfl_sync(0xffffffffu, fl, ch * 8 + j);
+                if (!row_ok || ch * 8 + j >= ncols) continue;
+                const float hi = hv[j], lo = lv[j];
+                bool ok = true;
+                const int sc = em + fn;
+                double v = f32_scaled_to_f64(hi, sc, ok) + f32_scaled_to_f64(lo, sc, ok);
+                if (!ok) v = f32_pair_scaled_slow(hi, lo, sc);
+                *dst = (kc0 == wk.kc_lo) ? v : *dst + v;
+              }
             }
           }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&ss->acc_empty[buf]));
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&ss->acc_empty[buf]));
-      }
-      if (split && done && active) {
-        // the warp that completes this region of the tile last adds the parts in part order
-        __threadfence();
-        __syncwarp();
-        int* cnt = counters + (int64_t)wk.slot * OZ_EPI_WARPS + (warp - 2);
-        int last = 0;
-        if (lane == 0) last = atomicAdd(cnt, 1) == wk.nparts - 1;
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last) {
+        if (split && done && active) {
+          // the warp that completes this region of the tile last adds the parts in part order
           __threadfence();
-          if (row_ok) {
-            const double* src = pbase + (int64_t)c0 * OZ_BM + row;
-            double* out = C + s.c_off + nb * s.M + m;
-            for (int j = 0; j < ncols; ++j, src += OZ_BM, out += s.M) {
-              double v = __ldcg(src);
-              for (int p = 1; p < wk.nparts; ++p) v += __ldcg(src + (int64_t)p * (OZ_BM * BN));
-              *out = v;
+          __syncwarp();
+          int* cnt = counters + (int64_t)wk.slot * OZ_EPI_WARPS + (warp - 2);
+          int last = 0;
+          if (lane == 0) last = atomicAdd(cnt, 1) == wk.nparts - 1;
+          last = __shfl_sync(0xffffffffu, last, 0);
+          if (last) {
+            __threadfence();
+            if (row_ok) {
+              const double* src = pbase + (int64_t)c0 * OZ_BM + row;
+              double* out = C + s.c_off + nb * s.M + m;
+              for (int j = 0; j < ncols; ++j, src += OZ_BM, out += s.M) {
+                double v = __ldcg(src);
+                for (int p = 1; p < wk.nparts; ++p) v += __ldcg(src + (int64_t)p * (OZ_BM * BN));
+                *out = v;
+              }
             }
+            if (lane == 0) *cnt = 0;  // ready for the next launch
           }
-          if (lane == 0) *cnt = 0;  // ready for the next launch
         }
       }
     }
@@ -807,8 +850,10 @@ template <int BN, int MODE>
 int set_smem_attr() {
   size_t most = 0;  // the largest need over every slice count this kernel accepts
   for (int sl = 2; sl <= OZ_MAX_SLICES; ++sl) most = std::max(most, oz_smem_bytes(sl, BN, OzMode<MODE>::ROW));
-  return cudaFuncSetAttribute(k_oz_gemm<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) ==
-                 cudaSuccess
+  return cudaFuncSetAttribute(k_oz_gemm<BN, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most) ==
+                     cudaSuccess &&
+                 cudaFuncSetAttribute(k_oz_gemm<BN, MODE, OZ_BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)most) == cudaSuccess
              ? TK_OK
              : TK_ERR_CUDA;
 }
@@ -992,19 +1037,8 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
   return TK_OK;
 }
 
-int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
-                      void* stream) {
-  const OzLayout* L = static_cast<const OzLayout*>(cp.oz.get());
-  if (!L) {
-    ctx->last_error = "split-precision tables missing";
-    return TK_ERR_UNSUPPORTED;
-  }
-  if (L->nwork == 0) return TK_OK;
-  if (((uintptr_t)ws & 15) != 0) {
-    ctx->last_error = "split-precision workspace must be 16-byte aligned";
-    return TK_ERR_WORKSPACE;
-  }
-  const size_t smem = oz_smem_bytes(L->slices, L->bn, L->mode == 0 ? OzMode<0>::ROW : OzMode<1>::ROW);
+namespace {
+int ensure_smem_attrs(Ctx* ctx) {
   static bool attr_set[64] = {false};
   if (ctx->device < 64 && !attr_set[ctx->device]) {
     if (set_smem_attr<OZ_BN_WIDE, 0>() != TK_OK || set_smem_attr<OZ_BN_NARROW, 0>() != TK_OK ||
@@ -1014,14 +1048,25 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
     }
     attr_set[ctx->device] = true;
   }
+  return TK_OK;
+}
+
+// Scale and slice one request's operands into its workspace and describe it for the GEMM launch.
+int prepare_ozaki_request(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
+                          void* stream, OzReq& R) {
+  const OzLayout* L = static_cast<const OzLayout*>(cp.oz.get());
+  if (((uintptr_t)ws & 15) != 0) {
+    ctx->last_error = "split-precision workspace must be 16-byte aligned";
+    return TK_ERR_WORKSPACE;
+  }
   char* w = (char*)ws;
   void* ta = w + L->off_ta;
   void* tb = w + L->off_tb;
   int32_t* sa = (int32_t*)(w + L->off_sa);
   int32_t* sb = (int32_t*)(w + L->off_sb);
-  CUtensorMap ma, mb;
-  if (make_tile_map(&ma, ta, L->ntiles_a, OZ_BM, L->mode) != TK_OK ||
-      make_tile_map(&mb, tb, L->ntiles_b, L->bn, L->mode) != TK_OK) {
+  std::memset(&R, 0, sizeof(R));
+  if (make_tile_map(&R.ma, ta, L->ntiles_a, OZ_BM, L->mode) != TK_OK ||
+      make_tile_map(&R.mb, tb, L->ntiles_b, L->bn, L->mode) != TK_OK) {
     ctx->last_error = "cuTensorMapEncodeTiled failed";
     return TK_ERR_CUDA;
   }
@@ -1047,31 +1092,90 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
     if (cudaGetLastError() != cudaSuccess) return TK_ERR_CUDA;
     ctx->launches += 1;
   }
-  {
-    ProfScope prof(ctx, "k_oz_gemm", stream);
-    const int grid = L->ncta;
-    double* part = (double*)(w + L->off_part);
-#define TK_OZ_LAUNCH(BNV, MODEV)                                                                           \
-  k_oz_gemm<BNV, MODEV><<<grid, OZ_THREADS, smem, s>>>(ma, mb, L->d_sectors, L->d_work, L->d_cta_work, L->pairs,  \
-                                                       L->slices, sa, sb, (double*)c, part, counters, ctx->d_status)
-    if (L->mode == 0) {
-      if (L->bn == OZ_BN_WIDE)
-        TK_OZ_LAUNCH(OZ_BN_WIDE, 0);
-      else
-        TK_OZ_LAUNCH(OZ_BN_NARROW, 0);
-    } else {
-      if (L->bn == OZ_BN_WIDE)
-        TK_OZ_LAUNCH(OZ_BN_WIDE, 1);
-      else
-        TK_OZ_LAUNCH(OZ_BN_NARROW, 1);
+  R.secs = L->d_sectors;
+  R.work = L->d_work;
+  R.cta_work = L->d_cta_work;
+  R.sa = sa;
+  R.sb = sb;
+  R.C = (double*)c;
+  R.partials = (double*)(w + L->off_part);
+  R.counters = counters;
+  R.ncta = L->ncta;
+  return TK_OK;
+}
+
+template <int NREQ>
+int launch_oz_gemm(Ctx* ctx, const OzLayout* L, const OzBatchT<NREQ>& B, int grid, void* stream) {
+  const size_t smem = oz_smem_bytes(L->slices, L->bn, L->mode == 0 ? OzMode<0>::ROW : OzMode<1>::ROW);
+  cudaStream_t s = (cudaStream_t)stream;
+  ProfScope prof(ctx, "k_oz_gemm", stream);
+  if (L->mode == 0) {
+    if (L->bn == OZ_BN_WIDE)
+      k_oz_gemm<OZ_BN_WIDE, 0, NREQ><<<grid, OZ_THREADS, smem, s>>>(B, L->pairs, L->slices, ctx->d_status);
+    else
+      k_oz_gemm<OZ_BN_NARROW, 0, NREQ><<<grid, OZ_THREADS, smem, s>>>(B, L->pairs, L->slices, ctx->d_status);
+  } else {
+    if (L->bn == OZ_BN_WIDE)
+      k_oz_gemm<OZ_BN_WIDE, 1, NREQ><<<grid, OZ_THREADS, smem, s>>>(B, L->pairs, L->slices, ctx->d_status);
+    else
+      k_oz_gemm<OZ_BN_NARROW, 1, NREQ><<<grid, OZ_THREADS, smem, s>>>(B, L->pairs, L->slices, ctx->d_status);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ctx->last_error = std::string("k_oz_gemm launch: ") + cudaGetErrorString(e);
+    return TK_ERR_CUDA;
+  }
+  ctx->launches += 1;
+  return TK_OK;
+}
+}  // namespace
+
+int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
+                      void* stream) {
+  const OzLayout* L = static_cast<const OzLayout*>(cp.oz.get());
+  if (!L) {
+    ctx->last_error = "split-precision tables missing";
+    return TK_ERR_UNSUPPORTED;
+  }
+  if (L->nwork == 0) return TK_OK;
+  int rc = ensure_smem_attrs(ctx);
+  if (rc != TK_OK) return rc;
+  OzBatchT<1> B;
+  std::memset(&B, 0, sizeof(B));
+  if ((rc = prepare_ozaki_request(ctx, cp, a, b, c, ws, stream, B.req[0])) != TK_OK) return rc;
+  B.nreq = 1;
+  return launch_oz_gemm<1>(ctx, L, B, L->ncta, stream);
+}
+
+int launch_gemm_ozaki_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const void* const* a,
+                            const void* const* b, void* const* c, void* const* ws, void* stream) {
+  int rc = ensure_smem_attrs(ctx);
+  if (rc != TK_OK) return rc;
+  // requests that share the launch parameters (mode, tile width, slice count) share a launch
+  std::vector<int> todo;
+  for (int i = 0; i < n; ++i) {
+    const OzLayout* L = static_cast<const OzLayout*>(plans[i]->oz.get());
+    if (L && L->nwork > 0) todo.push_back(i);
+  }
+  static thread_local OzBatchT<OZ_BATCH> B;  // ~12 KB of kernel parameters
+  while (!todo.empty()) {
+    const OzLayout* L0 = static_cast<const OzLayout*>(plans[todo[0]]->oz.get());
+    std::vector<int> rest;
+    std::memset(&B, 0, sizeof(B));
+    int grid = 0;
+    for (int i : todo) {
+      const OzLayout* L = static_cast<const OzLayout*>(plans[i]->oz.get());
+      if (B.nreq < OZ_BATCH && L->mode == L0->mode && L->bn == L0->bn && L->slices == L0->slices) {
+        if ((rc = prepare_ozaki_request(ctx, *plans[i], a[i], b[i], c[i], ws[i], stream, B.req[B.nreq])) != TK_OK)
+          return rc;
+        grid = std::max(grid, L->ncta);
+        B.nreq += 1;
+      } else {
+        rest.push_back(i);
+      }
     }
-#undef TK_OZ_LAUNCH
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      ctx->last_error = std::string("k_oz_gemm launch: ") + cudaGetErrorString(e);
-      return TK_ERR_CUDA;
-    }
-    ctx->launches += 1;
+    if ((rc = launch_oz_gemm<OZ_BATCH>(ctx, L0, B, grid, stream)) != TK_OK) return rc;
+    todo.swap(rest);
   }
   return TK_OK;
 }

@@ -306,6 +306,11 @@ int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream);
 int upload_gemm_tables(Ctx* ctx, ContractPlan& cp);
 int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
                       void* slices_ws, void* stream);
+// The split-precision GEMMs of several requests (their workspaces' slice regions in ws): scaling
+// and slicing per request, then one packed tensor-core launch per group of up to 32 requests that
+// share mode, tile width and slice count.
+int launch_gemm_ozaki_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const void* const* a,
+                            const void* const* b, void* const* c, void* const* ws, void* stream);
 int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp);
 // The launch sequence of one planned contraction with scratch at `ws` (Algorithm 4 / 8).
 int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,

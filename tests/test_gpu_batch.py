@@ -26,7 +26,7 @@ def _tm(ctx, sym, legs):
     return ctx.tmap([ctx.space(sym, s, d) for s, d in cod], [ctx.space(sym, s, d) for s, d in dom])
 
 
-def _requests(ctx, dtype, seed0):
+def _requests(ctx, dtype, seed0, gemm="fp64"):
     """(plan, A data, B data) for a mix of shapes: U(1) and SU(2) L.x, C0, a zero-block case,
     and one shape twice (two requests sharing a plan)."""
     from paper_2508_10076_gb300 import api
@@ -37,26 +37,29 @@ def _requests(ctx, dtype, seed0):
         V, P, W = wl.heff_spaces(sym, D)
         legs = wl.heff_legs(V, P, W)
         L, x = _tm(ctx, sym, legs["L"]), _tm(ctx, sym, legs["x"])
-        plan = api.contract_plan(ctx, L, *wl.LX_SPEC[:2], x, *wl.LX_SPEC[2:], dtype=dtype)
+        plan = api.contract_plan(ctx, L, *wl.LX_SPEC[:2], x, *wl.LX_SPEC[2:], dtype=dtype, gemm=gemm)
         reqs.append((plan, rnd(seed0 + 2 * k, L.numel), rnd(seed0 + 2 * k + 1, x.numel)))
     v = {-2: 1, -1: 2, 0: 3, 1: 2, 2: 1}
     A = _tm(ctx, "U1", ([(v, False), (v, False)], [(v, False), (v, False)]))
     B = _tm(ctx, "U1", ([(v, False), (v, True)], [(v, False), (v, False)]))
-    plan = api.contract_plan(ctx, A, *wl.C0_SPEC[:2], B, *wl.C0_SPEC[2:], dtype=dtype)
+    plan = api.contract_plan(ctx, A, *wl.C0_SPEC[:2], B, *wl.C0_SPEC[2:], dtype=dtype, gemm=gemm)
     reqs.append((plan, rnd(seed0 + 20, A.numel), rnd(seed0 + 21, B.numel)))
     A = _tm(ctx, "U1", ([({0: 2, 1: 3}, False)], [({0: 3}, False)]))
     B = _tm(ctx, "U1", ([({0: 3}, False)], [({0: 2, 1: 1}, False)]))
-    plan = api.contract_plan(ctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), dtype=dtype)
+    plan = api.contract_plan(ctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), dtype=dtype, gemm=gemm)
     reqs.append((plan, rnd(seed0 + 22, A.numel), rnd(seed0 + 23, B.numel)))
     dev = [(p, torch.from_numpy(np.ascontiguousarray(a)).to("cuda", tdt),
             torch.from_numpy(np.ascontiguousarray(b)).to("cuda", tdt)) for p, a, b in reqs]
     return dev, tdt
 
 
-@pytest.mark.parametrize("dtype", ["f64", "c128"])
-def test_batch_equals_each_request_alone(gctx, dtype):
+@pytest.mark.parametrize("dtype,gemm", [("f64", "fp64"), ("c128", "fp64"), ("f64", "ozaki"), ("f64", "tf32x3")])
+def test_batch_equals_each_request_alone(gctx, dtype, gemm):
+    """Split-precision batches pack every request's double-float rows into one launch and its
+    tensor-core products into one launch per (tile width, slice count): still the bits of each
+    request alone."""
     from paper_2508_10076_gb300 import api
-    reqs, tdt = _requests(gctx, dtype, 40)
+    reqs, tdt = _requests(gctx, dtype, 40, gemm)
     alone, outs, wss = [], [], []
     for plan, a, b in reqs:
         c = torch.full((plan.output().numel,), float("nan"), dtype=tdt, device="cuda")
@@ -85,7 +88,16 @@ def test_batch_rejects_mixed_modes_and_small_workspace(gctx):
     L, x = _tm(gctx, "U1", legs["L"]), _tm(gctx, "U1", legs["x"])
     oz = api.contract_plan(gctx, L, *wl.LX_SPEC[:2], x, *wl.LX_SPEC[2:], gemm="ozaki")
     ws = torch.empty(max(1, oz.workspace_bytes), dtype=torch.uint8, device="cuda")
-    with pytest.raises(api.TKError) as e:
-        api.contract_batch(gctx, [oz], [a], [b], [c], [ws])
+    ws64 = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
+    with pytest.raises(api.TKError) as e:  # mixed gemm modes
+        api.contract_batch(gctx, [plan, oz], [a, a], [b, b], [c, c], [ws64, ws])
+    assert e.value.code == 7
+    cz = api.contract_plan(gctx, L, *wl.LX_SPEC[:2], x, *wl.LX_SPEC[2:], dtype="c128", gemm="ozaki")
+    wsz = torch.empty(max(1, cz.workspace_bytes), dtype=torch.uint8, device="cuda")
+    cc = torch.empty(cz.output().numel, dtype=torch.complex128, device="cuda")
+    az = torch.zeros(L.numel, dtype=torch.complex128, device="cuda")
+    bz = torch.zeros(x.numel, dtype=torch.complex128, device="cuda")
+    with pytest.raises(api.TKError) as e:  # complex split precision runs one by one
+        api.contract_batch(gctx, [cz], [az], [bz], [cc], [wsz])
     assert e.value.code == 7
     api.contract_batch(gctx, [], [], [], [], [])  # empty batch: no-op
