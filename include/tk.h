@@ -204,8 +204,8 @@ int tk_contract(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, 
  * every input permute in one launch, the zero fill in one, every sector GEMM tile in one grouped
  * GEMM, every output permute in one (a stage with more than 160 segments is split into several
  * launches).  In the split-precision modes the double-float row blocks of all requests share one
- * launch and the tensor-core products one launch per group of up to 32 requests with the same
- * tile width and slice count (each request's operands are scaled and sliced by its own launches).
+ * launch, and up to 32 requests with the same tile width and slice count share one scaling, one
+ * slicing and one tensor-core launch.
  * Each c[i] equals what tk_contract would write for that request alone.  All plans must share
  * the dtype and the gemm mode, and complex split-precision plans are not batched (else
  * TK_ERR_UNSUPPORTED); pointer arrays are host arrays of device pointers; n = 0 is a no-op. */

@@ -279,13 +279,52 @@ __device__ __forceinline__ int exponent_of(double mx) {
   return -1074 + (64 - __clzll((long long)b));  // subnormal: highest set bit
 }
 
-__global__ void __launch_bounds__(256) k_oz_scale(const OzSector* __restrict__ secs, const OzJob* __restrict__ jobs,
-                                                  const double* __restrict__ A, const double* __restrict__ B,
-                                                  int32_t* __restrict__ scale_a, int32_t* __restrict__ scale_b,
-                                                  int* __restrict__ counters, int ncounters) {
-  if (blockIdx.x == 0)  // the GEMM's split-K arrival counters start at zero
-    for (int i = threadIdx.x; i < ncounters; i += blockDim.x) counters[i] = 0;
-  const OzJob jb = jobs[blockIdx.x];
+// One request of a scale or slice launch: its job list, operands, scale arrays and slice tiles;
+// its jobs are blocks [block0, block0 + njobs) of the launch.
+struct OzPrepSeg {
+  const OzSector* secs;
+  const OzJob* jobs;
+  const double* A;
+  const double* B;
+  int32_t* sa;
+  int32_t* sb;
+  int* counters;
+  void* ta;
+  void* tb;
+  int64_t block0;
+  int32_t ncounters, pad;
+};
+template <int NSEG>
+struct OzPrepT {
+  OzPrepSeg seg[NSEG];
+  int32_t nseg;
+};
+template <int NSEG>
+__device__ __forceinline__ const OzPrepSeg& prep_seg(const OzPrepT<NSEG>& P, int64_t& local) {
+  int lo = 0, hi = P.nseg - 1;  // the segment with the largest block0 <= blockIdx.x
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.seg[mid].block0 <= (int64_t)blockIdx.x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  local = (int64_t)blockIdx.x - P.seg[lo].block0;
+  return P.seg[lo];
+}
+
+template <int NSEG>
+__global__ void __launch_bounds__(256) k_oz_scale(const __grid_constant__ OzPrepT<NSEG> P) {
+  int64_t local;
+  const OzPrepSeg& g = prep_seg(P, local);
+  const OzSector* __restrict__ secs = g.secs;
+  const double* __restrict__ A = g.A;
+  const double* __restrict__ B = g.B;
+  int32_t* __restrict__ scale_a = g.sa;
+  int32_t* __restrict__ scale_b = g.sb;
+  if (local == 0)  // the GEMM's split-K arrival counters start at zero
+    for (int i = threadIdx.x; i < g.ncounters; i += blockDim.x) g.counters[i] = 0;
+  const OzJob jb = g.jobs[local];
   const OzSector s = secs[jb.sector];
   const int64_t k0 = (int64_t)jb.kc * OZ_SCALE_KCHUNK;
   const int64_t k1 = min(s.K, k0 + OZ_SCALE_KCHUNK);
@@ -404,14 +443,19 @@ __device__ __forceinline__ void oz_slice_pair(double v0, double v1, int e, __nv_
 // pair) store and a half-warp writes a full tile row; A~ (column-major, rows contiguous) is staged
 // through shared memory to keep its reads coalesced, B~ (k contiguous) is read directly.
 // MODE 0 writes s BF16 digit slices, MODE 1 the TF32 pair (hi, lo).
-template <int MODE>
-__global__ void __launch_bounds__(256) k_oz_slice(const OzSector* __restrict__ secs, const OzJob* __restrict__ jobs,
-                                                  const double* __restrict__ A, const double* __restrict__ B,
-                                                  const int32_t* __restrict__ scale_a,
-                                                  const int32_t* __restrict__ scale_b, void* __restrict__ tiles_a,
-                                                  void* __restrict__ tiles_b, int nslices) {
+template <int MODE, int NSEG>
+__global__ void __launch_bounds__(256) k_oz_slice(const __grid_constant__ OzPrepT<NSEG> P, int nslices) {
   __shared__ double xs[OZ_BK][OZ_TROWS + 1];
-  const OzJob jb = jobs[blockIdx.x];
+  int64_t local;
+  const OzPrepSeg& g = prep_seg(P, local);
+  const OzSector* __restrict__ secs = g.secs;
+  const double* __restrict__ A = g.A;
+  const double* __restrict__ B = g.B;
+  const int32_t* __restrict__ scale_a = g.sa;
+  const int32_t* __restrict__ scale_b = g.sb;
+  void* __restrict__ tiles_a = g.ta;
+  void* __restrict__ tiles_b = g.tb;
+  const OzJob jb = g.jobs[local];
   const OzSector s = secs[jb.sector];
   const int op = jb.operand;
   const int64_t R = op == 0 ? s.M : s.N;
@@ -1051,9 +1095,9 @@ int ensure_smem_attrs(Ctx* ctx) {
   return TK_OK;
 }
 
-// Scale and slice one request's operands into its workspace and describe it for the GEMM launch.
-int prepare_ozaki_request(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
-                          void* stream, OzReq& R) {
+// Describe one request for the scale / slice launches and the GEMM launch; clears its scale arrays.
+int describe_ozaki_request(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
+                           void* stream, OzPrepSeg& P, OzReq& R) {
   const OzLayout* L = static_cast<const OzLayout*>(cp.oz.get());
   if (((uintptr_t)ws & 15) != 0) {
     ctx->last_error = "split-precision workspace must be 16-byte aligned";
@@ -1070,28 +1114,19 @@ int prepare_ozaki_request(Ctx* ctx, const ContractPlan& cp, const void* a, const
     ctx->last_error = "cuTensorMapEncodeTiled failed";
     return TK_ERR_CUDA;
   }
-  cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(sa, 0x80, L->off_sb - L->off_sa + (size_t)L->ncols_b * 4, s) != cudaSuccess) return TK_ERR_CUDA;
+  if (cudaMemsetAsync(sa, 0x80, L->off_sb - L->off_sa + (size_t)L->ncols_b * 4, (cudaStream_t)stream) != cudaSuccess)
+    return TK_ERR_CUDA;
   int* counters = (int*)(w + L->off_cnt);  // cleared by the scale kernel
-  {
-    ProfScope prof(ctx, "k_oz_scale", stream);
-    k_oz_scale<<<(unsigned)L->nscale_jobs, 256, 0, s>>>(L->d_sectors, L->d_scale_jobs, (const double*)a,
-                                                       (const double*)b, sa, sb, counters,
-                                                       (int)(L->nslots * OZ_EPI_WARPS));
-    if (cudaGetLastError() != cudaSuccess) return TK_ERR_CUDA;
-    ctx->launches += 1;
-  }
-  {
-    ProfScope prof(ctx, "k_oz_slice", stream);
-    if (L->mode == 0)
-      k_oz_slice<0><<<(unsigned)L->nslice_jobs, 256, 0, s>>>(L->d_sectors, L->d_slice_jobs, (const double*)a,
-                                                            (const double*)b, sa, sb, ta, tb, L->slices);
-    else
-      k_oz_slice<1><<<(unsigned)L->nslice_jobs, 256, 0, s>>>(L->d_sectors, L->d_slice_jobs, (const double*)a,
-                                                            (const double*)b, sa, sb, ta, tb, L->slices);
-    if (cudaGetLastError() != cudaSuccess) return TK_ERR_CUDA;
-    ctx->launches += 1;
-  }
+  std::memset(&P, 0, sizeof(P));
+  P.secs = L->d_sectors;
+  P.A = (const double*)a;
+  P.B = (const double*)b;
+  P.sa = sa;
+  P.sb = sb;
+  P.counters = counters;
+  P.ncounters = (int32_t)(L->nslots * OZ_EPI_WARPS);
+  P.ta = ta;
+  P.tb = tb;
   R.secs = L->d_sectors;
   R.work = L->d_work;
   R.cta_work = L->d_cta_work;
@@ -1101,6 +1136,40 @@ int prepare_ozaki_request(Ctx* ctx, const ContractPlan& cp, const void* a, const
   R.partials = (double*)(w + L->off_part);
   R.counters = counters;
   R.ncta = L->ncta;
+  return TK_OK;
+}
+
+// Scale, then slice, the operands of every request of one batch (one launch each).
+template <int NSEG>
+int launch_oz_prep(Ctx* ctx, const OzLayout* const* lay, OzPrepT<NSEG>& P, int mode, int nslices, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t blocks = 0;
+  for (int i = 0; i < P.nseg; ++i) {
+    P.seg[i].block0 = blocks;
+    P.seg[i].jobs = lay[i]->d_scale_jobs;
+    blocks += lay[i]->nscale_jobs;
+  }
+  if (blocks > 0) {
+    ProfScope prof(ctx, "k_oz_scale", stream);
+    k_oz_scale<NSEG><<<(unsigned)blocks, 256, 0, s>>>(P);
+    if (cudaGetLastError() != cudaSuccess) return TK_ERR_CUDA;
+    ctx->launches += 1;
+  }
+  blocks = 0;
+  for (int i = 0; i < P.nseg; ++i) {
+    P.seg[i].block0 = blocks;
+    P.seg[i].jobs = lay[i]->d_slice_jobs;
+    blocks += lay[i]->nslice_jobs;
+  }
+  if (blocks > 0) {
+    ProfScope prof(ctx, "k_oz_slice", stream);
+    if (mode == 0)
+      k_oz_slice<0, NSEG><<<(unsigned)blocks, 256, 0, s>>>(P, nslices);
+    else
+      k_oz_slice<1, NSEG><<<(unsigned)blocks, 256, 0, s>>>(P, nslices);
+    if (cudaGetLastError() != cudaSuccess) return TK_ERR_CUDA;
+    ctx->launches += 1;
+  }
   return TK_OK;
 }
 
@@ -1141,9 +1210,14 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
   int rc = ensure_smem_attrs(ctx);
   if (rc != TK_OK) return rc;
   OzBatchT<1> B;
+  OzPrepT<1> P;
   std::memset(&B, 0, sizeof(B));
-  if ((rc = prepare_ozaki_request(ctx, cp, a, b, c, ws, stream, B.req[0])) != TK_OK) return rc;
+  std::memset(&P, 0, sizeof(P));
+  if ((rc = describe_ozaki_request(ctx, cp, a, b, c, ws, stream, P.seg[0], B.req[0])) != TK_OK) return rc;
   B.nreq = 1;
+  P.nseg = 1;
+  const OzLayout* lay[1] = {L};
+  if ((rc = launch_oz_prep<1>(ctx, lay, P, L->mode, L->slices, stream)) != TK_OK) return rc;
   return launch_oz_gemm<1>(ctx, L, B, L->ncta, stream);
 }
 
@@ -1158,22 +1232,29 @@ int launch_gemm_ozaki_batch(Ctx* ctx, int n, const ContractPlan* const* plans, c
     if (L && L->nwork > 0) todo.push_back(i);
   }
   static thread_local OzBatchT<OZ_BATCH> B;  // ~12 KB of kernel parameters
+  static thread_local OzPrepT<OZ_BATCH> P;   // ~3 KB
   while (!todo.empty()) {
     const OzLayout* L0 = static_cast<const OzLayout*>(plans[todo[0]]->oz.get());
     std::vector<int> rest;
     std::memset(&B, 0, sizeof(B));
+    std::memset(&P, 0, sizeof(P));
+    const OzLayout* lay[OZ_BATCH];
     int grid = 0;
     for (int i : todo) {
       const OzLayout* L = static_cast<const OzLayout*>(plans[i]->oz.get());
       if (B.nreq < OZ_BATCH && L->mode == L0->mode && L->bn == L0->bn && L->slices == L0->slices) {
-        if ((rc = prepare_ozaki_request(ctx, *plans[i], a[i], b[i], c[i], ws[i], stream, B.req[B.nreq])) != TK_OK)
+        if ((rc = describe_ozaki_request(ctx, *plans[i], a[i], b[i], c[i], ws[i], stream, P.seg[B.nreq],
+                                         B.req[B.nreq])) != TK_OK)
           return rc;
+        lay[B.nreq] = L;
         grid = std::max(grid, L->ncta);
         B.nreq += 1;
       } else {
         rest.push_back(i);
       }
     }
+    P.nseg = B.nreq;
+    if ((rc = launch_oz_prep<OZ_BATCH>(ctx, lay, P, L0->mode, L0->slices, stream)) != TK_OK) return rc;
     if ((rc = launch_oz_gemm<OZ_BATCH>(ctx, L0, B, grid, stream)) != TK_OK) return rc;
     todo.swap(rest);
   }
