@@ -239,3 +239,31 @@ def test_single_site_heff_split_precision(gctx):
     gctx.sync()
     cs, rd = oracle_heff("SU2", 256, seed=8, tier="block", sites=1)[-1]
     assert rel_frobenius_per_block(cs, got.cpu().numpy(), rd) <= SPLIT_TOL
+
+
+EDGE_CASES = [
+    # (legs of A, legs of B): contraction of A's domain with B's codomain
+    # an empty inner dimension (sector 1 has no K): zero block
+    (([({0: 2, 1: 3}, False)], [({0: 3}, False)]), ([({0: 3}, False)], [({0: 2, 1: 1}, False)])),
+    # single rows / columns and K = 1 (thin products on the double-float rows)
+    (([({0: 1, 1: 1}, False)], [({0: 1, 1: 1}, False)]), ([({0: 1, 1: 1}, False)], [({0: 1, 1: 1}, False)])),
+    # M just over one 128-row tile, N over a 128-column tile by 9, K crossing 32-deep chunks raggedly
+    (([({0: 129, 1: 7}, False)], [({0: 33, 1: 70}, False)]), ([({0: 33, 1: 70}, False)], [({0: 137, 1: 16}, False)])),
+]
+
+
+@pytest.mark.parametrize("gemm", ["ozaki", "tf32x3"])
+@pytest.mark.parametrize("case", range(len(EDGE_CASES)))
+def test_split_precision_edge_cases(gctx, gemm, case):
+    """Split-precision plans on degenerate and ragged shapes: every output entry written (no NaN
+    left), values against the oracle within the mode's bound."""
+    api = _api()
+    la, lb = EDGE_CASES[case]
+    A, B = _tm(gctx, "U1", la), _tm(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), gemm=gemm)
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    xa, xb = wl.normal(70 + case, oa.numel), wl.normal(80 + case, ob.numel)
+    cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
+    got = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda()).cpu().numpy()
+    assert not np.isnan(got).any()
+    assert rel_frobenius_per_block(cs, got, ref) <= (SPLIT_TOL if gemm == "ozaki" else 2e-5)
