@@ -164,6 +164,11 @@ int tk_contract_plan(tk_ctx* ctx, const tk_tmap* a, int npa, const int* pa, int 
                      const tk_tmap* b, int npb, const int* pb, int nqb, const int* qb,
                      int npab, const int* pab, int nqab, const int* qab, int dtype, int gemm_mode,
                      int slices, tk_plan** out);
+/* Composition A o B : cod(A) <- dom(B) of A : cod(A) <- dom(A) and B : cod(B) <- dom(B) with
+ * dom(A) = cod(B) (Sec. 2.3): the contraction plan with every leg kept in place (TK_ERR_SPACE_MISMATCH
+ * if the spaces or their duality differ). */
+int tk_compose_plan(tk_ctx* ctx, const tk_tmap* a, const tk_tmap* b, int dtype, int gemm_mode, int slices,
+                    tk_plan** out);
 void tk_plan_destroy(tk_plan* plan);
 int tk_plan_output(tk_ctx* ctx, const tk_plan* plan, tk_tmap** out);  /* result structure     */
 size_t tk_plan_workspace_bytes(const tk_plan* plan);  /* device scratch needed by tk_contract  */

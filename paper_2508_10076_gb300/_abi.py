@@ -45,6 +45,7 @@ SIGNATURES = {
     "tk_contract_plan": (C.c_int, [c_vp, c_vp, C.c_int, c_intp, C.c_int, c_intp, c_vp, C.c_int, c_intp,
                                    C.c_int, c_intp, C.c_int, c_intp, C.c_int, c_intp, C.c_int, C.c_int,
                                    C.c_int, C.POINTER(c_vp)]),
+    "tk_compose_plan": (C.c_int, [c_vp, c_vp, c_vp, C.c_int, C.c_int, C.c_int, C.POINTER(c_vp)]),
     "tk_plan_destroy": (None, [c_vp]),
     "tk_plan_output": (C.c_int, [c_vp, c_vp, C.POINTER(c_vp)]),
     "tk_plan_workspace_bytes": (C.c_size_t, [c_vp]),

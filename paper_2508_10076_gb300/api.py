@@ -327,6 +327,13 @@ def svd_truncate(ctx, plan, keep, u, s, vh, ut, st, vht, stream=None):
                                   _stream_handle(stream)), ctx)
 
 
+def compose_plan(ctx, a, b, dtype="f64", gemm="fp64", slices=0):
+    """Plan of the composition A o B (domain of A = codomain of B), legs kept in place."""
+    h = C.c_void_p()
+    _check(_lib().tk_compose_plan(ctx._h, a._h, b._h, DTYPE[dtype], GEMM[gemm], int(slices), C.byref(h)), ctx)
+    return Plan(ctx, h, "contract")
+
+
 def contract_plan(ctx, a, pa, qa, b, pb, qb, pab, qab, dtype="f64", gemm="fp64", slices=0):
     args = []
     for xs in (pa, qa):

@@ -399,6 +399,24 @@ int tk_contract_plan(tk_ctx* ctx, const tk_tmap* a, int npa, const int* pa, int 
   });
 }
 
+int tk_compose_plan(tk_ctx* ctx, const tk_tmap* a, const tk_tmap* b, int dtype, int gemm_mode, int slices,
+                    tk_plan** out) {
+  if (!ctx || !a || !b || !out) return fail(ctx, TK_ERR_ARG, "null argument");
+  // A o B = the contraction of A's domain with B's codomain, legs kept in place (Sec. 2.3)
+  const int n1a = (int)a->st->cod.size(), n2a = (int)a->st->dom.size();
+  const int n1b = (int)b->st->cod.size(), n2b = (int)b->st->dom.size();
+  std::vector<int> pa(n1a), qa(n2a), pb(n1b), qb(n2b), pab(n1a), qab(n2b);
+  for (int i = 0; i < n1a; ++i) pa[i] = pab[i] = i;
+  for (int i = 0; i < n2a; ++i) qa[i] = n1a + i;
+  for (int i = 0; i < n1b; ++i) pb[i] = i;
+  for (int i = 0; i < n2b; ++i) {
+    qb[i] = n1b + i;
+    qab[i] = n1a + i;
+  }
+  return tk_contract_plan(ctx, a, n1a, pa.data(), n2a, qa.data(), b, n1b, pb.data(), n2b, qb.data(), n1a,
+                          pab.data(), n2b, qab.data(), dtype, gemm_mode, slices, out);
+}
+
 void tk_plan_destroy(tk_plan* plan) { delete plan; }
 
 int tk_plan_output(tk_ctx* ctx, const tk_plan* plan, tk_tmap** out) {

@@ -404,3 +404,24 @@ def test_heff_chain_su2_heisenberg(gctx, gemm, tol):
     for i, ((cs, rd), b) in enumerate(zip(ref, outs)):
         assert ch.steps[i].out.blocks() == [(c, r, k, o) for c, r, k, o in cs.blocks]
         assert rel_frobenius_per_block(cs, b.cpu().numpy(), rd) <= tol, i
+
+
+@pytest.mark.parametrize("gemm,tol", [("fp64", FP64_TOL), ("ozaki", 1e-10)])
+def test_compose_parity(gctx, gemm, tol):
+    """Composition A o B (Sec. 2.3): SU(2) blocks, against the oracle's block composition."""
+    api = _api()
+    v = {0: 40, 1: 70, 2: 55, 3: 20}
+    p = {1: 1}
+    la = ([(v, False), (p, False)], [(v, False)])
+    lb = ([(v, False)], [(v, False), (p, True)])
+    oa, ob = ostruct("SU2", la), ostruct("SU2", lb)
+    xa, xb = wl.normal(91, oa.numel), wl.normal(92, ob.numel)
+    cs, ref = ops.compose_block(oa, xa, ob, xb)
+    A, B = _lib_tmap(gctx, "SU2", la), _lib_tmap(gctx, "SU2", lb)
+    plan = api.compose_plan(gctx, A, B, gemm=gemm)
+    assert plan.output().blocks() == [(c, r, k, o) for c, r, k, o in cs.blocks]
+    ws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
+    c = torch.full((plan.output().numel,), float("nan"), dtype=torch.float64, device="cuda")
+    api.contract(gctx, plan, _dev(xa), _dev(xb), c, ws)
+    gctx.sync()
+    assert rel_frobenius_per_block(cs, c.cpu().numpy(), ref) <= tol

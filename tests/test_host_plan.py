@@ -218,3 +218,22 @@ def test_mpo_leg_permute_uses_vector_tiles(hctx):
     ost = TensorStructure([GradedSpace(U1, s, d) for s, d in cod], [GradedSpace(U1, s, d) for s, d in dom])
     out, _ = _oracle_transform_offsets(ost, (0, 2), (1,))
     _same_structure(out, p.output())
+
+
+def test_compose_plan_structure_matches_oracle(hctx):
+    """A o B (Sec. 2.3) as a plan: output structure and block flops as the oracle's composition;
+    a domain / codomain mismatch is refused."""
+    v = {-1: 2, 0: 3, 1: 1}
+    w = {0: 2, 1: 2}
+    la = ([(v, False), (w, True)], [(v, False)])
+    lb = ([(v, False)], [(w, False)])
+    A, B = _mk(hctx, U1, la)[1], _mk(hctx, U1, lb)[1]
+    oa, ob = _mk(hctx, U1, la)[0], _mk(hctx, U1, lb)[0]
+    plan = api.compose_plan(hctx, A, B)
+    cs, _ = ops.compose_block(oa, np.zeros(oa.numel), ob, np.zeros(ob.numel))
+    _same_structure(cs, plan.output())
+    bb = {c: cols for c, rows, cols, _ in ob.blocks}
+    assert plan.flops == sum(2 * rows * k * bb[c] for c, rows, k, _ in oa.blocks if c in bb)
+    with pytest.raises(api.TKError) as e:
+        api.compose_plan(hctx, B, A)  # dom(B) = W is not cod(A) = V (x) W*
+    assert e.value.code == 2
