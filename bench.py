@@ -254,10 +254,10 @@ def run_ours(args):
         work.run()
     ctx.sync()
     # one application as a CUDA graph (eager launches if capture is unavailable)
-    step_fn, per_step_launches, mode = work.run, None, "eager"
+    step_fn, per_step_launches, mode, graph_out = work.run, None, "eager", None
     if not args.eager:
         try:
-            graph, _, per_step_launches = work.capture()
+            graph, graph_out, per_step_launches = work.capture()
             step_fn, mode = graph.replay, "cuda_graph"
             for _ in range(max(3, args.warmup)):
                 step_fn()
@@ -292,8 +292,11 @@ def run_ours(args):
     ctx.sync()
     prof = ctx.profile_read()
     ctx.profile(False)
-    # ---------------- end to end: pinned host inputs -> device -> chain -> host result
+    # ---------------- end to end: pinned host inputs -> device -> chain -> host result (the chain
+    # replayed from its CUDA graph when captured: the graph reads the same input buffers)
     ins, run = _inputs_and_output(work)
+    if graph_out is not None:
+        run = lambda: (step_fn(), graph_out)[1]  # noqa: E731
     host_in = [x.cpu().pin_memory() for x in ins]
     out_dev = run()
     host_out = torch.empty(out_dev.numel(), dtype=out_dev.dtype).pin_memory()
