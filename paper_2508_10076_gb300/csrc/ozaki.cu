@@ -20,11 +20,13 @@
 // tiles (64-byte rows); one persistent GEMM launch walks a work list of (sector, 128-row tile,
 // column tile) items, the last column tile of a sector as narrow as its remainder (MMA N a
 // multiple of 16).  Per CTA: warp 0 issues TMA loads (cp.async.bulk.tensor, 64-byte swizzle) of
-// all s A slices and all s B slices of one 32-deep k-chunk into a stage (two stages); one thread
-// of warp 1 issues every slice-pair MMA from the resident stage; warps 2..9 drain TMEM into
-// registers, release it to the MMA warp at once, and finish the FP64 conversion and the stores
-// while the next tile's MMAs run.  Every mbarrier wait is bounded: on timeout the kernel records
-// an error in the context's status word, drains its own copies and MMAs (bounded again), frees
+// all s A slices and all s B slices of one 32-deep k-chunk into a stage (two to four); one thread
+// of warp 1 issues every slice-pair MMA from the resident stage; sixteen epilogue warps (2..17,
+// four per TMEM lane quadrant) read the accumulators eight columns at a time, convert to FP64,
+// store, and then hand the buffer back to the MMA warp.  With 128-column tiles the four
+// accumulators fill TMEM, so the next tile's MMAs wait for that epilogue; 64-column tiles have
+// two buffers and overlap it.  Every mbarrier wait is bounded: on timeout the kernel records an
+// error in the context's status word, drains its own copies and MMAs (bounded again), frees
 // TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
