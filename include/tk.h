@@ -98,6 +98,13 @@ const char* tk_ctx_last_error(const tk_ctx* ctx);
 int tk_ctx_sync(tk_ctx* ctx, void* stream);
 /* Number of the library's own kernels launched through this context so far. */
 int64_t tk_ctx_launch_count(const tk_ctx* ctx);
+/* Failure-path self-test of the device-side bounded waits: launches (asynchronously, on
+ * `stream`) one CTA that waits on an mbarrier nobody completes, using the same bounded wait as
+ * the split-precision GEMM pipeline (limit 2 s).  When the limit runs out the kernel writes the
+ * timeout into the context's status word and returns, so the next tk_ctx_sync() returns
+ * TK_ERR_TIMEOUT (kernel tag 9 in tk_ctx_last_error), clears the word, and the context stays
+ * usable.  Returns TK_OK once launched; TK_ERR_NO_DEVICE for a host-only context. */
+int tk_ctx_selftest_timeout(tk_ctx* ctx, void* stream);
 /* Kernel profiling.  enable != 0: every later launch through ctx is bracketed by CUDA events
  * recorded on its own stream; enable == 0 stops recording.  tk_ctx_profile_read waits for the
  * recorded events and returns, per kernel name (at most max entries, names NUL-terminated in

@@ -23,6 +23,7 @@ SIGNATURES = {
     "tk_ctx_last_error": (C.c_char_p, [c_vp]),
     "tk_ctx_sync": (C.c_int, [c_vp, c_vp]),
     "tk_ctx_launch_count": (C.c_int64, [c_vp]),
+    "tk_ctx_selftest_timeout": (C.c_int, [c_vp, c_vp]),
     "tk_ctx_profile": (C.c_int, [c_vp, C.c_int]),
     "tk_ctx_profile_read": (C.c_int, [c_vp, C.c_int, C.c_char_p, c_i64p, c_dblp, c_intp]),
     "tk_space_create": (C.c_int, [c_vp, C.c_int, C.c_int, c_i32p, c_i64p, C.c_int, C.POINTER(c_vp)]),

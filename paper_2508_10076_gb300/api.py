@@ -93,6 +93,11 @@ class Context:
     def launches(self):
         return int(_lib().tk_ctx_launch_count(self._h))
 
+    def selftest_timeout(self, stream=None):
+        """Launch the bounded-wait self-test; the next sync() raises TKError (TK_ERR_TIMEOUT)."""
+        h = _stream_handle(stream) if self.device >= 0 else C.c_void_p(0)  # host-only: refused by the library
+        _check(_lib().tk_ctx_selftest_timeout(self._h, h), self)
+
     def profile(self, enable=True):
         _check(_lib().tk_ctx_profile(self._h, int(bool(enable))), self)
 

@@ -143,6 +143,13 @@ int tk_ctx_sync(tk_ctx* ctx, void* stream) {
 
 int64_t tk_ctx_launch_count(const tk_ctx* ctx) { return ctx ? ctx->c.launches : -1; }
 
+int tk_ctx_selftest_timeout(tk_ctx* ctx, void* stream) {
+  if (!ctx) return TK_ERR_ARG;
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  return guarded(ctx, [&] { return launch_wait_selftest(&ctx->c, stream); });
+}
+
 int tk_ctx_profile(tk_ctx* ctx, int enable) {
   if (!ctx) return TK_ERR_ARG;
   if (ctx->c.device < 0) return fail(ctx, TK_ERR_NO_DEVICE, "profiling needs a device context");

@@ -856,6 +856,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
 }
 
+// Failure-path check of the bounded waits: one mbarrier that expects an arrival nobody makes,
+// waited on by the same bounded wait the GEMM pipeline uses.  The wait gives up after its limit,
+// the kernel records the timeout in the context's status word (tag 9) and returns; nothing is in
+// flight and no TMEM is held, so the context stays usable.
+__global__ void k_wait_selftest(int* __restrict__ status) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(smem_u32(&bar), 0, &abort_flag, true)) {
+    atomicExch(status, 1);
+    atomicExch(status + 1, 9);  // kernel tag: wait self-test
+  }
+}
+
 // ------------------------------------------------------------------ host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -1260,6 +1279,13 @@ int launch_gemm_ozaki_batch(Ctx* ctx, int n, const ContractPlan* const* plans, c
     if ((rc = launch_oz_gemm<OZ_BATCH>(ctx, L0, B, grid, stream)) != TK_OK) return rc;
     todo.swap(rest);
   }
+  return TK_OK;
+}
+
+int launch_wait_selftest(Ctx* ctx, void* stream) {
+  k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(ctx->d_status);
+  if (cudaGetLastError() != cudaSuccess) return TK_ERR_CUDA;
+  ctx->launches += 1;
   return TK_OK;
 }
 

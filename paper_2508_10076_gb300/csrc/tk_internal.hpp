@@ -312,6 +312,8 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
 int launch_gemm_ozaki_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const void* const* a,
                             const void* const* b, void* const* c, void* const* ws, void* stream);
 int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp);
+// One-CTA kernel whose bounded mbarrier wait is left to run out (tk_ctx_selftest_timeout).
+int launch_wait_selftest(Ctx* ctx, void* stream);
 // The launch sequence of one planned contraction with scratch at `ws` (Algorithm 4 / 8).
 int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
                  void* stream);
