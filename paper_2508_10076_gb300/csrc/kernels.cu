@@ -1128,8 +1128,9 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
       const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want_rows, (int64_t)SPLIT_MAX, g.K / 8}));
       const int32_t cfg = cp.gemm_mode == TK_GEMM_FP64 ? CFG_ROWS : CFG_ROWS_DF;
       const int rpt = rows_per_thread(g);
-      // a CTA walks several row groups of a long product that needs one K chunk and no split
-      const int nblk = (nsplit == 1 && g.K <= ROWS_KCHUNK && rpt > 1) ? 4 : 1;
+      // a CTA walks several row groups of a product that needs one K chunk and no split: four
+      // of a long product, two of a shorter one when the launch still has four CTAs per SM
+      const int nblk = (nsplit == 1 && g.K <= ROWS_KCHUNK) ? (rpt > 1 ? 4 : rows_ctas >= 4 * sms ? 2 : 1) : 1;
       const int64_t rb = 256 * rpt * nblk;
       for (int64_t m0 = 0; m0 < g.M; m0 += rb)
         emit((int32_t)i, m0, 0, cfg, g.K, nsplit, 8, (int64_t)256 * rpt * g.N,
