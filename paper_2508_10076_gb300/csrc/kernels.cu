@@ -1129,7 +1129,8 @@ int upload_gemm_tables(Ctx* ctx, ContractPlan& cp) {
       const int32_t cfg = cp.gemm_mode == TK_GEMM_FP64 ? CFG_ROWS : CFG_ROWS_DF;
       const int rpt = rows_per_thread(g);
       // a CTA walks several row groups of a product that needs one K chunk and no split: four
-      // of a long product, two of a shorter one when the launch still has four CTAs per SM
+      // of a long product, two of a shorter one when the launch has at least four one-group
+      // blocks per SM (so at least two paired blocks per SM remain)
       const int nblk = (nsplit == 1 && g.K <= ROWS_KCHUNK) ? (rpt > 1 ? 4 : rows_ctas >= 4 * sms ? 2 : 1) : 1;
       const int64_t rb = 256 * rpt * nblk;
       for (int64_t m0 = 0; m0 < g.M; m0 += rb)
