@@ -425,3 +425,38 @@ def test_compose_parity(gctx, gemm, tol):
     api.contract(gctx, plan, _dev(xa), _dev(xb), c, ws)
     gctx.sync()
     assert rel_frobenius_per_block(cs, c.cpu().numpy(), ref) <= tol
+
+
+@pytest.mark.parametrize("dtype", ["f64", "c128"])
+@pytest.mark.parametrize("gemm,tol", [("fp64", FP64_TOL), ("ozaki", 1e-10)])
+@pytest.mark.parametrize("sym", ["Z2", "Z2xU1"])
+def test_z2_family_contraction(gctx, sym, gemm, tol, dtype):
+    """Z2 and Z2 x U(1) (parity x charge, bosonic braiding) sectors through the L.x contraction:
+    block structure bit-exact, values against the oracle block tier in FP64 and split precision,
+    real and complex."""
+    from oracle.symmetry import Z2xU1
+    api = _api()
+    if sym == "Z2":
+        vs, ps, ws = {0: 70, 1: 55}, {0: 1, 1: 1}, {0: 3, 1: 2}
+    else:
+        P = Z2xU1.pair
+        vs = {P(a, q): n for (a, q), n in {(0, -2): 11, (1, -1): 25, (0, 0): 38, (1, 0): 14, (0, 1): 27,
+                                             (1, 1): 30, (0, 2): 9}.items()}
+        ps = {P(1, 1): 1, P(1, -1): 1, P(0, 0): 1}
+        ws = {P(0, 0): 2, P(0, 2): 1, P(0, -2): 1}
+    la = ([(vs, False)], [(vs, False), (ws, False)])
+    lx = ([(vs, False), (ps, False)], [(vs, False), (ps, True)])
+    oa, ox = ostruct(sym, la), ostruct(sym, lx)
+    gen = wl.normal_complex if dtype == "c128" else wl.normal
+    xa, xx = gen(41, oa.numel), gen(42, ox.numel)
+    spec = ((0, 2), (1,), (0,), (1, 2, 3), (0, 1, 2, 3, 4), ())
+    cs, ref = ops.contract(oa, xa, *spec[:2], ox, xx, *spec[2:], tier="block")
+    A, X = _lib_tmap(gctx, sym, la), _lib_tmap(gctx, sym, lx)
+    plan = api.contract_plan(gctx, A, *spec[:2], X, *spec[2:], dtype=dtype, gemm=gemm)
+    assert plan.output().blocks() == [(c, r, k, o) for c, r, k, o in cs.blocks]
+    ws_ = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
+    tdt = torch.complex128 if dtype == "c128" else torch.float64
+    c = torch.full((plan.output().numel,), float("nan"), dtype=tdt, device="cuda")
+    api.contract(gctx, plan, _dev(xa), _dev(xx), c, ws_)
+    gctx.sync()
+    assert rel_frobenius_per_block(cs, c.cpu().numpy(), ref) <= tol
