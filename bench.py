@@ -168,6 +168,23 @@ def cpu_baseline(name, budget_s=15.0):
     return n, dt, cores
 
 
+def cpu_baseline_single_thread(name, budget_s):
+    """The same oracle run in a fresh process whose BLAS and OpenMP pools hold one thread (the
+    paper's own timings are single-threaded); returns (applications, seconds)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+              "NUMEXPR_NUM_THREADS", "VECLIB_MAXIMUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""  # the worker needs no GPU
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--config", name,
+                        "--cpu-budget", str(budget_s)], env=env, capture_output=True, text=True,
+                       timeout=20 * budget_s + 300)
+    if r.returncode != 0:
+        raise RuntimeError("single-thread CPU baseline failed: " + r.stderr[-500:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return out["n"], out["dt"]
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -450,6 +467,11 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": flops * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{n} whole applications of {args.config} by the oracle block tier "
                                           f"({dt:.1f} s)"}
+        n1, dt1 = cpu_baseline_single_thread(args.config, budget_s=min(args.cpu_budget, 10.0))
+        line["cpu_baseline_single_thread"] = {
+            "value": flops * n1 / dt1 / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n1} whole applications of {args.config} by the oracle block tier in a process with "
+                      f"one BLAS / OpenMP thread ({dt1:.1f} s)"}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -472,7 +494,12 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic work lists")
     ap.add_argument("--serve-load", type=float, default=0.7, help="offered load relative to alone service time")
     ap.add_argument("--serve-fp64", action="store_true", help="serve every request in FP64 (no split-precision solo path)")
+    ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)  # single-thread baseline process
     args = ap.parse_args()
+    if args.cpu_worker:
+        n, dt, _ = cpu_baseline(args.config, budget_s=args.cpu_budget)
+        print(json.dumps({"n": n, "dt": dt}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
