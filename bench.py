@@ -27,6 +27,9 @@ METRIC = "symmetric contraction block-GFLOP/s (FP64 vs split-prec); serve p50/p9
 UNIT = "block-GFLOP/s"
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64, nominal
+# DRAM bytes (read + write) per k_gemm_f64 launch of the D = 1024 U(1) heff chain, mean of the four
+# launches of one application, from one ncu capture (profiles/k_gemm_f64_u1_heff_d1024_launches.md)
+K2_TRAFFIC_BYTES = {"c1_u1_heff_d1024": 7.41e6}
 
 
 def _peaks():
@@ -431,7 +434,9 @@ def run_ours(args):
     if kname == "k_gemm_f64":
         achieved = flops * args.steps / (kms * 1e-3) / 1e12
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS / 1e3,
-                "unit": "TFLOP/s", "frac": achieved / (FP64_NOMINAL_GFLOPS / 1e3), "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / (FP64_NOMINAL_GFLOPS / 1e3),
+                "traffic": K2_TRAFFIC_BYTES.get(args.config) if not args.eager else None,
+                "traffic_note": "DRAM bytes per launch (ncu); operands read once, outputs written back after the launch",
                 "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s); no FP64 figure in MEASURED_PEAKS.json"}
     elif kname == "k_permute":
         achieved = permute_bytes * args.steps / (kms * 1e-3) / 1e9
