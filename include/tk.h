@@ -204,7 +204,10 @@ int tk_plan_transform(const tk_plan* plan, int which, int64_t k, int64_t* src_of
 
 /* ---- execution (asynchronous on `stream`, a cudaStream_t; NULL = legacy default stream) -------
  * All pointers are device pointers to buffers laid out as the plan's input/output structures.
- * C is fully overwritten.  A and B are never modified. */
+ * C is fully overwritten.  A and B are never modified.  In the split-precision modes the products
+ * left to the CUDA cores run on a second stream owned by the context, forked from `stream` after
+ * the input permutes and joined back before the output permute (a fork and a join in a captured
+ * CUDA graph); all work is still ordered after earlier and before later work on `stream`. */
 int tk_permute(tk_ctx* ctx, const tk_plan* plan, const void* a, void* c, void* stream);
 int tk_contract(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, void* c,
                 void* workspace, size_t workspace_bytes, void* stream);

@@ -105,6 +105,20 @@ int tk_ctx_create(int device, tk_ctx** out) {
       return TK_ERR_OOM;
     }
     cudaMemset(ctx->c.d_status, 0, sizeof(int) * 4);
+    cudaStream_t side = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) {
+      if (side) cudaStreamDestroy(side);
+      if (e0) cudaEventDestroy(e0);
+      cudaFree(ctx->c.d_status);
+      delete ctx;
+      return TK_ERR_CUDA;
+    }
+    ctx->c.side = side;
+    ctx->c.ev_fork = e0;
+    ctx->c.ev_join = e1;
   }
   *out = ctx;
   return TK_OK;
@@ -118,6 +132,9 @@ void tk_ctx_destroy(tk_ctx* ctx) {
     ctx->c.contract_cache.clear();
     tk::destroy_solver_handle(&ctx->c);
     if (ctx->c.d_status) cudaFree(ctx->c.d_status);
+    if (ctx->c.side) cudaStreamDestroy((cudaStream_t)ctx->c.side);
+    if (ctx->c.ev_fork) cudaEventDestroy((cudaEvent_t)ctx->c.ev_fork);
+    if (ctx->c.ev_join) cudaEventDestroy((cudaEvent_t)ctx->c.ev_join);
   }
   delete ctx;
 }

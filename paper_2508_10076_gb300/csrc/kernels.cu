@@ -1298,11 +1298,28 @@ int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b,
   // both operands in one launch, which also clears the split-K counters
   if ((rc = launch_permutes(ctx, in_jobs, 2, stream, &clear, cp.split_slots > 0 ? 1 : 0)) != TK_OK) return rc;
   if ((rc = launch_zero(ctx, cp, ct, stream)) != TK_OK) return rc;
-  if (!cp.gemms_fp64.empty() &&
-      (rc = launch_gemm_fp64(ctx, cp, at, bt, ct, w + cp.ws_partials, (int*)(w + cp.ws_counters), stream)) != TK_OK)
-    return rc;
-  if (!cp.gemms_oz.empty() && (rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream)) != TK_OK)
-    return rc;
+  if (!cp.gemms_fp64.empty() && !cp.gemms_oz.empty() && ctx->side) {
+    // split precision with CUDA-core products too: those run on the side stream beside the
+    // scale / slice / tensor-core launches.  They write other C blocks (or other columns of a
+    // block), their own split-K partials and counters, and read only the permuted operands.
+    cudaStream_t s = (cudaStream_t)stream, side = (cudaStream_t)ctx->side;
+    std::lock_guard<std::mutex> lk(ctx->side_mu);
+    if (cudaEventRecord((cudaEvent_t)ctx->ev_fork, s) != cudaSuccess ||
+        cudaStreamWaitEvent(side, (cudaEvent_t)ctx->ev_fork, 0) != cudaSuccess)
+      return TK_ERR_CUDA;
+    if ((rc = launch_gemm_fp64(ctx, cp, at, bt, ct, w + cp.ws_partials, (int*)(w + cp.ws_counters), side)) != TK_OK)
+      return rc;
+    if (cudaEventRecord((cudaEvent_t)ctx->ev_join, side) != cudaSuccess) return TK_ERR_CUDA;
+    rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream);
+    if (cudaStreamWaitEvent(s, (cudaEvent_t)ctx->ev_join, 0) != cudaSuccess) return TK_ERR_CUDA;  // join first
+    if (rc != TK_OK) return rc;
+  } else {
+    if (!cp.gemms_fp64.empty() &&
+        (rc = launch_gemm_fp64(ctx, cp, at, bt, ct, w + cp.ws_partials, (int*)(w + cp.ws_counters), stream)) != TK_OK)
+      return rc;
+    if (!cp.gemms_oz.empty() && (rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream)) != TK_OK)
+      return rc;
+  }
   if (cp.pc && (rc = launch_permute(ctx, *cp.pc, ct, c, stream)) != TK_OK) return rc;
   return TK_OK;
 }

@@ -249,6 +249,13 @@ struct Ctx {
   };
   std::vector<Rec> prof;
   void* solver = nullptr;  // cuSOLVER dense handle, created on first use (block SVD)
+  // a second stream and two events: in the split-precision modes the CUDA-core products of a
+  // contraction run beside its tensor-core chain (fork after the input permutes, join before the
+  // output permute); recorded into CUDA graphs as a fork and a join
+  void* side = nullptr;
+  void* ev_fork = nullptr;
+  void* ev_join = nullptr;
+  std::mutex side_mu;  // one fork / join at a time: the two events are shared by every caller
 };
 
 // ---- block SVD (Algorithm 9 after the two-site step of Algorithm 12)
