@@ -106,7 +106,7 @@ static_assert(sizeof(PermTask) % sizeof(int64_t) == 0, "PermTask must be 8-byte 
 // e.g. both operands of a contraction); each segment owns a contiguous range of blocks.
 struct PermSeg {
   int32_t kind;    // 0: contiguous runs, 1: tiles, 2: clear nwork ints at out (split-K counters)
-  int32_t pad_;
+  int32_t group;   // runs: lanes per run (32, or 16 when the runs are short)
   int64_t block0, nblocks, nwork;  // blocks [block0, block0 + nblocks); runs or tiles to do
   const PermRun* runs;
   const PermTask* tasks;  // run tasks (kind 0) or tile tasks (kind 1)
@@ -262,7 +262,10 @@ __device__ __forceinline__ void permute_tiles(const PermSeg& g, int64_t bid, T (
 // along the run, U elements per lane in flight.  Copy runs (one source, weight 1) carry their
 // source offset, so the next run's record is the only load before the data; it is fetched while
 // the current run is copied.  SU(2) runs sum their weighted sources in FP64.
-template <typename T>
+// Contiguous runs, G lanes per run (a warp, or half a warp when the runs are short so that two
+// runs' loads are in flight per warp), U loads in flight per lane; the next run's descriptor is
+// fetched while the current run is copied.
+template <typename T, int G>
 __device__ __forceinline__ void permute_runs(const PermSeg& g, int64_t bid) {
   constexpr int U = 4;
   const PermRun* __restrict__ runs = g.runs;
@@ -270,35 +273,36 @@ __device__ __forceinline__ void permute_runs(const PermSeg& g, int64_t bid) {
   const PermSrc* __restrict__ srcs = g.srcs;
   const T* __restrict__ in = (const T*)g.in;
   T* __restrict__ out = (T*)g.out;
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = (g.nblocks * blockDim.x) >> 5;
-  int64_t r = (bid * blockDim.x + threadIdx.x) >> 5;
+  constexpr int LG = G == 16 ? 4 : 5;
+  const int sub = threadIdx.x & (G - 1);  // lane within the run's group
+  const int64_t ngroups = (g.nblocks * blockDim.x) >> LG;
+  int64_t r = (bid * blockDim.x + threadIdx.x) >> LG;
   PermRun next;
   if (r < g.nwork) next = runs[r];
-  for (; r < g.nwork; r += nwarps) {
+  for (; r < g.nwork; r += ngroups) {
     const PermRun run = next;
-    if (r + nwarps < g.nwork) next = runs[r + nwarps];
+    if (r + ngroups < g.nwork) next = runs[r + ngroups];
     T* dst = out + run.dst;
     if (run.task < 0) {
       const T* src = in + run.ir;
       if (run.task == -2) {  // adjoint: conjugating copy
-        for (int e = lane; e < run.len; e += 32) dst[e] = Elem<T>::conj(__ldg(src + e));
+        for (int e = sub; e < run.len; e += G) dst[e] = Elem<T>::conj(__ldg(src + e));
         continue;
       }
-      for (int e = lane; e < run.len; e += 32 * U) {
+      for (int e = sub; e < run.len; e += G * U) {
         T v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (e + 32 * u < run.len) v[u] = __ldg(src + e + 32 * u);
+          if (e + G * u < run.len) v[u] = __ldg(src + e + G * u);
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (e + 32 * u < run.len) dst[e + 32 * u] = v[u];
+          if (e + G * u < run.len) dst[e + G * u] = v[u];
       }
       continue;
     }
     const int nsrc = __ldg(&tasks[run.task].nsrc);
     const int sb = __ldg(&tasks[run.task].src_begin);
-    for (int e = lane; e < run.len; e += 32)
+    for (int e = sub; e < run.len; e += G)
       dst[e] = gather<T>(srcs, nsrc, sb, in, run.ir + e, run.ic);
   }
 }
@@ -310,7 +314,13 @@ __global__ void __launch_bounds__(256, 4) k_permute(const __grid_constant__ Perm
   const PermSeg& g = L.seg[find_seg(L.seg, L.nseg, (int64_t)blockIdx.x)];
   const int64_t bid = (int64_t)blockIdx.x - g.block0;
   if (g.kind == 0) {
-    permute_runs<T>(g, bid);
+    if constexpr (sizeof(T) == 8) {  // complex runs move 16 B per element: always a warp per run
+      if (g.group == 16) {
+        permute_runs<T, 16>(g, bid);
+        return;
+      }
+    }
+    permute_runs<T, 32>(g, bid);
   } else if (g.kind == 1) {
     permute_tiles<T>(g, bid, tile, task_words);
   } else {
@@ -916,6 +926,7 @@ void perm_segments(const PermJob* jobs, int njobs, std::vector<PermSeg>& segs, s
       PermSeg g;
       std::memset(&g, 0, sizeof(g));
       g.kind = 0;
+      g.group = pp.dtype == TK_C128 ? 32 : pp.run_group;
       g.nwork = (int64_t)pp.runs.size();
       g.runs = pp.d_runs;
       g.tasks = pp.d_rtasks;
@@ -923,7 +934,8 @@ void perm_segments(const PermJob* jobs, int njobs, std::vector<PermSeg>& segs, s
       g.in = jobs[j].in;
       g.out = jobs[j].out;
       segs.push_back(g);
-      natural.push_back((g.nwork + 7) / 8);
+      const int64_t per_block = 256 / g.group;  // runs in flight per block
+      natural.push_back((g.nwork + per_block - 1) / per_block);
     }
     if (!pp.tasks.empty() && pp.total_tiles > 0) {
       PermSeg g;

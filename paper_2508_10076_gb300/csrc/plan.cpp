@@ -349,8 +349,13 @@ static void emit_task(PermutePlan& pp, PermTask t, std::vector<int64_t>& ext, st
   pp.tasks.push_back(t);
 }
 
-// Tile prefix of the tile-kernel tasks.
+// Tile prefix of the tile-kernel tasks; lanes per run of the run kernel.
 static void finish_tiles(PermutePlan& pp) {
+  if (!pp.runs.empty()) {
+    int64_t elems = 0;
+    for (const PermRun& r : pp.runs) elems += r.len;
+    pp.run_group = elems <= 64 * (int64_t)pp.runs.size() ? 16 : 32;  // short runs: two per warp
+  }
   int64_t acc = 0;
   for (auto& t : pp.tasks) {
     t.tile_begin = acc;

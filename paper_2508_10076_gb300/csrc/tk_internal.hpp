@@ -135,6 +135,7 @@ struct PermutePlan {
   std::vector<PermRun> runs;
   std::vector<PermSrc> srcs;
   int64_t total_tiles = 0;
+  int32_t run_group = 32;     // lanes per run in the run kernel: 16 when the runs average <= 64 elements
   double bytes = 0;           // algorithmic bytes for one launch (complex counts 16 B/element)
   int dtype = TK_F64;
   // device copies
