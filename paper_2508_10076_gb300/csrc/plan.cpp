@@ -349,8 +349,33 @@ static void emit_task(PermutePlan& pp, PermTask t, std::vector<int64_t>& ext, st
   pp.tasks.push_back(t);
 }
 
+// A permute with few, long runs leaves the run kernel short of warps (one group of lanes per
+// run, each with about 1 KB of loads in flight): cut the runs into pieces of at least 128
+// elements until there are about kRunTarget of them (one and a half per warp slot of a 152-SM
+// part with four resident 8-warp blocks per SM).  A piece of a run is again a run: both sides
+// stay contiguous, and the source index advances with the destination (plain runs carry a
+// resolved source offset, gathering runs an in-task index).
+constexpr int64_t kRunTarget = 152 * 4 * 8 * 3 / 2;
+constexpr int64_t kRunPieceMin = 128;
+static void balance_runs(PermutePlan& pp) {
+  const int64_t n = (int64_t)pp.runs.size();
+  if (n == 0 || n >= kRunTarget) return;
+  int64_t elems = 0;
+  for (const PermRun& r : pp.runs) elems += r.len;
+  int64_t piece = (elems + kRunTarget - 1) / kRunTarget;
+  piece = std::max<int64_t>(kRunPieceMin, (piece + 31) / 32 * 32);
+  if (piece >= kRunChunk) return;
+  std::vector<PermRun> out;
+  out.reserve((size_t)(elems / piece + n));
+  for (const PermRun& r : pp.runs)
+    for (int32_t e0 = 0; e0 < r.len; e0 += (int32_t)piece)
+      out.push_back(PermRun{r.dst + e0, r.ir + e0, r.ic, (int32_t)std::min<int64_t>(piece, r.len - e0), r.task});
+  pp.runs.swap(out);
+}
+
 // Tile prefix of the tile-kernel tasks; lanes per run of the run kernel.
 static void finish_tiles(PermutePlan& pp) {
+  balance_runs(pp);
   if (!pp.runs.empty()) {
     int64_t elems = 0;
     for (const PermRun& r : pp.runs) elems += r.len;
