@@ -322,18 +322,33 @@ def run_ours(args):
     host_out = torch.empty(out_dev.numel(), dtype=out_dev.dtype).pin_memory()
     h2d = sum(x.numel() * x.element_size() for x in host_in)
     d2h = host_out.numel() * host_out.element_size()
+    e2e_step = None
+    if hasattr(work, "run_host"):
+        # the chain's host-to-host call: W and R copied beside the first contraction
+        host_map = dict(zip(("x", "L", "W", "R"), host_in))
+        e2e_step = lambda: work.run_host(host_map, host_out)  # noqa: E731
+        if graph_out is not None:
+            from paper_2508_10076_gb300.chain import capture_graph
+            e2e_graph, _, _ = capture_graph(ctx, e2e_step)
+            e2e_step = e2e_graph.replay
     e_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
     for i in range(args.steps):
         flush.zero_()
         e_start[i].record(stream)
-        for hx, dx in zip(host_in, ins):
-            api.copy_h2d(ctx, dx, hx.data_ptr(), hx.numel() * hx.element_size(), stream)
-        out_dev = run()
-        api.copy_d2h(ctx, host_out.data_ptr(), out_dev, d2h, stream)
+        if e2e_step is not None:
+            e2e_step()
+        else:
+            for hx, dx in zip(host_in, ins):
+                api.copy_h2d(ctx, dx, hx.data_ptr(), hx.numel() * hx.element_size(), stream)
+            out_dev = run()
+            api.copy_d2h(ctx, host_out.data_ptr(), out_dev, d2h, stream)
         e_end[i].record(stream)
     barrier()
+    torch.cuda.synchronize()
+    if not torch.equal(host_out, out_dev.cpu() if e2e_step is None else run().cpu()):
+        raise RuntimeError("the end-to-end result differs from the device path's")
     e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_start, e_end))
     e2e_ms = max_over_ranks(dist, e2e_ms)
     e2e_value = job_throughput(flops, args.steps, world, e2e_ms)

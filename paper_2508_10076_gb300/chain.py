@@ -130,6 +130,31 @@ class HeffChain:
             t = st.run(t, self.dev[other], stream)
         return t
 
+    def run_host(self, host, host_out):
+        """One application from pinned host buffers to a pinned host result, every copy through
+        the C ABI: x and L are copied and L x runs on the current stream while W and R are copied
+        on a side stream (they are needed only by the later steps); x' is read back at the end.
+        host: dict of pinned CPU tensors "x", "L", "W", "R" matching the device inputs."""
+        main = torch.cuda.current_stream()
+        if not hasattr(self, "_copy_stream"):
+            self._copy_stream = torch.cuda.Stream(device=self.dev["x"].device)
+        side = self._copy_stream
+
+        def h2d(k, st):
+            api.copy_h2d(self.ctx, self.dev[k], host[k].data_ptr(), host[k].numel() * host[k].element_size(), st)
+
+        side.wait_stream(main)  # fork: the device copies of W and R are free to overwrite
+        h2d("W", side)
+        h2d("R", side)
+        h2d("x", main)
+        h2d("L", main)
+        t = self.steps[0].run(self.dev["L"], self.dev["x"], main)
+        main.wait_stream(side)  # join before W is read
+        for st, other in zip(self.steps[1:], self.others[1:]):
+            t = st.run(t, self.dev[other], main)
+        api.copy_d2h(self.ctx, host_out.data_ptr(), t, host_out.numel() * host_out.element_size(), main)
+        return host_out
+
     def autotune(self):
         """Tune every step on the chain's own intermediates (before any graph capture)."""
         x = self.dev["x"]

@@ -460,3 +460,26 @@ def test_z2_family_contraction(gctx, sym, gemm, tol, dtype):
     api.contract(gctx, plan, _dev(xa), _dev(xx), c, ws_)
     gctx.sync()
     assert rel_frobenius_per_block(cs, c.cpu().numpy(), ref) <= tol
+
+
+def test_heff_chain_host_to_host(gctx):
+    """HeffChain.run_host (pinned host inputs, W and R copied beside the first contraction, x'
+    read back) gives the device path's bits, eagerly and replayed from a CUDA graph."""
+    from paper_2508_10076_gb300.chain import HeffChain, capture_graph
+    ch = HeffChain(gctx, "U1", 128, seed=6)
+    ref = ch.run().clone()
+    gctx.sync()
+    host = {k: ch.dev[k].cpu().pin_memory() for k in ("x", "L", "W", "R")}
+    for k in host:  # the call must copy every input itself
+        ch.dev[k].zero_()
+    out = torch.empty(ref.numel(), dtype=ref.dtype).pin_memory()
+    ch.run_host(host, out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref.cpu())
+    graph, _, _ = capture_graph(gctx, lambda: ch.run_host(host, out))
+    out.zero_()
+    for k in host:
+        ch.dev[k].zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref.cpu())
