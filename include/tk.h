@@ -90,6 +90,13 @@ const char* tk_status_string(int status);   /* static string, never NULL        
  * device >= 0: the CUDA device all plans and launches of this context use (it is made current
  * inside every call).  device < 0: host-only context -- spaces, tensor structures and plans can
  * be built and inspected, execution calls return TK_ERR_NO_DEVICE. */
+/* Concurrency: plans are built and cached under a mutex of the context, so several host threads
+ * may plan at once; executions on different streams are independent (each call uses only the
+ * buffers and workspace it is given), except that the short fork / join section of a
+ * split-precision contraction (its second stream and two events belong to the context) is taken
+ * by one call at a time.  Calls that share a workspace must not overlap: a contraction's
+ * split-K partials and arrival counters live in its workspace (a plan may serve overlapping
+ * calls that each have their own). */
 int tk_ctx_create(int device, tk_ctx** out);
 void tk_ctx_destroy(tk_ctx* ctx);
 const char* tk_ctx_last_error(const tk_ctx* ctx);
