@@ -106,7 +106,7 @@ static_assert(sizeof(PermTask) % sizeof(int64_t) == 0, "PermTask must be 8-byte 
 // e.g. both operands of a contraction); each segment owns a contiguous range of blocks.
 struct PermSeg {
   int32_t kind;    // 0: contiguous runs, 1: tiles, 2: clear nwork ints at out (split-K counters)
-  int32_t group;   // runs: lanes per run (32, or 16 when the runs are short)
+  int32_t group;   // runs: lanes per run (32, or 16 when the runs are short); clears: the fill value
   int64_t block0, nblocks, nwork;  // blocks [block0, block0 + nblocks); runs or tiles to do
   const PermRun* runs;
   const PermTask* tasks;  // run tasks (kind 0) or tile tasks (kind 1)
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(256, 4) k_permute(const __grid_constant__ Perm
     permute_tiles<T>(g, bid, tile, task_words);
   } else {
     int* p = (int*)g.out;
-    for (int64_t i = bid * blockDim.x + threadIdx.x; i < g.nwork; i += g.nblocks * blockDim.x) p[i] = 0;
+    for (int64_t i = bid * blockDim.x + threadIdx.x; i < g.nwork; i += g.nblocks * blockDim.x) p[i] = g.group;
   }
 }
 
@@ -981,7 +981,8 @@ int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream, cons
   perm_segments(jobs, njobs, segs, natural, dtype);
   if (segs.empty()) {  // nothing to permute: clear with plain memsets
     for (int i = 0; i < nclears; ++i)
-      if (cudaMemsetAsync(clears[i].p, 0, (size_t)clears[i].n * sizeof(int), (cudaStream_t)stream) != cudaSuccess)
+      if (cudaMemsetAsync(clears[i].p, clears[i].fill & 0xFF, (size_t)clears[i].n * sizeof(int), (cudaStream_t)stream) !=
+          cudaSuccess)
         return TK_ERR_CUDA;
     return TK_OK;
   }
@@ -989,6 +990,7 @@ int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream, cons
     PermSeg g;
     std::memset(&g, 0, sizeof(g));
     g.kind = 2;
+    g.group = clears[i].fill;
     g.nwork = clears[i].n;
     g.out = clears[i].p;
     segs.push_back(g);
@@ -1306,9 +1308,14 @@ int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b,
   void* ct = cp.pc ? (void*)(w + cp.ws_ct) : c;
   int rc;
   const PermJob in_jobs[2] = {{cp.pa.get(), a, (void*)at}, {cp.pb.get(), b, (void*)bt}};
-  const IntClear clear{(int*)(w + cp.ws_counters), (int64_t)cp.split_slots};
-  // both operands in one launch, which also clears the split-K counters
-  if ((rc = launch_permutes(ctx, in_jobs, 2, stream, &clear, cp.split_slots > 0 ? 1 : 0)) != TK_OK) return rc;
+  IntClear clears[2];
+  int nclears = 0;
+  if (cp.split_slots > 0) clears[nclears++] = IntClear{(int*)(w + cp.ws_counters), (int64_t)cp.split_slots};
+  const bool scales = !cp.gemms_oz.empty() && ozaki_scale_clear(cp, w + cp.ws_slices, &clears[nclears]);
+  if (scales) ++nclears;
+  // both operands in one launch, which also clears the split-K counters and the split-precision
+  // scale arrays
+  if ((rc = launch_permutes(ctx, in_jobs, 2, stream, clears, nclears)) != TK_OK) return rc;
   if ((rc = launch_zero(ctx, cp, ct, stream)) != TK_OK) return rc;
   if (!cp.gemms_fp64.empty() && !cp.gemms_oz.empty() && ctx->side) {
     // split precision with CUDA-core products too: those run on the side stream beside the
@@ -1322,14 +1329,14 @@ int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b,
     if ((rc = launch_gemm_fp64(ctx, cp, at, bt, ct, w + cp.ws_partials, (int*)(w + cp.ws_counters), side)) != TK_OK)
       return rc;
     if (cudaEventRecord((cudaEvent_t)ctx->ev_join, side) != cudaSuccess) return TK_ERR_CUDA;
-    rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream);
+    rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream, scales);
     if (cudaStreamWaitEvent(s, (cudaEvent_t)ctx->ev_join, 0) != cudaSuccess) return TK_ERR_CUDA;  // join first
     if (rc != TK_OK) return rc;
   } else {
     if (!cp.gemms_fp64.empty() &&
         (rc = launch_gemm_fp64(ctx, cp, at, bt, ct, w + cp.ws_partials, (int*)(w + cp.ws_counters), stream)) != TK_OK)
       return rc;
-    if (!cp.gemms_oz.empty() && (rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream)) != TK_OK)
+    if (!cp.gemms_oz.empty() && (rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream, scales)) != TK_OK)
       return rc;
   }
   if (cp.pc && (rc = launch_permute(ctx, *cp.pc, ct, c, stream)) != TK_OK) return rc;

@@ -1118,7 +1118,7 @@ int ensure_smem_attrs(Ctx* ctx) {
 
 // Describe one request for the scale / slice launches and the GEMM launch; clears its scale arrays.
 int describe_ozaki_request(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
-                           void* stream, OzPrepSeg& P, OzReq& R) {
+                           void* stream, OzPrepSeg& P, OzReq& R, bool scales_cleared = false) {
   const OzLayout* L = static_cast<const OzLayout*>(cp.oz.get());
   if (((uintptr_t)ws & 15) != 0) {
     ctx->last_error = "split-precision workspace must be 16-byte aligned";
@@ -1135,7 +1135,8 @@ int describe_ozaki_request(Ctx* ctx, const ContractPlan& cp, const void* a, cons
     ctx->last_error = "cuTensorMapEncodeTiled failed";
     return TK_ERR_CUDA;
   }
-  if (cudaMemsetAsync(sa, 0x80, L->off_sb - L->off_sa + (size_t)L->ncols_b * 4, (cudaStream_t)stream) != cudaSuccess)
+  if (!scales_cleared &&
+      cudaMemsetAsync(sa, 0x80, L->off_sb - L->off_sa + (size_t)L->ncols_b * 4, (cudaStream_t)stream) != cudaSuccess)
     return TK_ERR_CUDA;
   int* counters = (int*)(w + L->off_cnt);  // cleared by the scale kernel
   std::memset(&P, 0, sizeof(P));
@@ -1220,8 +1221,17 @@ int launch_oz_gemm(Ctx* ctx, const OzLayout* L, const OzBatchT<NREQ>& B, int gri
 }
 }  // namespace
 
+bool ozaki_scale_clear(const ContractPlan& cp, void* ws, IntClear* out) {
+  const OzLayout* L = static_cast<const OzLayout*>(cp.oz.get());
+  if (!L || L->nwork == 0) return false;
+  out->p = (int*)((char*)ws + L->off_sa);
+  out->n = (int64_t)((L->off_sb - L->off_sa) / 4 + L->ncols_b);
+  out->fill = kNoScale;
+  return true;
+}
+
 int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
-                      void* stream) {
+                      void* stream, bool scales_cleared) {
   const OzLayout* L = static_cast<const OzLayout*>(cp.oz.get());
   if (!L) {
     ctx->last_error = "split-precision tables missing";
@@ -1234,7 +1244,8 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
   OzPrepT<1> P;
   std::memset(&B, 0, sizeof(B));
   std::memset(&P, 0, sizeof(P));
-  if ((rc = describe_ozaki_request(ctx, cp, a, b, c, ws, stream, P.seg[0], B.req[0])) != TK_OK) return rc;
+  if ((rc = describe_ozaki_request(ctx, cp, a, b, c, ws, stream, P.seg[0], B.req[0], scales_cleared)) != TK_OK)
+    return rc;
   B.nreq = 1;
   P.nseg = 1;
   const OzLayout* lay[1] = {L};

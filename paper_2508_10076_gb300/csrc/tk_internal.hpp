@@ -304,6 +304,7 @@ struct PermJob {
 struct IntClear {
   int* p;
   int64_t n;
+  int32_t fill = 0;  // value written to every int (a repeated byte: the no-permute path memsets)
 };
 // Several permutes in one launch (identity plans are skipped; more than 160 segments take several
 // launches), optionally also clearing int arrays (split-K counters) in the same launch.
@@ -313,7 +314,10 @@ int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void
 int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream);
 int upload_gemm_tables(Ctx* ctx, ContractPlan& cp);
 int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
-                      void* slices_ws, void* stream);
+                      void* slices_ws, void* stream, bool scales_cleared = false);
+// The split-precision scale arrays of a plan in its workspace region, to be filled with the
+// "no entry yet" pattern before the scale launch (false when the plan has no tensor-core part).
+bool ozaki_scale_clear(const ContractPlan& cp, void* slices_ws, IntClear* out);
 // The split-precision GEMMs of several requests (their workspaces' slice regions in ws): scaling
 // and slicing per request, then one packed tensor-core launch per group of up to 32 requests that
 // share mode, tile width and slice count.
