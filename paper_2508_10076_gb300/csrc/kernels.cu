@@ -105,8 +105,10 @@ static_assert(sizeof(PermTask) % sizeof(int64_t) == 0, "PermTask must be 8-byte 
 // One launch serves up to four segments (the run list and the tile list of up to two permutes,
 // e.g. both operands of a contraction); each segment owns a contiguous range of blocks.
 struct PermSeg {
-  int32_t kind;    // 0: contiguous runs, 1: tiles, 2: clear nwork ints at out (split-K counters)
-  int32_t group;   // runs: lanes per run (32, or 16 when the runs are short); clears: the fill value
+  int32_t kind;    // 0: contiguous runs, 1: tiles, 2: fill nwork ints at out (split-K counters,
+                   // scale arrays), 3: zero fill of the ZeroItems at in (nwork = items x chunks)
+  int32_t group;   // runs: lanes per run (32, or 16 when the runs are short); fills: the value;
+                   // zero fill: the number of items
   int64_t block0, nblocks, nwork;  // blocks [block0, block0 + nblocks); runs or tiles to do
   const PermRun* runs;
   const PermTask* tasks;  // run tasks (kind 0) or tile tasks (kind 1)
@@ -115,7 +117,8 @@ struct PermSeg {
   const void* in;
   void* out;
 };
-constexpr int kMaxPermSegs = 6;       // one contraction: runs + tiles of two operands, counter clears
+constexpr int kMaxPermSegs = 7;       // one contraction: runs + tiles of two operands, fills, zero fill
+constexpr int kZeroChunk = 2048;      // elements of a zero-fill unit
 constexpr int kBatchSegs = 160;       // a packed launch over many requests (about 13 KB of parameters)
 template <int NSEG>
 struct PermLaunchT {
@@ -323,9 +326,17 @@ __global__ void __launch_bounds__(256, 4) k_permute(const __grid_constant__ Perm
     permute_runs<T, 32>(g, bid);
   } else if (g.kind == 1) {
     permute_tiles<T>(g, bid, tile, task_words);
-  } else {
+  } else if (g.kind == 2) {
     int* p = (int*)g.out;
     for (int64_t i = bid * blockDim.x + threadIdx.x; i < g.nwork; i += g.nblocks * blockDim.x) p[i] = g.group;
+  } else {  // unit u: chunk u / nitems of item u % nitems
+    const ZeroItem* __restrict__ items = (const ZeroItem*)g.in;
+    T* __restrict__ c = (T*)g.out;
+    for (int64_t u = bid; u < g.nwork; u += g.nblocks) {
+      const ZeroItem z = items[u % g.group];
+      const int64_t e0 = (u / g.group) * kZeroChunk, e1 = min(z.n, e0 + kZeroChunk);
+      for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) c[z.off + e] = Elem<T>::zero();
+    }
   }
 }
 
@@ -892,16 +903,6 @@ __global__ void k_zero_batch(const __grid_constant__ ZeroBatch L, int64_t total_
   }
 }
 
-template <typename T>
-__global__ void k_zero(const ZeroItem* __restrict__ items, int nitems, T* __restrict__ c) {
-  for (int i = blockIdx.y; i < nitems; i += gridDim.y) {
-    const ZeroItem z = items[i];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < z.n;
-         e += (int64_t)gridDim.x * blockDim.x)
-      c[z.off + e] = Elem<T>::zero();
-  }
-}
-
 int check_launch(Ctx* ctx, const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -974,11 +975,28 @@ int64_t fill_perm_launch(PermLaunchT<NSEG>& L, const PermSeg* segs, const int64_
 }
 }  // namespace
 
-int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream, const IntClear* clears, int nclears) {
+int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream, const IntClear* clears, int nclears,
+                    const ZeroJob* zero) {
   std::vector<PermSeg> segs;
   std::vector<int64_t> natural;
   int dtype = TK_F64;
   perm_segments(jobs, njobs, segs, natural, dtype);
+  if (zero) dtype = zero->dtype;  // the same as the permutes' (one contraction)
+  if (segs.empty() && zero) {  // nothing to permute: the zero fill takes its own launch
+    const int64_t units = zero->nitems * ((zero->maxn + kZeroChunk - 1) / kZeroChunk);
+    if (units > 0) {
+      PermSeg g;
+      std::memset(&g, 0, sizeof(g));
+      g.kind = 3;
+      g.group = (int32_t)zero->nitems;
+      g.nwork = units;
+      g.in = zero->items;
+      g.out = zero->c;
+      segs.push_back(g);
+      natural.push_back(units);
+      zero = nullptr;
+    }
+  }
   if (segs.empty()) {  // nothing to permute: clear with plain memsets
     for (int i = 0; i < nclears; ++i)
       if (cudaMemsetAsync(clears[i].p, clears[i].fill & 0xFF, (size_t)clears[i].n * sizeof(int), (cudaStream_t)stream) !=
@@ -995,6 +1013,20 @@ int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream, cons
     g.out = clears[i].p;
     segs.push_back(g);
     natural.push_back(1);
+  }
+  if (zero) {  // zero fill of the GEMM output's empty blocks rides along too
+    const int64_t units = zero->nitems * ((zero->maxn + kZeroChunk - 1) / kZeroChunk);
+    if (units > 0) {
+      PermSeg g;
+      std::memset(&g, 0, sizeof(g));
+      g.kind = 3;
+      g.group = (int32_t)zero->nitems;
+      g.nwork = units;
+      g.in = zero->items;
+      g.out = zero->c;
+      segs.push_back(g);
+      natural.push_back(units);
+    }
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t cap = (int64_t)std::max(ctx->num_sms, 1) * 8;
@@ -1209,20 +1241,6 @@ int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void
   return check_launch(ctx, "k_gemm_f64");
 }
 
-int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream) {
-  if (cp.zeros.empty()) return TK_OK;
-  int64_t maxn = 0;
-  for (auto& z : cp.zeros) maxn = std::max(maxn, z.n);
-  dim3 grid((unsigned)std::min<int64_t>((maxn + 255) / 256, 1024), (unsigned)std::min<size_t>(cp.zeros.size(), 65535));
-  cudaStream_t s = (cudaStream_t)stream;
-  ProfScope prof(ctx, "k_zero", stream);
-  if (cp.dtype == TK_C128)
-    k_zero<double2><<<grid, 256, 0, s>>>((const ZeroItem*)cp.d_zero, (int)cp.zeros.size(), (double2*)c);
-  else
-    k_zero<double><<<grid, 256, 0, s>>>((const ZeroItem*)cp.d_zero, (int)cp.zeros.size(), (double*)c);
-  return check_launch(ctx, "k_zero");
-}
-
 namespace {
 // Complex operands of a split-precision plan: real and imaginary parts into separate arrays, and
 // the four real products back into one complex result.
@@ -1314,9 +1332,11 @@ int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b,
   const bool scales = !cp.gemms_oz.empty() && ozaki_scale_clear(cp, w + cp.ws_slices, &clears[nclears]);
   if (scales) ++nclears;
   // both operands in one launch, which also clears the split-K counters and the split-precision
-  // scale arrays
-  if ((rc = launch_permutes(ctx, in_jobs, 2, stream, clears, nclears)) != TK_OK) return rc;
-  if ((rc = launch_zero(ctx, cp, ct, stream)) != TK_OK) return rc;
+  // scale arrays and zero-fills the output blocks with an empty inner dimension
+  ZeroJob zj{(const ZeroItem*)cp.d_zero, (int64_t)cp.zeros.size(), 0, ct, cp.dtype};
+  for (const ZeroItem& z : cp.zeros) zj.maxn = std::max(zj.maxn, z.n);
+  if ((rc = launch_permutes(ctx, in_jobs, 2, stream, clears, nclears, cp.zeros.empty() ? nullptr : &zj)) != TK_OK)
+    return rc;
   if (!cp.gemms_fp64.empty() && !cp.gemms_oz.empty() && ctx->side) {
     // split precision with CUDA-core products too: those run on the side stream beside the
     // scale / slice / tensor-core launches.  They write other C blocks (or other columns of a

@@ -308,10 +308,18 @@ struct IntClear {
 };
 // Several permutes in one launch (identity plans are skipped; more than 160 segments take several
 // launches), optionally also clearing int arrays (split-K counters) in the same launch.
-int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream, const IntClear* clears, int nclears);
+// zero: optionally, a plan's zero-fill list (blocks with an empty inner dimension) of output c,
+// done in the same launch.
+struct ZeroJob {
+  const ZeroItem* items;  // device
+  int64_t nitems, maxn;
+  void* c;
+  int dtype;  // element type of c (TK_F64 / TK_C128): the launch's type when no permute is left
+};
+int launch_permutes(Ctx* ctx, const PermJob* jobs, int njobs, void* stream, const IntClear* clears, int nclears,
+                    const ZeroJob* zero = nullptr);
 int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
                      void* partials, int* counters, void* stream);
-int launch_zero(Ctx* ctx, const ContractPlan& cp, void* c, void* stream);
 int upload_gemm_tables(Ctx* ctx, ContractPlan& cp);
 int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
                       void* slices_ws, void* stream, bool scales_cleared = false);
