@@ -1,9 +1,11 @@
 // Device kernels of the contraction path (sm_103a):
 //   K1 k_permute   -- fusion-tree permute: every destination reduced array is a
 //                     coefficient-weighted sum of strided transposes of source reduced arrays
-//                     (Algorithm 10; Algorithm 6 for abelian symmetries, one source, weight 1).
+//                     (Algorithm 10; Algorithm 6 for abelian symmetries, one source, weight 1);
+//                     the input permute launch also zero-fills the output blocks of coupled
+//                     sectors whose inner dimension is empty and fills counter / scale arrays.
 //   K2 k_gemm_f64  -- grouped FP64 GEMM over the coupled sectors (Algorithm 8, step 2).
-//   k_zero         -- zero blocks of coupled sectors whose inner dimension is empty.
+//   k_zero_batch   -- the zero fill of many requests of one packed batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
