@@ -248,9 +248,13 @@ def svd_block(struct: TensorStructure, data):
 
 
 def truncation_keep(struct: TensorStructure, svals, dmax):
-    """Keep counts per block for a truncation to at most dmax states: the largest singular values
-    over all sectors, each value of sector c standing for d_c states (an SU(2) multiplet); ties
-    broken by ascending sector.  Returns (keep per block, relative discarded weight
+    """Keep counts per block for a truncation to at most dmax states (the truncated SVD after the
+    two-site step of Algorithm 12; the paper fixes no rule, this is the reading used here).  Every
+    value of sector c stands for d_c states (an SU(2) multiplet), so the dense spectrum of t is
+    the block values each repeated d_c times.  Values are taken in descending order over all
+    sectors (ties: ascending sector), whole multiplets only, and the walk stops at the first
+    multiplet that no longer fits: the kept states are a prefix of the dense spectrum cut at a
+    multiplet boundary.  Returns (keep per block, relative discarded weight
     sqrt(sum_discarded d_c s^2 / sum_all d_c s^2))."""
     entries = []
     for b, (c, s) in enumerate(svals):
@@ -259,13 +263,15 @@ def truncation_keep(struct: TensorStructure, svals, dmax):
     entries.sort()
     keep = [0] * len(svals)
     used, kept_w, total_w = 0, 0.0, 0.0
+    full = False
     for negv, c, b in entries:
         d = struct.sym.dim(c)
         total_w += d * negv * negv
-        if used + d <= dmax:
+        if not full and used + d <= dmax:
             keep[b] += 1
             used += d
             kept_w += d * negv * negv
+        else:
+            full = True
     err = np.sqrt(max(total_w - kept_w, 0.0) / total_w) if total_w > 0 else 0.0
     return keep, err
-

@@ -240,6 +240,82 @@ def test_block_svd_matches_dense_spectrum_and_reconstructs():
         assert np.all(s[:k][:, None] >= s[k:][None, :])
 
 
+def _dense_spectrum(st, d):
+    """Singular values of the dense embedded matrix (codomain x domain), descending."""
+    dense = embed(st, d)
+    rows = int(np.prod(dense.shape[:len(st.cod)]))
+    return np.sort(np.linalg.svd(dense.reshape(rows, -1), compute_uv=False))[::-1]
+
+
+def _check_truncation_against_dense(st, d, dmax, keep_fn=None):
+    """The truncation rule checked against the dense SVD of t, which knows nothing of sectors:
+    the kept states are the largest dense singular values (a prefix of the dense spectrum), the
+    cut falls on a multiplet boundary (the next dense value's multiplet would not fit), and the
+    error is the discarded share of the dense spectrum's weight."""
+    keep_fn = keep_fn or ops.truncation_keep
+    blocks = ops.svd_block(st, d)
+    keep, err = keep_fn(st, [(c, s) for c, _, s, _ in blocks], dmax)
+    dense = _dense_spectrum(st, d)
+    kept = np.sort(np.concatenate([np.repeat(s[:k], st.sym.dim(c)) for (c, _, s, _), k in zip(blocks, keep)]))[::-1]
+    n = len(kept)
+    assert n <= dmax
+    assert np.allclose(kept, dense[:n], rtol=1e-12, atol=1e-13 * dense[0])
+    if n < len(dense):
+        nxt = dense[n]
+        mult = int(np.sum(np.abs(dense - nxt) <= 1e-9 * dense[0]))
+        assert n + mult > dmax, "a whole multiplet below the cut would still have fitted"
+    want = np.sqrt(np.sum(dense[n:] ** 2) / np.sum(dense ** 2))
+    assert abs(err - want) <= 1e-12
+    return keep, err
+
+
+@pytest.mark.parametrize("dmax", list(range(1, 26)))
+def test_truncation_keep_is_a_prefix_of_the_dense_spectrum(dmax):
+    """SU(2): multiplets of dimension 1, 2 and 3 compete across sectors; every bond dimension from
+    1 to beyond the full rank is checked against the dense SVD."""
+    st, d = _su2_tensor(11, [({0: 2, 1: 2, 2: 1}, False), ({1: 1}, False)],
+                        [({0: 1, 1: 2, 2: 1}, False), ({1: 1}, True)])
+    _check_truncation_against_dense(st, d, dmax)
+
+
+def test_truncation_keep_u1_takes_the_top_values():
+    """U(1): every multiplet has one state, so keeping dmax states is the top dmax dense values."""
+    v = GradedSpace(U1, {-1: 2, 0: 3, 1: 2})
+    st = TensorStructure([v, v], [v])
+    d = np.random.default_rng(3).standard_normal(st.numel)
+    for dmax in (1, 3, 5, 8, 13):
+        keep, _ = _check_truncation_against_dense(st, d, dmax)
+        assert sum(keep) == min(dmax, len(_dense_spectrum(st, d)))
+
+
+def test_truncation_pin_rejects_planted_mistakes():
+    """The dense check fails a rule that picks per sector without comparing across sectors, and a
+    rule whose error leaves out the d_c weight."""
+    st, d = _su2_tensor(11, [({0: 2, 1: 2, 2: 1}, False), ({1: 1}, False)],
+                        [({0: 1, 1: 2, 2: 1}, False), ({1: 1}, True)])
+
+    def per_sector(struct, svals, dmax):  # the same share of each sector, no comparison across them
+        total = sum(len(s) * struct.sym.dim(c) for c, s in svals)
+        keep = [int(len(s) * min(1.0, dmax / total)) for c, s in svals]
+        _, err = ops.truncation_keep(struct, svals, dmax)
+        return keep, err
+
+    def unweighted(struct, svals, dmax):  # the right keep counts, error without d_c
+        keep, _ = ops.truncation_keep(struct, svals, dmax)
+        tot = sum(float(np.sum(s ** 2)) for _, s in svals)
+        kept = sum(float(np.sum(s[:k] ** 2)) for (_, s), k in zip(svals, keep))
+        return keep, np.sqrt(max(tot - kept, 0.0) / tot)
+
+    for bad in (per_sector, unweighted):
+        failed = 0
+        for dmax in range(2, 20):
+            try:
+                _check_truncation_against_dense(st, d, dmax, keep_fn=bad)
+            except AssertionError:
+                failed += 1
+        assert failed > 0, bad.__name__
+
+
 def test_product_symmetry_contraction_dense_vs_block_and_bruteforce():
     """U(1) x SU(2) (charge x spin, Sec. 5.2 product sectors): the block contraction (overlap-route
     recoupling of Kronecker-product splitting tensors) equals the dense contraction, and the dense
