@@ -72,14 +72,21 @@ def oracle_heff(sym, D, seed=0, tier="block", dtype="f64", steps=None, sites=2, 
 def rel_frobenius_per_block(struct, got, ref):
     """max over blocks of ||got - ref||_F / ||ref||_F.
 
-    A block whose exact value is zero (an empty inner dimension, or a reference norm at the
-    rounding level of the whole tensor) is measured against the norm of the whole tensor.
+    A block that the reference holds at exactly zero (every entry 0: a coupled sector with an
+    empty inner dimension, Algorithm 8, carried through the output permute) must be exactly zero
+    in `got` too; any other value there makes the result infinite.  A reference block that is not
+    exactly zero but sits at the rounding level of the whole tensor (the dense tier's projection
+    of such a block) is measured against the norm of the whole tensor.
     """
     got, ref = np.asarray(got), np.asarray(ref)
     total = max(float(np.linalg.norm(ref)), 1e-300)
     worst = 0.0
     for c, r, k, off in struct.blocks:
         g, f = got[off:off + r * k], ref[off:off + r * k]
+        if f.size and not np.any(f):
+            if np.any(g != 0):
+                return float("inf")
+            continue
         nf = float(np.linalg.norm(f))
         den = nf if nf > 1e-13 * total else total
         worst = max(worst, float(np.linalg.norm(g - f) / den))
