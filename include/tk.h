@@ -55,6 +55,7 @@ extern "C" {
 #define TK_ERR_TIMEOUT 8        /* a bounded device-side wait gave up                         */
 #define TK_ERR_WORKSPACE 9      /* workspace too small                                        */
 #define TK_ERR_NO_DEVICE 10     /* execution call on a host-only context                      */
+#define TK_ERR_BUDGET 11        /* the context's device-memory budget would be exceeded       */
 
 /* ---- enums ------------------------------------------------------------------------------ */
 #define TK_SYM_Z2 0
@@ -89,18 +90,37 @@ const char* tk_status_string(int status);   /* static string, never NULL        
 /* ---- context ------------------------------------------------------------------------------
  * device >= 0: the CUDA device all plans and launches of this context use (it is made current
  * inside every call).  device < 0: host-only context -- spaces, tensor structures and plans can
- * be built and inspected, execution calls return TK_ERR_NO_DEVICE. */
+ * be built and inspected, execution calls return TK_ERR_NO_DEVICE.
+ *
+ * stream (a cudaStream_t, may be NULL = legacy default stream): the context's stream.  Execution
+ * calls given a NULL stream run on it, and plan tables are uploaded on it (each upload waits for
+ * the stream).
+ *
+ * Allocator hooks: every device allocation the library makes itself -- plan tables, the context's
+ * status word, tk_ctx_alloc / tk_tmap_alloc buffers -- goes through alloc(bytes, user), which
+ * returns device memory of the context's device (at least 256-byte aligned) or NULL, and is given
+ * back through release(ptr, bytes, user).  With both hooks NULL the library uses cudaMalloc /
+ * cudaFree; giving only one of them is TK_ERR_ARG.  A hook is called with the context's device
+ * current, from the thread that made the library call.  The hooks and `user` must stay valid
+ * until every plan built by the context has been destroyed (plan tables are released when the
+ * last reference to a plan goes, which may be after tk_ctx_destroy).  Scratch memory of execution
+ * calls is never allocated by the library: the caller passes it (workspace arguments). */
+typedef void* (*tk_alloc_fn)(size_t bytes, void* user);
+typedef void (*tk_free_fn)(void* ptr, size_t bytes, void* user);
+
 /* Concurrency: plans are built and cached under a mutex of the context, so several host threads
  * may plan at once; executions on different streams are independent (each call uses only the
  * buffers and workspace it is given), except that the short fork / join section of a
  * split-precision contraction (its second stream and two events belong to the context) is taken
  * by one call at a time.  Calls that share a workspace must not overlap: a contraction's
  * split-K partials and arrival counters live in its workspace (a plan may serve overlapping
- * calls that each have their own). */
-int tk_ctx_create(int device, tk_ctx** out);
+ * calls that each have their own).  A plan must not be destroyed while launches that use it are
+ * in flight (with caller hooks nothing waits for them before release is called). */
+int tk_ctx_create(int device, void* stream, tk_alloc_fn alloc, tk_free_fn release, void* alloc_user,
+                  tk_ctx** out);
 void tk_ctx_destroy(tk_ctx* ctx);
 const char* tk_ctx_last_error(const tk_ctx* ctx);
-/* Waits for `stream` (a cudaStream_t, NULL = legacy default) and reports deferred device errors
+/* Waits for `stream` (a cudaStream_t, NULL = the context's stream) and reports deferred device errors
  * (TK_ERR_TIMEOUT if a bounded wait gave up, TK_ERR_CUDA for launch/runtime failures). */
 int tk_ctx_sync(tk_ctx* ctx, void* stream);
 /* Number of the library's own kernels launched through this context so far. */
@@ -112,6 +132,25 @@ int64_t tk_ctx_launch_count(const tk_ctx* ctx);
  * TK_ERR_TIMEOUT (kernel tag 9 in tk_ctx_last_error), clears the word, and the context stays
  * usable.  Returns TK_OK once launched; TK_ERR_NO_DEVICE for a host-only context. */
 int tk_ctx_selftest_timeout(tk_ctx* ctx, void* stream);
+/* Device-memory budget (HBM admission).  bytes = 0 removes the budget.  Counted against it: the
+ * bytes the library holds (plan tables, status word, tk_ctx_alloc buffers) plus the bytes the
+ * caller has reserved.  A library allocation that would exceed it fails with TK_ERR_BUDGET (plan
+ * creation returns that code), and so does a reservation: tk_ctx_reserve(bytes) admits work whose
+ * memory the caller allocates itself (outputs, workspaces, resident inputs), tk_ctx_release gives
+ * the bytes back (TK_ERR_ARG if more than reserved).  Setting a budget below the current use is
+ * allowed; later allocations and reservations then fail until use drops.  tk_ctx_memory reports
+ * the library's bytes, the reserved bytes, the budget and the number of live library allocations
+ * (any out pointer may be NULL). */
+int tk_ctx_set_budget(tk_ctx* ctx, size_t bytes);
+int tk_ctx_reserve(tk_ctx* ctx, size_t bytes);
+int tk_ctx_release(tk_ctx* ctx, size_t bytes);
+int tk_ctx_memory(tk_ctx* ctx, size_t* library_bytes, size_t* reserved_bytes, size_t* budget_bytes,
+                  int64_t* allocations);
+/* Device buffers through the context's allocator, counted against its budget (TK_ERR_BUDGET,
+ * TK_ERR_OOM).  tk_ctx_free takes only pointers returned by tk_ctx_alloc / tk_tmap_alloc
+ * (TK_ERR_ARG otherwise; NULL is a no-op); the caller makes sure no launch still uses the buffer. */
+int tk_ctx_alloc(tk_ctx* ctx, size_t bytes, void** out);
+int tk_ctx_free(tk_ctx* ctx, void* ptr);
 /* Kernel profiling.  enable != 0: every later launch through ctx is bracketed by CUDA events
  * recorded on its own stream; enable == 0 stops recording.  tk_ctx_profile_read waits for the
  * recorded events and returns, per kernel name (at most max entries, names NUL-terminated in
@@ -154,6 +193,18 @@ int64_t tk_tmap_ntreepairs(const tk_tmap* t);
  * NULL. */
 int tk_tmap_treepair(const tk_tmap* t, int64_t i, int32_t* labels, int64_t* offset, int64_t* ld,
                      int64_t* dims);
+
+/* Data of a tensor map (Sec. 2: a TensorMap is its structure plus one block per coupled sector).
+ * The device buffer holds the blocks in canonical order (the storage layout above), so host data
+ * in that order moves as one copy.  bytes must equal tk_tmap_numel(t) * element size of dtype
+ * (8 for TK_F64, 16 for TK_C128), else TK_ERR_ARG.  Asynchronous on stream (NULL: the context's);
+ * pinned host memory makes the copy truly asynchronous.  tk_tmap_alloc allocates a device buffer
+ * of that size through the context's allocator (release it with tk_ctx_free). */
+int tk_tmap_upload(tk_ctx* ctx, const tk_tmap* t, int dtype, const void* host, size_t bytes, void* device,
+                   void* stream);
+int tk_tmap_download(tk_ctx* ctx, const tk_tmap* t, int dtype, const void* device, void* host, size_t bytes,
+                     void* stream);
+int tk_tmap_alloc(tk_ctx* ctx, const tk_tmap* t, int dtype, void** out);
 
 /* ---- plans ------------------------------------------------------------------------------------
  * A plan holds everything that depends only on structure: output spaces (Algorithm 2),
@@ -209,7 +260,7 @@ int tk_plan_permute_stats(const tk_plan* plan, int which, int64_t* stats);
 int tk_plan_transform(const tk_plan* plan, int which, int64_t k, int64_t* src_offset,
                       int64_t* dst_offset, double* coef);
 
-/* ---- execution (asynchronous on `stream`, a cudaStream_t; NULL = legacy default stream) -------
+/* ---- execution (asynchronous on `stream`, a cudaStream_t; NULL = the context's stream) --------
  * All pointers are device pointers to buffers laid out as the plan's input/output structures.
  * C is fully overwritten.  A and B are never modified.  In the split-precision modes the products
  * left to the CUDA cores run on a second stream owned by the context, forked from `stream` after
@@ -282,18 +333,28 @@ int tk_plan_autotune(tk_ctx* ctx, tk_plan* plan, const void* a, const void* b, v
  *   - Limit: plans whose tk_plan_workspace_bytes() exceeds TK_NOALLOC_SCRATCH_BYTES are rejected
  *     with TK_ERR_WORKSPACE.  Every GPU that loads libtk holds the array until the process exits.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *     that device current; make that first call before any stream capture.
+ *     that device current and keeps it for the life of the process; make that first call before
+ *     any stream capture, and do not call cudaDeviceReset on that device afterwards (the kept
+ *     address would then be stale).
  *   - All calls share the one array, which keeps the previous call's contents; a call writes every
  *     scratch byte it reads, so nothing has to start at zero.  Calls whose kernels overlap on the
  *     GPU (other streams, other host threads) race on the array: serialise them. */
 #define TK_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+size_t tk_noalloc_scratch_bytes(void);  /* TK_NOALLOC_SCRATCH_BYTES as built into the library */
 int tk_contract_noalloc(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, void* c,
-                        void* stream);
+                        void* stream);  /* stream NULL: the context's stream */
 
 /* Host <-> device copies on the context's device (cudaMemcpyAsync; pinned host memory makes
  * them asynchronous). */
 int tk_copy_h2d(tk_ctx* ctx, void* dst_device, const void* src_host, size_t bytes, void* stream);
 int tk_copy_d2h(tk_ctx* ctx, void* dst_host, const void* src_device, size_t bytes, void* stream);
+
+/* ---- measurement --------------------------------------------------------------------------
+ * Peak probe of the FP64 pipe (not in the paper; the denominator of the FP64 sector GEMMs'
+ * roofline): a register-only kernel of independent FMA chains on every SM, sized to run about
+ * `seconds` (0 < seconds <= 30) on `stream` (NULL: the context's), timed with CUDA events.
+ * *tflops = 2 x FMAs / elapsed time; *ms (may be NULL) = the timed launch's duration. */
+int tk_probe_fp64_peak(tk_ctx* ctx, double seconds, double* tflops, double* ms, void* stream);
 
 /* ---- topological data (host, exact) ----------------------------------------------------------
  * F^{abc}_d[e; f] (e couples (a b), f couples (b c)): for SU(2) eq. SU2FSymbol with the 6j symbol

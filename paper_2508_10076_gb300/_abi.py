@@ -13,12 +13,23 @@ c_i64p = C.POINTER(C.c_int64)
 c_intp = C.POINTER(C.c_int)
 c_dblp = C.POINTER(C.c_double)
 c_vp = C.c_void_p
+c_szp = C.POINTER(C.c_size_t)
+
+# allocator hooks of tk_ctx_create (tk_alloc_fn, tk_free_fn)
+ALLOC_FN = C.CFUNCTYPE(c_vp, C.c_size_t, c_vp)
+FREE_FN = C.CFUNCTYPE(None, c_vp, C.c_size_t, c_vp)
 
 # name: (restype, argtypes)
 SIGNATURES = {
     "tk_version": (C.c_int, []),
     "tk_status_string": (C.c_char_p, [C.c_int]),
-    "tk_ctx_create": (C.c_int, [C.c_int, C.POINTER(c_vp)]),
+    "tk_ctx_create": (C.c_int, [C.c_int, c_vp, ALLOC_FN, FREE_FN, c_vp, C.POINTER(c_vp)]),
+    "tk_ctx_set_budget": (C.c_int, [c_vp, C.c_size_t]),
+    "tk_ctx_reserve": (C.c_int, [c_vp, C.c_size_t]),
+    "tk_ctx_release": (C.c_int, [c_vp, C.c_size_t]),
+    "tk_ctx_memory": (C.c_int, [c_vp, c_szp, c_szp, c_szp, c_i64p]),
+    "tk_ctx_alloc": (C.c_int, [c_vp, C.c_size_t, C.POINTER(c_vp)]),
+    "tk_ctx_free": (C.c_int, [c_vp, c_vp]),
     "tk_ctx_destroy": (None, [c_vp]),
     "tk_ctx_last_error": (C.c_char_p, [c_vp]),
     "tk_ctx_sync": (C.c_int, [c_vp, c_vp]),
@@ -41,6 +52,9 @@ SIGNATURES = {
     "tk_tmap_block": (C.c_int, [c_vp, C.c_int, c_i32p, c_i64p, c_i64p, c_i64p]),
     "tk_tmap_ntreepairs": (C.c_int64, [c_vp]),
     "tk_tmap_treepair": (C.c_int, [c_vp, C.c_int64, c_i32p, c_i64p, c_i64p, c_i64p]),
+    "tk_tmap_upload": (C.c_int, [c_vp, c_vp, C.c_int, c_vp, C.c_size_t, c_vp, c_vp]),
+    "tk_tmap_download": (C.c_int, [c_vp, c_vp, C.c_int, c_vp, c_vp, C.c_size_t, c_vp]),
+    "tk_tmap_alloc": (C.c_int, [c_vp, c_vp, C.c_int, C.POINTER(c_vp)]),
     "tk_permute_plan": (C.c_int, [c_vp, c_vp, C.c_int, c_intp, C.c_int, c_intp, C.c_int, C.POINTER(c_vp)]),
     "tk_adjoint_plan": (C.c_int, [c_vp, c_vp, C.c_int, C.POINTER(c_vp)]),
     "tk_contract_plan": (C.c_int, [c_vp, c_vp, C.c_int, c_intp, C.c_int, c_intp, c_vp, C.c_int, c_intp,
@@ -59,6 +73,7 @@ SIGNATURES = {
     "tk_permute": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tk_contract": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
     "tk_contract_noalloc": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "tk_noalloc_scratch_bytes": (C.c_size_t, []),
     "tk_contract_batch": (C.c_int, [c_vp, C.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tk_svd_plan": (C.c_int, [c_vp, c_vp, C.c_int, C.POINTER(c_vp)]),
     "tk_svd_outputs": (C.c_int, [c_vp, c_vp, C.POINTER(c_vp), C.POINTER(c_vp), C.POINTER(C.c_int64)]),
@@ -70,6 +85,7 @@ SIGNATURES = {
     "tk_plan_autotune": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, C.c_size_t, c_vp, c_vp]),
     "tk_copy_h2d": (C.c_int, [c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
     "tk_copy_d2h": (C.c_int, [c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
+    "tk_probe_fp64_peak": (C.c_int, [c_vp, C.c_double, c_dblp, c_dblp, c_vp]),
     "tk_fsymbol": (C.c_double, [C.c_int, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "tk_rsymbol": (C.c_double, [C.c_int, C.c_int32, C.c_int32, C.c_int32]),
 }

@@ -59,6 +59,17 @@ def _stream_handle(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
+def _host_buffer(x):
+    """(address, bytes) of a contiguous numpy array or torch CPU tensor."""
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffer must be contiguous")
+        return x.ctypes.data, x.nbytes
+    if not x.is_contiguous():
+        raise ValueError("host buffer must be contiguous")
+    return x.data_ptr(), x.numel() * x.element_size()
+
+
 def _ptr(t):
     if t is None:
         return C.c_void_p(0)
@@ -67,13 +78,54 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-class Context:
-    """device >= 0: CUDA device; device < 0: host-only (planning and inspection only)."""
+def _make_hooks(device, stream, allocator):
+    """ctypes allocator hooks for tk_ctx_create: PyTorch's caching allocator ("torch") or a pair of
+    Python callables (alloc(bytes) -> int, free(int, bytes))."""
+    if allocator == "torch":
+        import torch
 
-    def __init__(self, device: int = 0):
+        def alloc(nbytes):
+            s = torch.cuda.current_stream(device) if stream is None else stream
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), device, s))
+
+        def free(ptr, nbytes):
+            torch.cuda.caching_allocator_delete(int(ptr))
+    else:
+        alloc, free = allocator
+
+    def c_alloc(nbytes, _user):
+        try:
+            return alloc(int(nbytes)) or None
+        except Exception:
+            return None
+
+    def c_free(ptr, nbytes, _user):
+        try:
+            free(int(ptr), int(nbytes))
+        except Exception:
+            pass
+
+    return _abi.ALLOC_FN(c_alloc), _abi.FREE_FN(c_free)
+
+
+class Context:
+    """device >= 0: CUDA device; device < 0: host-only (planning and inspection only).
+
+    stream: the context's stream (a torch.cuda.Stream or a raw handle; None: the legacy default
+    stream); execution calls given no stream still pass torch's current stream.
+    allocator: None (the library's cudaMalloc / cudaFree) or "torch" (plan tables and the other
+    library allocations come from PyTorch's caching allocator through tk_ctx_create's hooks), or a
+    pair (alloc(bytes) -> int pointer, free(int pointer, bytes)) of Python callables."""
+
+    def __init__(self, device: int = 0, stream=None, allocator=None):
         self._h = C.c_void_p()
-        _check(_lib().tk_ctx_create(int(device), C.byref(self._h)))
         self.device = device
+        self._hooks = (_abi.ALLOC_FN(), _abi.FREE_FN())  # NULL hooks
+        if allocator is not None and device >= 0:
+            self._hooks = _make_hooks(device, stream, allocator)
+        sh = C.c_void_p(0) if stream is None else (C.c_void_p(stream) if isinstance(stream, int)
+                                                   else C.c_void_p(stream.cuda_stream))
+        _check(_lib().tk_ctx_create(int(device), sh, self._hooks[0], self._hooks[1], None, C.byref(self._h)))
 
     def close(self):
         if self._h:
@@ -88,6 +140,37 @@ class Context:
 
     def sync(self, stream=None):
         _check(_lib().tk_ctx_sync(self._h, _stream_handle(stream)), self)
+
+    def _stream(self, stream):
+        """Stream handle for a call (host-only contexts: NULL, no torch CUDA query)."""
+        return C.c_void_p(0) if self.device < 0 and stream is None else _stream_handle(stream)
+
+    # ---- device memory (tk_ctx_set_budget / reserve / release / memory / alloc / free)
+    def set_budget(self, nbytes):
+        _check(_lib().tk_ctx_set_budget(self._h, C.c_size_t(int(nbytes))), self)
+
+    def reserve(self, nbytes):
+        """Admit nbytes of caller-allocated memory against the budget (TKError code 11 if over)."""
+        _check(_lib().tk_ctx_reserve(self._h, C.c_size_t(int(nbytes))), self)
+
+    def release(self, nbytes):
+        _check(_lib().tk_ctx_release(self._h, C.c_size_t(int(nbytes))), self)
+
+    def memory(self):
+        """dict(library_bytes, reserved_bytes, budget_bytes, allocations)."""
+        lb, rb, bb, n = C.c_size_t(), C.c_size_t(), C.c_size_t(), C.c_int64()
+        _check(_lib().tk_ctx_memory(self._h, C.byref(lb), C.byref(rb), C.byref(bb), C.byref(n)), self)
+        return {"library_bytes": lb.value, "reserved_bytes": rb.value, "budget_bytes": bb.value,
+                "allocations": n.value}
+
+    def alloc(self, nbytes):
+        """Raw device pointer (int) of nbytes through the context's allocator; free with free()."""
+        p = C.c_void_p()
+        _check(_lib().tk_ctx_alloc(self._h, C.c_size_t(int(nbytes)), C.byref(p)), self)
+        return p.value or 0
+
+    def free(self, ptr):
+        _check(_lib().tk_ctx_free(self._h, C.c_void_p(ptr)), self)
 
     @property
     def launches(self):
@@ -202,6 +285,19 @@ class TensorMap:
             _check(_lib().tk_tmap_block(self._h, i, C.byref(s), C.byref(r), C.byref(c), C.byref(o)))
             out.append((s.value, r.value, c.value, o.value))
         return out
+
+    def upload(self, host, device, dtype="f64", stream=None):
+        """tk_tmap_upload: host buffer (numpy array or torch CPU tensor) -> device tensor, blocks in
+        canonical order; the sizes must match this structure."""
+        hp, nb = _host_buffer(host)
+        _check(_lib().tk_tmap_upload(self.ctx._h, self._h, DTYPE[dtype], C.c_void_p(hp), C.c_size_t(nb),
+                                     _ptr(device), self.ctx._stream(stream)), self.ctx)
+
+    def download(self, device, host, dtype="f64", stream=None):
+        """tk_tmap_download: device tensor -> host buffer (numpy array or torch CPU tensor)."""
+        hp, nb = _host_buffer(host)
+        _check(_lib().tk_tmap_download(self.ctx._h, self._h, DTYPE[dtype], _ptr(device), C.c_void_p(hp),
+                                       C.c_size_t(nb), self.ctx._stream(stream)), self.ctx)
 
     def treepairs(self):
         """[(uncoupled labels, split inner, coupled, fusion inner, offset, ld, dims)]"""
@@ -395,8 +491,9 @@ def autotune(ctx, plan, a, b, c, workspace, stream=None):
     return choice.value // 8, choice.value % 8
 
 
-# Mirrors TK_NOALLOC_SCRATCH_BYTES in include/tk.h.
-NOALLOC_SCRATCH_BYTES = 32 << 20
+def noalloc_scratch_bytes():
+    """Size of libtk's built-in scratch array (tk_noalloc_scratch_bytes)."""
+    return int(_lib().tk_noalloc_scratch_bytes())
 
 
 def contract_noalloc(ctx, plan, a, b, c, stream=None):
@@ -413,6 +510,13 @@ def copy_h2d(ctx, dst, src_host_ptr, nbytes, stream=None):
 def copy_d2h(ctx, dst_host_ptr, src, nbytes, stream=None):
     _check(_lib().tk_copy_d2h(ctx._h, C.c_void_p(dst_host_ptr), _ptr(src), C.c_size_t(nbytes),
                               _stream_handle(stream)), ctx)
+
+
+def probe_fp64_peak(ctx, seconds=1.0, stream=None):
+    """tk_probe_fp64_peak: (TFLOP/s of a register-only FP64 FMA loop on every SM, its ms)."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(_lib().tk_probe_fp64_peak(ctx._h, C.c_double(seconds), C.byref(tf), C.byref(ms), _stream_handle(stream)), ctx)
+    return tf.value, ms.value
 
 
 def fsymbol(sym, a, b, c, d, e, f):

@@ -6,23 +6,7 @@
 #include <exception>
 #include <new>
 
-#include "tk_internal.hpp"
-
-struct tk_ctx {
-  tk::Ctx c;
-};
-struct tk_space {
-  tk::Space s;
-};
-struct tk_tmap {
-  std::shared_ptr<tk::Structure> st;
-};
-struct tk_plan {
-  int kind = 0;  // 0 permute, 1 contract, 2 block SVD
-  std::shared_ptr<tk::PermutePlan> perm;
-  std::shared_ptr<tk::ContractPlan> con;
-  std::shared_ptr<tk::SvdPlan> svd;
-};
+#include "abi_handles.hpp"
 
 namespace {
 
@@ -60,6 +44,9 @@ int set_device(tk_ctx* ctx) {
   return TK_OK;
 }
 
+// An execution call given a NULL stream runs on the context's stream.
+void* use_stream(const tk_ctx* ctx, void* stream) { return stream ? stream : ctx->c.stream; }
+
 }  // namespace
 
 extern "C" {
@@ -79,16 +66,25 @@ const char* tk_status_string(int s) {
     case TK_ERR_TIMEOUT: return "device wait timed out";
     case TK_ERR_WORKSPACE: return "workspace too small";
     case TK_ERR_NO_DEVICE: return "host-only context";
+    case TK_ERR_BUDGET: return "device memory budget exceeded";
   }
   return "unknown status";
 }
 
-int tk_ctx_create(int device, tk_ctx** out) {
+int tk_ctx_create(int device, void* stream, tk_alloc_fn alloc, tk_free_fn release, void* alloc_user,
+                  tk_ctx** out) {
   if (!out) return TK_ERR_ARG;
   *out = nullptr;
+  if ((alloc == nullptr) != (release == nullptr)) return TK_ERR_ARG;  // both hooks or neither
   tk_ctx* ctx = new (std::nothrow) tk_ctx();
   if (!ctx) return TK_ERR_OOM;
   ctx->c.device = device < 0 ? -1 : device;
+  ctx->c.stream = device < 0 ? nullptr : stream;
+  ctx->c.mem = std::make_shared<tk::DeviceMemory>();
+  ctx->c.mem->device = ctx->c.device;
+  ctx->c.mem->alloc = alloc;
+  ctx->c.mem->release = release;
+  ctx->c.mem->user = alloc_user;
   if (device >= 0) {
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || device >= n) {
@@ -100,19 +96,23 @@ int tk_ctx_create(int device, tk_ctx** out) {
       delete ctx;
       return TK_ERR_CUDA;
     }
-    if (cudaMalloc((void**)&ctx->c.d_status, sizeof(int) * 4) != cudaSuccess) {
+    void* st = nullptr;
+    int rc = tk::dev_alloc(&ctx->c, &st, sizeof(int) * 4);
+    if (rc != TK_OK) {
       delete ctx;
-      return TK_ERR_OOM;
+      return rc;
     }
-    cudaMemset(ctx->c.d_status, 0, sizeof(int) * 4);
+    ctx->c.d_status = (int*)st;
     cudaStream_t side = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaMemsetAsync(ctx->c.d_status, 0, sizeof(int) * 4, (cudaStream_t)stream) != cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) {
       if (side) cudaStreamDestroy(side);
       if (e0) cudaEventDestroy(e0);
-      cudaFree(ctx->c.d_status);
+      tk::dev_free(ctx->c.d_status);
       delete ctx;
       return TK_ERR_CUDA;
     }
@@ -131,7 +131,7 @@ void tk_ctx_destroy(tk_ctx* ctx) {
     ctx->c.perm_cache.clear();
     ctx->c.contract_cache.clear();
     tk::destroy_solver_handle(&ctx->c);
-    if (ctx->c.d_status) cudaFree(ctx->c.d_status);
+    tk::dev_free(ctx->c.d_status);
     if (ctx->c.side) cudaStreamDestroy((cudaStream_t)ctx->c.side);
     if (ctx->c.ev_fork) cudaEventDestroy((cudaEvent_t)ctx->c.ev_fork);
     if (ctx->c.ev_join) cudaEventDestroy((cudaEvent_t)ctx->c.ev_join);
@@ -139,9 +139,72 @@ void tk_ctx_destroy(tk_ctx* ctx) {
   delete ctx;
 }
 
+int tk_ctx_set_budget(tk_ctx* ctx, size_t bytes) {
+  if (!ctx) return TK_ERR_ARG;
+  std::lock_guard<std::mutex> lk(ctx->c.mem->mu);
+  ctx->c.mem->budget = bytes;
+  return TK_OK;
+}
+
+int tk_ctx_reserve(tk_ctx* ctx, size_t bytes) {
+  if (!ctx) return TK_ERR_ARG;
+  tk::DeviceMemory& m = *ctx->c.mem;
+  std::lock_guard<std::mutex> lk(m.mu);
+  if (m.budget && m.in_use + m.reserved + bytes > m.budget) {
+    ctx->c.last_error = "reserving " + std::to_string(bytes) + " bytes would exceed the budget of " +
+                        std::to_string(m.budget) + " (library " + std::to_string(m.in_use) + ", reserved " +
+                        std::to_string(m.reserved) + ")";
+    return TK_ERR_BUDGET;
+  }
+  m.reserved += bytes;
+  return TK_OK;
+}
+
+int tk_ctx_release(tk_ctx* ctx, size_t bytes) {
+  if (!ctx) return TK_ERR_ARG;
+  tk::DeviceMemory& m = *ctx->c.mem;
+  std::lock_guard<std::mutex> lk(m.mu);
+  if (bytes > m.reserved) return fail(ctx, TK_ERR_ARG, "releasing more than was reserved");
+  m.reserved -= bytes;
+  return TK_OK;
+}
+
+int tk_ctx_memory(tk_ctx* ctx, size_t* library_bytes, size_t* reserved_bytes, size_t* budget_bytes,
+                  int64_t* allocations) {
+  if (!ctx) return TK_ERR_ARG;
+  tk::DeviceMemory& m = *ctx->c.mem;
+  std::lock_guard<std::mutex> lk(m.mu);
+  if (library_bytes) *library_bytes = m.in_use;
+  if (reserved_bytes) *reserved_bytes = m.reserved;
+  if (budget_bytes) *budget_bytes = m.budget;
+  if (allocations) *allocations = (int64_t)m.allocations;
+  return TK_OK;
+}
+
+int tk_ctx_alloc(tk_ctx* ctx, size_t bytes, void** out) {
+  if (!ctx || !out) return fail(ctx, TK_ERR_ARG, "null argument");
+  *out = nullptr;
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  rc = tk::dev_alloc(&ctx->c, out, bytes);
+  if (rc == TK_ERR_BUDGET) return fail(ctx, rc, "allocation of " + std::to_string(bytes) + " bytes exceeds the budget");
+  if (rc != TK_OK) return fail(ctx, rc, "device allocation failed");
+  return TK_OK;
+}
+
+int tk_ctx_free(tk_ctx* ctx, void* ptr) {
+  if (!ctx) return TK_ERR_ARG;
+  if (!ptr) return TK_OK;
+  if (!tk::dev_owns(ptr)) return fail(ctx, TK_ERR_ARG, "not an allocation of the library");
+  if (ctx->c.device >= 0) cudaSetDevice(ctx->c.device);
+  tk::dev_free(ptr);
+  return TK_OK;
+}
+
 const char* tk_ctx_last_error(const tk_ctx* ctx) { return ctx ? ctx->c.last_error.c_str() : "null context"; }
 
 int tk_ctx_sync(tk_ctx* ctx, void* stream) {
+  if (ctx) stream = use_stream(ctx, stream);
   if (!ctx) return TK_ERR_ARG;
   int rc = set_device(ctx);
   if (rc != TK_OK) return rc;
@@ -161,6 +224,7 @@ int tk_ctx_sync(tk_ctx* ctx, void* stream) {
 int64_t tk_ctx_launch_count(const tk_ctx* ctx) { return ctx ? ctx->c.launches : -1; }
 
 int tk_ctx_selftest_timeout(tk_ctx* ctx, void* stream) {
+  if (ctx) stream = use_stream(ctx, stream);
   if (!ctx) return TK_ERR_ARG;
   int rc = set_device(ctx);
   if (rc != TK_OK) return rc;
@@ -532,6 +596,7 @@ int tk_plan_permute_stats(const tk_plan* plan, int which, int64_t* stats) {
 }
 
 int tk_permute(tk_ctx* ctx, const tk_plan* plan, const void* a, void* c, void* stream) {
+  if (ctx) stream = use_stream(ctx, stream);
   if (!ctx || !plan || plan->kind != 0) return fail(ctx, TK_ERR_ARG, "not a permute plan");
   if (!a || !c) return fail(ctx, TK_ERR_ARG, "null buffer");
   int rc = set_device(ctx);
@@ -549,6 +614,7 @@ int tk_permute(tk_ctx* ctx, const tk_plan* plan, const void* a, void* c, void* s
 
 int tk_contract(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, void* c,
                 void* workspace, size_t workspace_bytes, void* stream) {
+  if (ctx) stream = use_stream(ctx, stream);
   if (!ctx || !plan || plan->kind != 1) return fail(ctx, TK_ERR_ARG, "not a contraction plan");
   if (!a || !b || !c) return fail(ctx, TK_ERR_ARG, "null buffer");
   const tk::ContractPlan& cp = *plan->con;
@@ -563,6 +629,7 @@ int tk_contract(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, 
 int tk_contract_batch(tk_ctx* ctx, int n, const tk_plan* const* plans, const void* const* a,
                       const void* const* b, void* const* c, void* const* workspace,
                       const size_t* workspace_bytes, void* stream) {
+  if (ctx) stream = use_stream(ctx, stream);
   if (!ctx || n < 0) return fail(ctx, TK_ERR_ARG, "bad batch");
   if (n == 0) return TK_OK;
   if (!plans || !a || !b || !c || !workspace || !workspace_bytes) return fail(ctx, TK_ERR_ARG, "null array");
@@ -654,6 +721,7 @@ static int autotune_contract(tk_ctx* ctx, tk::ContractPlan& cp, const void* a, c
 
 int tk_plan_autotune(tk_ctx* ctx, tk_plan* plan, const void* a, const void* b, void* c, void* workspace,
                      size_t workspace_bytes, void* stream, int* choice) {
+  if (ctx) stream = use_stream(ctx, stream);
   if (!ctx || !plan || plan->kind != 1) return fail(ctx, TK_ERR_ARG, "not a contraction plan");
   if (!a || !b || !c || !workspace) return fail(ctx, TK_ERR_ARG, "null buffer");
   int rc = set_device(ctx);
@@ -724,6 +792,7 @@ int tk_svd_block(const tk_plan* plan, int64_t i, int32_t* sector, int64_t* rows,
 
 int tk_svd(tk_ctx* ctx, const tk_plan* plan, const void* a, void* u, double* s, void* vh, void* workspace,
            size_t workspace_bytes, void* stream) {
+  if (ctx) stream = use_stream(ctx, stream);
   if (!ctx || !plan || plan->kind != 2) return fail(ctx, TK_ERR_ARG, "not an SVD plan");
   if (!a || !u || !s || !vh) return fail(ctx, TK_ERR_ARG, "null buffer");
   const tk::SvdPlan& sp = *plan->svd;
@@ -737,6 +806,7 @@ int tk_svd(tk_ctx* ctx, const tk_plan* plan, const void* a, void* u, double* s, 
 
 int tk_svd_truncate(tk_ctx* ctx, const tk_plan* plan, const int64_t* keep, const void* u, const double* s,
                     const void* vh, void* ut, double* st, void* vht, void* stream) {
+  if (ctx) stream = use_stream(ctx, stream);
   if (!ctx || !plan || plan->kind != 2 || !keep) return fail(ctx, TK_ERR_ARG, "not an SVD plan");
   int rc = set_device(ctx);
   if (rc != TK_OK) return rc;
@@ -744,7 +814,52 @@ int tk_svd_truncate(tk_ctx* ctx, const tk_plan* plan, const int64_t* keep, const
   return rc == TK_OK ? TK_OK : fail(ctx, rc, "truncation copy failed");
 }
 
+static int tmap_io_check(tk_ctx* ctx, const tk_tmap* t, int dtype, size_t bytes) {
+  if (!t) return fail(ctx, TK_ERR_ARG, "null tensor map");
+  if (dtype != TK_F64 && dtype != TK_C128) return fail(ctx, TK_ERR_ARG, "unknown dtype");
+  const size_t want = (size_t)t->st->numel * (dtype == TK_C128 ? 16 : 8);
+  if (bytes != want)
+    return fail(ctx, TK_ERR_ARG, "tensor map of " + std::to_string(t->st->numel) + " elements holds " +
+                                     std::to_string(want) + " bytes, not " + std::to_string(bytes));
+  return TK_OK;
+}
+
+int tk_tmap_upload(tk_ctx* ctx, const tk_tmap* t, int dtype, const void* host, size_t bytes, void* device,
+                   void* stream) {
+  if (!ctx) return TK_ERR_ARG;
+  stream = use_stream(ctx, stream);
+  int rc = tmap_io_check(ctx, t, dtype, bytes);
+  if (rc != TK_OK) return rc;
+  if (bytes && (!host || !device)) return fail(ctx, TK_ERR_ARG, "null buffer");
+  if ((rc = set_device(ctx)) != TK_OK) return rc;
+  if (bytes && cudaMemcpyAsync(device, host, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream) != cudaSuccess)
+    return fail(ctx, TK_ERR_CUDA, "host to device copy failed");
+  return TK_OK;
+}
+
+int tk_tmap_download(tk_ctx* ctx, const tk_tmap* t, int dtype, const void* device, void* host, size_t bytes,
+                     void* stream) {
+  if (!ctx) return TK_ERR_ARG;
+  stream = use_stream(ctx, stream);
+  int rc = tmap_io_check(ctx, t, dtype, bytes);
+  if (rc != TK_OK) return rc;
+  if (bytes && (!host || !device)) return fail(ctx, TK_ERR_ARG, "null buffer");
+  if ((rc = set_device(ctx)) != TK_OK) return rc;
+  if (bytes && cudaMemcpyAsync(host, device, bytes, cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
+    return fail(ctx, TK_ERR_CUDA, "device to host copy failed");
+  return TK_OK;
+}
+
+int tk_tmap_alloc(tk_ctx* ctx, const tk_tmap* t, int dtype, void** out) {
+  if (!ctx || !out) return fail(ctx, TK_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (!t) return fail(ctx, TK_ERR_ARG, "null tensor map");
+  if (dtype != TK_F64 && dtype != TK_C128) return fail(ctx, TK_ERR_ARG, "unknown dtype");
+  return tk_ctx_alloc(ctx, (size_t)t->st->numel * (dtype == TK_C128 ? 16 : 8), out);
+}
+
 int tk_copy_h2d(tk_ctx* ctx, void* dst_device, const void* src_host, size_t bytes, void* stream) {
+  if (ctx) stream = use_stream(ctx, stream);
   if (!ctx || (bytes && (!dst_device || !src_host))) return fail(ctx, TK_ERR_ARG, "null argument");
   int rc = set_device(ctx);
   if (rc != TK_OK) return rc;
@@ -754,6 +869,7 @@ int tk_copy_h2d(tk_ctx* ctx, void* dst_device, const void* src_host, size_t byte
 }
 
 int tk_copy_d2h(tk_ctx* ctx, void* dst_host, const void* src_device, size_t bytes, void* stream) {
+  if (ctx) stream = use_stream(ctx, stream);
   if (!ctx || (bytes && (!dst_host || !src_device))) return fail(ctx, TK_ERR_ARG, "null argument");
   int rc = set_device(ctx);
   if (rc != TK_OK) return rc;

@@ -18,21 +18,6 @@
 namespace tk {
 
 // ------------------------------------------------------------------ helpers
-int dev_upload(Ctx* ctx, void** dst, const void* src, size_t bytes) {
-  if (bytes == 0) {
-    *dst = nullptr;
-    return TK_OK;
-  }
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return TK_ERR_CUDA;
-  if (cudaMalloc(dst, bytes) != cudaSuccess) return TK_ERR_OOM;
-  if (cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return TK_ERR_CUDA;
-  return TK_OK;
-}
-
-void dev_free(void* p) {
-  if (p) cudaFree(p);
-}
-
 ProfScope::ProfScope(Ctx* c, const char* n, void* s) : ctx(c), name(n), stream(s) {
   if (!ctx->profiling) return;
   cudaEvent_t e;

@@ -20,7 +20,7 @@
 #include <mutex>
 #include <string>
 
-#include "tk_internal.hpp"
+#include "abi_handles.hpp"
 
 namespace {
 
@@ -54,20 +54,12 @@ int scratch_address(int device, void** out, std::string& err) {
 
 }  // namespace
 
-// The ABI handle layouts are private to abi.cpp; this file reaches the plan and context through
-// the same definitions.
-struct tk_ctx {
-  tk::Ctx c;
-};
-struct tk_plan {
-  int kind = 0;
-  std::shared_ptr<tk::PermutePlan> perm;
-  std::shared_ptr<tk::ContractPlan> con;
-};
+extern "C" size_t tk_noalloc_scratch_bytes(void) { return kNoallocScratchBytes; }
 
 extern "C" int tk_contract_noalloc(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, void* c,
                                    void* stream) {
   if (!ctx) return TK_ERR_ARG;
+  if (!stream) stream = ctx->c.stream;
   if (!plan || plan->kind != 1) {
     ctx->c.last_error = "not a contraction plan";
     return TK_ERR_ARG;

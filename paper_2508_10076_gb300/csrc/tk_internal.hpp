@@ -232,8 +232,27 @@ struct Error {
   std::string msg;
 };
 
+// Device memory of one context: every allocation the library makes (plan tables, the status
+// word) goes through the caller's hooks, or cudaMalloc / cudaFree when none were given, and is
+// counted.  With a budget set, an allocation or a caller reservation that would take the library
+// bytes plus the reserved bytes above it fails with TK_ERR_BUDGET.  Allocations remember their
+// DeviceMemory, which therefore lives until its last allocation is freed, after the context.
+struct DeviceMemory {
+  int device = -1;
+  tk_alloc_fn alloc = nullptr;
+  tk_free_fn release = nullptr;
+  void* user = nullptr;
+  std::mutex mu;
+  size_t in_use = 0;    // bytes the library holds
+  size_t reserved = 0;  // bytes the caller reserved (tk_ctx_reserve)
+  size_t budget = 0;    // 0: no budget
+  size_t allocations = 0;
+};
+
 struct Ctx {
   int device = -1;
+  void* stream = nullptr;  // the context's stream: execution calls given a NULL stream use it
+  std::shared_ptr<DeviceMemory> mem;
   std::string last_error;
   int64_t launches = 0;
   int num_sms = 0;
@@ -293,8 +312,12 @@ struct ProfScope {
 };
 
 // ------------------------------------------------------------------ device side (kernels)
+// Allocation through the context's DeviceMemory (TK_ERR_BUDGET over budget, TK_ERR_OOM when the
+// allocator fails); dev_free finds the allocation's DeviceMemory by address.
+int dev_alloc(Ctx* ctx, void** dst, size_t bytes);
 int dev_upload(Ctx* ctx, void** dst, const void* src, size_t bytes);
 void dev_free(void* p);
+bool dev_owns(void* p);  // p is a live allocation of the library (tk_ctx_free checks it)
 int launch_permute(Ctx* ctx, const PermutePlan& pp, const void* in, void* out, void* stream);
 struct PermJob {
   const PermutePlan* plan;

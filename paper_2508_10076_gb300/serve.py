@@ -4,8 +4,10 @@ dimension D, SU(2) at reduced multiplicity D/4), FP64 or complex128, arriving as
 
 Scheduling, per pass of the loop:
   * requests whose arrival time has passed join the queue;
-  * queued requests are admitted while their device memory (output + workspace) fits the HBM
-    budget and an in-flight slot is free;
+  * the HBM budget is the context's (tk_ctx_set_budget): the plan tables libtk holds count against
+    it, every shape's resident inputs are reserved when the shape is created (tk_ctx_reserve), and a
+    queued request is admitted while its output + workspace can be reserved too (TK_ERR_BUDGET
+    otherwise) and an in-flight slot is free; a finished batch releases its reservation;
   * the admitted requests of one dtype go to the GPU together through tk_contract_batch (their
     permutes, zero fills and sector-GEMM tiles share launches) on the next of several CUDA streams,
     so batches overlap on the device while new requests keep arriving;
@@ -14,7 +16,8 @@ Scheduling, per pass of the loop:
     instead of in the FP64 batches;
   * finished batches (their end event has completed) release memory and slots.
 Latency = completion time on the device clock - arrival time, both relative to one start event.
-Plans (structure, recoupling tables, GEMM work lists) are built once per shape and stay resident.
+Plans (structure, recoupling tables, GEMM work lists) are built once per shape, autotuned once
+on the shape's resident inputs (tk_plan_autotune) before any request is timed, and stay resident.
 """
 
 import time
@@ -51,24 +54,49 @@ def request_stream(n, seed=0, rate_per_s=None, grid=None):
     return [dict(idx=i, gap=float(gaps[i]), sym=str(sym[i]), D=int(D[i]), dtype=str(dtype[i])) for i in range(n)]
 
 
+def shape_inputs(ctx, sym, D, dtype, seed=0):
+    """(legs, L structure, x structure, host data of L, host data of x) of one request shape: U(1)
+    at bond dimension D, SU(2) at reduced multiplicity D/4 (at least 8), seeded N(0,1) blocks
+    (N(0,1/2) per component for complex128)."""
+    V, P, W = wl.heff_spaces(sym, D if sym == "U1" else max(8, D // 4))
+    legs = wl.heff_legs(V, P, W)
+    L, x = _tmap(ctx, sym, legs["L"]), _tmap(ctx, sym, legs["x"])
+    rnd = wl.normal_complex if dtype == "c128" else wl.normal
+    return legs, L, x, np.ascontiguousarray(rnd(seed * 16 + 1, L.numel)), np.ascontiguousarray(rnd(seed * 16 + 0, x.numel))
+
+
 class Shape:
-    """Plans and resident inputs of one request shape (symmetry, D, dtype)."""
+    """Plans and resident inputs of one request shape (symmetry, D, dtype).  The resident inputs
+    are reserved against the context's budget for the life of the shape."""
 
     def __init__(self, ctx, sym, D, dtype, seed=0, split_gemm=None):
-        V, P, W = wl.heff_spaces(sym, D if sym == "U1" else max(8, D // 4))
-        legs = wl.heff_legs(V, P, W)
-        L, x = _tmap(ctx, sym, legs["L"]), _tmap(ctx, sym, legs["x"])
+        legs, L, x, a_host, b_host = shape_inputs(ctx, sym, D, dtype, seed)
+        self.legs = legs
         self.plan = api.contract_plan(ctx, L, *wl.LX_SPEC[:2], x, *wl.LX_SPEC[2:], dtype=dtype)
         self.flops = self.plan.flops
         self.tdt = torch.complex128 if dtype == "c128" else torch.float64
-        rnd = wl.normal_complex if dtype == "c128" else wl.normal
-        self.a = torch.from_numpy(np.ascontiguousarray(rnd(seed * 16 + 1, L.numel))).to("cuda", self.tdt)
-        self.b = torch.from_numpy(np.ascontiguousarray(rnd(seed * 16 + 0, x.numel))).to("cuda", self.tdt)
+        self.esize = 16 if dtype == "c128" else 8
+        self.resident = (L.numel + x.numel) * self.esize
+        ctx.reserve(self.resident)
+        self.a = torch.from_numpy(a_host).to("cuda", self.tdt)
+        self.b = torch.from_numpy(b_host).to("cuda", self.tdt)
         self.split_plan = (api.contract_plan(ctx, L, *wl.LX_SPEC[:2], x, *wl.LX_SPEC[2:], dtype=dtype, gemm=split_gemm)
                            if split_gemm else None)
         self.solo = False  # served alone in split precision (set by calibrated_rate)
         self.out_numel = self.plan.output().numel
-        self.esize = 16 if dtype == "c128" else 8
+        self.tuned = False
+
+    def autotune(self, ctx):
+        """Pick each plan's work list on the resident inputs (tk_plan_autotune), once."""
+        if self.tuned:
+            return
+        for plan in (self.plan, self.split_plan):
+            if plan is None:
+                continue
+            c = torch.empty(self.out_numel, dtype=self.tdt, device="cuda")
+            ws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
+            api.autotune(ctx, plan, self.a, self.b, c, ws)
+        self.tuned = True
 
     @property
     def serve_plan(self):
@@ -80,12 +108,13 @@ class Shape:
 
     @property
     def bytes(self):
+        """Device bytes of one request in flight: its output and its workspace."""
         return self.out_numel * self.esize + self.ws_bytes
 
 
 class Server:
     def __init__(self, ctx, budget_bytes=150 << 30, streams=3, max_batch=64, max_inflight=256,
-                 split_gemm=None, solo_ms=1.0):
+                 split_gemm=None, solo_ms=1.0, autotune=True):
         self.ctx = ctx
         self.split_gemm = split_gemm
         self.solo_ms = solo_ms
@@ -93,13 +122,42 @@ class Server:
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
         self.max_batch = max_batch
         self.max_inflight = max_inflight
+        self.autotune = autotune
         self.shapes = {}
+
+    @property
+    def budget(self):
+        return self.ctx.memory()["budget_bytes"]
+
+    @budget.setter
+    def budget(self, nbytes):
+        """The HBM budget of the server's context (tk_ctx_set_budget)."""
+        self.ctx.set_budget(int(nbytes))
 
     def shape(self, sym, D, dtype):
         key = (sym, D, dtype)
         if key not in self.shapes:
-            self.shapes[key] = Shape(self.ctx, sym, D, dtype, split_gemm=self.split_gemm)
+            sh = Shape(self.ctx, sym, D, dtype, split_gemm=self.split_gemm)
+            if self.autotune:
+                sh.autotune(self.ctx)
+            self.shapes[key] = sh
         return self.shapes[key]
+
+    def close(self):
+        """Drop the shapes: their resident inputs' reservations go back to the context."""
+        for sh in self.shapes.values():
+            self.ctx.release(sh.resident)
+        self.shapes = {}
+
+    def _admit(self, nbytes):
+        """Reserve a request's output + workspace against the budget; False if it does not fit."""
+        try:
+            self.ctx.reserve(nbytes)
+            return True
+        except api.TKError as e:
+            if e.code != 11:  # TK_ERR_BUDGET
+                raise
+            return False
 
     def run(self, requests, rate_per_s, keep_outputs=False):
         """Serve `requests` (from request_stream) arriving at rate_per_s; returns per-request
@@ -114,7 +172,7 @@ class Server:
         host0 = time.perf_counter()
         pending = list(range(len(requests)))  # in arrival order
         queue, inflight, done = [], [], {}
-        in_use, slots, next_stream, p = 0, 0, 0, 0
+        slots, next_stream, p = 0, 0, 0
         outputs = {}
         batches = 0
         while p < len(pending) or queue or inflight:
@@ -129,7 +187,7 @@ class Server:
                     t_end = t_start.elapsed_time(b["end"])  # ms since start, device clock
                     for i in b["reqs"]:
                         done[i] = t_end - 1e3 * arrivals[i]
-                    in_use -= b["bytes"]
+                    self.ctx.release(b["bytes"])
                     slots -= len(b["reqs"])
                     if not keep_outputs:
                         b["bufs"] = None
@@ -144,14 +202,17 @@ class Server:
                 r = requests[i]
                 sh = self.shape(r["sym"], r["D"], r["dtype"])
                 group = solo if sh.solo else admitted[r["dtype"]]
-                if (in_use + sh.bytes <= self.budget and slots < self.max_inflight and
-                        (sh.solo or len(group) < self.max_batch)):
+                if (slots < self.max_inflight and (sh.solo or len(group) < self.max_batch) and
+                        self._admit(sh.bytes)):
                     group.append(i)
-                    in_use += sh.bytes
                     slots += 1
                 else:
                     rest.append(i)
             queue = rest
+            if queue and not inflight and slots == 0:
+                r = requests[queue[0]]
+                raise RuntimeError(f"request {r} needs {self.shape(r['sym'], r['D'], r['dtype']).bytes} bytes, more "
+                                   f"than the budget leaves with nothing in flight ({self.ctx.memory()})")
             for dt, group in admitted.items():
                 if not group:
                     continue

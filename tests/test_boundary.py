@@ -1,0 +1,86 @@
+"""Host-side logic of the C ABI's context: budget admission (TK_ERR_BUDGET), reservations,
+allocator-hook arguments, typed tensor-map I/O size checks, and the built-in scratch size.
+Host-only contexts run no device code, so these run on the CPU."""
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2508_10076_gb300 import api, build_library
+from paper_2508_10076_gb300 import _abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TK_ERR_ARG, TK_ERR_NO_DEVICE, TK_ERR_BUDGET = 1, 10, 11
+
+
+@pytest.fixture(scope="module")
+def hctx():
+    build_library()
+    return api.Context(-1)
+
+
+def test_budget_admits_reservations_until_full(hctx):
+    hctx.set_budget(1000)
+    assert hctx.memory()["budget_bytes"] == 1000
+    hctx.reserve(600)
+    with pytest.raises(api.TKError) as e:
+        hctx.reserve(401)
+    assert e.value.code == TK_ERR_BUDGET
+    hctx.reserve(400)                      # exactly full
+    assert hctx.memory()["reserved_bytes"] == 1000
+    hctx.release(600)
+    hctx.reserve(500)
+    with pytest.raises(api.TKError) as e:  # giving back more than is reserved
+        hctx.release(10_000)
+    assert e.value.code == TK_ERR_ARG
+    hctx.release(900)
+    hctx.set_budget(0)                     # no budget: anything goes
+    hctx.reserve(1 << 60)
+    hctx.release(1 << 60)
+    assert hctx.memory()["reserved_bytes"] == 0
+
+
+def test_host_only_context_refuses_device_allocation(hctx):
+    with pytest.raises(api.TKError) as e:
+        hctx.alloc(256)
+    assert e.value.code == TK_ERR_NO_DEVICE
+    assert hctx.memory()["library_bytes"] == 0 and hctx.memory()["allocations"] == 0
+
+
+def test_allocator_hooks_come_in_pairs():
+    build_library()
+    lib = _abi.load()
+    h = C.c_void_p()
+    only_alloc = _abi.ALLOC_FN(lambda n, u: None)
+    rc = lib.tk_ctx_create(-1, None, only_alloc, _abi.FREE_FN(), None, C.byref(h))
+    assert rc == TK_ERR_ARG and not h.value
+
+
+def test_tmap_io_checks_size_and_dtype(hctx):
+    s = hctx.space("U1", {-1: 2, 0: 3, 1: 2})
+    t = hctx.tmap([s, s], [s])
+    host = np.zeros(t.numel, dtype=np.float64)
+    with pytest.raises(api.TKError) as e:  # wrong size: checked before any device work
+        t.upload(host[:-1], 0)
+    assert e.value.code == TK_ERR_ARG
+    with pytest.raises(api.TKError) as e:  # a float64 buffer is half of what complex128 needs
+        t.upload(host, 0, dtype="c128")
+    assert e.value.code == TK_ERR_ARG
+    with pytest.raises(api.TKError) as e:  # right size, but no device on this context (the address
+        t.upload(host, 4096)               # is never dereferenced: the call stops at the device check)
+    assert e.value.code == TK_ERR_NO_DEVICE
+    cx = np.zeros(t.numel, dtype=np.complex128)
+    with pytest.raises(api.TKError) as e:
+        t.download(0, cx)                  # f64 download into a buffer twice too large
+    assert e.value.code == TK_ERR_ARG
+
+
+def test_noalloc_scratch_size_matches_header():
+    build_library()
+    with open(os.path.join(ROOT, "include", "tk.h")) as fh:
+        m = re.search(r"#define TK_NOALLOC_SCRATCH_BYTES \(\(size_t\)(\d+) << (\d+)\)", fh.read())
+    assert m, "TK_NOALLOC_SCRATCH_BYTES not found in tk.h"
+    assert api.noalloc_scratch_bytes() == int(m.group(1)) << int(m.group(2))
