@@ -1,9 +1,12 @@
 """Benchmark of the symmetric-contraction hot path on GB300 (one JSON line on rank 0).
 
 Default workload: the U(1) two-site effective-Hamiltonian application x' = L.x.W.W.R at
-D = 1024 (charges -16..16, n_q ~ exp(-q^2/72)), XXZ MPO, plain FP64 -- four pairwise
-contractions, each a fusion-tree permute of both operands, one grouped GEMM over the coupled
-sectors and the output permute.  A step is one application of the chain.
+D = 4096 (charges -16..16, n_q ~ exp(-q^2/72)), XXZ MPO -- four pairwise contractions, each a
+fusion-tree permute of both operands, one grouped GEMM over the coupled sectors and the output
+permute.  A step is one application of the chain.  `value` is the plain FP64 path; the same line
+carries the split-precision paths (Ozaki BF16 slices and 3xTF32 on tcgen05) on the same workload,
+the D = 1024 chain and the SU(2) L.x at reduced multiplicity 1024 as extra workloads, and the
+serving loop (10,000 mixed requests, p50 / p99).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--config NAME] [--gemm fp64|ozaki]
@@ -15,6 +18,7 @@ no collective on the data path): value = all ranks' block flops / max-over-ranks
 import argparse
 import json
 import os
+import resource
 import statistics
 import subprocess
 import sys
@@ -26,10 +30,12 @@ sys.path.insert(0, ROOT)
 METRIC = "symmetric contraction block-GFLOP/s (FP64 vs split-prec); serve p50/p99 ms"
 UNIT = "block-GFLOP/s"
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
-FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64, nominal
-# DRAM bytes (read + write) per k_gemm_f64 launch of the D = 1024 U(1) heff chain, mean of the four
-# launches of one application, from one ncu capture (profiles/k_gemm_f64_u1_heff_d1024_launches.md)
-K2_TRAFFIC_BYTES = {"c1_u1_heff_d1024": 7.41e6}
+DEFAULT_CONFIG = "c3_u1_heff_d4096"
+EXTRA_CONFIGS = ("c1_u1_heff_d1024", "c3_su2_lx_n1024")
+# DRAM bytes (read + write) per launch of the FP64 sector GEMM on the D = 4096 U(1) chain: the mean
+# over the four launches of one application, from one ncu capture of the current kernel (None
+# for workloads without a capture).
+K2_TRAFFIC_BYTES = {"c3_u1_heff_d4096": None}
 
 
 def _peaks():
@@ -131,15 +137,34 @@ def _workload(ctx, name, gemm, dtype="f64", seed=0):
     raise SystemExit(f"config {name} is a parity case, not a bench line")
 
 
-def _inputs_and_output(work):
+def _inputs(work):
     from paper_2508_10076_gb300.chain import HeffChain
     if isinstance(work, HeffChain):
-        return [work.dev[k] for k in ("x", "L", "W", "R")], (lambda: work.run())
-    return [work.dev[k] for k in ("L", "x")], (lambda: work.run())
+        return [work.dev[k] for k in ("x", "L", "W", "R")]
+    return [work.dev[k] for k in ("L", "x")]
 
 
-def cpu_baseline(name, budget_s=15.0):
-    """The oracle's block tier on the same workload, repeated for a bounded time on the host."""
+def _out_blocks(work):
+    return (work.steps[-1].out if hasattr(work, "steps") else work.step.out).blocks()
+
+
+def rel_err_per_block(blocks, got, ref):
+    """Largest per-block relative Frobenius difference (numpy arrays or tensors on the host)."""
+    import numpy as np
+    got, ref = np.asarray(got), np.asarray(ref)
+    total = max(float(np.linalg.norm(ref)), 1e-300)
+    worst = 0.0
+    for _, r, k, o in blocks:
+        d = float(np.linalg.norm(got[o:o + r * k] - ref[o:o + r * k]))
+        n = float(np.linalg.norm(ref[o:o + r * k]))
+        worst = max(worst, d / (n if n > 1e-13 * total else total))
+    return worst
+
+
+# ------------------------------------------------------------------------------------------ oracle
+def _oracle_run(name):
+    """A callable running the oracle's block tier on workload `name` (seed 0) and returning its
+    result's data."""
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from harness import oracle_heff, oracle_heff_inputs  # noqa: E402
     from oracle import ops  # noqa: E402
@@ -147,28 +172,70 @@ def cpu_baseline(name, budget_s=15.0):
     cfg = wl.CONFIGS[name]
     if cfg["kind"] in ("heff", "heff1"):
         sites = 2 if cfg["kind"] == "heff" else 1
-        run = lambda: oracle_heff(cfg["sym"], cfg["D"], tier="block", sites=sites, mpo=cfg.get("mpo"))  # noqa: E731
-        flops = None
-    else:
-        st, data = oracle_heff_inputs(cfg["sym"], cfg["D"])
-        run = lambda: ops.contract(st["L"], data["L"], *wl.LX_SPEC[:2], st["x"], data["x"],  # noqa: E731
-                                   *wl.LX_SPEC[2:], tier="block")
-        flops = None
-    run()  # warm caches of the oracle
-    n, t0 = 0, time.perf_counter()
+        return lambda: oracle_heff(cfg["sym"], cfg["D"], tier="block", sites=sites, mpo=cfg.get("mpo"))[-1][1]
+    st, data = oracle_heff_inputs(cfg["sym"], cfg["D"])
+    return lambda: ops.contract(st["L"], data["L"], *wl.LX_SPEC[:2], st["x"], data["x"], *wl.LX_SPEC[2:],
+                                tier="block")[1]
+
+
+def oracle_block_flops(name):
+    """Block flops of one step of workload `name` counted on the oracle's own structures: sum over
+    the coupled sectors of every contraction of 2 M K N, with M, K from the permuted A's block and
+    N from the permuted B's block (sectors with K = 0 cost nothing)."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from harness import ostruct  # noqa: E402
+    from oracle import TensorStructure  # noqa: E402
+    from oracle.ops import permute_spaces  # noqa: E402
+    from paper_2508_10076_gb300 import workloads as wl
+    cfg = wl.CONFIGS[name]
+    V, P, W = wl.heff_spaces(cfg["sym"], cfg["D"])
+    legs = wl.heff1_legs(V, P, W) if cfg["kind"] == "heff1" else wl.heff_legs(V, P, W)
+    st = {k: ostruct(cfg["sym"], legs[k]) for k in ("x", "L", "W", "R")}
+
+    def one(a, pa, qa, b, pb, qb, pab, qab):
+        at = TensorStructure(*permute_spaces(a, pa, qa))
+        bt = TensorStructure(*permute_spaces(b, pb, qb))
+        bb = {c: (r, k) for c, r, k, _ in bt.blocks}
+        flops = 0.0
+        for c, m, k, _ in at.blocks:
+            if c in bb and k > 0:
+                flops += 2.0 * m * k * bb[c][1]
+        ct = TensorStructure(at.cod, bt.dom)
+        return flops, TensorStructure(*permute_spaces(ct, pab, qab))
+
+    if cfg["kind"] == "lx":
+        return one(st["L"], *wl.LX_SPEC[:2], st["x"], *wl.LX_SPEC[2:])[0]
+    specs = wl.HEFF_SPECS if cfg["kind"] == "heff" else wl.HEFF1_SPECS
+    others = ("L", "W", "W", "R") if cfg["kind"] == "heff" else ("L", "W", "R")
+    total, cur = 0.0, st["x"]
+    for i, spec in enumerate(specs):
+        a, b = (st["L"], cur) if i == 0 else (cur, st[others[i]])
+        f, cur = one(a, *spec[:2], b, *spec[2:])
+        total += f
+    return total
+
+
+def cpu_baseline(name, budget_s=15.0):
+    """The oracle's block tier on the same workload, repeated for a bounded time on the host.
+    Returns (applications, wall seconds, effective cores = CPU seconds / wall seconds, BLAS
+    threads available, the oracle's result)."""
+    run = _oracle_run(name)
+    result = run()  # warm caches of the oracle; its result doubles as the error reference
+    r0, n, t0 = resource.getrusage(resource.RUSAGE_SELF), 0, time.perf_counter()
     while True:
         run()
         n += 1
         if time.perf_counter() - t0 >= budget_s or n >= 200:
             break
     dt = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
     try:
         from threadpoolctl import threadpool_info
-        cores = max((i.get("num_threads", 1) for i in threadpool_info()), default=os.cpu_count())
+        threads = max((i.get("num_threads", 1) for i in threadpool_info()), default=os.cpu_count())
     except Exception:
-        cores = os.cpu_count()
-    del flops
-    return n, dt, cores
+        threads = os.cpu_count()
+    return n, dt, cpu / dt, threads, result
 
 
 def cpu_baseline_single_thread(name, budget_s):
@@ -189,61 +256,132 @@ def cpu_baseline_single_thread(name, budget_s):
 
 
 def run_reference(args):
+    """The reference arm: the oracle's block tier (the paper's method written out plainly, on the
+    host cores), timed on the same workload, metric and unit; no GPU and no libtk."""
     world, rank, _ = _dist()
     if rank != 0:
         return
-    from paper_2508_10076_gb300 import workloads as wl
-    from paper_2508_10076_gb300.chain import HeffChain, LxContraction  # noqa: F401
-    # block flops per step from the host-only planner (no GPU work)
-    from paper_2508_10076_gb300 import api, build_library
-    build_library()
-    hctx = api.Context(-1)
-    flops = _host_flops(hctx, args.config)
-    per_step = max(1, int(round(args.budget / max(1, args.steps))))
-    times = []
+    flops = oracle_block_flops(args.config)
+    per_step = max(1.0, args.budget / max(1, args.steps))
     for _ in range(args.warmup):
         cpu_baseline(args.config, budget_s=0.0)
+    times, cores = [], []
     for _ in range(args.steps):
-        n, dt, cores = cpu_baseline(args.config, budget_s=per_step)
+        n, dt, eff, threads, _ = cpu_baseline(args.config, budget_s=per_step)
         times.append(dt / n)
+        cores.append(eff)
     ms = 1e3 * statistics.mean(times)
     value = flops / (ms * 1e-3) / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.config, "gemm": "fp64 (numpy BLAS)", "tier": "oracle block tier"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"whole {args.config} applications repeated for ~{per_step}s per step"},
+        "config": {"workload": args.config, "gemm": "fp64 (numpy BLAS)", "tier": "oracle block tier",
+                   "block_flops_per_step": flops, "flops_source": "the oracle's own structures"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": round(statistics.mean(cores), 1),
+                         "threads_available": threads, "kind": "oracle",
+                         "sample": f"whole {args.config} applications repeated for ~{per_step:.0f}s per step; "
+                                   "cores = CPU seconds / wall seconds"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def _host_flops(hctx, name):
-    from paper_2508_10076_gb300 import workloads as wl
-    from paper_2508_10076_gb300 import api
-    cfg = wl.CONFIGS[name]
-    V, P, W = wl.heff_spaces(cfg["sym"], cfg["D"])
-    legs = wl.heff_legs(V, P, W) if cfg["kind"] != "heff1" else wl.heff1_legs(V, P, W)
+# ------------------------------------------------------------------------------------------ GPU arm
+class Timer:
+    """K steps, the L2 flushed before each, CUDA events on the launching stream around each."""
 
-    def tm(k):
-        cod, dom = legs[k]
-        return hctx.tmap([hctx.space(cfg["sym"], s, d) for s, d in cod], [hctx.space(cfg["sym"], s, d) for s, d in dom])
+    def __init__(self, torch, stream, flush, barrier):
+        self.torch, self.stream, self.flush, self.barrier = torch, stream, flush, barrier
 
-    if cfg["kind"] == "lx":
-        return api.contract_plan(hctx, tm("L"), *wl.LX_SPEC[:2], tm("x"), *wl.LX_SPEC[2:]).flops
-    total, cur = 0.0, tm("x")
-    specs = wl.HEFF_SPECS if cfg["kind"] != "heff1" else wl.HEFF1_SPECS
-    others = ("L", "W", "W", "R") if cfg["kind"] != "heff1" else ("L", "W", "R")
-    for i, spec in enumerate(specs):
-        if i == 0:
-            pl = api.contract_plan(hctx, tm("L"), *spec[:2], cur, *spec[2:])
-        else:
-            pl = api.contract_plan(hctx, cur, *spec[:2], tm(others[i]), *spec[2:])
-        total += pl.flops
-        cur = pl.output()
-    return total
+    def __call__(self, fn, steps, clocks=None):
+        """Total ms of `steps` timed calls of fn; clocks (a Clocks) samples the timed region only."""
+        t = self.torch
+        starts = [t.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [t.cuda.Event(enable_timing=True) for _ in range(steps)]
+        self.barrier()
+        if clocks is not None:
+            clocks.start()
+        for i in range(steps):
+            self.flush.zero_()
+            starts[i].record(self.stream)
+            fn()
+            ends[i].record(self.stream)
+        self.barrier()
+        if clocks is not None:
+            self.clk = clocks.stop()
+        return sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+
+
+def measure(ctx, name, gemm, args, timer, rank, steps, want_graph=True, clocks=None):
+    """One workload in one GEMM mode: autotune, warm up, capture one step as a CUDA graph, time
+    `steps` replays, then the same loop eager with libtk's launch profiler on."""
+    work = _workload(ctx, name, gemm, seed=replica_seed(rank))
+    tuned = work.autotune() if not args.no_autotune else None  # before any graph capture
+    for _ in range(max(3, args.warmup)):
+        work.run()
+    ctx.sync()
+    step_fn, per_step_launches, mode, graph_out = work.run, None, "eager", None
+    if want_graph and not args.eager:
+        try:
+            graph, graph_out, per_step_launches = work.capture()
+            step_fn, mode = graph.replay, "cuda_graph"
+            for _ in range(max(3, args.warmup)):
+                step_fn()
+        except Exception as exc:  # keep the eager path; report why
+            step_fn, mode = work.run, f"eager (graph capture failed: {exc})"
+    timer.torch.cuda.synchronize()
+    launches0 = ctx.launches
+    total_ms = timer(step_fn, steps, clocks)
+    launches = ctx.launches - launches0 if per_step_launches is None else per_step_launches * steps
+    ctx.sync()
+    ctx.profile(True)
+    for _ in range(steps):
+        timer.flush.zero_()
+        work.run()
+    ctx.sync()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    out = (graph_out if graph_out is not None else work.run())
+    timer.torch.cuda.synchronize()
+    return dict(work=work, tuned=tuned, step_fn=step_fn, mode=mode, graph_out=graph_out, total_ms=total_ms,
+                launches=launches, prof=prof, out=out.clone())
+
+
+def kernels_table(prof, steps):
+    return {k: {"launches": c, "ms_per_step": ms / steps} for k, (c, ms) in prof.items()}
+
+
+def split_roofline(gemm, m, steps):
+    """Roofline of the split-precision GEMM launch: executed tensor flops (slice products x the
+    block flops routed to the tensor cores) / its event-measured time, against the BF16 peak."""
+    work, prof = m["work"], m["prof"]
+    kms = prof.get("k_oz_gemm", (0, 0.0))[1]
+    if kms <= 0 or work.tensor_flops <= 0:
+        return None
+    bf = _peaks().get("bf16_tflops")
+    if gemm == "ozaki":
+        products, peak, src = 21, bf, "measured bf16_tflops (burst)"
+    else:  # TF32 dense rate is half of BF16 on this part (nominal 1.1 vs 2.25 PFLOP/s)
+        products, peak, src = 3, (bf / 2 if bf else None), "measured bf16_tflops (burst) x 1/2 (nominal TF32:BF16)"
+    executed = products * work.tensor_flops * steps / (kms * 1e-3) / 1e12
+    return {"kernel": "k_oz_gemm", "bound": "tensor", "achieved": executed, "peak": peak, "unit": "TFLOP/s",
+            "frac": executed / peak if peak else None, "traffic": None, "peak_source": src,
+            "note": f"achieved = {products} products x tensor-path block flops / k_oz_gemm time"}
+
+
+def permute_roofline(work, prof, steps):
+    kms = prof.get("k_permute", (0, 0.0))[1]
+    if kms <= 0:
+        return None
+    peaks = _peaks()
+    pk = peaks.get("hbm_gbs", 6800.0)
+    achieved = work.permute_bytes * steps / (kms * 1e-3) / 1e9
+    return {"kernel": "k_permute", "bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
+            "frac": achieved / pk, "traffic": None,
+            "peak_source": "measured hbm_gbs" if "hbm_gbs" in peaks else "fallback",
+            "note": "algorithmic bytes (every source element read once per use, every output written once) "
+                    "/ k_permute time"}
 
 
 def run_ours(args):
@@ -259,9 +397,6 @@ def run_ours(args):
     from paper_2508_10076_gb300 import api, build_library
     build_library()
     ctx = api.Context(local)
-    work = _workload(ctx, args.config, args.gemm, seed=replica_seed(rank))
-    tuned = work.autotune() if not args.no_autotune else None  # before any graph capture
-    flops = work.flops
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -270,159 +405,102 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(max(3, args.warmup)):
-        work.run()
-    ctx.sync()
-    # one application as a CUDA graph (eager launches if capture is unavailable)
-    step_fn, per_step_launches, mode, graph_out = work.run, None, "eager", None
-    if not args.eager:
-        try:
-            graph, graph_out, per_step_launches = work.capture()
-            step_fn, mode = graph.replay, "cuda_graph"
-            for _ in range(max(3, args.warmup)):
-                step_fn()
-            torch.cuda.synchronize()
-        except Exception as exc:  # keep the eager path; report why
-            step_fn, mode = work.run, f"eager (graph capture failed: {exc})"
-    # ---------------- timed region: K steps, L2 flushed before each, events around each step
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = Clocks(local)
-    barrier()
-    clocks.start()
-    launches0 = ctx.launches
-    for i in range(args.steps):
-        flush.zero_()
-        starts[i].record(stream)
-        step_fn()
-        ends[i].record(stream)
-    barrier()
-    clk = clocks.stop()
-    launches = ctx.launches - launches0 if per_step_launches is None else per_step_launches * args.steps
-    ctx.sync()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    total_ms = max_over_ranks(dist, total_ms)
+    timer = Timer(torch, stream, flush, barrier)
+    # ---------------- the headline: FP64 on the default workload, clocks sampled
+    m = measure(ctx, args.config, args.gemm, args, timer, rank, args.steps, clocks=Clocks(local))
+    clk = timer.clk
+    work, prof = m["work"], m["prof"]
+    flops = work.flops
+    total_ms = max_over_ranks(dist, m["total_ms"])
     value = job_throughput(flops, args.steps, world, total_ms)
-    # ---------------- per-kernel event times: the same loop with libtk's launch profiler on
-    ctx.profile(True)
-    for i in range(args.steps):
-        flush.zero_()
-        work.run()
-    ctx.sync()
-    prof = ctx.profile_read()
-    ctx.profile(False)
-    # ---------------- end to end: pinned host inputs -> device -> chain -> host result (the chain
-    # replayed from its CUDA graph when captured: the graph reads the same input buffers)
-    ins, run = _inputs_and_output(work)
-    if graph_out is not None:
-        run = lambda: (step_fn(), graph_out)[1]  # noqa: E731
+    # ---------------- end to end: pinned host inputs -> device -> chain -> host result through the
+    # C ABI, captured as one graph when the device path is
+    ins = _inputs(work)
     host_in = [x.cpu().pin_memory() for x in ins]
-    out_dev = run()
-    host_out = torch.empty(out_dev.numel(), dtype=out_dev.dtype).pin_memory()
+    host_out = torch.empty(m["out"].numel(), dtype=m["out"].dtype).pin_memory()
     h2d = sum(x.numel() * x.element_size() for x in host_in)
     d2h = host_out.numel() * host_out.element_size()
-    e2e_step = None
     if hasattr(work, "run_host"):
-        # the chain's host-to-host call: W and R copied beside the first contraction
         host_map = dict(zip(("x", "L", "W", "R"), host_in))
         e2e_step = lambda: work.run_host(host_map, host_out)  # noqa: E731
-        if graph_out is not None:
+        if m["mode"] == "cuda_graph":
             from paper_2508_10076_gb300.chain import capture_graph
             e2e_graph, _, _ = capture_graph(ctx, e2e_step)
             e2e_step = e2e_graph.replay
-    e_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    e_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    barrier()
-    for i in range(args.steps):
-        flush.zero_()
-        e_start[i].record(stream)
-        if e2e_step is not None:
-            e2e_step()
-        else:
+    else:
+        def e2e_step():
             for hx, dx in zip(host_in, ins):
                 api.copy_h2d(ctx, dx, hx.data_ptr(), hx.numel() * hx.element_size(), stream)
-            out_dev = run()
-            api.copy_d2h(ctx, host_out.data_ptr(), out_dev, d2h, stream)
-        e_end[i].record(stream)
-    barrier()
+            out = work.run()
+            api.copy_d2h(ctx, host_out.data_ptr(), out, d2h, stream)
+    e2e_ms = max_over_ranks(dist, timer(e2e_step, args.steps))
     torch.cuda.synchronize()
-    if not torch.equal(host_out, out_dev.cpu() if e2e_step is None else run().cpu()):
+    if not torch.equal(host_out, m["out"].cpu()):
         raise RuntimeError("the end-to-end result differs from the device path's")
-    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_start, e_end))
-    e2e_ms = max_over_ranks(dist, e2e_ms)
     e2e_value = job_throughput(flops, args.steps, world, e2e_ms)
     ctx.sync()
-    # ---------------- split-precision variants of the same workload on tcgen05: Ozaki BF16 slices
-    # (s = 6, 21 slice pairs) and 3xTF32 (3 products, tensor rate half of BF16)
-    def split_variant(gemm, ref_out):
-        oz = _workload(ctx, args.config, gemm, seed=replica_seed(rank))
-        oz_tuned = oz.autotune() if not args.no_autotune else None
-        for _ in range(max(3, args.warmup)):
-            oz.run()
-        oz_fn = oz.run
-        if mode == "cuda_graph":
-            oz_graph, _, _ = oz.capture()
-            oz_fn = oz_graph.replay
-            for _ in range(max(3, args.warmup)):
-                oz_fn()
-        o_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        o_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        barrier()
-        for i in range(args.steps):
-            flush.zero_()
-            o_start[i].record(stream)
-            oz_fn()
-            o_end[i].record(stream)
-        barrier()
-        oz_ms = sum(s.elapsed_time(e) for s, e in zip(o_start, o_end))
-        oz_ms = max_over_ranks(dist, oz_ms)
-        oz_out = oz.run()
-        ctx.profile(True)
-        for i in range(args.steps):
-            flush.zero_()
-            oz.run()
-        ctx.sync()
-        oz_prof = ctx.profile_read()
-        ctx.profile(False)
-        out_blocks = (oz.steps[-1].out if hasattr(oz, "steps") else oz.step.out).blocks()
-        worst = 0.0
-        refn = float(torch.linalg.norm(ref_out))
-        for _, r_, k_, o_ in out_blocks:
-            d = float(torch.linalg.norm(oz_out[o_:o_ + r_ * k_] - ref_out[o_:o_ + r_ * k_]))
-            n_ = float(torch.linalg.norm(ref_out[o_:o_ + r_ * k_]))
-            worst = max(worst, d / (n_ if n_ > 1e-13 * refn else refn))
-        oz_kms = oz_prof.get("k_oz_gemm", (0, 0.0))[1]
-        if gemm == "ozaki":
-            products, peak, peak_key = 21, _peaks().get("bf16_tflops"), "measured bf16_tflops (burst)"
-        else:  # TF32 dense rate is half of BF16 on this part (nominal 1.1 vs 2.25 PFLOP/s)
-            bf = _peaks().get("bf16_tflops")
-            products, peak, peak_key = 3, (bf / 2 if bf else None), "measured bf16_tflops (burst) x 1/2 (nominal TF32:BF16)"
-        roof = None
-        if oz_kms > 0 and oz.tensor_flops > 0:
-            executed = products * oz.tensor_flops * args.steps / (oz_kms * 1e-3) / 1e12
-            roof = {"kernel": "k_oz_gemm", "bound": "tensor", "achieved": executed, "peak": peak,
-                    "unit": "TFLOP/s", "frac": executed / peak if peak else None, "traffic": None,
-                    "peak_source": peak_key,
-                    "note": f"achieved = {products} products x tensor-path block flops / k_oz_gemm time"}
-        return {"value": job_throughput(flops, args.steps, world, oz_ms), "unit": UNIT,
-                "ms_per_step": oz_ms / args.steps, "roofline": roof, "autotune": oz_tuned,
-                "tensor_path_flops_per_step": oz.tensor_flops,
-                "rel_frobenius_per_block_vs_fp64_path": worst,
-                "kernels": {k: {"launches": c, "ms_per_step": ms / args.steps} for k, (c, ms) in oz_prof.items()}}
-
-    split = tf32 = None
+    # ---------------- roofline of the dominant kernel; FP64 peak measured on this GPU now
+    fp64_peak, fp64_probe_ms = api.probe_fp64_peak(ctx, seconds=1.0)
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (0, 0.0))
+    kname, (kcount, kms) = dom
+    if kname == "k_gemm_f64":
+        achieved = flops * args.steps / (kms * 1e-3) / 1e12
+        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak,
+                "traffic": K2_TRAFFIC_BYTES.get(args.config) if not args.eager else None,
+                "traffic_note": "DRAM bytes per launch (ncu, mean of one application's launches)",
+                "peak_source": f"measured in this run: register-only FP64 FMA loop on every SM "
+                               f"(tk_probe_fp64_peak, {fp64_probe_ms:.0f} ms)"}
+    elif kname == "k_permute":
+        roof = permute_roofline(work, prof, args.steps)
+    else:
+        roof = split_roofline(args.gemm, m, args.steps)
+    # ---------------- split-precision variants of the same workload: Ozaki BF16 (s = 6, 21 slice
+    # pairs) and 3xTF32 (3 products); error against the FP64 path's output
+    variants = {}
     if not args.no_split:
-        ref_out = run().clone()
-        split = split_variant("ozaki", ref_out)
-        split["slices"] = 6
-        tf32 = split_variant("tf32x3", ref_out)
+        for gemm in ("ozaki", "tf32x3"):
+            v = measure(ctx, args.config, gemm, args, timer, rank, args.steps)
+            v_ms = max_over_ranks(dist, v["total_ms"])
+            variants[gemm] = {
+                "value": job_throughput(flops, args.steps, world, v_ms), "unit": UNIT,
+                "ms_per_step": v_ms / args.steps, "roofline": split_roofline(gemm, v, args.steps),
+                "autotune": v["tuned"], "tensor_path_flops_per_step": v["work"].tensor_flops,
+                "gpu_launches_per_step": v["launches"] / args.steps,
+                "rel_frobenius_per_block_vs_fp64_path": rel_err_per_block(
+                    _out_blocks(v["work"]), v["out"].cpu().numpy(), m["out"].cpu().numpy()),
+                "kernels": kernels_table(v["prof"], args.steps), "out": v["out"]}
+            if gemm == "ozaki":
+                variants[gemm]["slices"] = 6
+    # ---------------- the other configurations named by the metric (fewer steps)
+    extra = {}
+    if not args.no_extra:
+        for name in EXTRA_CONFIGS:
+            if name == args.config:
+                continue
+            row = {}
+            ref_out = None
+            for gemm in ("fp64", "ozaki", "tf32x3"):
+                e = measure(ctx, name, gemm, args, timer, rank, args.extra_steps)
+                e_ms = max_over_ranks(dist, e["total_ms"])
+                row[gemm] = {"value": job_throughput(e["work"].flops, args.extra_steps, world, e_ms),
+                             "ms_per_step": e_ms / args.extra_steps}
+                if gemm == "fp64":
+                    ref_out = e["out"]
+                    row["block_flops_per_step"] = e["work"].flops
+                    row["permute_roofline"] = permute_roofline(e["work"], e["prof"], args.extra_steps)
+                else:
+                    row[gemm]["rel_frobenius_per_block_vs_fp64_path"] = rel_err_per_block(
+                        _out_blocks(e["work"]), e["out"].cpu().numpy(), ref_out.cpu().numpy())
+                    row[gemm]["roofline"] = split_roofline(gemm, e, args.extra_steps)
+            extra[name] = row
     # ---------------- serving: Poisson stream of mixed requests through the continuous-batching loop
     serve = None
     if args.serve_requests > 0:
         from paper_2508_10076_gb300.serve import Server, calibrated_rate, request_stream
         reqs = request_stream(args.serve_requests, seed=1000 + replica_seed(rank))
-        server = Server(ctx, budget_bytes=150 << 30, split_gemm=None if args.serve_fp64 else "ozaki")
+        serve_ctx = api.Context(local)  # its own context: the 150 GB budget covers the server alone
+        server = Server(serve_ctx, budget_bytes=150 << 30, split_gemm=None if args.serve_fp64 else "ozaki")
         for r in reqs:
             server.shape(r["sym"], r["D"], r["dtype"])
         rate, mean_s = calibrated_rate(server, reqs, load=args.serve_load)
@@ -430,68 +508,67 @@ def run_ours(args):
         _, serve, _ = server.run(reqs, rate)
         serve["p99_ms"] = max_over_ranks(dist, serve["p99_ms"])
         solo = sorted(k for k, sh in server.shapes.items() if sh.solo)
+        mem = serve_ctx.memory()
         serve.update({"precision": "FP64 (complex128) in packed batches; shapes whose FP64 service alone is >= 1 ms and "
                       "faster in Ozaki BF16 (s = 6, <= 1e-10) are served one by one in that mode"
                       if not args.serve_fp64 else "FP64 (complex128) in packed batches",
-                      "split_precision_shapes": len(solo), "shapes": len(server.shapes)})
+                      "split_precision_shapes": len(solo), "shapes": len(server.shapes),
+                      "plans": "autotuned once per shape before the timed loop",
+                      "budget_gb": 150, "resident_gb": (mem["library_bytes"] + mem["reserved_bytes"]) / 2**30,
+                      "budget_counts": "plan tables held by libtk + resident inputs (reserved) + in-flight "
+                                       "outputs and workspaces (reserved at admission)"})
         serve.update({"load": args.serve_load, "mean_service_ms_alone": 1e3 * mean_s,
-                      "budget_gb": 150, "mix": "U(1) L.x at D / SU(2) L.x at D/4, D log-uniform 64-4096 "
+                      "mix": "U(1) L.x at D / SU(2) L.x at D/4, D log-uniform 64-4096 "
                       "(25-level grid), half complex128, Poisson arrivals"})
+        server.close()
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    # ---------------- roofline of the dominant kernel
-    peaks = _peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (0, 0.0))
-    kname, (kcount, kms) = dom
-    permute_bytes = work.permute_bytes
-    if kname == "k_gemm_f64":
-        achieved = flops * args.steps / (kms * 1e-3) / 1e12
-        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS / 1e3,
-                "unit": "TFLOP/s", "frac": achieved / (FP64_NOMINAL_GFLOPS / 1e3),
-                "traffic": K2_TRAFFIC_BYTES.get(args.config) if not args.eager else None,
-                "traffic_note": "DRAM bytes per launch (ncu); operands read once, outputs written back after the launch",
-                "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s); no FP64 figure in MEASURED_PEAKS.json"}
-    elif kname == "k_permute":
-        achieved = permute_bytes * args.steps / (kms * 1e-3) / 1e9
-        pk = peaks.get("hbm_gbs", 6800.0)
-        roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
-                "frac": achieved / pk, "traffic": None, "peak_source": "measured hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
-    else:
-        roof = {"kernel": kname, "bound": "tensor", "achieved": None, "peak": peaks.get("bf16_tflops"),
-                "unit": "TFLOP/s", "frac": None, "traffic": None}
-    kernels = {k: {"launches": c, "ms_per_step": ms / args.steps} for k, (c, ms) in prof.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.config, "gemm": args.gemm, "block_flops_per_step": flops,
-                   "permute_bytes_per_step": permute_bytes, "l2": "flushed (512 MB write) before every timed step",
-                   "launch": mode, "autotune": tuned,
+                   "permute_bytes_per_step": work.permute_bytes,
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "launch": m["mode"], "autotune": m["tuned"],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches,
+        "gpu_launches": m["launches"],
         "roofline": roof,
-        "kernels": kernels,
+        "roofline_permute": permute_roofline(work, prof, args.steps),
+        "fp64_peak_probe": {"tflops": fp64_peak, "ms": fp64_probe_ms,
+                            "how": "register-only FP64 FMA loop, 16 independent chains per thread, 8 CTAs x 256 "
+                                   "threads per SM, CUDA events"},
+        "kernels": kernels_table(prof, args.steps),
     }
-    if split is not None:
-        line["split_precision"] = split
-    if tf32 is not None:
-        line["split_precision_tf32x3"] = tf32
+    if "ozaki" in variants:
+        line["split_precision"] = {k: v for k, v in variants["ozaki"].items() if k != "out"}
+    if "tf32x3" in variants:
+        line["split_precision_tf32x3"] = {k: v for k, v in variants["tf32x3"].items() if k != "out"}
+    if extra:
+        line["extra_workloads"] = extra
     if serve is not None:
         line["serve"] = serve
     if world == 1 and not args.no_cpu_baseline:
-        n, dt, cores = cpu_baseline(args.config, budget_s=args.cpu_budget)
-        line["cpu_baseline"] = {"value": flops * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+        n, dt, eff, threads, oracle_out = cpu_baseline(args.config, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": flops * n / dt / 1e9, "unit": UNIT, "cores": round(eff, 1),
+                                "threads_available": threads, "kind": "oracle",
                                 "sample": f"{n} whole applications of {args.config} by the oracle block tier "
-                                          f"({dt:.1f} s)"}
+                                          f"({dt:.1f} s); cores = CPU seconds / wall seconds (BLAS threads "
+                                          f"in the large sector products, the rest one Python thread)"}
         n1, dt1 = cpu_baseline_single_thread(args.config, budget_s=min(args.cpu_budget, 10.0))
         line["cpu_baseline_single_thread"] = {
             "value": flops * n1 / dt1 / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n1} whole applications of {args.config} by the oracle block tier in a process with "
                       f"one BLAS / OpenMP thread ({dt1:.1f} s)"}
+        # every result of the line against the FP64 oracle (seed 0 inputs, rank 0)
+        blocks = _out_blocks(work)
+        line["rel_frobenius_per_block_vs_oracle"] = {
+            "fp64": rel_err_per_block(blocks, m["out"].cpu().numpy(), oracle_out),
+            **{g: rel_err_per_block(blocks, v["out"].cpu().numpy(), oracle_out) for g, v in variants.items()}}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -503,12 +580,14 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c1_u1_heff_d1024")
+    ap.add_argument("--config", default=DEFAULT_CONFIG)
     ap.add_argument("--gemm", default="fp64", choices=["fp64", "ozaki"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--budget", type=float, default=60.0, help="reference arm: total CPU seconds")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-split", action="store_true", help="skip the split-precision variant")
+    ap.add_argument("--no-split", action="store_true", help="skip the split-precision variants")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads")
+    ap.add_argument("--extra-steps", type=int, default=10)
     ap.add_argument("--eager", action="store_true", help="launch kernels one by one instead of a CUDA graph")
     ap.add_argument("--serve-requests", type=int, default=10000, help="serving requests (0: skip serving)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic work lists")
@@ -517,7 +596,7 @@ def main():
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)  # single-thread baseline process
     args = ap.parse_args()
     if args.cpu_worker:
-        n, dt, _ = cpu_baseline(args.config, budget_s=args.cpu_budget)
+        n, dt, _, _, _ = cpu_baseline(args.config, budget_s=args.cpu_budget)
         print(json.dumps({"n": n, "dt": dt}), flush=True)
         return
     if args.impl == "reference":

@@ -23,9 +23,7 @@ def main():
     slowest = bench.max_over_ranks(dist, 10.0 + 3.0 * rank)
     seeds = [None] * world
     dist.all_gather_object(seeds, bench.replica_seed(rank))
-    from paper_2508_10076_gb300 import api
-    hctx = api.Context(-1)
-    flops = bench._host_flops(hctx, "c1_u1_heff_d1024")
+    flops = bench.oracle_block_flops("c1_u1_heff_d1024")
     all_flops = [None] * world
     dist.all_gather_object(all_flops, flops)
     from paper_2508_10076_gb300.chain import HeffChain  # noqa: F401  (import only: no device here)
