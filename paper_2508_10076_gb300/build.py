@@ -79,7 +79,7 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + [
-        "-cudart", "shared", "-lcusolver", "-Xlinker", "-rpath," + os.path.join(CUDA_HOME, "lib64")]
+        "-cudart", "shared", "-Xlinker", "-rpath," + os.path.join(CUDA_HOME, "lib64")]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"linking libtk.so failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

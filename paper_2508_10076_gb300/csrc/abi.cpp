@@ -130,7 +130,6 @@ void tk_ctx_destroy(tk_ctx* ctx) {
     cudaSetDevice(ctx->c.device);
     ctx->c.perm_cache.clear();
     ctx->c.contract_cache.clear();
-    tk::destroy_solver_handle(&ctx->c);
     tk::dev_free(ctx->c.d_status);
     if (ctx->c.side) cudaStreamDestroy((cudaStream_t)ctx->c.side);
     if (ctx->c.ev_fork) cudaEventDestroy((cudaEvent_t)ctx->c.ev_fork);

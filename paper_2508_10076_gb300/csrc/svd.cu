@@ -5,40 +5,214 @@
 // columns: fusion trees of dom).  With orthonormal canonical trees the SVD of t is the SVD of
 // each block: t = U S V^dagger with the bond space W = sum_c (c, r_c), r_c = min(rows_c, cols_c),
 // U : cod <- W (block c: rows_c x r_c), S diagonal on W and V^dagger : W <- dom (block c:
-// r_c x cols_c).  Each block is factorised by cuSOLVER's Jacobi SVD (gesvdj, economy size) on a
-// copy in the caller's workspace; V is turned into V^dagger by a transpose kernel (conjugating
-// complex data).  Truncation keeps, per sector, the leading k_c <= r_c singular triplets: the
-// first k_c columns of U's block (a contiguous prefix, column-major) and the first k_c rows of
-// V^dagger's block (a strided 2-D copy).
+// r_c x cols_c).
+//
+// All blocks are factorised in one launch, one CTA per block, by one-sided Jacobi (Hestenes):
+// the columns of a working copy G (the block, or its adjoint when it has fewer rows than columns,
+// so that G is M x N with M >= N) are made mutually orthogonal by plane rotations, which are
+// accumulated in an N x N matrix Q (G_final = G_0 Q).  Then the singular values are the column
+// norms of G_final, its normalised columns are the left vectors of G_0 and Q holds the right
+// vectors.  A sweep visits every column pair once, in the round-robin (circle) order: each round
+// is N/2 disjoint pairs, one per warp, so the rounds of a sweep need no other synchronisation
+// than a CTA barrier between them.  A pair (i, j) with Gram entries a = |g_i|^2, b = |g_j|^2,
+// g = g_i^H g_j is rotated when |g| > tol sqrt(a b), tol = sqrt(M) eps: with g = |g| e^{i phi},
+// the phase e^{-i phi} on column j makes the 2 x 2 Gram matrix real, and the Jacobi rotation
+// [[c, s], [-s, c]] with t = s / c = sign(z) / (|z| + sqrt(1 + z^2)), z = (b - a) / (2 |g|)
+// diagonalises it.  The sweeps stop when a sweep rotates no pair (or after kMaxSweeps).
+// Singular values are then ordered descending within the block by rank counting.
+//
+// Truncation keeps, per sector, the leading k_c <= r_c singular triplets: the first k_c columns
+// of U's block (a contiguous prefix, column-major) and the first k_c rows of V^dagger's block (a
+// strided 2-D copy).
 #include <cuda_runtime.h>
-#include <cusolverDn.h>
 
 #include <algorithm>
 #include <cstring>
 
+#include "tk_device.cuh"
 #include "tk_internal.hpp"
 
 namespace tk {
 
-SvdPlan::~SvdPlan() = default;
+SvdPlan::~SvdPlan() { dev_free(d_jobs); }
 
-void* solver_handle(Ctx* ctx) {
-  if (!ctx || ctx->device < 0) return nullptr;
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  if (!ctx->solver) {
-    cusolverDnHandle_t h = nullptr;
-    if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) return nullptr;
-    ctx->solver = h;
-  }
-  return ctx->solver;
+namespace {
+
+constexpr int kSvdThreads = 512;  // 16 warps: 16 column pairs rotated at a time
+constexpr int kMaxSweeps = 60;
+
+struct SvdJob {       // one block's factorisation, device side
+  int64_t m, n;       // block rows, columns
+  int64_t a_off, u_off, vh_off, s_off;
+  int64_t g_off, q_off, norm_off;  // working arrays in the workspace (elements of T / doubles)
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// scalar helpers for double and interleaved complex double
+__device__ __forceinline__ double cj(double x) { return x; }
+__device__ __forceinline__ double2 cj(double2 x) { return make_double2(x.x, -x.y); }
+__device__ __forceinline__ double abs2(double x) { return x * x; }
+__device__ __forceinline__ double abs2(double2 x) { return x.x * x.x + x.y * x.y; }
+// x^H y accumulated into acc
+__device__ __forceinline__ void dot_acc(double& acc, double x, double y) { acc = fma(x, y, acc); }
+__device__ __forceinline__ void dot_acc(double2& acc, double2 x, double2 y) {
+  acc.x = fma(x.x, y.x, fma(x.y, y.y, acc.x));
+  acc.y = fma(x.x, y.y, fma(-x.y, y.x, acc.y));
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double2 warp_sum(double2 v) { return make_double2(warp_sum(v.x), warp_sum(v.y)); }
+__device__ __forceinline__ double mag(double g) { return fabs(g); }
+__device__ __forceinline__ double mag(double2 g) { return hypot(g.x, g.y); }
+// e^{-i phi} for g = |g| e^{i phi} (|g| > 0)
+__device__ __forceinline__ double unit_conj_phase(double g, double) { return g >= 0.0 ? 1.0 : -1.0; }
+__device__ __forceinline__ double2 unit_conj_phase(double2 g, double ag) { return make_double2(g.x / ag, -g.y / ag); }
+__device__ __forceinline__ double mul(double a, double b) { return a * b; }
+__device__ __forceinline__ double2 mul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double scale(double a, double s) { return a * s; }
+__device__ __forceinline__ double2 scale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ T zero_of();
+template <>
+__device__ __forceinline__ double zero_of<double>() { return 0.0; }
+template <>
+__device__ __forceinline__ double2 zero_of<double2>() { return make_double2(0.0, 0.0); }
+template <typename T>
+__device__ __forceinline__ T one_of();
+template <>
+__device__ __forceinline__ double one_of<double>() { return 1.0; }
+template <>
+__device__ __forceinline__ double2 one_of<double2>() { return make_double2(1.0, 0.0); }
+
+// Column p of the round-robin schedule in round r (positions 0 .. np-1, np even): position 0 is
+// fixed, the others rotate; pair k of round r is (pos(k), pos(np - 1 - k)).
+__device__ __forceinline__ int64_t rr_column(int64_t pos, int64_t r, int64_t np) {
+  return pos == 0 ? 0 : ((pos - 1 + r) % (np - 1)) + 1;
 }
 
-void destroy_solver_handle(Ctx* ctx) {
-  if (ctx && ctx->solver) {
-    cusolverDnDestroy((cusolverDnHandle_t)ctx->solver);
-    ctx->solver = nullptr;
+template <typename T>
+__global__ void __launch_bounds__(kSvdThreads) k_svd_jacobi(const SvdJob* __restrict__ jobs, const T* __restrict__ a,
+                                                            T* __restrict__ u, double* __restrict__ s,
+                                                            T* __restrict__ vh, T* __restrict__ ws,
+                                                            double* __restrict__ wsd) {
+  const SvdJob jb = jobs[blockIdx.x];
+  const bool tall = jb.m >= jb.n;
+  const int64_t M = tall ? jb.m : jb.n, N = tall ? jb.n : jb.m;  // G is M x N, M >= N
+  T* G = ws + jb.g_off;
+  T* Q = ws + jb.q_off;
+  double* nrm = wsd + jb.norm_off;
+  const T* A = a + jb.a_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kSvdThreads / 32;
+  // G = A (tall) or A^H (wide); Q = identity
+  for (int64_t e = tid; e < M * N; e += kSvdThreads) {
+    const int64_t i = e % M, j = e / M;
+    G[e] = tall ? A[i + j * jb.m] : cj(A[j + i * jb.m]);
+  }
+  for (int64_t e = tid; e < N * N; e += kSvdThreads) Q[e] = (e % N == e / N) ? one_of<T>() : zero_of<T>();
+  __syncthreads();
+  const double tol = sqrt((double)M) * 2.220446049250313e-16;
+  const int64_t np = N + (N & 1);  // even number of positions (an odd N has one idle position)
+  __shared__ int rotated;
+  for (int sweep = 0; sweep < kMaxSweeps && N > 1; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    bool any = false;
+    for (int64_t r = 0; r < np - 1; ++r) {
+      for (int64_t k = warp; k < np / 2; k += nwarps) {
+        int64_t i = rr_column(k, r, np), j = rr_column(np - 1 - k, r, np);
+        if (i > j) {
+          const int64_t t = i;
+          i = j;
+          j = t;
+        }
+        if (j >= N) continue;  // the idle position of an odd N
+        T* gi = G + i * M;
+        T* gj = G + j * M;
+        double al = 0.0, be = 0.0;
+        T ga = zero_of<T>();
+        for (int64_t e = lane; e < M; e += 32) {
+          const T x = gi[e], y = gj[e];
+          al += abs2(x);
+          be += abs2(y);
+          dot_acc(ga, x, y);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        const double ag = mag(ga);
+        if (!(ag > tol * sqrt(al * be))) continue;  // already orthogonal to working precision
+        any = true;
+        const double z = (be - al) / (2.0 * ag);
+        const double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
+        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        const T ph = unit_conj_phase(ga, ag);  // e^{-i phi}
+        for (int64_t e = lane; e < M; e += 32) {
+          const T x = gi[e], y = mul(gj[e], ph);
+          gi[e] = add(scale(x, c), scale(y, -sn));
+          gj[e] = add(scale(x, sn), scale(y, c));
+        }
+        T* qi = Q + i * N;
+        T* qj = Q + j * N;
+        for (int64_t e = lane; e < N; e += 32) {
+          const T x = qi[e], y = mul(qj[e], ph);
+          qi[e] = add(scale(x, c), scale(y, -sn));
+          qj[e] = add(scale(x, sn), scale(y, c));
+        }
+      }
+      __syncthreads();
+    }
+    if (any && lane == 0) atomicOr(&rotated, 1);
+    __syncthreads();
+    if (!rotated) break;
+    __syncthreads();
+  }
+  // singular values: column norms of G, ordered descending (ties by column index)
+  for (int64_t j = warp; j < N; j += nwarps) {
+    double acc = 0.0;
+    for (int64_t e = lane; e < M; e += 32) acc += abs2(G[e + j * M]);
+    acc = warp_sum(acc);
+    if (lane == 0) nrm[j] = sqrt(acc);
+  }
+  __syncthreads();
+  const int64_t r = N;  // = min(m, n)
+  for (int64_t j = tid; j < N; j += kSvdThreads) {
+    const double sj = nrm[j];
+    int64_t rank = 0;
+    for (int64_t k = 0; k < N; ++k) {
+      const double sk = nrm[k];
+      rank += (sk > sj || (sk == sj && k < j)) ? 1 : 0;
+    }
+    s[jb.s_off + rank] = sj;
+    nrm[N + j] = (double)rank;  // the column's place in the output
+  }
+  __syncthreads();
+  T* U = u + jb.u_off;   // m x r
+  T* VH = vh + jb.vh_off;  // r x n
+  for (int64_t e = tid; e < M * N; e += kSvdThreads) {
+    const int64_t i = e % M, j = e / M;
+    const int64_t rk = (int64_t)nrm[N + j];
+    const double sj = nrm[j];
+    const T g = sj > 0.0 ? scale(G[e], 1.0 / sj) : G[e];
+    if (tall) U[i + rk * jb.m] = g;      // left vectors of A
+    else VH[rk + i * r] = cj(g);         // G = A^H: its left vectors are A's right vectors
+  }
+  for (int64_t e = tid; e < N * N; e += kSvdThreads) {
+    const int64_t i = e % N, j = e / N;
+    const int64_t rk = (int64_t)nrm[N + j];
+    if (tall) VH[rk + i * r] = cj(Q[e]);  // V^dagger row rk = (column j of Q)^H
+    else U[i + rk * jb.m] = Q[e];
   }
 }
+
+}  // namespace
 
 std::shared_ptr<SvdPlan> make_svd_plan(Ctx* ctx, std::shared_ptr<Structure> in, int dtype) {
   auto sp = std::make_shared<SvdPlan>();
@@ -57,7 +231,7 @@ std::shared_ptr<SvdPlan> make_svd_plan(Ctx* ctx, std::shared_ptr<Structure> in, 
   sp->bond = w;
   sp->u = build_structure(in->sym, in->cod, {w});
   sp->vh = build_structure(in->sym, {w}, in->dom);
-  int64_t s_off = 0, amax = 0;
+  int64_t s_off = 0;
   for (const Block& b : in->blocks) {
     const int64_t r = std::min(b.rows, b.cols);
     if (r == 0) continue;
@@ -71,116 +245,59 @@ std::shared_ptr<SvdPlan> make_svd_plan(Ctx* ctx, std::shared_ptr<Structure> in, 
     k.vh_off = sp->vh->blocks[sp->vh->block_of(b.c)].offset;
     k.s_off = s_off;
     s_off += r;
-    amax = std::max(amax, b.rows * b.cols + b.cols * r);  // A copy + V (n x r)
     sp->blocks.push_back(k);
   }
   sp->nvalues = s_off;
-  // workspace: the largest block's A copy and V, then the solver's work array and info word
+  // workspace: per block G (M x N) and Q (N x N) in the element type, then 2 N doubles (norms and
+  // output ranks); largest blocks first in the job list so they start first
   const size_t es = dtype == TK_C128 ? 16 : 8;
-  sp->ws_solver = ((size_t)amax * es + 255) & ~(size_t)255;
-  sp->lwork = 0;
-  if (ctx && ctx->device >= 0 && !sp->blocks.empty()) {
-    cusolverDnHandle_t h = (cusolverDnHandle_t)solver_handle(ctx);
-    if (!h) throw Error{TK_ERR_CUDA, "cusolverDnCreate failed"};
-    gesvdjInfo_t params;
-    if (cusolverDnCreateGesvdjInfo(&params) != CUSOLVER_STATUS_SUCCESS) throw Error{TK_ERR_CUDA, "gesvdj info"};
-    for (const SvdBlock& k : sp->blocks) {
-      int lw = 0;
-      cusolverStatus_t st;
-      if (dtype == TK_C128)
-        st = cusolverDnZgesvdj_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, 1, (int)k.m, (int)k.n, nullptr, (int)k.m,
-                                          nullptr, nullptr, (int)k.m, nullptr, (int)k.n, &lw, params);
-      else
-        st = cusolverDnDgesvdj_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, 1, (int)k.m, (int)k.n, nullptr, (int)k.m,
-                                          nullptr, nullptr, (int)k.m, nullptr, (int)k.n, &lw, params);
-      if (st != CUSOLVER_STATUS_SUCCESS) {
-        cusolverDnDestroyGesvdjInfo(params);
-        throw Error{TK_ERR_CUDA, "gesvdj buffer size query failed"};
-      }
-      sp->lwork = std::max<int64_t>(sp->lwork, lw);
-    }
-    cusolverDnDestroyGesvdjInfo(params);
+  std::vector<SvdJob> jobs;
+  int64_t elems = 0, dbl = 0;
+  std::vector<size_t> order(sp->blocks.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+    const SvdBlock &p = sp->blocks[x], &q = sp->blocks[y];
+    return p.m * p.n * p.r > q.m * q.n * q.r;
+  });
+  for (size_t i : order) {
+    const SvdBlock& k = sp->blocks[i];
+    const int64_t M = std::max(k.m, k.n), N = std::min(k.m, k.n);
+    SvdJob j{k.m, k.n, k.a_off, k.u_off, k.vh_off, k.s_off, elems, elems + M * N, dbl};
+    elems += M * N + N * N;
+    dbl += 2 * N;
+    jobs.push_back(j);
   }
-  sp->ws_total = sp->ws_solver + (((size_t)sp->lwork * es + 255) & ~(size_t)255) + 256;
+  sp->ws_solver = align256((size_t)elems * es);          // G and Q of every block
+  sp->lwork = dbl;
+  sp->ws_total = sp->ws_solver + align256((size_t)dbl * 8);
+  sp->d_jobs = nullptr;
+  sp->njobs = (int64_t)jobs.size();
+  if (ctx && ctx->device >= 0 && !jobs.empty()) {
+    int rc = dev_upload(ctx, &sp->d_jobs, jobs.data(), jobs.size() * sizeof(SvdJob));
+    if (rc != TK_OK) throw Error{rc, "uploading the SVD job table failed"};
+  }
   return sp;
 }
 
-namespace {
-
-// V (n x r, column-major) -> V^dagger (r x n, column-major), conjugated for complex data.
-template <typename T>
-__global__ void k_adjoint_copy(const T* __restrict__ v, T* __restrict__ vh, int64_t n, int64_t r) {
-  __shared__ T tile[32][33];
-  const int64_t bi = blockIdx.x * 32, bj = blockIdx.y * 32;  // bi over n, bj over r
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  for (int y = ty; y < 32; y += 8) {
-    const int64_t i = bi + tx, j = bj + y;
-    if (i < n && j < r) tile[y][tx] = v[i + j * n];
-  }
-  __syncthreads();
-  for (int y = ty; y < 32; y += 8) {
-    const int64_t j = bj + tx, i = bi + y;
-    if (i < n && j < r) {
-      T x = tile[tx][y];
-      if constexpr (sizeof(T) == 16) x.y = -x.y;
-      vh[j + i * r] = x;
-    }
-  }
-}
-
-}  // namespace
-
 int run_svd(Ctx* ctx, const SvdPlan& sp, const void* a, void* u, double* s, void* vh, void* ws, void* stream) {
-  if (sp.blocks.empty()) return TK_OK;
+  if (sp.njobs == 0) return TK_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  cusolverDnHandle_t h = (cusolverDnHandle_t)solver_handle(ctx);
-  if (!h || cusolverDnSetStream(h, st) != CUSOLVER_STATUS_SUCCESS) {
-    ctx->last_error = "cuSOLVER handle unavailable";
+  double* wsd = (double*)((char*)ws + sp.ws_solver);
+  {
+    ProfScope prof(ctx, "k_svd_jacobi", stream);
+    if (sp.dtype == TK_C128)
+      k_svd_jacobi<double2><<<(unsigned)sp.njobs, kSvdThreads, 0, st>>>(
+          (const SvdJob*)sp.d_jobs, (const double2*)a, (double2*)u, s, (double2*)vh, (double2*)ws, wsd);
+    else
+      k_svd_jacobi<double><<<(unsigned)sp.njobs, kSvdThreads, 0, st>>>(
+          (const SvdJob*)sp.d_jobs, (const double*)a, (double*)u, s, (double*)vh, (double*)ws, wsd);
+  }
+  if (cudaGetLastError() != cudaSuccess) {
+    ctx->last_error = "block SVD launch failed";
     return TK_ERR_CUDA;
   }
-  gesvdjInfo_t params;
-  if (cusolverDnCreateGesvdjInfo(&params) != CUSOLVER_STATUS_SUCCESS) return TK_ERR_CUDA;
-  const size_t es = sp.dtype == TK_C128 ? 16 : 8;
-  char* w = (char*)ws;
-  void* acopy = w;
-  void* work = w + sp.ws_solver;
-  int* info = (int*)(w + sp.ws_total - 256);
-  int rc = TK_OK;
-  ProfScope prof(ctx, "svd_gesvdj", stream);
-  for (const SvdBlock& k : sp.blocks) {
-    char* vbuf = (char*)acopy + (size_t)k.m * k.n * es;  // V (n x r) after the A copy
-    if (cudaMemcpyAsync(acopy, (const char*)a + (size_t)k.a_off * es, (size_t)k.m * k.n * es, cudaMemcpyDeviceToDevice,
-                        st) != cudaSuccess) {
-      rc = TK_ERR_CUDA;
-      break;
-    }
-    cusolverStatus_t cs;
-    if (sp.dtype == TK_C128)
-      cs = cusolverDnZgesvdj(h, CUSOLVER_EIG_MODE_VECTOR, 1, (int)k.m, (int)k.n, (cuDoubleComplex*)acopy, (int)k.m,
-                             s + k.s_off, (cuDoubleComplex*)u + k.u_off, (int)k.m, (cuDoubleComplex*)vbuf, (int)k.n,
-                             (cuDoubleComplex*)work, (int)sp.lwork, info, params);
-    else
-      cs = cusolverDnDgesvdj(h, CUSOLVER_EIG_MODE_VECTOR, 1, (int)k.m, (int)k.n, (double*)acopy, (int)k.m, s + k.s_off,
-                             (double*)u + k.u_off, (int)k.m, (double*)vbuf, (int)k.n, (double*)work, (int)sp.lwork,
-                             info, params);
-    if (cs != CUSOLVER_STATUS_SUCCESS) {
-      ctx->last_error = "gesvdj failed";
-      rc = TK_ERR_CUDA;
-      break;
-    }
-    const dim3 grid((unsigned)((k.n + 31) / 32), (unsigned)((k.r + 31) / 32)), block(32, 8);
-    if (sp.dtype == TK_C128)
-      k_adjoint_copy<double2><<<grid, block, 0, st>>>((const double2*)vbuf, (double2*)vh + k.vh_off, k.n, k.r);
-    else
-      k_adjoint_copy<double><<<grid, block, 0, st>>>((const double*)vbuf, (double*)vh + k.vh_off, k.n, k.r);
-    if (cudaGetLastError() != cudaSuccess) {
-      rc = TK_ERR_CUDA;
-      break;
-    }
-    ctx->launches += 1;
-  }
-  cusolverDnDestroyGesvdjInfo(params);
-  return rc;
+  ctx->launches += 1;
+  return TK_OK;
 }
 
 int run_svd_truncate(Ctx* ctx, const SvdPlan& sp, const int64_t* keep, const void* u, const double* s, const void* vh,

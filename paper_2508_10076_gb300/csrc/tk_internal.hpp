@@ -268,7 +268,6 @@ struct Ctx {
     void* end;
   };
   std::vector<Rec> prof;
-  void* solver = nullptr;  // cuSOLVER dense handle, created on first use (block SVD)
   // a second stream and two events: in the split-precision modes the CUDA-core products of a
   // contraction run beside its tensor-core chain (fork after the input permutes, join before the
   // output permute); recorded into CUDA graphs as a fork and a join
@@ -289,13 +288,13 @@ struct SvdPlan {
   Space bond;                            // W = sum_c (c, min(rows_c, cols_c))
   std::vector<SvdBlock> blocks;
   int64_t nvalues = 0;                   // singular values, concatenated by sector
-  int64_t lwork = 0;
-  size_t ws_solver = 0, ws_total = 0;
+  int64_t lwork = 0;                     // doubles of per-block norms / ranks in the workspace
+  size_t ws_solver = 0, ws_total = 0;    // bytes of the Jacobi working matrices; whole workspace
   int dtype = TK_F64;
+  void* d_jobs = nullptr;                // device job table of the grouped Jacobi launch
+  int64_t njobs = 0;
   ~SvdPlan();
 };
-void* solver_handle(Ctx* ctx);  // the context's cuSOLVER handle (created on first use), or null
-void destroy_solver_handle(Ctx* ctx);
 std::shared_ptr<SvdPlan> make_svd_plan(Ctx* ctx, std::shared_ptr<Structure> in, int dtype);
 int run_svd(Ctx* ctx, const SvdPlan& sp, const void* a, void* u, double* s, void* vh, void* ws, void* stream);
 int run_svd_truncate(Ctx* ctx, const SvdPlan& sp, const int64_t* keep, const void* u, const double* s, const void* vh,

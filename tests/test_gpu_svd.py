@@ -1,4 +1,5 @@
-"""Block SVD (cuSOLVER Jacobi per coupled sector) and its truncation against the oracle."""
+"""Block SVD (one grouped one-sided Jacobi launch over the coupled sectors) and its truncation
+against the oracle."""
 
 import numpy as np
 import pytest
@@ -96,3 +97,45 @@ def test_block_svd_and_truncation(gctx, sym, D, dtype):
         r3, k3, o3 = vtb[c]
         assert np.array_equal(hvt[o3:o3 + r3 * k3].reshape(k3, r3), hv[vo:vo + vr * vk].reshape(vk, vr)[:, :k])
         so2 += k
+
+
+@pytest.mark.parametrize("sym,D,wide,dtype", [("U1", 256, False, "f64"), ("U1", 256, True, "c128"),
+                                              ("SU2", 96, False, "c128"), ("SU2", 96, True, "f64")])
+def test_block_svd_rectangular_blocks(gctx, sym, D, wide, dtype):
+    """An MPS tensor V (x) P <- V has blocks with about twice as many rows as columns, its adjoint
+    V <- V (x) P the transpose shape: both Jacobi orientations against the oracle's block SVD
+    (values), with U^dagger U = 1, V^dagger rows orthonormal and U S V^dagger = t."""
+    from paper_2508_10076_gb300 import api
+    V, P, W = wl.heff_spaces(sym, D)
+    legs = ([(V, False)], [(V, False), (P, False)]) if wide else ([(V, False), (P, False)], [(V, False)])
+    ost = ostruct(sym, legs)
+    x = wl.normal_complex(7, ost.numel) if dtype == "c128" else wl.normal(7, ost.numel)
+    tdt = torch.complex128 if dtype == "c128" else torch.float64
+    plan = api.svd_plan(gctx, _tm(gctx, sym, legs), dtype=dtype)
+    us, vs, n = plan.outputs()
+    u = torch.full((us.numel,), float("nan"), dtype=tdt, device="cuda")
+    vh = torch.full((vs.numel,), float("nan"), dtype=tdt, device="cuda")
+    s = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    api.svd(gctx, plan, torch.from_numpy(np.ascontiguousarray(x)).cuda(), u, s, vh, ws)
+    gctx.sync()
+    ref = dict((c, sv) for c, _, sv, _ in ops.svd_block(ost, x))
+    hs, hu, hv = s.cpu().numpy(), u.cpu().numpy(), vh.cpu().numpy()
+    ub, vb = dict((c, (r, k, o)) for c, r, k, o in us.blocks()), dict((c, (r, k, o)) for c, r, k, o in vs.blocks())
+    top = max(float(v[0]) for v in ref.values())
+    ob = dict((cc, (rr, kk, oo)) for cc, rr, kk, oo in ost.blocks)
+    shapes = set()
+    for c, m, nn, so in plan.blocks():
+        r = min(m, nn)
+        shapes.add(m > nn)
+        assert np.allclose(hs[so:so + r], ref[c], atol=1e-12 * top, rtol=0)
+        assert np.all(np.diff(hs[so:so + r]) <= 0)
+        ur, uk, uo = ub[c]
+        vr, vk, vo = vb[c]
+        umat = hu[uo:uo + ur * uk].reshape(uk, ur).T
+        vmat = hv[vo:vo + vr * vk].reshape(vk, vr).T
+        assert np.allclose(umat.conj().T @ umat, np.eye(r), atol=1e-12)
+        assert np.allclose(vmat @ vmat.conj().T, np.eye(r), atol=1e-12)
+        r0, k0, o0 = ob[c]
+        assert np.allclose((umat * hs[so:so + r]) @ vmat, x[o0:o0 + r0 * k0].reshape(k0, r0).T, atol=1e-12 * top)
+    assert (not wide) in shapes  # the orientation this case is about occurs
