@@ -33,9 +33,9 @@ L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 DEFAULT_CONFIG = "c3_u1_heff_d4096"
 EXTRA_CONFIGS = ("c1_u1_heff_d1024", "c3_su2_lx_n1024")
 # DRAM bytes (read + write) per launch of the FP64 sector GEMM on the D = 4096 U(1) chain: the mean
-# over the four launches of one application, from one ncu capture of the current kernel (None
-# for workloads without a capture).
-K2_TRAFFIC_BYTES = {"c3_u1_heff_d4096": None}
+# over the four launches of one application in the timed region, from one ncu capture of the
+# current kernel (None for workloads without a capture).
+K2_TRAFFIC_BYTES = {"c3_u1_heff_d4096": 1.856e8}
 
 
 def _peaks():
@@ -294,19 +294,22 @@ class Timer:
     def __init__(self, torch, stream, flush, barrier):
         self.torch, self.stream, self.flush, self.barrier = torch, stream, flush, barrier
 
-    def __call__(self, fn, steps, clocks=None):
-        """Total ms of `steps` timed calls of fn; clocks (a Clocks) samples the timed region only."""
+    def __call__(self, fn, steps, clocks=None, label="timed"):
+        """Total ms of `steps` timed calls of fn; clocks (a Clocks) samples the timed region only.
+        The region is an NVTX range named `label` (ncu --nvtx-include selects its launches)."""
         t = self.torch
         starts = [t.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [t.cuda.Event(enable_timing=True) for _ in range(steps)]
         self.barrier()
         if clocks is not None:
             clocks.start()
+        t.cuda.nvtx.range_push(label)
         for i in range(steps):
             self.flush.zero_()
             starts[i].record(self.stream)
             fn()
             ends[i].record(self.stream)
+        t.cuda.nvtx.range_pop()
         self.barrier()
         if clocks is not None:
             self.clk = clocks.stop()
@@ -332,7 +335,7 @@ def measure(ctx, name, gemm, args, timer, rank, steps, want_graph=True, clocks=N
             step_fn, mode = work.run, f"eager (graph capture failed: {exc})"
     timer.torch.cuda.synchronize()
     launches0 = ctx.launches
-    total_ms = timer(step_fn, steps, clocks)
+    total_ms = timer(step_fn, steps, clocks, label=f"timed_{name}_{gemm}")
     launches = ctx.launches - launches0 if per_step_launches is None else per_step_launches * steps
     ctx.sync()
     ctx.profile(True)
@@ -433,14 +436,18 @@ def run_ours(args):
                 api.copy_h2d(ctx, dx, hx.data_ptr(), hx.numel() * hx.element_size(), stream)
             out = work.run()
             api.copy_d2h(ctx, host_out.data_ptr(), out, d2h, stream)
-    e2e_ms = max_over_ranks(dist, timer(e2e_step, args.steps))
+    e2e_ms = max_over_ranks(dist, timer(e2e_step, args.steps, label=f"timed_e2e_{args.config}"))
     torch.cuda.synchronize()
     if not torch.equal(host_out, m["out"].cpu()):
         raise RuntimeError("the end-to-end result differs from the device path's")
     e2e_value = job_throughput(flops, args.steps, world, e2e_ms)
     ctx.sync()
     # ---------------- roofline of the dominant kernel; FP64 peak measured on this GPU now
+    probe_clocks = Clocks(local)
+    torch.cuda.synchronize()
+    probe_clocks.start()
     fp64_peak, fp64_probe_ms = api.probe_fp64_peak(ctx, seconds=1.0)
+    probe_clk = probe_clocks.stop()
     dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (0, 0.0))
     kname, (kcount, kms) = dom
     if kname == "k_gemm_f64":
@@ -539,9 +546,9 @@ def run_ours(args):
         "gpu_launches": m["launches"],
         "roofline": roof,
         "roofline_permute": permute_roofline(work, prof, args.steps),
-        "fp64_peak_probe": {"tflops": fp64_peak, "ms": fp64_probe_ms,
-                            "how": "register-only FP64 FMA loop, 16 independent chains per thread, 8 CTAs x 256 "
-                                   "threads per SM, CUDA events"},
+        "fp64_peak_probe": {"tflops": fp64_peak, "ms": fp64_probe_ms, "clocks": probe_clk,
+                            "how": "register-only FP64 FMA loop: a 4 x 4 outer product per thread (16 independent "
+                                   "chains), 4 CTAs x 256 threads per SM, CUDA events"},
         "kernels": kernels_table(prof, args.steps),
     }
     if "ozaki" in variants:
