@@ -3,7 +3,7 @@
 //                     coefficient-weighted sum of strided transposes of source reduced arrays
 //                     (Algorithm 10; Algorithm 6 for abelian symmetries, one source, weight 1);
 //                     the input permute launch also zero-fills the output blocks of coupled
-//                     sectors whose inner dimension is empty and fills counter / scale arrays.
+//                     sectors whose inner dimension is empty and clears the split-K counters.
 //   K2 k_gemm_f64  -- grouped FP64 GEMM over the coupled sectors (Algorithm 8, step 2).
 //   k_zero_batch   -- the zero fill of many requests of one packed batch.
 #include <cuda_runtime.h>
@@ -1313,20 +1313,18 @@ int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b,
   void* ct = cp.pc ? (void*)(w + cp.ws_ct) : c;
   int rc;
   const PermJob in_jobs[2] = {{cp.pa.get(), a, (void*)at}, {cp.pb.get(), b, (void*)bt}};
-  IntClear clears[2];
+  IntClear clears[1];
   int nclears = 0;
   if (cp.split_slots > 0) clears[nclears++] = IntClear{(int*)(w + cp.ws_counters), (int64_t)cp.split_slots};
-  const bool scales = !cp.gemms_oz.empty() && ozaki_scale_clear(cp, w + cp.ws_slices, &clears[nclears]);
-  if (scales) ++nclears;
-  // both operands in one launch, which also clears the split-K counters and the split-precision
-  // scale arrays and zero-fills the output blocks with an empty inner dimension
+  // both operands in one launch, which also clears the split-K counters and zero-fills the output
+  // blocks with an empty inner dimension
   ZeroJob zj{(const ZeroItem*)cp.d_zero, (int64_t)cp.zeros.size(), 0, ct, cp.dtype};
   for (const ZeroItem& z : cp.zeros) zj.maxn = std::max(zj.maxn, z.n);
   if ((rc = launch_permutes(ctx, in_jobs, 2, stream, clears, nclears, cp.zeros.empty() ? nullptr : &zj)) != TK_OK)
     return rc;
   if (!cp.gemms_fp64.empty() && !cp.gemms_oz.empty() && ctx->side) {
     // split precision with CUDA-core products too: those run on the side stream beside the
-    // scale / slice / tensor-core launches.  They write other C blocks (or other columns of a
+    // prep / tensor-core launches.  They write other C blocks (or other columns of a
     // block), their own split-K partials and counters, and read only the permuted operands.
     cudaStream_t s = (cudaStream_t)stream, side = (cudaStream_t)ctx->side;
     std::lock_guard<std::mutex> lk(ctx->side_mu);
@@ -1336,14 +1334,14 @@ int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b,
     if ((rc = launch_gemm_fp64(ctx, cp, at, bt, ct, w + cp.ws_partials, (int*)(w + cp.ws_counters), side)) != TK_OK)
       return rc;
     if (cudaEventRecord((cudaEvent_t)ctx->ev_join, side) != cudaSuccess) return TK_ERR_CUDA;
-    rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream, scales);
+    rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream);
     if (cudaStreamWaitEvent(s, (cudaEvent_t)ctx->ev_join, 0) != cudaSuccess) return TK_ERR_CUDA;  // join first
     if (rc != TK_OK) return rc;
   } else {
     if (!cp.gemms_fp64.empty() &&
         (rc = launch_gemm_fp64(ctx, cp, at, bt, ct, w + cp.ws_partials, (int*)(w + cp.ws_counters), stream)) != TK_OK)
       return rc;
-    if (!cp.gemms_oz.empty() && (rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream, scales)) != TK_OK)
+    if (!cp.gemms_oz.empty() && (rc = launch_gemm_ozaki(ctx, cp, at, bt, ct, w + cp.ws_slices, stream)) != TK_OK)
       return rc;
   }
   if (cp.pc && (rc = launch_permute(ctx, *cp.pc, ct, c, stream)) != TK_OK) return rc;

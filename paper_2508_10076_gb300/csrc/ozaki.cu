@@ -16,8 +16,9 @@
 //     applies 2^{e_m + f_n}.
 // With s = 6 the relative Frobenius error against FP64 is ~1e-12 on N(0,1) data.
 //
-// Data path: a scale kernel and a slicer kernel write the slices as pre-tiled 128 x 32 BF16
-// tiles (64-byte rows); one persistent GEMM launch walks a work list of (sector, 128-row tile,
+// Data path: one prep launch (clusters of 8 CTAs per 128-row operand tile, the scale maxima
+// exchanged through distributed shared memory) writes the scales and the slices as pre-tiled
+// 128 x 32 BF16 tiles (64-byte rows); one persistent GEMM launch walks a work list of (sector, 128-row tile,
 // column tile) items, the last column tile of a sector as narrow as its remainder (MMA N a
 // multiple of 16).  Per CTA: warp 0 issues TMA loads (cp.async.bulk.tensor, 64-byte swizzle) of
 // all s A slices and all s B slices of one 32-deep k-chunk into a stage (two to four); one thread
@@ -28,6 +29,7 @@
 // two buffers and overlap it.  Every mbarrier wait is bounded: on timeout the kernel records an
 // error in the context's status word, drains its own copies and MMAs (bounded again), frees
 // TMEM and returns.
+#include <cooperative_groups.h>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -38,6 +40,8 @@
 
 #include "tk_device.cuh"
 #include "tk_internal.hpp"
+
+namespace cg = cooperative_groups;
 
 namespace tk {
 namespace {
@@ -80,7 +84,7 @@ struct OzWork {
   int32_t part, nparts, slot, pad;  // split-K: part index, parts of the tile, tile slot (-1: no split)
 };
 constexpr int OZ_MAX_PARTS = 4;
-struct OzJob {  // slicer / scale job
+struct OzJob {  // k_oz_prep job: one 128-row tile (r0) of one operand of one sector
   int32_t sector, operand, r0, kc;
 };
 struct OzPairs {
@@ -97,11 +101,10 @@ struct OzLayout {
   int mode = 0;           // 0: Ozaki BF16 slices, 1: 3xTF32
   int bn = OZ_BN_NARROW;  // output tile width of this launch
   OzPairs pairs;
-  int64_t nwork = 0, nslice_jobs = 0, nscale_jobs = 0;
+  int64_t nwork = 0, nprep_jobs = 0;
   OzSector* d_sectors = nullptr;
   OzWork* d_work = nullptr;
-  OzJob* d_slice_jobs = nullptr;
-  OzJob* d_scale_jobs = nullptr;
+  OzJob* d_prep_jobs = nullptr;  // one per 128-row tile of each operand: a k_oz_prep cluster each
   std::vector<int32_t> cta_work;   // work of CTA b: work[cta_work[b] .. cta_work[b + 1])
   int32_t* d_cta_work = nullptr;
   int ncta = 0;
@@ -266,11 +269,9 @@ __device__ __forceinline__ long long round_scaled(double v, int shift) {
 // ------------------------------------------------------------------ scale and slice kernels
 // Operand views: A~^c element (m, k) at A[a_off + m + k M]; B~^c element (k, n) at B[b_off + k + n K].
 
-// Scale exponents 2^e > max_k |x_rk| for every row of A~^c and every column of B~^c.  The
-// exponent of a maximum is the maximum of the exponents, so each job covers a chunk of K and
-// folds its partial result in with atomicMax (the arrays start at kNoScale).
-constexpr int32_t kNoScale = (int32_t)0x80808080;  // memset pattern 0x80 = "no non-zero entry yet"
-constexpr int OZ_SCALE_KCHUNK = 256;
+// Scale exponents 2^e > max_k |x_rk| for every row of A~^c and every column of B~^c (k_oz_prep).
+constexpr int32_t kNoScale = (int32_t)0x80808080;  // the scale of an all-zero row or column
+constexpr int OZ_PREP_CLUSTER = 8;                 // CTAs sharing one 128-row tile in k_oz_prep
 
 // e with 2^(e-1) <= mx < 2^e for a non-negative finite mx (kNoScale for 0), from the bits.
 __device__ __forceinline__ int exponent_of(double mx) {
@@ -281,7 +282,7 @@ __device__ __forceinline__ int exponent_of(double mx) {
   return -1074 + (64 - __clzll((long long)b));  // subnormal: highest set bit
 }
 
-// One request of a scale or slice launch: its job list, operands, scale arrays and slice tiles;
+// One request of a prep launch: its job list, operands, scale arrays and slice tiles;
 // its jobs are blocks [block0, block0 + njobs) of the launch.
 struct OzPrepSeg {
   const OzSector* secs;
@@ -313,54 +314,6 @@ __device__ __forceinline__ const OzPrepSeg& prep_seg(const OzPrepT<NSEG>& P, int
   }
   local = (int64_t)blockIdx.x - P.seg[lo].block0;
   return P.seg[lo];
-}
-
-template <int NSEG>
-__global__ void __launch_bounds__(256) k_oz_scale(const __grid_constant__ OzPrepT<NSEG> P) {
-  int64_t local;
-  const OzPrepSeg& g = prep_seg(P, local);
-  const OzSector* __restrict__ secs = g.secs;
-  const double* __restrict__ A = g.A;
-  const double* __restrict__ B = g.B;
-  int32_t* __restrict__ scale_a = g.sa;
-  int32_t* __restrict__ scale_b = g.sb;
-  if (local == 0)  // the GEMM's split-K arrival counters start at zero
-    for (int i = threadIdx.x; i < g.ncounters; i += blockDim.x) g.counters[i] = 0;
-  const OzJob jb = g.jobs[local];
-  const OzSector s = secs[jb.sector];
-  const int64_t k0 = (int64_t)jb.kc * OZ_SCALE_KCHUNK;
-  const int64_t k1 = min(s.K, k0 + OZ_SCALE_KCHUNK);
-  double mx = 0.0;
-  if (jb.operand == 0) {  // 256 rows, one thread per row, k-chunk of 256
-    const int64_t r = jb.r0 + threadIdx.x;
-    if (r >= s.M) return;
-    const long long* x = reinterpret_cast<const long long*>(A) + s.a_off + r;
-    unsigned long long mb = 0;  // |x| ordered as unsigned integers: no FP64 instructions
-    int64_t k = k0;
-    for (; k + 8 <= k1; k += 8) {  // eight independent loads in flight
-      unsigned long long v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = (unsigned long long)__ldg(x + (k + u) * s.M);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) mb = max(mb, v[u] & 0x7FFFFFFFFFFFFFFFull);
-    }
-    for (; k < k1; ++k) mb = max(mb, (unsigned long long)__ldg(x + k * s.M) & 0x7FFFFFFFFFFFFFFFull);
-    mx = __longlong_as_double((long long)mb);
-    const int e = exponent_of(mx);
-    if (e != kNoScale) atomicMax(&scale_a[s.sa_off + r], e);
-  } else {  // 8 columns, one warp per column, lanes along k
-    const int64_t r = jb.r0 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (r >= s.N) return;  // the whole warp leaves together
-    const long long* x = reinterpret_cast<const long long*>(B) + s.b_off + r * s.K;
-    unsigned long long mb = 0;
-    for (int64_t k = k0 + lane; k < k1; k += 32) mb = max(mb, (unsigned long long)__ldg(x + k) & 0x7FFFFFFFFFFFFFFFull);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mb = max(mb, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mb, o));
-    mx = __longlong_as_double((long long)mb);
-    const int e = exponent_of(mx);
-    if (lane == 0 && e != kNoScale) atomicMax(&scale_b[s.sb_off + r], e);
-  }
 }
 
 // v 2^-e (|v| < 2^e) as hi + lo, both TF32 values in FP32 containers (11 significant bits, the
@@ -440,43 +393,32 @@ __device__ __forceinline__ void oz_slice_pair(double v0, double v1, int e, __nv_
   }
 }
 
-// One 128 x 32 (rows x k) tile of one operand per CTA, all slices.  Each thread takes two
-// consecutive k of a row, so a slice of the pair is one packed 32-bit (BF16 pair) or 64-bit (TF32
-// pair) store and a half-warp writes a full tile row; A~ (column-major, rows contiguous) is staged
-// through shared memory to keep its reads coalesced, B~ (k contiguous) is read directly.
-// MODE 0 writes s BF16 digit slices, MODE 1 the TF32 pair (hi, lo).
-template <int MODE, int NSEG>
-__global__ void __launch_bounds__(256) k_oz_slice(const __grid_constant__ OzPrepT<NSEG> P, int nslices) {
-  __shared__ double xs[OZ_BK][OZ_TROWS + 1];
-  int64_t local;
-  const OzPrepSeg& g = prep_seg(P, local);
-  const OzSector* __restrict__ secs = g.secs;
-  const double* __restrict__ A = g.A;
-  const double* __restrict__ B = g.B;
-  const int32_t* __restrict__ scale_a = g.sa;
-  const int32_t* __restrict__ scale_b = g.sb;
-  void* __restrict__ tiles_a = g.ta;
-  void* __restrict__ tiles_b = g.tb;
-  const OzJob jb = g.jobs[local];
-  const OzSector s = secs[jb.sector];
-  const int op = jb.operand;
+// One 128 x 32 (rows x k) tile (row tile rt, k-chunk kc) of one operand, all slices, with the
+// rows' scale exponents in esc.  Each thread takes two consecutive k of a row, so a slice of the
+// pair is one packed 32-bit (BF16 pair) or 64-bit (TF32 pair) store and a half-warp writes a full
+// tile row; A~ (column-major, rows contiguous) is staged through shared memory to keep its reads
+// coalesced, B~ (k contiguous) is read directly.  MODE 0 writes s BF16 digit slices, MODE 1 the
+// TF32 pair (hi, lo).  Called by all 256 threads of the CTA (it synchronises them).
+template <int MODE>
+__device__ __forceinline__ void slice_tile(const OzPrepSeg& g, const OzSector& s, int op, int64_t rt, int kc,
+                                           const int* esc, double (*xs)[OZ_TROWS + 1], int nslices) {
   const int64_t R = op == 0 ? s.M : s.N;
-  const int64_t rt = jb.r0;  // row-tile index
-  const int64_t r0 = rt * OZ_TROWS, k0 = (int64_t)jb.kc * OZ_BK;
+  const int64_t r0 = rt * OZ_TROWS, k0 = (int64_t)kc * OZ_BK;
   const int tid = threadIdx.x;
   if (op == 0) {
+    __syncthreads();  // the previous tile's readers are done with xs
     for (int e = tid; e < OZ_TROWS * OZ_BK; e += 256) {
       const int ml = e & (OZ_TROWS - 1), kk = e / OZ_TROWS;
       const int64_t m = r0 + ml, k = k0 + kk;
-      xs[kk][ml] = (m < R && k < s.K) ? __ldg(A + s.a_off + m + k * s.M) : 0.0;
+      xs[kk][ml] = (m < R && k < s.K) ? __ldg(g.A + s.a_off + m + k * s.M) : 0.0;
     }
     __syncthreads();
   }
   const int kp = (tid & 15) * 2, rw = tid >> 4;  // k pair and row of this thread
   const int64_t nrt = op == 0 ? s.nmt : s.nnt;
-  const int64_t tile0 = (op == 0 ? s.ta_base : s.tb_base) + rt * s.nkc + jb.kc;  // slice 0
+  const int64_t tile0 = (op == 0 ? s.ta_base : s.tb_base) + rt * s.nkc + kc;  // slice 0
   const int64_t slice_stride = nrt * s.nkc * (int64_t)(OZ_TROWS * OZ_BK);  // elements
-  const int32_t* scl = op == 0 ? scale_a + s.sa_off : scale_b + s.sb_off;
+  void* __restrict__ tiles = op == 0 ? g.ta : g.tb;
 #pragma unroll 2
   for (int i = 0; i < OZ_TROWS / 16; ++i) {
     const int rl = rw + 16 * i;
@@ -486,17 +428,15 @@ __global__ void __launch_bounds__(256) k_oz_slice(const __grid_constant__ OzPrep
       v0 = xs[kp][rl];
       v1 = xs[kp + 1][rl];
     } else {
-      const double* src = B + s.b_off + k + r * s.K;
+      const double* src = g.B + s.b_off + k + r * s.K;
       v0 = (r < R && k < s.K) ? __ldg(src) : 0.0;
       v1 = (r < R && k + 1 < s.K) ? __ldg(src + 1) : 0.0;
     }
-    int e = (r < R) ? scl[r] : 0;
-    if (e == kNoScale) e = 0;  // an all-zero row or column
+    const int e = esc[rl];
     const int64_t at = tile0 * (OZ_TROWS * OZ_BK) + rl * OZ_BK + kp;  // element index of slice 0
     if constexpr (MODE == 0) {
       // at is even and tiles are 1 KB aligned: the pair is a 4-byte aligned store
-      __nv_bfloat162* dst =
-          reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(op == 0 ? tiles_a : tiles_b) + at);
+      __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(tiles) + at);
       const int64_t st2 = slice_stride / 2;
       switch (nslices) {
         case 2: oz_slice_pair<2>(v0, v1, e, dst, st2); break;
@@ -510,11 +450,104 @@ __global__ void __launch_bounds__(256) k_oz_slice(const __grid_constant__ OzPrep
       float h0, l0, h1, l1;
       tf32_split(v0, e, h0, l0);
       tf32_split(v1, e, h1, l1);
-      float2* dst = reinterpret_cast<float2*>(reinterpret_cast<float*>(op == 0 ? tiles_a : tiles_b) + at);
+      float2* dst = reinterpret_cast<float2*>(reinterpret_cast<float*>(tiles) + at);
       dst[0] = make_float2(h0, h1);
       dst[slice_stride / 2] = make_float2(l0, l1);
     }
   }
+}
+
+// Scale and slice in one launch.  A cluster of OZ_PREP_CLUSTER CTAs owns one 128-row tile of one
+// operand (rows of A~^c, columns of B~^c) and splits its k-chunks evenly among its CTAs.
+//   1. Every CTA takes the maximum |x| of each of the 128 rows over its k-chunks (as FP64 bit
+//      patterns, ordered as unsigned integers: no FP64 instruction).
+//   2. After a cluster barrier every CTA reads the 8 partial maxima of its rows from the other CTAs'
+//      shared memory (distributed shared memory), so all of them hold the row's power-of-two
+//      scale 2^e > max_k |x| (the exponent of a maximum is the maximum of the exponents); rank 0
+//      writes it for the GEMM's epilogue.  A second cluster barrier keeps every CTA's shared
+//      memory alive until the others have read it.
+//   3. Every CTA slices its own k-chunks, re-reading them (now from L2).
+// The operands are read from HBM once instead of twice (a separate scale pass), and the scales
+// need no initial fill.  The first CTA of each request also clears the GEMM's split-K counters.
+template <int MODE, int NSEG>
+__global__ void __cluster_dims__(OZ_PREP_CLUSTER, 1, 1) __launch_bounds__(256)
+    k_oz_prep(const __grid_constant__ OzPrepT<NSEG> P, int nslices) {
+  __shared__ double xs[OZ_BK][OZ_TROWS + 1];
+  __shared__ unsigned long long pmax[OZ_TROWS];  // this CTA's maxima (read by the cluster)
+  __shared__ unsigned long long half[OZ_TROWS];
+  __shared__ int esc[OZ_TROWS];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  int64_t local;
+  const OzPrepSeg& g = prep_seg(P, local);
+  const int tid = threadIdx.x;
+  if (local == 0)  // the GEMM's split-K arrival counters start at zero
+    for (int i = tid; i < g.ncounters; i += blockDim.x) g.counters[i] = 0;
+  const OzJob jb = g.jobs[local / OZ_PREP_CLUSTER];
+  const OzSector s = g.secs[jb.sector];
+  const int op = jb.operand;
+  const int64_t R = op == 0 ? s.M : s.N;
+  const int64_t r0 = (int64_t)jb.r0 * OZ_TROWS;
+  const int kc_lo = (int)((int64_t)rank * s.nkc / OZ_PREP_CLUSTER);
+  const int kc_hi = (int)((int64_t)(rank + 1) * s.nkc / OZ_PREP_CLUSTER);
+  const int64_t k_lo = (int64_t)kc_lo * OZ_BK, k_hi = min(s.K, (int64_t)kc_hi * OZ_BK);
+  constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
+  // ---- 1. partial maxima over this CTA's k range
+  if (op == 0) {  // A~: rows contiguous; thread (row, half) walks every other column
+    const int rl = tid & (OZ_TROWS - 1), h = tid >> 7;
+    const int64_t m = r0 + rl;
+    unsigned long long mb = 0;
+    if (m < R) {
+      const long long* x = reinterpret_cast<const long long*>(g.A) + s.a_off + m;
+      int64_t k = k_lo + h;
+      for (; k + 14 < k_hi; k += 16) {  // eight independent loads in flight
+        unsigned long long v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = (unsigned long long)__ldg(x + (k + 2 * u) * s.M);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) mb = max(mb, v[u] & kAbs);
+      }
+      for (; k < k_hi; k += 2) mb = max(mb, (unsigned long long)__ldg(x + k * s.M) & kAbs);
+    }
+    if (h == 1) half[rl] = mb;
+    __syncthreads();
+    if (h == 0) pmax[rl] = max(mb, half[rl]);
+  } else {  // B~: columns contiguous along k; a warp per column, lanes along k
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int cl = warp; cl < OZ_TROWS; cl += 8) {
+      const int64_t n = r0 + cl;
+      unsigned long long mb = 0;
+      if (n < R) {
+        const long long* x = reinterpret_cast<const long long*>(g.B) + s.b_off + n * s.K;
+        int64_t k = k_lo + lane;
+        for (; k + 96 < k_hi; k += 128) {
+          unsigned long long v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = (unsigned long long)__ldg(x + k + 32 * u);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) mb = max(mb, v[u] & kAbs);
+        }
+        for (; k < k_hi; k += 32) mb = max(mb, (unsigned long long)__ldg(x + k) & kAbs);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        mb = max(mb, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mb, o));
+      if (lane == 0) pmax[cl] = mb;
+    }
+  }
+  // ---- 2. the cluster's maxima -> the rows' scale exponents
+  cluster.sync();
+  if (tid < OZ_TROWS) {
+    unsigned long long mb = 0;
+#pragma unroll
+    for (int q = 0; q < OZ_PREP_CLUSTER; ++q) mb = max(mb, *cluster.map_shared_rank(&pmax[tid], q));
+    const int e = exponent_of(__longlong_as_double((long long)mb));
+    if (rank == 0 && r0 + tid < R) (op == 0 ? g.sa + s.sa_off : g.sb + s.sb_off)[r0 + tid] = e;
+    esc[tid] = e == kNoScale ? 0 : e;  // an all-zero row or column slices to zeros with any scale
+  }
+  cluster.sync();
+  // ---- 3. slices of this CTA's k-chunks
+  for (int kc = kc_lo; kc < kc_hi; ++kc) slice_tile<MODE>(g, s, op, jb.r0, kc, esc, xs, nslices);
 }
 
 // ------------------------------------------------------------------ the persistent GEMM
@@ -949,7 +982,7 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
         ++P.n;
       }
   std::vector<OzWork> work;
-  std::vector<OzJob> slice_jobs, scale_jobs;
+  std::vector<OzJob> prep_jobs;
   std::vector<std::pair<double, OzWork>> wcost;
   // Tile width: measured in this kernel, a 128 x 64 x 16 MMA takes ~72 cycles and a 128 x 128 x 16
   // one ~65 (the full rate), so 128-column tiles do nearly twice the work per cycle; but they hold
@@ -1003,14 +1036,9 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
         t.nw = nw;
         wcost.push_back({(double)s.nkc, t});
       }
-    for (int rt = 0; rt < s.nmt; ++rt)
-      for (int kc = 0; kc < s.nkc; ++kc) slice_jobs.push_back(OzJob{sid, 0, rt, kc});
-    for (int rt = 0; rt < s.nnt; ++rt)
-      for (int kc = 0; kc < s.nkc; ++kc) slice_jobs.push_back(OzJob{sid, 1, rt, kc});
-    for (int kc = 0; kc * OZ_SCALE_KCHUNK < s.K; ++kc) {
-      for (int64_t r0 = 0; r0 < s.M; r0 += 256) scale_jobs.push_back(OzJob{sid, 0, (int32_t)r0, kc});
-      for (int64_t r0 = 0; r0 < s.N; r0 += 8) scale_jobs.push_back(OzJob{sid, 1, (int32_t)r0, kc});
-    }
+    // one prep cluster per 128-row tile of A~ and per 128-column tile of B~
+    for (int rt = 0; rt < s.nmt; ++rt) prep_jobs.push_back(OzJob{sid, 0, rt, 0});
+    for (int rt = 0; rt < s.nnt; ++rt) prep_jobs.push_back(OzJob{sid, 1, rt, 0});
   }
   std::stable_sort(wcost.begin(), wcost.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
   // Split-K: a launch with fewer than two tiles per SM cuts deep tiles into up to OZ_MAX_PARTS
@@ -1076,8 +1104,7 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
     work.swap(ordered);
   }
   L->nwork = (int64_t)work.size();
-  L->nslice_jobs = (int64_t)slice_jobs.size();
-  L->nscale_jobs = (int64_t)scale_jobs.size();
+  L->nprep_jobs = (int64_t)prep_jobs.size();
   // workspace layout: A tiles | B tiles | row scales | column scales | split-K partial tiles
   L->off_ta = 0;
   L->off_tb = al1k((size_t)L->ntiles_a * tile_bytes);
@@ -1090,12 +1117,11 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
   if (!L->sectors.empty()) {
     if ((rc = dev_upload(ctx, (void**)&L->d_sectors, L->sectors.data(), L->sectors.size() * sizeof(OzSector))) != TK_OK ||
         (rc = dev_upload(ctx, (void**)&L->d_work, work.data(), work.size() * sizeof(OzWork))) != TK_OK ||
-        (rc = dev_upload(ctx, (void**)&L->d_slice_jobs, slice_jobs.data(), slice_jobs.size() * sizeof(OzJob))) != TK_OK ||
-        (rc = dev_upload(ctx, (void**)&L->d_scale_jobs, scale_jobs.data(), scale_jobs.size() * sizeof(OzJob))) != TK_OK ||
+        (rc = dev_upload(ctx, (void**)&L->d_prep_jobs, prep_jobs.data(), prep_jobs.size() * sizeof(OzJob))) != TK_OK ||
         (rc = dev_upload(ctx, (void**)&L->d_cta_work, L->cta_work.data(), L->cta_work.size() * sizeof(int32_t))) != TK_OK)
       return rc;
   }
-  cp.d_oz = {L->d_sectors, L->d_work, L->d_slice_jobs, L->d_scale_jobs, L->d_cta_work};
+  cp.d_oz = {L->d_sectors, L->d_work, L->d_prep_jobs, L->d_cta_work};
   cp.oz_nwork = L->nwork;
   cp.oz_bytes = L->bytes;
   cp.oz = L;
@@ -1116,9 +1142,9 @@ int ensure_smem_attrs(Ctx* ctx) {
   return TK_OK;
 }
 
-// Describe one request for the scale / slice launches and the GEMM launch; clears its scale arrays.
+// Describe one request for the prep launch and the GEMM launch.
 int describe_ozaki_request(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
-                           void* stream, OzPrepSeg& P, OzReq& R, bool scales_cleared = false) {
+                           OzPrepSeg& P, OzReq& R) {
   const OzLayout* L = static_cast<const OzLayout*>(cp.oz.get());
   if (((uintptr_t)ws & 15) != 0) {
     ctx->last_error = "split-precision workspace must be 16-byte aligned";
@@ -1135,10 +1161,7 @@ int describe_ozaki_request(Ctx* ctx, const ContractPlan& cp, const void* a, cons
     ctx->last_error = "cuTensorMapEncodeTiled failed";
     return TK_ERR_CUDA;
   }
-  if (!scales_cleared &&
-      cudaMemsetAsync(sa, 0x80, L->off_sb - L->off_sa + (size_t)L->ncols_b * 4, (cudaStream_t)stream) != cudaSuccess)
-    return TK_ERR_CUDA;
-  int* counters = (int*)(w + L->off_cnt);  // cleared by the scale kernel
+  int* counters = (int*)(w + L->off_cnt);  // cleared by k_oz_prep
   std::memset(&P, 0, sizeof(P));
   P.secs = L->d_sectors;
   P.A = (const double*)a;
@@ -1161,37 +1184,28 @@ int describe_ozaki_request(Ctx* ctx, const ContractPlan& cp, const void* a, cons
   return TK_OK;
 }
 
-// Scale, then slice, the operands of every request of one batch (one launch each).
+// Scale and slice the operands of every request of one batch: one launch of k_oz_prep clusters.
 template <int NSEG>
 int launch_oz_prep(Ctx* ctx, const OzLayout* const* lay, OzPrepT<NSEG>& P, int mode, int nslices, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   int64_t blocks = 0;
-  for (int i = 0; i < P.nseg; ++i) {
+  for (int i = 0; i < P.nseg; ++i) {  // every segment starts on a cluster boundary
     P.seg[i].block0 = blocks;
-    P.seg[i].jobs = lay[i]->d_scale_jobs;
-    blocks += lay[i]->nscale_jobs;
+    P.seg[i].jobs = lay[i]->d_prep_jobs;
+    blocks += lay[i]->nprep_jobs * OZ_PREP_CLUSTER;
   }
-  if (blocks > 0) {
-    ProfScope prof(ctx, "k_oz_scale", stream);
-    k_oz_scale<NSEG><<<(unsigned)blocks, 256, 0, s>>>(P);
-    if (cudaGetLastError() != cudaSuccess) return TK_ERR_CUDA;
-    ctx->launches += 1;
+  if (blocks == 0) return TK_OK;
+  ProfScope prof(ctx, "k_oz_prep", stream);
+  if (mode == 0)
+    k_oz_prep<0, NSEG><<<(unsigned)blocks, 256, 0, s>>>(P, nslices);
+  else
+    k_oz_prep<1, NSEG><<<(unsigned)blocks, 256, 0, s>>>(P, nslices);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ctx->last_error = std::string("k_oz_prep launch: ") + cudaGetErrorString(e);
+    return TK_ERR_CUDA;
   }
-  blocks = 0;
-  for (int i = 0; i < P.nseg; ++i) {
-    P.seg[i].block0 = blocks;
-    P.seg[i].jobs = lay[i]->d_slice_jobs;
-    blocks += lay[i]->nslice_jobs;
-  }
-  if (blocks > 0) {
-    ProfScope prof(ctx, "k_oz_slice", stream);
-    if (mode == 0)
-      k_oz_slice<0, NSEG><<<(unsigned)blocks, 256, 0, s>>>(P, nslices);
-    else
-      k_oz_slice<1, NSEG><<<(unsigned)blocks, 256, 0, s>>>(P, nslices);
-    if (cudaGetLastError() != cudaSuccess) return TK_ERR_CUDA;
-    ctx->launches += 1;
-  }
+  ctx->launches += 1;
   return TK_OK;
 }
 
@@ -1221,17 +1235,8 @@ int launch_oz_gemm(Ctx* ctx, const OzLayout* L, const OzBatchT<NREQ>& B, int gri
 }
 }  // namespace
 
-bool ozaki_scale_clear(const ContractPlan& cp, void* ws, IntClear* out) {
-  const OzLayout* L = static_cast<const OzLayout*>(cp.oz.get());
-  if (!L || L->nwork == 0) return false;
-  out->p = (int*)((char*)ws + L->off_sa);
-  out->n = (int64_t)((L->off_sb - L->off_sa) / 4 + L->ncols_b);
-  out->fill = kNoScale;
-  return true;
-}
-
 int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c, void* ws,
-                      void* stream, bool scales_cleared) {
+                      void* stream) {
   const OzLayout* L = static_cast<const OzLayout*>(cp.oz.get());
   if (!L) {
     ctx->last_error = "split-precision tables missing";
@@ -1244,7 +1249,7 @@ int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const voi
   OzPrepT<1> P;
   std::memset(&B, 0, sizeof(B));
   std::memset(&P, 0, sizeof(P));
-  if ((rc = describe_ozaki_request(ctx, cp, a, b, c, ws, stream, P.seg[0], B.req[0], scales_cleared)) != TK_OK)
+  if ((rc = describe_ozaki_request(ctx, cp, a, b, c, ws, P.seg[0], B.req[0])) != TK_OK)
     return rc;
   B.nreq = 1;
   P.nseg = 1;
@@ -1275,8 +1280,8 @@ int launch_gemm_ozaki_batch(Ctx* ctx, int n, const ContractPlan* const* plans, c
     for (int i : todo) {
       const OzLayout* L = static_cast<const OzLayout*>(plans[i]->oz.get());
       if (B.nreq < OZ_BATCH && L->mode == L0->mode && L->bn == L0->bn && L->slices == L0->slices) {
-        if ((rc = describe_ozaki_request(ctx, *plans[i], a[i], b[i], c[i], ws[i], stream, P.seg[B.nreq],
-                                         B.req[B.nreq])) != TK_OK)
+        if ((rc = describe_ozaki_request(ctx, *plans[i], a[i], b[i], c[i], ws[i], P.seg[B.nreq], B.req[B.nreq])) !=
+            TK_OK)
           return rc;
         lay[B.nreq] = L;
         grid = std::max(grid, L->ncta);

@@ -344,10 +344,7 @@ int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void
                      void* partials, int* counters, void* stream);
 int upload_gemm_tables(Ctx* ctx, ContractPlan& cp);
 int launch_gemm_ozaki(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b, void* c,
-                      void* slices_ws, void* stream, bool scales_cleared = false);
-// The split-precision scale arrays of a plan in its workspace region, to be filled with the
-// "no entry yet" pattern before the scale launch (false when the plan has no tensor-core part).
-bool ozaki_scale_clear(const ContractPlan& cp, void* slices_ws, IntClear* out);
+                      void* slices_ws, void* stream);
 // The split-precision GEMMs of several requests (their workspaces' slice regions in ws): scaling
 // and slicing per request, then one packed tensor-core launch per group of up to 32 requests that
 // share mode, tile width and slice count.
