@@ -387,6 +387,36 @@ def permute_roofline(work, prof, steps):
                     "/ k_permute time"}
 
 
+def run_serving(api, local, dist, rank, args, split):
+    """The C4 serving loop on its own context (the 150 GB budget covers the server alone):
+    calibrate the arrival rate to the offered load, warm up, serve the request stream."""
+    from paper_2508_10076_gb300.serve import Server, calibrated_rate, request_stream
+    reqs = request_stream(args.serve_requests, seed=1000 + replica_seed(rank))
+    serve_ctx = api.Context(local)
+    server = Server(serve_ctx, budget_bytes=150 << 30, split_gemm="ozaki" if split else None)
+    for r in reqs:
+        server.shape(r["sym"], r["D"], r["dtype"])
+    rate, mean_s = calibrated_rate(server, reqs, load=args.serve_load)
+    server.run(reqs[:200], rate)  # warm-up pass (allocator, first launches)
+    _, out, _ = server.run(reqs, rate)
+    out["p99_ms"] = max_over_ranks(dist, out["p99_ms"])
+    solo = sorted(k for k, sh in server.shapes.items() if sh.solo)
+    mem = serve_ctx.memory()
+    out.update({"precision": "FP64 (complex128) in packed batches; shapes whose FP64 service alone is >= 1 ms and "
+                "faster in Ozaki BF16 (s = 6, <= 1e-10) are served one by one in that mode"
+                if split else "FP64 (complex128) in packed batches, every request",
+                "split_precision_shapes": len(solo), "shapes": len(server.shapes),
+                "plans": "autotuned once per shape before the timed loop",
+                "budget_gb": 150, "resident_gb": (mem["library_bytes"] + mem["reserved_bytes"]) / 2**30,
+                "budget_counts": "plan tables held by libtk + resident inputs (reserved) + in-flight "
+                                 "outputs and workspaces (reserved at admission)",
+                "load": args.serve_load, "mean_service_ms_alone": 1e3 * mean_s,
+                "mix": "U(1) L.x at D / SU(2) L.x at D/4, D log-uniform 64-4096 "
+                       "(25-level grid), half complex128, Poisson arrivals"})
+    server.close()
+    return out
+
+
 def run_ours(args):
     import torch
     world, rank, local = _dist()
@@ -501,33 +531,13 @@ def run_ours(args):
                         _out_blocks(e["work"]), e["out"].cpu().numpy(), ref_out.cpu().numpy())
                     row[gemm]["roofline"] = split_roofline(gemm, e, args.extra_steps)
             extra[name] = row
-    # ---------------- serving: Poisson stream of mixed requests through the continuous-batching loop
-    serve = None
+    # ---------------- serving: Poisson stream of mixed requests through the continuous-batching loop,
+    # mixed precision (the largest shapes one by one in Ozaki BF16) and FP64 only
+    serve = serve_fp64 = None
     if args.serve_requests > 0:
-        from paper_2508_10076_gb300.serve import Server, calibrated_rate, request_stream
-        reqs = request_stream(args.serve_requests, seed=1000 + replica_seed(rank))
-        serve_ctx = api.Context(local)  # its own context: the 150 GB budget covers the server alone
-        server = Server(serve_ctx, budget_bytes=150 << 30, split_gemm=None if args.serve_fp64 else "ozaki")
-        for r in reqs:
-            server.shape(r["sym"], r["D"], r["dtype"])
-        rate, mean_s = calibrated_rate(server, reqs, load=args.serve_load)
-        server.run(reqs[:200], rate)  # warm-up pass (allocator, first launches)
-        _, serve, _ = server.run(reqs, rate)
-        serve["p99_ms"] = max_over_ranks(dist, serve["p99_ms"])
-        solo = sorted(k for k, sh in server.shapes.items() if sh.solo)
-        mem = serve_ctx.memory()
-        serve.update({"precision": "FP64 (complex128) in packed batches; shapes whose FP64 service alone is >= 1 ms and "
-                      "faster in Ozaki BF16 (s = 6, <= 1e-10) are served one by one in that mode"
-                      if not args.serve_fp64 else "FP64 (complex128) in packed batches",
-                      "split_precision_shapes": len(solo), "shapes": len(server.shapes),
-                      "plans": "autotuned once per shape before the timed loop",
-                      "budget_gb": 150, "resident_gb": (mem["library_bytes"] + mem["reserved_bytes"]) / 2**30,
-                      "budget_counts": "plan tables held by libtk + resident inputs (reserved) + in-flight "
-                                       "outputs and workspaces (reserved at admission)"})
-        serve.update({"load": args.serve_load, "mean_service_ms_alone": 1e3 * mean_s,
-                      "mix": "U(1) L.x at D / SU(2) L.x at D/4, D log-uniform 64-4096 "
-                      "(25-level grid), half complex128, Poisson arrivals"})
-        server.close()
+        serve = run_serving(api, local, dist, rank, args, split=True)
+        if not args.no_serve_fp64:
+            serve_fp64 = run_serving(api, local, dist, rank, args, split=False)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -559,6 +569,8 @@ def run_ours(args):
         line["extra_workloads"] = extra
     if serve is not None:
         line["serve"] = serve
+    if serve_fp64 is not None:
+        line["serve_fp64"] = serve_fp64
     if world == 1 and not args.no_cpu_baseline:
         n, dt, eff, threads, oracle_out = cpu_baseline(args.config, budget_s=args.cpu_budget)
         line["cpu_baseline"] = {"value": flops * n / dt / 1e9, "unit": UNIT, "cores": round(eff, 1),
@@ -599,7 +611,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=10000, help="serving requests (0: skip serving)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic work lists")
     ap.add_argument("--serve-load", type=float, default=0.7, help="offered load relative to alone service time")
-    ap.add_argument("--serve-fp64", action="store_true", help="serve every request in FP64 (no split-precision solo path)")
+    ap.add_argument("--no-serve-fp64", action="store_true", help="skip the FP64-only serving run")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)  # single-thread baseline process
     args = ap.parse_args()
     if args.cpu_worker:
