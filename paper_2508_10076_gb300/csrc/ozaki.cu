@@ -3,9 +3,9 @@
 // C~^c = A~^c B~^c with FP64 operands split into s BF16 slices (Ozaki-style error-free
 // splitting; not part of the paper, which multiplies blocks with BLAS):
 //   * every row m of A~^c gets a power-of-two scale 2^{e_m} > max_k |a_mk| and every column n
-//     of B~^c a scale 2^{f_n}; a_mk 2^{-e_m} is rounded to 7 s fraction bits and written as s
-//     balanced base-128 digits d_0..d_{s-1} (|d_0| <= 128, |d_i| <= 64), slice i holding
-//     d_i 2^{-7(i+1)} exactly in BF16;
+//     of B~^c a scale 2^{f_n}; a_mk 2^{-e_m} is written as s balanced base-128 digits
+//     d_0..d_{s-1} to within 2^-43 + 2^-46 (|d_0| <= 128, |d_1|, |d_2| <= 64, the later ones
+//     below 81), slice i holding d_i 2^{-7(i+1)} exactly in BF16;
 //   * the products A_i B_j with i + j <= s - 1 run as tcgen05.mma kind::f16 (BF16 x BF16, FP32
 //     accumulate in TMEM) into four accumulators by level i + j = 0, 1, 2 and >= 3.  Levels 0..2
 //     are sums of integers times one power of two: per k a level-0 term is at most 128^2 = 2^14
@@ -241,31 +241,6 @@ __device__ __noinline__ double f32_pair_scaled_slow(float hi, float lo, int sc) 
   return scale_pow2_slow(f32_to_f64(hi) + f32_to_f64(lo), sc);
 }
 
-// round(v * 2^shift) to the nearest integer (ties away from zero) from the bit pattern of v; the
-// caller guarantees |v| 2^shift <= 2^62.
-__device__ __forceinline__ long long round_scaled(double v, int shift) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  int e2;
-  if (ex == 0) {
-    if (m == 0) return 0;
-    e2 = -1074;  // subnormal: v = m 2^-1074
-  } else {
-    m |= 1ull << 52;
-    e2 = ex - 1075;  // v = m 2^(ex - 1075)
-  }
-  const int sh = e2 + shift;
-  unsigned long long q;
-  if (sh >= 0)
-    q = m << sh;
-  else if (sh <= -64)
-    q = 0;
-  else
-    q = (m >> (-sh)) + ((m >> (-sh - 1)) & 1ull);
-  return (b >> 63) ? -(long long)q : (long long)q;
-}
-
 // ------------------------------------------------------------------ scale and slice kernels
 // Operand views: A~^c element (m, k) at A[a_off + m + k M]; B~^c element (k, n) at B[b_off + k + n K].
 
@@ -356,100 +331,132 @@ __device__ __forceinline__ void tf32_split(double v, int e, float& hi, float& lo
   lo = __uint_as_float(slo | ((uint32_t)el << 23) | ((uint32_t)(q - 1024) << 13));
 }
 
-// The S balanced base-128 digits of q (|q| <= 2^(7 S)), lowest first as in the 64-bit recurrence
-// d = ((q + 64) mod 128) - 64, q = (q - d) / 128, but in 32-bit arithmetic: the low 7 (S - 4)
-// bits are peeled off first (their carry joins the high part), then the high part fits an int.
-template <int S>
-__device__ __forceinline__ void oz_digits(long long q, int (&d)[S]) {
-  constexpr int NP = S > 4 ? S - 4 : 0;
-  uint32_t L = (uint32_t)(q & ((1ll << (7 * NP)) - 1));
-  int H = (int)(q >> (7 * NP));
-#pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    const int x = (int)((L + 64u) & 127u) - 64;
-    d[S - 1 - j] = x;
-    L = (uint32_t)((int)L - x) >> 7;
-  }
-  H += (int)L;
-#pragma unroll
-  for (int i = S - 1 - NP; i >= 1; --i) {
-    const int x = ((H + 64) & 127) - 64;
-    d[i] = x;
-    H = (H - x) >> 7;
-  }
-  d[0] = H;
+// x = v 2^-e (|x| < 1) as hi + lo: two FP32 numbers holding the top 24 significant bits of x
+// (hi: sign, exponent, 23 stored fraction bits) and the next 23 bits (lo), both exact, formed
+// from the FP64 bit pattern with 32-bit integer operations (lo as a normal FP32 with those bits as
+// its fraction minus the same number with a zero fraction: an exact subtraction).  The last 6
+// fraction bits of v are dropped (< 2^-46 |x|), and so are parts below the FP32 normal range
+// (x < 2^-126, or lo when x < 2^-103): far below the last digit, 2^-42.
+__device__ __forceinline__ void scaled_split(double v, int e, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
+  const int ex = (int)((bh >> 20) & 0x7FFu);
+  const int ef = ex - 1023 - e + 127;  // FP32 exponent field of x
+  hi = lo = 0.f;
+  if (ex == 0 || ef <= 0) return;
+  const uint32_t sign = bh & 0x80000000u;
+  hi = __uint_as_float(sign | ((uint32_t)ef << 23) | ((bh & 0xFFFFFu) << 3) | (bl >> 29));
+  if (ef < 24) return;
+  const uint32_t e2 = (uint32_t)(ef - 23) << 23;  // lo = bits 28..6 of the fraction, 2^-46 units
+  const float l = __fsub_rn(__uint_as_float(e2 | ((bl >> 6) & 0x7FFFFFu)), __uint_as_float(e2));
+  lo = __uint_as_float(__float_as_uint(l) ^ sign);
 }
 
-// Digits of a pair of entries, written as S packed BF16 pairs (slice i holds d_i 2^(-7 (i + 1))).
+// The S balanced base-128 digits d_i of x = hi + lo, x ~ sum_i d_i 2^(-7 (i + 1)), in FP32 on the
+// FMA pipe: with t the remainder (t = hi at first), y = 128 t is exact, d = (y + 1.5 2^23) -
+// 1.5 2^23 rounds y to the nearest integer (|y| <= 128), and t = y - d is exact again, |t| <= 1/2.
+// So |d_0| <= 128 and |d_1|, |d_2| <= 64 (these three make the exact levels 0..2).  After three
+// digits the 24 bits of hi are used up and lo joins the remainder (one rounding, <= 2^-46 of the
+// scale); the later digits (level >= 3 only, an inexact accumulator anyway) stay below 81.  The
+// result is within 2^-43 + 2^-46 of x, every d_i an integer (exact in BF16).
 template <int S>
-__device__ __forceinline__ void oz_slice_pair(double v0, double v1, int e, __nv_bfloat162* dst, int64_t stride2) {
-  int d0[S], d1[S];
-  oz_digits<S>(round_scaled(v0, 7 * S - e), d0);  // round(v 2^(7 S - e)), |q| <= 2^(7 S)
-  oz_digits<S>(round_scaled(v1, 7 * S - e), d1);
+__device__ __forceinline__ void f32_digits(float hi, float lo, float (&d)[S]) {
+  constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
+  float t = hi;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    if (i == 3) t = __fadd_rn(t, __fmul_rn(lo, 2097152.0f));  // lo in the units of the 4th digit (2^21)
+    const float y = __fmul_rn(t, 128.0f);
+    const float di = __fsub_rn(__fadd_rn(y, kRound), kRound);
+    t = __fsub_rn(y, di);
+    d[i] = di;
+  }
+}
+
+// Digits of a pair of entries, written as S packed BF16 pairs (slice i holds d_i 2^(-7 (i + 1))):
+// d_i 2^(-7 (i + 1)) has at most 8 significant bits, so its BF16 pattern is the upper half of its
+// FP32 pattern and two of them pack with one byte permute (no conversion instruction).
+template <int S>
+__device__ __forceinline__ void oz_slice_pair(double v0, double v1, int e, uint32_t* dst, int64_t stride2) {
+  float h0, l0, h1, l1, d0[S], d1[S];
+  scaled_split(v0, e, h0, l0);
+  scaled_split(v1, e, h1, l1);
+  f32_digits<S>(h0, l0, d0);
+  f32_digits<S>(h1, l1, d1);
 #pragma unroll
   for (int sl = 0; sl < S; ++sl) {
     const float sc = __int_as_float((127 - 7 * (sl + 1)) << 23);  // 2^(-7 (sl + 1)), exact
-    dst[sl * stride2] = __floats2bfloat162_rn((float)d0[sl] * sc, (float)d1[sl] * sc);
+    const uint32_t u0 = __float_as_uint(__fmul_rn(d0[sl], sc)), u1 = __float_as_uint(__fmul_rn(d1[sl], sc));
+    dst[sl * stride2] = __byte_perm(u0, u1, 0x7632);  // (u1 >> 16) << 16 | u0 >> 16
   }
 }
 
+// Shared staging of one k-chunk of an A~ tile: buf[kk][r] = x(row r0 + r, k0 + kk), zero outside
+// the sector.  The padding column keeps the row-pair reads below spread over the banks.
+using PrepBuf = double[OZ_BK][OZ_TROWS + 1];
+constexpr size_t OZ_PREP_SMEM = sizeof(PrepBuf);
+
 // One 128 x 32 (rows x k) tile (row tile rt, k-chunk kc) of one operand, all slices, with the
-// rows' scale exponents in esc.  Each thread takes two consecutive k of a row, so a slice of the
-// pair is one packed 32-bit (BF16 pair) or 64-bit (TF32 pair) store and a half-warp writes a full
-// tile row; A~ (column-major, rows contiguous) is staged through shared memory to keep its reads
-// coalesced, B~ (k contiguous) is read directly.  MODE 0 writes s BF16 digit slices, MODE 1 the
+// rows' scale exponents in esc.  Every load of a thread is issued before any arithmetic.  A~
+// (column-major, rows contiguous) is staged through shared memory so that its reads coalesce; B~
+// (k contiguous) is read straight into the slicing layout.  Each thread then takes two consecutive
+// k of 8 rows, so a slice of the pair is one packed 32-bit (BF16 pair) or 64-bit (TF32 pair) store
+// and a half-warp writes a full 64-byte tile row.  MODE 0 writes S BF16 digit slices, MODE 1 the
 // TF32 pair (hi, lo).  Called by all 256 threads of the CTA (it synchronises them).
-template <int MODE>
+template <int MODE, int S>
 __device__ __forceinline__ void slice_tile(const OzPrepSeg& g, const OzSector& s, int op, int64_t rt, int kc,
-                                           const int* esc, double (*xs)[OZ_TROWS + 1], int nslices) {
+                                           const int* esc, PrepBuf& xs) {
+  constexpr int NI = OZ_TROWS / 16;  // rows per thread
   const int64_t R = op == 0 ? s.M : s.N;
   const int64_t r0 = rt * OZ_TROWS, k0 = (int64_t)kc * OZ_BK;
   const int tid = threadIdx.x;
+  const int kp = (tid & 15) * 2, rw = tid >> 4;  // k pair and first row of this thread
+  double v[NI][2];
   if (op == 0) {
+    const int ml = tid & (OZ_TROWS - 1), kk0 = tid >> 7;
+    const bool mok = r0 + ml < R;
+    const double* src = g.A + s.a_off + (r0 + ml) + (k0 + kk0) * s.M;
+    const int64_t step = 2 * s.M;
+    double x[OZ_BK / 2];
+#pragma unroll
+    for (int j = 0; j < OZ_BK / 2; ++j) x[j] = (mok && k0 + kk0 + 2 * j < s.K) ? __ldg(src + j * step) : 0.0;
     __syncthreads();  // the previous tile's readers are done with xs
-    for (int e = tid; e < OZ_TROWS * OZ_BK; e += 256) {
-      const int ml = e & (OZ_TROWS - 1), kk = e / OZ_TROWS;
-      const int64_t m = r0 + ml, k = k0 + kk;
-      xs[kk][ml] = (m < R && k < s.K) ? __ldg(g.A + s.a_off + m + k * s.M) : 0.0;
-    }
+#pragma unroll
+    for (int j = 0; j < OZ_BK / 2; ++j) xs[kk0 + 2 * j][ml] = x[j];
     __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      v[i][0] = xs[kp][rw + 16 * i];
+      v[i][1] = xs[kp + 1][rw + 16 * i];
+    }
+  } else {
+    const int64_t k = k0 + kp;
+    const double* src = g.B + s.b_off + k + (r0 + rw) * s.K;
+    const int64_t step = 16 * s.K;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const bool rok = r0 + rw + 16 * i < R;
+      v[i][0] = (rok && k < s.K) ? __ldg(src + i * step) : 0.0;
+      v[i][1] = (rok && k + 1 < s.K) ? __ldg(src + i * step + 1) : 0.0;
+    }
   }
-  const int kp = (tid & 15) * 2, rw = tid >> 4;  // k pair and row of this thread
   const int64_t nrt = op == 0 ? s.nmt : s.nnt;
   const int64_t tile0 = (op == 0 ? s.ta_base : s.tb_base) + rt * s.nkc + kc;  // slice 0
   const int64_t slice_stride = nrt * s.nkc * (int64_t)(OZ_TROWS * OZ_BK);  // elements
   void* __restrict__ tiles = op == 0 ? g.ta : g.tb;
-#pragma unroll 2
-  for (int i = 0; i < OZ_TROWS / 16; ++i) {
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
     const int rl = rw + 16 * i;
-    const int64_t r = r0 + rl, k = k0 + kp;
-    double v0, v1;
-    if (op == 0) {
-      v0 = xs[kp][rl];
-      v1 = xs[kp + 1][rl];
-    } else {
-      const double* src = g.B + s.b_off + k + r * s.K;
-      v0 = (r < R && k < s.K) ? __ldg(src) : 0.0;
-      v1 = (r < R && k + 1 < s.K) ? __ldg(src + 1) : 0.0;
-    }
     const int e = esc[rl];
     const int64_t at = tile0 * (OZ_TROWS * OZ_BK) + rl * OZ_BK + kp;  // element index of slice 0
     if constexpr (MODE == 0) {
       // at is even and tiles are 1 KB aligned: the pair is a 4-byte aligned store
-      __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(tiles) + at);
-      const int64_t st2 = slice_stride / 2;
-      switch (nslices) {
-        case 2: oz_slice_pair<2>(v0, v1, e, dst, st2); break;
-        case 3: oz_slice_pair<3>(v0, v1, e, dst, st2); break;
-        case 4: oz_slice_pair<4>(v0, v1, e, dst, st2); break;
-        case 5: oz_slice_pair<5>(v0, v1, e, dst, st2); break;
-        case 6: oz_slice_pair<6>(v0, v1, e, dst, st2); break;
-        default: oz_slice_pair<7>(v0, v1, e, dst, st2); break;
-      }
+      uint32_t* dst = reinterpret_cast<uint32_t*>(reinterpret_cast<__nv_bfloat16*>(tiles) + at);
+      oz_slice_pair<S>(v[i][0], v[i][1], e, dst, slice_stride / 2);
     } else {
       float h0, l0, h1, l1;
-      tf32_split(v0, e, h0, l0);
-      tf32_split(v1, e, h1, l1);
+      tf32_split(v[i][0], e, h0, l0);
+      tf32_split(v[i][1], e, h1, l1);
       float2* dst = reinterpret_cast<float2*>(reinterpret_cast<float*>(tiles) + at);
       dst[0] = make_float2(h0, h1);
       dst[slice_stride / 2] = make_float2(l0, l1);
@@ -469,10 +476,11 @@ __device__ __forceinline__ void slice_tile(const OzPrepSeg& g, const OzSector& s
 //   3. Every CTA slices its own k-chunks, re-reading them (now from L2).
 // The operands are read from HBM once instead of twice (a separate scale pass), and the scales
 // need no initial fill.  The first CTA of each request also clears the GEMM's split-K counters.
-template <int MODE, int NSEG>
-__global__ void __cluster_dims__(OZ_PREP_CLUSTER, 1, 1) __launch_bounds__(256)
-    k_oz_prep(const __grid_constant__ OzPrepT<NSEG> P, int nslices) {
-  __shared__ double xs[OZ_BK][OZ_TROWS + 1];
+template <int MODE, int NSEG, int S>
+__global__ void __cluster_dims__(OZ_PREP_CLUSTER, 1, 1) __launch_bounds__(256, 3)
+    k_oz_prep(const __grid_constant__ OzPrepT<NSEG> P) {
+  extern __shared__ __align__(16) unsigned char prep_dyn[];
+  PrepBuf& buf = *reinterpret_cast<PrepBuf*>(prep_dyn);
   __shared__ unsigned long long pmax[OZ_TROWS];  // this CTA's maxima (read by the cluster)
   __shared__ unsigned long long half[OZ_TROWS];
   __shared__ int esc[OZ_TROWS];
@@ -547,7 +555,7 @@ __global__ void __cluster_dims__(OZ_PREP_CLUSTER, 1, 1) __launch_bounds__(256)
   }
   cluster.sync();
   // ---- 3. slices of this CTA's k-chunks
-  for (int kc = kc_lo; kc < kc_hi; ++kc) slice_tile<MODE>(g, s, op, jb.r0, kc, esc, xs, nslices);
+  for (int kc = kc_lo; kc < kc_hi; ++kc) slice_tile<MODE, S>(g, s, op, jb.r0, kc, esc, buf);
 }
 
 // ------------------------------------------------------------------ the persistent GEMM
@@ -1129,11 +1137,24 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
 }
 
 namespace {
+template <typename K>
+bool prep_attr(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_PREP_SMEM) == cudaSuccess;
+}
+template <int NSEG>
+int set_prep_attrs() {
+  return prep_attr(k_oz_prep<1, NSEG, 2>) && prep_attr(k_oz_prep<0, NSEG, 2>) && prep_attr(k_oz_prep<0, NSEG, 3>) &&
+                 prep_attr(k_oz_prep<0, NSEG, 4>) && prep_attr(k_oz_prep<0, NSEG, 5>) &&
+                 prep_attr(k_oz_prep<0, NSEG, 6>) && prep_attr(k_oz_prep<0, NSEG, 7>)
+             ? TK_OK
+             : TK_ERR_CUDA;
+}
 int ensure_smem_attrs(Ctx* ctx) {
   static bool attr_set[64] = {false};
   if (ctx->device < 64 && !attr_set[ctx->device]) {
     if (set_smem_attr<OZ_BN_WIDE, 0>() != TK_OK || set_smem_attr<OZ_BN_NARROW, 0>() != TK_OK ||
-        set_smem_attr<OZ_BN_WIDE, 1>() != TK_OK || set_smem_attr<OZ_BN_NARROW, 1>() != TK_OK) {
+        set_smem_attr<OZ_BN_WIDE, 1>() != TK_OK || set_smem_attr<OZ_BN_NARROW, 1>() != TK_OK ||
+        set_prep_attrs<1>() != TK_OK || set_prep_attrs<OZ_BATCH>() != TK_OK) {
       ctx->last_error = "cannot reserve shared memory for the split-precision GEMM";
       return TK_ERR_CUDA;
     }
@@ -1196,10 +1217,19 @@ int launch_oz_prep(Ctx* ctx, const OzLayout* const* lay, OzPrepT<NSEG>& P, int m
   }
   if (blocks == 0) return TK_OK;
   ProfScope prof(ctx, "k_oz_prep", stream);
-  if (mode == 0)
-    k_oz_prep<0, NSEG><<<(unsigned)blocks, 256, 0, s>>>(P, nslices);
-  else
-    k_oz_prep<1, NSEG><<<(unsigned)blocks, 256, 0, s>>>(P, nslices);
+  const unsigned grid = (unsigned)blocks;
+  if (mode == 1) {
+    k_oz_prep<1, NSEG, 2><<<grid, 256, OZ_PREP_SMEM, s>>>(P);
+  } else {
+    switch (nslices) {
+      case 2: k_oz_prep<0, NSEG, 2><<<grid, 256, OZ_PREP_SMEM, s>>>(P); break;
+      case 3: k_oz_prep<0, NSEG, 3><<<grid, 256, OZ_PREP_SMEM, s>>>(P); break;
+      case 4: k_oz_prep<0, NSEG, 4><<<grid, 256, OZ_PREP_SMEM, s>>>(P); break;
+      case 5: k_oz_prep<0, NSEG, 5><<<grid, 256, OZ_PREP_SMEM, s>>>(P); break;
+      case 6: k_oz_prep<0, NSEG, 6><<<grid, 256, OZ_PREP_SMEM, s>>>(P); break;
+      default: k_oz_prep<0, NSEG, 7><<<grid, 256, OZ_PREP_SMEM, s>>>(P); break;
+    }
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     ctx->last_error = std::string("k_oz_prep launch: ") + cudaGetErrorString(e);
