@@ -261,7 +261,9 @@ int tk_plan_transform(const tk_plan* plan, int which, int64_t k, int64_t* src_of
                       int64_t* dst_offset, double* coef);
 
 /* ---- execution (asynchronous on `stream`, a cudaStream_t; NULL = the context's stream) --------
- * All pointers are device pointers to buffers laid out as the plan's input/output structures.
+ * All pointers are device pointers to buffers laid out as the plan's input/output structures; a
+ * pointer may be NULL only when its structure has no elements (no admissible coupled sector), and
+ * a call whose output has no elements launches nothing.
  * C is fully overwritten.  A and B are never modified.  In the split-precision modes the products
  * left to the CUDA cores run on a second stream owned by the context, forked from `stream` after
  * the input permutes and joined back before the output permute (a fork and a join in a captured
@@ -290,8 +292,9 @@ int tk_contract_batch(tk_ctx* ctx, int n, const tk_plan* const* plans, const voi
  * Algorithm 12).  For t : cod <- dom the SVD is block-wise: t = U S V^dagger with the bond space
  * W = sum_c (c, r_c), r_c = min(rows_c, cols_c) over the coupled sectors c of t, U : cod <- W,
  * V^dagger : W <- dom, and the singular values concatenated by sector (descending within a
- * sector; SU(2) values stand for d_c states each).  Blocks are factorised with cuSOLVER's Jacobi
- * SVD (gesvdj) on a copy in the workspace.
+ * sector; SU(2) values stand for d_c states each).  All blocks are factorised in one launch of a
+ * grouped one-sided (Hestenes) Jacobi kernel, one CTA per block, on copies in the workspace; a map
+ * without blocks is a no-op (its buffers may then be NULL).
  *   tk_svd_plan     plan for t's structure (dtype TK_F64 or TK_C128);
  *   tk_svd_outputs  structures of U and V^dagger (caller frees with tk_tmap_destroy) and the number
  *                   of singular values;
@@ -299,7 +302,8 @@ int tk_contract_batch(tk_ctx* ctx, int n, const tk_plan* const* plans, const voi
  *   tk_svd          t -> U, S, V^dagger (device buffers; workspace of tk_plan_workspace_bytes);
  *   tk_svd_truncate keep[i] (0..min(rows, cols)) leading triplets of block i into the truncated
  *                   U : cod <- W', S, V^dagger : W' <- dom with W' = sum_c (c, keep_c) (sectors with
- *                   keep 0 dropped), all concatenated in sector order. */
+ *                   keep 0 dropped), all concatenated in sector order; with nothing kept it
+ *                   copies nothing and the buffers may be NULL. */
 int tk_svd_plan(tk_ctx* ctx, const tk_tmap* a, int dtype, tk_plan** out);
 int tk_svd_outputs(tk_ctx* ctx, const tk_plan* plan, tk_tmap** u, tk_tmap** vh, int64_t* nvalues);
 int64_t tk_svd_nblocks(const tk_plan* plan);

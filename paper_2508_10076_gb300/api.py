@@ -139,7 +139,7 @@ class Context:
             pass
 
     def sync(self, stream=None):
-        _check(_lib().tk_ctx_sync(self._h, _stream_handle(stream)), self)
+        _check(_lib().tk_ctx_sync(self._h, self._stream(stream)), self)
 
     def _stream(self, stream):
         """Stream handle for a call (host-only contexts: NULL, no torch CUDA query)."""
@@ -178,7 +178,7 @@ class Context:
 
     def selftest_timeout(self, stream=None):
         """Launch the bounded-wait self-test; the next sync() raises TKError (TK_ERR_TIMEOUT)."""
-        h = _stream_handle(stream) if self.device >= 0 else C.c_void_p(0)  # host-only: refused by the library
+        h = self._stream(stream)  # host-only: refused by the library
         _check(_lib().tk_ctx_selftest_timeout(self._h, h), self)
 
     def profile(self, enable=True):
@@ -418,14 +418,14 @@ def svd(ctx, plan, a, u, s, vh, workspace, stream=None):
     """tk_svd: a -> (u, s, vh) device tensors laid out as plan.outputs()."""
     nbytes = workspace.numel() * workspace.element_size()
     _check(_lib().tk_svd(ctx._h, plan._h, _ptr(a), _ptr(u), _ptr(s), _ptr(vh), _ptr(workspace),
-                         C.c_size_t(nbytes), _stream_handle(stream)), ctx)
+                         C.c_size_t(nbytes), ctx._stream(stream)), ctx)
 
 
 def svd_truncate(ctx, plan, keep, u, s, vh, ut, st, vht, stream=None):
     """tk_svd_truncate: keep[i] leading triplets of block i (plan.blocks() order)."""
     arr = (C.c_int64 * max(1, len(keep)))(*[int(k) for k in keep])
     _check(_lib().tk_svd_truncate(ctx._h, plan._h, arr, _ptr(u), _ptr(s), _ptr(vh), _ptr(ut), _ptr(st), _ptr(vht),
-                                  _stream_handle(stream)), ctx)
+                                  ctx._stream(stream)), ctx)
 
 
 def compose_plan(ctx, a, b, dtype="f64", gemm="fp64", slices=0):
@@ -457,13 +457,13 @@ def contract_plan(ctx, a, pa, qa, b, pb, qb, pab, qab, dtype="f64", gemm="fp64",
 
 
 def permute(ctx, plan, a, c, stream=None):
-    _check(_lib().tk_permute(ctx._h, plan._h, _ptr(a), _ptr(c), _stream_handle(stream)), ctx)
+    _check(_lib().tk_permute(ctx._h, plan._h, _ptr(a), _ptr(c), ctx._stream(stream)), ctx)
 
 
 def contract(ctx, plan, a, b, c, workspace=None, stream=None):
     nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(_lib().tk_contract(ctx._h, plan._h, _ptr(a), _ptr(b), _ptr(c), _ptr(workspace),
-                              C.c_size_t(nbytes), _stream_handle(stream)), ctx)
+                              C.c_size_t(nbytes), ctx._stream(stream)), ctx)
 
 
 def contract_batch(ctx, plans, a, b, c, workspaces, stream=None):
@@ -478,7 +478,7 @@ def contract_batch(ctx, plans, a, b, c, workspaces, stream=None):
     ha, hb, hc = vp(*[_ptr(x) for x in a]), vp(*[_ptr(x) for x in b]), vp(*[_ptr(x) for x in c])
     hw = vp(*[_ptr(w) for w in workspaces])
     hn = sz(*[0 if w is None else w.numel() * w.element_size() for w in workspaces])
-    _check(_lib().tk_contract_batch(ctx._h, n, hp, ha, hb, hc, hw, hn, _stream_handle(stream)), ctx)
+    _check(_lib().tk_contract_batch(ctx._h, n, hp, ha, hb, hc, hw, hn, ctx._stream(stream)), ctx)
 
 
 def autotune(ctx, plan, a, b, c, workspace, stream=None):
@@ -487,7 +487,7 @@ def autotune(ctx, plan, a, b, c, workspace, stream=None):
     choice = C.c_int(0)
     nbytes = workspace.numel() * workspace.element_size()
     _check(_lib().tk_plan_autotune(ctx._h, plan._h, _ptr(a), _ptr(b), _ptr(c), _ptr(workspace),
-                                   C.c_size_t(nbytes), _stream_handle(stream), C.byref(choice)), ctx)
+                                   C.c_size_t(nbytes), ctx._stream(stream), C.byref(choice)), ctx)
     return choice.value // 8, choice.value % 8
 
 
@@ -499,23 +499,23 @@ def noalloc_scratch_bytes():
 def contract_noalloc(ctx, plan, a, b, c, stream=None):
     """tk_contract_noalloc: the contraction with its scratch in libtk's built-in device array,
     for callers that cannot allocate device memory (see include/tk.h)."""
-    _check(_lib().tk_contract_noalloc(ctx._h, plan._h, _ptr(a), _ptr(b), _ptr(c), _stream_handle(stream)), ctx)
+    _check(_lib().tk_contract_noalloc(ctx._h, plan._h, _ptr(a), _ptr(b), _ptr(c), ctx._stream(stream)), ctx)
 
 
 def copy_h2d(ctx, dst, src_host_ptr, nbytes, stream=None):
     _check(_lib().tk_copy_h2d(ctx._h, _ptr(dst), C.c_void_p(src_host_ptr), C.c_size_t(nbytes),
-                              _stream_handle(stream)), ctx)
+                              ctx._stream(stream)), ctx)
 
 
 def copy_d2h(ctx, dst_host_ptr, src, nbytes, stream=None):
     _check(_lib().tk_copy_d2h(ctx._h, C.c_void_p(dst_host_ptr), _ptr(src), C.c_size_t(nbytes),
-                              _stream_handle(stream)), ctx)
+                              ctx._stream(stream)), ctx)
 
 
 def probe_fp64_peak(ctx, seconds=1.0, stream=None):
     """tk_probe_fp64_peak: (TFLOP/s of a register-only FP64 FMA loop on every SM, its ms)."""
     tf, ms = C.c_double(), C.c_double()
-    _check(_lib().tk_probe_fp64_peak(ctx._h, C.c_double(seconds), C.byref(tf), C.byref(ms), _stream_handle(stream)), ctx)
+    _check(_lib().tk_probe_fp64_peak(ctx._h, C.c_double(seconds), C.byref(tf), C.byref(ms), ctx._stream(stream)), ctx)
     return tf.value, ms.value
 
 

@@ -47,6 +47,13 @@ int set_device(tk_ctx* ctx) {
 // An execution call given a NULL stream runs on the context's stream.
 void* use_stream(const tk_ctx* ctx, void* stream) { return stream ? stream : ctx->c.stream; }
 
+// A buffer may be NULL only when its tensor map has no elements (nothing is read or written).
+bool have(const void* p, int64_t numel) { return p != nullptr || numel == 0; }
+
+bool operands_present(const tk::ContractPlan& cp, const void* a, const void* b, const void* c) {
+  return have(a, cp.pa->in->numel) && have(b, cp.pb->in->numel) && have(c, cp.c->numel);
+}
+
 }  // namespace
 
 extern "C" {
@@ -597,10 +604,11 @@ int tk_plan_permute_stats(const tk_plan* plan, int which, int64_t* stats) {
 int tk_permute(tk_ctx* ctx, const tk_plan* plan, const void* a, void* c, void* stream) {
   if (ctx) stream = use_stream(ctx, stream);
   if (!ctx || !plan || plan->kind != 0) return fail(ctx, TK_ERR_ARG, "not a permute plan");
-  if (!a || !c) return fail(ctx, TK_ERR_ARG, "null buffer");
+  const tk::PermutePlan& pp = *plan->perm;
+  if (!have(a, pp.in->numel) || !have(c, pp.out->numel)) return fail(ctx, TK_ERR_ARG, "null buffer");
   int rc = set_device(ctx);
   if (rc != TK_OK) return rc;
-  const tk::PermutePlan& pp = *plan->perm;
+  if (pp.out->numel == 0) return TK_OK;  // nothing to write: no launch
   if (pp.identity) {
     size_t bytes = (size_t)pp.in->numel * (pp.dtype == TK_C128 ? 16 : 8);
     if (a == c) return TK_OK;
@@ -615,13 +623,14 @@ int tk_contract(tk_ctx* ctx, const tk_plan* plan, const void* a, const void* b, 
                 void* workspace, size_t workspace_bytes, void* stream) {
   if (ctx) stream = use_stream(ctx, stream);
   if (!ctx || !plan || plan->kind != 1) return fail(ctx, TK_ERR_ARG, "not a contraction plan");
-  if (!a || !b || !c) return fail(ctx, TK_ERR_ARG, "null buffer");
   const tk::ContractPlan& cp = *plan->con;
+  if (!operands_present(cp, a, b, c)) return fail(ctx, TK_ERR_ARG, "null buffer");
   const size_t need = tk::contract_ws_bytes(cp);
   if (workspace_bytes < need || (need > 0 && !workspace))
     return fail(ctx, TK_ERR_WORKSPACE, "workspace smaller than tk_plan_workspace_bytes()");
   int rc = set_device(ctx);
   if (rc != TK_OK) return rc;
+  if (cp.c->numel == 0) return TK_OK;  // nothing to write: no launch
   return tk::run_contract(&ctx->c, cp, a, b, c, workspace, stream);
 }
 
@@ -635,8 +644,8 @@ int tk_contract_batch(tk_ctx* ctx, int n, const tk_plan* const* plans, const voi
   std::vector<const tk::ContractPlan*> cps((size_t)n);
   for (int i = 0; i < n; ++i) {
     if (!plans[i] || plans[i]->kind != 1) return fail(ctx, TK_ERR_ARG, "not a contraction plan");
-    if (!a[i] || !b[i] || !c[i]) return fail(ctx, TK_ERR_ARG, "null buffer");
     const tk::ContractPlan& cp = *plans[i]->con;
+    if (!operands_present(cp, a[i], b[i], c[i])) return fail(ctx, TK_ERR_ARG, "null buffer");
     if (workspace_bytes[i] < cp.ws_total || (cp.ws_total > 0 && !workspace[i]))
       return fail(ctx, TK_ERR_WORKSPACE, "workspace smaller than tk_plan_workspace_bytes()");
     if (cp.gemm_mode != plans[0]->con->gemm_mode || cp.dtype != plans[0]->con->dtype)
@@ -722,10 +731,14 @@ int tk_plan_autotune(tk_ctx* ctx, tk_plan* plan, const void* a, const void* b, v
                      size_t workspace_bytes, void* stream, int* choice) {
   if (ctx) stream = use_stream(ctx, stream);
   if (!ctx || !plan || plan->kind != 1) return fail(ctx, TK_ERR_ARG, "not a contraction plan");
-  if (!a || !b || !c || !workspace) return fail(ctx, TK_ERR_ARG, "null buffer");
+  tk::ContractPlan& cp = *plan->con;
+  if (!operands_present(cp, a, b, c) || !workspace) return fail(ctx, TK_ERR_ARG, "null buffer");
+  if (cp.c->numel == 0) {  // nothing to time: keep the heuristic work lists
+    if (choice) *choice = 0;
+    return TK_OK;
+  }
   int rc = set_device(ctx);
   if (rc != TK_OK) return rc;
-  tk::ContractPlan& cp = *plan->con;
   if (!cp.re) return autotune_contract(ctx, cp, a, b, c, workspace, workspace_bytes, stream, choice);
   // complex split precision: one full run leaves Re A and Re B in the workspace; the real plan
   // is tuned on them (its result buffer is the first real product's), then the total is resized
@@ -793,8 +806,9 @@ int tk_svd(tk_ctx* ctx, const tk_plan* plan, const void* a, void* u, double* s, 
            size_t workspace_bytes, void* stream) {
   if (ctx) stream = use_stream(ctx, stream);
   if (!ctx || !plan || plan->kind != 2) return fail(ctx, TK_ERR_ARG, "not an SVD plan");
-  if (!a || !u || !s || !vh) return fail(ctx, TK_ERR_ARG, "null buffer");
   const tk::SvdPlan& sp = *plan->svd;
+  if (sp.blocks.empty()) return TK_OK;  // a map with no blocks: nothing to factor, no launch
+  if (!a || !u || !s || !vh) return fail(ctx, TK_ERR_ARG, "null buffer");
   if (workspace_bytes < sp.ws_total || !workspace)
     return fail(ctx, TK_ERR_WORKSPACE, "workspace smaller than tk_plan_workspace_bytes()");
   int rc = set_device(ctx);
@@ -806,7 +820,17 @@ int tk_svd(tk_ctx* ctx, const tk_plan* plan, const void* a, void* u, double* s, 
 int tk_svd_truncate(tk_ctx* ctx, const tk_plan* plan, const int64_t* keep, const void* u, const double* s,
                     const void* vh, void* ut, double* st, void* vht, void* stream) {
   if (ctx) stream = use_stream(ctx, stream);
-  if (!ctx || !plan || plan->kind != 2 || !keep) return fail(ctx, TK_ERR_ARG, "not an SVD plan");
+  if (!ctx || !plan || plan->kind != 2) return fail(ctx, TK_ERR_ARG, "not an SVD plan");
+  const size_t nb = plan->svd->blocks.size();
+  if (nb > 0 && !keep) return fail(ctx, TK_ERR_ARG, "null keep counts");
+  int64_t kept = 0;
+  for (size_t i = 0; i < nb; ++i) {
+    if (keep[i] < 0 || keep[i] > plan->svd->blocks[i].r)
+      return fail(ctx, TK_ERR_ARG, "keep count outside 0..min(rows, cols)");
+    kept += keep[i];
+  }
+  if (kept == 0) return TK_OK;  // nothing kept: empty outputs, no copy
+  if (!u || !s || !vh || !ut || !st || !vht) return fail(ctx, TK_ERR_ARG, "null buffer");
   int rc = set_device(ctx);
   if (rc != TK_OK) return rc;
   rc = tk::run_svd_truncate(&ctx->c, *plan->svd, keep, u, s, vh, ut, st, vht, stream);

@@ -64,7 +64,9 @@ extern "C" int tk_contract_noalloc(tk_ctx* ctx, const tk_plan* plan, const void*
     ctx->c.last_error = "not a contraction plan";
     return TK_ERR_ARG;
   }
-  if (!a || !b || !c) {
+  const tk::ContractPlan& cp = *plan->con;
+  // a buffer may be NULL only when its tensor map has no elements
+  if ((!a && cp.pa->in->numel > 0) || (!b && cp.pb->in->numel > 0) || (!c && cp.c->numel > 0)) {
     ctx->c.last_error = "null buffer";
     return TK_ERR_ARG;
   }
@@ -72,7 +74,6 @@ extern "C" int tk_contract_noalloc(tk_ctx* ctx, const tk_plan* plan, const void*
     ctx->c.last_error = "execution call on a host-only context";
     return TK_ERR_NO_DEVICE;
   }
-  const tk::ContractPlan& cp = *plan->con;
   if (tk::contract_ws_bytes(cp) > kNoallocScratchBytes) {
     ctx->c.last_error = "plan needs " + std::to_string(tk::contract_ws_bytes(cp)) +
                         " bytes of scratch; tk_contract_noalloc has " + std::to_string(kNoallocScratchBytes) +
@@ -83,6 +84,7 @@ extern "C" int tk_contract_noalloc(tk_ctx* ctx, const tk_plan* plan, const void*
     ctx->c.last_error = "cudaSetDevice failed";
     return TK_ERR_CUDA;
   }
+  if (cp.c->numel == 0) return TK_OK;  // nothing to write: no launch
   void* scratch = nullptr;
   std::string err;
   int rc = scratch_address(ctx->c.device, &scratch, err);

@@ -84,3 +84,37 @@ def test_noalloc_scratch_size_matches_header():
         m = re.search(r"#define TK_NOALLOC_SCRATCH_BYTES \(\(size_t\)(\d+) << (\d+)\)", fh.read())
     assert m, "TK_NOALLOC_SCRATCH_BYTES not found in tk.h"
     assert api.noalloc_scratch_bytes() == int(m.group(1)) << int(m.group(2))
+
+
+def _empty_and_full(hctx):
+    """t : V1 (x) V2 <- W has no admissible coupled sector (charge 2 against 0), so no elements;
+    u : V1 (x) V2 <- X has one (charge 2)."""
+    v1, v2 = hctx.space("U1", {1: 2}), hctx.space("U1", {1: 3})
+    w, x = hctx.space("U1", {0: 1}), hctx.space("U1", {2: 4})
+    return hctx.tmap([v1, v2], [w]), hctx.tmap([w], [x]), hctx.tmap([v1, v2], [x])
+
+
+def test_null_buffers_only_for_maps_without_elements(hctx):
+    """A NULL buffer passes the argument check exactly when its map has no elements: the host-only
+    context then stops at the device check (TK_ERR_NO_DEVICE), never at the null check."""
+    t, b, u = _empty_and_full(hctx)
+    assert t.numel == 0 and b.numel == 0 and u.numel == 24
+    pe = api.permute_plan(hctx, t, (1, 0), (2,))
+    pf = api.permute_plan(hctx, u, (1, 0), (2,))
+    with pytest.raises(api.TKError) as e:
+        api.permute(hctx, pe, None, None)
+    assert e.value.code == TK_ERR_NO_DEVICE
+    with pytest.raises(api.TKError) as e:
+        api.permute(hctx, pf, None, 4096)
+    assert e.value.code == TK_ERR_ARG
+    cp = api.compose_plan(hctx, t, b)           # C = t o b : V1 (x) V2 <- X, every block zero
+    assert cp.output().numel == 24
+    with pytest.raises(api.TKError) as e:       # A and B may be NULL, C may not
+        api.contract(hctx, cp, None, None, None)
+    assert e.value.code == TK_ERR_ARG
+    with pytest.raises(api.TKError) as e:
+        api.contract(hctx, cp, None, None, 4096)
+    assert cp.workspace_bytes == 0 and e.value.code == TK_ERR_NO_DEVICE
+    with pytest.raises(api.TKError) as e:
+        api.contract_noalloc(hctx, cp, None, None, None)
+    assert e.value.code == TK_ERR_ARG
