@@ -16,8 +16,9 @@
 //     applies 2^{e_m + f_n}.
 // With s = 6 the relative Frobenius error against FP64 is ~1e-12 on N(0,1) data.
 //
-// Data path: one prep launch (clusters of 8 CTAs per 128-row operand tile, the scale maxima
-// exchanged through distributed shared memory) writes the scales and the slices as pre-tiled
+// Data path: one prep launch (clusters of 8 CTAs; a 128-row operand tile takes one to eight of
+// them by its depth, their scale maxima exchanged through distributed shared memory) writes the
+// scales and the slices as pre-tiled
 // 128 x 32 BF16 tiles (64-byte rows); one persistent GEMM launch walks a work list of (sector, 128-row tile,
 // column tile) items, the last column tile of a sector as narrow as its remainder (MMA N a
 // multiple of 16).  Per CTA: warp 0 issues TMA loads (cp.async.bulk.tensor, 64-byte swizzle) of
@@ -84,8 +85,11 @@ struct OzWork {
   int32_t part, nparts, slot, pad;  // split-K: part index, parts of the tile, tile slot (-1: no split)
 };
 constexpr int OZ_MAX_PARTS = 4;
-struct OzJob {  // k_oz_prep job: one 128-row tile (r0) of one operand of one sector
-  int32_t sector, operand, r0, kc;
+struct OzJob {  // the work of one k_oz_prep CTA: its share of one 128-row tile of one operand
+  int32_t sector;         // -1: an idle CTA (pads a request's list to whole clusters)
+  int32_t operand;        // 0: rows of A~, 1: columns of B~
+  int32_t r0;             // row tile
+  int16_t gbase, gsize;   // ranks [gbase, gbase + gsize) of the cluster share the tile
 };
 struct OzPairs {
   int8_t i[OZ_MAX_PAIRS], j[OZ_MAX_PAIRS], lvl[OZ_MAX_PAIRS];
@@ -101,10 +105,10 @@ struct OzLayout {
   int mode = 0;           // 0: Ozaki BF16 slices, 1: 3xTF32
   int bn = OZ_BN_NARROW;  // output tile width of this launch
   OzPairs pairs;
-  int64_t nwork = 0, nprep_jobs = 0;
+  int64_t nwork = 0, nprep_ctas = 0;
   OzSector* d_sectors = nullptr;
   OzWork* d_work = nullptr;
-  OzJob* d_prep_jobs = nullptr;  // one per 128-row tile of each operand: a k_oz_prep cluster each
+  OzJob* d_prep_jobs = nullptr;  // one per k_oz_prep CTA, a multiple of OZ_PREP_CLUSTER
   std::vector<int32_t> cta_work;   // work of CTA b: work[cta_work[b] .. cta_work[b + 1])
   int32_t* d_cta_work = nullptr;
   int ncta = 0;
@@ -352,23 +356,29 @@ __device__ __forceinline__ void scaled_split(double v, int e, float& hi, float& 
   lo = __uint_as_float(__float_as_uint(l) ^ sign);
 }
 
-// The S balanced base-128 digits d_i of x = hi + lo, x ~ sum_i d_i 2^(-7 (i + 1)), in FP32 on the
-// FMA pipe: with t the remainder (t = hi at first), y = 128 t is exact, d = (y + 1.5 2^23) -
+// The S balanced base-128 digits d_i of x = hi + lo, x ~ sum_i d_i 2^(-7 (i + 1)), in FP32 for two
+// entries at once (paired FP32 instructions, each half rounded on its own as a scalar operation
+// would be): with t the remainder (t = hi at first), y = 128 t is exact, d = (y + 1.5 2^23) -
 // 1.5 2^23 rounds y to the nearest integer (|y| <= 128), and t = y - d is exact again, |t| <= 1/2.
 // So |d_0| <= 128 and |d_1|, |d_2| <= 64 (these three make the exact levels 0..2).  After three
-// digits the 24 bits of hi are used up and lo joins the remainder (one rounding, <= 2^-46 of the
-// scale); the later digits (level >= 3 only, an inexact accumulator anyway) stay below 81.  The
-// result is within 2^-43 + 2^-46 of x, every d_i an integer (exact in BF16).
+// digits the 24 bits of hi are used up and lo joins the remainder (lo 2^21 is exact, so the fused
+// multiply-add rounds once, <= 2^-46 of the scale); the later digits (level >= 3 only, an inexact
+// accumulator anyway) stay below 81.  The result is within 2^-43 + 2^-46 of x, every d_i an
+// integer (exact in BF16).
 template <int S>
-__device__ __forceinline__ void f32_digits(float hi, float lo, float (&d)[S]) {
-  constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
-  float t = hi;
+__device__ __forceinline__ void f32_digits2(float2 hi, float2 lo, float2 (&d)[S]) {
+  const float2 k128 = make_float2(128.0f, 128.0f);
+  const float2 kRound = make_float2(12582912.0f, 12582912.0f);  // 1.5 * 2^23
+  const float2 kNegRound = make_float2(-12582912.0f, -12582912.0f);
+  const float2 kNegOne = make_float2(-1.0f, -1.0f);
+  const float2 kLo = make_float2(2097152.0f, 2097152.0f);  // lo in the units of the 4th digit (2^21)
+  float2 t = hi;
 #pragma unroll
   for (int i = 0; i < S; ++i) {
-    if (i == 3) t = __fadd_rn(t, __fmul_rn(lo, 2097152.0f));  // lo in the units of the 4th digit (2^21)
-    const float y = __fmul_rn(t, 128.0f);
-    const float di = __fsub_rn(__fadd_rn(y, kRound), kRound);
-    t = __fsub_rn(y, di);
+    if (i == 3) t = __ffma2_rn(lo, kLo, t);
+    const float2 y = __fmul2_rn(t, k128);
+    const float2 di = __fadd2_rn(__fadd2_rn(y, kRound), kNegRound);
+    t = __ffma2_rn(di, kNegOne, y);  // y - d, exact
     d[i] = di;
   }
 }
@@ -378,16 +388,16 @@ __device__ __forceinline__ void f32_digits(float hi, float lo, float (&d)[S]) {
 // FP32 pattern and two of them pack with one byte permute (no conversion instruction).
 template <int S>
 __device__ __forceinline__ void oz_slice_pair(double v0, double v1, int e, uint32_t* dst, int64_t stride2) {
-  float h0, l0, h1, l1, d0[S], d1[S];
+  float h0, l0, h1, l1;
+  float2 d[S];
   scaled_split(v0, e, h0, l0);
   scaled_split(v1, e, h1, l1);
-  f32_digits<S>(h0, l0, d0);
-  f32_digits<S>(h1, l1, d1);
+  f32_digits2<S>(make_float2(h0, h1), make_float2(l0, l1), d);
 #pragma unroll
   for (int sl = 0; sl < S; ++sl) {
     const float sc = __int_as_float((127 - 7 * (sl + 1)) << 23);  // 2^(-7 (sl + 1)), exact
-    const uint32_t u0 = __float_as_uint(__fmul_rn(d0[sl], sc)), u1 = __float_as_uint(__fmul_rn(d1[sl], sc));
-    dst[sl * stride2] = __byte_perm(u0, u1, 0x7632);  // (u1 >> 16) << 16 | u0 >> 16
+    const float2 u = __fmul2_rn(d[sl], make_float2(sc, sc));
+    dst[sl * stride2] = __byte_perm(__float_as_uint(u.x), __float_as_uint(u.y), 0x7632);  // (y >> 16) << 16 | x >> 16
   }
 }
 
@@ -464,15 +474,16 @@ __device__ __forceinline__ void slice_tile(const OzPrepSeg& g, const OzSector& s
   }
 }
 
-// Scale and slice in one launch.  A cluster of OZ_PREP_CLUSTER CTAs owns one 128-row tile of one
-// operand (rows of A~^c, columns of B~^c) and splits its k-chunks evenly among its CTAs.
+// Scale and slice in one launch.  A group of g CTAs of one cluster (g = min(k-chunks, 8), several
+// groups per cluster when g < 8) owns one 128-row tile of one operand (rows of A~^c, columns of
+// B~^c) and splits its k-chunks evenly among its CTAs.
 //   1. Every CTA takes the maximum |x| of each of the 128 rows over its k-chunks (as FP64 bit
 //      patterns, ordered as unsigned integers: no FP64 instruction).
-//   2. After a cluster barrier every CTA reads the 8 partial maxima of its rows from the other CTAs'
+//   2. After a cluster barrier every CTA reads the g partial maxima of its rows from its group's
 //      shared memory (distributed shared memory), so all of them hold the row's power-of-two
-//      scale 2^e > max_k |x| (the exponent of a maximum is the maximum of the exponents); rank 0
-//      writes it for the GEMM's epilogue.  A second cluster barrier keeps every CTA's shared
-//      memory alive until the others have read it.
+//      scale 2^e > max_k |x| (the exponent of a maximum is the maximum of the exponents); the
+//      group's first CTA writes it for the GEMM's epilogue.  A second cluster barrier keeps every
+//      CTA's shared memory alive until the others have read it.
 //   3. Every CTA slices its own k-chunks, re-reading them (now from L2).
 // The operands are read from HBM once instead of twice (a separate scale pass), and the scales
 // need no initial fill.  The first CTA of each request also clears the GEMM's split-K counters.
@@ -491,13 +502,19 @@ __global__ void __cluster_dims__(OZ_PREP_CLUSTER, 1, 1) __launch_bounds__(256, 3
   const int tid = threadIdx.x;
   if (local == 0)  // the GEMM's split-K arrival counters start at zero
     for (int i = tid; i < g.ncounters; i += blockDim.x) g.counters[i] = 0;
-  const OzJob jb = g.jobs[local / OZ_PREP_CLUSTER];
+  const OzJob jb = g.jobs[local];
+  if (jb.sector < 0) {  // an idle rank: it only takes part in the cluster's two barriers
+    cluster.sync();
+    cluster.sync();
+    return;
+  }
   const OzSector s = g.secs[jb.sector];
   const int op = jb.operand;
   const int64_t R = op == 0 ? s.M : s.N;
   const int64_t r0 = (int64_t)jb.r0 * OZ_TROWS;
-  const int kc_lo = (int)((int64_t)rank * s.nkc / OZ_PREP_CLUSTER);
-  const int kc_hi = (int)((int64_t)(rank + 1) * s.nkc / OZ_PREP_CLUSTER);
+  const int gr = rank - jb.gbase, gs = jb.gsize;  // this CTA's rank in its group, the group's size
+  const int kc_lo = (int)((int64_t)gr * s.nkc / gs);
+  const int kc_hi = (int)((int64_t)(gr + 1) * s.nkc / gs);
   const int64_t k_lo = (int64_t)kc_lo * OZ_BK, k_hi = min(s.K, (int64_t)kc_hi * OZ_BK);
   constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
   // ---- 1. partial maxima over this CTA's k range
@@ -546,11 +563,11 @@ __global__ void __cluster_dims__(OZ_PREP_CLUSTER, 1, 1) __launch_bounds__(256, 3
   // ---- 2. the cluster's maxima -> the rows' scale exponents
   cluster.sync();
   if (tid < OZ_TROWS) {
-    unsigned long long mb = 0;
-#pragma unroll
-    for (int q = 0; q < OZ_PREP_CLUSTER; ++q) mb = max(mb, *cluster.map_shared_rank(&pmax[tid], q));
+    unsigned long long mb = pmax[tid];
+    for (int q = 0; q < gs; ++q)
+      if (q != gr) mb = max(mb, *cluster.map_shared_rank(&pmax[tid], jb.gbase + q));
     const int e = exponent_of(__longlong_as_double((long long)mb));
-    if (rank == 0 && r0 + tid < R) (op == 0 ? g.sa + s.sa_off : g.sb + s.sb_off)[r0 + tid] = e;
+    if (gr == 0 && r0 + tid < R) (op == 0 ? g.sa + s.sa_off : g.sb + s.sb_off)[r0 + tid] = e;
     esc[tid] = e == kNoScale ? 0 : e;  // an all-zero row or column slices to zeros with any scale
   }
   cluster.sync();
@@ -966,6 +983,44 @@ int set_smem_attr() {
 
 size_t al1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
 
+// The k_oz_prep CTAs of one request.  A tile nkc k-chunks deep takes g = min(nkc, 8) CTAs of one
+// cluster (at least one k-chunk each): a shallow tile spread over a whole cluster would leave most
+// of its CTAs without work, and the launch would run in many short waves.  Tiles go into clusters
+// of OZ_PREP_CLUSTER CTAs deepest first, each into the open cluster with the least room that still
+// holds it (best fit decreasing); the ranks a cluster leaves free become idle entries.
+std::vector<OzJob> pack_prep_tiles(std::vector<OzJob> tiles) {
+  std::stable_sort(tiles.begin(), tiles.end(), [](const OzJob& a, const OzJob& b) { return a.gsize > b.gsize; });
+  std::vector<std::vector<OzJob>> clusters;
+  std::vector<int> used;
+  std::vector<int> open[OZ_PREP_CLUSTER];  // open[r]: clusters with r free ranks, 0 < r < OZ_PREP_CLUSTER
+  for (OzJob t : tiles) {
+    int c = -1;
+    for (int r = t.gsize; r < OZ_PREP_CLUSTER && c < 0; ++r)
+      if (!open[r].empty()) {
+        c = open[r].back();
+        open[r].pop_back();
+      }
+    if (c < 0) {
+      c = (int)clusters.size();
+      clusters.emplace_back();
+      used.push_back(0);
+    }
+    t.gbase = (int16_t)used[(size_t)c];
+    clusters[(size_t)c].push_back(t);
+    used[(size_t)c] += t.gsize;
+    const int left = OZ_PREP_CLUSTER - used[(size_t)c];
+    if (left > 0) open[left].push_back(c);
+  }
+  std::vector<OzJob> ctas;
+  ctas.reserve(clusters.size() * OZ_PREP_CLUSTER);
+  for (size_t c = 0; c < clusters.size(); ++c) {
+    for (const OzJob& t : clusters[c])
+      for (int q = 0; q < t.gsize; ++q) ctas.push_back(t);
+    for (int q = used[c]; q < OZ_PREP_CLUSTER; ++q) ctas.push_back(OzJob{-1, 0, 0, 0, 1});
+  }
+  return ctas;
+}
+
 }  // namespace
 
 int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
@@ -990,7 +1045,7 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
         ++P.n;
       }
   std::vector<OzWork> work;
-  std::vector<OzJob> prep_jobs;
+  std::vector<OzJob> prep_jobs, prep_tiles;
   std::vector<std::pair<double, OzWork>> wcost;
   // Tile width: measured in this kernel, a 128 x 64 x 16 MMA takes ~72 cycles and a 128 x 128 x 16
   // one ~65 (the full rate), so 128-column tiles do nearly twice the work per cycle; but they hold
@@ -1044,10 +1099,12 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
         t.nw = nw;
         wcost.push_back({(double)s.nkc, t});
       }
-    // one prep cluster per 128-row tile of A~ and per 128-column tile of B~
-    for (int rt = 0; rt < s.nmt; ++rt) prep_jobs.push_back(OzJob{sid, 0, rt, 0});
-    for (int rt = 0; rt < s.nnt; ++rt) prep_jobs.push_back(OzJob{sid, 1, rt, 0});
+    // the prep tiles: every 128-row tile of A~ and 128-column tile of B~, with its depth
+    const int16_t gsz = (int16_t)std::min(s.nkc, OZ_PREP_CLUSTER);
+    for (int rt = 0; rt < s.nmt; ++rt) prep_tiles.push_back(OzJob{sid, 0, rt, 0, gsz});
+    for (int rt = 0; rt < s.nnt; ++rt) prep_tiles.push_back(OzJob{sid, 1, rt, 0, gsz});
   }
+  prep_jobs = pack_prep_tiles(prep_tiles);
   std::stable_sort(wcost.begin(), wcost.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
   // Split-K: a launch with fewer than two tiles per SM cuts deep tiles into up to OZ_MAX_PARTS
   // parts (at least 8 k-chunks each); their FP64 partial tiles are added in part order by the
@@ -1112,7 +1169,7 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
     work.swap(ordered);
   }
   L->nwork = (int64_t)work.size();
-  L->nprep_jobs = (int64_t)prep_jobs.size();
+  L->nprep_ctas = (int64_t)prep_jobs.size();
   // workspace layout: A tiles | B tiles | row scales | column scales | split-K partial tiles
   L->off_ta = 0;
   L->off_tb = al1k((size_t)L->ntiles_a * tile_bytes);
@@ -1213,7 +1270,7 @@ int launch_oz_prep(Ctx* ctx, const OzLayout* const* lay, OzPrepT<NSEG>& P, int m
   for (int i = 0; i < P.nseg; ++i) {  // every segment starts on a cluster boundary
     P.seg[i].block0 = blocks;
     P.seg[i].jobs = lay[i]->d_prep_jobs;
-    blocks += lay[i]->nprep_jobs * OZ_PREP_CLUSTER;
+    blocks += lay[i]->nprep_ctas;
   }
   if (blocks == 0) return TK_OK;
   ProfScope prof(ctx, "k_oz_prep", stream);
