@@ -229,17 +229,27 @@ __host__ __device__ constexpr uint32_t idesc_mma(int m, int n) {
 
 __device__ __noinline__ double scale_pow2_slow(double v, int e) { return ldexp(v, e); }
 
-// f * 2^sc as FP64, built from the FP32 bit pattern by adding sc to the exponent field: exact.
-// ok is cleared when f is neither zero nor normal or the result leaves the normal FP64 range.
-__device__ __forceinline__ double f32_scaled_to_f64(float f, int sc, bool& ok) {
-  const uint32_t u = __float_as_uint(f);
-  const int ex = (int)((u >> 23) & 0xFFu);
-  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-  if ((u << 1) == 0u) return __longlong_as_double((long long)sign);
-  const int e64 = ex + 896 + sc;
-  ok = ok && ex != 0 && ex != 0xFF && e64 > 0 && e64 < 0x7FF;
-  return __longlong_as_double(
-      (long long)(sign | ((unsigned long long)(e64 & 0x7FF) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+// The FP64 value of a normal FP32 bit pattern u times 2^sc, kexp = (896 + sc) << 20, with 32-bit
+// operations only: the high word is u's sign | ((u without its sign) >> 3) + kexp (the exponent
+// rebiased by 1023 - 127 and raised by sc, the top 20 fraction bits below it), the low word the last
+// 3 fraction bits.
+__device__ __forceinline__ double f32_bits_scaled(uint32_t u, uint32_t kexp) {
+  return __hiloint2double((int)((u & 0x80000000u) | (((u & 0x7FFFFFFFu) >> 3) + kexp)), (int)(u << 29));
+}
+
+// (hi + lo) 2^sc in FP64 for a two-sum pair (|lo| <= ulp(hi) / 2): both converted with a handful of
+// 32-bit integer operations and added by one FP64 add (the epilogue is bound by the integer pipe
+// first, then by that add).  hi must be normal and sc in [-895, 2045 - hi's exponent field], which
+// keeps both scaled exponents inside the normal FP64 range; lo with a zero exponent field (zero, or
+// an FP32 subnormal: far below hi's last place) counts as zero.  Anything else clears ok, and the
+// caller takes the exact slow path.
+__device__ __forceinline__ double f32_pair_scaled(float hi, float lo, int sc, bool& ok) {
+  const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
+  const uint32_t eh = (uh >> 23) & 0xFFu;
+  ok = (eh - 1u) < 254u && (uint32_t)(sc + 895) <= (uint32_t)(2045 - (int)eh);
+  const uint32_t kexp = (uint32_t)(896 + sc) << 20;
+  const double dl = (ul & 0x7F800000u) ? f32_bits_scaled(ul, kexp) : 0.0;
+  return f32_bits_scaled(uh, kexp) + dl;
 }
 __device__ __noinline__ double f32_pair_scaled_slow(float hi, float lo, int sc) {
   return scale_pow2_slow(f32_to_f64(hi) + f32_to_f64(lo), sc);
@@ -838,8 +848,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               tc_ld8(lane_addr + 2 * BN + ch * 8, r2);
               tc_ld8(lane_addr + 3 * BN + ch * 8, r3);
               tc_wait_ld();
-              // level sums, two columns per instruction: hi + lo = r0 + r1 + r2 (exact levels, the
-              // FP32 rounding of the last two-sum kept in lo) with the inexact level r3 added to lo
+              // level sums, two columns per instruction: hi + lo = r0 + r1 + r2 + r3, the exact
+              // levels' two-sum remainders and the inexact level r3 gathered in lo, and a last
+              // two-sum leaving |lo| <= ulp(hi) / 2 for the conversion below
               float hv[8], lv[8];
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
@@ -848,12 +859,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 const float2 x1 = has1 ? make_float2(__uint_as_float(r1[2 * q]), __uint_as_float(r1[2 * q + 1])) : z;
                 const float2 x2 = has2 ? make_float2(__uint_as_float(r2[2 * q]), __uint_as_float(r2[2 * q + 1])) : z;
                 const float2 x3 = has3 ? make_float2(__uint_as_float(r3[2 * q]), __uint_as_float(r3[2 * q + 1])) : z;
-                float2 hi, lo, e1, e2;
+                float2 hi, lo, e1;
                 two_sum2(x0, x1, hi, lo);
                 two_sum2(hi, x2, hi, e1);
-                lo = __fadd2_rn(lo, e1);
-                two_sum2(hi, lo, hi, e2);
-                lo = __fadd2_rn(e2, x3);
+                lo = __fadd2_rn(__fadd2_rn(lo, e1), x3);
+                two_sum2(hi, lo, hi, lo);
                 hv[2 * q] = hi.x;
                 hv[2 * q + 1] = hi.y;
                 lv[2 * q] = lo.x;
@@ -865,9 +875,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 const int fn = __shfl_sync(0xffffffffu, fl, ch * 8 + j);
                 if (!row_ok || ch * 8 + j >= ncols) continue;
                 const float hi = hv[j], lo = lv[j];
-                bool ok = true;
+                bool ok;
                 const int sc = em + fn;
-                double v = f32_scaled_to_f64(hi, sc, ok) + f32_scaled_to_f64(lo, sc, ok);
+                double v = f32_pair_scaled(hi, lo, sc, ok);
                 if (!ok) v = f32_pair_scaled_slow(hi, lo, sc);
                 *dst = (kc0 == wk.kc_lo) ? v : *dst + v;
               }
