@@ -906,39 +906,43 @@ namespace {
 // Segments (runs and tiles) of the non-identity permutes among jobs, with their natural block counts.
 void perm_segments(const PermJob* jobs, int njobs, std::vector<PermSeg>& segs, std::vector<int64_t>& natural,
                    int& dtype) {
-  for (int j = 0; j < njobs; ++j) {
-    const PermutePlan& pp = *jobs[j].plan;
-    if (pp.identity) continue;
-    dtype = pp.dtype;
-    if (!pp.runs.empty()) {
-      PermSeg g;
-      std::memset(&g, 0, sizeof(g));
-      g.kind = 0;
-      g.group = pp.dtype == TK_C128 ? 32 : pp.run_group;
-      g.nwork = (int64_t)pp.runs.size();
-      g.runs = pp.d_runs;
-      g.tasks = pp.d_rtasks;
-      g.srcs = pp.d_srcs;
-      g.in = jobs[j].in;
-      g.out = jobs[j].out;
-      segs.push_back(g);
-      const int64_t per_block = 256 / g.group;  // runs in flight per block
-      natural.push_back((g.nwork + per_block - 1) / per_block);
+  // Tile segments first: blocks start in index order, and a launch holds about two waves of them,
+  // so the transposes (the slower work per block) start in the first wave and the runs fill in
+  // around them instead of queueing the transposes behind every run.
+  for (int pass = 0; pass < 2; ++pass)
+    for (int j = 0; j < njobs; ++j) {
+      const PermutePlan& pp = *jobs[j].plan;
+      if (pp.identity) continue;
+      dtype = pp.dtype;
+      if (pass == 1 && !pp.runs.empty()) {
+        PermSeg g;
+        std::memset(&g, 0, sizeof(g));
+        g.kind = 0;
+        g.group = pp.dtype == TK_C128 ? 32 : pp.run_group;
+        g.nwork = (int64_t)pp.runs.size();
+        g.runs = pp.d_runs;
+        g.tasks = pp.d_rtasks;
+        g.srcs = pp.d_srcs;
+        g.in = jobs[j].in;
+        g.out = jobs[j].out;
+        segs.push_back(g);
+        const int64_t per_block = 256 / g.group;  // runs in flight per block
+        natural.push_back((g.nwork + per_block - 1) / per_block);
+      }
+      if (pass == 0 && !pp.tasks.empty() && pp.total_tiles > 0) {
+        PermSeg g;
+        std::memset(&g, 0, sizeof(g));
+        g.kind = 1;
+        g.nwork = pp.total_tiles;
+        g.tasks = pp.d_tasks;
+        g.tile_task = pp.d_tile_task;
+        g.srcs = pp.d_srcs;
+        g.in = jobs[j].in;
+        g.out = jobs[j].out;
+        segs.push_back(g);
+        natural.push_back(g.nwork);
+      }
     }
-    if (!pp.tasks.empty() && pp.total_tiles > 0) {
-      PermSeg g;
-      std::memset(&g, 0, sizeof(g));
-      g.kind = 1;
-      g.nwork = pp.total_tiles;
-      g.tasks = pp.d_tasks;
-      g.tile_task = pp.d_tile_task;
-      g.srcs = pp.d_srcs;
-      g.in = jobs[j].in;
-      g.out = jobs[j].out;
-      segs.push_back(g);
-      natural.push_back(g.nwork);
-    }
-  }
 }
 
 // Blocks per segment: natural counts, or a share of 8 blocks per SM in proportion to the work when
