@@ -229,27 +229,31 @@ __host__ __device__ constexpr uint32_t idesc_mma(int m, int n) {
 
 __device__ __noinline__ double scale_pow2_slow(double v, int e) { return ldexp(v, e); }
 
-// The FP64 value of a normal FP32 bit pattern u times 2^sc, kexp = (896 + sc) << 20, with 32-bit
-// operations only: the high word is u's sign | ((u without its sign) >> 3) + kexp (the exponent
-// rebiased by 1023 - 127 and raised by sc, the top 20 fraction bits below it), the low word the last
-// 3 fraction bits.
-__device__ __forceinline__ double f32_bits_scaled(uint32_t u, uint32_t kexp) {
-  return __hiloint2double((int)((u & 0x80000000u) | (((u & 0x7FFFFFFFu) >> 3) + kexp)), (int)(u << 29));
-}
-
-// (hi + lo) 2^sc in FP64 for a two-sum pair (|lo| <= ulp(hi) / 2): both converted with a handful of
-// 32-bit integer operations and added by one FP64 add (the epilogue is bound by the integer pipe
-// first, then by that add).  hi must be normal and sc in [-895, 2045 - hi's exponent field], which
-// keeps both scaled exponents inside the normal FP64 range; lo with a zero exponent field (zero, or
-// an FP32 subnormal: far below hi's last place) counts as zero.  Anything else clears ok, and the
-// caller takes the exact slow path.
+// (hi + lo) 2^sc in FP64 for a two-sum pair (|lo| <= ulp(hi) / 2), with no FP64 instruction (the
+// FP64 pipe retires two lanes per SM per clock here, and one add per output bounded this
+// epilogue).  hi's FP64 words come from its bits with 32-bit operations: the high word is hi's
+// sign | ((hi's bits without the sign) >> 3) + (896 + sc) << 20 (exponent rebiased by 1023 - 127
+// and raised by sc), the low word its last 3 fraction bits.  lo then moves that pattern by a whole
+// number of last places of the result's binade: |lo| times 2^(179 - e_hi) (exact in FP32, at most
+// 2^29) rounded to the nearest integer, added when lo has hi's sign and subtracted otherwise; when
+// hi is a power of two and lo has the other sign the result lies one binade lower, where a last
+// place is half as large, so the count is taken at twice the scale.  Adding to the pattern crosses
+// into that binade by itself.  hi must have an FP32 exponent field in [53, 253] (the scale 2^(179 -
+// e_hi), or twice it, is then a normal FP32) and sc in [-895, 2045 - e_hi] (both results normal in
+// FP64); anything else clears ok and the caller takes the exact slow path.
+template <bool SAFE_SC>
 __device__ __forceinline__ double f32_pair_scaled(float hi, float lo, int sc, bool& ok) {
   const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
   const uint32_t eh = (uh >> 23) & 0xFFu;
-  ok = (eh - 1u) < 254u && (uint32_t)(sc + 895) <= (uint32_t)(2045 - (int)eh);
-  const uint32_t kexp = (uint32_t)(896 + sc) << 20;
-  const double dl = (ul & 0x7F800000u) ? f32_bits_scaled(ul, kexp) : 0.0;
-  return f32_bits_scaled(uh, kexp) + dl;
+  // SAFE_SC: the caller knows |sc| <= 896, which with e_hi in [53, 253] keeps both results normal
+  ok = (eh - 53u) < 201u && (SAFE_SC || (uint32_t)(sc + 895) <= (uint32_t)(2045 - (int)eh));
+  const uint32_t whi = (uh & 0x80000000u) | (((uh & 0x7FFFFFFFu) >> 3) + ((uint32_t)(896 + sc) << 20));
+  const uint32_t against = (uh ^ ul) >> 31;
+  const uint32_t below = against & (uint32_t)((uh & 0x7FFFFFu) == 0u);
+  const float scale = __uint_as_float((306u - eh + below) << 23);  // 2^(179 - e_hi + below)
+  const int off = __float2int_rn(__fmul_rn(fabsf(lo), scale));
+  const long long bits = (long long)(((unsigned long long)whi << 32) | (uh << 29));
+  return __longlong_as_double(bits + (against ? -(long long)off : (long long)off));
 }
 __device__ __noinline__ double f32_pair_scaled_slow(float hi, float lo, int sc) {
   return scale_pow2_slow(f32_to_f64(hi) + f32_to_f64(lo), sc);
@@ -797,6 +801,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int row = quad * 32 + lane;
     // accumulators of levels without any slice pair (fewer than 4 slices) are never written
     const bool has1 = pairs.first[1] >= 0, has2 = pairs.first[2] >= 0, has3 = pairs.first[3] >= 0;
+    const bool all_levels = has1 && has2 && has3;
     uint32_t seg = 0;
     for (int r = 0; r < L.nreq && !*abort_flag; ++r) {
       const OzReq& R = L.req[r];
@@ -823,6 +828,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int ncols = left < WCOLS ? (int)left : WCOLS;  // valid columns of this warp (may be <= 0)
         int fl = (lane < ncols) ? scale_b[s.sb_off + nb + lane] : 0;  // WCOLS <= 32: one per lane
         if (fl == kNoScale) fl = 0;
+        const bool fast = all_levels && __all_sync(0xffffffffu, em >= -448 && em <= 448 && fl >= -448 && fl <= 448);
         // a split tile's parts go to its partial buffers (column-major 128 x BN, one per part)
         const bool split = wk.nparts > 1;
         double* const pbase = split ? partials + (int64_t)wk.slot * OZ_MAX_PARTS * (OZ_BM * BN) : nullptr;
@@ -839,9 +845,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           tc_fence_after();
           if (active) {
             const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + buf * (OZ_NACC * BN) + c0;
-#pragma unroll 1
-            for (int ch = 0; ch < WCOLS / 8; ++ch) {
-              if (ch * 8 >= ncols) break;  // warp-uniform
+            // one chunk of eight columns; FAST: every level accumulator was written (four or more
+            // slices) and every row and column scale of this warp is within +-448, so no level
+            // is masked and no output can leave the normal FP64 range through its scale
+            auto chunk = [&](auto fast_tag, int ch) {
+              constexpr bool FAST = decltype(fast_tag)::value;
               uint32_t r0[8], r1[8], r2[8], r3[8];
               tc_ld8(lane_addr + 0 * BN + ch * 8, r0);
               tc_ld8(lane_addr + 1 * BN + ch * 8, r1);
@@ -856,9 +864,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               for (int q = 0; q < 4; ++q) {
                 const float2 z = make_float2(0.f, 0.f);
                 const float2 x0 = make_float2(__uint_as_float(r0[2 * q]), __uint_as_float(r0[2 * q + 1]));
-                const float2 x1 = has1 ? make_float2(__uint_as_float(r1[2 * q]), __uint_as_float(r1[2 * q + 1])) : z;
-                const float2 x2 = has2 ? make_float2(__uint_as_float(r2[2 * q]), __uint_as_float(r2[2 * q + 1])) : z;
-                const float2 x3 = has3 ? make_float2(__uint_as_float(r3[2 * q]), __uint_as_float(r3[2 * q + 1])) : z;
+                const float2 y1 = make_float2(__uint_as_float(r1[2 * q]), __uint_as_float(r1[2 * q + 1]));
+                const float2 y2 = make_float2(__uint_as_float(r2[2 * q]), __uint_as_float(r2[2 * q + 1]));
+                const float2 y3 = make_float2(__uint_as_float(r3[2 * q]), __uint_as_float(r3[2 * q + 1]));
+                const float2 x1 = (FAST || has1) ? y1 : z;
+                const float2 x2 = (FAST || has2) ? y2 : z;
+                const float2 x3 = (FAST || has3) ? y3 : z;
                 float2 hi, lo, e1;
                 two_sum2(x0, x1, hi, lo);
                 two_sum2(hi, x2, hi, e1);
@@ -877,10 +888,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 const float hi = hv[j], lo = lv[j];
                 bool ok;
                 const int sc = em + fn;
-                double v = f32_pair_scaled(hi, lo, sc, ok);
+                double v = f32_pair_scaled<FAST>(hi, lo, sc, ok);
                 if (!ok) v = f32_pair_scaled_slow(hi, lo, sc);
                 *dst = (kc0 == wk.kc_lo) ? v : *dst + v;
               }
+            };
+#pragma unroll 1
+            for (int ch = 0; ch < WCOLS / 8; ++ch) {
+              if (ch * 8 >= ncols) break;  // warp-uniform
+              if (fast)
+                chunk(std::true_type{}, ch);
+              else
+                chunk(std::false_type{}, ch);
             }
           }
           tc_fence_before();
