@@ -551,27 +551,30 @@ __global__ void __cluster_dims__(OZ_PREP_CLUSTER, 1, 1) __launch_bounds__(256, 3
     if (h == 1) half[rl] = mb;
     __syncthreads();
     if (h == 0) pmax[rl] = max(mb, half[rl]);
-  } else {  // B~: columns contiguous along k; a warp per column, lanes along k
+  } else {  // B~: columns contiguous along k; a warp takes four columns at a time, lanes along k
     const int warp = tid >> 5, lane = tid & 31;
-    for (int cl = warp; cl < OZ_TROWS; cl += 8) {
-      const int64_t n = r0 + cl;
-      unsigned long long mb = 0;
-      if (n < R) {
-        const long long* x = reinterpret_cast<const long long*>(g.B) + s.b_off + n * s.K;
-        int64_t k = k_lo + lane;
-        for (; k + 96 < k_hi; k += 128) {
-          unsigned long long v[4];
+    for (int cl0 = warp * 4; cl0 < OZ_TROWS; cl0 += 32) {
+      const long long* x[4];
+      bool nok[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) v[u] = (unsigned long long)__ldg(x + k + 32 * u);
+      for (int u = 0; u < 4; ++u) {
+        nok[u] = r0 + cl0 + u < R;
+        x[u] = reinterpret_cast<const long long*>(g.B) + s.b_off + (nok[u] ? (r0 + cl0 + u) * s.K : 0);
+      }
+      unsigned long long mb[4] = {0, 0, 0, 0};
+      for (int64_t k = k_lo + lane; k < k_hi; k += 32) {  // four independent loads in flight
+        unsigned long long v[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) mb = max(mb, v[u] & kAbs);
-        }
-        for (; k < k_hi; k += 32) mb = max(mb, (unsigned long long)__ldg(x + k) & kAbs);
+        for (int u = 0; u < 4; ++u) v[u] = nok[u] ? (unsigned long long)__ldg(x[u] + k) : 0ull;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) mb[u] = max(mb[u], v[u] & kAbs);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1)
-        mb = max(mb, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mb, o));
-      if (lane == 0) pmax[cl] = mb;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          mb[u] = max(mb[u], (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mb[u], o));
+      if (lane < 4) pmax[cl0 + lane] = lane == 0 ? mb[0] : lane == 1 ? mb[1] : lane == 2 ? mb[2] : mb[3];
     }
   }
   // ---- 2. the cluster's maxima -> the rows' scale exponents
