@@ -1015,9 +1015,10 @@ int set_smem_attr() {
 
 size_t al1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
 
-// The k_oz_prep CTAs of one request.  A tile nkc k-chunks deep takes g = min(nkc, 8) CTAs of one
-// cluster (at least one k-chunk each): a shallow tile spread over a whole cluster would leave most
-// of its CTAs without work, and the launch would run in many short waves.  Tiles go into clusters
+// The k_oz_prep CTAs of one request.  A tile nkc k-chunks deep takes g = min(ceil(nkc / cpt), 8)
+// CTAs of one cluster (cpt k-chunks or more each, cpt set by the launch's size): a shallow tile
+// spread over a whole cluster would leave most of its CTAs without work, and the launch would run
+// in many short waves.  Tiles go into clusters
 // of OZ_PREP_CLUSTER CTAs deepest first, each into the open cluster with the least room that still
 // holds it (best fit decreasing); the ranks a cluster leaves free become idle entries.
 std::vector<OzJob> pack_prep_tiles(std::vector<OzJob> tiles) {
@@ -1078,6 +1079,7 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
       }
   std::vector<OzWork> work;
   std::vector<OzJob> prep_jobs, prep_tiles;
+  int64_t prep_chunks = 0;
   std::vector<std::pair<double, OzWork>> wcost;
   // Tile width: measured in this kernel, a 128 x 64 x 16 MMA takes ~72 cycles and a 128 x 128 x 16
   // one ~65 (the full rate), so 128-column tiles do nearly twice the work per cycle; but they hold
@@ -1131,10 +1133,21 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
         t.nw = nw;
         wcost.push_back({(double)s.nkc, t});
       }
-    // the prep tiles: every 128-row tile of A~ and 128-column tile of B~, with its depth
-    const int16_t gsz = (int16_t)std::min(s.nkc, OZ_PREP_CLUSTER);
-    for (int rt = 0; rt < s.nmt; ++rt) prep_tiles.push_back(OzJob{sid, 0, rt, 0, gsz});
-    for (int rt = 0; rt < s.nnt; ++rt) prep_tiles.push_back(OzJob{sid, 1, rt, 0, gsz});
+    // the prep tiles: every 128-row tile of A~ and 128-column tile of B~ (group sizes below)
+    for (int rt = 0; rt < s.nmt; ++rt) prep_tiles.push_back(OzJob{sid, 0, rt, 0, 1});
+    for (int rt = 0; rt < s.nnt; ++rt) prep_tiles.push_back(OzJob{sid, 1, rt, 0, 1});
+    prep_chunks += (int64_t)(s.nmt + s.nnt) * s.nkc;
+  }
+  {
+    // k-chunks per prep CTA: one while the launch has fewer than two waves' worth of chunks (at
+    // three CTAs per SM), up to three for large launches, where fewer and longer-lived CTAs lose
+    // less to the per-CTA latency (job tables, two cluster barriers, first loads)
+    const int64_t wave = 3 * (int64_t)std::max(ctx->num_sms, 1);
+    const int cpt = (int)std::max<int64_t>(1, std::min<int64_t>(3, prep_chunks / (2 * wave)));
+    for (OzJob& t : prep_tiles) {
+      const int nkc = L->sectors[(size_t)t.sector].nkc;
+      t.gsize = (int16_t)std::min((nkc + cpt - 1) / cpt, OZ_PREP_CLUSTER);
+    }
   }
   prep_jobs = pack_prep_tiles(prep_tiles);
   std::stable_sort(wcost.begin(), wcost.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
