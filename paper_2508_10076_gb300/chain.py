@@ -4,6 +4,8 @@ contraction.  Everything on the path is a libtk launch; this module allocates de
 with PyTorch, fills inputs from :mod:`.workloads` and sequences the ABI calls.
 """
 
+import time
+
 import numpy as np
 import torch
 
@@ -89,7 +91,9 @@ class HeffChain:
         self.sectors = (V, P, W)
         legs = wl.heff_legs(V, P, W) if sites == 2 else wl.heff1_legs(V, P, W)
         self.legs = legs
+        t0 = time.perf_counter()  # structures (spaces, fusion trees, block layout) of the operands
         self.tm = {k: _tmap(ctx, sym, legs[k]) for k in ("x", "L", "W", "R")}
+        struct_ms = (time.perf_counter() - t0) * 1e3
         self.host = {}
         rnd = wl.normal_complex if dtype == "c128" else wl.normal
         for i, k in enumerate(("x", "L", "R")):
@@ -111,6 +115,7 @@ class HeffChain:
         self.others = ("L", "W", "W", "R") if sites == 2 else ("L", "W", "R")
         self.steps = []
         cur = self.tm["x"]
+        t0 = time.perf_counter()  # and every contraction plan (the inputs are drawn in between)
         for i, other in enumerate(self.others):
             first = i == 0
             if first:  # T1 = L x : A = L, B = x
@@ -119,6 +124,7 @@ class HeffChain:
                 st = Contraction(ctx, cur, self.tm[other], specs[i], dtype, gemm, slices, device)
             self.steps.append(st)
             cur = st.out
+        self.plan_build_ms = struct_ms + (time.perf_counter() - t0) * 1e3
         self.flops = sum(s.plan.flops for s in self.steps)
         self.tensor_flops = sum(s.plan.tensor_flops for s in self.steps)
         self.permute_bytes = sum(s.plan.permute_bytes for s in self.steps)
