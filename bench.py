@@ -125,15 +125,15 @@ def replica_seed(rank):
     return rank
 
 
-def _workload(ctx, name, gemm, dtype="f64", seed=0):
+def _workload(ctx, name, gemm, dtype="f64", seed=0, slices=0):
     from paper_2508_10076_gb300 import workloads as wl
     from paper_2508_10076_gb300.chain import HeffChain, LxContraction
     cfg = wl.CONFIGS[name]
     if cfg["kind"] in ("heff", "heff1"):
         return HeffChain(ctx, cfg["sym"], cfg["D"], gemm=gemm, dtype=dtype, seed=seed,
-                         sites=2 if cfg["kind"] == "heff" else 1, mpo=cfg.get("mpo"))
+                         sites=2 if cfg["kind"] == "heff" else 1, mpo=cfg.get("mpo"), slices=slices)
     if cfg["kind"] == "lx":
-        return LxContraction(ctx, cfg["sym"], cfg["D"], gemm=gemm, dtype=dtype, seed=seed)
+        return LxContraction(ctx, cfg["sym"], cfg["D"], gemm=gemm, dtype=dtype, seed=seed, slices=slices)
     raise SystemExit(f"config {name} is a parity case, not a bench line")
 
 
@@ -316,10 +316,10 @@ class Timer:
         return sum(s.elapsed_time(e) for s, e in zip(starts, ends))
 
 
-def measure(ctx, name, gemm, args, timer, rank, steps, want_graph=True, clocks=None):
+def measure(ctx, name, gemm, args, timer, rank, steps, want_graph=True, clocks=None, slices=0):
     """One workload in one GEMM mode: autotune, warm up, capture one step as a CUDA graph, time
     `steps` replays, then the same loop eager with libtk's launch profiler on."""
-    work = _workload(ctx, name, gemm, seed=replica_seed(rank))
+    work = _workload(ctx, name, gemm, seed=replica_seed(rank), slices=slices)
     tuned = work.autotune() if not args.no_autotune else None  # before any graph capture
     for _ in range(max(3, args.warmup)):
         work.run()
@@ -518,6 +518,18 @@ def run_ours(args):
                 "kernels": kernels_table(v["prof"], args.steps), "out": v["out"]}
             if gemm == "ozaki":
                 variants[gemm]["slices"] = 6
+        # the same workload at other slice counts (fewer steps): rate against accuracy
+        if not args.no_extra:
+            sweep = {}
+            for sl in (4, 5, 7):
+                v = measure(ctx, args.config, "ozaki", args, timer, rank, args.extra_steps, slices=sl)
+                v_ms = max_over_ranks(dist, v["total_ms"])
+                sweep[str(sl)] = {
+                    "value": job_throughput(flops, args.extra_steps, world, v_ms), "unit": UNIT,
+                    "ms_per_step": v_ms / args.extra_steps, "slice_pairs": sl * (sl + 1) // 2,
+                    "rel_frobenius_per_block_vs_fp64_path": rel_err_per_block(
+                        _out_blocks(v["work"]), v["out"].cpu().numpy(), m["out"].cpu().numpy())}
+            variants["ozaki"]["slice_sweep"] = sweep
     # ---------------- the other configurations named by the metric (fewer steps)
     extra = {}
     if not args.no_extra:
