@@ -645,23 +645,28 @@ __device__ __forceinline__ void gemm_rows(const GemmItem& it, const GemmTile& tl
 // a = hi + lo to within 2^-46 |a|, by integer operations on the FP64 bit pattern: hi keeps the
 // sign, the exponent and the top 23 stored mantissa bits; lo is the next 23 bits, formed as a
 // normal FP32 with those bits as its fraction minus the same number with a zero fraction (an
-// exact subtraction), so no conversion instruction runs.  Values outside the normal FP32 range
-// take the conversion instructions.
-__device__ __noinline__ void df_split_slow(double a, float& hi, float& lo) {
-  hi = __double2float_rn(a);
-  lo = __double2float_rn(a - (double)hi);
+// exact subtraction), so no conversion instruction runs.  The pair arithmetic keeps its precision
+// while every product and its error term stay normal FP32: each A value in [2^-58, 2^96) and each
+// B value (the MPO side) in [2^-20, 2^20) give products in [2^-78, 2^116) (and sums of up to 2^10
+// of them below 2^127).  A nonzero value outside its window (FP64 subnormals included) counts as
+// zero here and marks the block; the block flags its tile, and the launch after it redoes the
+// flagged tiles' output rows in plain FP64 (rows_df_redo).  The window test is the exponent branch
+// every value takes anyway; only the rare values pay for more.
+__shared__ int s_df_oor;  // the block met an out-of-range value (cleared at the block's start)
+__device__ __noinline__ void df_split_rare(double a, float& hi, float& lo) {
+  if (__double_as_longlong(a) << 1) s_df_oor = 1;  // zero is in range
+  hi = 0.f;
+  lo = 0.f;
 }
+// EMIN, EMAX: the window [2^EMIN, 2^EMAX) of magnitudes split here.
+template <int EMIN, int EMAX>
 __device__ __forceinline__ void df_split(double a, float& hi, float& lo) {
+  static_assert(EMIN >= -103 && EMAX <= 127, "the window must keep hi and lo normal FP32");
   const unsigned long long b = (unsigned long long)__double_as_longlong(a);
   const int ex = (int)((b >> 52) & 0x7FF);
   const int ef = ex - 1023 + 127;
-  if ((unsigned int)(ef - 53) >= 202u) {  // lo's scale 2^(ex-1069) must be a normal FP32
-    if (ex == 0) {                        // zero or FP64 subnormal (far below FP32)
-      hi = 0.f;
-      lo = 0.f;
-    } else {
-      df_split_slow(a, hi, lo);           // rare, out of line
-    }
+  if ((unsigned int)(ef - (127 + EMIN)) >= (unsigned int)(EMAX - EMIN)) {
+    df_split_rare(a, hi, lo);  // out of line
     return;
   }
   const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
@@ -671,6 +676,7 @@ __device__ __forceinline__ void df_split(double a, float& hi, float& lo) {
   const float l = __fsub_rn(__uint_as_float(e2 | ((unsigned int)(b >> 6) & 0x7FFFFFu)), __uint_as_float(e2));
   lo = __uint_as_float(__float_as_uint(l) ^ sign);
 }
+constexpr int DF_A_EMIN = -58, DF_A_EMAX = 96, DF_B_EMIN = -20, DF_B_EMAX = 20;
 // Double-float multiply-add on two output columns at once with the packed FP32 pair instructions
 // (one instruction per pair): (sh, sl) += a * b, a = ah + al, b = bh + bl; no operation is
 // contracted.
@@ -690,7 +696,7 @@ __device__ __forceinline__ void df_rows_group(float2 (&sh)[RPT][NP], float2 (&sl
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     float ah, al;
-    df_split(a[r], ah, al);
+    df_split<DF_A_EMIN, DF_A_EMAX>(a[r], ah, al);
 #pragma unroll
     for (int q = 0; q < NP; ++q) df_mac2(sh[r][q], sl[r][q], ah, al, bh[q], bl[q]);
   }
@@ -726,8 +732,8 @@ __device__ __forceinline__ void gemm_rows_df_n(const GemmItem& it, const GemmTil
         for (int e = tid; e < kmax * NP; e += 256) {
           const int kk = e % kmax, q = e / kmax;
           float h0, l0, h1 = 0.f, l1 = 0.f;
-          df_split(Bb[(k0 + kk) + (2 * q) * K], h0, l0);
-          if (2 * q + 1 < NT) df_split(Bb[(k0 + kk) + (2 * q + 1) * K], h1, l1);
+          df_split<DF_B_EMIN, DF_B_EMAX>(Bb[(k0 + kk) + (2 * q) * K], h0, l0);
+          if (2 * q + 1 < NT) df_split<DF_B_EMIN, DF_B_EMAX>(Bb[(k0 + kk) + (2 * q + 1) * K], h1, l1);
           Bh[kk][q] = make_float2(h0, h1);
           Bl[kk][q] = make_float2(l0, l1);
         }
@@ -814,15 +820,69 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 1) k_gemm_f64(const 
 // Split-precision modes: every product left to the CUDA cores is an N <= 8 row block in
 // double-float (the planner cuts wider thin products into such blocks), so this launch runs the
 // row code alone, with the registers of four CTAs per SM.
+// The double-float launch's exact fallback, run after it: the output rows of every tile whose
+// flag is set (a value out of range), again in plain FP64 over the whole inner dimension, straight
+// to C (the launch, split-K sums included, has finished; two flagged parts of one split tile write
+// the same values).  Each block reads 256 flags at a time, one per thread, so a launch with no
+// flag set costs one load round; the flagged tiles of the round are then redone one by one.
+__device__ __noinline__ void rows_df_redo(const GemmItem* __restrict__ items, const GemmTile* __restrict__ tiles,
+                                          int64_t ntiles, const double* __restrict__ A,
+                                          const double* __restrict__ B, double* __restrict__ C,
+                                          const int* __restrict__ flags, int64_t block, int64_t nblocks) {
+  __shared__ int64_t list[256];
+  __shared__ int count;
+  for (int64_t t0 = block * 256; t0 < ntiles; t0 += nblocks * 256) {
+    const int64_t t = t0 + threadIdx.x;
+    const int f = t < ntiles ? *(volatile const int*)&flags[t] : 0;
+    if (!__syncthreads_or(f)) continue;
+    if (threadIdx.x == 0) count = 0;
+    __syncthreads();
+    if (f) list[atomicAdd(&count, 1)] = t;
+    __syncthreads();
+    for (int i = 0; i < count; ++i) {
+      const GemmTile tl = tiles[list[i]];
+      const GemmItem it = items[tl.item];
+      const int64_t rows = (int64_t)256 * tl.rpt * tl.nblk;
+      for (int64_t m = tl.m0 + threadIdx.x; m < min(it.M, (int64_t)tl.m0 + rows); m += blockDim.x)
+        for (int64_t j = 0; j < it.N; ++j) {
+          double s = 0.0;
+          for (int64_t k = 0; k < it.K; ++k) s = __fma_rn(A[it.a_off + m + k * it.M], B[it.b_off + k + j * it.K], s);
+          C[it.c_off + m + j * it.M] = s;
+        }
+    }
+    __syncthreads();  // list and count are reused by the next round
+  }
+}
+// Start of a double-float block: clear its out-of-range mark before any value is split.
+__device__ __forceinline__ void rows_df_clear_mark() {
+  if (threadIdx.x == 0) s_df_oor = 0;
+  __syncthreads();
+}
+// End of a double-float block: flag its tile if the block met an out-of-range value.
+__device__ __forceinline__ void rows_df_mark(int* flag) {
+  __syncthreads();
+  if (threadIdx.x == 0 && s_df_oor) *flag = 1;
+}
+// A small launch after a double-float launch (one block per 256 tiles, one SM's worth at most):
+// the exact fallback for the flagged tiles, else nothing.
+__global__ void __launch_bounds__(256) k_rows_df_fixup(const GemmItem* __restrict__ items,
+                                                       const GemmTile* __restrict__ tiles, int64_t ntiles,
+                                                       const double* __restrict__ A, const double* __restrict__ B,
+                                                       double* __restrict__ C, const int* flags) {
+  rows_df_redo(items, tiles, ntiles, A, B, C, flags, blockIdx.x, gridDim.x);
+}
+
 __global__ void __launch_bounds__(256, 4) k_gemm_rows_df(const GemmItem* __restrict__ items,
                                                          const GemmTile* __restrict__ tiles,
                                                          const double* __restrict__ A, const double* __restrict__ B,
                                                          double* __restrict__ C, double* __restrict__ partials,
-                                                         int* __restrict__ counters) {
+                                                         int* __restrict__ counters, int* guard) {
   __shared__ double smem[ROWS_KCHUNK * ROWS_NMAX];  // B of one K chunk as double-float pairs
   const GemmTile tl = tiles[blockIdx.x];
   const GemmItem it = items[tl.item];
+  rows_df_clear_mark();
   gemm_rows_df(it, tl, A, B, C, smem, partials, counters);
+  rows_df_mark(guard + blockIdx.x);
 }
 
 // Packed FP64 GEMM over many requests: each segment carries one request's work list and buffers.
@@ -832,6 +892,7 @@ struct GemmSeg {
   const void *A, *B;
   void *C, *partials;
   int* counters;
+  int* guard;  // double-float launches: one out-of-range flag per tile
   int64_t block0, ntiles;
 };
 struct GemmBatch {
@@ -864,8 +925,17 @@ __global__ void __launch_bounds__(256, 4) k_gemm_rows_df_batch(const __grid_cons
   const GemmSeg& g = L.seg[find_seg(L.seg, L.nseg, (int64_t)blockIdx.x)];
   const GemmTile tl = g.tiles[blockIdx.x - g.block0];
   const GemmItem it = g.items[tl.item];
+  rows_df_clear_mark();
   gemm_rows_df(it, tl, (const double*)g.A, (const double*)g.B, (double*)g.C, smem, (double*)g.partials,
                g.counters);
+  rows_df_mark(g.guard + (blockIdx.x - g.block0));
+}
+// After a packed double-float launch: blocks (x, s) run the exact fallback for segment s's flagged
+// tiles, block x reading rounds x, x + gridDim.x, ... of 256 flags.
+__global__ void __launch_bounds__(256) k_rows_df_fixup_batch(const __grid_constant__ GemmBatch L) {
+  const GemmSeg& g = L.seg[blockIdx.y];
+  rows_df_redo(g.items, g.tiles, g.ntiles, (const double*)g.A, (const double*)g.B, (double*)g.C, g.guard, blockIdx.x,
+               gridDim.x);
 }
 
 // Packed zero fill: block row y belongs to the segment whose first item index is the largest <= y.
@@ -1219,8 +1289,13 @@ int launch_gemm_fp64(Ctx* ctx, const ContractPlan& cp, const void* a, const void
   if (cp.dtype != TK_C128 && cp.gemm_mode != TK_GEMM_FP64) {
     ProfScope prof(ctx, "k_gemm_rows_df", stream);
     k_gemm_rows_df<<<grid, 256, 0, s>>>(items, tiles, (const double*)a, (const double*)b, (double*)c,
-                                        (double*)partials, counters);
-    return check_launch(ctx, "k_gemm_rows_df");
+                                        (double*)partials, counters, counters + cp.split_slots);
+    int rc = check_launch(ctx, "k_gemm_rows_df");
+    if (rc != TK_OK) return rc;
+    const unsigned fix_grid = (unsigned)std::min<int64_t>((cp.n_gemm_tiles + 255) / 256, std::max(ctx->num_sms, 1));
+    k_rows_df_fixup<<<fix_grid, 256, 0, s>>>(items, tiles, cp.n_gemm_tiles, (const double*)a, (const double*)b,
+                                             (double*)c, counters + cp.split_slots);
+    return check_launch(ctx, "k_rows_df_fixup");
   }
   ProfScope prof(ctx, "k_gemm_f64", stream);
   if (cp.dtype == TK_C128)
@@ -1319,7 +1394,8 @@ int run_contract(Ctx* ctx, const ContractPlan& cp, const void* a, const void* b,
   const PermJob in_jobs[2] = {{cp.pa.get(), a, (void*)at}, {cp.pb.get(), b, (void*)bt}};
   IntClear clears[1];
   int nclears = 0;
-  if (cp.split_slots > 0) clears[nclears++] = IntClear{(int*)(w + cp.ws_counters), (int64_t)cp.split_slots};
+  const int64_t nclear = (int64_t)cp.split_slots + df_guard_words(cp);  // split-K counters, rows guard
+  if (nclear > 0) clears[nclears++] = IntClear{(int*)(w + cp.ws_counters), nclear};
   // both operands in one launch, which also clears the split-K counters and zero-fills the output
   // blocks with an empty inner dimension
   ZeroJob zj{(const ZeroItem*)cp.d_zero, (int64_t)cp.zeros.size(), 0, ct, cp.dtype};
@@ -1370,7 +1446,8 @@ int run_contract_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const 
     in_jobs.push_back({cp.pa.get(), a[i], (void*)at[i]});
     in_jobs.push_back({cp.pb.get(), b[i], (void*)bt[i]});
     if (cp.pc) out_jobs.push_back({cp.pc.get(), ct[i], c[i]});
-    if (cp.split_slots > 0) clears.push_back({(int*)(w + cp.ws_counters), (int64_t)cp.split_slots});
+    const int64_t nclear = (int64_t)cp.split_slots + df_guard_words(cp);
+    if (nclear > 0) clears.push_back({(int*)(w + cp.ws_counters), nclear});
   }
   int rc = launch_permutes(ctx, in_jobs.data(), (int)in_jobs.size(), stream, clears.data(), (int)clears.size());
   if (rc != TK_OK) return rc;
@@ -1416,9 +1493,12 @@ int run_contract_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const 
       if (split) {
         ProfScope prof(ctx, "k_gemm_rows_df", stream);
         k_gemm_rows_df_batch<<<(unsigned)blocks, 256, 0, s>>>(gb);
+        int rc2 = check_launch(ctx, "k_gemm_rows_df_batch");
+        if (rc2 != TK_OK) return rc2;
+        k_rows_df_fixup_batch<<<dim3(4, (unsigned)gb.nseg), 256, 0, s>>>(gb);
         gb.nseg = 0;
         blocks = 0;
-        return check_launch(ctx, "k_gemm_rows_df_batch");
+        return check_launch(ctx, "k_rows_df_fixup");
       }
       ProfScope prof(ctx, "k_gemm_f64", stream);
       if (cplx)
@@ -1441,6 +1521,7 @@ int run_contract_batch(Ctx* ctx, int n, const ContractPlan* const* plans, const 
       g.C = ct[i];
       g.partials = w + cp.ws_partials;
       g.counters = (int*)(w + cp.ws_counters);
+      g.guard = g.counters + cp.split_slots;
       g.block0 = blocks;
       g.ntiles = cp.n_gemm_tiles;
       blocks += cp.n_gemm_tiles;

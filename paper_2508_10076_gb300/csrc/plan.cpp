@@ -607,7 +607,7 @@ int finalize_device_tables(Ctx* ctx, ContractPlan& cp) {
   cp.ws_partials = off;
   off += align256(cp.partials_bytes);
   cp.ws_counters = off;
-  off += align256((size_t)cp.split_slots * sizeof(int));
+  off += align256((size_t)(cp.split_slots + df_guard_words(cp)) * sizeof(int));
   cp.ws_slices = off;
   cp.ws_total = off;
   if (cp.gemm_mode != TK_GEMM_FP64) {

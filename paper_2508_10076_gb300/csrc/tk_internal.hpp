@@ -201,6 +201,12 @@ struct ContractPlan {
 };
 
 
+// Ints after the split-K counters: one out-of-range flag per tile of the double-float rows launch
+// (real split-precision plans only; cleared with the counters).
+inline int64_t df_guard_words(const ContractPlan& cp) {
+  return (cp.gemm_mode != TK_GEMM_FP64 && cp.dtype != TK_C128) ? cp.n_gemm_tiles : 0;
+}
+
 // Workspace bytes a call of this contraction plan needs (a complex split-precision plan adds its
 // real plan's current size, which the autotuner may change).
 inline size_t contract_ws_bytes(const ContractPlan& cp) { return cp.re ? cp.ws_cx + cp.re->ws_total : cp.ws_total; }

@@ -118,3 +118,15 @@ def test_null_buffers_only_for_maps_without_elements(hctx):
     with pytest.raises(api.TKError) as e:
         api.contract_noalloc(hctx, cp, None, None, None)
     assert e.value.code == TK_ERR_ARG
+
+
+def test_fp64_probe_argument_checks(hctx):
+    with pytest.raises(api.TKError) as e:
+        api.probe_fp64_peak(hctx, seconds=0.5)    # host-only context
+    assert e.value.code == TK_ERR_NO_DEVICE
+    with pytest.raises(api.TKError) as e:
+        api.probe_fp64_peak(hctx, seconds=0.0)    # out of (0, 30]
+    assert e.value.code == TK_ERR_ARG
+    with pytest.raises(api.TKError) as e:
+        api.probe_fp64_peak(hctx, seconds=31.0)
+    assert e.value.code == TK_ERR_ARG

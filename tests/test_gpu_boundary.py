@@ -134,3 +134,14 @@ def test_tmap_upload_download_round_trip_and_context_stream():
     cs, ref = ops.contract(ostruct("SU2", legs["L"]), a, *wl.LX_SPEC[:2], ostruct("SU2", legs["x"]), b,
                            *wl.LX_SPEC[2:], tier="block")
     assert rel_frobenius_per_block(cs, c.cpu().numpy(), ref) <= 1e-12
+
+
+def test_fp64_peak_probe_is_plausible():
+    """The FP64 roofline denominator: a register-only FMA loop on every SM for the requested time.
+    GB300's FP64 pipe retires 2 FMA per clock per SM (152 SMs, up to 2.07 GHz): 1.26 TFLOP/s."""
+    build_library()
+    from paper_2508_10076_gb300 import api
+    ctx = api.Context(0)
+    tflops, ms = api.probe_fp64_peak(ctx, seconds=0.2)
+    assert 0.6 < tflops < 1.3
+    assert 150 < ms < 260

@@ -144,6 +144,57 @@ def test_scales_span_many_binades(gctx):
         assert np.all(err <= bound)
 
 
+def _elementwise_bound_check(oa, xa, ob, xb, cs, ref, got, factor):
+    """|got - ref| <= factor K max|a_m.| max|b_.n| element by element (the split's error is relative
+    to the row and column maxima, which the power-of-two scales follow)."""
+    for (ca, ra, ka, oa_), (cb, rb, kb, ob_), (cc, rc, kc, oc) in zip(oa.blocks, ob.blocks, cs.blocks):
+        am = xa[oa_:oa_ + ra * ka].reshape(ka, ra).T
+        bm = xb[ob_:ob_ + rb * kb].reshape(kb, rb).T
+        bound = factor * ka * np.abs(am).max(axis=1)[:, None] * np.abs(bm).max(axis=0)[None, :]
+        err = np.abs(got[oc:oc + rc * kc] - ref[oc:oc + rc * kc]).reshape(kc, rc).T
+        assert np.all(err <= bound)
+
+
+@pytest.mark.parametrize("ea,eb", [(500, -500), (-600, -400), (600, 300)])
+def test_scales_outside_the_fast_epilogue_range(gctx, ea, eb):
+    """Row scales near 2^ea and column scales near 2^eb, beyond the +-448 for which the epilogue
+    skips its range checks: the checked path (and, for results near 2^-1000 or 2^1000, the exact
+    slow conversion) must give the same accuracy as ordinary scales."""
+    api = _api()
+    la = ([({0: 130, 1: 20}, False)], [({0: 100, 1: 9}, False)])
+    lb = ([({0: 100, 1: 9}, False)], [({0: 140, 1: 33}, False)])
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    rng = np.random.default_rng(11)
+    xa = wl.normal(3, oa.numel) * np.exp2(ea + rng.integers(-8, 9, oa.numel).astype(float))
+    xb = wl.normal(4, ob.numel) * np.exp2(eb + rng.integers(-8, 9, ob.numel).astype(float))
+    cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
+    A, B = _tm(gctx, "U1", la), _tm(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), gemm="ozaki")
+    c = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda())
+    _elementwise_bound_check(oa, xa, ob, xb, cs, ref, c.cpu().numpy(), 8 * 2.0 ** (-42))
+
+
+@pytest.mark.parametrize("slices", [2, 3, 4, 5])
+def test_low_slice_counts(gctx, slices):
+    """Fewer than four slices leave level accumulators unwritten (the epilogue's masked path); the
+    error follows the digits kept: each operand entry within 2^(-7s) of its row's (column's)
+    maximum, and the dropped slice pairs at most (s + 2) 2^(-7s) more per product, with scales up
+    to twice the maxima (factor 4)."""
+    api = _api()
+    la = ([({0: 130, 1: 20}, False)], [({0: 100, 1: 9}, False)])
+    lb = ([({0: 100, 1: 9}, False)], [({0: 140, 1: 33}, False)])
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    xa, xb = wl.normal(5, oa.numel), wl.normal(6, ob.numel)
+    cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
+    A, B = _tm(gctx, "U1", la), _tm(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), gemm="ozaki", slices=slices)
+    c = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda())
+    got = c.cpu().numpy()
+    _elementwise_bound_check(oa, xa, ob, xb, cs, ref, got, 4 * (slices + 4) * 2.0 ** (-7 * slices))
+    # and not far better than the digits allow: the error does shrink with the slice count
+    assert rel_frobenius_per_block(cs, got, ref) > 2.0 ** (-7 * slices - 14)
+
+
 TF32X3_TOL = 1e-5  # about FP32 accuracy: reported, not gated at the split-precision bar
 
 
@@ -267,3 +318,39 @@ def test_split_precision_edge_cases(gctx, gemm, case):
     got = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda()).cpu().numpy()
     assert not np.isnan(got).any()
     assert rel_frobenius_per_block(cs, got, ref) <= (SPLIT_TOL if gemm == "ozaki" else 2e-5)
+
+
+@pytest.mark.parametrize("planted", ["tiny", "huge", "mpo"])
+def test_skinny_products_outside_the_double_float_window(gctx, planted):
+    """The N <= 8 products of the split-precision modes run in double-float arithmetic, which keeps
+    its precision only for A values in [2^-58, 2^96) and B values in [2^-20, 2^20).  Plant a few
+    values outside those windows in one part of a long skinny product: the row blocks that meet
+    them are redone in FP64 after the launch, the others keep their double-float results, and the
+    whole output matches the oracle block by block."""
+    api = _api()
+    la = ([({0: 3000, 1: 2500}, False)], [({0: 4, 1: 4}, False)])   # A: M x K with K = 4
+    lb = ([({0: 4, 1: 4}, False)], [({0: 4, 1: 3}, False)])         # B: K x N with N <= 4
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    xa, xb = wl.normal(21, oa.numel), wl.normal(22, ob.numel)
+    if planted == "tiny":
+        xa[100:104] = 2.0 ** -70 * np.array([1.0, -3.0, 0.5, 7.0])    # in the first row block only
+    elif planted == "huge":
+        xa[-5:] = 2.0 ** 100                                            # the last rows of the last sector
+    else:
+        xb[3] = 2.0 ** 30                                              # one MPO-side value
+    cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
+    A, B = _tm(gctx, "U1", la), _tm(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), gemm="ozaki")
+    c = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda())
+    got = c.cpu().numpy()
+    assert np.isfinite(got).all()
+    assert rel_frobenius_per_block(cs, got, ref) <= 1e-12
+    # and row by row: every output row within the double-float bound of its own terms
+    for (ca, ra, ka, oa_), (cb, rb, kb, ob_), (cc, rc, kc, oc) in zip(oa.blocks, ob.blocks, cs.blocks):
+        am = xa[oa_:oa_ + ra * ka].reshape(ka, ra).T
+        bm = xb[ob_:ob_ + rb * kb].reshape(kb, rb).T
+        bound = 2.0 ** -40 * (np.abs(am) @ np.abs(bm))
+        err = np.abs(got[oc:oc + rc * kc] - ref[oc:oc + rc * kc]).reshape(kc, rc).T
+        assert np.all(err <= bound)
+    c2 = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda())
+    assert torch.equal(c, c2)  # the flags are cleared for every call: same bits again
