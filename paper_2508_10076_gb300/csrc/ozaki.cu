@@ -16,11 +16,11 @@
 //     applies 2^{e_m + f_n}.
 // With s = 6 the relative Frobenius error against FP64 is ~1e-12 on N(0,1) data.
 //
-// Data path: one prep launch (clusters of 8 CTAs; a 128-row operand tile takes one to eight of
-// them by its depth, their scale maxima exchanged through distributed shared memory) writes the
-// scales and the slices as pre-tiled
-// 128 x 32 BF16 tiles (64-byte rows); one persistent GEMM launch walks a work list of (sector, 128-row tile,
-// column tile) items, the last column tile of a sector as narrow as its remainder (MMA N a
+// Data path: one prep launch (clusters of 4 or 8 CTAs; a 128-row operand tile takes one to eight
+// of them by its depth, their scale maxima exchanged through distributed shared memory) writes the
+// scales and the slices as pre-tiled 128 x 32 BF16 tiles (64-byte rows); one persistent GEMM
+// launch walks a work list of (sector, 128-row tile, column tile) items, the last column tile of a
+// sector as narrow as its remainder (MMA N a
 // multiple of 16).  Per CTA: warp 0 issues TMA loads (cp.async.bulk.tensor, 64-byte swizzle) of
 // all s A slices and all s B slices of one 32-deep k-chunk into a stage (two to four); one thread
 // of warp 1 issues every slice-pair MMA from the resident stage; sixteen epilogue warps (2..17,
@@ -108,7 +108,8 @@ struct OzLayout {
   int64_t nwork = 0, nprep_ctas = 0;
   OzSector* d_sectors = nullptr;
   OzWork* d_work = nullptr;
-  OzJob* d_prep_jobs = nullptr;  // one per k_oz_prep CTA, a multiple of OZ_PREP_CLUSTER
+  OzJob* d_prep_jobs = nullptr;  // one per k_oz_prep CTA, a multiple of prep_cluster
+  int prep_cluster = 8;  // CTAs per k_oz_prep cluster: 4 or 8
   std::vector<int32_t> cta_work;   // work of CTA b: work[cta_work[b] .. cta_work[b + 1])
   int32_t* d_cta_work = nullptr;
   int ncta = 0;
@@ -264,7 +265,7 @@ __device__ __noinline__ double f32_pair_scaled_slow(float hi, float lo, int sc) 
 
 // Scale exponents 2^e > max_k |x_rk| for every row of A~^c and every column of B~^c (k_oz_prep).
 constexpr int32_t kNoScale = (int32_t)0x80808080;  // the scale of an all-zero row or column
-constexpr int OZ_PREP_CLUSTER = 8;                 // CTAs sharing one 128-row tile in k_oz_prep
+constexpr int OZ_PREP_CLUSTER = 8;                 // largest k_oz_prep cluster (4 or 8 CTAs per launch)
 
 // e with 2^(e-1) <= mx < 2^e for a non-negative finite mx (kNoScale for 0), from the bits.
 __device__ __forceinline__ int exponent_of(double mx) {
@@ -488,9 +489,10 @@ __device__ __forceinline__ void slice_tile(const OzPrepSeg& g, const OzSector& s
   }
 }
 
-// Scale and slice in one launch.  A group of g CTAs of one cluster (g = min(k-chunks, 8), several
-// groups per cluster when g < 8) owns one 128-row tile of one operand (rows of A~^c, columns of
-// B~^c) and splits its k-chunks evenly among its CTAs.
+// Scale and slice in one launch of thread-block clusters (4 or 8 CTAs, chosen per launch).  A
+// group of g CTAs of one cluster (g set by the tile's depth, several groups per cluster when g is
+// below the cluster size) owns one 128-row tile of one operand (rows of A~^c, columns of B~^c) and
+// splits its k-chunks evenly among its CTAs.
 //   1. Every CTA takes the maximum |x| of each of the 128 rows over its k-chunks (as FP64 bit
 //      patterns, ordered as unsigned integers: no FP64 instruction).
 //   2. After a cluster barrier every CTA reads the g partial maxima of its rows from its group's
@@ -502,7 +504,7 @@ __device__ __forceinline__ void slice_tile(const OzPrepSeg& g, const OzSector& s
 // The operands are read from HBM once instead of twice (a separate scale pass), and the scales
 // need no initial fill.  The first CTA of each request also clears the GEMM's split-K counters.
 template <int MODE, int NSEG, int S>
-__global__ void __cluster_dims__(OZ_PREP_CLUSTER, 1, 1) __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 3)
     k_oz_prep(const __grid_constant__ OzPrepT<NSEG> P) {
   extern __shared__ __align__(16) unsigned char prep_dyn[];
   PrepBuf& buf = *reinterpret_cast<PrepBuf*>(prep_dyn);
@@ -1021,14 +1023,14 @@ size_t al1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
 // in many short waves.  Tiles go into clusters
 // of OZ_PREP_CLUSTER CTAs deepest first, each into the open cluster with the least room that still
 // holds it (best fit decreasing); the ranks a cluster leaves free become idle entries.
-std::vector<OzJob> pack_prep_tiles(std::vector<OzJob> tiles) {
+std::vector<OzJob> pack_prep_tiles(std::vector<OzJob> tiles, int csize) {
   std::stable_sort(tiles.begin(), tiles.end(), [](const OzJob& a, const OzJob& b) { return a.gsize > b.gsize; });
   std::vector<std::vector<OzJob>> clusters;
   std::vector<int> used;
-  std::vector<int> open[OZ_PREP_CLUSTER];  // open[r]: clusters with r free ranks, 0 < r < OZ_PREP_CLUSTER
+  std::vector<int> open[OZ_PREP_CLUSTER];  // open[r]: clusters with r free ranks, 0 < r < csize
   for (OzJob t : tiles) {
     int c = -1;
-    for (int r = t.gsize; r < OZ_PREP_CLUSTER && c < 0; ++r)
+    for (int r = t.gsize; r < csize && c < 0; ++r)
       if (!open[r].empty()) {
         c = open[r].back();
         open[r].pop_back();
@@ -1041,15 +1043,15 @@ std::vector<OzJob> pack_prep_tiles(std::vector<OzJob> tiles) {
     t.gbase = (int16_t)used[(size_t)c];
     clusters[(size_t)c].push_back(t);
     used[(size_t)c] += t.gsize;
-    const int left = OZ_PREP_CLUSTER - used[(size_t)c];
+    const int left = csize - used[(size_t)c];
     if (left > 0) open[left].push_back(c);
   }
   std::vector<OzJob> ctas;
-  ctas.reserve(clusters.size() * OZ_PREP_CLUSTER);
+  ctas.reserve(clusters.size() * csize);
   for (size_t c = 0; c < clusters.size(); ++c) {
     for (const OzJob& t : clusters[c])
       for (int q = 0; q < t.gsize; ++q) ctas.push_back(t);
-    for (int q = used[c]; q < OZ_PREP_CLUSTER; ++q) ctas.push_back(OzJob{-1, 0, 0, 0, 1});
+    for (int q = used[c]; q < csize; ++q) ctas.push_back(OzJob{-1, 0, 0, 0, 1});
   }
   return ctas;
 }
@@ -1144,12 +1146,21 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
     // less to the per-CTA latency (job tables, two cluster barriers, first loads)
     const int64_t wave = 3 * (int64_t)std::max(ctx->num_sms, 1);
     const int cpt = (int)std::max<int64_t>(1, std::min<int64_t>(3, prep_chunks / (2 * wave)));
+    // clusters of 4 where no tile needs more (or the launch is large): they pack into more of
+    // the SMs (at most 51 clusters of 8 are resident on this part); else of 8, so that deep tiles
+    // of small launches keep eight CTAs
+    int maxg = 1;
+    for (const OzJob& t : prep_tiles) {
+      const int nkc = L->sectors[(size_t)t.sector].nkc;
+      maxg = std::max(maxg, std::min((nkc + cpt - 1) / cpt, OZ_PREP_CLUSTER));
+    }
+    L->prep_cluster = (cpt >= 2 || maxg <= 4) ? 4 : OZ_PREP_CLUSTER;
     for (OzJob& t : prep_tiles) {
       const int nkc = L->sectors[(size_t)t.sector].nkc;
-      t.gsize = (int16_t)std::min((nkc + cpt - 1) / cpt, OZ_PREP_CLUSTER);
+      t.gsize = (int16_t)std::min((nkc + cpt - 1) / cpt, L->prep_cluster);
     }
   }
-  prep_jobs = pack_prep_tiles(prep_tiles);
+  prep_jobs = pack_prep_tiles(prep_tiles, L->prep_cluster);
   std::stable_sort(wcost.begin(), wcost.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
   // Split-K: a launch with fewer than two tiles per SM cuts deep tiles into up to OZ_MAX_PARTS
   // parts (at least 8 k-chunks each); their FP64 partial tiles are added in part order by the
@@ -1319,20 +1330,36 @@ int launch_oz_prep(Ctx* ctx, const OzLayout* const* lay, OzPrepT<NSEG>& P, int m
   }
   if (blocks == 0) return TK_OK;
   ProfScope prof(ctx, "k_oz_prep", stream);
-  const unsigned grid = (unsigned)blocks;
+  // a thread-block-cluster launch: every segment's CTA list is a whole number of clusters of the
+  // launch's size (the requests of one launch share it)
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = OZ_PREP_SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr;
+  std::memset(&attr, 0, sizeof(attr));
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = (unsigned)lay[0]->prep_cluster;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  cudaError_t e;
   if (mode == 1) {
-    k_oz_prep<1, NSEG, 2><<<grid, 256, OZ_PREP_SMEM, s>>>(P);
+    e = cudaLaunchKernelEx(&cfg, k_oz_prep<1, NSEG, 2>, P);
   } else {
     switch (nslices) {
-      case 2: k_oz_prep<0, NSEG, 2><<<grid, 256, OZ_PREP_SMEM, s>>>(P); break;
-      case 3: k_oz_prep<0, NSEG, 3><<<grid, 256, OZ_PREP_SMEM, s>>>(P); break;
-      case 4: k_oz_prep<0, NSEG, 4><<<grid, 256, OZ_PREP_SMEM, s>>>(P); break;
-      case 5: k_oz_prep<0, NSEG, 5><<<grid, 256, OZ_PREP_SMEM, s>>>(P); break;
-      case 6: k_oz_prep<0, NSEG, 6><<<grid, 256, OZ_PREP_SMEM, s>>>(P); break;
-      default: k_oz_prep<0, NSEG, 7><<<grid, 256, OZ_PREP_SMEM, s>>>(P); break;
+      case 2: e = cudaLaunchKernelEx(&cfg, k_oz_prep<0, NSEG, 2>, P); break;
+      case 3: e = cudaLaunchKernelEx(&cfg, k_oz_prep<0, NSEG, 3>, P); break;
+      case 4: e = cudaLaunchKernelEx(&cfg, k_oz_prep<0, NSEG, 4>, P); break;
+      case 5: e = cudaLaunchKernelEx(&cfg, k_oz_prep<0, NSEG, 5>, P); break;
+      case 6: e = cudaLaunchKernelEx(&cfg, k_oz_prep<0, NSEG, 6>, P); break;
+      default: e = cudaLaunchKernelEx(&cfg, k_oz_prep<0, NSEG, 7>, P); break;
     }
   }
-  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     ctx->last_error = std::string("k_oz_prep launch: ") + cudaGetErrorString(e);
     return TK_ERR_CUDA;
@@ -1411,7 +1438,8 @@ int launch_gemm_ozaki_batch(Ctx* ctx, int n, const ContractPlan* const* plans, c
     int grid = 0;
     for (int i : todo) {
       const OzLayout* L = static_cast<const OzLayout*>(plans[i]->oz.get());
-      if (B.nreq < OZ_BATCH && L->mode == L0->mode && L->bn == L0->bn && L->slices == L0->slices) {
+      if (B.nreq < OZ_BATCH && L->mode == L0->mode && L->bn == L0->bn && L->slices == L0->slices &&
+          L->prep_cluster == L0->prep_cluster) {
         if ((rc = describe_ozaki_request(ctx, *plans[i], a[i], b[i], c[i], ws[i], P.seg[B.nreq], B.req[B.nreq])) !=
             TK_OK)
           return rc;
