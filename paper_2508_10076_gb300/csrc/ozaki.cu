@@ -242,13 +242,15 @@ __device__ __noinline__ double scale_pow2_slow(double v, int e) { return ldexp(v
 // into that binade by itself.  hi must have an FP32 exponent field in [53, 253] (the scale 2^(179 -
 // e_hi), or twice it, is then a normal FP32) and sc in [-895, 2045 - e_hi] (both results normal in
 // FP64); anything else clears ok and the caller takes the exact slow path.
+// kexp = (896 + sc) << 20 (modulo 2^32), which the caller may have assembled from per-row and
+// per-column parts.
 template <bool SAFE_SC>
-__device__ __forceinline__ double f32_pair_scaled(float hi, float lo, int sc, bool& ok) {
+__device__ __forceinline__ double f32_pair_scaled(float hi, float lo, int sc, uint32_t kexp, bool& ok) {
   const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
   const uint32_t eh = (uh >> 23) & 0xFFu;
   // SAFE_SC: the caller knows |sc| <= 896, which with e_hi in [53, 253] keeps both results normal
   ok = (eh - 53u) < 201u && (SAFE_SC || (uint32_t)(sc + 895) <= (uint32_t)(2045 - (int)eh));
-  const uint32_t whi = (uh & 0x80000000u) | (((uh & 0x7FFFFFFFu) >> 3) + ((uint32_t)(896 + sc) << 20));
+  const uint32_t whi = (uh & 0x80000000u) | (((uh & 0x7FFFFFFFu) >> 3) + kexp);
   const uint32_t against = (uh ^ ul) >> 31;
   const uint32_t below = against & (uint32_t)((uh & 0x7FFFFFu) == 0u);
   const float scale = __uint_as_float((306u - eh + below) << 23);  // 2^(179 - e_hi + below)
@@ -833,7 +835,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int ncols = left < WCOLS ? (int)left : WCOLS;  // valid columns of this warp (may be <= 0)
         int fl = (lane < ncols) ? scale_b[s.sb_off + nb + lane] : 0;  // WCOLS <= 32: one per lane
         if (fl == kNoScale) fl = 0;
-        const bool fast = all_levels && __all_sync(0xffffffffu, em >= -448 && em <= 448 && fl >= -448 && fl <= 448);
+        // the fast chunk body: all levels present, every scale of the warp within +-448, and the
+        // warp's 32 x WCOLS part of the tile wholly inside the block (no row or column checks)
+        const bool fast = all_levels && ncols >= WCOLS &&
+                          __all_sync(0xffffffffu, row_ok && em >= -448 && em <= 448 && fl >= -448 && fl <= 448);
+        const uint32_t kem = (uint32_t)(896 + em) << 20, kfl = (uint32_t)fl << 20;  // exponent-field parts
         // a split tile's parts go to its partial buffers (column-major 128 x BN, one per part)
         const bool split = wk.nparts > 1;
         double* const pbase = split ? partials + (int64_t)wk.slot * OZ_MAX_PARTS * (OZ_BM * BN) : nullptr;
@@ -851,8 +857,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           if (active) {
             const uint32_t lane_addr = tmem + ((uint32_t)(quad * 32) << 16) + buf * (OZ_NACC * BN) + c0;
             // one chunk of eight columns; FAST: every level accumulator was written (four or more
-            // slices) and every row and column scale of this warp is within +-448, so no level
-            // is masked and no output can leave the normal FP64 range through its scale
+            // slices), every row and column scale of this warp is within +-448 and its part of the
+            // tile is whole, so no level is masked, no output can leave the normal FP64 range
+            // through its scale and no output needs a bounds check
             auto chunk = [&](auto fast_tag, int ch) {
               constexpr bool FAST = decltype(fast_tag)::value;
               uint32_t r0[8], r1[8], r2[8], r3[8];
@@ -888,13 +895,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               double* dst = crow + (int64_t)(ch * 8) * ld;
 #pragma unroll
               for (int j = 0; j < 8; ++j, dst += ld) {
-                const int fn = __shfl_sync(0xffffffffu, fl, ch * 8 + j);
-                if (!row_ok || ch * 8 + j >= ncols) continue;
                 const float hi = hv[j], lo = lv[j];
                 bool ok;
-                const int sc = em + fn;
-                double v = f32_pair_scaled<FAST>(hi, lo, sc, ok);
-                if (!ok) v = f32_pair_scaled_slow(hi, lo, sc);
+                double v;
+                if constexpr (FAST) {
+                  const uint32_t kfn = (uint32_t)__shfl_sync(0xffffffffu, (int)kfl, ch * 8 + j);
+                  v = f32_pair_scaled<true>(hi, lo, 0, kem + kfn, ok);
+                  if (!ok) v = f32_pair_scaled_slow(hi, lo, em + ((int)kfn >> 20));
+                } else {
+                  const int fn = __shfl_sync(0xffffffffu, fl, ch * 8 + j);
+                  if (!row_ok || ch * 8 + j >= ncols) continue;
+                  const int sc = em + fn;
+                  v = f32_pair_scaled<false>(hi, lo, sc, (uint32_t)(896 + sc) << 20, ok);
+                  if (!ok) v = f32_pair_scaled_slow(hi, lo, sc);
+                }
                 *dst = (kc0 == wk.kc_lo) ? v : *dst + v;
               }
             };
