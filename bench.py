@@ -351,6 +351,40 @@ def measure(ctx, name, gemm, args, timer, rank, steps, want_graph=True, clocks=N
                 launches=launches, prof=prof, out=out.clone())
 
 
+def measure_svd(api, ctx, tm, data, torch, reps=5):
+    """The block SVD after the two-site step (Alg. 9 in Alg. 12) of one chain's result x': one
+    k_svd_jacobi launch over every coupled sector, timed with CUDA events (median of `reps` after a
+    warm-up), its singular values checked block by block against numpy's LAPACK SVD."""
+    import numpy as np
+    sp = api.svd_plan(ctx, tm)
+    u_t, vh_t, nval = sp.outputs()
+    u = torch.empty(u_t.numel, dtype=torch.float64, device="cuda")
+    vh = torch.empty(vh_t.numel, dtype=torch.float64, device="cuda")
+    s = torch.empty(max(1, nval), dtype=torch.float64, device="cuda")
+    ws = torch.empty(max(1, sp.workspace_bytes), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    api.svd(ctx, sp, data, u, s, vh, ws)
+    ctx.sync()
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        api.svd(ctx, sp, data, u, s, vh, ws)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    x, sv = data.cpu().numpy(), s.cpu().numpy()
+    worst, largest = 0.0, (0, 0)
+    for (c, r, k, o), (c2, r2, k2, so) in zip(tm.blocks(), sp.blocks()):
+        ref = np.linalg.svd(x[o:o + r * k].reshape(k, r).T, compute_uv=False)
+        worst = max(worst, float(np.abs(sv[so:so + len(ref)] - ref).max() / max(ref[0], 1e-300)))
+        largest = max(largest, (r, k), key=lambda t: t[0] * t[1])
+    return {"ms": sorted(times)[len(times) // 2], "blocks": len(sp.blocks()), "largest_block": list(largest),
+            "singular_values": nval,
+            "max_rel_diff_singular_values_vs_numpy": worst,
+            "what": "block SVD of the D = 1024 chain's x' (V (x) P <- V (x) P*), all sectors in one launch"}
+
+
 def kernels_table(prof, steps):
     return {k: {"launches": c, "ms_per_step": ms / steps} for k, (c, ms) in prof.items()}
 
@@ -547,6 +581,8 @@ def run_ours(args):
                     ref_out = e["out"]
                     row["block_flops_per_step"] = e["work"].flops
                     row["permute_roofline"] = permute_roofline(e["work"], e["prof"], args.extra_steps)
+                    if hasattr(e["work"], "steps") and name == "c1_u1_heff_d1024":
+                        row["block_svd"] = measure_svd(api, ctx, e["work"].steps[-1].out, e["out"], torch)
                 else:
                     row[gemm]["rel_frobenius_per_block_vs_fp64_path"] = rel_err_per_block(
                         _out_blocks(e["work"]), e["out"].cpu().numpy(), ref_out.cpu().numpy())
