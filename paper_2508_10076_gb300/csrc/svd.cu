@@ -39,6 +39,7 @@ SvdPlan::~SvdPlan() { dev_free(d_jobs); }
 namespace {
 
 constexpr int kSvdThreads = 512;  // 16 warps: 16 column pairs rotated at a time
+constexpr int kSvdGroup = 512;    // pairs of one round handled per three-step group
 constexpr int kMaxSweeps = 60;
 
 struct SvdJob {       // one block's factorisation, device side
@@ -120,56 +121,100 @@ __global__ void __launch_bounds__(kSvdThreads) k_svd_jacobi(const SvdJob* __rest
   __syncthreads();
   const double tol = sqrt((double)M) * 2.220446049250313e-16;
   const int64_t np = N + (N & 1);  // even number of positions (an odd N has one idle position)
+  // A round's disjoint pairs go in groups of up to kSvdGroup, in three steps: every warp forms
+  // the Gram entries of its pairs (lane sums), one thread per pair turns them into the rotation
+  // (the square roots and divisions, done once per pair instead of once per lane), and every warp
+  // rotates its pairs' columns of G and Q.  On this part the FP64 pipe retires two lanes per SM
+  // per clock, and the per-pair scalar work done by all 32 lanes of a warp cost about as much as
+  // the column arithmetic.
+  __shared__ double s_al[kSvdGroup], s_be[kSvdGroup], s_c[kSvdGroup], s_sn[kSvdGroup];
+  __shared__ T s_ga[kSvdGroup], s_ph[kSvdGroup];
   __shared__ int rotated;
   for (int sweep = 0; sweep < kMaxSweeps && N > 1; ++sweep) {
     if (tid == 0) rotated = 0;
     __syncthreads();
-    bool any = false;
     for (int64_t r = 0; r < np - 1; ++r) {
-      for (int64_t k = warp; k < np / 2; k += nwarps) {
-        int64_t i = rr_column(k, r, np), j = rr_column(np - 1 - k, r, np);
-        if (i > j) {
-          const int64_t t = i;
-          i = j;
-          j = t;
+      for (int64_t k0 = 0; k0 < np / 2; k0 += kSvdGroup) {
+        const int64_t kn = min((int64_t)kSvdGroup, np / 2 - k0);
+        // 1. Gram entries |g_i|^2, |g_j|^2, g_i^H g_j of each pair (an idle pair gets zeros)
+        for (int64_t k = warp; k < kn; k += nwarps) {
+          int64_t i = rr_column(k0 + k, r, np), j = rr_column(np - 1 - (k0 + k), r, np);
+          if (i > j) {
+            const int64_t t = i;
+            i = j;
+            j = t;
+          }
+          double al = 0.0, be = 0.0;
+          T ga = zero_of<T>();
+          if (j < N) {
+            const T* gi = G + i * M;
+            const T* gj = G + j * M;
+            for (int64_t e = lane; e < M; e += 32) {
+              const T x = gi[e], y = gj[e];
+              al += abs2(x);
+              be += abs2(y);
+              dot_acc(ga, x, y);
+            }
+            al = warp_sum(al);
+            be = warp_sum(be);
+            ga = warp_sum(ga);
+          }
+          if (lane == 0) {
+            s_al[k] = al;
+            s_be[k] = be;
+            s_ga[k] = ga;
+          }
         }
-        if (j >= N) continue;  // the idle position of an odd N
-        T* gi = G + i * M;
-        T* gj = G + j * M;
-        double al = 0.0, be = 0.0;
-        T ga = zero_of<T>();
-        for (int64_t e = lane; e < M; e += 32) {
-          const T x = gi[e], y = gj[e];
-          al += abs2(x);
-          be += abs2(y);
-          dot_acc(ga, x, y);
+        __syncthreads();
+        // 2. one thread per pair: the rotation, or c = 0 marking "leave this pair alone"
+        for (int64_t k = tid; k < kn; k += kSvdThreads) {
+          const double al = s_al[k], be = s_be[k];
+          const T ga = s_ga[k];
+          const double ag = mag(ga);
+          double c = 0.0, sn = 0.0;
+          T ph = zero_of<T>();
+          if (ag > tol * sqrt(al * be)) {  // not yet orthogonal to working precision
+            const double z = (be - al) / (2.0 * ag);
+            const double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = c * t;
+            ph = unit_conj_phase(ga, ag);  // e^{-i phi}
+            rotated = 1;                   // every writer writes 1
+          }
+          s_c[k] = c;
+          s_sn[k] = sn;
+          s_ph[k] = ph;
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        const double ag = mag(ga);
-        if (!(ag > tol * sqrt(al * be))) continue;  // already orthogonal to working precision
-        any = true;
-        const double z = (be - al) / (2.0 * ag);
-        const double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
-        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-        const T ph = unit_conj_phase(ga, ag);  // e^{-i phi}
-        for (int64_t e = lane; e < M; e += 32) {
-          const T x = gi[e], y = mul(gj[e], ph);
-          gi[e] = add(scale(x, c), scale(y, -sn));
-          gj[e] = add(scale(x, sn), scale(y, c));
+        __syncthreads();
+        // 3. the rotations of G's and Q's columns
+        for (int64_t k = warp; k < kn; k += nwarps) {
+          const double c = s_c[k], sn = s_sn[k];
+          if (c == 0.0) continue;  // warp-uniform: nothing to rotate (c = 1/sqrt(1 + t^2) > 0 otherwise)
+          const T ph = s_ph[k];
+          int64_t i = rr_column(k0 + k, r, np), j = rr_column(np - 1 - (k0 + k), r, np);
+          if (i > j) {
+            const int64_t t = i;
+            i = j;
+            j = t;
+          }
+          T* gi = G + i * M;
+          T* gj = G + j * M;
+          for (int64_t e = lane; e < M; e += 32) {
+            const T x = gi[e], y = mul(gj[e], ph);
+            gi[e] = add(scale(x, c), scale(y, -sn));
+            gj[e] = add(scale(x, sn), scale(y, c));
+          }
+          T* qi = Q + i * N;
+          T* qj = Q + j * N;
+          for (int64_t e = lane; e < N; e += 32) {
+            const T x = qi[e], y = mul(qj[e], ph);
+            qi[e] = add(scale(x, c), scale(y, -sn));
+            qj[e] = add(scale(x, sn), scale(y, c));
+          }
         }
-        T* qi = Q + i * N;
-        T* qj = Q + j * N;
-        for (int64_t e = lane; e < N; e += 32) {
-          const T x = qi[e], y = mul(qj[e], ph);
-          qi[e] = add(scale(x, c), scale(y, -sn));
-          qj[e] = add(scale(x, sn), scale(y, c));
-        }
+        __syncthreads();  // the next group reuses the shared arrays; the next round reads these columns
       }
-      __syncthreads();
     }
-    if (any && lane == 0) atomicOr(&rotated, 1);
     __syncthreads();
     if (!rotated) break;
     __syncthreads();
