@@ -40,6 +40,7 @@ namespace {
 
 constexpr int kSvdThreads = 512;  // 16 warps: 16 column pairs rotated at a time
 constexpr int kSvdGroup = 512;    // pairs of one round handled per three-step group
+constexpr size_t kSvdSmemG = 180 * 1024;  // a block whose G fits in this many bytes keeps G in shared memory
 constexpr int kMaxSweeps = 60;
 
 struct SvdJob {       // one block's factorisation, device side
@@ -72,13 +73,11 @@ __device__ __forceinline__ double mag(double2 g) { return hypot(g.x, g.y); }
 // e^{-i phi} for g = |g| e^{i phi} (|g| > 0)
 __device__ __forceinline__ double unit_conj_phase(double g, double) { return g >= 0.0 ? 1.0 : -1.0; }
 __device__ __forceinline__ double2 unit_conj_phase(double2 g, double ag) { return make_double2(g.x / ag, -g.y / ag); }
-__device__ __forceinline__ double mul(double a, double b) { return a * b; }
 __device__ __forceinline__ double2 mul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ double scale(double a, double s) { return a * s; }
 __device__ __forceinline__ double2 scale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
-__device__ __forceinline__ double add(double a, double b) { return a + b; }
 __device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 template <typename T>
 __device__ __forceinline__ T zero_of();
@@ -93,6 +92,27 @@ __device__ __forceinline__ double one_of<double>() { return 1.0; }
 template <>
 __device__ __forceinline__ double2 one_of<double2>() { return make_double2(1.0, 0.0); }
 
+// The plane rotation of columns x, y (n entries, one warp, lanes along the column):
+// x' = c x - s ph y, y' = s x + c ph y.  For real data ph = +-1 is folded into the coefficients
+// (four FP64 operations per entry instead of five).
+__device__ __forceinline__ void rotate_columns(double* x, double* y, int64_t n, double c, double sn, double ph,
+                                               int lane) {
+  const double sp = sn * ph, cp = c * ph;
+  for (int64_t e = lane; e < n; e += 32) {
+    const double a = x[e], b = y[e];
+    x[e] = fma(-sp, b, c * a);
+    y[e] = fma(cp, b, sn * a);
+  }
+}
+__device__ __forceinline__ void rotate_columns(double2* x, double2* y, int64_t n, double c, double sn, double2 ph,
+                                               int lane) {
+  for (int64_t e = lane; e < n; e += 32) {
+    const double2 a = x[e], b = mul(y[e], ph);
+    x[e] = add(scale(a, c), scale(b, -sn));
+    y[e] = add(scale(a, sn), scale(b, c));
+  }
+}
+
 // Column p of the round-robin schedule in round r (positions 0 .. np-1, np even): position 0 is
 // fixed, the others rotate; pair k of round r is (pos(k), pos(np - 1 - k)).
 __device__ __forceinline__ int64_t rr_column(int64_t pos, int64_t r, int64_t np) {
@@ -103,11 +123,14 @@ template <typename T>
 __global__ void __launch_bounds__(kSvdThreads) k_svd_jacobi(const SvdJob* __restrict__ jobs, const T* __restrict__ a,
                                                             T* __restrict__ u, double* __restrict__ s,
                                                             T* __restrict__ vh, T* __restrict__ ws,
-                                                            double* __restrict__ wsd) {
+                                                            double* __restrict__ wsd, size_t g_smem) {
+  extern __shared__ __align__(16) unsigned char svd_dyn[];
   const SvdJob jb = jobs[blockIdx.x];
   const bool tall = jb.m >= jb.n;
   const int64_t M = tall ? jb.m : jb.n, N = tall ? jb.n : jb.m;  // G is M x N, M >= N
-  T* G = ws + jb.g_off;
+  // G in shared memory when the launch gave enough (the largest fitting block sets the size), else
+  // in the workspace; Q always in the workspace
+  T* G = (size_t)jb.m * (size_t)jb.n * sizeof(T) <= g_smem ? reinterpret_cast<T*>(svd_dyn) : ws + jb.g_off;
   T* Q = ws + jb.q_off;
   double* nrm = wsd + jb.norm_off;
   const T* A = a + jb.a_off;
@@ -197,20 +220,8 @@ __global__ void __launch_bounds__(kSvdThreads) k_svd_jacobi(const SvdJob* __rest
             i = j;
             j = t;
           }
-          T* gi = G + i * M;
-          T* gj = G + j * M;
-          for (int64_t e = lane; e < M; e += 32) {
-            const T x = gi[e], y = mul(gj[e], ph);
-            gi[e] = add(scale(x, c), scale(y, -sn));
-            gj[e] = add(scale(x, sn), scale(y, c));
-          }
-          T* qi = Q + i * N;
-          T* qj = Q + j * N;
-          for (int64_t e = lane; e < N; e += 32) {
-            const T x = qi[e], y = mul(qj[e], ph);
-            qi[e] = add(scale(x, c), scale(y, -sn));
-            qj[e] = add(scale(x, sn), scale(y, c));
-          }
+          rotate_columns(G + i * M, G + j * M, M, c, sn, ph, lane);
+          rotate_columns(Q + i * N, Q + j * N, N, c, sn, ph, lane);
         }
         __syncthreads();  // the next group reuses the shared arrays; the next round reads these columns
       }
@@ -328,14 +339,33 @@ int run_svd(Ctx* ctx, const SvdPlan& sp, const void* a, void* u, double* s, void
   if (sp.njobs == 0) return TK_OK;
   cudaStream_t st = (cudaStream_t)stream;
   double* wsd = (double*)((char*)ws + sp.ws_solver);
+  // dynamic shared memory: the largest G (m n elements) that fits in kSvdSmemG
+  const size_t es = sp.dtype == TK_C128 ? 16 : 8;
+  size_t g_smem = 0;
+  for (const SvdBlock& k : sp.blocks) {
+    const size_t b = (size_t)k.m * (size_t)k.n * es;
+    if (b <= kSvdSmemG) g_smem = std::max(g_smem, b);
+  }
+  static bool attr_set[64][2] = {};
+  if (ctx->device >= 0 && ctx->device < 64 && !attr_set[ctx->device][es == 16]) {
+    const cudaError_t e = es == 16 ? cudaFuncSetAttribute(k_svd_jacobi<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)kSvdSmemG)
+                                   : cudaFuncSetAttribute(k_svd_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)kSvdSmemG);
+    if (e != cudaSuccess) {
+      ctx->last_error = "cannot reserve shared memory for the block SVD";
+      return TK_ERR_CUDA;
+    }
+    attr_set[ctx->device][es == 16] = true;
+  }
   {
     ProfScope prof(ctx, "k_svd_jacobi", stream);
     if (sp.dtype == TK_C128)
-      k_svd_jacobi<double2><<<(unsigned)sp.njobs, kSvdThreads, 0, st>>>(
-          (const SvdJob*)sp.d_jobs, (const double2*)a, (double2*)u, s, (double2*)vh, (double2*)ws, wsd);
+      k_svd_jacobi<double2><<<(unsigned)sp.njobs, kSvdThreads, g_smem, st>>>(
+          (const SvdJob*)sp.d_jobs, (const double2*)a, (double2*)u, s, (double2*)vh, (double2*)ws, wsd, g_smem);
     else
-      k_svd_jacobi<double><<<(unsigned)sp.njobs, kSvdThreads, 0, st>>>(
-          (const SvdJob*)sp.d_jobs, (const double*)a, (double*)u, s, (double*)vh, (double*)ws, wsd);
+      k_svd_jacobi<double><<<(unsigned)sp.njobs, kSvdThreads, g_smem, st>>>(
+          (const SvdJob*)sp.d_jobs, (const double*)a, (double*)u, s, (double*)vh, (double*)ws, wsd, g_smem);
   }
   if (cudaGetLastError() != cudaSuccess) {
     ctx->last_error = "block SVD launch failed";
