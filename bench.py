@@ -335,7 +335,7 @@ def measure(ctx, name, gemm, args, timer, rank, steps, want_graph=True, clocks=N
             step_fn, mode = work.run, f"eager (graph capture failed: {exc})"
     timer.torch.cuda.synchronize()
     launches0 = ctx.launches
-    total_ms = timer(step_fn, steps, clocks, label=f"timed_{name}_{gemm}")
+    total_ms = timer(step_fn, steps, clocks, label=f"timed_{name}_{gemm}" + (f"_s{slices}" if slices else ""))
     launches = ctx.launches - launches0 if per_step_launches is None else per_step_launches * steps
     ctx.sync()
     ctx.profile(True)
