@@ -312,46 +312,6 @@ __device__ __forceinline__ const OzPrepSeg& prep_seg(const OzPrepT<NSEG>& P, int
   return P.seg[lo];
 }
 
-// v 2^-e (|v| < 2^e) as hi + lo, both TF32 values in FP32 containers (11 significant bits, the
-// 13 low mantissa bits zero), by integer operations on the FP64 bit pattern: hi is v 2^-e rounded
-// to 11 bits, lo the remainder rounded to 11 bits.  Parts below the FP32 normal range are
-// dropped (they are below 2^-126 of the row's or column's scale).
-__device__ __forceinline__ void tf32_split(double v, int e, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  hi = lo = 0.f;
-  if (ex == 0) return;  // zero, or an FP64 subnormal: far below any scale
-  const uint32_t sign = (uint32_t)(b >> 63) << 31;
-  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  int E = ex - 1023 - e;  // v 2^-e = m 2^(E - 52)
-  unsigned long long mh = (m + (1ull << 41)) >> 42;  // 11 bits, or 2^11 after rounding up
-  const long long r = (long long)m - (long long)(mh << 42);  // remainder, |r| <= 2^41
-  const int Er = E;
-  if (mh >> 11) {
-    mh >>= 1;
-    E += 1;
-  }
-  if (E + 127 <= 0) return;
-  hi = __uint_as_float(sign | ((uint32_t)(E + 127) << 23) | ((uint32_t)(mh - 1024) << 13));
-  if (r == 0) return;
-  unsigned long long ar = (unsigned long long)(r < 0 ? -r : r);
-  int p = 63 - __clzll((long long)ar);  // leading one of |r|
-  unsigned long long q;
-  if (p > 10) {
-    q = (ar + (1ull << (p - 11))) >> (p - 10);
-    if (q >> 11) {
-      q >>= 1;
-      p += 1;
-    }
-  } else {
-    q = ar << (10 - p);
-  }
-  const int el = Er - 52 + p + 127;  // FP32 exponent field of lo
-  if (el <= 0) return;
-  const uint32_t slo = r < 0 ? (sign ^ 0x80000000u) : sign;
-  lo = __uint_as_float(slo | ((uint32_t)el << 23) | ((uint32_t)(q - 1024) << 13));
-}
-
 // x = v 2^-e (|x| < 1) as hi + lo: two FP32 numbers holding the top 24 significant bits of x
 // (hi: sign, exponent, 23 stored fraction bits) and the next 23 bits (lo), both exact, formed
 // from the FP64 bit pattern with 32-bit integer operations (lo as a normal FP32 with those bits as
@@ -371,6 +331,21 @@ __device__ __forceinline__ void scaled_split(double v, int e, float& hi, float& 
   const uint32_t e2 = (uint32_t)(ef - 23) << 23;  // lo = bits 28..6 of the fraction, 2^-46 units
   const float l = __fsub_rn(__uint_as_float(e2 | ((bl >> 6) & 0x7FFFFFu)), __uint_as_float(e2));
   lo = __uint_as_float(__float_as_uint(l) ^ sign);
+}
+
+// v 2^-e (|v| < 2^e) as hi + lo, both TF32 values in FP32 containers (11 significant bits, the
+// 13 low fraction bits zero), from the FP32 pair (h, l) above with 32-bit operations: hi is h
+// rounded to 11 bits (half away from zero, on the bit pattern, so that a carry moves into the
+// exponent), h - hi is exact, and lo is (h - hi) + l rounded to FP32 and then to 11 bits.  hi
+// equals v 2^-e rounded to 11 bits (h holds its top 24 bits and l has h's sign); |x - hi - lo| <=
+// 2^-23 |x|.  Parts below the FP32 normal range are dropped.
+__device__ __forceinline__ void tf32_split(double v, int e, float& hi, float& lo) {
+  float h, l;
+  scaled_split(v, e, h, l);
+  hi = __uint_as_float((__float_as_uint(h) + 0x1000u) & 0xFFFFE000u);
+  const float t = __fadd_rn(__fsub_rn(h, hi), l);
+  const uint32_t tb = (__float_as_uint(t) + 0x1000u) & 0xFFFFE000u;
+  lo = (tb & 0x7F800000u) ? __uint_as_float(tb) : 0.f;
 }
 
 // The S balanced base-128 digits d_i of x = hi + lo, x ~ sum_i d_i 2^(-7 (i + 1)), in FP32 for two
