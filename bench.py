@@ -576,7 +576,7 @@ def run_ours(args):
                 e = measure(ctx, name, gemm, args, timer, rank, args.extra_steps)
                 e_ms = max_over_ranks(dist, e["total_ms"])
                 row[gemm] = {"value": job_throughput(e["work"].flops, args.extra_steps, world, e_ms),
-                             "ms_per_step": e_ms / args.extra_steps}
+                             "ms_per_step": e_ms / args.extra_steps, "autotune": e["tuned"]}
                 if gemm == "fp64":
                     ref_out = e["out"]
                     row["block_flops_per_step"] = e["work"].flops

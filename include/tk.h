@@ -318,13 +318,19 @@ int tk_svd_truncate(tk_ctx* ctx, const tk_plan* plan, const int64_t* keep, const
  * buffers (median of three runs each, CUDA events on `stream`, which is synchronised) and keeps the
  * fastest: FP64 tiles 32 or 64 wide with split-K off or at its maximum, or the built-in heuristic;
  * for split-precision plans then also the tensor-core tile width (64 / 128 columns) and its
- * split-K.  Candidates whose workspace would exceed workspace_bytes are skipped, so the plan's
+ * split-K, and the operand preparation without its k-chunks in shared memory.  Candidates whose workspace would exceed workspace_bytes are skipped, so the plan's
  * tk_plan_workspace_bytes() stays <= workspace_bytes.  The plan's device tables are rebuilt: call
  * it before capturing the plan in a CUDA graph and while no launch of the plan is in flight.
- * c and the workspace are overwritten.  *choice (if not NULL) receives 8 * fp64 candidate + split-
- * precision candidate (candidate 0 = heuristic). */
+ * c and the workspace are overwritten.  *choice (if not NULL) receives 64 * preparation candidate
+ * + 8 * fp64 candidate + split-precision candidate (candidate 0 = heuristic; preparation 1 = no
+ * chunks in shared memory, 2 = chunks in shared memory). */
 int tk_plan_autotune(tk_ctx* ctx, tk_plan* plan, const void* a, const void* b, void* c, void* workspace,
                      size_t workspace_bytes, void* stream, int* choice);
+/* Apply a choice in tk_plan_autotune's encoding without timing anything (to reuse a choice found
+ * earlier, or to pin one): the plan's device tables are rebuilt, so call it while no launch of the
+ * plan is in flight, and size the workspace from tk_plan_workspace_bytes() afterwards.  Returns
+ * TK_ERR_ARG for a value the autotuner cannot produce. */
+int tk_plan_set_choice(tk_ctx* ctx, tk_plan* plan, int choice);
 
 /* Contraction without any device allocation -- no counterpart in the paper.  Same result and
  * launch sequence as tk_contract, but the scratch memory (permuted operands and the intermediate

@@ -83,6 +83,7 @@ SIGNATURES = {
     "tk_svd": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
     "tk_svd_truncate": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tk_plan_autotune": (C.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, C.c_size_t, c_vp, c_vp]),
+    "tk_plan_set_choice": (C.c_int, [c_vp, c_vp, C.c_int]),
     "tk_copy_h2d": (C.c_int, [c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
     "tk_copy_d2h": (C.c_int, [c_vp, c_vp, c_vp, C.c_size_t, c_vp]),
     "tk_probe_fp64_peak": (C.c_int, [c_vp, C.c_double, c_dblp, c_dblp, c_vp]),

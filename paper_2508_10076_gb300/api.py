@@ -483,12 +483,18 @@ def contract_batch(ctx, plans, a, b, c, workspaces, stream=None):
 
 def autotune(ctx, plan, a, b, c, workspace, stream=None):
     """tk_plan_autotune: time the plan's candidate work lists on these buffers, keep the fastest.
-    Returns (fp64 candidate, split-precision candidate); 0 means the built-in heuristic."""
+    Returns (fp64 candidate, split-precision candidate, preparation candidate); 0 means the
+    built-in heuristic."""
     choice = C.c_int(0)
     nbytes = workspace.numel() * workspace.element_size()
     _check(_lib().tk_plan_autotune(ctx._h, plan._h, _ptr(a), _ptr(b), _ptr(c), _ptr(workspace),
                                    C.c_size_t(nbytes), ctx._stream(stream), C.byref(choice)), ctx)
-    return choice.value // 8, choice.value % 8
+    return (choice.value // 8) % 8, choice.value % 8, choice.value // 64
+
+
+def set_choice(ctx, plan, fp64=0, split=0, prep=0):
+    """tk_plan_set_choice: apply an autotuner choice (the triple `autotune` returns) untimed."""
+    _check(_lib().tk_plan_set_choice(ctx._h, plan._h, C.c_int(64 * prep + 8 * fp64 + split)), ctx)
 
 
 def noalloc_scratch_bytes():

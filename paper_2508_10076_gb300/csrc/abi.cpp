@@ -690,7 +690,7 @@ static int autotune_contract(tk_ctx* ctx, tk::ContractPlan& cp, const void* a, c
   };
   const Cand fp64c[] = {{0, 0}, {32, 1}, {64, 1}, {32, 2}, {64, 2}};
   const Cand ozc[] = {{0, 0}, {64, 1}, {128, 1}, {64, 2}, {128, 2}};
-  int best_i = 0, best_j = 0;
+  int best_i = 0, best_j = 0, best_k = 0;
   float best = 1e30f, ms = 0;
   for (int i = 0; i < 5 && rc == TK_OK; ++i) {  // FP64 work list (heuristic split-precision choice)
     cp.tune_tile = fp64c[i].tile;
@@ -708,9 +708,22 @@ static int autotune_contract(tk_ctx* ctx, tk::ContractPlan& cp, const void* a, c
     for (int j = 0; j < 5 && rc == TK_OK; ++j) {  // split-precision work list
       cp.tune_oz_bn = ozc[j].tile;
       cp.tune_oz_split = ozc[j].split;
+      cp.tune_oz_img = 0;
       if ((rc = measure(&ms)) == TK_OK && ms < best) {
         best = ms;
         best_j = j;
+      }
+    }
+    cp.tune_oz_bn = ozc[best_j].tile;
+    cp.tune_oz_split = ozc[best_j].split;
+    // the preparation without chunk images (where its heuristic uses them): only switching them
+    // off is tried, since these back-to-back runs keep the operands in L2, which favours the
+    // images more than a cold-cache run beside the double-float rows does
+    for (int k = 1; k < 2 && rc == TK_OK; ++k) {
+      cp.tune_oz_img = k;
+      if ((rc = measure(&ms)) == TK_OK && ms < best) {
+        best = ms;
+        best_k = k;
       }
     }
   }
@@ -720,10 +733,29 @@ static int autotune_contract(tk_ctx* ctx, tk::ContractPlan& cp, const void* a, c
   cp.tune_split = fp64c[best_i].split;
   cp.tune_oz_bn = ozc[best_j].tile;
   cp.tune_oz_split = ozc[best_j].split;
+  cp.tune_oz_img = best_k;
   const int rc2 = tk::finalize_device_tables(&ctx->c, cp);
   if (rc != TK_OK) return fail(ctx, rc, "autotuning run failed");
   if (rc2 != TK_OK) return fail(ctx, rc2, "rebuilding the chosen work lists failed");
-  if (choice) *choice = best_i * 8 + best_j;
+  if (choice) *choice = best_k * 64 + best_i * 8 + best_j;
+  return TK_OK;
+}
+
+int tk_plan_set_choice(tk_ctx* ctx, tk_plan* plan, int choice) {
+  if (!ctx || !plan || plan->kind != 1) return fail(ctx, TK_ERR_ARG, "not a contraction plan");
+  const int i = (choice / 8) % 8, j = choice % 8, k = choice / 64;
+  if (choice < 0 || i > 4 || j > 4 || k > 2) return fail(ctx, TK_ERR_ARG, "not an autotuner choice");
+  static const int tile[] = {0, 32, 64, 32, 64}, split[] = {0, 1, 1, 2, 2};
+  static const int oz_tile[] = {0, 64, 128, 64, 128};
+  tk::ContractPlan& cp = plan->con->re ? *plan->con->re : *plan->con;
+  int rc = set_device(ctx);
+  if (rc != TK_OK) return rc;
+  cp.tune_tile = tile[i];
+  cp.tune_split = split[i];
+  cp.tune_oz_bn = oz_tile[j];
+  cp.tune_oz_split = split[j];
+  cp.tune_oz_img = k;
+  if ((rc = tk::finalize_device_tables(&ctx->c, cp)) != TK_OK) return fail(ctx, rc, "rebuilding the work lists failed");
   return TK_OK;
 }
 

@@ -110,6 +110,7 @@ struct OzLayout {
   OzWork* d_work = nullptr;
   OzJob* d_prep_jobs = nullptr;  // one per k_oz_prep CTA, a multiple of prep_cluster
   int prep_cluster = 8;  // CTAs per k_oz_prep cluster: 4 or 8
+  bool prep_img = false;  // k_oz_prep keeps each CTA's first two k-chunks in shared memory
   std::vector<int32_t> cta_work;   // work of CTA b: work[cta_work[b] .. cta_work[b + 1])
   int32_t* d_cta_work = nullptr;
   int ncta = 0;
@@ -297,6 +298,7 @@ template <int NSEG>
 struct OzPrepT {
   OzPrepSeg seg[NSEG];
   int32_t nseg;
+  int32_t img;  // each CTA keeps its first two k-chunks in shared memory (two chunk images)
 };
 template <int NSEG>
 __device__ __forceinline__ const OzPrepSeg& prep_seg(const OzPrepT<NSEG>& P, int64_t& local) {
@@ -393,10 +395,13 @@ __device__ __forceinline__ void oz_slice_pair(double v0, double v1, int e, uint3
   }
 }
 
-// Shared staging of one k-chunk of an A~ tile: buf[kk][r] = x(row r0 + r, k0 + kk), zero outside
-// the sector.  The padding column keeps the row-pair reads below spread over the banks.
+// Shared staging of one k-chunk of a tile: buf[kk][r] = x(row r0 + r, k0 + kk) (for B~, r runs over
+// its columns), zero outside the sector.  The padding column keeps the row-pair reads below spread
+// over the banks.  A launch with chunk images holds two of them (the second also serves as the
+// staging buffer of later chunks).
 using PrepBuf = double[OZ_BK][OZ_TROWS + 1];
 constexpr size_t OZ_PREP_SMEM = sizeof(PrepBuf);
+constexpr size_t OZ_PREP_SMEM_IMG = 2 * sizeof(PrepBuf);
 
 // One 128 x 32 (rows x k) tile (row tile rt, k-chunk kc) of one operand, all slices, with the
 // rows' scale exponents in esc.  Every load of a thread is issued before any arithmetic.  A~
@@ -404,8 +409,10 @@ constexpr size_t OZ_PREP_SMEM = sizeof(PrepBuf);
 // (k contiguous) is read straight into the slicing layout.  Each thread then takes two consecutive
 // k of 8 rows, so a slice of the pair is one packed 32-bit (BF16 pair) or 64-bit (TF32 pair) store
 // and a half-warp writes a full 64-byte tile row.  MODE 0 writes S BF16 digit slices, MODE 1 the
-// TF32 pair (hi, lo).  Called by all 256 threads of the CTA (it synchronises them).
-template <int MODE, int S>
+// TF32 pair (hi, lo).  IMG: the chunk is already in xs (kept there by the maxima pass, zeros
+// outside the sector, either operand), so nothing is loaded and no barrier is needed.  Otherwise
+// called by all 256 threads of the CTA (the A path synchronises them).
+template <int MODE, int S, bool IMG>
 __device__ __forceinline__ void slice_tile(const OzPrepSeg& g, const OzSector& s, int op, int64_t rt, int kc,
                                            const int* esc, PrepBuf& xs) {
   constexpr int NI = OZ_TROWS / 16;  // rows per thread
@@ -414,7 +421,13 @@ __device__ __forceinline__ void slice_tile(const OzPrepSeg& g, const OzSector& s
   const int tid = threadIdx.x;
   const int kp = (tid & 15) * 2, rw = tid >> 4;  // k pair and first row of this thread
   double v[NI][2];
-  if (op == 0) {
+  if (IMG) {
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      v[i][0] = xs[kp][rw + 16 * i];
+      v[i][1] = xs[kp + 1][rw + 16 * i];
+    }
+  } else if (op == 0) {
     const int ml = tid & (OZ_TROWS - 1), kk0 = tid >> 7;
     const bool mok = r0 + ml < R;
     const double* src = g.A + s.a_off + (r0 + ml) + (k0 + kk0) * s.M;
@@ -477,14 +490,16 @@ __device__ __forceinline__ void slice_tile(const OzPrepSeg& g, const OzSector& s
 //      scale 2^e > max_k |x| (the exponent of a maximum is the maximum of the exponents); the
 //      group's first CTA writes it for the GEMM's epilogue.  A second cluster barrier keeps every
 //      CTA's shared memory alive until the others have read it.
-//   3. Every CTA slices its own k-chunks, re-reading them (now from L2).
+//   3. Every CTA slices its own k-chunks, re-reading them (now from L2).  In a launch with chunk
+//      images (P.img: launches whose CTAs own one to three chunks) step 1 also keeps the CTA's
+//      first two chunks in shared memory, and step 3 slices those from there.
 // The operands are read from HBM once instead of twice (a separate scale pass), and the scales
 // need no initial fill.  The first CTA of each request also clears the GEMM's split-K counters.
 template <int MODE, int NSEG, int S>
 __global__ void __launch_bounds__(256, 3)
     k_oz_prep(const __grid_constant__ OzPrepT<NSEG> P) {
   extern __shared__ __align__(16) unsigned char prep_dyn[];
-  PrepBuf& buf = *reinterpret_cast<PrepBuf*>(prep_dyn);
+  PrepBuf* img = reinterpret_cast<PrepBuf*>(prep_dyn);  // P.img ? two chunk images : the staging buffer
   __shared__ unsigned long long pmax[OZ_TROWS];  // this CTA's maxima (read by the cluster)
   __shared__ unsigned long long half[OZ_TROWS];
   __shared__ int esc[OZ_TROWS];
@@ -508,15 +523,35 @@ __global__ void __launch_bounds__(256, 3)
   const int gr = rank - jb.gbase, gs = jb.gsize;  // this CTA's rank in its group, the group's size
   const int kc_lo = (int)((int64_t)gr * s.nkc / gs);
   const int kc_hi = (int)((int64_t)(gr + 1) * s.nkc / gs);
-  const int64_t k_lo = (int64_t)kc_lo * OZ_BK, k_hi = min(s.K, (int64_t)kc_hi * OZ_BK);
+  const int nimg = P.img ? min(2, kc_hi - kc_lo) : 0;   // chunks kept in shared memory
+  const int64_t k_lo = (int64_t)(kc_lo + nimg) * OZ_BK;  // the rest, read straight
+  const int64_t k_hi = min(s.K, (int64_t)kc_hi * OZ_BK);
   constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
   // ---- 1. partial maxima over this CTA's k range
   if (op == 0) {  // A~: rows contiguous; thread (row, half) walks every other column
     const int rl = tid & (OZ_TROWS - 1), h = tid >> 7;
     const int64_t m = r0 + rl;
+    const bool mok = m < R;
     unsigned long long mb = 0;
-    if (m < R) {
-      const long long* x = reinterpret_cast<const long long*>(g.A) + s.a_off + m;
+    const long long* x = reinterpret_cast<const long long*>(g.A) + s.a_off + (mok ? m : 0);
+    for (int c = 0; c < nimg; ++c) {  // image c: every (kk, row) written, zeros outside the sector
+      const int64_t kb = (int64_t)(kc_lo + c) * OZ_BK + h;
+#pragma unroll
+      for (int j0 = 0; j0 < OZ_BK / 2; j0 += 8) {
+        long long v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int64_t k = kb + 2 * (j0 + u);
+          v[u] = (mok && k < s.K) ? __ldg(x + k * s.M) : 0ll;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          mb = max(mb, (unsigned long long)v[u] & kAbs);
+          img[c][h + 2 * (j0 + u)][rl] = __longlong_as_double(v[u]);
+        }
+      }
+    }
+    if (mok) {
       int64_t k = k_lo + h;
       for (; k + 14 < k_hi; k += 16) {  // eight independent loads in flight
         unsigned long long v[8];
@@ -541,6 +576,17 @@ __global__ void __launch_bounds__(256, 3)
         x[u] = reinterpret_cast<const long long*>(g.B) + s.b_off + (nok[u] ? (r0 + cl0 + u) * s.K : 0);
       }
       unsigned long long mb[4] = {0, 0, 0, 0};
+      for (int c = 0; c < nimg; ++c) {  // image c: lane = kk, column cl0 + u, zeros outside the sector
+        const int64_t k = (int64_t)(kc_lo + c) * OZ_BK + lane;
+        unsigned long long v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = (nok[u] && k < s.K) ? (unsigned long long)__ldg(x[u] + k) : 0ull;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          mb[u] = max(mb[u], v[u] & kAbs);
+          img[c][lane][cl0 + u] = __longlong_as_double((long long)v[u]);
+        }
+      }
       for (int64_t k = k_lo + lane; k < k_hi; k += 32) {  // four independent loads in flight
         unsigned long long v[4];
 #pragma unroll
@@ -567,8 +613,15 @@ __global__ void __launch_bounds__(256, 3)
     esc[tid] = e == kNoScale ? 0 : e;  // an all-zero row or column slices to zeros with any scale
   }
   cluster.sync();
-  // ---- 3. slices of this CTA's k-chunks
-  for (int kc = kc_lo; kc < kc_hi; ++kc) slice_tile<MODE, S>(g, s, op, jb.r0, kc, esc, buf);
+  // ---- 3. slices of this CTA's k-chunks (the images were written before the cluster barriers);
+  // a later chunk's A staging reuses image 1 after the slices of chunk 1 (its barrier orders them)
+  for (int kc = kc_lo; kc < kc_hi; ++kc) {
+    const int c = kc - kc_lo;
+    if (c < nimg)
+      slice_tile<MODE, S, true>(g, s, op, jb.r0, kc, esc, img[c]);
+    else
+      slice_tile<MODE, S, false>(g, s, op, jb.r0, kc, esc, img[nimg > 1 ? 1 : 0]);
+  }
 }
 
 // ------------------------------------------------------------------ the persistent GEMM
@@ -1144,6 +1197,19 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
       maxg = std::max(maxg, std::min((nkc + cpt - 1) / cpt, OZ_PREP_CLUSTER));
     }
     L->prep_cluster = (cpt >= 2 || maxg <= 4) ? 4 : OZ_PREP_CLUSTER;
+    // chunk images (the first two chunks of each CTA kept in shared memory): measured faster for
+    // launches at one or two chunks per CTA and slower at three, where they cover a small part of
+    // a CTA's chunks.  A contraction whose double-float rows (on the second stream, beside this
+    // launch and the GEMM) move more than half the bytes the preparation reads measured slower as
+    // a whole with them (66 KB of shared memory per CTA leaves less room for the rows' CTAs).
+    // The default takes the launches at two chunks per CTA with light rows; the autotuner tries
+    // both settings.
+    double rows_bytes = 0;
+    for (const GemmItem& it : cp.gemms_fp64) rows_bytes += 8.0 * (double)it.M * (double)(it.K + it.N);
+    const double prep_bytes = 8.0 * (double)prep_chunks * (OZ_TROWS * OZ_BK);
+    L->prep_img = cp.tune_oz_img == 2   ? true
+                  : cp.tune_oz_img == 1 ? false
+                                        : cpt == 2 && 2.0 * rows_bytes < prep_bytes;
     for (OzJob& t : prep_tiles) {
       const int nkc = L->sectors[(size_t)t.sector].nkc;
       t.gsize = (int16_t)std::min((nkc + cpt - 1) / cpt, L->prep_cluster);
@@ -1241,7 +1307,8 @@ int upload_ozaki_tables(Ctx* ctx, ContractPlan& cp) {
 namespace {
 template <typename K>
 bool prep_attr(K kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_PREP_SMEM) == cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_PREP_SMEM_IMG) ==
+         cudaSuccess;
 }
 template <int NSEG>
 int set_prep_attrs() {
@@ -1312,10 +1379,12 @@ template <int NSEG>
 int launch_oz_prep(Ctx* ctx, const OzLayout* const* lay, OzPrepT<NSEG>& P, int mode, int nslices, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   int64_t blocks = 0;
+  P.img = 1;  // chunk images only if every request of the launch asks for them
   for (int i = 0; i < P.nseg; ++i) {  // every segment starts on a cluster boundary
     P.seg[i].block0 = blocks;
     P.seg[i].jobs = lay[i]->d_prep_jobs;
     blocks += lay[i]->nprep_ctas;
+    if (!lay[i]->prep_img) P.img = 0;
   }
   if (blocks == 0) return TK_OK;
   ProfScope prof(ctx, "k_oz_prep", stream);
@@ -1325,7 +1394,7 @@ int launch_oz_prep(Ctx* ctx, const OzLayout* const* lay, OzPrepT<NSEG>& P, int m
   std::memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = OZ_PREP_SMEM;
+  cfg.dynamicSmemBytes = P.img ? OZ_PREP_SMEM_IMG : OZ_PREP_SMEM;
   cfg.stream = s;
   cudaLaunchAttribute attr;
   std::memset(&attr, 0, sizeof(attr));

@@ -190,6 +190,7 @@ struct ContractPlan {
   int tune_split = 0;     // FP64 split-K: 1 off, 2 as many parts as allowed
   int tune_oz_bn = 0;     // split-precision tile width: 64 or 128
   int tune_oz_split = 0;  // split-precision split-K: 1 off, 2 as many parts as allowed
+  int tune_oz_img = 0;    // split-precision prep keeps chunks in shared memory: 1 off, 2 on
   size_t ws_base = 0;     // workspace bytes of the permuted operands and C~ (before GEMM scratch)
   // Complex tensors in a split-precision mode: C = A B runs as the four real products
   // Re A Re B, Im A Im B, Re A Im B, Im A Re B of the real plan `re`, on de-interleaved copies of

@@ -130,3 +130,19 @@ def test_fp64_probe_argument_checks(hctx):
     with pytest.raises(api.TKError) as e:
         api.probe_fp64_peak(hctx, seconds=31.0)
     assert e.value.code == TK_ERR_ARG
+
+
+def test_set_choice_takes_only_autotuner_values(hctx):
+    """tk_plan_set_choice: contraction plans only, and only values tk_plan_autotune can return
+    (64 prep + 8 fp64 + split, with fp64 and split in 0..4 and prep in 0..2); a valid value on a
+    host-only context stops at the device check."""
+    t, b, u = _empty_and_full(hctx)
+    cp = api.compose_plan(hctx, t, b)
+    pf = api.permute_plan(hctx, u, (1, 0), (2,))
+    lib = _abi.load()
+    for bad in (-1, 5, 8 * 5, 64 * 3, 64 * 2 + 8 * 4 + 5):
+        assert lib.tk_plan_set_choice(hctx._h, cp._h, bad) == TK_ERR_ARG
+    assert lib.tk_plan_set_choice(hctx._h, pf._h, 0) == TK_ERR_ARG
+    with pytest.raises(api.TKError) as e:
+        api.set_choice(hctx, cp, fp64=4, split=4, prep=2)
+    assert e.value.code == TK_ERR_NO_DEVICE

@@ -155,6 +155,73 @@ def _elementwise_bound_check(oa, xa, ob, xb, cs, ref, got, factor):
         assert np.all(err <= bound)
 
 
+PREP_CASES = [
+    # (A legs, B legs): one k-chunk per CTA; several chunks of a deep tile per CTA (K = 5000, up
+    # to eight CTAs per tile, so CTAs own two chunks in images and more straight from L2); ragged
+    # rows, columns and inner dimensions throughout
+    (([({0: 130, 1: 20}, False)], [({0: 100, 1: 9}, False)]),
+     ([({0: 100, 1: 9}, False)], [({0: 140, 1: 33}, False)])),
+    (([({0: 300, 1: 7}, False)], [({0: 5000, 1: 3}, False)]),
+     ([({0: 5000, 1: 3}, False)], [({0: 200, 1: 5}, False)])),
+]
+
+
+@pytest.mark.parametrize("gemm,tol", [("ozaki", SPLIT_TOL), ("tf32x3", 2e-5)])
+@pytest.mark.parametrize("case", range(len(PREP_CASES)))
+def test_prep_chunk_images_leave_the_result_unchanged(gctx, gemm, tol, case):
+    """The operand preparation with and without its k-chunks kept in shared memory (the two
+    settings the autotuner chooses between, pinned with tk_plan_set_choice) writes the same slices,
+    so the products agree bit for bit, and both match the oracle."""
+    api = _api()
+    la, lb = PREP_CASES[case]
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    xa, xb = wl.normal(31, oa.numel), wl.normal(32, ob.numel)
+    cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
+    A, B = _tm(gctx, "U1", la), _tm(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), gemm=gemm)
+    da, db = torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda()
+    out = []
+    for prep in (1, 2):
+        api.set_choice(gctx, plan, prep=prep)
+        out.append(_run(gctx, plan, da, db))
+    assert torch.equal(out[0], out[1])
+    assert rel_frobenius_per_block(cs, out[1].cpu().numpy(), ref) <= tol
+
+
+@pytest.mark.parametrize("gemm", ["ozaki", "tf32x3"])
+def test_identity_product_shows_the_operand_split(gctx, gemm):
+    """C = A I: with every B entry 0 or 1 (column scale 2, one digit 1/2, no TF32 remainder) the
+    result is A's split representation itself, so the split's own error shows element by element.
+    Ozaki BF16 (six digits): within (2^-43 + 2^-46) of the row's power-of-two scale, below
+    2^-41 max|a_m.|.  3xTF32: hi + lo within 2^-23 |a| of a, plus one FP32 rounding of their sum in
+    the accumulator, below 2^-21 |a|.  Entries spread over 2^+-20 inside each row, ragged tiles
+    (M = 300, K = N = 100 in the wide sector; the 9-wide sector runs as double-float rows)."""
+    api = _api()
+    la = ([({0: 300, 1: 20}, False)], [({0: 100, 1: 9}, False)])
+    lb = ([({0: 100, 1: 9}, False)], [({0: 100, 1: 9}, False)])
+    oa, ob = ostruct("U1", la), ostruct("U1", lb)
+    rng = np.random.default_rng(21)
+    xa = wl.normal(9, oa.numel) * np.exp2(rng.integers(-20, 21, oa.numel).astype(float))
+    xb = np.zeros(ob.numel)
+    for _c, rows, cols, off in ob.blocks:
+        assert rows == cols
+        xb[off + np.arange(rows) * (rows + 1)] = 1.0
+    cs, ref = ops.contract(oa, xa, (0,), (1,), ob, xb, (0,), (1,), (0,), (1,), tier="block")
+    A, B = _tm(gctx, "U1", la), _tm(gctx, "U1", lb)
+    plan = api.contract_plan(gctx, A, (0,), (1,), B, (0,), (1,), (0,), (1,), gemm=gemm)
+    assert plan.tensor_flops > 0  # the wide sector is on the tensor-core path
+    got = _run(gctx, plan, torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda()).cpu().numpy()
+    for _c, rows, cols, off in cs.blocks:
+        r = ref[off:off + rows * cols].reshape(cols, rows).T
+        g = got[off:off + rows * cols].reshape(cols, rows).T
+        if gemm == "ozaki":
+            bound = 2.0 ** (-41) * np.abs(r).max(axis=1)[:, None]
+        else:
+            bound = 2.0 ** (-21) * np.abs(r)
+        assert np.all(np.abs(g - r) <= bound)
+        assert np.any(g != r)  # the split is not exact for these entries: the bound is what holds
+
+
 @pytest.mark.parametrize("gemm,factor", [("ozaki", 8 * 2.0 ** (-42)), ("tf32x3", 2.0 ** (-17))])
 @pytest.mark.parametrize("ea,eb", [(500, -500), (-600, -400), (600, 300)])
 def test_scales_outside_the_fast_epilogue_range(gctx, ea, eb, gemm, factor):
