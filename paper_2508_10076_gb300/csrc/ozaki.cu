@@ -491,8 +491,8 @@ __device__ __forceinline__ void slice_tile(const OzPrepSeg& g, const OzSector& s
 //      group's first CTA writes it for the GEMM's epilogue.  A second cluster barrier keeps every
 //      CTA's shared memory alive until the others have read it.
 //   3. Every CTA slices its own k-chunks, re-reading them (now from L2).  In a launch with chunk
-//      images (P.img: launches whose CTAs own one to three chunks) step 1 also keeps the CTA's
-//      first two chunks in shared memory, and step 3 slices those from there.
+//      images (P.img, set per launch by the plan) step 1 also keeps the CTA's first two chunks in
+//      shared memory, and step 3 slices those from there.
 // The operands are read from HBM once instead of twice (a separate scale pass), and the scales
 // need no initial fill.  The first CTA of each request also clears the GEMM's split-K counters.
 template <int MODE, int NSEG, int S>
